@@ -1,0 +1,270 @@
+"""Python handle on the FP64 CPU oracle (``oracle/sph_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` import this package.  The library under
+``paper_2305_13380_gb300/`` never imports it and shares no code with it.
+
+The oracle computes the SPH sums of SWIFT (Schaller et al. 2024) Sec. 3.1-3.2
+straight from their definitions in double precision; see the header of
+``sph_oracle.c`` for the readings of the paper it takes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sph_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+GAMMA_K = 1.825742  # H/h of the 3-D cubic spline (Dehnen & Aly 2012 convention)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+class _Particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("L", C.c_double)] + [
+        (k, C.c_void_p) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u")]
+
+
+class _Config(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("eta", C.c_double), ("alpha_v", C.c_double),
+                ("beta_v", C.c_double), ("eps_balsara", C.c_double), ("h_tol", C.c_double),
+                ("max_iter", C.c_int32), ("brute", C.c_int32)]
+
+
+_DENS_F = ("h", "rho", "drho_dh", "n_hat", "dn_dh", "div_v", "curl_x", "curl_y", "curl_z",
+           "curl_norm", "f", "P", "c", "B")
+_DENS_I = ("n_ngb", "n_iter")
+
+
+class _DensOut(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in _DENS_F + _DENS_I]
+
+
+class _DensState(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("h", "rho", "f", "P", "c", "B")]
+
+
+_FORCE_F = ("ax", "ay", "az", "du_dt", "v_sig")
+
+
+class _ForceOut(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in _FORCE_F + ("n_pairs",)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        L.oracle_w.restype = C.c_double
+        L.oracle_w.argtypes = [C.c_double]
+        L.oracle_dw_dq.restype = C.c_double
+        L.oracle_dw_dq.argtypes = [C.c_double]
+        L.oracle_gamma_k.restype = C.c_double
+        L.oracle_wrap.restype = C.c_double
+        L.oracle_wrap.argtypes = [C.c_double, C.c_double]
+        L.oracle_cell_coord.restype = C.c_int32
+        L.oracle_cell_coord.argtypes = [C.c_double, C.c_double, C.c_int32]
+        L.oracle_build_cells.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_double, C.c_int32, C.c_void_p, C.c_void_p]
+        L.oracle_density.argtypes = [C.POINTER(_Particles), C.POINTER(_Config), C.c_void_p,
+                                     C.c_int64, C.c_void_p, C.POINTER(_DensOut)]
+        L.oracle_density_at.argtypes = [C.POINTER(_Particles), C.POINTER(_Config), C.c_void_p,
+                                        C.c_int64, C.c_void_p, C.POINTER(_DensOut)]
+        L.oracle_force.argtypes = [C.POINTER(_Particles), C.POINTER(_Config),
+                                   C.POINTER(_DensState), C.c_int64, C.c_void_p,
+                                   C.POINTER(_ForceOut)]
+        L.oracle_neighbours.argtypes = [C.POINTER(_Particles), C.c_int64, C.c_void_p, C.c_void_p,
+                                        C.c_int32, C.c_int64, C.c_void_p, C.c_void_p]
+        L.oracle_step.argtypes = [C.c_int64, C.c_double, C.POINTER(_Config), C.c_double] + \
+            [C.c_void_p] * 14 + [C.c_void_p, C.POINTER(C.c_double)]
+        _lib = L
+    return _lib
+
+
+@dataclass
+class Physics:
+    """Physical constants of the "Minimal" SPH flavour (Sec. 3.2)."""
+    gamma: float = 5.0 / 3.0
+    eta: float = 1.2348
+    alpha_v: float = 0.8
+    beta_v: float = 3.0
+    eps_balsara: float = 1e-4
+    h_tol: float = 1e-13
+    max_iter: int = 200
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class _Keep:
+    """Keeps the float64 copies alive for the duration of a call."""
+
+    def __init__(self):
+        self.items = []
+
+    def __call__(self, a):
+        a = _d(a)
+        self.items.append(a)
+        return _ptr(a)
+
+
+def _particles(keep, p):
+    n = int(np.asarray(p["x"]).shape[0])
+    return _Particles(n, float(p["L"]), *[keep(p[k]) for k in
+                                          ("x", "y", "z", "vx", "vy", "vz", "m", "u")])
+
+
+def _config(phys: Physics, brute: bool):
+    return _Config(phys.gamma, phys.eta, phys.alpha_v, phys.beta_v, phys.eps_balsara,
+                   phys.h_tol, phys.max_iter, 1 if brute else 0)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def w(q: float) -> float:
+    return lib().oracle_w(float(q))
+
+
+def dw_dq(q: float) -> float:
+    return lib().oracle_dw_dq(float(q))
+
+
+def cell_coord(x: float, L: float, n_c: int) -> int:
+    return lib().oracle_cell_coord(float(x), float(L), int(n_c))
+
+
+def wrap(x: float, L: float) -> float:
+    return lib().oracle_wrap(float(x), float(L))
+
+
+def build_cells(x, y, z, L: float, n_c: int):
+    """Stable counting sort of particles into the n_c^3 cell grid (Sec. 2.1)."""
+    keep = _Keep()
+    n = int(np.asarray(x).shape[0])
+    cell_start = np.zeros(n_c ** 3 + 1, dtype=np.int32)
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().oracle_build_cells(n, keep(x), keep(y), keep(z), float(L), int(n_c),
+                                    _ptr(cell_start), _ptr(perm)), "build_cells")
+    return cell_start, perm[:n]
+
+
+def density(p: dict, h0, targets=None, phys: Physics = Physics(), brute: bool = False) -> dict:
+    """Density loop + smoothing-length solve for the given targets (all by default).
+
+    ``p`` holds x, y, z, vx, vy, vz, m, u (length n) and the box side L;
+    ``h0`` the starting guess of h for all n particles."""
+    keep = _Keep()
+    P = _particles(keep, p)
+    n = P.n
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else int(tg.shape[0])
+    out = {k: np.zeros(nt) for k in _DENS_F}
+    out.update({k: np.zeros(nt, dtype=np.int32) for k in _DENS_I})
+    D = _DensOut(*[_ptr(out[k]) for k in _DENS_F + _DENS_I])
+    cfg = _config(phys, brute)
+    _check(lib().oracle_density(C.byref(P), C.byref(cfg), keep(h0), nt, _ptr(tg), C.byref(D)),
+           "density")
+    return out
+
+
+def density_at(p: dict, h_t, targets=None, phys: Physics = Physics(),
+               brute: bool = False) -> dict:
+    """Density-loop sums at the given smoothing length h_t[t] of each target (no solve)."""
+    keep = _Keep()
+    P = _particles(keep, p)
+    n = P.n
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else int(tg.shape[0])
+    out = {k: np.zeros(nt) for k in _DENS_F}
+    out.update({k: np.zeros(nt, dtype=np.int32) for k in _DENS_I})
+    D = _DensOut(*[_ptr(out[k]) for k in _DENS_F + _DENS_I])
+    cfg = _config(phys, brute)
+    _check(lib().oracle_density_at(C.byref(P), C.byref(cfg), keep(h_t), nt, _ptr(tg),
+                                   C.byref(D)), "density_at")
+    return out
+
+
+def force(p: dict, state: dict, targets=None, phys: Physics = Physics(),
+          brute: bool = False) -> dict:
+    """Force loop for the given targets; ``state`` holds h, rho, f, P, c, B for all n."""
+    keep = _Keep()
+    P = _particles(keep, p)
+    n = P.n
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else int(tg.shape[0])
+    S = _DensState(*[keep(state[k]) for k in ("h", "rho", "f", "P", "c", "B")])
+    out = {k: np.zeros(nt) for k in _FORCE_F}
+    out["n_pairs"] = np.zeros(nt, dtype=np.int32)
+    F = _ForceOut(*[_ptr(out[k]) for k in _FORCE_F + ("n_pairs",)])
+    cfg = _config(phys, brute)
+    _check(lib().oracle_force(C.byref(P), C.byref(cfg), C.byref(S), nt, _ptr(tg), C.byref(F)),
+           "force")
+    return out
+
+
+def neighbours(p: dict, targets, R, brute: bool = False, cap: int = 4096):
+    """Indices j != t with minimum-image distance < R[t], per target (list of arrays)."""
+    keep = _Keep()
+    P = _particles(keep, p)
+    tg = np.ascontiguousarray(targets, dtype=np.int64)
+    Rr = np.ascontiguousarray(R, dtype=np.float64)
+    nt = int(tg.shape[0])
+    nbr = np.zeros(nt * cap, dtype=np.int32)
+    cnt = np.zeros(nt, dtype=np.int64)
+    _check(lib().oracle_neighbours(C.byref(P), nt, _ptr(tg), _ptr(Rr), 1 if brute else 0, cap,
+                                   _ptr(nbr), _ptr(cnt)), "neighbours")
+    if np.any(cnt > cap):
+        raise RuntimeError("neighbour capacity exceeded")
+    return [np.sort(nbr[t * cap:t * cap + cnt[t]]) for t in range(nt)]
+
+
+def density_force(p: dict, h0, phys: Physics = Physics(), brute: bool = False):
+    """Density then force on every particle; returns (density dict, force dict)."""
+    d = density(p, h0, None, phys, brute)
+    f = force(p, d, None, phys, brute)
+    return d, f
+
+
+def step(s: dict, cfl: float, phys: Physics = Physics(), brute: bool = False) -> float:
+    """One KDK step in place on the state dict s (x, y, z, vx, vy, vz, m, u, h,
+    ax, ay, az, du_dt, v_sig, L); returns dt.  s must hold float64 arrays."""
+    for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "ax", "ay", "az", "du_dt", "v_sig"):
+        if not (isinstance(s[k], np.ndarray) and s[k].dtype == np.float64 and s[k].flags.c_contiguous):
+            s[k] = _d(s[k])
+    n = int(s["x"].shape[0])
+    cfg = _config(phys, brute)
+    rho = np.zeros(n)
+    dt = C.c_double(0.0)
+    args = [_ptr(s[k]) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "ax", "ay", "az",
+                                 "du_dt", "v_sig")]
+    _check(lib().oracle_step(n, float(s["L"]), C.byref(cfg), float(cfl), *args, _ptr(rho),
+                             C.byref(dt)), "step")
+    s["rho"] = rho
+    return dt.value

@@ -1,0 +1,154 @@
+"""Pins of the oracle's density loop and smoothing-length solve
+(Sec. 3.1.1-3.1.2, eqs. "numberdensity", "partition", "eos", "balsara")."""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+from paper_2305_13380_gb300 import inputs
+
+ETA = 1.2348
+
+
+def _shells(orc, kmax=4):
+    k = np.arange(-kmax, kmax + 1)
+    K = np.array(np.meshgrid(k, k, k, indexing="ij")).reshape(3, -1).T
+    return np.sqrt((K ** 2).sum(1))
+
+
+def _lattice_s(orc):
+    """h/d of a perfect cubic lattice: the root of sum_k w(|k| / (gamma_K s)) =
+    (gamma_K eta)^3 over the lattice vectors, found by scipy's brentq."""
+    r = _shells(orc)
+    g = orc.GAMMA_K
+
+    def F(s):
+        return sum(orc.w(ri / (g * s)) for ri in r) - (g * ETA) ** 3
+    return brentq(F, 1.0, 1.6, xtol=1e-15, rtol=1e-15)
+
+
+def test_lattice_closed_form(orc):
+    s = _lattice_s(orc)
+    assert s == pytest.approx(1.2331490390680, abs=2e-13)  # value in tests/golden
+    n = 10
+    p = inputs.lattice(n, jitter=0.0, sigma_v=0.0, u_noise=0.0)
+    d = orc.density(p, p["h0"])
+    assert np.allclose(d["h"], s / n, rtol=1e-12, atol=0)
+    assert np.all(d["n_ngb"] == 57)  # shells |k|^2 <= 5
+    # rho = m n_hat, eq. "partition" holds
+    assert np.allclose(d["rho"], p["m"] * d["n_hat"], rtol=1e-13)
+    assert np.allclose(d["n_hat"] * (d["h"] / ETA) ** 3, 1.0, rtol=1e-12)
+    # at rest: no divergence, no curl
+    assert np.all(d["div_v"] == 0.0) and np.all(d["curl_norm"] == 0.0)
+
+
+def test_golden_lattice_value(orc):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "lattice_cubic_eta1.2348.txt")
+    vals = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            vals[k.strip()] = float(v)
+    assert _lattice_s(orc) == pytest.approx(vals["h_over_d"], abs=1e-13)
+    assert int(vals["n_ngb"]) == 57
+
+
+def test_root_of_partition(orc):
+    p = inputs.lattice(12, seed=4)
+    d = orc.density(p, p["h0"], targets=np.arange(0, 1728, 7))
+    t = np.arange(0, 1728, 7)
+    for e in (1e-9, -1e-9):
+        a = orc.density_at(p, d["h"] * (1 + e), targets=t)
+        val = a["n_hat"] * (a["h"] / ETA) ** 3 - 1.0
+        assert np.all(np.sign(val) == np.sign(e))
+
+
+def test_dh_derivatives_match_finite_differences(orc):
+    p = inputs.lattice(10, seed=2)
+    t = np.arange(0, 1000, 13)
+    h = np.full(t.shape, 1.3 / 10)
+    d0 = orc.density_at(p, h, targets=t)
+    dh = 1e-6 * h
+    dp = orc.density_at(p, h + dh, targets=t)
+    dm = orc.density_at(p, h - dh, targets=t)
+    fd_n = (dp["n_hat"] - dm["n_hat"]) / (2 * dh)
+    fd_r = (dp["rho"] - dm["rho"]) / (2 * dh)
+    assert np.allclose(d0["dn_dh"], fd_n, rtol=1e-6, atol=1e-6 * np.abs(fd_n).max())
+    assert np.allclose(d0["drho_dh"], fd_r, rtol=1e-6, atol=1e-6 * np.abs(fd_r).max())
+
+
+def test_grid_equals_brute_force_clustered(orc):
+    p = inputs.clustered(1500, n_spheres=3, seed=7)
+    a = orc.density(p, p["h0"], brute=False)
+    b = orc.density(p, p["h0"], brute=True)
+    # h spans two orders of magnitude in this input
+    assert a["h"].max() / a["h"].min() > 50
+    for k in ("h", "rho", "div_v", "curl_norm", "f", "B"):
+        assert np.allclose(a[k], b[k], rtol=1e-11, atol=1e-11 * np.abs(b[k]).max()), k
+    assert np.array_equal(a["n_ngb"], b["n_ngb"])
+
+
+def _linear_field(orc, A):
+    n = 12
+    p = inputs.lattice(n, jitter=0.0, sigma_v=0.0, u_noise=0.0)
+    X = np.stack([p["x"], p["y"], p["z"]], 1) - 0.5
+    V = X @ A.T
+    p["vx"], p["vy"], p["vz"] = V[:, 0].copy(), V[:, 1].copy(), V[:, 2].copy()
+    s = _lattice_s(orc)
+    H = orc.GAMMA_K * s / n
+    inner = np.where(np.all(np.abs(X) < 0.5 - 1.5 * H, axis=1))[0]
+    d = orc.density(p, p["h0"], targets=inner)
+    # S = -(1/3) sum_k r W'(r) / sum_k W(r) over the perfect lattice
+    r = _shells(orc) / n
+    Hs = orc.GAMMA_K * s / n
+    num = sum(ri * orc.dw_dq(ri / Hs) / Hs ** 4 for ri in r)
+    den = sum(orc.w(ri / Hs) / Hs ** 3 for ri in r)
+    S = -num / (3.0 * den)
+    return d, S
+
+
+def test_linear_expansion_divergence(orc):
+    lam = 0.37
+    d, S = _linear_field(orc, lam * np.eye(3))
+    assert S == pytest.approx(1.0, abs=0.05)
+    assert np.allclose(d["div_v"], 3 * lam * S, rtol=1e-10)
+    assert np.all(d["curl_norm"] < 1e-10)
+    # pure compression switches the Balsara limiter fully on
+    assert np.all(d["B"] > 0.99)
+
+
+def test_rigid_rotation_curl(orc):
+    w = np.array([0.3, -0.2, 0.5])
+    A = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+    d, S = _linear_field(orc, A)
+    assert np.all(np.abs(d["div_v"]) < 1e-10)
+    for k, comp in enumerate(("curl_x", "curl_y", "curl_z")):
+        assert np.allclose(d[comp], 2 * w[k] * S, rtol=1e-10)
+    # pure shear/rotation switches viscosity off
+    assert np.all(d["B"] < 1e-10)
+
+
+def test_galilean_invariance(orc):
+    p = inputs.lattice(10, seed=5)
+    a = orc.density(p, p["h0"])
+    q = dict(p)
+    q["vx"] = p["vx"] + 3.0
+    q["vy"] = p["vy"] - 1.5
+    b = orc.density(q, p["h0"])
+    assert np.array_equal(a["h"], b["h"])
+    for k in ("div_v", "curl_norm", "B"):
+        assert np.allclose(a[k], b[k], rtol=1e-9, atol=1e-9 * np.abs(a[k]).max())
+
+
+def test_eos_and_factors(orc):
+    p = inputs.lattice(8, seed=9)
+    d = orc.density(p, p["h0"])
+    g = 5.0 / 3.0
+    assert np.allclose(d["P"], (g - 1) * p["u"] * d["rho"], rtol=1e-14)
+    assert np.allclose(d["c"], np.sqrt(g * (g - 1) * p["u"]), rtol=1e-14)
+    # f-factor is the inverse of the grad-h term
+    assert np.allclose(1.0 / d["f"], 1 + d["h"] / (3 * d["rho"]) * d["drho_dh"], rtol=1e-13)
+    assert np.all((d["B"] >= 0) & (d["B"] <= 1))
