@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""SPH density + force throughput on GB300 (particle-updates per second).
+
+One step is one kick-drift-kick step of the whole hot path through the C ABI
+(`sph_step`): time-step reduction, half kick and drift, cell build (counting
+sort, in-cell order), density loop with the smoothing-length solve, force
+loop, second half kick.  Default workload: the 128^3 = 2,097,152-particle
+jittered lattice in a periodic unit box (FP64 positions, FP32 pair math).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (under torchrun) every rank advances its own copy of the workload
+(independent replicas: the configuration has no cross-rank exchange); value is
+the whole-job rate.  `--impl reference` times the FP64 CPU oracle on bounded
+samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH density+force particle-updates/s at 2M"
+UNIT = "particle-updates/s"
+# Flops per in-support pair of the oracle's formulas (every add, multiply,
+# divide and square root counts 1; see the design notes for the tally).
+F_DENSITY = 66
+F_FORCE = 72
+# Kernel launches of one sph_step: dt + kick/drift (2), cell build (10),
+# two gathers (2), density (1), force (1), kick (1).
+LAUNCHES_PER_STEP = 17
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="lattice128")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of oracle work for the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=120.0,
+                    help="seconds of oracle work for the whole --impl reference run")
+    return ap.parse_args()
+
+
+def make_workload(name: str) -> dict:
+    from paper_2305_13380_gb300 import inputs
+    if name.startswith("lattice"):
+        n = int(name[len("lattice"):])
+        p = inputs.lattice(n, seed=0)
+        p["desc"] = (f"jittered lattice {n}^3 = {n ** 3} particles, periodic unit box, "
+                     "jitter +-0.1 d, sigma_v = 0.01, u = 1 +- 1%, equal masses, seed 0")
+        return p
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------- clocks ---
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.strip().split(",") for ln in self.file.read().splitlines() if ln.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle ----
+def _f32(p):
+    import numpy as np
+    q = {k: p[k] for k in ("x", "y", "z", "L")}
+    for k in ("vx", "vy", "vz", "m", "u", "h0"):
+        q[k] = np.asarray(p[k], dtype=np.float32).astype(np.float64)
+    return q
+
+
+def oracle_sample(p, n_target: int, seed: int):
+    """Oracle density + force for the particles of a sub-cube holding about
+    n_target particles (the density also runs on a margin of one support
+    around it, which the force needs).  Returns (particles updated, seconds)."""
+    import numpy as np
+
+    import oracle
+    q = _f32(p)
+    L = q["L"]
+    n = len(q["x"])
+    side = L * min(1.0, (n_target / n) ** (1.0 / 3.0))
+    rng = np.random.default_rng(seed)
+    c0 = rng.uniform(0, L, 3)
+    H = 1.825742 * float(np.max(q["h0"])) * 1.1
+
+    def inside(s):
+        d = [np.abs((q[k] - c0[i] + 0.5 * L) % L - 0.5 * L) for i, k in enumerate("xyz")]
+        return np.where((d[0] < s / 2) & (d[1] < s / 2) & (d[2] < s / 2))[0]
+    core = inside(side)
+    halo = inside(side + 2 * H)
+    t0 = time.perf_counter()
+    d = oracle.density(q, q["h0"], targets=halo)
+    state = {k: np.zeros(n) for k in ("h", "rho", "f", "P", "c", "B")}
+    for k in state:
+        state[k][halo] = d[k]
+    oracle.force(q, state, targets=core)
+    return len(core), time.perf_counter() - t0
+
+
+def cpu_baseline(p, budget_s: float) -> dict:
+    import oracle
+    oracle.build()
+    # calibrate on a small sample, then size the timed sample to the budget
+    n0, t0 = oracle_sample(p, 2000, seed=1)
+    n_target = int(max(2000, min(len(p["x"]), n0 * budget_s / max(t0, 1e-3))))
+    nu, sec = oracle_sample(p, n_target, seed=2)
+    return {"value": nu / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{nu} particles of a sub-cube (density also on a one-support halo, "
+                       f"grid build over all {len(p['x'])} particles included), "
+                       f"{sec:.1f} s on 1 host core")}
+
+
+def run_reference(args, world: int, rank: int):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = make_workload(args.workload)
+    # size every sample so that the whole run stays near args.ref_budget seconds
+    n0, t0 = oracle_sample(p, 1000, seed=99)
+    per_step = args.ref_budget / max(1, args.steps + args.warmup)
+    n_target = int(max(200, min(len(p["x"]), n0 * per_step / max(t0, 1e-3))))
+    for w in range(args.warmup):
+        oracle_sample(p, n_target, seed=100 + w)
+    done, sec = 0, 0.0
+    for k in range(args.steps):
+        nu, s = oracle_sample(p, n_target, seed=1000 + k)
+        done += nu
+        sec += s
+    value = done / sec
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "desc": p["desc"],
+                       "sample": f"{n_target}-particle sub-cubes per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} sub-cubes of ~{n_target} particles"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ ours ---
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2305_13380_gb300", "csrc", kernel + ".cu")
+    try:
+        rec = json.load(open(path))[kernel]
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256") == sha:
+            return rec["bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2305_13380_gb300 import build as B
+    B.build()
+    from paper_2305_13380_gb300 import sph
+
+    p = make_workload(args.workload)
+    n = len(p["x"])
+    L = float(p["L"])
+    t = sph.to_device(p)
+    dev = "cuda"
+    f32 = lambda: torch.empty(n, dtype=torch.float32, device=dev)  # noqa: E731
+    arrays = dict(x=t["x"], y=t["y"], z=t["z"], vx=t["vx"], vy=t["vy"], vz=t["vz"], u=t["u"],
+                  m=t["m"], h=f32(), ax=f32(), ay=f32(), az=f32(), du_dt=f32(), v_sig=f32(),
+                  rho=f32(), f=f32(), div_v=f32(), curl_v=f32(), P=f32(), c=f32(), balsara=f32(),
+                  dt=torch.zeros(1, dtype=torch.float64, device=dev))
+    sim_offset = torch.tensor([0, n], dtype=torch.int64, device=dev)
+    box = torch.tensor([L], dtype=torch.float64, device=dev)
+
+    # initial density + force (untimed) through the single-simulation calls
+    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC))
+    part = sph.particles(t)
+    dout = sph.density_out({k: arrays[k] for k in sph.DENSITY_FIELDS})
+    h_in = t["h0"]
+    for _ in range(8):
+        cells = sph.sph_build_cells(init, t["x"], t["y"], t["z"], h_in)
+        try:
+            sph.sph_density(init, cells, part, h_in, dout)
+            break
+        except sph.SPHError as e:
+            if e.code != sph.SPH_E_REBUILD:
+                raise
+            h_in = arrays["h"].clone()
+    sph.sph_force(init, cells, part, dout, sph.force_out({k: arrays[k] for k in sph.FORCE_FIELDS}))
+    init.close()
+
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING))
+    pool = sph.pool(sim_offset, box, arrays)
+    for _ in range(args.warmup):
+        sph.sph_step(ctx, pool)
+    torch.cuda.synchronize()
+    st = sph.sph_status(ctx)
+    if st:
+        raise SystemExit(f"device status {st} after warm-up")
+    sph.sph_kernel_times(ctx)  # reset
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(gpu_id)
+    time.sleep(0.25)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sph.sph_step(ctx, pool)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kt = sph.sph_kernel_times(ctx)
+    st = sph.sph_status(ctx)
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * n * args.steps / (ms / 1e3)
+
+    # one more step (untimed) that counts pairs and Newton passes
+    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS))
+    arrays["n_iter"] = torch.zeros(n, dtype=torch.int32, device=dev)
+    sph.sph_step(cnt, sph.pool(sim_offset, box, arrays))
+    pairs_d, pairs_f = sph.sph_pair_counts(cnt)
+    mean_pass = float(arrays.pop("n_iter").double().mean().item())
+    cnt.close()
+
+    # end to end: state in pinned host memory, copied in and out every step
+    in_keys = ("x", "y", "z", "vx", "vy", "vz", "u", "m", "h", "ax", "ay", "az", "du_dt", "v_sig")
+    out_keys = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du_dt", "v_sig")
+    host = {k: arrays[k].cpu().pin_memory() for k in in_keys}
+    bi = sum(host[k].numel() * host[k].element_size() for k in in_keys)
+    bo = sum(host[k].numel() * host[k].element_size() for k in out_keys)
+    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L))
+    for it in range(2 + args.e2e_steps):
+        if it == 2:
+            torch.cuda.synchronize()
+            e0.record(stream)
+        for k in in_keys:
+            arrays[k].copy_(host[k], non_blocking=True)
+        sph.sph_step(e2e_ctx, pool)
+        for k in out_keys:
+            host[k].copy_(arrays[k], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value = world * n * args.e2e_steps / (e2e_ms / 1e3)
+    if sph.sph_status(e2e_ctx):
+        raise SystemExit("device status set in the end-to-end run")
+
+    # roofline of the dominant loop kernel (ALU bound: FP32 pipe, no tensor cores)
+    props = torch.cuda.get_device_properties(local)
+    peak_mhz = clk["sm_max_mhz"] or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    dens_ms = kt["density"][0] / max(kt["density"][1], 1)
+    force_ms = kt["force"][0] / max(kt["force"][1], 1)
+    if dens_ms >= force_ms:
+        kname, kms, flops = "density", dens_ms, pairs_d * mean_pass * F_DENSITY
+    else:
+        kname, kms, flops = "force", force_ms, pairs_f * F_FORCE
+    achieved = flops / (kms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"k_{kname}", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(kname),
+                "peak_basis": (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
+                               f"lanes x 2 flop x {peak_mhz:.0f} MHz (derived; no measured FP32 "
+                               "peak in MEASURED_PEAKS.json)"),
+                "flops_per_launch": flops}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, args.cpu_budget)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": p["desc"], "particles_per_gpu": n,
+                   "step": "sph_step: dt, kick+drift, cell build, density (h solve), force, kick",
+                   "l2": "inputs larger than L2: each step touches ~0.5 GB of state and scratch",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo, "steps": args.e2e_steps},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"], "samples": clk["samples"]},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "pairs_per_step": {"density_final_pass": pairs_d, "force": pairs_f,
+                           "mean_newton_passes": mean_pass},
+        "device_status": st,
+        "wall_s": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * sph.h -- C ABI of the GB300 (sm_103a) SPH neighbour-loop library.
+ *
+ * The library computes the hot path of the SPH solver of SWIFT (Schaller et
+ * al., MNRAS 2024): particles are binned into a periodic cell grid whose cells
+ * are at least the kernel support wide (Sec. 2.1, the Verlet-list grid); the
+ * density loop solves every particle's smoothing length by Newton-Raphson
+ * (Sec. 3.1.1, eqs. "numberdensity" and "partition") and accumulates the
+ * density, its h-derivative and the velocity divergence and curl (Sec. 3.1.2);
+ * the force loop then accumulates the pressure acceleration, the
+ * Balsara-switched artificial viscosity and du/dt of the "Minimal"
+ * density-energy flavour (Sec. 3.2, eqs. "densityenergy", "basicartvisc",
+ * "alpha", "nuij", "balsara"); a kick-drift-kick step with one global
+ * time-step (Sec. 2.4, operators of Sec. 5.4 with a = 1) ties them together.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers to particle data are DEVICE pointers owned by the caller; the
+ *    library never frees them.  Arrays are structure-of-arrays, indexed by the
+ *    caller's particle index ("input order").  Positions are double in
+ *    [0, L); every other per-particle array is float.
+ *  - Work is enqueued on the stream given to sph_create; calls return when the
+ *    work is enqueued unless the context was created with SPH_FLAG_SYNC, in
+ *    which case they wait for the stream and report device-side status.
+ *  - Return values: SPH_OK (0) or a negative SPH_E_* code; no call throws,
+ *    aborts or traps.  Device-side conditions (smoothing length not converged,
+ *    a support larger than the cell, ...) are OR-ed into a status word that
+ *    sph_status() returns and clears.
+ *  - Kernel: cubic spline in the Dehnen & Aly (2012) form W(r,h) = w(r/H)/H^3,
+ *    H = gamma_K h, gamma_K = 1.825742 (Sec. 3.1, eq. "kernel").
+ *  - One context per stream; a context is not thread-safe.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+enum {
+  SPH_OK = 0,
+  SPH_E_INVAL = -1,     /* bad argument (NULL pointer, negative size, ...)   */
+  SPH_E_NOMEM = -2,     /* device allocation of context scratch failed       */
+  SPH_E_H_NOCONV = -3,  /* some smoothing length did not converge            */
+  SPH_E_REBUILD = -4,   /* some support H exceeds its cell: rebuild needed   */
+  SPH_E_BOX = -5,       /* the box holds fewer than 3 cells of side max H    */
+  SPH_E_TIMEOUT = -6,   /* a bounded device wait expired                     */
+  SPH_E_CUDA = -7,      /* a CUDA runtime call failed                        */
+  SPH_E_CAPACITY = -8   /* a fixed-size limit of the library was exceeded    */
+};
+
+/* ---- device status bits (sph_status) ------------------------------------ */
+enum {
+  SPH_ST_H_NOCONV = 1,  /* Newton-Raphson hit max_h_iter                     */
+  SPH_ST_REBUILD = 2,   /* a converged H is larger than the cell size        */
+  SPH_ST_BOX = 4,       /* fewer than 3 cells per side would be needed       */
+  SPH_ST_CAPACITY = 8,  /* a cell held more particles than a kernel handles  */
+  SPH_ST_NEG_U = 16     /* a kick made some internal energy negative         */
+};
+
+/* ---- context flags ------------------------------------------------------ */
+enum {
+  SPH_FLAG_SYNC = 1,        /* wait after each call, return device status    */
+  SPH_FLAG_COUNT_PAIRS = 2, /* count in-support pairs (diagnostics, slower)  */
+  SPH_FLAG_TIMING = 4       /* record CUDA events around each kernel group   */
+};
+
+/* Kernel groups timed with SPH_FLAG_TIMING (index into sph_kernel_times). */
+enum {
+  SPH_T_BUILD = 0,      /* cell grid, keys, counting sort, in-cell order   */
+  SPH_T_GATHER = 1,     /* sorted cell-relative copies for the loops       */
+  SPH_T_DENSITY = 2,    /* density loop with the smoothing-length solve    */
+  SPH_T_FORCE = 3,      /* force loop                                      */
+  SPH_T_INTEGRATE = 4,  /* time-step reduction, kicks and drift            */
+  SPH_T_COUNT = 5
+};
+
+/* Physical and numerical parameters.  sph_default_params fills the values of
+ * the paper's "Minimal" flavour: gamma = 5/3, eta = 1.2348 (~48 neighbours),
+ * alpha_V = 0.8, beta = 3, epsilon = 1e-4 (Sec. 3.2), plus h_tol = 1e-6,
+ * max_h_iter = 30, C_CFL = 0.1 and a 5 % cell margin. */
+typedef struct sph_params {
+  double box_size;     /* side L of the periodic cubic box (> 0)                  */
+  double gamma;        /* ratio of specific heats, eq. "eos"                      */
+  double eta;          /* resolution parameter of eq. "partition"                 */
+  double alpha_v;      /* viscosity constant alpha_V, eq. "balsara"               */
+  double beta_v;       /* signal-velocity constant beta                           */
+  double eps_balsara;  /* epsilon of eq. "balsara"                                */
+  double h_tol;        /* Newton-Raphson stops when |dh| <= h_tol h               */
+  double cfl;          /* C_CFL of the global time-step                           */
+  double cell_margin;  /* cells are >= (1 + cell_margin) * gamma_K * max h        */
+  int32_t max_h_iter;  /* iteration cap of the smoothing-length solve             */
+  int32_t flags;       /* SPH_FLAG_*                                              */
+} sph_params;
+
+/* Opaque context: holds the stream, the parameters and the device scratch
+ * (cell keys, cell offsets, sorted particle copies), grown on demand. */
+typedef struct sph_ctx sph_ctx;
+
+/* Cell lists of one simulation, produced by sph_build_cells.  Device pointers
+ * into context scratch, valid until the next sph_build_cells/sph_step on the
+ * same context.  cell_start[c] .. cell_start[c+1] is the range of sorted
+ * positions of cell c = kx + n_c (ky + n_c kz); perm[s] is the input index of
+ * the particle at sorted position s; inside a cell the input indices ascend. */
+typedef struct sph_cells {
+  int64_t n;                 /* particles binned                                  */
+  int32_t n_c;               /* cells per side (host copy; needs SPH_FLAG_SYNC or
+                                sph_cells_sync, else -1)                          */
+  const int32_t* n_c_dev;    /* device: cells per side                            */
+  const int32_t* cell_start; /* device: n_c^3 + 1 offsets                         */
+  const int32_t* perm;       /* device: n                                         */
+} sph_cells;
+
+/* Input particles of one simulation (device pointers, length n). */
+typedef struct sph_particles {
+  int64_t n;
+  const double *x, *y, *z;    /* positions in [0, L)                              */
+  const float *vx, *vy, *vz;  /* velocities                                       */
+  const float *m;             /* masses                                           */
+  const float *u;             /* internal energy per unit mass                    */
+} sph_particles;
+
+/* Outputs of the density loop (device pointers, length n, input order).
+ * n_iter may be NULL. */
+typedef struct sph_density_out {
+  float *h;        /* converged smoothing length                                   */
+  float *rho;      /* density rho_i = sum_j m_j W(r_ij, h_i), self included        */
+  float *f;        /* f_i = [1 + h_i/(3 rho_i) d rho_i/dh]^-1                       */
+  float *div_v;    /* velocity divergence                                          */
+  float *curl_v;   /* norm of the velocity curl                                    */
+  float *P;        /* pressure (gamma - 1) u rho                                   */
+  float *c;        /* sound speed sqrt(gamma P / rho)                              */
+  float *balsara;  /* Balsara switch B_i                                           */
+  int32_t *n_iter; /* Newton-Raphson passes used (optional)                        */
+} sph_density_out;
+
+/* Outputs of the force loop (device pointers, length n, input order). */
+typedef struct sph_force_out {
+  float *ax, *ay, *az;  /* acceleration                                            */
+  float *du_dt;         /* internal energy rate                                    */
+  float *v_sig;         /* max_j signal velocity over neighbours                   */
+} sph_force_out;
+
+/* State of a pool of independent simulations advanced together by sph_step.
+ * All arrays are device pointers over the whole pool (length n_total);
+ * simulation s owns particles [sim_offset[s], sim_offset[s+1]) and lives in a
+ * periodic cube of side box_size[s].  a, du/dt and v_sig hold the previous
+ * force evaluation on entry (run sph_density + sph_force once to start) and
+ * the new one on exit; the density outputs are refreshed too. */
+typedef struct sph_pool {
+  int32_t n_sims;
+  int64_t n_total;
+  const int64_t* sim_offset;  /* device, n_sims + 1, ascending, [0] = 0            */
+  const double* box_size;     /* device, n_sims                                    */
+  double *x, *y, *z;          /* in/out positions                                  */
+  float *vx, *vy, *vz;        /* in/out velocities                                 */
+  float *u;                   /* in/out internal energy                            */
+  const float *m;             /* masses                                            */
+  float *h;                   /* in/out smoothing length (warm start)              */
+  float *ax, *ay, *az, *du_dt, *v_sig;             /* in/out force results         */
+  float *rho, *f, *div_v, *curl_v, *P, *c, *balsara; /* out density results        */
+  double *dt;                 /* device, n_sims: time-step taken by each sim       */
+  int32_t *n_iter;            /* optional (NULL): Newton-Raphson passes            */
+} sph_pool;
+
+void sph_default_params(sph_params* p);
+
+/* Creates a context bound to `stream` (a cudaStream_t; NULL = legacy default
+ * stream).  Allocates nothing on the device until the first call that needs
+ * scratch.  Returns SPH_E_INVAL for bad parameters. */
+int sph_create(sph_ctx** ctx, const sph_params* p, void* stream);
+void sph_destroy(sph_ctx* ctx);
+const char* sph_error_string(int code);
+
+/* Device status word accumulated since the last call (SPH_ST_* bits); waits
+ * for the context's stream, then clears the word. */
+int sph_status(sph_ctx* ctx, int32_t* status_out);
+
+/* Bins n particles into the cell grid (Sec. 2.1).  The grid has
+ * n_c = floor(L / ((1 + cell_margin) gamma_K max_i h_i)) cells per side,
+ * computed on the device; fewer than 3 sets SPH_ST_BOX (and SPH_E_BOX when
+ * synchronous).  Cell coordinates are k = floor(fl(fl(x n_c) / L)), clamped
+ * to n_c - 1 (IEEE double, round to nearest); the order inside a cell is
+ * ascending input index, so the lists are exactly reproducible. */
+int sph_build_cells(sph_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+                    const float* h, sph_cells* out);
+
+/* Waits for the stream and fills out->n_c from the device. */
+int sph_cells_sync(sph_ctx* ctx, sph_cells* cells);
+
+/* Copies the cell lists of `cells` into caller buffers (host or device;
+ * cell_start_dst holds n_c^3 + 1 entries, perm_dst holds n).  Waits for the
+ * stream; fills cells->n_c. */
+int sph_cells_copy(sph_ctx* ctx, sph_cells* cells, int32_t* cell_start_dst, int32_t* perm_dst);
+
+/* Density loop with the smoothing-length solve (Sec. 3.1).  h_in is the
+ * starting guess (may alias out->h).  Each particle's h is iterated with
+ * Newton-Raphson on n_hat(h) - (eta/h)^3, using dn_hat/dh, until the relative
+ * change is below h_tol; H is capped at the cell size (a particle that would
+ * need more sets SPH_ST_REBUILD: rebuild the cells from out->h and call
+ * again).  Sums are accumulated in FP32 on coordinates relative to the
+ * particle's cell; the convergence test runs in FP64. */
+int sph_density(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in, const float* h_in,
+                sph_density_out* out);
+
+/* Force loop (Sec. 3.2) over all pairs with r_ij < max(H_i, H_j), reading the
+ * density results d (h, rho, f, P, c, balsara; input order). */
+int sph_force(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
+              const sph_density_out* d, sph_force_out* out);
+
+/* One kick-drift-kick step of every simulation of the pool (Sec. 2.4):
+ *   dt = C_CFL min_i H_i / v_sig,i per simulation (FP64 reduction),
+ *   half kick of v and u, drift of x in FP64 with periodic wrap, prediction
+ *   of v and u for the loops, cell rebuild, density, force, half kick.
+ * n_sims = 1 is the plain path; n_sims > 1 runs every loop as one launch over
+ * all simulations.  With SPH_FLAG_SYNC, a step whose density reports
+ * SPH_ST_REBUILD is rebuilt with larger cells and repeated internally. */
+int sph_step(sph_ctx* ctx, const sph_pool* pool);
+
+/* FP64 conservation sums of a pool after a force evaluation, per simulation:
+ * out[4 s + 0..2] = sum m a, out[4 s + 3] = sum m (v . a + du/dt) with the
+ * velocities given (device array out of 4 n_sims doubles). */
+int sph_conservation(sph_ctx* ctx, const sph_pool* pool, double* out);
+
+/* With SPH_FLAG_TIMING: waits for the stream, then returns the summed device
+ * time in milliseconds (ms_out[SPH_T_COUNT]) and the number of timed launches
+ * of each group (calls_out[SPH_T_COUNT], may be NULL) since the last query,
+ * and resets both. */
+int sph_kernel_times(sph_ctx* ctx, double* ms_out, int64_t* calls_out);
+
+/* Number of pairs counted by the last density and force launches when the
+ * context has SPH_FLAG_COUNT_PAIRS (waits for the stream):
+ * out[0] = density pairs r < H_i (self included, last Newton pass),
+ * out[1] = force pairs r < max(H_i, H_j), j != i. */
+int sph_pair_counts(sph_ctx* ctx, int64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

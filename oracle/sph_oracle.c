@@ -317,18 +317,32 @@ typedef struct {      /* per target */
   int32_t *n_pairs;   /* j != i with r_ij < max(H_i, H_j) */
 } oracle_force_out;
 
-/* Median of a copy of v (for the bucket size hint). */
-static int or_cmp_d(const void* a, const void* b) {
-  double x = *(const double*)a, y = *(const double*)b;
-  return (x > y) - (x < y);
-}
+/* Median of the positive entries of v (for the bucket size hint only),
+ * by Hoare's selection. */
 static double or_median(const double* v, int64_t n) {
   if (n <= 0) return 0.0;
   double* t = (double*)malloc(sizeof(double) * (size_t)n);
-  if (!t) return v[0];
-  memcpy(t, v, sizeof(double) * (size_t)n);
-  qsort(t, (size_t)n, sizeof(double), or_cmp_d);
-  double m = t[n / 2];
+  if (!t) return 0.0;
+  int64_t k = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (v[i] > 0.0) t[k++] = v[i];
+  double m = 0.0;
+  if (k > 0) {
+    int64_t lo = 0, hi = k - 1, want = k / 2;
+    while (lo < hi) {
+      double piv = t[lo + (hi - lo) / 2];
+      int64_t i = lo, j = hi;
+      while (i <= j) {
+        while (t[i] < piv) ++i;
+        while (t[j] > piv) --j;
+        if (i <= j) { double x = t[i]; t[i] = t[j]; t[j] = x; ++i; --j; }
+      }
+      if (want <= j) hi = j;
+      else if (want >= i) lo = i;
+      else break;
+    }
+    m = t[want];
+  }
   free(t);
   return m;
 }

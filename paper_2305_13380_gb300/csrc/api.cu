@@ -1,0 +1,623 @@
+// api.cu -- the C ABI declared in include/sph.h: context and scratch
+// management, argument checks and the order of the kernel launches.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "sph_internal.cuh"
+#include "sph_launch.h"
+
+using sphk::GridDev;
+using sphk::PhysDev;
+
+struct sph_ctx {
+  sph_params p;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  int num_sms = 1;
+  // capacities of the scratch below
+  int64_t cap_n = 0;
+  int64_t cap_cells = 0;
+  int cap_sims = 0;
+  // fixed buffers
+  int32_t* misc = nullptr;
+  unsigned long long* pairs = nullptr;
+  int64_t* off1 = nullptr;  // single-simulation tables (device)
+  double* box1 = nullptr;
+  int64_t* h_off1 = nullptr;  // pinned mirrors
+  double* h_box1 = nullptr;
+  // grown buffers
+  GridDev* grid = nullptr;
+  int32_t *key = nullptr, *slot = nullptr, *count = nullptr, *cell_start = nullptr;
+  int32_t *scan_sums = nullptr, *perm = nullptr, *big = nullptr;
+  float4 *pos4 = nullptr, *vel4 = nullptr, *th4 = nullptr;
+  float *hs = nullptr, *rho_s = nullptr;
+  float *vpx = nullptr, *vpy = nullptr, *vpz = nullptr, *up = nullptr;
+  // CUDA-event timing of kernel groups (SPH_FLAG_TIMING)
+  std::vector<cudaEvent_t> ev_start[SPH_T_COUNT], ev_stop[SPH_T_COUNT];
+  int ev_used[SPH_T_COUNT] = {0, 0, 0, 0, 0};
+  double t_ms[SPH_T_COUNT] = {0, 0, 0, 0, 0};
+  int64_t t_calls[SPH_T_COUNT] = {0, 0, 0, 0, 0};
+  // last build
+  int built_sims = 0;
+  int64_t built_n = -1;
+  const int64_t* built_offset = nullptr;
+};
+
+namespace {
+
+template <class T>
+void dfree(T*& ptr) {
+  if (ptr) cudaFree((void*)ptr);
+  ptr = nullptr;
+}
+
+template <class T>
+bool dalloc(T*& ptr, int64_t count) {
+  void* v = nullptr;
+  if (cudaMalloc(&v, (size_t)(count > 0 ? count : 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+    return false;
+  }
+  ptr = (T*)v;
+  return true;
+}
+
+void free_grown(sph_ctx* c) {
+  dfree(c->grid);
+  dfree(c->key);
+  dfree(c->slot);
+  dfree(c->count);
+  dfree(c->cell_start);
+  dfree(c->scan_sums);
+  dfree(c->perm);
+  dfree(c->big);
+  dfree(c->pos4);
+  dfree(c->vel4);
+  dfree(c->th4);
+  dfree(c->hs);
+  dfree(c->rho_s);
+  dfree(c->vpx);
+  dfree(c->vpy);
+  dfree(c->vpz);
+  dfree(c->up);
+  c->cap_n = c->cap_cells = 0;
+  c->cap_sims = 0;
+}
+
+// Scratch for n particles in n_sims simulations; every simulation may use
+// up to 8 n_s + 216 cells, so the total is bounded by 8 n + 216 n_sims.
+int ensure(sph_ctx* c, int64_t n, int n_sims) {
+  const int64_t need_cells = 8 * n + 216 * (int64_t)n_sims;
+  if (n <= c->cap_n && n_sims <= c->cap_sims && need_cells <= c->cap_cells) return SPH_OK;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  free_grown(c);
+  const int64_t cn = n + n / 4 + 64;
+  const int cs = n_sims + n_sims / 4 + 1;
+  const int64_t cc = 8 * cn + 216 * (int64_t)cs;
+  bool ok = dalloc(c->grid, cs) && dalloc(c->key, cn) && dalloc(c->slot, cn) &&
+            dalloc(c->count, cc + 1) && dalloc(c->cell_start, cc + 1) &&
+            dalloc(c->scan_sums, cc / 1024 + 2) && dalloc(c->perm, cn) &&
+            dalloc(c->big, cn / (sphk::kSmallCell + 1) + 2) && dalloc(c->pos4, cn) &&
+            dalloc(c->vel4, cn) && dalloc(c->th4, cn) && dalloc(c->hs, cn) && dalloc(c->rho_s, cn) &&
+            dalloc(c->vpx, cn) && dalloc(c->vpy, cn) && dalloc(c->vpz, cn) && dalloc(c->up, cn);
+  if (!ok) {
+    free_grown(c);
+    return SPH_E_NOMEM;
+  }
+  c->cap_n = cn;
+  c->cap_sims = cs;
+  c->cap_cells = cc;
+  c->built_n = -1;
+  return SPH_OK;
+}
+
+// Folds the recorded event pairs of group k into t_ms (waits for them).
+void t_collect(sph_ctx* c, int k) {
+  for (int i = 0; i < c->ev_used[k]; ++i) {
+    float ms = 0.f;
+    cudaEventSynchronize(c->ev_stop[k][i]);
+    if (cudaEventElapsedTime(&ms, c->ev_start[k][i], c->ev_stop[k][i]) == cudaSuccess) c->t_ms[k] += ms;
+  }
+  c->ev_used[k] = 0;
+  cudaGetLastError();
+}
+
+void t_begin(sph_ctx* c, int k) {
+  if (!(c->p.flags & SPH_FLAG_TIMING)) return;
+  if (c->ev_used[k] >= 1024) t_collect(c, k);
+  const int i = c->ev_used[k];
+  if (i == (int)c->ev_start[k].size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    c->ev_start[k].push_back(a);
+    c->ev_stop[k].push_back(b);
+  }
+  cudaEventRecord(c->ev_start[k][i], c->st);
+}
+
+void t_end(sph_ctx* c, int k) {
+  if (!(c->p.flags & SPH_FLAG_TIMING)) return;
+  const int i = c->ev_used[k];
+  if (i >= (int)c->ev_stop[k].size()) return;
+  cudaEventRecord(c->ev_stop[k][i], c->st);
+  c->ev_used[k] = i + 1;
+  c->t_calls[k] += 1;
+}
+
+PhysDev phys_of(const sph_params& p) {
+  PhysDev ph;
+  ph.gamma = (float)p.gamma;
+  ph.eta3 = (float)(p.eta * p.eta * p.eta);
+  ph.alpha_v = (float)p.alpha_v;
+  ph.beta_v = (float)p.beta_v;
+  ph.eps_balsara = (float)p.eps_balsara;
+  ph.h_tol = p.h_tol;
+  ph.max_h_iter = p.max_h_iter;
+  ph.count_pairs = (p.flags & SPH_FLAG_COUNT_PAIRS) ? 1 : 0;
+  return ph;
+}
+
+int cuda_code(cudaError_t e) { return e == cudaSuccess ? SPH_OK : SPH_E_CUDA; }
+
+// Maps device status bits to the most severe return code.
+int code_of_status(int32_t s) {
+  if (s & SPH_ST_BOX) return SPH_E_BOX;
+  if (s & SPH_ST_CAPACITY) return SPH_E_CAPACITY;
+  if (s & SPH_ST_REBUILD) return SPH_E_REBUILD;
+  if (s & SPH_ST_H_NOCONV) return SPH_E_H_NOCONV;
+  return SPH_OK;
+}
+
+int read_status(sph_ctx* c, int32_t* out) {
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  int32_t s = 0;
+  if (cudaMemcpy(&s, c->misc + sphk::kStatus, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SPH_E_CUDA;
+  if (cudaMemsetAsync(c->misc + sphk::kStatus, 0, sizeof(int32_t), c->st) != cudaSuccess)
+    return SPH_E_CUDA;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  *out = s;
+  return SPH_OK;
+}
+
+int finish(sph_ctx* c) {
+  if (cudaGetLastError() != cudaSuccess) return SPH_E_CUDA;
+  if (!(c->p.flags & SPH_FLAG_SYNC)) return SPH_OK;
+  int32_t s = 0;
+  int rc = read_status(c, &s);
+  return rc != SPH_OK ? rc : code_of_status(s);
+}
+
+bool params_ok(const sph_params& p) {
+  return p.box_size > 0 && p.gamma > 1 && p.eta > 0 && p.alpha_v >= 0 && p.beta_v >= 0 &&
+         p.eps_balsara > 0 && p.h_tol > 0 && p.cfl > 0 && p.cell_margin >= 0 && p.max_h_iter > 0;
+}
+
+int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const double* box,
+             const double* x, const double* y, const double* z, const float* h) {
+  sphh::BuildArgs b;
+  b.n_sims = n_sims;
+  b.n_total = n_total;
+  b.cap_cells = 8 * n_total + 216 * (int64_t)n_sims;
+  b.num_sms = c->num_sms;
+  b.margin = c->p.cell_margin;
+  b.sim_offset = off;
+  b.box = box;
+  b.x = x;
+  b.y = y;
+  b.z = z;
+  b.h = h;
+  b.grid = c->grid;
+  b.misc = c->misc;
+  b.key = c->key;
+  b.slot = c->slot;
+  b.count = c->count;
+  b.cell_start = c->cell_start;
+  b.scan_sums = c->scan_sums;
+  b.perm = c->perm;
+  b.big = c->big;
+  t_begin(c, SPH_T_BUILD);
+  if (sphh::launch_build(b, c->st) != cudaSuccess) return SPH_E_CUDA;
+  t_end(c, SPH_T_BUILD);
+  c->built_sims = n_sims;
+  c->built_n = n_total;
+  c->built_offset = off;
+  return SPH_OK;
+}
+
+int do_density(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
+               const float* vy, const float* vz, const float* m, const float* u, const float* h_in,
+               float* h, float* rho, float* f, float* div_v, float* curl_v, float* P, float* cs,
+               float* B, int32_t* n_iter) {
+  sphh::GatherDensityArgs g;
+  g.n_total = c->built_n;
+  g.n_sims = c->built_sims;
+  g.perm = c->perm;
+  g.key = c->key;
+  g.grid = c->grid;
+  g.x = x;
+  g.y = y;
+  g.z = z;
+  g.vx = vx;
+  g.vy = vy;
+  g.vz = vz;
+  g.m = m;
+  g.u = u;
+  g.h = h_in;
+  g.pos4 = c->pos4;
+  g.vel4 = c->vel4;
+  g.hs = c->hs;
+  t_begin(c, SPH_T_GATHER);
+  if (sphh::launch_gather_density(g, c->st) != cudaSuccess) return SPH_E_CUDA;
+  t_end(c, SPH_T_GATHER);
+  if (c->p.flags & SPH_FLAG_COUNT_PAIRS)
+    if (cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+  sphh::DensityArgs d;
+  d.n_sims = c->built_sims;
+  d.num_sms = c->num_sms;
+  d.grid = c->grid;
+  d.misc_ro = c->misc;
+  d.status = c->misc + sphk::kStatus;
+  d.pairs = c->pairs;
+  d.cell_start = c->cell_start;
+  d.perm = c->perm;
+  d.pos4 = c->pos4;
+  d.vel4 = c->vel4;
+  d.hs = c->hs;
+  d.h = h;
+  d.rho = rho;
+  d.f = f;
+  d.div_v = div_v;
+  d.curl_v = curl_v;
+  d.P = P;
+  d.c = cs;
+  d.B = B;
+  d.n_iter = n_iter;
+  t_begin(c, SPH_T_DENSITY);
+  const cudaError_t e = sphh::launch_density(d, phys_of(c->p), c->st);
+  t_end(c, SPH_T_DENSITY);
+  return cuda_code(e);
+}
+
+int do_force(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
+             const float* vy, const float* vz, const float* m, const float* h, const float* rho,
+             const float* f, const float* P, const float* cs, const float* B, float* ax, float* ay,
+             float* az, float* du_dt, float* v_sig) {
+  sphh::GatherForceArgs g;
+  g.n_total = c->built_n;
+  g.n_sims = c->built_sims;
+  g.perm = c->perm;
+  g.key = c->key;
+  g.grid = c->grid;
+  g.x = x;
+  g.y = y;
+  g.z = z;
+  g.vx = vx;
+  g.vy = vy;
+  g.vz = vz;
+  g.m = m;
+  g.h = h;
+  g.rho = rho;
+  g.f = f;
+  g.P = P;
+  g.c = cs;
+  g.B = B;
+  g.pos4 = c->pos4;
+  g.vel4 = c->vel4;
+  g.th4 = c->th4;
+  g.rho_s = c->rho_s;
+  t_begin(c, SPH_T_GATHER);
+  if (sphh::launch_gather_force(g, c->st) != cudaSuccess) return SPH_E_CUDA;
+  t_end(c, SPH_T_GATHER);
+  if (c->p.flags & SPH_FLAG_COUNT_PAIRS)
+    if (cudaMemsetAsync(c->pairs + 1, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+  sphh::ForceArgs a;
+  a.n_sims = c->built_sims;
+  a.num_sms = c->num_sms;
+  a.grid = c->grid;
+  a.misc_ro = c->misc;
+  a.pairs = c->pairs + 1;
+  a.cell_start = c->cell_start;
+  a.perm = c->perm;
+  a.pos4 = c->pos4;
+  a.vel4 = c->vel4;
+  a.th4 = c->th4;
+  a.rho_s = c->rho_s;
+  a.ax = ax;
+  a.ay = ay;
+  a.az = az;
+  a.du_dt = du_dt;
+  a.v_sig = v_sig;
+  t_begin(c, SPH_T_FORCE);
+  const cudaError_t e = sphh::launch_force(a, phys_of(c->p), c->st);
+  t_end(c, SPH_T_FORCE);
+  return cuda_code(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+void sph_default_params(sph_params* p) {
+  if (!p) return;
+  p->box_size = 1.0;
+  p->gamma = 5.0 / 3.0;
+  p->eta = 1.2348;
+  p->alpha_v = 0.8;
+  p->beta_v = 3.0;
+  p->eps_balsara = 1e-4;
+  p->h_tol = 1e-6;
+  p->cfl = 0.1;
+  p->cell_margin = 0.05;
+  p->max_h_iter = 30;
+  p->flags = 0;
+}
+
+int sph_create(sph_ctx** out, const sph_params* p, void* stream) {
+  if (!out || !p) return SPH_E_INVAL;
+  *out = nullptr;
+  if (!params_ok(*p)) return SPH_E_INVAL;
+  sph_ctx* c = new (std::nothrow) sph_ctx();
+  if (!c) return SPH_E_NOMEM;
+  c->p = *p;
+  c->st = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return SPH_E_CUDA;
+  }
+  bool ok = dalloc(c->misc, sphk::kMiscWords) && dalloc(c->pairs, 2) && dalloc(c->off1, 2) &&
+            dalloc(c->box1, 1);
+  if (ok) ok = cudaMallocHost((void**)&c->h_off1, 2 * sizeof(int64_t)) == cudaSuccess &&
+               cudaMallocHost((void**)&c->h_box1, sizeof(double)) == cudaSuccess;
+  if (ok) ok = cudaMemsetAsync(c->misc, 0, sphk::kMiscWords * sizeof(int32_t), c->st) == cudaSuccess &&
+               cudaMemsetAsync(c->pairs, 0, 2 * sizeof(unsigned long long), c->st) == cudaSuccess;
+  if (!ok) {
+    sph_destroy(c);
+    return SPH_E_NOMEM;
+  }
+  c->h_off1[0] = 0;
+  c->h_off1[1] = -1;
+  c->h_box1[0] = -1.0;
+  *out = c;
+  return SPH_OK;
+}
+
+void sph_destroy(sph_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  for (int k = 0; k < SPH_T_COUNT; ++k) {
+    for (cudaEvent_t e : c->ev_start[k]) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_stop[k]) cudaEventDestroy(e);
+  }
+  free_grown(c);
+  dfree(c->misc);
+  dfree(c->pairs);
+  dfree(c->off1);
+  dfree(c->box1);
+  if (c->h_off1) cudaFreeHost(c->h_off1);
+  if (c->h_box1) cudaFreeHost(c->h_box1);
+  cudaGetLastError();
+  delete c;
+}
+
+const char* sph_error_string(int code) {
+  switch (code) {
+    case SPH_OK: return "ok";
+    case SPH_E_INVAL: return "invalid argument";
+    case SPH_E_NOMEM: return "device allocation failed";
+    case SPH_E_H_NOCONV: return "smoothing length did not converge";
+    case SPH_E_REBUILD: return "kernel support larger than the cell: rebuild the cells";
+    case SPH_E_BOX: return "box holds fewer than 3 cells of the largest support";
+    case SPH_E_TIMEOUT: return "bounded device wait expired";
+    case SPH_E_CUDA: return "CUDA runtime error";
+    case SPH_E_CAPACITY: return "fixed-size library limit exceeded";
+    default: return "unknown error";
+  }
+}
+
+int sph_status(sph_ctx* c, int32_t* status_out) {
+  if (!c || !status_out) return SPH_E_INVAL;
+  return read_status(c, status_out);
+}
+
+int sph_build_cells(sph_ctx* c, int64_t n, const double* x, const double* y, const double* z,
+                    const float* h, sph_cells* out) {
+  if (!c || !out || n < 0 || n > INT32_MAX / 16) return SPH_E_INVAL;
+  if (n > 0 && (!x || !y || !z || !h)) return SPH_E_INVAL;
+  int rc = ensure(c, n, 1);
+  if (rc != SPH_OK) return rc;
+  if (c->h_off1[1] != n || c->h_box1[0] != c->p.box_size) {
+    // the pinned mirrors may still feed an earlier copy: wait before rewriting
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+    c->h_off1[0] = 0;
+    c->h_off1[1] = n;
+    c->h_box1[0] = c->p.box_size;
+    if (cudaMemcpyAsync(c->off1, c->h_off1, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->box1, c->h_box1, sizeof(double), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+  }
+  rc = do_build(c, 1, n, c->off1, c->box1, x, y, z, h);
+  if (rc != SPH_OK) return rc;
+  out->n = n;
+  out->n_c = -1;
+  out->n_c_dev = &c->grid[0].n_c;
+  out->cell_start = c->cell_start;
+  out->perm = c->perm;
+  rc = finish(c);
+  if (rc == SPH_OK && (c->p.flags & SPH_FLAG_SYNC)) return sph_cells_sync(c, out);
+  return rc;
+}
+
+int sph_cells_sync(sph_ctx* c, sph_cells* cells) {
+  if (!c || !cells || !cells->n_c_dev) return SPH_E_INVAL;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  int32_t nc = -1;
+  if (cudaMemcpy(&nc, cells->n_c_dev, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SPH_E_CUDA;
+  cells->n_c = nc;
+  return SPH_OK;
+}
+
+int sph_cells_copy(sph_ctx* c, sph_cells* cells, int32_t* cell_start_dst, int32_t* perm_dst) {
+  if (!c || !cells || !cell_start_dst || (!perm_dst && cells->n > 0)) return SPH_E_INVAL;
+  int rc = sph_cells_sync(c, cells);
+  if (rc != SPH_OK) return rc;
+  const int64_t nc = cells->n_c;
+  if (nc < 1) return SPH_E_INVAL;
+  if (cudaMemcpy(cell_start_dst, cells->cell_start, (size_t)(nc * nc * nc + 1) * sizeof(int32_t),
+                 cudaMemcpyDefault) != cudaSuccess)
+    return SPH_E_CUDA;
+  if (cells->n > 0 &&
+      cudaMemcpy(perm_dst, cells->perm, (size_t)cells->n * sizeof(int32_t), cudaMemcpyDefault) !=
+          cudaSuccess)
+    return SPH_E_CUDA;
+  return SPH_OK;
+}
+
+int sph_density(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const float* h_in,
+                sph_density_out* out) {
+  if (!c || !cells || !in || !out) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1) return SPH_E_INVAL;
+  if (in->n == 0) return SPH_OK;
+  if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !in->u || !h_in ||
+      !out->h || !out->rho || !out->f || !out->div_v || !out->curl_v || !out->P || !out->c ||
+      !out->balsara)
+    return SPH_E_INVAL;
+  int rc = do_density(c, in->x, in->y, in->z, in->vx, in->vy, in->vz, in->m, in->u, h_in, out->h,
+                      out->rho, out->f, out->div_v, out->curl_v, out->P, out->c, out->balsara,
+                      out->n_iter);
+  return rc != SPH_OK ? rc : finish(c);
+}
+
+int sph_force(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
+              sph_force_out* out) {
+  if (!c || !cells || !in || !d || !out) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1) return SPH_E_INVAL;
+  if (in->n == 0) return SPH_OK;
+  if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !d->h || !d->rho ||
+      !d->f || !d->P || !d->c || !d->balsara || !out->ax || !out->ay || !out->az || !out->du_dt ||
+      !out->v_sig)
+    return SPH_E_INVAL;
+  int rc = do_force(c, in->x, in->y, in->z, in->vx, in->vy, in->vz, in->m, d->h, d->rho, d->f, d->P,
+                    d->c, d->balsara, out->ax, out->ay, out->az, out->du_dt, out->v_sig);
+  return rc != SPH_OK ? rc : finish(c);
+}
+
+int sph_step(sph_ctx* c, const sph_pool* pl) {
+  if (!c || !pl || pl->n_sims < 1 || pl->n_total < 0 || pl->n_total > INT32_MAX / 16) return SPH_E_INVAL;
+  if (!pl->sim_offset || !pl->box_size || !pl->dt) return SPH_E_INVAL;
+  if (pl->n_total > 0 &&
+      (!pl->x || !pl->y || !pl->z || !pl->vx || !pl->vy || !pl->vz || !pl->u || !pl->m || !pl->h ||
+       !pl->ax || !pl->ay || !pl->az || !pl->du_dt || !pl->v_sig || !pl->rho || !pl->f ||
+       !pl->div_v || !pl->curl_v || !pl->P || !pl->c || !pl->balsara))
+    return SPH_E_INVAL;
+  int rc = ensure(c, pl->n_total, pl->n_sims);
+  if (rc != SPH_OK) return rc;
+  sphh::StepArgs s;
+  s.n_sims = pl->n_sims;
+  s.n_total = pl->n_total;
+  s.num_sms = c->num_sms;
+  s.sim_offset = pl->sim_offset;
+  s.box = pl->box_size;
+  s.cfl = c->p.cfl;
+  s.x = pl->x;
+  s.y = pl->y;
+  s.z = pl->z;
+  s.vx = pl->vx;
+  s.vy = pl->vy;
+  s.vz = pl->vz;
+  s.u = pl->u;
+  s.m = pl->m;
+  s.h = pl->h;
+  s.ax = pl->ax;
+  s.ay = pl->ay;
+  s.az = pl->az;
+  s.du_dt = pl->du_dt;
+  s.v_sig = pl->v_sig;
+  s.vpx = c->vpx;
+  s.vpy = c->vpy;
+  s.vpz = c->vpz;
+  s.up = c->up;
+  s.dt = pl->dt;
+  s.status = c->misc + sphk::kStatus;
+  t_begin(c, SPH_T_INTEGRATE);
+  if (sphh::launch_dt(s, c->st) != cudaSuccess) return SPH_E_CUDA;
+  if (sphh::launch_kick_drift(s, c->st) != cudaSuccess) return SPH_E_CUDA;
+  t_end(c, SPH_T_INTEGRATE);
+  const bool sync = (c->p.flags & SPH_FLAG_SYNC) != 0;
+  for (int attempt = 0;; ++attempt) {
+    rc = do_build(c, pl->n_sims, pl->n_total, pl->sim_offset, pl->box_size, pl->x, pl->y, pl->z, pl->h);
+    if (rc != SPH_OK) return rc;
+    rc = do_density(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, c->up, pl->h, pl->h,
+                    pl->rho, pl->f, pl->div_v, pl->curl_v, pl->P, pl->c, pl->balsara, pl->n_iter);
+    if (rc != SPH_OK) return rc;
+    if (!sync) break;
+    int32_t st = 0;
+    rc = read_status(c, &st);
+    if (rc != SPH_OK) return rc;
+    if (!(st & SPH_ST_REBUILD) || attempt >= 8) {
+      const int code = code_of_status(st);
+      if (code != SPH_OK) return code;
+      break;
+    }
+    // h now holds the capped values; the next build sizes the cells from
+    // them with the margin, which makes every cell larger.
+  }
+  rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P,
+                pl->c, pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig);
+  if (rc != SPH_OK) return rc;
+  t_begin(c, SPH_T_INTEGRATE);
+  if (sphh::launch_kick(s, c->st) != cudaSuccess) return SPH_E_CUDA;
+  t_end(c, SPH_T_INTEGRATE);
+  return finish(c);
+}
+
+int sph_conservation(sph_ctx* c, const sph_pool* pl, double* out) {
+  if (!c || !pl || !out || pl->n_sims < 1 || !pl->sim_offset) return SPH_E_INVAL;
+  if (pl->n_total > 0 && (!pl->m || !pl->vx || !pl->vy || !pl->vz || !pl->ax || !pl->ay || !pl->az ||
+                          !pl->du_dt))
+    return SPH_E_INVAL;
+  if (sphh::launch_conservation(pl->n_sims, pl->sim_offset, pl->m, pl->vx, pl->vy, pl->vz, pl->ax,
+                                pl->ay, pl->az, pl->du_dt, out, c->st) != cudaSuccess)
+    return SPH_E_CUDA;
+  return finish(c);
+}
+
+int sph_kernel_times(sph_ctx* c, double* ms_out, int64_t* calls_out) {
+  if (!c || !ms_out) return SPH_E_INVAL;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  for (int k = 0; k < SPH_T_COUNT; ++k) {
+    t_collect(c, k);
+    ms_out[k] = c->t_ms[k];
+    if (calls_out) calls_out[k] = c->t_calls[k];
+    c->t_ms[k] = 0.0;
+    c->t_calls[k] = 0;
+  }
+  return SPH_OK;
+}
+
+int sph_pair_counts(sph_ctx* c, int64_t* out) {
+  if (!c || !out) return SPH_E_INVAL;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  unsigned long long v[2];
+  if (cudaMemcpy(v, c->pairs, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SPH_E_CUDA;
+  out[0] = (int64_t)v[0];
+  out[1] = (int64_t)v[1];
+  return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,378 @@
+// cells.cu -- cell grid construction on the device (Sec. 2.1, the Verlet-list
+// grid whose cells are at least the search radius wide).
+//
+// Pipeline (all sizes that depend on the data stay on the device, so a whole
+// step can be captured in a CUDA graph):
+//   k_grid_setup   per simulation: max h -> cells per side n_c
+//   k_grid_base    prefix of n_c^3 over simulations -> global cell ids
+//   k_key_count    FP64 cell coordinates, cell id, atomic count + arrival slot
+//   k_scan_*       exclusive scan of the counts -> cell_start
+//   k_scatter      sorted position = cell_start[key] + slot
+//   k_segsort_*    restore ascending input index inside each cell, which
+//                  makes the lists independent of the order of the atomics
+//   k_gather_*     sorted float copies relative to each particle's cell
+#include "sph_internal.cuh"
+#include "sph_launch.h"
+
+namespace sphk {
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Cells-per-side bound of a simulation of n particles: n_c^3 <= 8 n + 216.
+__device__ __forceinline__ int32_t cap_cells_per_side(int64_t n) {
+  double lim = 8.0 * (double)n + 216.0;
+  int32_t c = (int32_t)cbrt(lim);
+  while ((double)(c + 1) * (c + 1) * (c + 1) <= lim) ++c;
+  while (c > 3 && (double)c * c * c > lim) --c;
+  return c;
+}
+
+// One block per simulation.
+__global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const double* __restrict__ box,
+                             const float* __restrict__ h, int n_sims, double margin,
+                             GridDev* __restrict__ grid, int32_t* __restrict__ misc) {
+  const int s = blockIdx.x;
+  if (s >= n_sims) return;
+  const int64_t a = sim_offset[s], b = sim_offset[s + 1];
+  float hm = 0.0f;
+  for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) hm = fmaxf(hm, h[p]);
+  __shared__ float red[32];
+  hm = warp_max(hm);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = hm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    const double L = box[s];
+    const double Hmax = kGammaKd * (double)m * (1.0 + margin);
+    const int32_t cap = cap_cells_per_side(b - a);
+    int32_t nc = cap;
+    if (Hmax > 0.0) {
+      const double t = floor(L / Hmax);
+      nc = t < (double)cap ? (int32_t)t : cap;
+    }
+    if (nc < 3) {
+      atomicOr(&misc[kStatus], SPH_ST_BOX);
+      nc = 3;
+    }
+    GridDev g;
+    g.L = L;
+    g.n_c = nc;
+    g.cell = L / (double)nc;
+    g.cell_f = (float)g.cell;
+    g.cell_base = 0;
+    g.pad = 0;
+    g.part_base = a;
+    g.n = b - a;
+    grid[s] = g;
+  }
+}
+
+__global__ void k_grid_base(GridDev* __restrict__ grid, int n_sims, int32_t* __restrict__ misc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t base = 0;
+  for (int s = 0; s < n_sims; ++s) {
+    grid[s].cell_base = (int32_t)base;
+    const int64_t nc = grid[s].n_c;
+    base += nc * nc * nc;
+  }
+  misc[kTotalCells] = (int32_t)base;
+  misc[kNumBigCells] = 0;
+}
+
+__global__ void k_zero_counts(int32_t* __restrict__ count, const int32_t* __restrict__ misc) {
+  const int32_t total = misc[kTotalCells];
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= total; c += gridDim.x * blockDim.x)
+    count[c] = 0;
+}
+
+__global__ void k_key_count(int64_t n_total, const double* __restrict__ x, const double* __restrict__ y,
+                            const double* __restrict__ z, const int64_t* __restrict__ sim_offset,
+                            int n_sims, const GridDev* __restrict__ grid, int32_t* __restrict__ key,
+                            int32_t* __restrict__ slot, int32_t* __restrict__ count) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = sim_of_particle(sim_offset, n_sims, p);
+    const GridDev G = grid[s];
+    const int32_t kx = cell_coord(x[p], G.L, G.n_c);
+    const int32_t ky = cell_coord(y[p], G.L, G.n_c);
+    const int32_t kz = cell_coord(z[p], G.L, G.n_c);
+    const int32_t k = G.cell_base + kx + G.n_c * (ky + G.n_c * kz);
+    key[p] = k;
+    slot[p] = atomicAdd(&count[k], 1);
+  }
+}
+
+// ---- exclusive scan with a device-side length ------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* total) {
+  __shared__ int32_t ws[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int32_t s = lane < kScanThreads / 32 ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    if (lane < kScanThreads / 32) ws[lane] = s;
+  }
+  __syncthreads();
+  const int32_t before = (w > 0 ? ws[w - 1] : 0) + x - v;
+  *total = ws[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+// count[0 .. total) -> out (tile-local exclusive), tile sums -> sums
+__global__ void k_scan_tiles(const int32_t* __restrict__ count, int32_t* __restrict__ out,
+                             int32_t* __restrict__ sums, const int32_t* __restrict__ misc) {
+  const int32_t total = misc[kTotalCells];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  if (base >= total) return;
+  int32_t v[kScanItems];
+  int32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t c = base + threadIdx.x * kScanItems + i;
+    v[i] = c < total ? count[c] : 0;
+    s += v[i];
+  }
+  int32_t tot;
+  int32_t run = block_exclusive_scan(s, &tot);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t c = base + threadIdx.x * kScanItems + i;
+    if (c < total) out[c] = run;
+    run += v[i];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of the tile sums; writes out[total] = grand total
+__global__ void k_scan_sums(int32_t* __restrict__ sums, int32_t* __restrict__ out,
+                            const int32_t* __restrict__ misc) {
+  const int32_t total = misc[kTotalCells];
+  const int32_t nt = (total + kScanTile - 1) / kScanTile;
+  int32_t carry = 0;
+  for (int32_t b0 = 0; b0 < nt; b0 += kScanThreads) {
+    const int32_t i = b0 + threadIdx.x;
+    const int32_t v = i < nt ? sums[i] : 0;
+    int32_t tot;
+    const int32_t ex = block_exclusive_scan(v, &tot);
+    if (i < nt) sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) out[total] = carry;
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ out, const int32_t* __restrict__ sums,
+                           const int32_t* __restrict__ misc) {
+  const int32_t total = misc[kTotalCells];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  if (base >= total) return;
+  const int32_t add = sums[blockIdx.x];
+  for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+    const int64_t c = base + i;
+    if (c < total) out[c] += add;
+  }
+}
+
+__global__ void k_scatter(int64_t n_total, const int32_t* __restrict__ key, const int32_t* __restrict__ slot,
+                          const int32_t* __restrict__ cell_start, int32_t* __restrict__ perm) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_total;
+       p += (int64_t)gridDim.x * blockDim.x)
+    perm[cell_start[key[p]] + slot[p]] = (int32_t)p;
+}
+
+// Small cells: insertion sort by one thread.  Larger cells are queued.
+__global__ void k_segsort_small(const int32_t* __restrict__ cell_start, int32_t* __restrict__ perm,
+                                int32_t* __restrict__ big, int32_t* __restrict__ misc) {
+  const int32_t total = misc[kTotalCells];
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+    const int32_t a = cell_start[c], b = cell_start[c + 1];
+    const int32_t len = b - a;
+    if (len <= 1) continue;
+    if (len > kSmallCell) {
+      big[atomicAdd(&misc[kNumBigCells], 1)] = c;
+      continue;
+    }
+    int32_t v[kSmallCell];
+    for (int32_t i = 0; i < len; ++i) v[i] = perm[a + i];
+    for (int32_t i = 1; i < len; ++i) {
+      const int32_t t = v[i];
+      int32_t j = i - 1;
+      while (j >= 0 && v[j] > t) {
+        v[j + 1] = v[j];
+        --j;
+      }
+      v[j + 1] = t;
+    }
+    for (int32_t i = 0; i < len; ++i) perm[a + i] = v[i];
+  }
+}
+
+// Larger cells: one block per cell, bitonic sort in shared memory.
+__global__ void __launch_bounds__(1024) k_segsort_big(const int32_t* __restrict__ cell_start,
+                                                      int32_t* __restrict__ perm,
+                                                      const int32_t* __restrict__ big,
+                                                      int32_t* __restrict__ misc) {
+  __shared__ int32_t v[kMaxSortCell];
+  const int32_t nbig = misc[kNumBigCells];
+  for (int32_t i = blockIdx.x; i < nbig; i += gridDim.x) {
+    const int32_t c = big[i];
+    const int32_t a = cell_start[c], len = cell_start[c + 1] - a;
+    if (len > kMaxSortCell) {
+      if (threadIdx.x == 0) atomicOr(&misc[kStatus], SPH_ST_CAPACITY);
+      continue;
+    }
+    int32_t m = 1;
+    while (m < len) m <<= 1;
+    for (int32_t k = threadIdx.x; k < m; k += blockDim.x) v[k] = k < len ? perm[a + k] : 0x7fffffff;
+    __syncthreads();
+    for (int32_t size = 2; size <= m; size <<= 1) {
+      for (int32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int32_t k = threadIdx.x; k < m; k += blockDim.x) {
+          const int32_t l = k ^ stride;
+          if (l > k) {
+            const bool up = (k & size) == 0;
+            const int32_t x = v[k], y = v[l];
+            if ((x > y) == up) {
+              v[k] = y;
+              v[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int32_t k = threadIdx.x; k < len; k += blockDim.x) perm[a + k] = v[k];
+    __syncthreads();
+  }
+}
+
+// Sorted copies for the density loop: position relative to the own cell's
+// lower corner (computed in FP64, rounded once), mass, velocity, u, h.
+__global__ void k_gather_density(int64_t n_total, const int32_t* __restrict__ perm,
+                                 const int32_t* __restrict__ key, const GridDev* __restrict__ grid,
+                                 int n_sims, const double* __restrict__ x, const double* __restrict__ y,
+                                 const double* __restrict__ z, const float* __restrict__ vx,
+                                 const float* __restrict__ vy, const float* __restrict__ vz,
+                                 const float* __restrict__ m, const float* __restrict__ u,
+                                 const float* __restrict__ h, float4* __restrict__ pos4,
+                                 float4* __restrict__ vel4, float* __restrict__ hs) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_total;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = perm[s];
+    const int32_t c = key[p];
+    const GridDev G = grid[sim_of_cell(grid, n_sims, c)];
+    const int32_t local = c - G.cell_base;
+    const int32_t kx = local % G.n_c, ky = (local / G.n_c) % G.n_c, kz = local / (G.n_c * G.n_c);
+    const float rx = (float)(x[p] - (double)kx * G.cell);
+    const float ry = (float)(y[p] - (double)ky * G.cell);
+    const float rz = (float)(z[p] - (double)kz * G.cell);
+    pos4[s] = make_float4(rx, ry, rz, m[p]);
+    vel4[s] = make_float4(vx[p], vy[p], vz[p], u[p]);
+    hs[s] = h[p];
+  }
+}
+
+// Sorted copies for the force loop: the density results of each particle
+// packed as (f P / rho^2, f, c, B), (rho, 1/H), and velocity with 1/H.
+__global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm,
+                               const int32_t* __restrict__ key, const GridDev* __restrict__ grid,
+                               int n_sims, const double* __restrict__ x, const double* __restrict__ y,
+                               const double* __restrict__ z, const float* __restrict__ vx,
+                               const float* __restrict__ vy, const float* __restrict__ vz,
+                               const float* __restrict__ m, const float* __restrict__ h,
+                               const float* __restrict__ rho, const float* __restrict__ f,
+                               const float* __restrict__ P, const float* __restrict__ c,
+                               const float* __restrict__ B, float4* __restrict__ pos4,
+                               float4* __restrict__ vel4, float4* __restrict__ th4,
+                               float* __restrict__ rho_s) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_total;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = perm[s];
+    const int32_t cc = key[p];
+    const GridDev G = grid[sim_of_cell(grid, n_sims, cc)];
+    const int32_t local = cc - G.cell_base;
+    const int32_t kx = local % G.n_c, ky = (local / G.n_c) % G.n_c, kz = local / (G.n_c * G.n_c);
+    const float rx = (float)(x[p] - (double)kx * G.cell);
+    const float ry = (float)(y[p] - (double)ky * G.cell);
+    const float rz = (float)(z[p] - (double)kz * G.cell);
+    pos4[s] = make_float4(rx, ry, rz, m[p]);
+    const float Hinv = 1.0f / (kGammaK * h[p]);
+    vel4[s] = make_float4(vx[p], vy[p], vz[p], Hinv);
+    const float r = rho[p];
+    th4[s] = make_float4(f[p] * P[p] / (r * r), f[p], c[p], B[p]);
+    rho_s[s] = r;
+  }
+}
+
+}  // namespace sphk
+
+// ---- host launchers --------------------------------------------------------
+namespace sphh {
+using namespace sphk;
+
+static int grid_for(int64_t n, int threads, int max_blocks) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+cudaError_t launch_build(const BuildArgs& a, cudaStream_t st) {
+  k_grid_setup<<<a.n_sims, 256, 0, st>>>(a.sim_offset, a.box, a.h, a.n_sims, a.margin, a.grid, a.misc);
+  k_grid_base<<<1, 32, 0, st>>>(a.grid, a.n_sims, a.misc);
+  const int zb = grid_for(a.cap_cells + 1, 256, 65535);
+  k_zero_counts<<<zb, 256, 0, st>>>(a.count, a.misc);
+  const int pb = grid_for(a.n_total, 256, 65535);
+  if (a.n_total > 0)
+    k_key_count<<<pb, 256, 0, st>>>(a.n_total, a.x, a.y, a.z, a.sim_offset, a.n_sims, a.grid, a.key,
+                                    a.slot, a.count);
+  const int64_t tiles = (a.cap_cells + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<(unsigned)(tiles > 0 ? tiles : 1), kScanThreads, 0, st>>>(a.count, a.cell_start, a.scan_sums, a.misc);
+  k_scan_sums<<<1, kScanThreads, 0, st>>>(a.scan_sums, a.cell_start, a.misc);
+  k_scan_add<<<(unsigned)(tiles > 0 ? tiles : 1), kScanThreads, 0, st>>>(a.cell_start, a.scan_sums, a.misc);
+  if (a.n_total > 0) {
+    k_scatter<<<pb, 256, 0, st>>>(a.n_total, a.key, a.slot, a.cell_start, a.perm);
+    k_segsort_small<<<grid_for(a.cap_cells, 128, 65535), 128, 0, st>>>(a.cell_start, a.perm, a.big,
+                                                                         a.misc);
+    k_segsort_big<<<a.num_sms * 2, 1024, 0, st>>>(a.cell_start, a.perm, a.big, a.misc);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_density(const GatherDensityArgs& a, cudaStream_t st) {
+  if (a.n_total <= 0) return cudaSuccess;
+  k_gather_density<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
+      a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.u, a.h,
+      a.pos4, a.vel4, a.hs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st) {
+  if (a.n_total <= 0) return cudaSuccess;
+  k_gather_force<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
+      a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.h, a.rho,
+      a.f, a.P, a.c, a.B, a.pos4, a.vel4, a.th4, a.rho_s);
+  return cudaGetLastError();
+}
+
+}  // namespace sphh

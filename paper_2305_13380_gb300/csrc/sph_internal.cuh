@@ -1,0 +1,120 @@
+// sph_internal.cuh -- device-side structures and helpers shared by the CUDA
+// translation units of the SPH library (cell build, density, force, step).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+
+namespace sphk {
+
+// H/h of the 3-D cubic spline in the Dehnen & Aly (2012) convention (Sec. 3.1).
+constexpr double kGammaKd = 1.825742;
+constexpr float kGammaK = 1.825742f;
+// Normalisation of the cubic spline with support H: w(0) = 8/pi.
+constexpr float kWNorm = 2.5464790894703255f;
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int kThreads = 32 * kWarpsPerBlock;
+
+// Cells larger than this many particles are sorted by the block-level path;
+// beyond kMaxSortCell the build reports SPH_ST_CAPACITY.
+constexpr int kSmallCell = 32;
+constexpr int kMaxSortCell = 8192;
+
+// Misc device words kept by a context.
+enum MiscSlot {
+  kStatus = 0,       // SPH_ST_* bits
+  kTotalCells = 1,   // number of cells over all simulations of the last build
+  kNumBigCells = 2,  // cells routed to the block-level sort
+  kMiscWords = 8
+};
+
+// One simulation's grid, computed on the device by the build.
+struct GridDev {
+  double L;           // periodic box side
+  double cell;        // cell side L / n_c (FP64)
+  float cell_f;       // cell side (FP32)
+  int32_t n_c;        // cells per side
+  int32_t cell_base;  // first global cell id of this simulation
+  int32_t pad;
+  int64_t part_base;  // first pool index of this simulation
+  int64_t n;          // particles in this simulation
+};
+
+// Physics constants passed by value to the loop kernels.
+struct PhysDev {
+  float gamma;
+  float eta3;        // eta^3
+  float alpha_v;
+  float beta_v;
+  float eps_balsara;
+  double h_tol;
+  int32_t max_h_iter;
+  int32_t count_pairs;
+};
+
+// Simulation owning a pool index (upper bound search over sim_offset).
+__device__ __forceinline__ int sim_of_particle(const int64_t* __restrict__ sim_offset, int n_sims,
+                                               int64_t p) {
+  int lo = 0, hi = n_sims - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (sim_offset[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Simulation owning a global cell id.
+__device__ __forceinline__ int sim_of_cell(const GridDev* __restrict__ grid, int n_sims, int32_t c) {
+  int lo = 0, hi = n_sims - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (grid[mid].cell_base <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Cell coordinate of one position component: k = floor(fl(fl(x n_c) / L)),
+// clamped to [0, n_c - 1]; both roundings are IEEE round-to-nearest.
+__device__ __forceinline__ int32_t cell_coord(double x, double L, int32_t n_c) {
+  double s = __ddiv_rn(__dmul_rn(x, (double)n_c), L);
+  int32_t k = (int32_t)floor(s);
+  k = k < 0 ? 0 : k;
+  return k > n_c - 1 ? n_c - 1 : k;
+}
+
+// Cubic spline pieces with q = r/H (Sec. 3.1): w(q) and g(q) = w'(q)/q,
+// branch-free; both vanish for q >= 1.  h_rinv = H / r is only used on the
+// outer piece (q >= 1/2), where it is finite.
+__device__ __forceinline__ void kernel_w_g(float q, float H_rinv, float& w, float& g) {
+  const float a = fmaxf(1.0f - q, 0.0f);
+  const bool inner = q < 0.5f;
+  const float w_in = kWNorm * fmaf(q * q, fmaf(6.0f, q, -6.0f), 1.0f);  // 8/pi (1 - 6q^2 + 6q^3)
+  const float w_out = 2.0f * kWNorm * a * a * a;                        // 16/pi (1 - q)^3
+  const float g_in = kWNorm * fmaf(18.0f, q, -12.0f);                   // 8/pi (18 q - 12)
+  const float g_out = -6.0f * kWNorm * a * a * H_rinv;                  // -48/pi (1-q)^2 / q
+  w = inner ? w_in : w_out;
+  g = inner ? g_in : g_out;
+}
+
+// g(q) = w'(q)/q only.
+__device__ __forceinline__ float kernel_g(float q, float H_rinv) {
+  const float a = fmaxf(1.0f - q, 0.0f);
+  const float g_in = kWNorm * fmaf(18.0f, q, -12.0f);
+  const float g_out = -6.0f * kWNorm * a * a * H_rinv;
+  return q < 0.5f ? g_in : g_out;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace sphk
+
+// Host-side launchers implemented in the .cu files.
+namespace sphh {
+struct Bufs;  // defined in api.cu
+}

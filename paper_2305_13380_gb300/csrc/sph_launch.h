@@ -1,0 +1,109 @@
+// sph_launch.h -- host-side argument records and launchers of the kernels
+// (implemented in cells.cu, density.cu, force.cu, step.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+
+namespace sphk {
+struct GridDev;
+struct PhysDev;
+}  // namespace sphk
+
+namespace sphh {
+
+struct BuildArgs {
+  int n_sims;
+  int64_t n_total;
+  int64_t cap_cells;  // upper bound of total cells (sizes count / cell_start)
+  int num_sms;
+  double margin;
+  const int64_t* sim_offset;
+  const double* box;
+  const double *x, *y, *z;
+  const float* h;
+  sphk::GridDev* grid;
+  int32_t* misc;
+  int32_t *key, *slot, *count, *cell_start, *scan_sums, *perm, *big;
+};
+cudaError_t launch_build(const BuildArgs& a, cudaStream_t st);
+
+struct GatherDensityArgs {
+  int64_t n_total;
+  int n_sims;
+  const int32_t *perm, *key;
+  const sphk::GridDev* grid;
+  const double *x, *y, *z;
+  const float *vx, *vy, *vz, *m, *u, *h;
+  float4 *pos4, *vel4;
+  float* hs;
+};
+cudaError_t launch_gather_density(const GatherDensityArgs& a, cudaStream_t st);
+
+struct GatherForceArgs {
+  int64_t n_total;
+  int n_sims;
+  const int32_t *perm, *key;
+  const sphk::GridDev* grid;
+  const double *x, *y, *z;
+  const float *vx, *vy, *vz, *m, *h, *rho, *f, *P, *c, *B;
+  float4 *pos4, *vel4, *th4;
+  float* rho_s;
+};
+cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
+
+// Outputs of the loops are written in pool order through perm.
+struct DensityArgs {
+  int n_sims;
+  int num_sms;
+  const sphk::GridDev* grid;
+  const int32_t* misc_ro;  // total cells
+  int32_t* status;
+  unsigned long long* pairs;
+  const int32_t *cell_start, *perm;
+  const float4 *pos4, *vel4;
+  const float* hs;
+  float *h, *rho, *f, *div_v, *curl_v, *P, *c, *B;
+  int32_t* n_iter;
+};
+cudaError_t launch_density(const DensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+
+struct ForceArgs {
+  int n_sims;
+  int num_sms;
+  const sphk::GridDev* grid;
+  const int32_t* misc_ro;
+  unsigned long long* pairs;
+  const int32_t *cell_start, *perm;
+  const float4 *pos4, *vel4, *th4;
+  const float* rho_s;
+  float *ax, *ay, *az, *du_dt, *v_sig;
+};
+cudaError_t launch_force(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+
+// Time integration over a pool (step.cu).
+struct StepArgs {
+  int n_sims;
+  int64_t n_total;
+  int num_sms;
+  const int64_t* sim_offset;
+  const double* box;
+  double cfl;
+  double *x, *y, *z;
+  float *vx, *vy, *vz, *u;
+  const float* m;
+  const float* h;
+  float *ax, *ay, *az, *du_dt, *v_sig;
+  float *vpx, *vpy, *vpz, *up;  // predicted velocity / energy (scratch)
+  double* dt;                   // per simulation
+  int32_t* status;
+};
+cudaError_t launch_dt(const StepArgs& a, cudaStream_t st);
+cudaError_t launch_kick_drift(const StepArgs& a, cudaStream_t st);
+cudaError_t launch_kick(const StepArgs& a, cudaStream_t st);
+cudaError_t launch_conservation(int n_sims, const int64_t* sim_offset, const float* m, const float* vx,
+                                const float* vy, const float* vz, const float* ax, const float* ay,
+                                const float* az, const float* du_dt, double* out, cudaStream_t st);
+
+}  // namespace sphh

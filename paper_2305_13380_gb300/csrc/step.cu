@@ -1,0 +1,160 @@
+// step.cu -- kick-drift-kick time integration with one global time-step per
+// simulation (Sec. 2.4 leapfrog; Sec. 5.4 kick and drift operators with the
+// scale factor a = 1, so every operator's time interval is dt), and the FP64
+// conservation sums.
+#include "sph_internal.cuh"
+#include "sph_launch.h"
+
+namespace sphk {
+
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// dt_s = C_CFL min_i H_i / v_sig,i over simulation s (one block per sim).
+// A simulation whose signal velocities are all zero gets dt = 0.
+__global__ void k_dt(const int64_t* __restrict__ sim_offset, int n_sims, double cfl,
+                     const float* __restrict__ h, const float* __restrict__ v_sig,
+                     double* __restrict__ dt, int32_t* __restrict__ status) {
+  const int s = blockIdx.x;
+  if (s >= n_sims) return;
+  double m = INFINITY;
+  for (int64_t p = sim_offset[s] + threadIdx.x; p < sim_offset[s + 1]; p += blockDim.x) {
+    const double vs = (double)v_sig[p];
+    if (vs > 0.0) m = fmin(m, kGammaKd * (double)h[p] / vs);
+  }
+  __shared__ double red[32];
+  m = warp_min_d(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmin(r, red[w]);
+    dt[s] = isinf(r) ? 0.0 : cfl * r;
+  }
+}
+
+__device__ __forceinline__ double wrap1(double x, double L) {
+  if (x < 0.0) x += L;
+  if (x >= L) x -= L;
+  return x;
+}
+
+// First half kick, drift (FP64, one periodic wrap), prediction for the loops.
+__global__ void k_kick_drift(sphh::StepArgs a) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = sim_of_particle(a.sim_offset, a.n_sims, p);
+    const double dt = a.dt[s];
+    const double L = a.box[s];
+    const float hdt = (float)(0.5 * dt);
+    const float vx = fmaf(hdt, a.ax[p], a.vx[p]);
+    const float vy = fmaf(hdt, a.ay[p], a.vy[p]);
+    const float vz = fmaf(hdt, a.az[p], a.vz[p]);
+    const float u = fmaf(hdt, a.du_dt[p], a.u[p]);
+    a.vx[p] = vx;
+    a.vy[p] = vy;
+    a.vz[p] = vz;
+    a.u[p] = u;
+    a.x[p] = wrap1(fma((double)vx, dt, a.x[p]), L);
+    a.y[p] = wrap1(fma((double)vy, dt, a.y[p]), L);
+    a.z[p] = wrap1(fma((double)vz, dt, a.z[p]), L);
+    a.vpx[p] = fmaf(hdt, a.ax[p], vx);
+    a.vpy[p] = fmaf(hdt, a.ay[p], vy);
+    a.vpz[p] = fmaf(hdt, a.az[p], vz);
+    const float up = fmaf(hdt, a.du_dt[p], u);
+    a.up[p] = up;
+    if (u < 0.0f || up < 0.0f) atomicOr(a.status, SPH_ST_NEG_U);
+  }
+}
+
+// Second half kick with the new accelerations.
+__global__ void k_kick(sphh::StepArgs a) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int s = sim_of_particle(a.sim_offset, a.n_sims, p);
+    const float hdt = (float)(0.5 * a.dt[s]);
+    a.vx[p] = fmaf(hdt, a.ax[p], a.vx[p]);
+    a.vy[p] = fmaf(hdt, a.ay[p], a.vy[p]);
+    a.vz[p] = fmaf(hdt, a.az[p], a.vz[p]);
+    const float u = fmaf(hdt, a.du_dt[p], a.u[p]);
+    a.u[p] = u;
+    if (u < 0.0f) atomicOr(a.status, SPH_ST_NEG_U);
+  }
+}
+
+// out[4 s + 0..2] = sum_i m_i a_i, out[4 s + 3] = sum_i m_i (v_i . a_i + du_i/dt)
+// in FP64, one block per simulation.
+__global__ void k_conservation(const int64_t* __restrict__ sim_offset, int n_sims,
+                               const float* __restrict__ m, const float* __restrict__ vx,
+                               const float* __restrict__ vy, const float* __restrict__ vz,
+                               const float* __restrict__ ax, const float* __restrict__ ay,
+                               const float* __restrict__ az, const float* __restrict__ du,
+                               double* __restrict__ out) {
+  const int s = blockIdx.x;
+  if (s >= n_sims) return;
+  double sx = 0, sy = 0, sz = 0, se = 0;
+  for (int64_t p = sim_offset[s] + threadIdx.x; p < sim_offset[s + 1]; p += blockDim.x) {
+    const double mi = m[p];
+    sx += mi * ax[p];
+    sy += mi * ay[p];
+    sz += mi * az[p];
+    se += mi * ((double)vx[p] * ax[p] + (double)vy[p] * ay[p] + (double)vz[p] * az[p] + du[p]);
+  }
+  __shared__ double red[4][32];
+  sx = warp_sum_d(sx);
+  sy = warp_sum_d(sy);
+  sz = warp_sum_d(sz);
+  se = warp_sum_d(se);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = sx;
+    red[1][w] = sy;
+    red[2][w] = sz;
+    red[3][w] = se;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+    out[4 * s + threadIdx.x] = t;
+  }
+}
+
+}  // namespace sphk
+
+namespace sphh {
+using namespace sphk;
+
+static int blocks_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
+}
+
+cudaError_t launch_dt(const StepArgs& a, cudaStream_t st) {
+  k_dt<<<a.n_sims, 256, 0, st>>>(a.sim_offset, a.n_sims, a.cfl, a.h, a.v_sig, a.dt, a.status);
+  return cudaGetLastError();
+}
+cudaError_t launch_kick_drift(const StepArgs& a, cudaStream_t st) {
+  if (a.n_total > 0) k_kick_drift<<<blocks_for(a.n_total), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_kick(const StepArgs& a, cudaStream_t st) {
+  if (a.n_total > 0) k_kick<<<blocks_for(a.n_total), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_conservation(int n_sims, const int64_t* sim_offset, const float* m, const float* vx,
+                                const float* vy, const float* vz, const float* ax, const float* ay,
+                                const float* az, const float* du_dt, double* out, cudaStream_t st) {
+  k_conservation<<<n_sims, 256, 0, st>>>(sim_offset, n_sims, m, vx, vy, vz, ax, ay, az, du_dt, out);
+  return cudaGetLastError();
+}
+
+}  // namespace sphh

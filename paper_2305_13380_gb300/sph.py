@@ -1,0 +1,311 @@
+"""Thin Python binding of the C ABI in ``include/sph.h`` (ctypes).
+
+Argument marshalling only: every step of the SPH path runs in the CUDA
+library ``_lib/libsph.so``.  Tensors are torch CUDA tensors (torch provides
+the device memory and the stream); they must be contiguous with the dtypes the
+header states.  If the library is missing the import of a function raises: no
+part of the path has a CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from .build import LIB
+
+SPH_OK = 0
+SPH_E_INVAL = -1
+SPH_E_NOMEM = -2
+SPH_E_H_NOCONV = -3
+SPH_E_REBUILD = -4
+SPH_E_BOX = -5
+SPH_E_TIMEOUT = -6
+SPH_E_CUDA = -7
+SPH_E_CAPACITY = -8
+
+SPH_ST_H_NOCONV = 1
+SPH_ST_REBUILD = 2
+SPH_ST_BOX = 4
+SPH_ST_CAPACITY = 8
+SPH_ST_NEG_U = 16
+
+SPH_FLAG_SYNC = 1
+SPH_FLAG_COUNT_PAIRS = 2
+SPH_FLAG_TIMING = 4
+
+TIMING_GROUPS = ("build", "gather", "density", "force", "integrate")
+
+_P = C.c_void_p
+
+
+class sph_params(C.Structure):
+    _fields_ = [("box_size", C.c_double), ("gamma", C.c_double), ("eta", C.c_double),
+                ("alpha_v", C.c_double), ("beta_v", C.c_double), ("eps_balsara", C.c_double),
+                ("h_tol", C.c_double), ("cfl", C.c_double), ("cell_margin", C.c_double),
+                ("max_h_iter", C.c_int32), ("flags", C.c_int32)]
+
+
+class sph_cells(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_c", C.c_int32), ("n_c_dev", _P), ("cell_start", _P),
+                ("perm", _P)]
+
+
+class sph_particles(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(k, _P) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u")]
+
+
+DENSITY_FIELDS = ("h", "rho", "f", "div_v", "curl_v", "P", "c", "balsara")
+
+
+class sph_density_out(C.Structure):
+    _fields_ = [(k, _P) for k in DENSITY_FIELDS + ("n_iter",)]
+
+
+FORCE_FIELDS = ("ax", "ay", "az", "du_dt", "v_sig")
+
+
+class sph_force_out(C.Structure):
+    _fields_ = [(k, _P) for k in FORCE_FIELDS]
+
+
+POOL_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "u", "m", "h", "ax", "ay", "az", "du_dt", "v_sig",
+               "rho", "f", "div_v", "curl_v", "P", "c", "balsara", "dt")
+
+
+class sph_pool(C.Structure):
+    _fields_ = [("n_sims", C.c_int32), ("n_total", C.c_int64), ("sim_offset", _P),
+                ("box_size", _P)] + [(k, _P) for k in POOL_FIELDS] + [("n_iter", _P)]
+
+
+class SPHError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {error_string(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"CUDA library {LIB} is missing: run __graft_entry__.build()")
+        L = C.CDLL(LIB)
+        L.sph_default_params.argtypes = [C.POINTER(sph_params)]
+        L.sph_default_params.restype = None
+        L.sph_create.argtypes = [C.POINTER(_P), C.POINTER(sph_params), _P]
+        L.sph_destroy.argtypes = [_P]
+        L.sph_destroy.restype = None
+        L.sph_error_string.argtypes = [C.c_int]
+        L.sph_error_string.restype = C.c_char_p
+        L.sph_status.argtypes = [_P, C.POINTER(C.c_int32)]
+        L.sph_build_cells.argtypes = [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(sph_cells)]
+        L.sph_cells_sync.argtypes = [_P, C.POINTER(sph_cells)]
+        L.sph_cells_copy.argtypes = [_P, C.POINTER(sph_cells), _P, _P]
+        L.sph_density.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles), _P,
+                                  C.POINTER(sph_density_out)]
+        L.sph_force.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
+                                C.POINTER(sph_density_out), C.POINTER(sph_force_out)]
+        L.sph_step.argtypes = [_P, C.POINTER(sph_pool)]
+        L.sph_conservation.argtypes = [_P, C.POINTER(sph_pool), _P]
+        L.sph_pair_counts.argtypes = [_P, C.POINTER(C.c_int64)]
+        L.sph_kernel_times.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        for f in ("sph_create", "sph_status", "sph_build_cells", "sph_cells_sync", "sph_cells_copy",
+                  "sph_density",
+                  "sph_force", "sph_step", "sph_conservation", "sph_pair_counts",
+                  "sph_kernel_times"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().sph_error_string(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != SPH_OK:
+        raise SPHError(rc, what)
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return _P(t.data_ptr())
+
+
+def sph_default_params(**overrides) -> sph_params:
+    p = sph_params()
+    lib().sph_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """Owns an ``sph_ctx`` bound to a CUDA stream (torch's current one by default)."""
+
+    def __init__(self, params: sph_params | None = None, stream: torch.cuda.Stream | None = None):
+        self.params = params if params is not None else sph_default_params()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _P()
+        _check(lib().sph_create(C.byref(h), C.byref(self.params), _P(self.stream.cuda_stream)),
+               "sph_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sph_create(params: sph_params | None = None, stream=None) -> Context:
+    return Context(params, stream)
+
+
+def sph_destroy(ctx: Context):
+    ctx.close()
+
+
+def sph_status(ctx: Context) -> int:
+    s = C.c_int32(0)
+    _check(lib().sph_status(ctx.handle, C.byref(s)), "sph_status")
+    return s.value
+
+
+def sph_build_cells(ctx: Context, x, y, z, h) -> sph_cells:
+    cells = sph_cells()
+    n = int(x.shape[0])
+    _check(lib().sph_build_cells(ctx.handle, n, _ptr(x, torch.float64), _ptr(y, torch.float64),
+                                 _ptr(z, torch.float64), _ptr(h, torch.float32), C.byref(cells)),
+           "sph_build_cells")
+    cells._keep = (x, y, z, h)
+    return cells
+
+
+def sph_cells_sync(ctx: Context, cells: sph_cells) -> int:
+    _check(lib().sph_cells_sync(ctx.handle, C.byref(cells)), "sph_cells_sync")
+    return cells.n_c
+
+
+def sph_cells_copy(ctx: Context, cells: sph_cells):
+    """Host copies (numpy int32) of cell_start (n_c^3 + 1) and perm (n)."""
+    import numpy as np
+    sph_cells_sync(ctx, cells)
+    nc = cells.n_c
+    cs = np.zeros(nc ** 3 + 1, dtype=np.int32)
+    perm = np.zeros(max(int(cells.n), 1), dtype=np.int32)
+    _check(lib().sph_cells_copy(ctx.handle, C.byref(cells), cs.ctypes.data_as(_P),
+                                perm.ctypes.data_as(_P)), "sph_cells_copy")
+    return cs, perm[:int(cells.n)]
+
+
+def particles(p: dict) -> sph_particles:
+    """Marshals a dict of CUDA tensors x, y, z (float64) and vx, vy, vz, m, u (float32)."""
+    s = sph_particles(int(p["x"].shape[0]), *(
+        [_ptr(p[k], torch.float64) for k in ("x", "y", "z")] +
+        [_ptr(p[k], torch.float32) for k in ("vx", "vy", "vz", "m", "u")]))
+    s._keep = p
+    return s
+
+
+def density_out(d: dict) -> sph_density_out:
+    s = sph_density_out(*([_ptr(d[k], torch.float32) for k in DENSITY_FIELDS] +
+                          [_ptr(d.get("n_iter"), torch.int32)]))
+    s._keep = d
+    return s
+
+
+def force_out(f: dict) -> sph_force_out:
+    s = sph_force_out(*[_ptr(f[k], torch.float32) for k in FORCE_FIELDS])
+    s._keep = f
+    return s
+
+
+def sph_density(ctx: Context, cells: sph_cells, part: sph_particles, h_in, out: sph_density_out):
+    _check(lib().sph_density(ctx.handle, C.byref(cells), C.byref(part), _ptr(h_in, torch.float32),
+                             C.byref(out)), "sph_density")
+
+
+def sph_force(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_density_out,
+              out: sph_force_out):
+    _check(lib().sph_force(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
+                           C.byref(out)), "sph_force")
+
+
+def pool(sim_offset, box_size, arrays: dict) -> sph_pool:
+    """Marshals a pool of simulations: sim_offset (int64, n_sims+1), box_size
+    (float64, n_sims) and the per-particle arrays of ``POOL_FIELDS`` (dt is a
+    float64 array of n_sims)."""
+    n_sims = int(box_size.shape[0])
+    vals = []
+    for k in POOL_FIELDS:
+        dt = torch.float64 if k in ("x", "y", "z", "dt") else torch.float32
+        vals.append(_ptr(arrays[k], dt))
+    s = sph_pool(n_sims, int(arrays["x"].shape[0]), _ptr(sim_offset, torch.int64),
+                 _ptr(box_size, torch.float64), *vals, _ptr(arrays.get("n_iter"), torch.int32))
+    s._keep = (sim_offset, box_size, arrays)
+    return s
+
+
+def sph_step(ctx: Context, pl: sph_pool):
+    _check(lib().sph_step(ctx.handle, C.byref(pl)), "sph_step")
+
+
+def sph_conservation(ctx: Context, pl: sph_pool, out):
+    _check(lib().sph_conservation(ctx.handle, C.byref(pl), _ptr(out, torch.float64)),
+           "sph_conservation")
+
+
+def sph_pair_counts(ctx: Context):
+    v = (C.c_int64 * 2)()
+    _check(lib().sph_pair_counts(ctx.handle, v), "sph_pair_counts")
+    return int(v[0]), int(v[1])
+
+
+def sph_kernel_times(ctx: Context):
+    """{group: (milliseconds, launches)} since the last query (SPH_FLAG_TIMING)."""
+    ms = (C.c_double * len(TIMING_GROUPS))()
+    calls = (C.c_int64 * len(TIMING_GROUPS))()
+    _check(lib().sph_kernel_times(ctx.handle, ms, calls), "sph_kernel_times")
+    return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(TIMING_GROUPS)}
+
+
+# ---- allocation helpers (marshalling of outputs) ----------------------------
+
+def to_device(p: dict, device="cuda") -> dict:
+    """Input dict of numpy arrays -> CUDA tensors with the ABI dtypes."""
+    out = {}
+    for k in ("x", "y", "z"):
+        out[k] = torch.as_tensor(p[k], dtype=torch.float64, device=device).contiguous()
+    for k in ("vx", "vy", "vz", "m", "u"):
+        out[k] = torch.as_tensor(p[k], dtype=torch.float32, device=device).contiguous()
+    out["h0"] = torch.as_tensor(p["h0"], dtype=torch.float32, device=device).contiguous()
+    return out
+
+
+def alloc_density(n: int, device="cuda", n_iter: bool = True) -> dict:
+    d = {k: torch.empty(n, dtype=torch.float32, device=device) for k in DENSITY_FIELDS}
+    if n_iter:
+        d["n_iter"] = torch.empty(n, dtype=torch.int32, device=device)
+    return d
+
+
+def alloc_force(n: int, device="cuda") -> dict:
+    return {k: torch.empty(n, dtype=torch.float32, device=device) for k in FORCE_FIELDS}

@@ -1,0 +1,116 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and the oracle on the same inputs (the GPU's float32 inputs, upcast)."""
+import math
+
+import numpy as np
+
+GAMMA_K = 1.825742
+
+# Tolerances of the CUDA path (FP32 pair arithmetic) against the FP64 oracle.
+# rho and h: 1e-5 relative.  Accelerations and du/dt: 1e-4 of their rms.
+# The other density outputs are derived from the same FP32 sums; their bounds
+# follow from the arithmetic: f, P, c and v_sig inherit the rho/h error
+# (1e-5 relative); div_v and |curl v| are sums with cancellation, bounded by
+# 1e-4 of their rms plus the h error times their size; B is bounded in
+# absolute terms by the div/curl errors relative to their sum.
+TOL = dict(h=1e-5, rho=1e-5, f=1e-5, P=1e-5, c=1e-5, v_sig=1e-5, acc=1e-4, du=1e-4,
+           divcurl=1e-4, balsara=2e-4)
+
+
+def as_f32(p):
+    """The float32 rounding the GPU sees, as float64 arrays for the oracle."""
+    q = dict(p)
+    for k in ("vx", "vy", "vz", "m", "u", "h0"):
+        q[k] = np.asarray(p[k], dtype=np.float32).astype(np.float64)
+    return q
+
+
+def expected_nc(h0_f32, L, margin=0.05, n=None):
+    """Cells per side from the definition in include/sph.h."""
+    hmax = float(np.max(np.asarray(h0_f32, dtype=np.float32)))
+    nc = int(math.floor(L / (GAMMA_K * hmax * (1.0 + margin))))
+    if n is not None:
+        lim = 8.0 * n + 216.0
+        cap = int(round(lim ** (1.0 / 3.0)))
+        while (cap + 1) ** 3 <= lim:
+            cap += 1
+        while cap > 3 and cap ** 3 > lim:
+            cap -= 1
+        nc = min(nc, cap)
+    return max(nc, 3)
+
+
+def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-6):
+    """build -> density -> (rebuild while the status asks) -> force on cuda:0."""
+    import torch
+    from paper_2305_13380_gb300 import sph
+    flags = sph.SPH_FLAG_COUNT_PAIRS if count_pairs else 0
+    params = sph.sph_default_params(box_size=float(p["L"]), cell_margin=margin, flags=flags,
+                                    h_tol=h_tol)
+    ctx = sph.Context(params)
+    t = sph.to_device(p)
+    n = int(t["x"].shape[0])
+    part = sph.particles(t)
+    d = sph.alloc_density(n)
+    f = sph.alloc_force(n)
+    h_in = t["h0"]
+    rebuilds = 0
+    for _ in range(8):
+        cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], h_in)
+        sph.sph_density(ctx, cells, part, h_in, sph.density_out(d))
+        st = sph.sph_status(ctx)
+        if not st & sph.SPH_ST_REBUILD:
+            break
+        rebuilds += 1
+        h_in = d["h"].clone()
+    assert st == 0, f"device status {st}"
+    pairs_d = sph.sph_pair_counts(ctx)[0] if count_pairs else None
+    sph.sph_force(ctx, cells, part, sph.density_out(d), sph.force_out(f))
+    assert sph.sph_status(ctx) == 0
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in d.items()}
+    out.update({k: v.cpu().numpy() for k, v in f.items()})
+    if count_pairs:
+        out["pairs"] = (pairs_d, sph.sph_pair_counts(ctx)[1])
+    out["rebuilds"] = rebuilds
+    out["_ctx"], out["_cells"] = ctx, cells
+    return out
+
+
+def rel_err(a, b):
+    return np.abs(a - b) / np.abs(b)
+
+
+def compare(g, od, of, idx=None):
+    """Asserts the GPU outputs g (indexed by idx) against oracle density od and
+    force of (already restricted to the same particles)."""
+    sel = (lambda a: a) if idx is None else (lambda a: a[idx])
+    report = {}
+    for k_g, k_o, tol in (("h", "h", TOL["h"]), ("rho", "rho", TOL["rho"]), ("f", "f", TOL["f"]),
+                          ("P", "P", TOL["P"]), ("c", "c", TOL["c"])):
+        e = rel_err(sel(g[k_g]), od[k_o]).max()
+        report[k_g] = e
+        assert e <= tol, f"{k_g}: max relative error {e:.3e} > {tol}"
+    for k_g, k_o in (("div_v", "div_v"), ("curl_v", "curl_norm")):
+        ref = od[k_o]
+        scale = np.sqrt(np.mean(ref ** 2)) + 1e-300
+        e = np.abs(sel(g[k_g]) - ref).max() / scale
+        report[k_g] = e
+        assert e <= TOL["divcurl"], f"{k_g}: max error / rms {e:.3e}"
+    e = np.abs(sel(g["balsara"]) - od["B"]).max()
+    report["balsara"] = e
+    assert e <= TOL["balsara"], f"balsara: max abs error {e:.3e}"
+    a_ref = np.stack([of["ax"], of["ay"], of["az"]], 1)
+    a_gpu = np.stack([sel(g["ax"]), sel(g["ay"]), sel(g["az"])], 1)
+    rms = np.sqrt(np.mean(np.sum(a_ref ** 2, 1)))
+    e = np.abs(a_gpu - a_ref).max() / rms
+    report["a"] = e
+    assert e <= TOL["acc"], f"a: max error / rms|a| {e:.3e}"
+    rms_u = np.sqrt(np.mean(of["du_dt"] ** 2))
+    e = np.abs(sel(g["du_dt"]) - of["du_dt"]).max() / rms_u
+    report["du_dt"] = e
+    assert e <= TOL["du"], f"du_dt: max error / rms {e:.3e}"
+    e = rel_err(sel(g["v_sig"]), of["v_sig"]).max()
+    report["v_sig"] = e
+    assert e <= TOL["v_sig"], f"v_sig: max relative error {e:.3e}"
+    return report
