@@ -36,9 +36,9 @@ UNIT = "particle-updates/s"
 # divide and square root counts 1; see the design notes for the tally).
 F_DENSITY = 66
 F_FORCE = 72
-# Kernel launches of one sph_step: dt + kick/drift (2), cell build (10),
-# two gathers (2), density (1), force (1), kick (1).
-LAUNCHES_PER_STEP = 17
+# Kernel launches of one sph_step: time-step reduction (3), kick/drift (1),
+# cell build (10), two gathers (2), density (1), force (1), kick (1).
+LAUNCHES_PER_STEP = 19
 FP32_LANES_PER_SM = 128
 
 

@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 
+#include "blocks.cuh"
 #include "sph_internal.cuh"
 #include "sph_launch.h"
 
@@ -33,9 +34,14 @@ struct sph_ctx {
   // grown buffers
   GridDev* grid = nullptr;
   int32_t *key = nullptr, *slot = nullptr, *count = nullptr, *cell_start = nullptr;
-  int32_t *scan_sums = nullptr, *perm = nullptr, *big = nullptr;
+  int32_t *scan_sums = nullptr, *perm = nullptr, *big = nullptr, *overflow = nullptr;
   float4 *pos4 = nullptr, *vel4 = nullptr, *th4 = nullptr;
-  float *hs = nullptr, *rho_s = nullptr;
+  float* hs = nullptr;
+  float2* fD = nullptr;
+  unsigned long long* dt_bits = nullptr;
+  int32_t* hmax_bits = nullptr;
+  uint16_t *lists = nullptr, *list_cnt = nullptr;
+  bool lists_valid = false;  // lists belong to the current build
   float *vpx = nullptr, *vpy = nullptr, *vpz = nullptr, *up = nullptr;
   // CUDA-event timing of kernel groups (SPH_FLAG_TIMING)
   std::vector<cudaEvent_t> ev_start[SPH_T_COUNT], ev_stop[SPH_T_COUNT];
@@ -77,11 +83,16 @@ void free_grown(sph_ctx* c) {
   dfree(c->scan_sums);
   dfree(c->perm);
   dfree(c->big);
+  dfree(c->overflow);
   dfree(c->pos4);
   dfree(c->vel4);
   dfree(c->th4);
   dfree(c->hs);
-  dfree(c->rho_s);
+  dfree(c->fD);
+  dfree(c->dt_bits);
+  dfree(c->hmax_bits);
+  dfree(c->lists);
+  dfree(c->list_cnt);
   dfree(c->vpx);
   dfree(c->vpy);
   dfree(c->vpz);
@@ -103,8 +114,10 @@ int ensure(sph_ctx* c, int64_t n, int n_sims) {
   bool ok = dalloc(c->grid, cs) && dalloc(c->key, cn) && dalloc(c->slot, cn) &&
             dalloc(c->count, cc + 1) && dalloc(c->cell_start, cc + 1) &&
             dalloc(c->scan_sums, cc / 1024 + 2) && dalloc(c->perm, cn) &&
-            dalloc(c->big, cn / (sphk::kSmallCell + 1) + 2) && dalloc(c->pos4, cn) &&
-            dalloc(c->vel4, cn) && dalloc(c->th4, cn) && dalloc(c->hs, cn) && dalloc(c->rho_s, cn) &&
+            dalloc(c->big, cn / (sphk::kSmallCell + 1) + 2) && dalloc(c->overflow, cc / 3 + 2) && dalloc(c->pos4, cn) &&
+            dalloc(c->vel4, cn) && dalloc(c->th4, cn) && dalloc(c->hs, cn) && dalloc(c->fD, cn) &&
+            dalloc(c->dt_bits, cs) && dalloc(c->hmax_bits, cs) &&
+            dalloc(c->lists, (int64_t)sphk::kListRegion * 4 * cn) && dalloc(c->list_cnt, 4 * cn) &&
             dalloc(c->vpx, cn) && dalloc(c->vpy, cn) && dalloc(c->vpz, cn) && dalloc(c->up, cn);
   if (!ok) {
     free_grown(c);
@@ -113,6 +126,7 @@ int ensure(sph_ctx* c, int64_t n, int n_sims) {
   c->cap_n = cn;
   c->cap_sims = cs;
   c->cap_cells = cc;
+  c->lists_valid = false;
   c->built_n = -1;
   return SPH_OK;
 }
@@ -219,6 +233,7 @@ int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const 
   b.h = h;
   b.grid = c->grid;
   b.misc = c->misc;
+  b.hmax_bits = c->hmax_bits;
   b.key = c->key;
   b.slot = c->slot;
   b.count = c->count;
@@ -232,6 +247,7 @@ int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const 
   c->built_sims = n_sims;
   c->built_n = n_total;
   c->built_offset = off;
+  c->lists_valid = false;
   return SPH_OK;
 }
 
@@ -268,6 +284,8 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   d.num_sms = c->num_sms;
   d.grid = c->grid;
   d.misc_ro = c->misc;
+  d.misc = c->misc;
+  d.overflow = c->overflow;
   d.status = c->misc + sphk::kStatus;
   d.pairs = c->pairs;
   d.cell_start = c->cell_start;
@@ -284,9 +302,12 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   d.c = cs;
   d.B = B;
   d.n_iter = n_iter;
+  d.lists = c->lists;
+  d.list_cnt = c->list_cnt;
   t_begin(c, SPH_T_DENSITY);
   const cudaError_t e = sphh::launch_density(d, phys_of(c->p), c->st);
   t_end(c, SPH_T_DENSITY);
+  c->lists_valid = (e == cudaSuccess);
   return cuda_code(e);
 }
 
@@ -313,10 +334,10 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   g.P = P;
   g.c = cs;
   g.B = B;
-  g.pos4 = c->pos4;
-  g.vel4 = c->vel4;
-  g.th4 = c->th4;
-  g.rho_s = c->rho_s;
+  g.fA = c->pos4;
+  g.fB = c->vel4;
+  g.fC = c->th4;
+  g.fD = c->fD;
   t_begin(c, SPH_T_GATHER);
   if (sphh::launch_gather_force(g, c->st) != cudaSuccess) return SPH_E_CUDA;
   t_end(c, SPH_T_GATHER);
@@ -328,18 +349,22 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   a.num_sms = c->num_sms;
   a.grid = c->grid;
   a.misc_ro = c->misc;
+  a.misc = c->misc;
+  a.overflow = c->overflow;
   a.pairs = c->pairs + 1;
   a.cell_start = c->cell_start;
   a.perm = c->perm;
-  a.pos4 = c->pos4;
-  a.vel4 = c->vel4;
-  a.th4 = c->th4;
-  a.rho_s = c->rho_s;
+  a.fA = c->pos4;
+  a.fB = c->vel4;
+  a.fC = c->th4;
+  a.fD = c->fD;
   a.ax = ax;
   a.ay = ay;
   a.az = az;
   a.du_dt = du_dt;
   a.v_sig = v_sig;
+  a.lists = c->lists_valid ? c->lists : nullptr;
+  a.list_cnt = c->list_cnt;
   t_begin(c, SPH_T_FORCE);
   const cudaError_t e = sphh::launch_force(a, phys_of(c->p), c->st);
   t_end(c, SPH_T_FORCE);
@@ -553,6 +578,7 @@ int sph_step(sph_ctx* c, const sph_pool* pl) {
   s.vpz = c->vpz;
   s.up = c->up;
   s.dt = pl->dt;
+  s.dt_bits = c->dt_bits;
   s.status = c->misc + sphk::kStatus;
   t_begin(c, SPH_T_INTEGRATE);
   if (sphh::launch_dt(s, c->st) != cudaSuccess) return SPH_E_CUDA;

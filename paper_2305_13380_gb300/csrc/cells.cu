@@ -31,22 +31,41 @@ __device__ __forceinline__ int32_t cap_cells_per_side(int64_t n) {
   return c;
 }
 
-// One block per simulation.
+// max h per simulation.  Non-negative floats order like their bit patterns,
+// so each thread keeps a running maximum for its simulation, lanes of one
+// simulation combine with shuffles and one of them publishes with an integer
+// atomicMax.  Non-positive and NaN values are ignored.
+__global__ void k_grid_hmax(const int64_t* __restrict__ sim_offset, int n_sims, int64_t n_total,
+                            const float* __restrict__ h, int32_t* __restrict__ hmax_bits) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int cur = -1;
+  float m = 0.0f;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_total; p += stride) {
+    const int s = sim_of_particle(sim_offset, n_sims, p);
+    if (s != cur) {
+      if (cur >= 0 && m > 0.0f) atomicMax(&hmax_bits[cur], __float_as_int(m));
+      cur = s;
+      m = 0.0f;
+    }
+    const float v = h[p];
+    if (v > m) m = v;
+  }
+  const unsigned grp = __match_any_sync(0xffffffffu, cur);
+  for (int o = 0; o < 32; ++o) {
+    const float other = __shfl_sync(0xffffffffu, m, o);
+    if ((grp >> o) & 1u) m = fmaxf(m, other);
+  }
+  if (cur >= 0 && m > 0.0f && (threadIdx.x & 31) == __ffs(grp) - 1)
+    atomicMax(&hmax_bits[cur], __float_as_int(m));
+}
+
+// One thread per simulation: cells per side from max h.
 __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const double* __restrict__ box,
-                             const float* __restrict__ h, int n_sims, double margin,
+                             const int32_t* __restrict__ hmax_bits, int n_sims, double margin,
                              GridDev* __restrict__ grid, int32_t* __restrict__ misc) {
-  const int s = blockIdx.x;
-  if (s >= n_sims) return;
-  const int64_t a = sim_offset[s], b = sim_offset[s + 1];
-  float hm = 0.0f;
-  for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) hm = fmaxf(hm, h[p]);
-  __shared__ float red[32];
-  hm = warp_max(hm);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = hm;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float m = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x) {
+    const int64_t a = sim_offset[s], b = sim_offset[s + 1];
+    const float m = __int_as_float(hmax_bits[s]);
     const double L = box[s];
     const double Hmax = kGammaKd * (double)m * (1.0 + margin);
     const int32_t cap = cap_cells_per_side(b - a);
@@ -65,7 +84,7 @@ __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const doubl
     g.cell = L / (double)nc;
     g.cell_f = (float)g.cell;
     g.cell_base = 0;
-    g.pad = 0;
+    g.blk_base = 0;
     g.part_base = a;
     g.n = b - a;
     grid[s] = g;
@@ -74,13 +93,17 @@ __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const doubl
 
 __global__ void k_grid_base(GridDev* __restrict__ grid, int n_sims, int32_t* __restrict__ misc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int64_t base = 0;
+  int64_t base = 0, bbase = 0;
   for (int s = 0; s < n_sims; ++s) {
     grid[s].cell_base = (int32_t)base;
+    grid[s].blk_base = (int32_t)bbase;
     const int64_t nc = grid[s].n_c;
+    const int64_t nb = (nc + 1) / 2;
     base += nc * nc * nc;
+    bbase += nb * nb * nb;
   }
   misc[kTotalCells] = (int32_t)base;
+  misc[kTotalBlocks] = (int32_t)bbase;
   misc[kNumBigCells] = 0;
 }
 
@@ -292,8 +315,8 @@ __global__ void k_gather_density(int64_t n_total, const int32_t* __restrict__ pe
   }
 }
 
-// Sorted copies for the force loop: the density results of each particle
-// packed as (f P / rho^2, f, c, B), (rho, 1/H), and velocity with 1/H.
+// Sorted copies for the force loop: position relative to the own cell with
+// the support H, velocity with the mass, (f P / rho^2, f, c, B), (rho, 1/H).
 __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm,
                                const int32_t* __restrict__ key, const GridDev* __restrict__ grid,
                                int n_sims, const double* __restrict__ x, const double* __restrict__ y,
@@ -302,9 +325,9 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
                                const float* __restrict__ m, const float* __restrict__ h,
                                const float* __restrict__ rho, const float* __restrict__ f,
                                const float* __restrict__ P, const float* __restrict__ c,
-                               const float* __restrict__ B, float4* __restrict__ pos4,
-                               float4* __restrict__ vel4, float4* __restrict__ th4,
-                               float* __restrict__ rho_s) {
+                               const float* __restrict__ B, float4* __restrict__ fA,
+                               float4* __restrict__ fB, float4* __restrict__ fC,
+                               float2* __restrict__ fD) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_total;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p = perm[s];
@@ -315,12 +338,12 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
     const float rx = (float)(x[p] - (double)kx * G.cell);
     const float ry = (float)(y[p] - (double)ky * G.cell);
     const float rz = (float)(z[p] - (double)kz * G.cell);
-    pos4[s] = make_float4(rx, ry, rz, m[p]);
-    const float Hinv = 1.0f / (kGammaK * h[p]);
-    vel4[s] = make_float4(vx[p], vy[p], vz[p], Hinv);
+    const float H = kGammaK * h[p];
+    fA[s] = make_float4(rx, ry, rz, H);
+    fB[s] = make_float4(vx[p], vy[p], vz[p], m[p]);
     const float r = rho[p];
-    th4[s] = make_float4(f[p] * P[p] / (r * r), f[p], c[p], B[p]);
-    rho_s[s] = r;
+    fC[s] = make_float4(f[p] * P[p] / (r * r), f[p], c[p], B[p]);
+    fD[s] = make_float2(r, 1.0f / H);
   }
 }
 
@@ -338,7 +361,14 @@ static int grid_for(int64_t n, int threads, int max_blocks) {
 }
 
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t st) {
-  k_grid_setup<<<a.n_sims, 256, 0, st>>>(a.sim_offset, a.box, a.h, a.n_sims, a.margin, a.grid, a.misc);
+  if (cudaMemsetAsync(a.hmax_bits, 0, sizeof(int32_t) * a.n_sims, st) != cudaSuccess) return cudaGetLastError();
+  if (a.n_total > 0) {
+    int64_t hb = (a.n_total + 255) / 256;
+    if (hb > (int64_t)a.num_sms * 8) hb = (int64_t)a.num_sms * 8;
+    k_grid_hmax<<<(int)hb, 256, 0, st>>>(a.sim_offset, a.n_sims, a.n_total, a.h, a.hmax_bits);
+  }
+  k_grid_setup<<<(a.n_sims + 127) / 128, 128, 0, st>>>(a.sim_offset, a.box, a.hmax_bits, a.n_sims,
+                                                       a.margin, a.grid, a.misc);
   k_grid_base<<<1, 32, 0, st>>>(a.grid, a.n_sims, a.misc);
   const int zb = grid_for(a.cap_cells + 1, 256, 65535);
   k_zero_counts<<<zb, 256, 0, st>>>(a.count, a.misc);
@@ -371,7 +401,7 @@ cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st) {
   if (a.n_total <= 0) return cudaSuccess;
   k_gather_force<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
       a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.h, a.rho,
-      a.f, a.P, a.c, a.B, a.pos4, a.vel4, a.th4, a.rho_s);
+      a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD);
   return cudaGetLastError();
 }
 

@@ -1,49 +1,396 @@
 // density.cu -- the SPH density loop with the per-particle smoothing-length
 // solve (Sec. 3.1.1-3.1.2).
 //
-// One warp owns one target cell at a time (persistent grid over the cells of
-// every simulation).  The particles of the 27 neighbour cells are staged in
-// shared memory with positions relative to the target cell; each lane owns a
-// target particle and walks the staged sources (a broadcast read).  For each
-// pass at the lane's current h the lane accumulates, in FP32,
-//   S_w   = sum_j w(q),            S_dw  = sum_j (3 w + q w'(q)),
-//   S_mw  = sum_j m_j w(q),        S_mdw = sum_j m_j (3 w + q w'(q)),
-//   S_div = sum_j m_j g(q) (v_j - v_i) . x_ij,
-//   S_curl= sum_j m_j g(q) (v_i - v_j) x x_ij,      g(q) = w'(q)/q,
-// so that n_hat = S_w / H^3, dn_hat/dh = -S_dw / (h H^3), rho = S_mw / H^3,
-// d rho/dh = -S_mdw / (h H^3), grad_i W_ij = g(q) x_ij / H^5.  Newton-Raphson
-// on n_hat(h) - (eta/h)^3 (the paper's iteration, with dn_hat/dh) is taken in
-// FP64: h <- h (1 - A/B) with A = S_w/gamma_K^3 - eta^3 and
-// B = 3 eta^3 - S_dw/gamma_K^3; the lane stops when |A/B| <= h_tol and
-// writes the quantities of the last pass.
+// k_density: one thread block per 2x2x2 block of cells (blocks.cuh), one warp
+// per target cell, the block's 4x4x4 neighbourhood staged once in shared
+// memory.  Each target is served by tpp lanes (threads per particle: 4 for
+// cells of <= 8 particles, else 2) that split the sources between them.
+//
+//  1. filter: each lane keeps, in its own column of a shared-memory list, the
+//     sources closer than the cell size (any support H <= cell can only
+//     reach those) together with their squared distance;
+//  2. Newton-Raphson passes run over the list only, accumulating
+//        S_w = sum_j w(q),   S_dw = sum_j (3 w + q w'(q)),   q = r / H,
+//     so that n_hat = S_w / H^3 and dn_hat/dh = -S_dw / (h H^3).  The
+//     iteration of the paper, h <- h - f/f' with f = n_hat - (eta/h)^3 and
+//     f' = dn_hat/dh + 3 eta^3 / h^4, is h <- h (1 - A/B) with
+//     A = S_w/gamma_K^3 - eta^3, B = 3 eta^3 - S_dw/gamma_K^3, taken in FP64;
+//     a target stops when |A/B| <= h_tol (or at the cell cap / max_h_iter);
+//  3. a final pass at the converged h accumulates, in FP32,
+//        S_mw = sum m_j w,  S_mdw = sum m_j (3 w + q w'),
+//        S_div = sum m_j g (v_j - v_i) . x_ij,  S_curl = sum m_j g (v_i - v_j) x x_ij,
+//     with g = w'(q)/q, so rho = S_mw / H^3, d rho/dh = -S_mdw / (h H^3) and
+//     grad_i W_ij = g x_ij / H^5.
+// The partial sums of the tpp lanes are combined with warp shuffles in a
+// fixed order, so results do not depend on scheduling.  A target whose list
+// overflows walks the staged sources directly.  A block whose neighbourhood
+// does not fit the staging buffer is queued for k_density_overflow, which
+// streams each target cell's 27 cells through a per-warp buffer.
+#include "blocks.cuh"
 #include "sph_internal.cuh"
 #include "sph_launch.h"
 #include "stencil.cuh"
 
 namespace sphk {
 
-constexpr int kDensCap = 448;  // staged sources per warp
-constexpr size_t kDensSmem = (size_t)kWarpsPerBlock * kDensCap * 2 * sizeof(float4);
+constexpr int kDensBlkCap = kBlkStageCap;  // staged sources per block
+constexpr int kListCap = kLaneListCap;     // list entries per lane
+// shared memory: staged sources (32 B each), per-warp lists (r^2, slot),
+// the staging table, the block's target rounds and its target slots/cells
+constexpr size_t kDensBlkSmem = (size_t)kDensBlkCap * 2 * sizeof(float4) +
+                                (size_t)kBlkWarps * kListCap * 32 * (sizeof(float) + sizeof(uint16_t)) +
+                                sizeof(StageTable) + sizeof(BlockTargets) +
+                                (size_t)kDensBlkCap * (sizeof(uint16_t) + sizeof(uint8_t));
+constexpr int kOvfCap = 256;  // per-warp staging of the overflow kernel
+constexpr size_t kOvfSmem = (size_t)kWarpsPerBlock * kOvfCap * 2 * sizeof(float4);
 
-__global__ void __launch_bounds__(kThreads) k_density(sphh::DensityArgs a, PhysDev ph) {
-  extern __shared__ float4 dsm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* spos = dsm + warp * (2 * kDensCap);
-  float4* svel = spos + kDensCap;
-  const int32_t total = a.misc_ro[kTotalCells];
+struct DensSums {
+  float w, dw, mw, mdw, div, cx, cy, cz;
+  int npair;
+};
+
+__device__ __forceinline__ void sums_zero(DensSums& s) {
+  s.w = s.dw = s.mw = s.mdw = s.div = s.cx = s.cy = s.cz = 0.f;
+  s.npair = 0;
+}
+
+__device__ __forceinline__ void sums_add(DensSums& s, const DensSums& t) {
+  s.w += t.w;
+  s.dw += t.dw;
+  s.mw += t.mw;
+  s.mdw += t.mdw;
+  s.div += t.div;
+  s.cx += t.cx;
+  s.cy += t.cy;
+  s.cz += t.cz;
+  s.npair += t.npair;
+}
+
+// Full density sums of one pair (target at pi/vi, source pj/vj) at H.
+__device__ __forceinline__ void dens_pair(const float4& pi, const float4& vi, const float4& pj,
+                                          const float4& vj, float H, float Hinv, DensSums& s) {
+  const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+  const float q = r2 * rinv * Hinv;
+  float w, g;
+  kernel_w_g(q, H * rinv, w, g);
+  const float dw = fmaf(q * q, g, 3.0f * w);
+  s.w += w;
+  s.dw += dw;
+  s.mw = fmaf(pj.w, w, s.mw);
+  s.mdw = fmaf(pj.w, dw, s.mdw);
+  const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
+  const float mg = pj.w * g;
+  s.div = fmaf(mg, fmaf(ux, dx, fmaf(uy, dy, uz * dz)), s.div);
+  s.cx = fmaf(mg, fmaf(uz, dy, -uy * dz), s.cx);
+  s.cy = fmaf(mg, fmaf(ux, dz, -uz * dx), s.cy);
+  s.cz = fmaf(mg, fmaf(uy, dx, -ux * dy), s.cz);
+  s.npair += q < 1.0f;
+}
+
+// One Newton-Raphson decision for a target whose pass at h gave (S_w, S_dw).
+// Returns true when the target is finished (converged, capped or out of
+// iterations); otherwise advances h.
+__device__ __forceinline__ bool newton_step(float Sw, float Sdw, double& h, double& lo, double& hi,
+                                            int& it, double hcap, const PhysDev& ph, bool& atcap,
+                                            bool& conv) {
   const double g3 = kGammaKd * kGammaKd * kGammaKd;
   const double eta3 = (double)ph.eta3;
+  const double A = (double)Sw / g3 - eta3;
+  const double B = 3.0 * eta3 - (double)Sdw / g3;
+  if (A < 0.0) lo = h; else hi = h;
+  conv = (B > 0.0) && (fabs(A) <= ph.h_tol * B);
+  atcap = (h >= hcap) && (A < 0.0);
+  const bool last = it + 1 >= ph.max_h_iter;
+  if (conv || atcap || last) return true;
+  double hn = (B > 0.0) ? h * (1.0 - A / B) : 2.0 * h;
+  hn = fmin(fmax(hn, 0.5 * h), 2.0 * h);
+  if (!(B > 0.0) || !(hn > lo) || !(hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
+  if (hn > hcap) hn = hcap;
+  h = hn;
+  ++it;
+  return false;
+}
+
+__device__ __forceinline__ double start_h(float h0, double hcap) {
+  double h = (double)h0;
+  if (!(h > 0.0)) h = 0.5 * hcap;
+  return h > hcap ? hcap : h;
+}
+
+// Writes the outputs of one target (sorted index ti) from its sums at h.
+__device__ __forceinline__ void dens_write(const sphh::DensityArgs& a, const PhysDev& ph, int32_t ti,
+                                           double h, const DensSums& s, float u_i, int passes,
+                                           bool conv, bool atcap) {
+  const float H = kGammaK * (float)h;
+  const float Hinv = 1.0f / H;
+  const float H2inv = Hinv * Hinv;
+  const int32_t p = a.perm[ti];
+  const float rho = s.mw * H2inv * Hinv;
+  const float fi = 1.0f / (1.0f - s.mdw / (3.0f * s.mw));
+  const float div = s.div * H2inv / s.mw;
+  const float curl = sqrtf(fmaf(s.cx, s.cx, fmaf(s.cy, s.cy, s.cz * s.cz))) * H2inv / s.mw;
+  const float P = (ph.gamma - 1.0f) * u_i * rho;
+  const float cs = sqrtf(ph.gamma * P / rho);
+  const float hf = (float)h;
+  const float B_i = fabsf(div) / (fabsf(div) + curl + ph.eps_balsara * cs / hf);
+  a.h[p] = hf;
+  a.rho[p] = rho;
+  a.f[p] = fi;
+  a.div_v[p] = div;
+  a.curl_v[p] = curl;
+  a.P[p] = P;
+  a.c[p] = cs;
+  a.B[p] = B_i;
+  if (a.n_iter) a.n_iter[p] = passes;
+  if (atcap) atomicOr(a.status, SPH_ST_REBUILD);
+  else if (!conv) atomicOr(a.status, SPH_ST_H_NOCONV);
+}
+
+__device__ __forceinline__ void combine(DensSums& s, int tpp) {
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    if (o < tpp) {
+      s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
+      s.dw += __shfl_xor_sync(0xffffffffu, s.dw, o);
+      s.mw += __shfl_xor_sync(0xffffffffu, s.mw, o);
+      s.mdw += __shfl_xor_sync(0xffffffffu, s.mdw, o);
+      s.div += __shfl_xor_sync(0xffffffffu, s.div, o);
+      s.cx += __shfl_xor_sync(0xffffffffu, s.cx, o);
+      s.cy += __shfl_xor_sync(0xffffffffu, s.cy, o);
+      s.cz += __shfl_xor_sync(0xffffffffu, s.cz, o);
+      s.npair += __shfl_xor_sync(0xffffffffu, s.npair, o);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a, PhysDev ph) {
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  float4* spos = reinterpret_cast<float4*>(dsm_raw);
+  float4* svel = spos + kDensBlkCap;
+  float* lr2_all = reinterpret_cast<float*>(svel + kDensBlkCap);
+  uint16_t* lj_all = reinterpret_cast<uint16_t*>(lr2_all + kBlkWarps * kListCap * 32);
+  StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * kListCap * 32);
+  BlockTargets& BT = *reinterpret_cast<BlockTargets*>(&T + 1);
+  uint16_t* tgt_slot = reinterpret_cast<uint16_t*>(&BT + 1);
+  uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + kDensBlkCap);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* lr2 = lr2_all + warp * (kListCap * 32);
+  uint16_t* lj = lj_all + warp * (kListCap * 32);
+  const int32_t total = a.misc_ro[kTotalBlocks];
   unsigned long long pair_acc = 0;
 
-  for (int32_t c = blockIdx.x * kWarpsPerBlock + warp; c < total; c += gridDim.x * kWarpsPerBlock) {
+  for (int32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const BlockGeom g = block_geom(a.grid, a.n_sims, b);
+    const int32_t nsrc = build_stage_table(g, a.cell_start, T);
+    if (nsrc > kDensBlkCap) {
+      if (threadIdx.x == 0) a.overflow[atomicAdd(&a.misc[kNumOverflow], 1)] = b;
+      __syncthreads();
+      continue;
+    }
+    for (int32_t v = threadIdx.x; v < nsrc; v += kBlkThreads) {
+      const int k = staged_cell_of(T, v);
+      float ox, oy, oz;
+      staged_offset(g, k, ox, oy, oz);
+      const int32_t j = T.gstart[k] + (v - T.start[k]);
+      float4 p = a.pos4[j];
+      p.x += ox;
+      p.y += oy;
+      p.z += oz;
+      spos[v] = p;
+      svel[v] = a.vel4[j];
+    }
+    build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+
+    const double hcap = (double)g.G.cell_f * (1.0 - 1e-5) / kGammaKd;
+    const float R2 = g.G.cell_f * g.G.cell_f;
+    const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
+    const int sub = lane & (tpp - 1);
+    for (int rd = warp; rd < BT.rounds; rd += kBlkWarps) {
+      const int t = lane >> lg;
+      const int32_t e_t = rd * per + t;
+      const bool valid = (t < per) && (e_t < BT.n);
+      int slot_i = 0, kc = BT.cell_k[0];
+      if (valid) {
+        slot_i = tgt_slot[e_t];
+        kc = BT.cell_k[tgt_cell[e_t]];
+      }
+      const int tx = kc % g.ex - 1, ty = (kc / g.ex) % g.ey - 1, tz = kc / (g.ex * g.ey) - 1;
+      const int32_t ti = T.gstart[kc] + (slot_i - T.start[kc]);  // sorted index
+      const float4 pi = spos[slot_i];
+      const float4 vi = svel[slot_i];
+      // 1. filter into the lane's own list column
+      int cnt = 0;
+      if (valid) {
+#pragma unroll 1
+        for (int r = 0; r < 9; ++r) {
+          int32_t A0, B0;
+          warp_run(g, T, tx, ty, tz, r, A0, B0);
+#pragma unroll 4
+          for (int32_t k = A0 + sub; k < B0; k += tpp) {
+            const float4 pj = spos[k];
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < R2) {
+              if (cnt < kListCap) {
+                lr2[cnt * 32 + lane] = r2;
+                lj[cnt * 32 + lane] = (uint16_t)k;
+              }
+              ++cnt;
+            }
+          }
+        }
+      }
+      const bool direct = cnt > kListCap;
+      // publish the list for the force loop of this build: 16-byte vectors
+      // into this lane's region (the force loop rebuilds the same rounds)
+      if (a.lists != nullptr && valid) {
+        const int64_t col = (int64_t)ti * 4 + sub;
+        a.list_cnt[col] = (uint16_t)(direct ? 0xffff : cnt);
+        if (!direct) {
+          uint4* dst = reinterpret_cast<uint4*>(a.lists + col * kListRegion);
+          for (int e8 = 0; e8 < cnt; e8 += 8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int e0 = e8 + 2 * q, e1 = e0 + 1;
+              const uint32_t lo = e0 < kListCap ? lj[e0 * 32 + lane] : 0u;
+              const uint32_t hi = e1 < kListCap ? lj[e1 * 32 + lane] : 0u;
+              w[q] = lo | (hi << 16);
+            }
+            dst[e8 >> 3] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+      }
+      // 2. Newton-Raphson passes over the list (or over all runs if it overflowed)
+      double h = valid ? start_h(a.hs[ti], hcap) : hcap;
+      double lo = 0.0, hi = INFINITY;
+      bool done = !valid, atcap = false, conv = false;
+      int it = 0, passes = 0;
+      while (__any_sync(0xffffffffu, !done)) {
+        const float H = kGammaK * (float)h;
+        const float Hinv = 1.0f / H;
+        float Sw0 = 0.f, Sdw0 = 0.f, Sw1 = 0.f, Sdw1 = 0.f;
+        if (!done && !direct) {
+          int e = 0;
+          for (; e + 1 < cnt; e += 2) {
+            const float r2a = lr2[e * 32 + lane], r2b = lr2[(e + 1) * 32 + lane];
+            const float ria = rsqrtf(fmaxf(r2a, 1e-30f)), rib = rsqrtf(fmaxf(r2b, 1e-30f));
+            const float qa = r2a * ria * Hinv, qb = r2b * rib * Hinv;
+            float wa, ga, wb, gb;
+            kernel_w_g(qa, H * ria, wa, ga);
+            kernel_w_g(qb, H * rib, wb, gb);
+            Sw0 += wa;
+            Sw1 += wb;
+            Sdw0 += fmaf(qa * qa, ga, 3.0f * wa);
+            Sdw1 += fmaf(qb * qb, gb, 3.0f * wb);
+          }
+          if (e < cnt) {
+            const float r2a = lr2[e * 32 + lane];
+            const float ria = rsqrtf(fmaxf(r2a, 1e-30f));
+            const float qa = r2a * ria * Hinv;
+            float wa, ga;
+            kernel_w_g(qa, H * ria, wa, ga);
+            Sw0 += wa;
+            Sdw0 += fmaf(qa * qa, ga, 3.0f * wa);
+          }
+        } else if (!done) {
+          for (int r = 0; r < 9; ++r) {
+            int32_t A0, B0;
+            warp_run(g, T, tx, ty, tz, r, A0, B0);
+            for (int32_t k = A0 + sub; k < B0; k += tpp) {
+              const float4 pj = spos[k];
+              const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const float ri = rsqrtf(fmaxf(r2, 1e-30f));
+              const float q = r2 * ri * Hinv;
+              float w, gg;
+              kernel_w_g(q, H * ri, w, gg);
+              Sw0 += w;
+              Sdw0 += fmaf(q * q, gg, 3.0f * w);
+            }
+          }
+        }
+        float Sw = Sw0 + Sw1, Sdw = Sdw0 + Sdw1;
+        Sw += __shfl_xor_sync(0xffffffffu, Sw, 1);
+        Sdw += __shfl_xor_sync(0xffffffffu, Sdw, 1);
+        if (tpp == 4) {
+          Sw += __shfl_xor_sync(0xffffffffu, Sw, 2);
+          Sdw += __shfl_xor_sync(0xffffffffu, Sdw, 2);
+        }
+        if (!done) {
+          passes = it + 1;
+          if (newton_step(Sw, Sdw, h, lo, hi, it, hcap, ph, atcap, conv)) done = true;
+        }
+      }
+      // 3. final pass at the converged h
+      const float H = kGammaK * (float)h;
+      const float Hinv = 1.0f / H;
+      DensSums s0, s1;
+      sums_zero(s0);
+      sums_zero(s1);
+      if (valid && !direct) {
+        int e = 0;
+        for (; e + 1 < cnt; e += 2) {
+          const int ka = lj[e * 32 + lane], kb = lj[(e + 1) * 32 + lane];
+          dens_pair(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
+          dens_pair(pi, vi, spos[kb], svel[kb], H, Hinv, s1);
+        }
+        if (e < cnt) {
+          const int ka = lj[e * 32 + lane];
+          dens_pair(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
+        }
+      } else if (valid) {
+        for (int r = 0; r < 9; ++r) {
+          int32_t A0, B0;
+          warp_run(g, T, tx, ty, tz, r, A0, B0);
+          for (int32_t k = A0 + sub; k < B0; k += tpp) {
+            const float4 pj = spos[k];
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2) dens_pair(pi, vi, pj, svel[k], H, Hinv, s0);
+          }
+        }
+      }
+      sums_add(s0, s1);
+      combine(s0, tpp);
+      if (valid && sub == 0) {
+        dens_write(a, ph, ti, h, s0, vi.w, passes, conv, atcap);
+        pair_acc += (unsigned long long)s0.npair;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  if (ph.count_pairs) {
+    unsigned long long v = pair_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(a.pairs, v);
+  }
+}
+
+// Blocks whose neighbourhood exceeded the staging buffer: one warp per target
+// cell; each lane owns a target and walks the 27 cells, streamed through a
+// per-warp shared buffer, with positions relative to the target cell.
+__global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs a, PhysDev ph) {
+  extern __shared__ float4 osm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* spos = osm + warp * (2 * kOvfCap);
+  float4* svel = spos + kOvfCap;
+  const int32_t n_items = a.misc_ro[kNumOverflow] * kBlkWarps;
+  unsigned long long pair_acc = 0;
+  for (int32_t item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
+       item += gridDim.x * kWarpsPerBlock) {
+    const BlockGeom g = block_geom(a.grid, a.n_sims, a.overflow[item / kBlkWarps]);
+    int tx, ty, tz;
+    if (!warp_cell(g, item % kBlkWarps, tx, ty, tz)) continue;
+    const int32_t nc = g.G.n_c;
+    const int32_t cx = g.c0x + tx, cy = g.c0y + ty, cz = g.c0z + tz;
+    const int32_t c = g.G.cell_base + cx + nc * (cy + nc * cz);
     const int32_t ts = a.cell_start[c], te = a.cell_start[c + 1];
-    if (ts >= te) continue;
-    const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, c)];
-    const int32_t local = c - G.cell_base, nc = G.n_c;
-    const int32_t cx = local % nc, cy = (local / nc) % nc, cz = local / (nc * nc);
-    const NbLane nb = neighbour_lane(lane, G.cell_base, cx, cy, cz, nc, G.cell_f, a.cell_start);
+    const NbLane nb = neighbour_lane(lane, g.G.cell_base, cx, cy, cz, nc, g.G.cell_f, a.cell_start);
     const int nsrc = warp_sum_int(nb.len);
-    const bool fits = nsrc <= kDensCap;
     auto put = [&](int slot, int32_t j, float ox, float oy, float oz) {
       float4 p = a.pos4[j];
       p.x += ox;
@@ -52,96 +399,36 @@ __global__ void __launch_bounds__(kThreads) k_density(sphh::DensityArgs a, PhysD
       spos[slot] = p;
       svel[slot] = a.vel4[j];
     };
-    if (fits) stage_sources(0, kDensCap, nb, lane, put);
-    // H may not exceed the cell: every neighbour must lie in the 27 cells.
-    const double hcap = (double)G.cell_f * (1.0 - 1e-5) / kGammaKd;
-
+    const double hcap = (double)g.G.cell_f * (1.0 - 1e-5) / kGammaKd;
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
       const bool valid = ti < te;
       const float4 pi = valid ? a.pos4[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 vi = valid ? a.vel4[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
-      double h = valid ? (double)a.hs[ti] : hcap;
-      if (!(h > 0.0)) h = 0.5 * hcap;
-      if (h > hcap) h = hcap;
+      double h = valid ? start_h(a.hs[ti], hcap) : hcap;
       double lo = 0.0, hi = INFINITY;
-      bool done = !valid;
+      bool done = !valid, atcap = false, conv = false;
       int it = 0;
       while (__any_sync(0xffffffffu, !done)) {
         const float H = kGammaK * (float)h;
         const float Hinv = 1.0f / H;
-        float Sw = 0.f, Sdw = 0.f, Smw = 0.f, Smdw = 0.f, Sdiv = 0.f, Scx = 0.f, Scy = 0.f, Scz = 0.f;
-        int npair = 0;
-        for (int v0 = 0; v0 < nsrc; v0 += kDensCap) {
-          const int cnt = fits ? nsrc : stage_sources(v0, kDensCap, nb, lane, put);
-#pragma unroll 4
-          for (int k = 0; k < cnt; ++k) {
-            const float4 pj = spos[k];
-            const float4 vj = svel[k];
-            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-            const float q = r2 * rinv * Hinv;
-            float w, g;
-            kernel_w_g(q, H * rinv, w, g);
-            const float dw = fmaf(q * q, g, 3.0f * w);
-            Sw += w;
-            Sdw += dw;
-            Smw = fmaf(pj.w, w, Smw);
-            Smdw = fmaf(pj.w, dw, Smdw);
-            const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
-            const float mg = pj.w * g;
-            Sdiv = fmaf(mg, fmaf(ux, dx, fmaf(uy, dy, uz * dz)), Sdiv);
-            Scx = fmaf(mg, fmaf(uz, dy, -uy * dz), Scx);
-            Scy = fmaf(mg, fmaf(ux, dz, -uz * dx), Scy);
-            Scz = fmaf(mg, fmaf(uy, dx, -ux * dy), Scz);
-            npair += q < 1.0f;
-          }
-          if (!fits) __syncwarp();
+        DensSums s;
+        sums_zero(s);
+        for (int v0 = 0; v0 < nsrc; v0 += kOvfCap) {
+          const int cnt = stage_sources(v0, kOvfCap, nb, lane, put);
+          for (int k = 0; k < cnt; ++k) dens_pair(pi, vi, spos[k], svel[k], H, Hinv, s);
+          __syncwarp();
         }
         if (!done) {
-          const double A = (double)Sw / g3 - eta3;
-          const double B = 3.0 * eta3 - (double)Sdw / g3;
-          if (A < 0.0) lo = h; else hi = h;
-          const bool conv = (B > 0.0) && (fabs(A) <= ph.h_tol * B);
-          const bool atcap = (h >= hcap) && (A < 0.0);
-          const bool last = it + 1 >= ph.max_h_iter;
-          if (conv || atcap || last) {
-            const int32_t p = a.perm[ti];
-            const float H2inv = Hinv * Hinv;
-            const float rho = Smw * H2inv * Hinv;
-            const float fi = 1.0f / (1.0f - Smdw / (3.0f * Smw));
-            const float div = Sdiv * H2inv / Smw;
-            const float curl = sqrtf(fmaf(Scx, Scx, fmaf(Scy, Scy, Scz * Scz))) * H2inv / Smw;
-            const float P = (ph.gamma - 1.0f) * vi.w * rho;
-            const float cs = sqrtf(ph.gamma * P / rho);
-            const float hf = (float)h;
-            const float B_i = fabsf(div) / (fabsf(div) + curl + ph.eps_balsara * cs / hf);
-            a.h[p] = hf;
-            a.rho[p] = rho;
-            a.f[p] = fi;
-            a.div_v[p] = div;
-            a.curl_v[p] = curl;
-            a.P[p] = P;
-            a.c[p] = cs;
-            a.B[p] = B_i;
-            if (a.n_iter) a.n_iter[p] = it + 1;
-            if (atcap) atomicOr(a.status, SPH_ST_REBUILD);
-            else if (!conv) atomicOr(a.status, SPH_ST_H_NOCONV);
-            pair_acc += (unsigned long long)npair;
+          const int passes = it + 1;
+          if (newton_step(s.w, s.dw, h, lo, hi, it, hcap, ph, atcap, conv)) {
+            dens_write(a, ph, ti, h, s, vi.w, passes, conv, atcap);
+            pair_acc += (unsigned long long)s.npair;
             done = true;
-          } else {
-            double hn = (B > 0.0) ? h * (1.0 - A / B) : 2.0 * h;
-            hn = fmin(fmax(hn, 0.5 * h), 2.0 * h);
-            if (!(B > 0.0) || !(hn > lo) || !(hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
-            if (hn > hcap) hn = hcap;
-            h = hn;
-            ++it;
           }
         }
       }
     }
-    __syncwarp();
   }
   if (ph.count_pairs) {
     unsigned long long v = pair_acc;
@@ -157,16 +444,25 @@ namespace sphh {
 using namespace sphk;
 
 cudaError_t launch_density(const DensityArgs& a, const PhysDev& ph, cudaStream_t st) {
-  static int blocks_per_sm = 0;
-  if (!blocks_per_sm) {
+  static int bps = 0, bps_o = 0;
+  if (!bps) {
     cudaError_t e = cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kDensSmem);
+                                         (int)kDensBlkSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_density, kThreads, kDensSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_density, kBlkThreads, kDensBlkSmem);
     if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    e = cudaFuncSetAttribute(k_density_overflow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kOvfSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_o, k_density_overflow, kThreads, kOvfSmem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+    if (bps_o < 1) bps_o = 1;
   }
-  k_density<<<a.num_sms * blocks_per_sm, kThreads, kDensSmem, st>>>(a, ph);
+  cudaError_t e = cudaMemsetAsync(a.misc + kNumOverflow, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  k_density<<<a.num_sms * bps, kBlkThreads, kDensBlkSmem, st>>>(a, ph);
+  k_density_overflow<<<a.num_sms * bps_o, kThreads, kOvfSmem, st>>>(a, ph);
   return cudaGetLastError();
 }
 

@@ -2,123 +2,337 @@
 // "Minimal" density-energy equations of motion, artificial viscosity with the
 // Balsara switch, du/dt and the signal velocity.
 //
-// Same layout as the density loop: one warp per target cell, the 27
-// neighbour cells staged in shared memory, one lane per target.  Per pair,
-// with x_ij = x_i - x_j, v_ij = v_i - v_j, G = g(q) / H^5 (so that
-// grad_i W(r_ij, h) = G x_ij) evaluated once with h_i and once with h_j:
+// k_force: the block layout of the density loop (blocks.cuh) with tpp lanes
+// per target.  A filter pass keeps, per lane, the staged sources with
+// r_ij < max(H_i, H_j), j != i (the force neighbour set); the pair pass then
+// walks only that list.  Per pair, with x_ij = x_i - x_j, v_ij = v_i - v_j,
+// and G = g(q) / H^5 (so that grad_i W(r_ij, h) = G x_ij) evaluated once with
+// h_i and once with h_j:
 //   mu     = min(v_ij . x_ij, 0) / r
 //   vsig   = c_i + c_j - beta mu
 //   nu     = -alpha_V (B_i + B_j)/2 mu vsig / ((rho_i + rho_j)/2)
 //   a_i   -= m_j [ fP_i G_i + fP_j G_j + nu/2 (f_i G_i + f_j G_j) ] x_ij
 //   du_i  += m_j [ fP_i G_i + nu/4 (f_i G_i + f_j G_j) ] v_ij . x_ij
-// with fP = f P / rho^2.  Both kernel gradients vanish beyond their support,
-// so candidates outside max(H_i, H_j) contribute exactly zero; only the
-// signal-velocity maximum needs the explicit r < max(H_i, H_j), j != i test.
+// with fP = f P / rho^2; v_sig,i is the maximum of vsig over the list.
+// Blocks whose neighbourhood does not fit are done by k_force_overflow.
+#include "blocks.cuh"
 #include "sph_internal.cuh"
 #include "sph_launch.h"
 #include "stencil.cuh"
 
 namespace sphk {
 
-constexpr int kForceCap = 384;
-// per source: pos4 (x, y, z, m), vel4 (vx, vy, vz, 1/H), th4 (fP, f, c, B),
-// rh4 (rho, H, 1/H^5, -), index
-constexpr size_t kForceSmem = (size_t)kWarpsPerBlock * kForceCap * (4 * sizeof(float4) + sizeof(int32_t));
+constexpr int kForceBlkCap = kBlkStageCap;
+constexpr int kFListCap = 48;
+// per source: A (x, y, z, H), B (vx, vy, vz, m), C (fP, f, c, B), D (rho, 1/H)
+constexpr size_t kForceBlkSmem = (size_t)kForceBlkCap * (3 * sizeof(float4) + sizeof(float2)) +
+                                 (size_t)kBlkWarps * kFListCap * 32 * sizeof(uint16_t) + sizeof(StageTable) +
+                                 sizeof(BlockTargets) + (size_t)kForceBlkCap * (sizeof(uint16_t) + sizeof(uint8_t));
+constexpr int kFOvfCap = 160;
+constexpr size_t kFOvfSmem = (size_t)kWarpsPerBlock * kFOvfCap * (3 * sizeof(float4) + sizeof(float2));
 
-__global__ void __launch_bounds__(kThreads) k_force(sphh::ForceArgs a, PhysDev ph) {
-  extern __shared__ float4 fsm[];
+struct ForceSums {
+  float ax, ay, az, du, vsig;
+  int npair;
+};
+
+struct ForceTarget {
+  float4 A, B, C;
+  float2 D;
+  float Hinv5;
+};
+
+__device__ __forceinline__ void fsums_zero(ForceSums& s) {
+  s.ax = s.ay = s.az = s.du = s.vsig = 0.f;
+  s.npair = 0;
+}
+
+__device__ __forceinline__ void force_pair(const ForceTarget& T, const float4& Aj, const float4& Bj,
+                                           const float4& Cj, const float2& Dj, const PhysDev& ph,
+                                           bool counted, ForceSums& s) {
+  const float dx = T.A.x - Aj.x, dy = T.A.y - Aj.y, dz = T.A.z - Aj.z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+  const float r = r2 * rinv;
+  const float Gi = kernel_g(r * T.D.y, T.A.w * rinv) * T.Hinv5;
+  const float Hj2 = Dj.y * Dj.y;
+  const float Gj = kernel_g(r * Dj.y, Aj.w * rinv) * (Hj2 * Hj2 * Dj.y);
+  const float vx = T.B.x - Bj.x, vy = T.B.y - Bj.y, vz = T.B.z - Bj.z;
+  const float vdotx = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+  const float mu = fminf(vdotx, 0.0f) * rinv;
+  const float vs = fmaf(-ph.beta_v, mu, T.C.z + Cj.z);
+  const float nu = __fdividef(-ph.alpha_v * (T.C.w + Cj.w) * mu * vs, T.D.x + Dj.x);
+  const float piG = T.C.x * Gi;
+  const float visc = fmaf(T.C.y, Gi, Cj.y * Gj);
+  const float sc = Bj.w * fmaf(0.5f * nu, visc, fmaf(Cj.x, Gj, piG));
+  s.ax = fmaf(-sc, dx, s.ax);
+  s.ay = fmaf(-sc, dy, s.ay);
+  s.az = fmaf(-sc, dz, s.az);
+  s.du = fmaf(Bj.w * fmaf(0.25f * nu, visc, piG), vdotx, s.du);
+  s.vsig = counted ? fmaxf(s.vsig, vs) : s.vsig;
+  s.npair += counted;
+}
+
+__device__ __forceinline__ void finish_target(ForceTarget& T) {
+  const float h2 = T.D.y * T.D.y;
+  T.Hinv5 = h2 * h2 * T.D.y;
+}
+
+__device__ __forceinline__ void force_write(const sphh::ForceArgs& a, int32_t ti, const ForceSums& s) {
+  const int32_t p = a.perm[ti];
+  a.ax[p] = s.ax;
+  a.ay[p] = s.ay;
+  a.az[p] = s.az;
+  a.du_dt[p] = s.du;
+  a.v_sig[p] = s.vsig;
+}
+
+__device__ __forceinline__ void fcombine(ForceSums& s, int tpp) {
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    if (o < tpp) {
+      s.ax += __shfl_xor_sync(0xffffffffu, s.ax, o);
+      s.ay += __shfl_xor_sync(0xffffffffu, s.ay, o);
+      s.az += __shfl_xor_sync(0xffffffffu, s.az, o);
+      s.du += __shfl_xor_sync(0xffffffffu, s.du, o);
+      s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, o));
+      s.npair += __shfl_xor_sync(0xffffffffu, s.npair, o);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, PhysDev ph) {
+  extern __shared__ __align__(16) unsigned char fsm_raw[];
+  float4* sA = reinterpret_cast<float4*>(fsm_raw);
+  float4* sB = sA + kForceBlkCap;
+  float4* sC = sB + kForceBlkCap;
+  float2* sD = reinterpret_cast<float2*>(sC + kForceBlkCap);
+  uint16_t* lj_all = reinterpret_cast<uint16_t*>(sD + kForceBlkCap);
+  StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * kFListCap * 32);
+  BlockTargets& BT = *reinterpret_cast<BlockTargets*>(&T + 1);
+  uint16_t* tgt_slot = reinterpret_cast<uint16_t*>(&BT + 1);
+  uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + kForceBlkCap);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* spos = fsm + warp * (4 * kForceCap);
-  float4* svel = spos + kForceCap;
-  float4* sth = svel + kForceCap;
-  float4* srh = sth + kForceCap;
-  int32_t* sidx = reinterpret_cast<int32_t*>(fsm + kWarpsPerBlock * 4 * kForceCap) + warp * kForceCap;
-  const int32_t total = a.misc_ro[kTotalCells];
-  const float half_alpha = 0.5f * ph.alpha_v;
+  uint16_t* lj = lj_all + warp * (kFListCap * 32);
+  const int32_t total = a.misc_ro[kTotalBlocks];
   unsigned long long pair_acc = 0;
 
-  for (int32_t c = blockIdx.x * kWarpsPerBlock + warp; c < total; c += gridDim.x * kWarpsPerBlock) {
-    const int32_t ts = a.cell_start[c], te = a.cell_start[c + 1];
-    if (ts >= te) continue;
-    const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, c)];
-    const int32_t local = c - G.cell_base, nc = G.n_c;
-    const int32_t cx = local % nc, cy = (local / nc) % nc, cz = local / (nc * nc);
-    const NbLane nb = neighbour_lane(lane, G.cell_base, cx, cy, cz, nc, G.cell_f, a.cell_start);
-    const int nsrc = warp_sum_int(nb.len);
-    const bool fits = nsrc <= kForceCap;
-    auto put = [&](int slot, int32_t j, float ox, float oy, float oz) {
-      float4 p = a.pos4[j];
+  for (int32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const BlockGeom g = block_geom(a.grid, a.n_sims, b);
+    const int32_t nsrc = build_stage_table(g, a.cell_start, T);
+    if (nsrc > kForceBlkCap) {
+      if (threadIdx.x == 0) a.overflow[atomicAdd(&a.misc[kNumOverflow], 1)] = b;
+      __syncthreads();
+      continue;
+    }
+    for (int32_t v = threadIdx.x; v < nsrc; v += kBlkThreads) {
+      const int k = staged_cell_of(T, v);
+      float ox, oy, oz;
+      staged_offset(g, k, ox, oy, oz);
+      const int32_t j = T.gstart[k] + (v - T.start[k]);
+      float4 p = a.fA[j];
       p.x += ox;
       p.y += oy;
       p.z += oz;
-      spos[slot] = p;
-      const float4 v = a.vel4[j];
-      svel[slot] = v;
-      sth[slot] = a.th4[j];
-      const float Hinv = v.w;
-      const float H2 = Hinv * Hinv;
-      srh[slot] = make_float4(a.rho_s[j], 1.0f / Hinv, H2 * H2 * Hinv, 0.0f);
-      sidx[slot] = j;
-    };
-    if (fits) stage_sources(0, kForceCap, nb, lane, put);
+      sA[v] = p;
+      sB[v] = a.fB[j];
+      sC[v] = a.fC[j];
+      sD[v] = a.fD[j];
+    }
+    build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
 
+    const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
+    const int sub = lane & (tpp - 1);
+    for (int rd = warp; rd < BT.rounds; rd += kBlkWarps) {
+      const int t = lane >> lg;
+      const int32_t e_t = rd * per + t;
+      const bool valid = (t < per) && (e_t < BT.n);
+      int self_slot = 0, kc = BT.cell_k[0];
+      if (valid) {
+        self_slot = tgt_slot[e_t];
+        kc = BT.cell_k[tgt_cell[e_t]];
+      }
+      const int tx = kc % g.ex - 1, ty = (kc / g.ex) % g.ey - 1, tz = kc / (g.ex * g.ey) - 1;
+      const int32_t ti = T.gstart[kc] + (self_slot - T.start[kc]);
+      ForceTarget Tg;
+      Tg.A = sA[self_slot];
+      Tg.B = sB[self_slot];
+      Tg.C = sC[self_slot];
+      Tg.D = sD[self_slot];
+      finish_target(Tg);
+      ForceSums s0, s1;
+      fsums_zero(s0);
+      fsums_zero(s1);
+      // the density loop's list of this lane (same build, same rounds): all
+      // sources within the cell size, a superset of r < max(H_i, H_j)
+      const int64_t col = (int64_t)ti * 4 + sub;
+      int cnt = -1;
+      if (a.lists != nullptr && valid) {
+        const int lc = (int)a.list_cnt[col];
+        if (lc <= kFListCap) {
+          const uint4* src = reinterpret_cast<const uint4*>(a.lists + col * kListRegion);
+          for (int e8 = 0; e8 < lc; e8 += 8) {
+            const uint4 v = src[e8 >> 3];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int e0 = e8 + 2 * q;
+              if (e0 < lc) lj[e0 * 32 + lane] = (uint16_t)(w[q] & 0xffffu);
+              if (e0 + 1 < lc) lj[(e0 + 1) * 32 + lane] = (uint16_t)(w[q] >> 16);
+            }
+          }
+          cnt = lc;
+        }
+      }
+      if (valid && cnt < 0) {
+        // own filter (no list, or the density list overflowed)
+        cnt = 0;
+        for (int r = 0; r < 9; ++r) {
+          int32_t A0, B0;
+          warp_run(g, T, tx, ty, tz, r, A0, B0);
+#pragma unroll 4
+          for (int32_t k = A0 + sub; k < B0; k += tpp) {
+            const float4 Aj = sA[k];
+            const float dx = Tg.A.x - Aj.x, dy = Tg.A.y - Aj.y, dz = Tg.A.z - Aj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float Hm = fmaxf(Tg.A.w, Aj.w);
+            if (r2 < Hm * Hm && k != self_slot) {
+              if (cnt < kFListCap) lj[cnt * 32 + lane] = (uint16_t)k;
+              ++cnt;
+            }
+          }
+        }
+      }
+      if (valid && cnt <= kFListCap) {
+        // pairs beyond both supports add exactly zero; the self pair and
+        // pairs beyond max(H_i, H_j) do not enter v_sig or the pair count
+        int e = 0;
+        for (; e + 1 < cnt; e += 2) {
+          const int ka = lj[e * 32 + lane], kb = lj[(e + 1) * 32 + lane];
+          const float4 Aa = sA[ka], Ab = sA[kb];
+          const float dxa = Tg.A.x - Aa.x, dya = Tg.A.y - Aa.y, dza = Tg.A.z - Aa.z;
+          const float dxb = Tg.A.x - Ab.x, dyb = Tg.A.y - Ab.y, dzb = Tg.A.z - Ab.z;
+          const float r2a = fmaf(dxa, dxa, fmaf(dya, dya, dza * dza));
+          const float r2b = fmaf(dxb, dxb, fmaf(dyb, dyb, dzb * dzb));
+          const float Hma = fmaxf(Tg.A.w, Aa.w), Hmb = fmaxf(Tg.A.w, Ab.w);
+          force_pair(Tg, Aa, sB[ka], sC[ka], sD[ka], ph, r2a < Hma * Hma && ka != self_slot, s0);
+          force_pair(Tg, Ab, sB[kb], sC[kb], sD[kb], ph, r2b < Hmb * Hmb && kb != self_slot, s1);
+        }
+        if (e < cnt) {
+          const int ka = lj[e * 32 + lane];
+          const float4 Aa = sA[ka];
+          const float dxa = Tg.A.x - Aa.x, dya = Tg.A.y - Aa.y, dza = Tg.A.z - Aa.z;
+          const float r2a = fmaf(dxa, dxa, fmaf(dya, dya, dza * dza));
+          const float Hma = fmaxf(Tg.A.w, Aa.w);
+          force_pair(Tg, Aa, sB[ka], sC[ka], sD[ka], ph, r2a < Hma * Hma && ka != self_slot, s0);
+        }
+      } else if (valid) {
+        // list overflow: walk the runs directly
+        for (int r = 0; r < 9; ++r) {
+          int32_t A0, B0;
+          warp_run(g, T, tx, ty, tz, r, A0, B0);
+          for (int32_t k = A0 + sub; k < B0; k += tpp) {
+            const float4 Aj = sA[k];
+            const float dx = Tg.A.x - Aj.x, dy = Tg.A.y - Aj.y, dz = Tg.A.z - Aj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float Hm = fmaxf(Tg.A.w, Aj.w);
+            if (r2 < Hm * Hm && k != self_slot) force_pair(Tg, Aj, sB[k], sC[k], sD[k], ph, true, s0);
+          }
+        }
+      }
+      s0.ax += s1.ax;
+      s0.ay += s1.ay;
+      s0.az += s1.az;
+      s0.du += s1.du;
+      s0.vsig = fmaxf(s0.vsig, s1.vsig);
+      s0.npair += s1.npair;
+      fcombine(s0, tpp);
+      if (valid && sub == 0) {
+        force_write(a, ti, s0);
+        pair_acc += (unsigned long long)s0.npair;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  if (ph.count_pairs) {
+    unsigned long long v = pair_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(a.pairs, v);
+  }
+}
+
+// Blocks whose neighbourhood exceeded the staging buffer: one warp per target
+// cell, lane = target, the 27 cells streamed through a per-warp buffer with
+// positions relative to the target cell.
+__global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, PhysDev ph) {
+  extern __shared__ __align__(16) unsigned char fo_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = fo_raw + warp * (kFOvfSmem / kWarpsPerBlock);
+  float4* sA = reinterpret_cast<float4*>(base);
+  float4* sB = sA + kFOvfCap;
+  float4* sC = sB + kFOvfCap;
+  float2* sD = reinterpret_cast<float2*>(sC + kFOvfCap);
+  const int32_t n_items = a.misc_ro[kNumOverflow] * kBlkWarps;
+  unsigned long long pair_acc = 0;
+  for (int32_t item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
+       item += gridDim.x * kWarpsPerBlock) {
+    const BlockGeom g = block_geom(a.grid, a.n_sims, a.overflow[item / kBlkWarps]);
+    int tx, ty, tz;
+    if (!warp_cell(g, item % kBlkWarps, tx, ty, tz)) continue;
+    const int32_t nc = g.G.n_c;
+    const int32_t cx = g.c0x + tx, cy = g.c0y + ty, cz = g.c0z + tz;
+    const int32_t c = g.G.cell_base + cx + nc * (cy + nc * cz);
+    const int32_t ts = a.cell_start[c], te = a.cell_start[c + 1];
+    const NbLane nb = neighbour_lane(lane, g.G.cell_base, cx, cy, cz, nc, g.G.cell_f, a.cell_start);
+    int incl = nb.len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int nsrc = __shfl_sync(0xffffffffu, incl, 31);
+    const int self_base = __shfl_sync(0xffffffffu, incl - nb.len, 13);
+    auto put = [&](int slot, int32_t j, float ox, float oy, float oz) {
+      float4 p = a.fA[j];
+      p.x += ox;
+      p.y += oy;
+      p.z += oz;
+      sA[slot] = p;
+      sB[slot] = a.fB[j];
+      sC[slot] = a.fC[j];
+      sD[slot] = a.fD[j];
+    };
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
       const bool valid = ti < te;
       const int32_t tl = valid ? ti : ts;
-      const float4 pi = a.pos4[tl];
-      const float4 vi = a.vel4[tl];
-      const float4 thi = a.th4[tl];
-      const float rhoi = a.rho_s[tl];
-      const float Hinv_i = vi.w;
-      const float H_i = 1.0f / Hinv_i;
-      const float Hinv5_i = Hinv_i * Hinv_i * Hinv_i * Hinv_i * Hinv_i;
-      float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f, vsig = 0.f;
-      int npair = 0;
-      for (int v0 = 0; v0 < nsrc; v0 += kForceCap) {
-        const int cnt = fits ? nsrc : stage_sources(v0, kForceCap, nb, lane, put);
-#pragma unroll 2
+      ForceTarget Tg;
+      Tg.A = a.fA[tl];
+      Tg.B = a.fB[tl];
+      Tg.C = a.fC[tl];
+      Tg.D = a.fD[tl];
+      finish_target(Tg);
+      ForceSums s;
+      fsums_zero(s);
+      for (int v0 = 0; v0 < nsrc; v0 += kFOvfCap) {
+        const int cnt = stage_sources(v0, kFOvfCap, nb, lane, put);
         for (int k = 0; k < cnt; ++k) {
-          const float4 pj = spos[k];
-          const float4 vj = svel[k];
-          const float4 thj = sth[k];
-          const float4 rhj = srh[k];
-          const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+          const float4 Aj = sA[k];
+          const float dx = Tg.A.x - Aj.x, dy = Tg.A.y - Aj.y, dz = Tg.A.z - Aj.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-          const float r = r2 * rinv;
-          const float Gi = kernel_g(r * Hinv_i, H_i * rinv) * Hinv5_i;
-          const float Gj = kernel_g(r * vj.w, rhj.y * rinv) * rhj.z;
-          const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-          const float vdotx = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
-          const float mu = fminf(vdotx, 0.0f) * rinv;
-          const float vs = fmaf(-ph.beta_v, mu, thi.z + thj.z);
-          const float nu = __fdividef(-half_alpha * (thi.w + thj.w) * mu * vs, 0.5f * (rhoi + rhj.x));
-          const float piG = thi.x * Gi;
-          const float visc = fmaf(thi.y, Gi, thj.y * Gj);
-          const float s = pj.w * fmaf(0.5f * nu, visc, fmaf(thj.x, Gj, piG));
-          ax = fmaf(-s, dx, ax);
-          ay = fmaf(-s, dy, ay);
-          az = fmaf(-s, dz, az);
-          du = fmaf(pj.w * fmaf(0.25f * nu, visc, piG), vdotx, du);
-          const float Hm = fmaxf(H_i, rhj.y);
-          const bool in = (r2 < Hm * Hm) && (sidx[k] != ti);
-          vsig = in ? fmaxf(vsig, vs) : vsig;
-          npair += in;
+          const float Hm = fmaxf(Tg.A.w, Aj.w);
+          const bool self = (v0 + k == self_base + (ti - ts));
+          if (r2 < Hm * Hm && !self) force_pair(Tg, Aj, sB[k], sC[k], sD[k], ph, true, s);
         }
         __syncwarp();
       }
       if (valid) {
-        const int32_t p = a.perm[ti];
-        a.ax[p] = ax;
-        a.ay[p] = ay;
-        a.az[p] = az;
-        a.du_dt[p] = du;
-        a.v_sig[p] = vsig;
-        pair_acc += (unsigned long long)npair;
+        force_write(a, ti, s);
+        pair_acc += (unsigned long long)s.npair;
       }
     }
-    __syncwarp();
   }
   if (ph.count_pairs) {
     unsigned long long v = pair_acc;
@@ -134,16 +348,25 @@ namespace sphh {
 using namespace sphk;
 
 cudaError_t launch_force(const ForceArgs& a, const PhysDev& ph, cudaStream_t st) {
-  static int blocks_per_sm = 0;
-  if (!blocks_per_sm) {
+  static int bps = 0, bps_o = 0;
+  if (!bps) {
     cudaError_t e = cudaFuncSetAttribute(k_force, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kForceSmem);
+                                         (int)kForceBlkSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_force, kThreads, kForceSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_force, kBlkThreads, kForceBlkSmem);
     if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    e = cudaFuncSetAttribute(k_force_overflow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFOvfSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_o, k_force_overflow, kThreads, kFOvfSmem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+    if (bps_o < 1) bps_o = 1;
   }
-  k_force<<<a.num_sms * blocks_per_sm, kThreads, kForceSmem, st>>>(a, ph);
+  cudaError_t e = cudaMemsetAsync(a.misc + kNumOverflow, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  k_force<<<a.num_sms * bps, kBlkThreads, kForceBlkSmem, st>>>(a, ph);
+  k_force_overflow<<<a.num_sms * bps_o, kThreads, kFOvfSmem, st>>>(a, ph);
   return cudaGetLastError();
 }
 

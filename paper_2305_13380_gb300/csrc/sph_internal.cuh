@@ -27,6 +27,8 @@ enum MiscSlot {
   kStatus = 0,       // SPH_ST_* bits
   kTotalCells = 1,   // number of cells over all simulations of the last build
   kNumBigCells = 2,  // cells routed to the block-level sort
+  kTotalBlocks = 3,  // number of 2x2x2 blocks of cells over all simulations
+  kNumOverflow = 4,  // blocks queued for the overflow kernel of a loop
   kMiscWords = 8
 };
 
@@ -37,7 +39,7 @@ struct GridDev {
   float cell_f;       // cell side (FP32)
   int32_t n_c;        // cells per side
   int32_t cell_base;  // first global cell id of this simulation
-  int32_t pad;
+  int32_t blk_base;   // first global 2x2x2-block id of this simulation
   int64_t part_base;  // first pool index of this simulation
   int64_t n;          // particles in this simulation
 };

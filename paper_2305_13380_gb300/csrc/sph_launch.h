@@ -25,6 +25,7 @@ struct BuildArgs {
   const float* h;
   sphk::GridDev* grid;
   int32_t* misc;
+  int32_t* hmax_bits;  // per simulation scratch
   int32_t *key, *slot, *count, *cell_start, *scan_sums, *perm, *big;
 };
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t st);
@@ -41,6 +42,8 @@ struct GatherDensityArgs {
 };
 cudaError_t launch_gather_density(const GatherDensityArgs& a, cudaStream_t st);
 
+// Force-loop copies: fA = (x, y, z, H), fB = (vx, vy, vz, m),
+// fC = (f P / rho^2, f, c, B), fD = (rho, 1/H); positions relative to the cell.
 struct GatherForceArgs {
   int64_t n_total;
   int n_sims;
@@ -48,8 +51,8 @@ struct GatherForceArgs {
   const sphk::GridDev* grid;
   const double *x, *y, *z;
   const float *vx, *vy, *vz, *m, *h, *rho, *f, *P, *c, *B;
-  float4 *pos4, *vel4, *th4;
-  float* rho_s;
+  float4 *fA, *fB, *fC;
+  float2* fD;
 };
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
 
@@ -58,7 +61,9 @@ struct DensityArgs {
   int n_sims;
   int num_sms;
   const sphk::GridDev* grid;
-  const int32_t* misc_ro;  // total cells
+  const int32_t* misc_ro;  // total cells / blocks, overflow count
+  int32_t* misc;           // same words, written by the loop kernels
+  int32_t* overflow;       // blocks queued for the overflow kernel
   int32_t* status;
   unsigned long long* pairs;
   const int32_t *cell_start, *perm;
@@ -66,6 +71,10 @@ struct DensityArgs {
   const float* hs;
   float *h, *rho, *f, *div_v, *curl_v, *P, *c, *B;
   int32_t* n_iter;
+  // optional neighbour lists for the force loop of the same build: the
+  // entries of (sorted target ti, lane s) in lists[(4 ti + s) * kListRegion ...]
+  uint16_t* lists;
+  uint16_t* list_cnt;  // per (4 ti + s); 0xffff = overflow (not stored)
 };
 cudaError_t launch_density(const DensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 
@@ -74,11 +83,15 @@ struct ForceArgs {
   int num_sms;
   const sphk::GridDev* grid;
   const int32_t* misc_ro;
+  int32_t* misc;
+  int32_t* overflow;
   unsigned long long* pairs;
   const int32_t *cell_start, *perm;
-  const float4 *pos4, *vel4, *th4;
-  const float* rho_s;
+  const float4 *fA, *fB, *fC;
+  const float2* fD;
   float *ax, *ay, *az, *du_dt, *v_sig;
+  const uint16_t* lists;  // the density loop's lists, or nullptr
+  const uint16_t* list_cnt;
 };
 cudaError_t launch_force(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 
@@ -97,9 +110,10 @@ struct StepArgs {
   float *ax, *ay, *az, *du_dt, *v_sig;
   float *vpx, *vpy, *vpz, *up;  // predicted velocity / energy (scratch)
   double* dt;                   // per simulation
+  unsigned long long* dt_bits;  // per simulation scratch (min of H / v_sig as FP64 bits)
   int32_t* status;
 };
-cudaError_t launch_dt(const StepArgs& a, cudaStream_t st);
+cudaError_t launch_dt(const StepArgs& a, cudaStream_t st);  // uses a.dt_bits scratch
 cudaError_t launch_kick_drift(const StepArgs& a, cudaStream_t st);
 cudaError_t launch_kick(const StepArgs& a, cudaStream_t st);
 cudaError_t launch_conservation(int n_sims, const int64_t* sim_offset, const float* m, const float* vx,

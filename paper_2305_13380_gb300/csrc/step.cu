@@ -18,26 +18,52 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// dt_s = C_CFL min_i H_i / v_sig,i over simulation s (one block per sim).
-// A simulation whose signal velocities are all zero gets dt = 0.
-__global__ void k_dt(const int64_t* __restrict__ sim_offset, int n_sims, double cfl,
-                     const float* __restrict__ h, const float* __restrict__ v_sig,
-                     double* __restrict__ dt, int32_t* __restrict__ status) {
-  const int s = blockIdx.x;
-  if (s >= n_sims) return;
+// dt_s = C_CFL min_i H_i / v_sig,i over simulation s.  Non-negative doubles
+// order like their bit patterns, so the minimum is taken with an integer
+// atomicMin on the bits: each thread keeps a running minimum for the
+// simulation it is in, lanes of one simulation combine with shuffles, and one
+// lane per group publishes.  Particles with v_sig = 0 do not limit dt; a
+// simulation without any signal velocity gets dt = 0.
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+
+__global__ void k_dt_init(unsigned long long* __restrict__ bits, int n_sims) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x)
+    bits[s] = kInfBits;
+}
+
+__global__ void k_dt_min(const int64_t* __restrict__ sim_offset, int n_sims, int64_t n_total,
+                         const float* __restrict__ h, const float* __restrict__ v_sig,
+                         unsigned long long* __restrict__ bits) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int cur = -1;
   double m = INFINITY;
-  for (int64_t p = sim_offset[s] + threadIdx.x; p < sim_offset[s + 1]; p += blockDim.x) {
+  for (; p < n_total; p += stride) {
+    const int s = sim_of_particle(sim_offset, n_sims, p);
+    if (s != cur) {
+      if (cur >= 0 && m < INFINITY) atomicMin(&bits[cur], (unsigned long long)__double_as_longlong(m));
+      cur = s;
+      m = INFINITY;
+    }
     const double vs = (double)v_sig[p];
     if (vs > 0.0) m = fmin(m, kGammaKd * (double)h[p] / vs);
   }
-  __shared__ double red[32];
-  m = warp_min_d(m);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = INFINITY;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmin(r, red[w]);
-    dt[s] = isinf(r) ? 0.0 : cfl * r;
+  // lanes holding the same simulation combine, then one of them publishes
+  const unsigned grp = __match_any_sync(0xffffffffu, cur);
+  const int lane = threadIdx.x & 31;
+  for (int o = 0; o < 32; ++o) {
+    const double other = __shfl_sync(0xffffffffu, m, o);
+    if ((grp >> o) & 1u) m = fmin(m, other);
+  }
+  if (cur >= 0 && m < INFINITY && lane == __ffs(grp) - 1)
+    atomicMin(&bits[cur], (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_dt_final(const unsigned long long* __restrict__ bits, int n_sims, double cfl,
+                           double* __restrict__ dt) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x) {
+    const double m = __longlong_as_double((long long)bits[s]);
+    dt[s] = isinf(m) ? 0.0 : cfl * m;
   }
 }
 
@@ -139,7 +165,15 @@ static int blocks_for(int64_t n) {
 }
 
 cudaError_t launch_dt(const StepArgs& a, cudaStream_t st) {
-  k_dt<<<a.n_sims, 256, 0, st>>>(a.sim_offset, a.n_sims, a.cfl, a.h, a.v_sig, a.dt, a.status);
+  const int sb = (a.n_sims + 255) / 256;
+  k_dt_init<<<sb, 256, 0, st>>>(a.dt_bits, a.n_sims);
+  if (a.n_total > 0) {
+    int64_t b = (a.n_total + 255) / 256;
+    const int64_t cap = (int64_t)a.num_sms * 8;
+    if (b > cap) b = cap;
+    k_dt_min<<<(int)b, 256, 0, st>>>(a.sim_offset, a.n_sims, a.n_total, a.h, a.v_sig, a.dt_bits);
+  }
+  k_dt_final<<<sb, 256, 0, st>>>(a.dt_bits, a.n_sims, a.cfl, a.dt);
   return cudaGetLastError();
 }
 cudaError_t launch_kick_drift(const StepArgs& a, cudaStream_t st) {
