@@ -236,6 +236,35 @@ int sph_kernel_times(sph_ctx* ctx, double* ms_out, int64_t* calls_out);
  * out[1] = force pairs r < max(H_i, H_j), j != i. */
 int sph_pair_counts(sph_ctx* ctx, int64_t* out);
 
+/* Cell build for callers that cannot allocate device memory (code running in
+ * another framework's memory arena, loops whose allocator must not
+ * synchronise the device, plugins that are only handed buffers).  The paper
+ * has no counterpart: this is a deployment variant of sph_build_cells.
+ *
+ * It computes the same grid and the same lists as sph_build_cells on a
+ * context whose parameters have box_size and cell_margin (bit-identical
+ * cell_start and perm), but keeps all of its scratch in one fixed array
+ * compiled into the library (about 2.6 MB, held by every GPU that loads the
+ * library until the process exits) and calls no allocating routine.
+ *   n              particles, 0 <= n <= 65536 (more: SPH_E_CAPACITY)
+ *   x, y, z, h     device inputs (length n)
+ *   cell_start     device output, cell_start_cap >= 8 n + 217 entries; the
+ *                  first n_c^3 + 1 are written
+ *   perm           device output (length n)
+ *   n_c_out        optional device int32: cells per side
+ *   status_out     optional device int32: SPH_ST_* bits of this build
+ *   stream         cudaStream_t (NULL = legacy default stream)
+ * The first call on a device resolves the address of the fixed array on that
+ * device (with that device current); make that first call before any stream
+ * capture.  Every call on a device shares the array: calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race
+ * and corrupt each other's results.  Returns SPH_OK when the work is
+ * enqueued. */
+int sph_build_cells_static(int64_t n, const double* x, const double* y, const double* z,
+                           const float* h, double box_size, double cell_margin,
+                           int32_t* cell_start, int64_t cell_start_cap, int32_t* perm,
+                           int32_t* n_c_out, int32_t* status_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

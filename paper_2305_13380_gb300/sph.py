@@ -114,10 +114,12 @@ def lib():
         L.sph_conservation.argtypes = [_P, C.POINTER(sph_pool), _P]
         L.sph_pair_counts.argtypes = [_P, C.POINTER(C.c_int64)]
         L.sph_kernel_times.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.sph_build_cells_static.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_double, C.c_double,
+                                             _P, C.c_int64, _P, _P, _P, _P]
         for f in ("sph_create", "sph_status", "sph_build_cells", "sph_cells_sync", "sph_cells_copy",
                   "sph_density",
                   "sph_force", "sph_step", "sph_conservation", "sph_pair_counts",
-                  "sph_kernel_times"):
+                  "sph_kernel_times", "sph_build_cells_static"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -285,6 +287,21 @@ def sph_kernel_times(ctx: Context):
     calls = (C.c_int64 * len(TIMING_GROUPS))()
     _check(lib().sph_kernel_times(ctx.handle, ms, calls), "sph_kernel_times")
     return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(TIMING_GROUPS)}
+
+
+STATIC_MAX_N = 65536
+
+
+def sph_build_cells_static(x, y, z, h, box_size: float, cell_margin: float, cell_start, perm,
+                           n_c_out=None, status_out=None, stream=None):
+    """The allocation-free cell build: every buffer is the caller's (CUDA
+    tensors), the library's scratch is a fixed array inside the library."""
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().sph_build_cells_static(
+        int(x.shape[0]), _ptr(x, torch.float64), _ptr(y, torch.float64), _ptr(z, torch.float64),
+        _ptr(h, torch.float32), float(box_size), float(cell_margin), _ptr(cell_start, torch.int32),
+        int(cell_start.shape[0]), _ptr(perm, torch.int32), _ptr(n_c_out, torch.int32),
+        _ptr(status_out, torch.int32), _P(st.cuda_stream)), "sph_build_cells_static")
 
 
 # ---- allocation helpers (marshalling of outputs) ----------------------------
