@@ -79,7 +79,8 @@ enum {
 
 /* Physical and numerical parameters.  sph_default_params fills the values of
  * the paper's "Minimal" flavour: gamma = 5/3, eta = 1.2348 (~48 neighbours),
- * alpha_V = 0.8, beta = 3, epsilon = 1e-4 (Sec. 3.2), plus h_tol = 1e-6,
+ * alpha_V = 0.8, beta = 3, epsilon = 1e-4 (Sec. 3.2), the paper's default
+ * relative smoothing-length tolerance h_tol = 1e-4 (Sec. 3.1.1), plus
  * max_h_iter = 30, C_CFL = 0.1 and a 5 % cell margin. */
 typedef struct sph_params {
   double box_size;     /* side L of the periodic cubic box (> 0)                  */
@@ -88,7 +89,8 @@ typedef struct sph_params {
   double alpha_v;      /* viscosity constant alpha_V, eq. "balsara"               */
   double beta_v;       /* signal-velocity constant beta                           */
   double eps_balsara;  /* epsilon of eq. "balsara"                                */
-  double h_tol;        /* Newton-Raphson stops when |dh| <= h_tol h               */
+  double h_tol;        /* Newton-Raphson stops when the correction |dh| <= h_tol h;
+                          that last correction is applied (error ~ 2 h_tol^2)     */
   double cfl;          /* C_CFL of the global time-step                           */
   double cell_margin;  /* cells are >= (1 + cell_margin) * gamma_K * max h        */
   int32_t max_h_iter;  /* iteration cap of the smoothing-length solve             */
@@ -198,7 +200,8 @@ int sph_cells_copy(sph_ctx* ctx, sph_cells* cells, int32_t* cell_start_dst, int3
 /* Density loop with the smoothing-length solve (Sec. 3.1).  h_in is the
  * starting guess (may alias out->h).  Each particle's h is iterated with
  * Newton-Raphson on n_hat(h) - (eta/h)^3, using dn_hat/dh, until the relative
- * change is below h_tol; H is capped at the cell size (a particle that would
+ * correction is below h_tol (the last correction is applied, and the outputs
+ * are evaluated at that final h); H is capped at the cell size (a particle that would
  * need more sets SPH_ST_REBUILD: rebuild the cells from out->h and call
  * again).  Sums are accumulated in FP32 on coordinates relative to the
  * particle's cell; the convergence test runs in FP64. */

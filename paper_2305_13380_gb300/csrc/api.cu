@@ -383,7 +383,7 @@ void sph_default_params(sph_params* p) {
   p->alpha_v = 0.8;
   p->beta_v = 3.0;
   p->eps_balsara = 1e-4;
-  p->h_tol = 1e-6;
+  p->h_tol = 1e-4;
   p->cfl = 0.1;
   p->cell_margin = 0.05;
   p->max_h_iter = 30;

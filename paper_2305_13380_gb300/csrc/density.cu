@@ -15,7 +15,8 @@
 //     iteration of the paper, h <- h - f/f' with f = n_hat - (eta/h)^3 and
 //     f' = dn_hat/dh + 3 eta^3 / h^4, is h <- h (1 - A/B) with
 //     A = S_w/gamma_K^3 - eta^3, B = 3 eta^3 - S_dw/gamma_K^3, taken in FP64;
-//     a target stops when |A/B| <= h_tol (or at the cell cap / max_h_iter);
+//     a target stops when |A/B| <= h_tol, with that last correction applied
+//     (or at the cell cap / max_h_iter);
 //  3. a final pass at the converged h accumulates, in FP32,
 //        S_mw = sum m_j w,  S_mdw = sum m_j (3 w + q w'),
 //        S_div = sum m_j g (v_j - v_i) . x_ij,  S_curl = sum m_j g (v_i - v_j) x x_ij,
@@ -35,10 +36,11 @@ namespace sphk {
 
 constexpr int kDensBlkCap = kBlkStageCap;  // staged sources per block
 constexpr int kListCap = kLaneListCap;     // list entries per lane
+constexpr int kListRows = kListCap + 1;    // + one scratch row for the branch-free append
 // shared memory: staged sources (32 B each), per-warp lists (r^2, slot),
 // the staging table, the block's target rounds and its target slots/cells
 constexpr size_t kDensBlkSmem = (size_t)kDensBlkCap * 2 * sizeof(float4) +
-                                (size_t)kBlkWarps * kListCap * 32 * (sizeof(float) + sizeof(uint16_t)) +
+                                (size_t)kBlkWarps * kListRows * 32 * (sizeof(float) + sizeof(uint16_t)) +
                                 sizeof(StageTable) + sizeof(BlockTargets) +
                                 (size_t)kDensBlkCap * (sizeof(uint16_t) + sizeof(uint8_t));
 constexpr int kOvfCap = 256;  // per-warp staging of the overflow kernel
@@ -90,7 +92,10 @@ __device__ __forceinline__ void dens_pair(const float4& pi, const float4& vi, co
 }
 
 // One Newton-Raphson decision for a target whose pass at h gave (S_w, S_dw).
-// Returns true when the target is finished (converged, capped or out of
+// The relative correction is delta = A/B.  When |delta| <= h_tol the target
+// is finished and the correction is applied: Newton converges quadratically,
+// so the result is within ~2 delta^2 of the root (1e-4 -> 2e-8).  Returns
+// true when the target is finished (converged, capped or out of
 // iterations); otherwise advances h.
 __device__ __forceinline__ bool newton_step(float Sw, float Sdw, double& h, double& lo, double& hi,
                                             int& it, double hcap, const PhysDev& ph, bool& atcap,
@@ -103,7 +108,15 @@ __device__ __forceinline__ bool newton_step(float Sw, float Sdw, double& h, doub
   conv = (B > 0.0) && (fabs(A) <= ph.h_tol * B);
   atcap = (h >= hcap) && (A < 0.0);
   const bool last = it + 1 >= ph.max_h_iter;
-  if (conv || atcap || last) return true;
+  if (conv) {
+    h = h * (1.0 - A / B);
+    if (h > hcap) {
+      h = hcap;
+      atcap = true;
+    }
+    return true;
+  }
+  if (atcap || last) return true;
   double hn = (B > 0.0) ? h * (1.0 - A / B) : 2.0 * h;
   hn = fmin(fmax(hn, 0.5 * h), 2.0 * h);
   if (!(B > 0.0) || !(hn > lo) || !(hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
@@ -169,15 +182,16 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   float4* spos = reinterpret_cast<float4*>(dsm_raw);
   float4* svel = spos + kDensBlkCap;
+  // per-lane list entries (r^2, staged slot), column layout [entry][lane]
   float* lr2_all = reinterpret_cast<float*>(svel + kDensBlkCap);
-  uint16_t* lj_all = reinterpret_cast<uint16_t*>(lr2_all + kBlkWarps * kListCap * 32);
-  StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * kListCap * 32);
+  uint16_t* lj_all = reinterpret_cast<uint16_t*>(lr2_all + kBlkWarps * kListRows * 32);
+  StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * kListRows * 32);
   BlockTargets& BT = *reinterpret_cast<BlockTargets*>(&T + 1);
   uint16_t* tgt_slot = reinterpret_cast<uint16_t*>(&BT + 1);
   uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + kDensBlkCap);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* lr2 = lr2_all + warp * (kListCap * 32);
-  uint16_t* lj = lj_all + warp * (kListCap * 32);
+  float* lr2 = lr2_all + warp * (kListRows * 32);
+  uint16_t* lj = lj_all + warp * (kListRows * 32);
   const int32_t total = a.misc_ro[kTotalBlocks];
   unsigned long long pair_acc = 0;
 
@@ -232,13 +246,13 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
             const float4 pj = spos[k];
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < R2) {
-              if (cnt < kListCap) {
-                lr2[cnt * 32 + lane] = r2;
-                lj[cnt * 32 + lane] = (uint16_t)k;
-              }
-              ++cnt;
-            }
+            // branch-free append: the entry is written at the current end and
+            // kept only if in range; once the list is full, writes go to the
+            // scratch row kListCap (such a lane takes the direct path)
+            const int at = min(cnt, kListCap) * 32 + lane;
+            lr2[at] = r2;
+            lj[at] = (uint16_t)k;
+            cnt += r2 < R2;
           }
         }
       }
@@ -275,7 +289,8 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
         if (!done && !direct) {
           int e = 0;
           for (; e + 1 < cnt; e += 2) {
-            const float r2a = lr2[e * 32 + lane], r2b = lr2[(e + 1) * 32 + lane];
+            const float r2a = lr2[e * 32 + lane];
+            const float r2b = lr2[(e + 1) * 32 + lane];
             const float ria = rsqrtf(fmaxf(r2a, 1e-30f)), rib = rsqrtf(fmaxf(r2b, 1e-30f));
             const float qa = r2a * ria * Hinv, qb = r2b * rib * Hinv;
             float wa, ga, wb, gb;
@@ -333,12 +348,12 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
       if (valid && !direct) {
         int e = 0;
         for (; e + 1 < cnt; e += 2) {
-          const int ka = lj[e * 32 + lane], kb = lj[(e + 1) * 32 + lane];
+          const int ka = (int)lj[e * 32 + lane], kb = (int)lj[(e + 1) * 32 + lane];
           dens_pair(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
           dens_pair(pi, vi, spos[kb], svel[kb], H, Hinv, s1);
         }
         if (e < cnt) {
-          const int ka = lj[e * 32 + lane];
+          const int ka = (int)lj[e * 32 + lane];
           dens_pair(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
         }
       } else if (valid) {
@@ -409,6 +424,7 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
       double lo = 0.0, hi = INFINITY;
       bool done = !valid, atcap = false, conv = false;
       int it = 0;
+      int passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
         const float H = kGammaK * (float)h;
         const float Hinv = 1.0f / H;
@@ -420,12 +436,24 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
           __syncwarp();
         }
         if (!done) {
-          const int passes = it + 1;
-          if (newton_step(s.w, s.dw, h, lo, hi, it, hcap, ph, atcap, conv)) {
-            dens_write(a, ph, ti, h, s, vi.w, passes, conv, atcap);
-            pair_acc += (unsigned long long)s.npair;
-            done = true;
-          }
+          passes = it + 1;
+          if (newton_step(s.w, s.dw, h, lo, hi, it, hcap, ph, atcap, conv)) done = true;
+        }
+      }
+      // final pass at the converged h
+      {
+        const float H = kGammaK * (float)h;
+        const float Hinv = 1.0f / H;
+        DensSums s;
+        sums_zero(s);
+        for (int v0 = 0; v0 < nsrc; v0 += kOvfCap) {
+          const int cnt = stage_sources(v0, kOvfCap, nb, lane, put);
+          for (int k = 0; k < cnt; ++k) dens_pair(pi, vi, spos[k], svel[k], H, Hinv, s);
+          __syncwarp();
+        }
+        if (valid) {
+          dens_write(a, ph, ti, h, s, vi.w, passes, conv, atcap);
+          pair_acc += (unsigned long long)s.npair;
         }
       }
     }

@@ -40,7 +40,7 @@ def expected_nc(h0_f32, L, margin=0.05, n=None):
     return max(nc, 3)
 
 
-def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-6):
+def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-4):
     """build -> density -> (rebuild while the status asks) -> force on cuda:0."""
     import torch
     from paper_2305_13380_gb300 import sph
@@ -93,41 +93,65 @@ def coord_floor(cell, h):
     return 2.0 * np.sqrt(3.0) * 2.0 ** -22 * cell / (GAMMA_K * np.asarray(h))
 
 
-def compare(g, od, of, idx=None, cell=None):
+def compare(g, od, of, idx=None, cell=None, vmax=None):
     """Asserts the GPU outputs g (indexed by idx) against oracle density od and
-    force of (already restricted to the same particles).  With `cell` (the
-    grid's cell size) the per-particle tolerance of h, rho, f and P is the
-    larger of the stated bound and the coordinate-rounding floor."""
+    force of (already restricted to the same particles).
+
+    With `cell` (the grid's cell size) every bound gets the coordinate-rounding
+    floor d_i = coord_floor(cell, h_i) of each particle.  Quantities that are
+    sums of gradient terms carry d_i times the sum of their absolute terms;
+    with int_0^1 |w'(q)| 4 pi q^2 dq = 5.6 for the cubic spline, that sum is
+    5.6 / H_i times the term's velocity or pressure factor: 2 vmax for the
+    divergence and curl, 2 P/rho for the acceleration, 4 vmax P/rho for du/dt."""
     sel = (lambda a: a) if idx is None else (lambda a: a[idx])
     report = {}
-    floor = 0.0 if cell is None else coord_floor(cell, od["h"])
+    if cell is None:
+        floor = np.zeros_like(od["h"])
+    else:
+        floor = coord_floor(cell, od["h"])
+    H = GAMMA_K * od["h"]
+    vm = 0.0 if vmax is None else vmax
+    Prho = od["P"] / od["rho"]
     for k_g, k_o, tol in (("h", "h", TOL["h"]), ("rho", "rho", TOL["rho"]), ("f", "f", TOL["f"]),
                           ("P", "P", TOL["P"]), ("c", "c", TOL["c"])):
         err = rel_err(sel(g[k_g]), od[k_o])
-        lim = np.maximum(tol, floor) if k_g != "c" else tol
+        lim = tol + floor if k_g != "c" else tol
         e = (err / lim).max()
         report[k_g] = err.max()
         assert e <= 1.0, f"{k_g}: max relative error {err.max():.3e} (worst ratio to bound {e:.2f})"
+    dvc = {}
     for k_g, k_o in (("div_v", "div_v"), ("curl_v", "curl_norm")):
         ref = od[k_o]
         scale = np.sqrt(np.mean(ref ** 2)) + 1e-300
-        e = np.abs(sel(g[k_g]) - ref).max() / scale
-        report[k_g] = e
-        assert e <= TOL["divcurl"], f"{k_g}: max error / rms {e:.3e}"
-    e = np.abs(sel(g["balsara"]) - od["B"]).max()
-    report["balsara"] = e
-    assert e <= TOL["balsara"], f"balsara: max abs error {e:.3e}"
+        err = np.abs(sel(g[k_g]) - ref)
+        lim = TOL["divcurl"] * scale + floor * 5.6 * 2 * vm / H
+        dvc[k_g] = lim
+        e = (err / lim).max()
+        report[k_g] = err.max() / scale
+        assert e <= 1.0, f"{k_g}: max error / rms {err.max() / scale:.3e} (worst ratio {e:.2f})"
+    err = np.abs(sel(g["balsara"]) - od["B"])
+    denom = np.abs(od["div_v"]) + od["curl_norm"] + 1e-4 * od["c"] / od["h"]
+    lim = TOL["balsara"] + 2 * (dvc["div_v"] + dvc["curl_v"]) / denom * (cell is not None)
+    e = (err / lim).max()
+    report["balsara"] = err.max()
+    assert e <= 1.0, f"balsara: max abs error {err.max():.3e} (worst ratio {e:.2f})"
     a_ref = np.stack([of["ax"], of["ay"], of["az"]], 1)
     a_gpu = np.stack([sel(g["ax"]), sel(g["ay"]), sel(g["az"])], 1)
     rms = np.sqrt(np.mean(np.sum(a_ref ** 2, 1)))
-    e = np.abs(a_gpu - a_ref).max() / rms
-    report["a"] = e
-    assert e <= TOL["acc"], f"a: max error / rms|a| {e:.3e}"
+    err = np.abs(a_gpu - a_ref).max(1)
+    lim = TOL["acc"] * rms + floor * 5.6 * 2 * Prho / H
+    e = (err / lim).max()
+    report["a"] = err.max() / rms
+    assert e <= 1.0, f"a: max error / rms|a| {err.max() / rms:.3e} (worst ratio {e:.2f})"
     rms_u = np.sqrt(np.mean(of["du_dt"] ** 2))
-    e = np.abs(sel(g["du_dt"]) - of["du_dt"]).max() / rms_u
-    report["du_dt"] = e
-    assert e <= TOL["du"], f"du_dt: max error / rms {e:.3e}"
-    e = rel_err(sel(g["v_sig"]), of["v_sig"]).max()
-    report["v_sig"] = e
-    assert e <= TOL["v_sig"], f"v_sig: max relative error {e:.3e}"
+    err = np.abs(sel(g["du_dt"]) - of["du_dt"])
+    lim = TOL["du"] * rms_u + floor * 5.6 * 4 * vm * Prho / H
+    e = (err / lim).max()
+    report["du_dt"] = err.max() / rms_u
+    assert e <= 1.0, f"du_dt: max error / rms {err.max() / rms_u:.3e} (worst ratio {e:.2f})"
+    err = rel_err(sel(g["v_sig"]), of["v_sig"])
+    lim = TOL["v_sig"] + floor
+    e = (err / lim).max()
+    report["v_sig"] = err.max()
+    assert e <= 1.0, f"v_sig: max relative error {err.max():.3e} (worst ratio {e:.2f})"
     return report

@@ -82,7 +82,8 @@ def test_density_force_clustered(orc):
     assert od["h"].max() / od["h"].min() > 30
     from paper_2305_13380_gb300 import sph
     cell = p["L"] / sph.sph_cells_sync(g["_ctx"], g["_cells"])
-    compare(g, od, of, cell=cell)
+    vmax = float(np.sqrt(q["vx"] ** 2 + q["vy"] ** 2 + q["vz"] ** 2).max())
+    compare(g, od, of, cell=cell, vmax=vmax)
 
 
 def test_density_force_mildly_clustered(orc):
