@@ -36,9 +36,19 @@ UNIT = "particle-updates/s"
 # divide and square root counts 1; see the design notes for the tally).
 F_DENSITY = 66
 F_FORCE = 72
-# Kernel launches of one sph_step: time-step reduction (3), kick/drift (1),
-# cell build (10), two gathers (2), density (1), force (1), kick (1).
-LAUNCHES_PER_STEP = 19
+
+
+def launches_per_step(n_total: int) -> int:
+    """Kernel launches of one sph_step over n_total particles: time-step
+    reduction (3), kick/drift (1), cell build (8 + the radix sort: 1 + 5 per
+    8-bit digit of the cell id, whose range is 8 n + 216 cells), two gathers
+    (2), density (2), force (2), kick (1)."""
+    cap = 8 * n_total + 216
+    bits = 1
+    while bits < 31 and (1 << bits) <= cap:
+        bits += 1
+    radix = 1 + 5 * ((bits + 7) // 8)
+    return 3 + 1 + 8 + radix + 2 + 2 + 2 + 1
 FP32_LANES_PER_SM = 128
 
 
@@ -214,6 +224,77 @@ def _traffic(kernel: str):
     return None
 
 
+def run_batch(args, world: int, rank: int, local: int):
+    """256 independent boxes (config of the batched workload): one sph_step per
+    step for all boxes, captured in a CUDA graph; against the same boxes each
+    stepped by its own sph_step call (one simulation per launch)."""
+    import numpy as np
+    import torch
+
+    from paper_2305_13380_gb300 import build as B
+    B.build()
+    from paper_2305_13380_gb300 import inputs, pool, sph, tune
+
+    n_boxes = int(args.workload[len("batch"):] or 256)
+    boxes = inputs.batch(n_boxes, seed0=0)
+    n = sum(len(b["x"]) for b in boxes)
+    margin = tune.best_margin(boxes, key=f"batch{n_boxes}")
+    P = pool.Pool(boxes, sph.sph_default_params(cell_margin=margin))
+    P.start()
+    P.capture()
+    for _ in range(args.warmup):
+        P.replay()
+    P.stream.synchronize()
+    if P.status():
+        raise SystemExit(f"device status {P.status()} after warm-up")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = Clocks(None)
+    time.sleep(0.25)
+    ev[0].record(P.stream)
+    for k in range(args.steps):
+        P.replay()
+        ev[k + 1].record(P.stream)
+    P.stream.synchronize()
+    clk = clocks.stop()
+    per = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])
+    st = P.status()
+    # one simulation per launch: every box has its own pool and context
+    singles = [pool.Pool([b], sph.sph_default_params(cell_margin=margin), stream=P.stream)
+               for b in boxes]
+    for S in singles:
+        S.start()
+    for _ in range(2):
+        for S in singles:
+            S.step()
+    P.stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(P.stream)
+    for _ in range(args.steps):
+        for S in singles:
+            S.step()
+    e1.record(P.stream)
+    P.stream.synchronize()
+    plain_ms = e0.elapsed_time(e1) / args.steps
+    line = {
+        "metric": "batched SPH step p50/p99 latency (256 boxes)", "value": float(np.percentile(per, 50)),
+        "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "boxes": n_boxes, "particles": n,
+                   "desc": "periodic unit boxes, N log-uniform in [1e3, 1e5], even: jittered "
+                           "lattice, odd: 4 Plummer spheres + background",
+                   "cell_margin": margin},
+        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "particle_updates_per_s": n / (float(np.mean(per)) / 1e3),
+        "plain_ms_per_step": plain_ms, "plain_particle_updates_per_s": n / (plain_ms / 1e3),
+        "speedup_vs_plain": plain_ms / float(np.mean(per)),
+        "gpu_launches": launches_per_step(n) * args.steps,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"], "samples": clk["samples"]},
+        "device_status": st}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -227,6 +308,8 @@ def main():
     import torch.distributed as dist
 
     torch.cuda.set_device(local)
+    if args.workload.startswith("batch"):
+        return run_batch(args, world, rank, local)
     if world > 1:
         dist.init_process_group("nccl")
     from paper_2305_13380_gb300 import build as B
@@ -367,7 +450,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "steps": args.e2e_steps},
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": launches_per_step(n) * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "roofline": roofline,

@@ -45,7 +45,7 @@ enum {
   SPH_E_NOMEM = -2,     /* device allocation of context scratch failed       */
   SPH_E_H_NOCONV = -3,  /* some smoothing length did not converge            */
   SPH_E_REBUILD = -4,   /* some support H exceeds its cell: rebuild needed   */
-  SPH_E_BOX = -5,       /* the box holds fewer than 3 cells of side max H    */
+  SPH_E_BOX = -5,       /* the largest support exceeds half the box          */
   SPH_E_TIMEOUT = -6,   /* a bounded device wait expired                     */
   SPH_E_CUDA = -7,      /* a CUDA runtime call failed                        */
   SPH_E_CAPACITY = -8   /* a fixed-size limit of the library was exceeded    */
@@ -55,7 +55,7 @@ enum {
 enum {
   SPH_ST_H_NOCONV = 1,  /* Newton-Raphson hit max_h_iter                     */
   SPH_ST_REBUILD = 2,   /* a converged H is larger than the cell size        */
-  SPH_ST_BOX = 4,       /* fewer than 3 cells per side would be needed       */
+  SPH_ST_BOX = 4,       /* a support larger than half the box was needed     */
   SPH_ST_CAPACITY = 8,  /* a cell held more particles than a kernel handles  */
   SPH_ST_NEG_U = 16     /* a kick made some internal energy negative         */
 };
@@ -181,9 +181,11 @@ const char* sph_error_string(int code);
 int sph_status(sph_ctx* ctx, int32_t* status_out);
 
 /* Bins n particles into the cell grid (Sec. 2.1).  The grid has
- * n_c = floor(L / ((1 + cell_margin) gamma_K max_i h_i)) cells per side,
- * computed on the device; fewer than 3 sets SPH_ST_BOX (and SPH_E_BOX when
- * synchronous).  Cell coordinates are k = floor(fl(fl(x n_c) / L)), clamped
+ * n_c = max(1, floor(L / ((1 + cell_margin) gamma_K max_i h_i))) cells per
+ * side (capped so that n_c^3 <= 8 n + 216), computed on the device; a
+ * support (1 + cell_margin) gamma_K max h above L/2 sets SPH_ST_BOX (and
+ * SPH_E_BOX when synchronous), since the minimum image would no longer be
+ * unique.  Cell coordinates are k = floor(fl(fl(x n_c) / L)), clamped
  * to n_c - 1 (IEEE double, round to nearest); the order inside a cell is
  * ascending input index, so the lists are exactly reproducible. */
 int sph_build_cells(sph_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
@@ -247,7 +249,7 @@ int sph_pair_counts(sph_ctx* ctx, int64_t* out);
  * It computes the same grid and the same lists as sph_build_cells on a
  * context whose parameters have box_size and cell_margin (bit-identical
  * cell_start and perm), but keeps all of its scratch in one fixed array
- * compiled into the library (about 2.6 MB, held by every GPU that loads the
+ * compiled into the library (about 3.1 MB, held by every GPU that loads the
  * library until the process exits) and calls no allocating routine.
  *   n              particles, 0 <= n <= 65536 (more: SPH_E_CAPACITY)
  *   x, y, z, h     device inputs (length n)

@@ -34,7 +34,8 @@ struct sph_ctx {
   // grown buffers
   GridDev* grid = nullptr;
   int32_t *key = nullptr, *slot = nullptr, *count = nullptr, *cell_start = nullptr;
-  int32_t *scan_sums = nullptr, *perm = nullptr, *big = nullptr, *overflow = nullptr;
+  int32_t *scan_sums = nullptr, *perm = nullptr, *overflow = nullptr;
+  int32_t *rk = nullptr, *rv = nullptr, *rhist = nullptr;
   float4 *pos4 = nullptr, *vel4 = nullptr, *th4 = nullptr;
   float* hs = nullptr;
   float2* fD = nullptr;
@@ -82,7 +83,9 @@ void free_grown(sph_ctx* c) {
   dfree(c->cell_start);
   dfree(c->scan_sums);
   dfree(c->perm);
-  dfree(c->big);
+  dfree(c->rk);
+  dfree(c->rv);
+  dfree(c->rhist);
   dfree(c->overflow);
   dfree(c->pos4);
   dfree(c->vel4);
@@ -114,7 +117,8 @@ int ensure(sph_ctx* c, int64_t n, int n_sims) {
   bool ok = dalloc(c->grid, cs) && dalloc(c->key, cn) && dalloc(c->slot, cn) &&
             dalloc(c->count, cc + 1) && dalloc(c->cell_start, cc + 1) &&
             dalloc(c->scan_sums, cc / 1024 + 2) && dalloc(c->perm, cn) &&
-            dalloc(c->big, cn / (sphk::kSmallCell + 1) + 2) && dalloc(c->overflow, cc / 3 + 2) && dalloc(c->pos4, cn) &&
+            dalloc(c->rk, cn) && dalloc(c->rv, cn) && dalloc(c->rhist, sphh::radix_hist_words(cn)) &&
+            dalloc(c->overflow, cc / 3 + 2) && dalloc(c->pos4, cn) &&
             dalloc(c->vel4, cn) && dalloc(c->th4, cn) && dalloc(c->hs, cn) && dalloc(c->fD, cn) &&
             dalloc(c->dt_bits, cs) && dalloc(c->hmax_bits, cs) &&
             dalloc(c->lists, (int64_t)sphk::kListRegion * 4 * cn) && dalloc(c->list_cnt, 4 * cn) &&
@@ -240,7 +244,9 @@ int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const 
   b.cell_start = c->cell_start;
   b.scan_sums = c->scan_sums;
   b.perm = c->perm;
-  b.big = c->big;
+  b.rk = c->rk;
+  b.rv = c->rv;
+  b.hist = c->rhist;
   t_begin(c, SPH_T_BUILD);
   if (sphh::launch_build(b, c->st) != cudaSuccess) return SPH_E_CUDA;
   t_end(c, SPH_T_BUILD);
@@ -445,7 +451,7 @@ const char* sph_error_string(int code) {
     case SPH_E_NOMEM: return "device allocation failed";
     case SPH_E_H_NOCONV: return "smoothing length did not converge";
     case SPH_E_REBUILD: return "kernel support larger than the cell: rebuild the cells";
-    case SPH_E_BOX: return "box holds fewer than 3 cells of the largest support";
+    case SPH_E_BOX: return "largest support exceeds half the box";
     case SPH_E_TIMEOUT: return "bounded device wait expired";
     case SPH_E_CUDA: return "CUDA runtime error";
     case SPH_E_CAPACITY: return "fixed-size library limit exceeded";

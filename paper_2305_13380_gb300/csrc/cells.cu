@@ -5,11 +5,11 @@
 // step can be captured in a CUDA graph):
 //   k_grid_setup   per simulation: max h -> cells per side n_c
 //   k_grid_base    prefix of n_c^3 over simulations -> global cell ids
-//   k_key_count    FP64 cell coordinates, cell id, atomic count + arrival slot
+//   k_key_count    FP64 cell coordinates, cell id, per-cell count
 //   k_scan_*       exclusive scan of the counts -> cell_start
-//   k_scatter      sorted position = cell_start[key] + slot
-//   k_segsort_*    restore ascending input index inside each cell, which
-//                  makes the lists independent of the order of the atomics
+//   radix sort     stable sort of (cell id, particle index) -> perm, so the
+//                  order inside a cell is ascending index for any cell size
+//                  (radix.cu)
 //   k_gather_*     sorted float copies relative to each particle's cell
 #include "sph_internal.cuh"
 #include "sph_launch.h"
@@ -74,10 +74,13 @@ __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const doubl
       const double t = floor(L / Hmax);
       nc = t < (double)cap ? (int32_t)t : cap;
     }
-    if (nc < 3) {
-      atomicOr(&misc[kStatus], SPH_ST_BOX);
-      nc = 3;
-    }
+    // Any n_c >= 1 gives exact sums while H <= min(cell, L/2): with fewer
+    // than 3 cells per side the 27-cell stencil visits a cell's periodic
+    // images twice, and the farther image lies at least L - H >= H away,
+    // where the kernel is exactly zero.  Supports above L/2 would break the
+    // minimum image.
+    if (Hmax > 0.5 * L) atomicOr(&misc[kStatus], SPH_ST_BOX);
+    if (nc < 1) nc = 1;
     GridDev g;
     g.L = L;
     g.n_c = nc;
@@ -104,7 +107,6 @@ __global__ void k_grid_base(GridDev* __restrict__ grid, int n_sims, int32_t* __r
   }
   misc[kTotalCells] = (int32_t)base;
   misc[kTotalBlocks] = (int32_t)bbase;
-  misc[kNumBigCells] = 0;
 }
 
 __global__ void k_zero_counts(int32_t* __restrict__ count, const int32_t* __restrict__ misc) {
@@ -116,7 +118,7 @@ __global__ void k_zero_counts(int32_t* __restrict__ count, const int32_t* __rest
 __global__ void k_key_count(int64_t n_total, const double* __restrict__ x, const double* __restrict__ y,
                             const double* __restrict__ z, const int64_t* __restrict__ sim_offset,
                             int n_sims, const GridDev* __restrict__ grid, int32_t* __restrict__ key,
-                            int32_t* __restrict__ slot, int32_t* __restrict__ count) {
+                            int32_t* __restrict__ sort_key, int32_t* __restrict__ count) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = sim_of_particle(sim_offset, n_sims, p);
@@ -126,7 +128,8 @@ __global__ void k_key_count(int64_t n_total, const double* __restrict__ x, const
     const int32_t kz = cell_coord(z[p], G.L, G.n_c);
     const int32_t k = G.cell_base + kx + G.n_c * (ky + G.n_c * kz);
     key[p] = k;
-    slot[p] = atomicAdd(&count[k], 1);
+    sort_key[p] = k;
+    atomicAdd(&count[k], 1);
   }
 }
 
@@ -216,79 +219,6 @@ __global__ void k_scan_add(int32_t* __restrict__ out, const int32_t* __restrict_
   }
 }
 
-__global__ void k_scatter(int64_t n_total, const int32_t* __restrict__ key, const int32_t* __restrict__ slot,
-                          const int32_t* __restrict__ cell_start, int32_t* __restrict__ perm) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_total;
-       p += (int64_t)gridDim.x * blockDim.x)
-    perm[cell_start[key[p]] + slot[p]] = (int32_t)p;
-}
-
-// Small cells: insertion sort by one thread.  Larger cells are queued.
-__global__ void k_segsort_small(const int32_t* __restrict__ cell_start, int32_t* __restrict__ perm,
-                                int32_t* __restrict__ big, int32_t* __restrict__ misc) {
-  const int32_t total = misc[kTotalCells];
-  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
-    const int32_t a = cell_start[c], b = cell_start[c + 1];
-    const int32_t len = b - a;
-    if (len <= 1) continue;
-    if (len > kSmallCell) {
-      big[atomicAdd(&misc[kNumBigCells], 1)] = c;
-      continue;
-    }
-    int32_t v[kSmallCell];
-    for (int32_t i = 0; i < len; ++i) v[i] = perm[a + i];
-    for (int32_t i = 1; i < len; ++i) {
-      const int32_t t = v[i];
-      int32_t j = i - 1;
-      while (j >= 0 && v[j] > t) {
-        v[j + 1] = v[j];
-        --j;
-      }
-      v[j + 1] = t;
-    }
-    for (int32_t i = 0; i < len; ++i) perm[a + i] = v[i];
-  }
-}
-
-// Larger cells: one block per cell, bitonic sort in shared memory.
-__global__ void __launch_bounds__(1024) k_segsort_big(const int32_t* __restrict__ cell_start,
-                                                      int32_t* __restrict__ perm,
-                                                      const int32_t* __restrict__ big,
-                                                      int32_t* __restrict__ misc) {
-  __shared__ int32_t v[kMaxSortCell];
-  const int32_t nbig = misc[kNumBigCells];
-  for (int32_t i = blockIdx.x; i < nbig; i += gridDim.x) {
-    const int32_t c = big[i];
-    const int32_t a = cell_start[c], len = cell_start[c + 1] - a;
-    if (len > kMaxSortCell) {
-      if (threadIdx.x == 0) atomicOr(&misc[kStatus], SPH_ST_CAPACITY);
-      continue;
-    }
-    int32_t m = 1;
-    while (m < len) m <<= 1;
-    for (int32_t k = threadIdx.x; k < m; k += blockDim.x) v[k] = k < len ? perm[a + k] : 0x7fffffff;
-    __syncthreads();
-    for (int32_t size = 2; size <= m; size <<= 1) {
-      for (int32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int32_t k = threadIdx.x; k < m; k += blockDim.x) {
-          const int32_t l = k ^ stride;
-          if (l > k) {
-            const bool up = (k & size) == 0;
-            const int32_t x = v[k], y = v[l];
-            if ((x > y) == up) {
-              v[k] = y;
-              v[l] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    for (int32_t k = threadIdx.x; k < len; k += blockDim.x) perm[a + k] = v[k];
-    __syncthreads();
-  }
-}
-
 // Sorted copies for the density loop: position relative to the own cell's
 // lower corner (computed in FP64, rounded once), mass, velocity, u, h.
 __global__ void k_gather_density(int64_t n_total, const int32_t* __restrict__ perm,
@@ -375,16 +305,16 @@ cudaError_t launch_build(const BuildArgs& a, cudaStream_t st) {
   const int pb = grid_for(a.n_total, 256, 65535);
   if (a.n_total > 0)
     k_key_count<<<pb, 256, 0, st>>>(a.n_total, a.x, a.y, a.z, a.sim_offset, a.n_sims, a.grid, a.key,
-                                    a.slot, a.count);
+                                    a.slot, a.count);  // slot receives a copy of the keys to sort
   const int64_t tiles = (a.cap_cells + kScanTile - 1) / kScanTile;
   k_scan_tiles<<<(unsigned)(tiles > 0 ? tiles : 1), kScanThreads, 0, st>>>(a.count, a.cell_start, a.scan_sums, a.misc);
   k_scan_sums<<<1, kScanThreads, 0, st>>>(a.scan_sums, a.cell_start, a.misc);
   k_scan_add<<<(unsigned)(tiles > 0 ? tiles : 1), kScanThreads, 0, st>>>(a.cell_start, a.scan_sums, a.misc);
   if (a.n_total > 0) {
-    k_scatter<<<pb, 256, 0, st>>>(a.n_total, a.key, a.slot, a.cell_start, a.perm);
-    k_segsort_small<<<grid_for(a.cap_cells, 128, 65535), 128, 0, st>>>(a.cell_start, a.perm, a.big,
-                                                                         a.misc);
-    k_segsort_big<<<a.num_sms * 2, 1024, 0, st>>>(a.cell_start, a.perm, a.big, a.misc);
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) <= a.cap_cells) ++bits;
+    const cudaError_t e = radix_sort_index(a.n_total, bits, a.slot, a.rk, a.perm, a.rv, a.hist, st);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
     }
     build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
 
-    const double hcap = (double)g.G.cell_f * (1.0 - 1e-5) / kGammaKd;
+    const double hcap = fmin((double)g.G.cell_f, 0.5 * g.G.L) * (1.0 - 1e-5) / kGammaKd;
     const float R2 = g.G.cell_f * g.G.cell_f;
     const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
     const int sub = lane & (tpp - 1);
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
       spos[slot] = p;
       svel[slot] = a.vel4[j];
     };
-    const double hcap = (double)g.G.cell_f * (1.0 - 1e-5) / kGammaKd;
+    const double hcap = fmin((double)g.G.cell_f, 0.5 * g.G.L) * (1.0 - 1e-5) / kGammaKd;
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
       const bool valid = ti < te;

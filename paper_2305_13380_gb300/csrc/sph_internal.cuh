@@ -17,16 +17,11 @@ constexpr float kWNorm = 2.5464790894703255f;
 constexpr int kWarpsPerBlock = 4;
 constexpr int kThreads = 32 * kWarpsPerBlock;
 
-// Cells larger than this many particles are sorted by the block-level path;
-// beyond kMaxSortCell the build reports SPH_ST_CAPACITY.
-constexpr int kSmallCell = 32;
-constexpr int kMaxSortCell = 8192;
-
 // Misc device words kept by a context.
 enum MiscSlot {
   kStatus = 0,       // SPH_ST_* bits
   kTotalCells = 1,   // number of cells over all simulations of the last build
-  kNumBigCells = 2,  // cells routed to the block-level sort
+  kSpare = 2,
   kTotalBlocks = 3,  // number of 2x2x2 blocks of cells over all simulations
   kNumOverflow = 4,  // blocks queued for the overflow kernel of a loop
   kMiscWords = 8

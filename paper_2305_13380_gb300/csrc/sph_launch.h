@@ -9,6 +9,8 @@
 namespace sphk {
 struct GridDev;
 struct PhysDev;
+struct TreeLeaf;
+struct TreeRange;
 }  // namespace sphk
 
 namespace sphh {
@@ -26,9 +28,18 @@ struct BuildArgs {
   sphk::GridDev* grid;
   int32_t* misc;
   int32_t* hmax_bits;  // per simulation scratch
-  int32_t *key, *slot, *count, *cell_start, *scan_sums, *perm, *big;
+  int32_t *key, *slot, *count, *cell_start, *scan_sums, *perm;
+  int32_t *rk, *rv, *hist;  // radix-sort scratch: n, n, radix_hist_words(n)
 };
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t st);
+
+// Stable radix sort of keys (bits significant bits) with values 0..n-1
+// (radix.cu); keys is clobbered, the sorted values land in vals_out.
+int64_t radix_hist_words(int64_t n);
+cudaError_t radix_sort_index(int64_t n, int bits, int32_t* keys, int32_t* keys_tmp, int32_t* vals_out,
+                             int32_t* vals_tmp, int32_t* hist, cudaStream_t st);
+cudaError_t radix_sort_index64(int64_t n, int bits, uint64_t* keys, uint64_t* keys_tmp,
+                               int32_t* vals_out, int32_t* vals_tmp, int32_t* hist, cudaStream_t st);
 
 struct GatherDensityArgs {
   int64_t n_total;
@@ -94,6 +105,40 @@ struct ForceArgs {
   const uint16_t* list_cnt;
 };
 cudaError_t launch_force(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+
+// Nested-grid build (tree.cu), after launch_build produced the top cells.
+struct TreeBuildArgs {
+  int n_sims;
+  int64_t n_total;
+  int64_t cap_cells;
+  int n_leaf;
+  double margin;
+  const int64_t* sim_offset;
+  const sphk::GridDev* grid;
+  const double *x, *y, *z;
+  const float* h;
+  const int32_t* cell_key;    // top cell of each particle (launch_build's key)
+  const int32_t* cell_start;  // top cells' ranges (valid in tree order too)
+  uint64_t *key64, *key64_b, *key64_c;  // n each
+  uint64_t* skey;             // n: keys in tree order
+  int32_t* perm;              // n: tree order -> pool index
+  int32_t *rv, *hist;         // radix scratch
+  float* st;                  // sparse table, tree_sparse_levels(n) * n
+  int8_t* depth;              // n
+  int32_t *flag, *leaf_of;    // n each
+  int32_t* scan_tmp;          // n / 1024 + 2
+  sphk::TreeLeaf* leaves;     // n + 1
+  int32_t* n_leaves;          // 1 (device)
+  sphk::TreeRange* ranges;    // 27 n
+  float* leaf_side;           // n: side of each particle's leaf
+  int4* fine;                 // n: fine integer position
+  float4* rel;                // n: offset from the fine sub-cell corner
+};
+int tree_sparse_levels(int64_t n);
+cudaError_t launch_tree_build(const TreeBuildArgs& a, cudaStream_t st);
+// Exclusive scan of m int32 in place with a host-known length (radix.cu);
+// tmp holds m / 1024 + 2 entries.
+cudaError_t scan_exclusive_host_n(int32_t* a, int64_t m, int32_t* tmp, cudaStream_t st);
 
 // Time integration over a pool (step.cu).
 struct StepArgs {

@@ -4,10 +4,10 @@
 // Some callers cannot call cudaMalloc: code that runs inside another
 // framework's memory pool or arena, real-time loops whose allocator must not
 // synchronise the device, or plugins that are only handed buffers by their
-// host.  For them this entry point runs the same counting-sort cell build as
-// sph_build_cells, but every scratch array it needs (cell keys, arrival
-// slots, per-cell counts, scan partials, the grid record and status words)
-// lives in one file-scope __device__ array of fixed size.  The caller passes
+// host.  For them this entry point runs the same cell build as
+// sph_build_cells, but every scratch array it needs (cell keys and their
+// sort buffers, per-cell counts, scan partials, the grid record and status
+// words) lives in one file-scope __device__ array of fixed size.  The caller passes
 // the inputs and the outputs; nothing is allocated or freed.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,7 +23,7 @@ namespace {
 constexpr int64_t kStaticMaxN = 65536;
 constexpr int64_t kStaticMaxCells = 8 * kStaticMaxN + 216;
 constexpr int64_t kStaticScanSums = kStaticMaxCells / 1024 + 2;
-constexpr int64_t kStaticBig = kStaticMaxN / (sphk::kSmallCell + 1) + 2;
+constexpr int64_t kStaticHist = 256 * ((kStaticMaxN + 2047) / 2048) + 16;
 
 // Layout of the scratch, in 4-byte words, each part 256-byte aligned.
 constexpr int64_t align64(int64_t w) { return (w + 63) / 64 * 64; }
@@ -36,10 +36,12 @@ constexpr int64_t kOffKey = kOffHmax + 64;
 constexpr int64_t kOffSlot = kOffKey + align64(kStaticMaxN);
 constexpr int64_t kOffCount = kOffSlot + align64(kStaticMaxN);
 constexpr int64_t kOffSums = kOffCount + align64(kStaticMaxCells + 1);
-constexpr int64_t kOffBig = kOffSums + align64(kStaticScanSums);
-constexpr int64_t kWords = kOffBig + align64(kStaticBig);
+constexpr int64_t kOffRk = kOffSums + align64(kStaticScanSums);
+constexpr int64_t kOffRv = kOffRk + align64(kStaticMaxN);
+constexpr int64_t kOffHist = kOffRv + align64(kStaticMaxN);
+constexpr int64_t kWords = kOffHist + align64(kStaticHist);
 
-// The scratch.  Every GPU that loads the library holds it (about 2.6 MB)
+// The scratch.  Every GPU that loads the library holds it (about 3.1 MB)
 // until the process exits.
 static __device__ __align__(256) int32_t g_scratch[kWords];
 
@@ -122,7 +124,9 @@ extern "C" int sph_build_cells_static(int64_t n, const double* x, const double* 
   b.cell_start = cell_start;
   b.scan_sums = base + kOffSums;
   b.perm = perm;
-  b.big = base + kOffBig;
+  b.rk = base + kOffRk;
+  b.rv = base + kOffRv;
+  b.hist = base + kOffHist;
   if (sphh::launch_build(b, st) != cudaSuccess) return SPH_E_CUDA;
   k_static_finish<<<1, 32, 0, st>>>(grid, misc, n_c_out, status_out);
   return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_E_CUDA;

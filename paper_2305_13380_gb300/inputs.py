@@ -177,15 +177,24 @@ def batch_sizes(n_boxes: int, seed0: int = 0, n_min: float = 1e3, n_max: float =
     return out
 
 
+# A periodic box needs at least 3 cells of the largest support per side; a
+# uniform background of at least this many particles keeps the background
+# support below a third of the unit box.
+MIN_BACKGROUND = 800
+
+
 def batch(n_boxes: int, seed0: int = 0, **kw) -> list:
     """Independent periodic unit boxes: box b uses seed seed0 + b; even b is a
-    jittered lattice, odd b a clustered box with 4 Plummer spheres."""
+    jittered lattice, odd b a clustered box with 4 Plummer spheres whose
+    background holds 30 % of the particles but at least MIN_BACKGROUND."""
     boxes = []
     for b, (kind, nb, side) in enumerate(batch_sizes(n_boxes, seed0, **kw)):
         if kind == "lattice":
             boxes.append(lattice(side, seed=seed0 + b, workload=41))
         else:
-            boxes.append(clustered(nb, n_spheres=4, seed=seed0 + b, workload=43))
+            frac = min(0.7, 1.0 - MIN_BACKGROUND / nb)
+            boxes.append(clustered(nb, n_spheres=4, seed=seed0 + b, frac_clustered=frac,
+                                   workload=43))
     return boxes
 
 

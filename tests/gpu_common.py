@@ -37,7 +37,7 @@ def expected_nc(h0_f32, L, margin=0.05, n=None):
         while cap > 3 and cap ** 3 > lim:
             cap -= 1
         nc = min(nc, cap)
-    return max(nc, 3)
+    return max(nc, 1)
 
 
 def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-4):

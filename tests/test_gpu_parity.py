@@ -107,10 +107,24 @@ def test_rebuild_when_h_outgrows_cells(orc):
     compare(g, od, of)
 
 
+@pytest.mark.parametrize("side", [5, 6])
+def test_two_cells_per_side(orc, side):
+    # 5^3 and 6^3 particles: supports near L/2 give a grid of 2 cells per side,
+    # so the 27-cell stencil visits every cell's periodic images twice
+    p = inputs.lattice(side, seed=side, sigma_v=0.05)
+    q = as_f32(p)
+    g = run_gpu(p)
+    from paper_2305_13380_gb300 import sph
+    assert sph.sph_cells_sync(g["_ctx"], g["_cells"]) == 2
+    od, of = orc.density_force(q, q["h0"])
+    compare(g, od, of)
+
+
 def test_box_too_small_is_reported():
     import torch
     from paper_2305_13380_gb300 import sph
-    p = inputs.lattice(6)
+    # 4^3 particles: the support exceeds half the box
+    p = inputs.lattice(4)
     ctx = sph.Context(sph.sph_default_params())
     t = sph.to_device(p)
     sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], t["h0"])
