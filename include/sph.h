@@ -64,7 +64,9 @@ enum {
 enum {
   SPH_FLAG_SYNC = 1,        /* wait after each call, return device status    */
   SPH_FLAG_COUNT_PAIRS = 2, /* count in-support pairs (diagnostics, slower)  */
-  SPH_FLAG_TIMING = 4       /* record CUDA events around each kernel group   */
+  SPH_FLAG_TIMING = 4,      /* record CUDA events around each kernel group   */
+  SPH_FLAG_TREE = 8         /* nested grids below the top cells (Sec. 2.1 and
+                               9.1) for smoothing lengths that span decades   */
 };
 
 /* Kernel groups timed with SPH_FLAG_TIMING (index into sph_kernel_times). */
@@ -95,6 +97,9 @@ typedef struct sph_params {
   double cell_margin;  /* cells are >= (1 + cell_margin) * gamma_K * max h        */
   int32_t max_h_iter;  /* iteration cap of the smoothing-length solve             */
   int32_t flags;       /* SPH_FLAG_*                                              */
+  int32_t n_leaf;      /* SPH_FLAG_TREE: a cell with at most n_leaf particles is
+                          not split (>= 1)                                        */
+  int32_t reserved;    /* 0                                                       */
 } sph_params;
 
 /* Opaque context: holds the stream, the parameters and the device scratch
@@ -187,7 +192,15 @@ int sph_status(sph_ctx* ctx, int32_t* status_out);
  * SPH_E_BOX when synchronous), since the minimum image would no longer be
  * unique.  Cell coordinates are k = floor(fl(fl(x n_c) / L)), clamped
  * to n_c - 1 (IEEE double, round to nearest); the order inside a cell is
- * ascending input index, so the lists are exactly reproducible. */
+ * ascending input index, so the lists are exactly reproducible.
+ *
+ * With SPH_FLAG_TREE the cells of this grid are the top level of nested
+ * grids: below each, a cell is split into 8 children until it holds at most
+ * n_leaf particles, or its children would be narrower than (1 + cell_margin)
+ * times the largest support inside it, or it is 1/1024 of the top cell.
+ * cell_start still delimits the top cells, but inside a top cell the order is
+ * the Morton order of the 1024^3 sub-cells (ties: ascending input index), so
+ * that every cell of every level is one contiguous range. */
 int sph_build_cells(sph_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
                     const float* h, sph_cells* out);
 
@@ -206,7 +219,10 @@ int sph_cells_copy(sph_ctx* ctx, sph_cells* cells, int32_t* cell_start_dst, int3
  * are evaluated at that final h); H is capped at the cell size (a particle that would
  * need more sets SPH_ST_REBUILD: rebuild the cells from out->h and call
  * again).  Sums are accumulated in FP32 on coordinates relative to the
- * particle's cell; the convergence test runs in FP64. */
+ * particle's cell; the convergence test runs in FP64.  With SPH_FLAG_TREE the
+ * cell is the particle's leaf, and coordinates are relative to the leaf with
+ * an exact integer part (1/1024 of a top cell), so precision follows the
+ * leaf's size. */
 int sph_density(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in, const float* h_in,
                 sph_density_out* out);
 

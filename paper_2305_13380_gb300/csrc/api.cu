@@ -11,6 +11,7 @@
 #include "blocks.cuh"
 #include "sph_internal.cuh"
 #include "sph_launch.h"
+#include "tree.cuh"
 
 using sphk::GridDev;
 using sphk::PhysDev;
@@ -44,6 +45,22 @@ struct sph_ctx {
   uint16_t *lists = nullptr, *list_cnt = nullptr;
   bool lists_valid = false;  // lists belong to the current build
   float *vpx = nullptr, *vpy = nullptr, *vpz = nullptr, *up = nullptr;
+  // nested-grid scratch (SPH_FLAG_TREE), grown separately
+  int64_t cap_tree = 0;
+  int64_t rev_cap = 0;
+  uint64_t *key64 = nullptr, *key64_b = nullptr, *key64_c = nullptr, *skey = nullptr;
+  int32_t *tgt = nullptr, *flag = nullptr, *leaf_of = nullptr, *n_leaves = nullptr;
+  sphk::TreeLeaf* leaves = nullptr;
+  sphk::TreeRange* ranges = nullptr;
+  float *leaf_side = nullptr, *lrad = nullptr;
+  int4* fine = nullptr;
+  float4* rel = nullptr;
+  uint32_t* tlists = nullptr;
+  uint64_t* rev_raw = nullptr;
+  uint32_t* rev = nullptr;
+  unsigned long long* rev_count = nullptr;
+  int32_t *rev_start = nullptr, *rev_fill = nullptr;
+  bool built_tree = false;
   // CUDA-event timing of kernel groups (SPH_FLAG_TIMING)
   std::vector<cudaEvent_t> ev_start[SPH_T_COUNT], ev_stop[SPH_T_COUNT];
   int ev_used[SPH_T_COUNT] = {0, 0, 0, 0, 0};
@@ -104,6 +121,66 @@ void free_grown(sph_ctx* c) {
   c->cap_sims = 0;
 }
 
+void free_tree(sph_ctx* c) {
+  dfree(c->key64);
+  dfree(c->key64_b);
+  dfree(c->key64_c);
+  dfree(c->skey);
+  dfree(c->tgt);
+  dfree(c->flag);
+  dfree(c->leaf_of);
+  dfree(c->n_leaves);
+  dfree(c->leaves);
+  dfree(c->ranges);
+  dfree(c->leaf_side);
+  dfree(c->lrad);
+  dfree(c->fine);
+  dfree(c->rel);
+  dfree(c->tlists);
+  dfree(c->rev_raw);
+  dfree(c->rev);
+  dfree(c->rev_count);
+  dfree(c->rev_start);
+  dfree(c->rev_fill);
+  c->cap_tree = 0;
+  c->rev_cap = 0;
+  c->built_tree = false;
+}
+
+// Nested-grid scratch for n particles (after ensure()): keys, the two
+// orders, target groups with their 27 neighbour ranges, tree-order copies, lists and the
+// reverse pairs.  Every reverse pair is one of its emitter's in-support
+// density pairs, whose total is ~50 per particle at the converged h; room
+// starts at 64 per particle, and SPH_ST_CAPACITY in a synchronous step
+// grows it to the emitted count.
+int ensure_tree(sph_ctx* c, int64_t n, int64_t rev_need) {
+  if (c->cap_tree > 0 && n <= c->cap_tree && rev_need <= c->rev_cap) return SPH_OK;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  const int64_t rev_old = c->rev_cap;
+  free_tree(c);
+  const int64_t cn = c->cap_n;
+  int64_t rc = 64 * cn + 65536;
+  if (rc < rev_need) rc = rev_need;
+  if (rc < rev_old) rc = rev_old;
+  if (rc > INT32_MAX) rc = INT32_MAX;
+  bool ok = dalloc(c->key64, cn) && dalloc(c->key64_b, cn) && dalloc(c->key64_c, cn) &&
+            dalloc(c->skey, cn) && dalloc(c->tgt, cn) && dalloc(c->flag, cn) && dalloc(c->leaf_of, cn) && dalloc(c->n_leaves, 1) &&
+            dalloc(c->leaves, cn + 1) && dalloc(c->ranges, 27 * cn) && dalloc(c->leaf_side, cn) &&
+            dalloc(c->lrad, cn) && dalloc(c->fine, cn) && dalloc(c->rel, cn) &&
+            dalloc(c->tlists, (int64_t)sphk::kTreeListRegion * sphk::kTreeTpp * cn) &&
+            dalloc(c->rev_raw, rc) && dalloc(c->rev, rc) && dalloc(c->rev_count, 1) &&
+            dalloc(c->rev_start, cn + 1) && dalloc(c->rev_fill, cn);
+  if (!ok) {
+    free_tree(c);
+    return SPH_E_NOMEM;
+  }
+  c->cap_tree = cn;
+  c->rev_cap = rc;
+  c->built_n = -1;
+  c->lists_valid = false;
+  return SPH_OK;
+}
+
 // Scratch for n particles in n_sims simulations; every simulation may use
 // up to 8 n_s + 216 cells, so the total is bounded by 8 n + 216 n_sims.
 int ensure(sph_ctx* c, int64_t n, int n_sims) {
@@ -111,6 +188,9 @@ int ensure(sph_ctx* c, int64_t n, int n_sims) {
   if (n <= c->cap_n && n_sims <= c->cap_sims && need_cells <= c->cap_cells) return SPH_OK;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
   free_grown(c);
+  const int64_t rev_keep = c->rev_cap;
+  free_tree(c);
+  c->rev_cap = rev_keep;
   const int64_t cn = n + n / 4 + 64;
   const int cs = n_sims + n_sims / 4 + 1;
   const int64_t cc = 8 * cn + 216 * (int64_t)cs;
@@ -218,7 +298,8 @@ int finish(sph_ctx* c) {
 
 bool params_ok(const sph_params& p) {
   return p.box_size > 0 && p.gamma > 1 && p.eta > 0 && p.alpha_v >= 0 && p.beta_v >= 0 &&
-         p.eps_balsara > 0 && p.h_tol > 0 && p.cfl > 0 && p.cell_margin >= 0 && p.max_h_iter > 0;
+         p.eps_balsara > 0 && p.h_tol > 0 && p.cfl > 0 && p.cell_margin >= 0 && p.max_h_iter > 0 &&
+         (!(p.flags & SPH_FLAG_TREE) || p.n_leaf >= 1);
 }
 
 int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const double* box,
@@ -247,20 +328,136 @@ int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const 
   b.rk = c->rk;
   b.rv = c->rv;
   b.hist = c->rhist;
+  const bool tree = (c->p.flags & SPH_FLAG_TREE) != 0;
+  b.sort_cells = tree ? 0 : 1;
+  if (tree) {
+    const int rc = ensure_tree(c, n_total, 0);
+    if (rc != SPH_OK) return rc;
+  }
   t_begin(c, SPH_T_BUILD);
   if (sphh::launch_build(b, c->st) != cudaSuccess) return SPH_E_CUDA;
+  if (tree) {
+    sphh::TreeBuildArgs t;
+    t.n_sims = n_sims;
+    t.n_total = n_total;
+    t.cap_cells = b.cap_cells;
+    t.n_leaf = c->p.n_leaf;
+    t.margin = c->p.cell_margin;
+    t.sim_offset = off;
+    t.grid = c->grid;
+    t.x = x;
+    t.y = y;
+    t.z = z;
+    t.h = h;
+    t.cell_key = c->key;
+    t.cell_start = c->cell_start;
+    t.key64 = c->key64;
+    t.key64_b = c->key64_b;
+    t.key64_c = c->key64_c;
+    t.skey = c->skey;
+    t.perm = c->perm;
+    t.tgt = c->tgt;
+    t.rv = c->rv;
+    t.hist = c->rhist;
+    t.flag = c->flag;
+    t.leaf_of = c->leaf_of;
+    t.scan_tmp = c->scan_sums;
+    t.leaves = c->leaves;
+    t.n_leaves = c->n_leaves;
+    t.ranges = c->ranges;
+    t.leaf_side = c->leaf_side;
+    if (sphh::launch_tree_build(t, c->st) != cudaSuccess) return SPH_E_CUDA;
+  }
   t_end(c, SPH_T_BUILD);
   c->built_sims = n_sims;
   c->built_n = n_total;
   c->built_offset = off;
+  c->built_tree = tree;
   c->lists_valid = false;
   return SPH_OK;
+}
+
+int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
+                    const float* vy, const float* vz, const float* m, const float* u, const float* h_in,
+                    float* h, float* rho, float* f, float* div_v, float* curl_v, float* P, float* cs,
+                    float* B, int32_t* n_iter) {
+  sphh::TreeGatherArgs g;
+  g.n_total = c->built_n;
+  g.n_sims = c->built_sims;
+  g.perm = c->perm;
+  g.skey = c->skey;
+  g.grid = c->grid;
+  g.x = x;
+  g.y = y;
+  g.z = z;
+  g.m = m;
+  g.vx = vx;
+  g.vy = vy;
+  g.vz = vz;
+  g.u = u;
+  g.h = h_in;
+  g.leaf_side = c->leaf_side;
+  g.list_reach = sphk::kTreeListReach;
+  g.fine = c->fine;
+  g.rel = c->rel;
+  g.vel4 = c->vel4;
+  g.hs = c->hs;
+  g.lrad = c->lrad;
+  t_begin(c, SPH_T_GATHER);
+  if (sphh::launch_tree_gather(g, c->st) != cudaSuccess) return SPH_E_CUDA;
+  t_end(c, SPH_T_GATHER);
+  if (c->p.flags & SPH_FLAG_COUNT_PAIRS)
+    if (cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+  sphh::TreeDensityArgs d;
+  d.n_sims = c->built_sims;
+  d.num_sms = c->num_sms;
+  d.n_total = c->built_n;
+  d.grid = c->grid;
+  d.tgt = c->tgt;
+  d.leaves = c->leaves;
+  d.n_leaves = c->n_leaves;
+  d.ranges = c->ranges;
+  d.fine = c->fine;
+  d.rel = c->rel;
+  d.vel4 = c->vel4;
+  d.hs = c->hs;
+  d.lrad = c->lrad;
+  d.leaf_side = c->leaf_side;
+  d.perm = c->perm;
+  d.status = c->misc + sphk::kStatus;
+  d.pairs = c->pairs;
+  d.h = h;
+  d.rho = rho;
+  d.f = f;
+  d.div_v = div_v;
+  d.curl_v = curl_v;
+  d.P = P;
+  d.c = cs;
+  d.B = B;
+  d.n_iter = n_iter;
+  d.lists = c->tlists;
+  d.list_cnt = c->list_cnt;
+  d.rev_raw = c->rev_raw;
+  d.rev_count = c->rev_count;
+  d.rev_start = c->rev_start;
+  d.rev_fill = c->rev_fill;
+  d.rev = c->rev;
+  d.rev_cap = c->rev_cap;
+  d.scan_tmp = c->scan_sums;
+  t_begin(c, SPH_T_DENSITY);
+  const cudaError_t e = sphh::launch_tree_density(d, phys_of(c->p), c->st);
+  t_end(c, SPH_T_DENSITY);
+  c->lists_valid = (e == cudaSuccess);
+  return cuda_code(e);
 }
 
 int do_density(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
                const float* vy, const float* vz, const float* m, const float* u, const float* h_in,
                float* h, float* rho, float* f, float* div_v, float* curl_v, float* P, float* cs,
                float* B, int32_t* n_iter) {
+  if (c->built_tree)
+    return do_tree_density(c, x, y, z, vx, vy, vz, m, u, h_in, h, rho, f, div_v, curl_v, P, cs, B, n_iter);
   sphh::GatherDensityArgs g;
   g.n_total = c->built_n;
   g.n_sims = c->built_sims;
@@ -350,6 +547,41 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   if (c->p.flags & SPH_FLAG_COUNT_PAIRS)
     if (cudaMemsetAsync(c->pairs + 1, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
       return SPH_E_CUDA;
+  if (c->built_tree) {
+    // the tree force needs the lists and reverse pairs of this build's density
+    if (!c->lists_valid) return SPH_E_INVAL;
+    sphh::TreeForceArgs a;
+    a.n_sims = c->built_sims;
+    a.num_sms = c->num_sms;
+    a.grid = c->grid;
+    a.tgt = c->tgt;
+    a.leaves = c->leaves;
+    a.n_leaves = c->n_leaves;
+    a.ranges = c->ranges;
+    a.fine = c->fine;
+    a.rel = c->rel;
+    a.lrad = c->lrad;
+    a.leaf_side = c->leaf_side;
+    a.perm = c->perm;
+    a.fA = c->pos4;
+    a.fB = c->vel4;
+    a.fC = c->th4;
+    a.fD = c->fD;
+    a.lists = c->tlists;
+    a.list_cnt = c->list_cnt;
+    a.rev_start = c->rev_start;
+    a.rev = c->rev;
+    a.pairs = c->pairs + 1;
+    a.ax = ax;
+    a.ay = ay;
+    a.az = az;
+    a.du_dt = du_dt;
+    a.v_sig = v_sig;
+    t_begin(c, SPH_T_FORCE);
+    const cudaError_t e = sphh::launch_tree_force(a, phys_of(c->p), c->st);
+    t_end(c, SPH_T_FORCE);
+    return cuda_code(e);
+  }
   sphh::ForceArgs a;
   a.n_sims = c->built_sims;
   a.num_sms = c->num_sms;
@@ -394,6 +626,8 @@ void sph_default_params(sph_params* p) {
   p->cell_margin = 0.05;
   p->max_h_iter = 30;
   p->flags = 0;
+  p->n_leaf = 16;
+  p->reserved = 0;
 }
 
 int sph_create(sph_ctx** out, const sph_params* p, void* stream) {
@@ -434,6 +668,7 @@ void sph_destroy(sph_ctx* c) {
     for (cudaEvent_t e : c->ev_stop[k]) cudaEventDestroy(e);
   }
   free_grown(c);
+  free_tree(c);
   dfree(c->misc);
   dfree(c->pairs);
   dfree(c->off1);
@@ -601,6 +836,15 @@ int sph_step(sph_ctx* c, const sph_pool* pl) {
     int32_t st = 0;
     rc = read_status(c, &st);
     if (rc != SPH_OK) return rc;
+    if (c->built_tree && (st & SPH_ST_CAPACITY) && attempt < 8) {
+      // more reverse pairs than room: grow to the emitted count and repeat
+      unsigned long long emitted = 0;
+      if (cudaMemcpy(&emitted, c->rev_count, sizeof(emitted), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SPH_E_CUDA;
+      rc = ensure_tree(c, pl->n_total, (int64_t)(emitted + emitted / 4 + 65536));
+      if (rc != SPH_OK) return rc;
+      continue;
+    }
     if (!(st & SPH_ST_REBUILD) || attempt >= 8) {
       const int code = code_of_status(st);
       if (code != SPH_OK) return code;

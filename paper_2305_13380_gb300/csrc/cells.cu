@@ -310,7 +310,7 @@ cudaError_t launch_build(const BuildArgs& a, cudaStream_t st) {
   k_scan_tiles<<<(unsigned)(tiles > 0 ? tiles : 1), kScanThreads, 0, st>>>(a.count, a.cell_start, a.scan_sums, a.misc);
   k_scan_sums<<<1, kScanThreads, 0, st>>>(a.scan_sums, a.cell_start, a.misc);
   k_scan_add<<<(unsigned)(tiles > 0 ? tiles : 1), kScanThreads, 0, st>>>(a.cell_start, a.scan_sums, a.misc);
-  if (a.n_total > 0) {
+  if (a.n_total > 0 && a.sort_cells) {
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) <= a.cap_cells) ++bits;
     const cudaError_t e = radix_sort_index(a.n_total, bits, a.slot, a.rk, a.perm, a.rv, a.hist, st);

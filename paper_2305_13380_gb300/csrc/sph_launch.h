@@ -1,5 +1,6 @@
 // sph_launch.h -- host-side argument records and launchers of the kernels
-// (implemented in cells.cu, density.cu, force.cu, step.cu).
+// (implemented in cells.cu, radix.cu, density.cu, force.cu, tree.cu,
+// tree_loops.cu, step.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -30,6 +31,7 @@ struct BuildArgs {
   int32_t* hmax_bits;  // per simulation scratch
   int32_t *key, *slot, *count, *cell_start, *scan_sums, *perm;
   int32_t *rk, *rv, *hist;  // radix-sort scratch: n, n, radix_hist_words(n)
+  int sort_cells = 1;       // 0: counts and cell_start only (the tree build orders)
 };
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t st);
 
@@ -106,7 +108,8 @@ struct ForceArgs {
 };
 cudaError_t launch_force(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 
-// Nested-grid build (tree.cu), after launch_build produced the top cells.
+// Nested-grid build (tree.cu), after launch_build produced the top cells
+// (counts and cell_start; no cell sort).
 struct TreeBuildArgs {
   int n_sims;
   int64_t n_total;
@@ -118,24 +121,95 @@ struct TreeBuildArgs {
   const double *x, *y, *z;
   const float* h;
   const int32_t* cell_key;    // top cell of each particle (launch_build's key)
-  const int32_t* cell_start;  // top cells' ranges (valid in tree order too)
-  uint64_t *key64, *key64_b, *key64_c;  // n each
-  uint64_t* skey;             // n: keys in tree order
-  int32_t* perm;              // n: tree order -> pool index
+  const int32_t* cell_start;  // top cells' ranges (valid in source order too)
+  uint64_t *key64, *key64_b, *key64_c;  // n each (scratch)
+  uint64_t* skey;             // n: source keys in source order
+  int32_t* perm;              // n: source order -> pool index
+  int32_t* tgt;               // n: target order -> source index
   int32_t *rv, *hist;         // radix scratch
-  float* st;                  // sparse table, tree_sparse_levels(n) * n
-  int8_t* depth;              // n
   int32_t *flag, *leaf_of;    // n each
   int32_t* scan_tmp;          // n / 1024 + 2
-  sphk::TreeLeaf* leaves;     // n + 1
+  sphk::TreeLeaf* leaves;     // n + 1: target groups, start in target order
   int32_t* n_leaves;          // 1 (device)
-  sphk::TreeRange* ranges;    // 27 n
-  float* leaf_side;           // n: side of each particle's leaf
-  int4* fine;                 // n: fine integer position
-  float4* rel;                // n: offset from the fine sub-cell corner
+  sphk::TreeRange* ranges;    // 27 n: source-order ranges of each group
+  float* leaf_side;           // n (source order): cell side of each particle's level
 };
-int tree_sparse_levels(int64_t n);
 cudaError_t launch_tree_build(const TreeBuildArgs& a, cudaStream_t st);
+
+// Tree-order copies for the tree loops: fine integer position, offset from
+// the fine sub-cell corner with the mass, (v, u), starting h, list radius.
+struct TreeGatherArgs {
+  int64_t n_total;
+  int n_sims;
+  const int32_t* perm;
+  const uint64_t* skey;
+  const sphk::GridDev* grid;
+  const double *x, *y, *z;
+  const float *m, *vx, *vy, *vz, *u, *h;
+  const float* leaf_side;
+  float list_reach;  // list radius / starting support
+  int4* fine;
+  float4 *rel, *vel4;
+  float *hs, *lrad;
+};
+cudaError_t launch_tree_gather(const TreeGatherArgs& a, cudaStream_t st);
+
+// Density on the leaves (tree_loops.cu).  Lists hold packed (tree index,
+// periodic shift) entries, kTreeListRegion per (4 ti + lane); list_cnt 0xffff
+// marks a target whose sums were taken without a list.  Pairs that only the
+// larger support reaches are emitted as reverse pairs and ordered by
+// receiver into rev_start / rev.
+struct TreeDensityArgs {
+  int n_sims;
+  int num_sms;
+  int64_t n_total;
+  const sphk::GridDev* grid;
+  const int32_t* tgt;  // target order -> source index
+  const sphk::TreeLeaf* leaves;
+  const int32_t* n_leaves;
+  const sphk::TreeRange* ranges;
+  const int4* fine;
+  const float4 *rel, *vel4;
+  const float *hs, *lrad, *leaf_side;
+  const int32_t* perm;
+  int32_t* status;
+  unsigned long long* pairs;
+  float *h, *rho, *f, *div_v, *curl_v, *P, *c, *B;
+  int32_t* n_iter;
+  uint32_t* lists;
+  uint16_t* list_cnt;
+  uint64_t* rev_raw;   // rev_cap emitted pairs (receiver << 32 | packed source)
+  unsigned long long* rev_count;  // 1: pairs emitted (may exceed rev_cap)
+  int32_t* rev_start;  // n + 1: per-receiver counts, then their exclusive scan
+  int32_t* rev_fill;   // n: scatter cursors
+  uint32_t* rev;       // rev_cap: packed sources ordered by (receiver, source)
+  int64_t rev_cap;
+  int32_t* scan_tmp;   // (n + 1) / 1024 + 2
+};
+cudaError_t launch_tree_density(const TreeDensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+
+struct TreeForceArgs {
+  int n_sims;
+  int num_sms;
+  const sphk::GridDev* grid;
+  const int32_t* tgt;
+  const sphk::TreeLeaf* leaves;
+  const int32_t* n_leaves;
+  const sphk::TreeRange* ranges;
+  const int4* fine;
+  const float4* rel;
+  const float *lrad, *leaf_side;
+  const int32_t* perm;
+  const float4 *fA, *fB, *fC;  // as GatherForceArgs (only H of fA is read)
+  const float2* fD;
+  const uint32_t* lists;
+  const uint16_t* list_cnt;
+  const int32_t* rev_start;
+  const uint32_t* rev;
+  unsigned long long* pairs;
+  float *ax, *ay, *az, *du_dt, *v_sig;
+};
+cudaError_t launch_tree_force(const TreeForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 // Exclusive scan of m int32 in place with a host-known length (radix.cu);
 // tmp holds m / 1024 + 2 entries.
 cudaError_t scan_exclusive_host_n(int32_t* a, int64_t m, int32_t* tmp, cudaStream_t st);

@@ -1,0 +1,676 @@
+// tree_loops.cu -- density and force loops on the leaves of the nested grids
+// (tree.cu).  Same mathematics as density.cu / force.cu (Sec. 3.1 and 3.2);
+// the unit of work is a leaf and the 27 cells of its size around it.
+//
+// Positions.  Every particle carries its fine integer position (1024
+// sub-cells per top cell) and its FP32 offset from that sub-cell's corner.
+// Relative to a leaf corner a position is
+//     (fine - corner + shift * N_fine) * s_fine + offset,
+// the integer part exact, so FP32 keeps the sub-cell scale's precision
+// however wide the top cells are.
+//
+// Density, one warp per leaf, kTreeTpp lanes per target:
+//   1. the 27 ranges are staged in chunks relative to the leaf corner;
+//   2. each target keeps, in per-lane lists, the sources closer than its list
+//      radius R_i = min(leaf side, kTreeListReach * starting support);
+//   3. Newton-Raphson passes read r^2 from the lists; if a support outgrows
+//      R_i (or a list overflows) the warp takes the list-free path, which sums
+//      over every staged source;
+//   4. the final pass at the converged h gathers the sources from memory and
+//      publishes the lists for the force loop.
+// A force pair needs r < max(H_i, H_j).  The list of i holds every j with
+// r < R_i >= H_i; a j with H_j > r >= R_i is only in j's own reach, so the
+// density of j emits it as a reverse pair (receiver i, source j).  Reverse
+// pairs are grouped by receiver and sorted by source (deterministic order).
+//
+// Force, one warp per leaf: each target walks its list and its reverse pairs.
+// Whether a pair is the list's or a reverse pair is decided in the target's
+// own leaf frame with the same arithmetic as the density filter, so no pair is
+// counted twice or dropped at the boundary; emission uses a margin so that the
+// reverse pairs are a superset.
+#include "sph_internal.cuh"
+#include "sph_launch.h"
+#include "tree.cuh"
+
+namespace sphk {
+
+constexpr int kTWarps = 4;       // warps per CTA
+constexpr int kTCap = 384;       // staged sources per warp and chunk
+constexpr int kTRows = kTreeList + 1;  // + one scratch row for the branch-free append
+constexpr int kTPer = 32 / kTreeTpp;   // targets per round
+constexpr size_t kTWarpSmem = (size_t)kTCap * (sizeof(float4) + sizeof(uint32_t)) +
+                              (size_t)kTRows * 32 * (sizeof(float) + sizeof(uint32_t));
+constexpr size_t kTDensSmem = kTWarps * kTWarpSmem;
+constexpr int kNoShift = 1 | (1 << 2) | (1 << 4);
+static_assert(kTWarpSmem % 16 == 0, "per-warp regions keep float4 alignment");
+static_assert(kTreeList <= kTreeListRegion, "published lists fit their regions");
+static_assert(kTreeListRegion % 4 == 0, "lists are published as 16-byte vectors");
+
+struct TGeo {
+  float s_fine;        // side of a fine sub-cell
+  float side;          // side of the leaf
+  double side_d;
+  int32_t nfine;       // fine sub-cells per box side
+  int32_t ox, oy, oz;  // fine integer position of the leaf corner
+  double L;
+};
+
+__device__ __forceinline__ TGeo leaf_geo(const TreeLeaf& Lf, const GridDev& G) {
+  TGeo g;
+  const int32_t local = Lf.cell - G.cell_base, nc = G.n_c;
+  const int32_t kx = local % nc, ky = (local / nc) % nc, kz = local / (nc * nc);
+  const int sh = kTreeDepth - Lf.depth;
+  g.ox = kx * kTreeFine + (Lf.lx << sh);
+  g.oy = ky * kTreeFine + (Lf.ly << sh);
+  g.oz = kz * kTreeFine + (Lf.lz << sh);
+  g.s_fine = (float)(G.cell / (double)kTreeFine);
+  g.side_d = G.cell / (double)(1 << Lf.depth);
+  g.side = (float)g.side_d;
+  g.nfine = nc * kTreeFine;
+  g.L = G.L;
+  return g;
+}
+
+// Position relative to the leaf corner of a particle seen with periodic shift
+// code sc (2 bits per axis, shift + 1).
+__device__ __forceinline__ float3 rel_to(const TGeo& g, const float4& rel, const int4& fine, int sc) {
+  const int sx = (sc & 3) - 1, sy = ((sc >> 2) & 3) - 1, sz = ((sc >> 4) & 3) - 1;
+  const int32_t dx = fine.x - g.ox + sx * g.nfine;
+  const int32_t dy = fine.y - g.oy + sy * g.nfine;
+  const int32_t dz = fine.z - g.oz + sz * g.nfine;
+  return make_float3(fmaf((float)dx, g.s_fine, rel.x), fmaf((float)dy, g.s_fine, rel.y),
+                     fmaf((float)dz, g.s_fine, rel.z));
+}
+
+__device__ __forceinline__ float r2_of(const float3& a, const float4& b) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// Pair vector x_i - x_j with the exact integer part (sc = shift code of j).
+__device__ __forceinline__ float3 pair_vec(const TGeo& g, const float4& rel_i, const int4& fine_i,
+                                           const float4& rel_j, const int4& fine_j, int sc) {
+  const int sx = (sc & 3) - 1, sy = ((sc >> 2) & 3) - 1, sz = ((sc >> 4) & 3) - 1;
+  const int32_t dx = fine_i.x - fine_j.x - sx * g.nfine;
+  const int32_t dy = fine_i.y - fine_j.y - sy * g.nfine;
+  const int32_t dz = fine_i.z - fine_j.z - sz * g.nfine;
+  return make_float3(fmaf((float)dx, g.s_fine, rel_i.x - rel_j.x), fmaf((float)dy, g.s_fine, rel_i.y - rel_j.y),
+                     fmaf((float)dz, g.s_fine, rel_i.z - rel_j.z));
+}
+
+// List entries pack the tree-order index (26 bits) with the shift code.
+__device__ __forceinline__ uint32_t pack_js(int32_t j, int sc) { return (uint32_t)j | ((uint32_t)sc << 26); }
+__device__ __forceinline__ int32_t unpack_j(uint32_t e) { return (int32_t)(e & 0x3ffffffu); }
+__device__ __forceinline__ int unpack_s(uint32_t e) { return (int)(e >> 26); }
+// Shift code of i seen from j, given that of j seen from i.
+__device__ __forceinline__ int mirror_s(int sc) {
+  return (2 - (sc & 3)) | ((2 - ((sc >> 2) & 3)) << 2) | ((2 - ((sc >> 4) & 3)) << 4);
+}
+
+struct TDSums {
+  float w, dw, mw, mdw, div, cx, cy, cz;
+  int npair;
+};
+
+__device__ __forceinline__ void tds_zero(TDSums& s) {
+  s.w = s.dw = s.mw = s.mdw = s.div = s.cx = s.cy = s.cz = 0.f;
+  s.npair = 0;
+}
+
+// One density pair with x_ij = (dx, dy, dz) (same terms as density.cu).
+__device__ __forceinline__ void tdens_pair(float dx, float dy, float dz, const float4& vi, const float4& vj,
+                                           float mj, float H, float Hinv, TDSums& s) {
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+  const float q = r2 * rinv * Hinv;
+  float w, g;
+  kernel_w_g(q, H * rinv, w, g);
+  const float dw = fmaf(q * q, g, 3.0f * w);
+  s.w += w;
+  s.dw += dw;
+  s.mw = fmaf(mj, w, s.mw);
+  s.mdw = fmaf(mj, dw, s.mdw);
+  const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
+  const float mg = mj * g;
+  s.div = fmaf(mg, fmaf(ux, dx, fmaf(uy, dy, uz * dz)), s.div);
+  s.cx = fmaf(mg, fmaf(uz, dy, -uy * dz), s.cx);
+  s.cy = fmaf(mg, fmaf(ux, dz, -uz * dx), s.cy);
+  s.cz = fmaf(mg, fmaf(uy, dx, -ux * dy), s.cz);
+  s.npair += q < 1.0f;
+}
+
+// n-hat and its h-derivative terms of one pair (Newton passes).
+__device__ __forceinline__ void tnewton_pair(float r2, float H, float Hinv, float& Sw, float& Sdw) {
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+  const float q = r2 * rinv * Hinv;
+  float w, g;
+  kernel_w_g(q, H * rinv, w, g);
+  Sw += w;
+  Sdw += fmaf(q * q, g, 3.0f * w);
+}
+
+// One Newton-Raphson update of f(h) = n-hat(h) - (eta / h)^3 (Sec. 3.1),
+// with the bracket and cap safeguards of density.cu.  Returns true when the
+// target is done.
+__device__ __forceinline__ bool tnewton(float Sw, float Sdw, double& h, double& lo, double& hi, int& it,
+                                        double hcap, const PhysDev& ph, bool& atcap, bool& conv) {
+  const double g3 = kGammaKd * kGammaKd * kGammaKd;
+  const double eta3 = (double)ph.eta3;
+  const double A = (double)Sw / g3 - eta3;
+  const double B = 3.0 * eta3 - (double)Sdw / g3;
+  if (A < 0.0) lo = h; else hi = h;
+  conv = (B > 0.0) && (fabs(A) <= ph.h_tol * B);
+  atcap = (h >= hcap) && (A < 0.0);
+  const bool last = it + 1 >= ph.max_h_iter;
+  if (conv) {
+    h = h * (1.0 - A / B);
+    if (h > hcap) {
+      h = hcap;
+      atcap = true;
+    }
+    return true;
+  }
+  if (atcap || last) return true;
+  double hn = (B > 0.0) ? h * (1.0 - A / B) : 2.0 * h;
+  hn = fmin(fmax(hn, 0.5 * h), 2.0 * h);
+  if (!(B > 0.0) || !(hn > lo) || !(hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
+  if (hn > hcap) hn = hcap;
+  h = hn;
+  ++it;
+  return false;
+}
+
+__device__ __forceinline__ float sum4(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+
+__device__ __forceinline__ void tcombine(TDSums& s) {
+  s.w = sum4(s.w);
+  s.dw = sum4(s.dw);
+  s.mw = sum4(s.mw);
+  s.mdw = sum4(s.mdw);
+  s.div = sum4(s.div);
+  s.cx = sum4(s.cx);
+  s.cy = sum4(s.cy);
+  s.cz = sum4(s.cz);
+  s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 1);
+  s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 2);
+}
+
+// The leaf's 27 ranges, lane r < 27 holding range r; lanes 27..31 hold empty
+// ranges, so lane 27's cumulative start is the total.
+struct TRanges {
+  int32_t lo, cum, sc;
+  int nsrc;
+};
+
+__device__ __forceinline__ TRanges load_ranges(const TreeRange* __restrict__ ranges, int32_t li, int lane) {
+  TRanges R;
+  int32_t len = 0;
+  R.lo = 0;
+  R.sc = kNoShift;
+  if (lane < 27) {
+    const TreeRange t = ranges[(int64_t)li * 27 + lane];
+    R.lo = t.lo;
+    len = t.hi - t.lo;
+    R.sc = t.shift;
+  }
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  R.cum = incl - len;
+  R.nsrc = __shfl_sync(0xffffffffu, incl, 31);
+  return R;
+}
+
+// Stages sources [v0, v0 + kTCap) of the concatenated ranges relative to the
+// leaf corner (position and mass, packed index).  Called by the whole warp.
+__device__ __forceinline__ int tstage(int v0, const TRanges& R, int lane, const TGeo& g,
+                                      const float4* __restrict__ rel, const int4* __restrict__ fine, float4* spos,
+                                      uint32_t* sidx) {
+  const int cnt = min(kTCap, R.nsrc - v0);
+  for (int r = 0; r < 27; ++r) {
+    const int32_t cm = __shfl_sync(0xffffffffu, R.cum, r);
+    const int32_t cm1 = __shfl_sync(0xffffffffu, R.cum, r + 1);
+    const int32_t lo = __shfl_sync(0xffffffffu, R.lo, r);
+    const int sc = __shfl_sync(0xffffffffu, R.sc, r);
+    const int a0 = max(cm, v0), b0 = min(cm1, v0 + cnt);
+    for (int v = a0 + lane; v < b0; v += 32) {
+      const int32_t j = lo + (v - cm);
+      const float4 rj = rel[j];
+      const float3 p = rel_to(g, rj, fine[j], sc);
+      spos[v - v0] = make_float4(p.x, p.y, p.z, rj.w);
+      sidx[v - v0] = pack_js(j, sc);
+    }
+  }
+  __syncwarp();
+  return cnt;
+}
+
+// Reverse pair of target ti (support H, leaf side s_i) and source j (shift
+// code sc of j seen from ti) at r^2 = r2 in ti's frame: wanted when r < H and
+// r reaches past j's list radius, lowered by a margin above the rounding of r
+// in either frame (the force decides again, exactly, in j's frame).
+__device__ __forceinline__ bool want_reverse(const sphh::TreeDensityArgs& a, int32_t ti, int32_t j, float r2,
+                                             float H2, float H, float s_i) {
+  if (!(r2 < H2) || j == ti) return false;
+  const float thr = a.lrad[j] - 0x1p-18f * (s_i + a.leaf_side[j] + H);
+  return !(thr > 0.0f && r2 < thr * thr);
+}
+
+// Appends the wanted records of the warp (one counter atomic per warp).
+// Called by all 32 lanes.
+__device__ __forceinline__ void emit_warp(const sphh::TreeDensityArgs& a, bool want, uint64_t rec, int lane) {
+  const unsigned em = __ballot_sync(0xffffffffu, want);
+  if (!em) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(a.rev_count, (unsigned long long)__popc(em));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (want) {
+    const unsigned long long k = base + (unsigned long long)__popc(em & ((1u << lane) - 1u));
+    if (k < (unsigned long long)a.rev_cap) {
+      a.rev_raw[k] = rec;
+      atomicAdd(&a.rev_start[(int32_t)(rec >> 32)], 1);
+    } else {
+      atomicOr(a.status, SPH_ST_CAPACITY);
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t reverse_rec(int32_t j, int32_t ti, int sc) {
+  return ((uint64_t)(uint32_t)j << 32) | pack_js(ti, mirror_s(sc));
+}
+
+__global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensityArgs a, PhysDev ph) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = tsm + (size_t)warp * kTWarpSmem;
+  float4* spos = reinterpret_cast<float4*>(base);
+  uint32_t* sidx = reinterpret_cast<uint32_t*>(spos + kTCap);
+  float* lr2 = reinterpret_cast<float*>(sidx + kTCap);
+  uint32_t* lje = reinterpret_cast<uint32_t*>(lr2 + kTRows * 32);
+  const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
+  const int32_t nl = *a.n_leaves;
+  unsigned long long pair_acc = 0;
+  for (int32_t li = blockIdx.x * kTWarps + warp; li < nl; li += gridDim.x * kTWarps) {
+    const TreeLeaf Lf = a.leaves[li];
+    const int32_t t_lo = Lf.start, n_t = a.leaves[li + 1].start - Lf.start;
+    const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, Lf.cell)];
+    const TGeo g = leaf_geo(Lf, G);
+    const TRanges R = load_ranges(a.ranges, li, lane);
+    const int nsrc = R.nsrc;
+    const double hcap = fmin(g.side_d, 0.5 * g.L) * (1.0 - 1e-5) / kGammaKd;
+    const bool one_chunk = nsrc <= kTCap;
+    if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx);
+    for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
+      const bool valid = t0 + t < n_t;
+      const int32_t ti = a.tgt[t_lo + (valid ? t0 + t : 0)];
+      const float4 reli = a.rel[ti];
+      const int4 fi = a.fine[ti];
+      const float3 pi = rel_to(g, reli, fi, kNoShift);
+      const float4 vi = a.vel4[ti];
+      const float Ri = a.lrad[ti];
+      const float R2 = Ri * Ri;
+      // 1. filter: sources with r < R_i into this lane's list
+      int cnt = 0;
+      for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
+        const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
+        if (valid) {
+          for (int k = sub; k < c; k += kTreeTpp) {
+            const float r2 = r2_of(pi, spos[k]);
+            const int at = min(cnt, kTreeList) * 32 + lane;
+            lr2[at] = r2;
+            lje[at] = sidx[k];
+            cnt += r2 < R2;
+          }
+        }
+        if (!one_chunk) __syncwarp();
+      }
+      bool direct = __any_sync(0xffffffffu, cnt > kTreeList);
+      // 2. Newton-Raphson passes
+      double h = valid ? (double)a.hs[ti] : hcap;
+      if (!(h > 0.0)) h = 0.5 * hcap;
+      if (h > hcap) h = hcap;
+      if (!direct) direct = __any_sync(0xffffffffu, valid && kGammaK * (float)h > Ri);
+      double hlo = 0.0, hhi = INFINITY;
+      bool done = !valid, atcap = false, conv = false;
+      int it = 0, passes = 0;
+      while (__any_sync(0xffffffffu, !done)) {
+        const float H = kGammaK * (float)h;
+        const float Hinv = 1.0f / H;
+        float Sw = 0.f, Sdw = 0.f;
+        if (!direct) {
+          const int m = done ? 0 : cnt;
+          for (int e = 0; e < m; ++e) tnewton_pair(lr2[e * 32 + lane], H, Hinv, Sw, Sdw);
+        } else {
+          for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
+            const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
+            if (!done)
+              for (int k = sub; k < c; k += kTreeTpp) tnewton_pair(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
+            if (!one_chunk) __syncwarp();
+          }
+        }
+        Sw = sum4(Sw);
+        Sdw = sum4(Sdw);
+        if (!done) {
+          passes = it + 1;
+          if (tnewton(Sw, Sdw, h, hlo, hhi, it, hcap, ph, atcap, conv)) done = true;
+        }
+        // the list holds r < R_i: a support beyond it needs every staged source
+        if (!direct) direct = __any_sync(0xffffffffu, valid && kGammaK * (float)h > Ri);
+      }
+      // 3. final pass at h
+      const float H = kGammaK * (float)h;
+      const float Hinv = 1.0f / H;
+      const float H2 = H * H;
+      TDSums s;
+      tds_zero(s);
+      if (!direct) {
+        if (valid) {
+          for (int e = 0; e < cnt; ++e) {
+            const uint32_t je = lje[e * 32 + lane];
+            const int32_t j = unpack_j(je);
+            const float4 rj = a.rel[j];
+            const float3 d = pair_vec(g, reli, fi, rj, a.fine[j], unpack_s(je));
+            tdens_pair(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
+          }
+        }
+        // reverse pairs from the list (warp-uniform trip count)
+        const int emax = __reduce_max_sync(0xffffffffu, valid ? cnt : 0);
+        for (int e = 0; e < emax; ++e) {
+          bool want = false;
+          uint64_t rec = 0;
+          if (valid && e < cnt) {
+            const uint32_t je = lje[e * 32 + lane];
+            const int32_t j = unpack_j(je);
+            want = want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side);
+            rec = reverse_rec(j, ti, unpack_s(je));
+          }
+          emit_warp(a, want, rec, lane);
+        }
+      } else {
+        for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
+          const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
+          for (int k0 = 0; k0 < c; k0 += kTreeTpp) {
+            const int k = k0 + sub;
+            bool want = false;
+            uint64_t rec = 0;
+            if (valid && k < c) {
+              const float4 pj = spos[k];
+              const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              if (r2 < H2) {
+                const uint32_t je = sidx[k];
+                const int32_t j = unpack_j(je);
+                tdens_pair(dx, dy, dz, vi, a.vel4[j], pj.w, H, Hinv, s);
+                want = want_reverse(a, ti, j, r2, H2, H, g.side);
+                rec = reverse_rec(j, ti, unpack_s(je));
+              }
+            }
+            emit_warp(a, want, rec, lane);
+          }
+          if (!one_chunk) __syncwarp();
+        }
+      }
+      tcombine(s);
+      // 4. publish the list (16-byte vectors) for the force loop
+      if (valid) {
+        const int64_t col = (int64_t)ti * kTreeTpp + sub;
+        a.list_cnt[col] = (uint16_t)(direct ? 0xffff : cnt);
+        if (!direct) {
+          uint4* dst = reinterpret_cast<uint4*>(a.lists + col * kTreeListRegion);
+          for (int e = 0; e < cnt; e += 4)
+            dst[e >> 2] = make_uint4(lje[e * 32 + lane], lje[(e + 1) * 32 + lane], lje[(e + 2) * 32 + lane],
+                                     lje[(e + 3) * 32 + lane]);
+        }
+      }
+      if (valid && sub == 0) {
+        const int32_t p = a.perm[ti];
+        const float H2inv = Hinv * Hinv;
+        const float rho = s.mw * H2inv * Hinv;
+        const float fval = 1.0f / (1.0f - s.mdw / (3.0f * s.mw));
+        const float div = s.div * H2inv / s.mw;
+        const float curl = sqrtf(fmaf(s.cx, s.cx, fmaf(s.cy, s.cy, s.cz * s.cz))) * H2inv / s.mw;
+        const float P = (ph.gamma - 1.0f) * vi.w * rho;
+        const float cs = sqrtf(ph.gamma * P / rho);
+        const float hf = (float)h;
+        a.h[p] = hf;
+        a.rho[p] = rho;
+        a.f[p] = fval;
+        a.div_v[p] = div;
+        a.curl_v[p] = curl;
+        a.P[p] = P;
+        a.c[p] = cs;
+        a.B[p] = fabsf(div) / (fabsf(div) + curl + ph.eps_balsara * cs / hf);
+        if (a.n_iter) a.n_iter[p] = passes;
+        if (atcap) atomicOr(a.status, SPH_ST_REBUILD);
+        else if (!conv) atomicOr(a.status, SPH_ST_H_NOCONV);
+        pair_acc += (unsigned long long)s.npair;
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+  }
+  if (ph.count_pairs) {
+    unsigned long long v = pair_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(a.pairs, v);
+  }
+}
+
+// Reverse pairs -> per-receiver segments: rev_start holds the exclusive scan
+// of the counts; each pair takes a slot of its receiver's segment.
+__global__ void k_rev_scatter(const uint64_t* __restrict__ raw, const unsigned long long* __restrict__ count,
+                              int64_t cap, const int32_t* __restrict__ start, int32_t* __restrict__ fill,
+                              uint32_t* __restrict__ rev) {
+  const int64_t m = (int64_t)min(*count, (unsigned long long)cap);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = raw[k];
+    const int32_t r = (int32_t)(e >> 32);
+    const int32_t pos = start[r] + atomicAdd(&fill[r], 1);
+    rev[pos] = (uint32_t)(e & 0xffffffffu);
+  }
+}
+
+// Sorts each receiver's segment by packed source (the slot order above is
+// arbitrary), so the force sums run in a fixed order.
+__global__ void k_rev_sort(int64_t n, const int32_t* __restrict__ start, uint32_t* __restrict__ rev) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = start[i], e = start[i + 1];
+    for (int32_t k = b + 1; k < e; ++k) {
+      const uint32_t v = rev[k];
+      int32_t q = k - 1;
+      while (q >= b && rev[q] > v) {
+        rev[q + 1] = rev[q];
+        --q;
+      }
+      rev[q + 1] = v;
+    }
+  }
+}
+
+// ---- force ------------------------------------------------------------------
+
+struct TFSums {
+  float ax, ay, az, du, vsig;
+  int npair;
+};
+
+// One force pair with x_ij = (dx, dy, dz) (same terms as force.cu).
+__device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const float4& vi, const float4& ci,
+                                            float Hi, float Hinv_i, float rho_i, const float4& vj,
+                                            const float4& cj, float Hj, float Hinv_j, float rho_j,
+                                            const PhysDev& ph, TFSums& s) {
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+  const float r = r2 * rinv;
+  const float hi2 = Hinv_i * Hinv_i, hj2 = Hinv_j * Hinv_j;
+  const float Gi = kernel_g(r * Hinv_i, Hi * rinv) * (hi2 * hi2 * Hinv_i);
+  const float Gj = kernel_g(r * Hinv_j, Hj * rinv) * (hj2 * hj2 * Hinv_j);
+  const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+  const float vdotx = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+  const float mu = fminf(vdotx, 0.0f) * rinv;
+  const float vs = fmaf(-ph.beta_v, mu, ci.z + cj.z);
+  const float nu = __fdividef(-ph.alpha_v * (ci.w + cj.w) * mu * vs, rho_i + rho_j);
+  const float piG = ci.x * Gi;
+  const float visc = fmaf(ci.y, Gi, cj.y * Gj);
+  const float mj = vj.w;
+  const float sc = mj * fmaf(0.5f * nu, visc, fmaf(cj.x, Gj, piG));
+  s.ax = fmaf(-sc, dx, s.ax);
+  s.ay = fmaf(-sc, dy, s.ay);
+  s.az = fmaf(-sc, dz, s.az);
+  s.du = fmaf(mj * fmaf(0.25f * nu, visc, piG), vdotx, s.du);
+  const float Hm = fmaxf(Hi, Hj);
+  const bool in = r2 < Hm * Hm;
+  s.vsig = in ? fmaxf(s.vsig, vs) : s.vsig;
+  s.npair += in;
+}
+
+__global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs a, PhysDev ph) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
+  const int32_t nl = *a.n_leaves;
+  unsigned long long pair_acc = 0;
+  for (int32_t li = blockIdx.x * kTWarps + warp; li < nl; li += gridDim.x * kTWarps) {
+    const TreeLeaf Lf = a.leaves[li];
+    const int32_t t_lo = Lf.start, n_t = a.leaves[li + 1].start - Lf.start;
+    const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, Lf.cell)];
+    const TGeo g = leaf_geo(Lf, G);
+    for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
+      const bool valid = t0 + t < n_t;
+      const int32_t ti = a.tgt[t_lo + (valid ? t0 + t : 0)];
+      TFSums s;
+      s.ax = s.ay = s.az = s.du = s.vsig = 0.f;
+      s.npair = 0;
+      if (valid) {
+        const float4 reli = a.rel[ti];
+        const int4 fi = a.fine[ti];
+        const float3 pi = rel_to(g, reli, fi, kNoShift);
+        const float4 vi = a.fB[ti];
+        const float4 ci = a.fC[ti];
+        const float2 di = a.fD[ti];
+        const float Hi = a.fA[ti].w;
+        const int64_t col = (int64_t)ti * kTreeTpp + sub;
+        const int lc = (int)a.list_cnt[col];
+        const bool direct = lc == 0xffff;
+        // own reach: the list radius, or the leaf side on the list-free path
+        const float C = direct ? g.side : a.lrad[ti];
+        const float C2 = C * C;
+        if (!direct) {
+          const uint32_t* lst = a.lists + col * kTreeListRegion;
+          for (int e = 0; e < lc; ++e) {
+            const uint32_t je = lst[e];
+            const int32_t j = unpack_j(je);
+            if (j == ti) continue;
+            const float4 rj = a.rel[j];
+            const float3 d = pair_vec(g, reli, fi, rj, a.fine[j], unpack_s(je));
+            const float2 dj = a.fD[j];
+            tforce_pair(d.x, d.y, d.z, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
+          }
+        } else {
+          for (int r = 0; r < 27; ++r) {
+            const TreeRange Rg = a.ranges[(int64_t)li * 27 + r];
+            for (int32_t j = Rg.lo + sub; j < Rg.hi; j += kTreeTpp) {
+              if (j == ti) continue;
+              const float4 rj = a.rel[j];
+              const float3 pj = rel_to(g, rj, a.fine[j], Rg.shift);
+              const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+              if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2) {
+                const float2 dj = a.fD[j];
+                tforce_pair(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
+              }
+            }
+          }
+        }
+        // reverse pairs beyond the own reach, split between the lanes
+        const int32_t r0 = a.rev_start[ti], r1 = a.rev_start[ti + 1];
+        for (int32_t k = r0 + sub; k < r1; k += kTreeTpp) {
+          const uint32_t je = a.rev[k];
+          const int32_t j = unpack_j(je);
+          const float4 rj = a.rel[j];
+          const float3 pj = rel_to(g, rj, a.fine[j], unpack_s(je));
+          const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+          if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2) {
+            const float2 dj = a.fD[j];
+            tforce_pair(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
+          }
+        }
+      }
+      s.ax = sum4(s.ax);
+      s.ay = sum4(s.ay);
+      s.az = sum4(s.az);
+      s.du = sum4(s.du);
+      s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, 1));
+      s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, 2));
+      s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 1);
+      s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 2);
+      if (valid && sub == 0) {
+        const int32_t p = a.perm[ti];
+        a.ax[p] = s.ax;
+        a.ay[p] = s.ay;
+        a.az[p] = s.az;
+        a.du_dt[p] = s.du;
+        a.v_sig[p] = s.vsig;
+        pair_acc += (unsigned long long)s.npair;
+      }
+    }
+  }
+  if (ph.count_pairs) {
+    unsigned long long v = pair_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(a.pairs, v);
+  }
+}
+
+}  // namespace sphk
+
+namespace sphh {
+using namespace sphk;
+
+static int tree_blocks(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
+}
+
+cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cudaStream_t st) {
+  static int bps = 0;
+  if (!bps) {
+    cudaError_t e = cudaFuncSetAttribute(k_tree_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTDensSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_density, kTWarps * 32, kTDensSmem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+  }
+  const int64_t n = a.n_total;
+  cudaError_t e = cudaMemsetAsync(a.rev_count, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.rev_start, 0, sizeof(int32_t) * (n + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.rev_fill, 0, sizeof(int32_t) * (n > 0 ? n : 1), st);
+  if (e != cudaSuccess) return e;
+  if (n <= 0) return cudaSuccess;
+  k_tree_density<<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
+  e = scan_exclusive_host_n(a.rev_start, n + 1, a.scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  k_rev_scatter<<<a.num_sms * 4, 256, 0, st>>>(a.rev_raw, a.rev_count, a.rev_cap, a.rev_start, a.rev_fill, a.rev);
+  k_rev_sort<<<tree_blocks(n), 256, 0, st>>>(n, a.rev_start, a.rev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tree_force(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+  static int bps = 0;
+  if (!bps) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_force, kTWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+  }
+  k_tree_force<<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
+  return cudaGetLastError();
+}
+
+}  // namespace sphh

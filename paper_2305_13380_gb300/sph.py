@@ -34,6 +34,7 @@ SPH_ST_NEG_U = 16
 SPH_FLAG_SYNC = 1
 SPH_FLAG_COUNT_PAIRS = 2
 SPH_FLAG_TIMING = 4
+SPH_FLAG_TREE = 8
 
 TIMING_GROUPS = ("build", "gather", "density", "force", "integrate")
 
@@ -44,7 +45,8 @@ class sph_params(C.Structure):
     _fields_ = [("box_size", C.c_double), ("gamma", C.c_double), ("eta", C.c_double),
                 ("alpha_v", C.c_double), ("beta_v", C.c_double), ("eps_balsara", C.c_double),
                 ("h_tol", C.c_double), ("cfl", C.c_double), ("cell_margin", C.c_double),
-                ("max_h_iter", C.c_int32), ("flags", C.c_int32)]
+                ("max_h_iter", C.c_int32), ("flags", C.c_int32), ("n_leaf", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class sph_cells(C.Structure):

@@ -40,20 +40,25 @@ def expected_nc(h0_f32, L, margin=0.05, n=None):
     return max(nc, 1)
 
 
-def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-4):
-    """build -> density -> (rebuild while the status asks) -> force on cuda:0."""
+def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-4, tree=False, n_leaf=16, h_start=None):
+    """build -> density -> (rebuild while the status asks) -> force on cuda:0.
+    tree: nested grids below the top cells; h_start: starting guess of h
+    (default p["h0"])."""
     import torch
     from paper_2305_13380_gb300 import sph
     flags = sph.SPH_FLAG_COUNT_PAIRS if count_pairs else 0
+    if tree:
+        flags |= sph.SPH_FLAG_TREE
     params = sph.sph_default_params(box_size=float(p["L"]), cell_margin=margin, flags=flags,
-                                    h_tol=h_tol)
+                                    h_tol=h_tol, n_leaf=n_leaf)
     ctx = sph.Context(params)
     t = sph.to_device(p)
     n = int(t["x"].shape[0])
     part = sph.particles(t)
     d = sph.alloc_density(n)
     f = sph.alloc_force(n)
-    h_in = t["h0"]
+    h_in = t["h0"] if h_start is None else torch.as_tensor(
+        np.asarray(h_start, dtype=np.float32), device="cuda")
     rebuilds = 0
     for _ in range(8):
         cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], h_in)
