@@ -38,17 +38,26 @@ F_DENSITY = 66
 F_FORCE = 72
 
 
-def launches_per_step(n_total: int) -> int:
-    """Kernel launches of one sph_step over n_total particles: time-step
-    reduction (3), kick/drift (1), cell build (8 + the radix sort: 1 + 5 per
-    8-bit digit of the cell id, whose range is 8 n + 216 cells), two gathers
-    (2), density (2), force (2), kick (1)."""
-    cap = 8 * n_total + 216
-    bits = 1
-    while bits < 31 and (1 << bits) <= cap:
-        bits += 1
-    radix = 1 + 5 * ((bits + 7) // 8)
-    return 3 + 1 + 8 + radix + 2 + 2 + 2 + 1
+def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False) -> int:
+    """Kernel launches of one sph_step over n_total particles.
+
+    Uniform grid: time-step reduction (3), kick/drift (1), cell build (8 + the
+    radix sort: 1 + 5 per 8-bit digit of the cell id, whose range is
+    8 n + 216 n_sims cells), two gathers (2), density (2), force (2), kick (1).
+    Nested grids: the cell build without its sort (8), the tree build (two
+    64-bit radix sorts of 30 + c and 34 + c bits, c the cell-id bits, plus
+    key, source keys, levels, target keys, flags, a 3-kernel scan, groups,
+    count, neighbour ranges: 12), the tree gather (1), density with the
+    reverse-pair grouping (6), force gather (1), force (1)."""
+    cap = 8 * n_total + 216 * n_sims
+    cbits = 1
+    while cbits < 30 and (1 << cbits) <= cap:
+        cbits += 1
+    radix = lambda bits: 1 + 5 * ((bits + 7) // 8)  # noqa: E731
+    integrate = 3 + 1 + 1
+    if not tree:
+        return integrate + 8 + radix(cbits) + 2 + 2 + 2
+    return integrate + 8 + radix(30 + cbits) + radix(34 + cbits) + 12 + 1 + 6 + 1 + 1
 FP32_LANES_PER_SM = 128
 
 
@@ -69,12 +78,25 @@ def parse():
 
 
 def make_workload(name: str) -> dict:
+    """latticeN: jittered N^3 lattice (uniform grid).  clusteredN / clusteredNM:
+    N (or N million, binary: 2M = 2^21) particles in 64 Plummer spheres plus a
+    30% uniform background (nested grids)."""
     from paper_2305_13380_gb300 import inputs
     if name.startswith("lattice"):
         n = int(name[len("lattice"):])
         p = inputs.lattice(n, seed=0)
         p["desc"] = (f"jittered lattice {n}^3 = {n ** 3} particles, periodic unit box, "
                      "jitter +-0.1 d, sigma_v = 0.01, u = 1 +- 1%, equal masses, seed 0")
+        p["tree"] = False
+        return p
+    if name.startswith("clustered"):
+        tail = name[len("clustered"):]
+        n = int(tail[:-1]) << 20 if tail.endswith("M") else int(tail)
+        p = inputs.clustered(n, n_spheres=64, seed=0)
+        p["desc"] = (f"{n} particles: 70% in 64 Plummer spheres (scale radii log-uniform "
+                     "0.002-0.02, centres uniform), 30% uniform background, periodic unit box, "
+                     "u log-normal sigma 1, sigma_v = 0.05, seed 0; nested grids")
+        p["tree"] = True
         return p
     raise SystemExit(f"unknown workload {name}")
 
@@ -154,10 +176,18 @@ def oracle_sample(p, n_target: int, seed: int):
         d = [np.abs((q[k] - c0[i] + 0.5 * L) % L - 0.5 * L) for i, k in enumerate("xyz")]
         return np.where((d[0] < s / 2) & (d[1] < s / 2) & (d[2] < s / 2))[0]
     core = inside(side)
+    if len(core):
+        # the halo reaches one (generous) support of the core's particles;
+        # wider particles outside it keep stand-in values from their h0
+        H = 1.825742 * float(np.max(q["h0"][core])) * 1.5
     halo = inside(side + 2 * H)
     t0 = time.perf_counter()
     d = oracle.density(q, q["h0"], targets=halo)
-    state = {k: np.zeros(n) for k in ("h", "rho", "f", "P", "c", "B")}
+    h0 = q["h0"]
+    rho0 = q["m"] * (1.2348 / h0) ** 3
+    P0 = (5.0 / 3.0 - 1.0) * q["u"] * rho0
+    state = {"h": h0.copy(), "rho": rho0, "f": np.ones(n), "P": P0,
+             "c": np.sqrt(5.0 / 3.0 * P0 / rho0), "B": np.full(n, 0.5)}
     for k in state:
         state[k][halo] = d[k]
     oracle.force(q, state, targets=core)
@@ -209,11 +239,11 @@ def run_reference(args, world: int, rank: int):
 
 
 # ------------------------------------------------------------------ ours ---
-def _traffic(kernel: str):
+def _traffic(kernel: str, source: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of that kernel."""
+    on the current source file of that kernel."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2305_13380_gb300", "csrc", kernel + ".cu")
+    src = os.path.join(ROOT, "paper_2305_13380_gb300", "csrc", source + ".cu")
     try:
         rec = json.load(open(path))[kernel]
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -238,8 +268,9 @@ def run_batch(args, world: int, rank: int, local: int):
     n_boxes = int(args.workload[len("batch"):] or 256)
     boxes = inputs.batch(n_boxes, seed0=0)
     n = sum(len(b["x"]) for b in boxes)
-    margin = tune.best_margin(boxes, key=f"batch{n_boxes}")
-    P = pool.Pool(boxes, sph.sph_default_params(cell_margin=margin))
+    over = tune.best_params(boxes, key=f"batch{n_boxes}")
+    prm = lambda: sph.sph_default_params(**over)  # noqa: E731
+    P = pool.Pool(boxes, prm())
     P.start()
     P.capture()
     for _ in range(args.warmup):
@@ -259,8 +290,7 @@ def run_batch(args, world: int, rank: int, local: int):
     per = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])
     st = P.status()
     # one simulation per launch: every box has its own pool and context
-    singles = [pool.Pool([b], sph.sph_default_params(cell_margin=margin), stream=P.stream)
-               for b in boxes]
+    singles = [pool.Pool([b], prm(), stream=P.stream) for b in boxes]
     for S in singles:
         S.start()
     for _ in range(2):
@@ -282,12 +312,12 @@ def run_batch(args, world: int, rank: int, local: int):
         "config": {"workload": args.workload, "boxes": n_boxes, "particles": n,
                    "desc": "periodic unit boxes, N log-uniform in [1e3, 1e5], even: jittered "
                            "lattice, odd: 4 Plummer spheres + background",
-                   "cell_margin": margin},
+                   "tuned": over},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "particle_updates_per_s": n / (float(np.mean(per)) / 1e3),
         "plain_ms_per_step": plain_ms, "plain_particle_updates_per_s": n / (plain_ms / 1e3),
         "speedup_vs_plain": plain_ms / float(np.mean(per)),
-        "gpu_launches": launches_per_step(n) * args.steps,
+        "gpu_launches": launches_per_step(n, n_boxes, bool(over["flags"] & sph.SPH_FLAG_TREE)) * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "device_status": st}
@@ -329,8 +359,9 @@ def main():
     sim_offset = torch.tensor([0, n], dtype=torch.int64, device=dev)
     box = torch.tensor([L], dtype=torch.float64, device=dev)
 
+    tree = sph.SPH_FLAG_TREE if p["tree"] else 0
     # initial density + force (untimed) through the single-simulation calls
-    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC))
+    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | tree))
     part = sph.particles(t)
     dout = sph.density_out({k: arrays[k] for k in sph.DENSITY_FIELDS})
     h_in = t["h0"]
@@ -346,7 +377,7 @@ def main():
     sph.sph_force(init, cells, part, dout, sph.force_out({k: arrays[k] for k in sph.FORCE_FIELDS}))
     init.close()
 
-    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING))
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | tree))
     pool = sph.pool(sim_offset, box, arrays)
     for _ in range(args.warmup):
         sph.sph_step(ctx, pool)
@@ -388,7 +419,7 @@ def main():
     value = world * n * args.steps / (ms / 1e3)
 
     # one more step (untimed) that counts pairs and Newton passes
-    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS))
+    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | tree))
     arrays["n_iter"] = torch.zeros(n, dtype=torch.int32, device=dev)
     sph.sph_step(cnt, sph.pool(sim_offset, box, arrays))
     pairs_d, pairs_f = sph.sph_pair_counts(cnt)
@@ -401,7 +432,7 @@ def main():
     host = {k: arrays[k].cpu().pin_memory() for k in in_keys}
     bi = sum(host[k].numel() * host[k].element_size() for k in in_keys)
     bo = sum(host[k].numel() * host[k].element_size() for k in out_keys)
-    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L))
+    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=tree))
     for it in range(2 + args.e2e_steps):
         if it == 2:
             torch.cuda.synchronize()
@@ -429,8 +460,10 @@ def main():
     else:
         kname, kms, flops = "force", force_ms, pairs_f * F_FORCE
     achieved = flops / (kms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": f"k_{kname}", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(kname),
+    kfull = f"k_tree_{kname}" if tree else f"k_{kname}"
+    roofline = {"bound": "alu", "kernel": kfull, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": _traffic(kfull[2:], "tree_loops" if tree else kname),
                 "peak_basis": (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                f"lanes x 2 flop x {peak_mhz:.0f} MHz (derived; no measured FP32 "
                                "peak in MEASURED_PEAKS.json)"),
@@ -450,7 +483,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "steps": args.e2e_steps},
-        "gpu_launches": launches_per_step(n) * args.steps,
+        "gpu_launches": launches_per_step(n, 1, bool(tree)) * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "roofline": roofline,

@@ -50,6 +50,8 @@ struct sph_ctx {
   int64_t rev_cap = 0;
   uint64_t *key64 = nullptr, *key64_b = nullptr, *key64_c = nullptr, *skey = nullptr;
   int32_t *tgt = nullptr, *flag = nullptr, *leaf_of = nullptr, *n_leaves = nullptr;
+  int8_t *level = nullptr, *fb_level = nullptr;
+  int32_t* fb_list = nullptr;
   sphk::TreeLeaf* leaves = nullptr;
   sphk::TreeRange* ranges = nullptr;
   float *leaf_side = nullptr, *lrad = nullptr;
@@ -127,6 +129,9 @@ void free_tree(sph_ctx* c) {
   dfree(c->key64_c);
   dfree(c->skey);
   dfree(c->tgt);
+  dfree(c->level);
+  dfree(c->fb_level);
+  dfree(c->fb_list);
   dfree(c->flag);
   dfree(c->leaf_of);
   dfree(c->n_leaves);
@@ -164,7 +169,8 @@ int ensure_tree(sph_ctx* c, int64_t n, int64_t rev_need) {
   if (rc < rev_old) rc = rev_old;
   if (rc > INT32_MAX) rc = INT32_MAX;
   bool ok = dalloc(c->key64, cn) && dalloc(c->key64_b, cn) && dalloc(c->key64_c, cn) &&
-            dalloc(c->skey, cn) && dalloc(c->tgt, cn) && dalloc(c->flag, cn) && dalloc(c->leaf_of, cn) && dalloc(c->n_leaves, 1) &&
+            dalloc(c->skey, cn) && dalloc(c->tgt, cn) && dalloc(c->flag, cn) && dalloc(c->level, cn) &&
+            dalloc(c->fb_level, cn) && dalloc(c->fb_list, cn) && dalloc(c->leaf_of, cn) && dalloc(c->n_leaves, 1) &&
             dalloc(c->leaves, cn + 1) && dalloc(c->ranges, 27 * cn) && dalloc(c->leaf_side, cn) &&
             dalloc(c->lrad, cn) && dalloc(c->fine, cn) && dalloc(c->rel, cn) &&
             dalloc(c->tlists, (int64_t)sphk::kTreeListRegion * sphk::kTreeTpp * cn) &&
@@ -366,6 +372,7 @@ int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const 
     t.n_leaves = c->n_leaves;
     t.ranges = c->ranges;
     t.leaf_side = c->leaf_side;
+    t.level = c->level;
     if (sphh::launch_tree_build(t, c->st) != cudaSuccess) return SPH_E_CUDA;
   }
   t_end(c, SPH_T_BUILD);
@@ -445,6 +452,14 @@ int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* 
   d.rev = c->rev;
   d.rev_cap = c->rev_cap;
   d.scan_tmp = c->scan_sums;
+  d.work = c->misc + sphk::kTreeWork;
+  d.skey = c->skey;
+  d.cell_start = c->cell_start;
+  d.level = c->level;
+  d.fb_list = c->fb_list;
+  d.fb_count = c->misc + sphk::kTreeFbCount;
+  d.fb_level = c->fb_level;
+  d.fb_work = c->misc + sphk::kTreeFbWork;
   t_begin(c, SPH_T_DENSITY);
   const cudaError_t e = sphh::launch_tree_density(d, phys_of(c->p), c->st);
   t_end(c, SPH_T_DENSITY);
@@ -577,6 +592,14 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
     a.az = az;
     a.du_dt = du_dt;
     a.v_sig = v_sig;
+    a.work = c->misc + sphk::kTreeWork;
+    a.n_total = c->built_n;
+    a.skey = c->skey;
+    a.cell_start = c->cell_start;
+    a.fb_list = c->fb_list;
+    a.fb_count = c->misc + sphk::kTreeFbCount;
+    a.fb_level = c->fb_level;
+    a.fb_work = c->misc + sphk::kTreeFbWork;
     t_begin(c, SPH_T_FORCE);
     const cudaError_t e = sphh::launch_tree_force(a, phys_of(c->p), c->st);
     t_end(c, SPH_T_FORCE);

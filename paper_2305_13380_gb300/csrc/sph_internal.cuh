@@ -21,9 +21,11 @@ constexpr int kThreads = 32 * kWarpsPerBlock;
 enum MiscSlot {
   kStatus = 0,       // SPH_ST_* bits
   kTotalCells = 1,   // number of cells over all simulations of the last build
-  kSpare = 2,
+  kTreeWork = 2,     // group counter of the tree loops
   kTotalBlocks = 3,  // number of 2x2x2 blocks of cells over all simulations
   kNumOverflow = 4,  // blocks queued for the overflow kernel of a loop
+  kTreeFbCount = 5,  // targets queued for the coarser-level solve of the tree loops
+  kTreeFbWork = 6,   // queue counter of the tree fallback kernels
   kMiscWords = 8
 };
 

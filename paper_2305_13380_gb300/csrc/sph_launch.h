@@ -132,6 +132,7 @@ struct TreeBuildArgs {
   sphk::TreeLeaf* leaves;     // n + 1: target groups, start in target order
   int32_t* n_leaves;          // 1 (device)
   sphk::TreeRange* ranges;    // 27 n: source-order ranges of each group
+  int8_t* level;              // n (source order): level of each particle
   float* leaf_side;           // n (source order): cell side of each particle's level
 };
 cudaError_t launch_tree_build(const TreeBuildArgs& a, cudaStream_t st);
@@ -185,6 +186,14 @@ struct TreeDensityArgs {
   uint32_t* rev;       // rev_cap: packed sources ordered by (receiver, source)
   int64_t rev_cap;
   int32_t* scan_tmp;   // (n + 1) / 1024 + 2
+  int32_t* work;       // 1: group counter (reset by the launcher)
+  // targets whose support outgrew their level, re-solved one level coarser
+  const uint64_t* skey;        // n: source keys
+  const int32_t* cell_start;   // top cells' ranges
+  const int8_t* level;         // n: level of each particle
+  int32_t *fb_list, *fb_count;  // n, 1
+  int8_t* fb_level;            // n: level of the fallback solve
+  int32_t* fb_work;            // 1
 };
 cudaError_t launch_tree_density(const TreeDensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 
@@ -208,6 +217,13 @@ struct TreeForceArgs {
   const uint32_t* rev;
   unsigned long long* pairs;
   float *ax, *ay, *az, *du_dt, *v_sig;
+  int32_t* work;  // 1: group counter (reset by the launcher)
+  int64_t n_total;
+  const uint64_t* skey;
+  const int32_t* cell_start;
+  const int32_t *fb_list, *fb_count;
+  const int8_t* fb_level;
+  int32_t* fb_work;
 };
 cudaError_t launch_tree_force(const TreeForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 // Exclusive scan of m int32 in place with a host-known length (radix.cu);

@@ -28,25 +28,6 @@
 
 namespace sphk {
 
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {
-  // 10 bits -> every third bit of 30
-  v &= 0x3ffu;
-  v = (v | (v << 16)) & 0x030000ffu;
-  v = (v | (v << 8)) & 0x0300f00fu;
-  v = (v | (v << 4)) & 0x030c30c3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-
-__device__ __forceinline__ uint32_t compact3(uint32_t v) {
-  v &= 0x09249249u;
-  v = (v | (v >> 2)) & 0x030c30c3u;
-  v = (v | (v >> 4)) & 0x0300f00fu;
-  v = (v | (v >> 8)) & 0x030000ffu;
-  v = (v | (v >> 16)) & 0x000003ffu;
-  return v;
-}
-
 // Fine coordinate on one axis: g = floor(1024 fl(fl(x n_c) / L)), clamped to
 // the top cell k (the same product and quotient that define k).
 __device__ __forceinline__ int32_t fine_coord(double x, double L, int32_t n_c, int32_t k) {
@@ -84,24 +65,14 @@ __global__ void k_tree_sorted(int64_t n, const int32_t* __restrict__ perm, const
     skey[s] = key64[perm[s]];
 }
 
-// First index in [lo, hi) whose key >= v.
-__device__ __forceinline__ int64_t lower_bound64(const uint64_t* __restrict__ a, int64_t lo, int64_t hi,
-                                                 uint64_t v) {
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (a[mid] < v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
 // Level of each particle (source order) by descending from its top cell, its
-// cell side, and its target key (top cell, Morton prefix of its cell at that
+// level and cell side, and its target key (top cell, Morton prefix of its cell at that
 // level, level) with a copy for the sort.
 __global__ void k_tree_level(int64_t n, const uint64_t* __restrict__ skey, const int32_t* __restrict__ perm,
                              const float* __restrict__ h, const int32_t* __restrict__ cell_start, int n_sims,
                              const GridDev* __restrict__ grid, int n_leaf, double margin,
-                             float* __restrict__ leaf_side, uint64_t* __restrict__ tkey,
-                             uint64_t* __restrict__ tkey_copy) {
+                             int8_t* __restrict__ level, float* __restrict__ leaf_side,
+                             uint64_t* __restrict__ tkey, uint64_t* __restrict__ tkey_copy) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = skey[s];
     const int32_t c = (int32_t)(key >> 30);
@@ -119,6 +90,7 @@ __global__ void k_tree_level(int64_t n, const uint64_t* __restrict__ skey, const
       if (d == kTreeDepth || hi - lo <= n_leaf) break;
       if (G.cell / (double)(1 << (d + 1)) < reach) break;
     }
+    level[s] = (int8_t)d;
     leaf_side[s] = G.cell_f / (float)(1 << d);
     const int sh = 3 * (kTreeDepth - d);
     const uint64_t m = ((key & 0x3fffffffull) >> sh) << sh;
@@ -179,35 +151,9 @@ __global__ void k_tree_neigh(const TreeLeaf* __restrict__ leaves, const int32_t*
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nl * 27;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int32_t li = (int32_t)(t / 27);
-    const int r = (int)(t % 27);
     const TreeLeaf L = leaves[li];
     const GridDev G = grid[sim_of_cell(grid, n_sims, L.cell)];
-    const int32_t local = L.cell - G.cell_base, nc = G.n_c;
-    const int32_t kx = local % nc, ky = (local / nc) % nc, kz = local / (nc * nc);
-    const int d = L.depth;
-    const int64_t span = (int64_t)nc << d;  // cells of this side per box side
-    const int dxs = r % 3 - 1, dys = (r / 3) % 3 - 1, dzs = r / 9 - 1;
-    int64_t gx = ((int64_t)kx << d) + L.lx + dxs;
-    int64_t gy = ((int64_t)ky << d) + L.ly + dys;
-    int64_t gz = ((int64_t)kz << d) + L.lz + dzs;
-    int sx = 0, sy = 0, sz = 0;
-    if (gx < 0) { gx += span; sx = -1; } else if (gx >= span) { gx -= span; sx = 1; }
-    if (gy < 0) { gy += span; sy = -1; } else if (gy >= span) { gy -= span; sy = 1; }
-    if (gz < 0) { gz += span; sz = -1; } else if (gz >= span) { gz -= span; sz = 1; }
-    const int32_t cx = (int32_t)(gx >> d), cy = (int32_t)(gy >> d), cz = (int32_t)(gz >> d);
-    const uint32_t mx = (uint32_t)(gx & ((1 << d) - 1)) << (kTreeDepth - d);
-    const uint32_t my = (uint32_t)(gy & ((1 << d) - 1)) << (kTreeDepth - d);
-    const uint32_t mz = (uint32_t)(gz & ((1 << d) - 1)) << (kTreeDepth - d);
-    const int32_t cid = G.cell_base + cx + nc * (cy + nc * cz);
-    const uint64_t base = ((uint64_t)(uint32_t)cid << 30) | (spread3(mx) | (spread3(my) << 1) | (spread3(mz) << 2));
-    const uint64_t width = (uint64_t)1 << (3 * (kTreeDepth - d));
-    const int64_t c0 = cell_start[cid], c1 = cell_start[cid + 1];
-    TreeRange R;
-    R.lo = (int32_t)lower_bound64(skey, c0, c1, base);
-    R.hi = (int32_t)lower_bound64(skey, R.lo, c1, base + width);
-    R.shift = (sx + 1) | ((sy + 1) << 2) | ((sz + 1) << 4);
-    R.pad = 0;
-    ranges[t] = R;
+    ranges[t] = neighbour_range(G, L, (int)(t % 27), skey, cell_start);
   }
 }
 
@@ -273,7 +219,7 @@ cudaError_t launch_tree_build(const TreeBuildArgs& a, cudaStream_t st) {
   k_tree_sorted<<<blocks_n(n), 256, 0, st>>>(n, a.perm, a.key64, a.skey);
   // levels and target order: (top cell, cell at the level, level), ties by source index
   k_tree_level<<<blocks_n(n), 256, 0, st>>>(n, a.skey, a.perm, a.h, a.cell_start, a.n_sims, a.grid, a.n_leaf,
-                                            a.margin, a.leaf_side, a.key64, a.key64_b);
+                                            a.margin, a.level, a.leaf_side, a.key64, a.key64_b);
   e = radix_sort_index64(n, 34 + cbits, a.key64_b, a.key64_c, a.tgt, a.rv, a.hist, st);
   if (e != cudaSuccess) return e;
   k_tree_tsorted<<<blocks_n(n), 256, 0, st>>>(n, a.tgt, a.key64, a.key64_c);

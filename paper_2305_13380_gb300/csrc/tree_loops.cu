@@ -42,6 +42,9 @@ constexpr size_t kTWarpSmem = (size_t)kTCap * (sizeof(float4) + sizeof(uint32_t)
                               (size_t)kTRows * 32 * (sizeof(float) + sizeof(uint32_t));
 constexpr size_t kTDensSmem = kTWarps * kTWarpSmem;
 constexpr int kNoShift = 1 | (1 << 2) | (1 << 4);
+// list_cnt markers: sums taken without a list; target re-solved by the fallback
+constexpr uint16_t kListNone = 0xffff;
+constexpr uint16_t kListFallback = 0xfffe;
 static_assert(kTWarpSmem % 16 == 0, "per-warp regions keep float4 alignment");
 static_assert(kTreeList <= kTreeListRegion, "published lists fit their regions");
 static_assert(kTreeListRegion % 4 == 0, "lists are published as 16-byte vectors");
@@ -105,6 +108,16 @@ __device__ __forceinline__ int unpack_s(uint32_t e) { return (int)(e >> 26); }
 // Shift code of i seen from j, given that of j seen from i.
 __device__ __forceinline__ int mirror_s(int sc) {
   return (2 - (sc & 3)) | ((2 - ((sc >> 2) & 3)) << 2) | ((2 - ((sc >> 4) & 3)) << 4);
+}
+
+// Groups are handed out one per warp from a counter: their costs differ by
+// orders of magnitude (a coarse group beside a dense core stages thousands of
+// sources), so a static assignment leaves a few warps running long after the
+// others are done.
+__device__ __forceinline__ int32_t next_group(int32_t* work, int lane) {
+  int32_t g = 0;
+  if (lane == 0) g = atomicAdd(work, 1);
+  return __shfl_sync(0xffffffffu, g, 0);
 }
 
 struct TDSums {
@@ -285,6 +298,33 @@ __device__ __forceinline__ uint64_t reverse_rec(int32_t j, int32_t ti, int sc) {
   return ((uint64_t)(uint32_t)j << 32) | pack_js(ti, mirror_s(sc));
 }
 
+// Outputs of target ti (source index) from its sums at h (Sec. 3.1 and the
+// equation of state of Sec. 3.2).
+__device__ __forceinline__ void tdens_write(const sphh::TreeDensityArgs& a, const PhysDev& ph, int32_t ti,
+                                            double h, const TDSums& s, float u_i, int passes, bool noconv) {
+  const int32_t p = a.perm[ti];
+  const float H = kGammaK * (float)h;
+  const float Hinv = 1.0f / H;
+  const float H2inv = Hinv * Hinv;
+  const float rho = s.mw * H2inv * Hinv;
+  const float fval = 1.0f / (1.0f - s.mdw / (3.0f * s.mw));
+  const float div = s.div * H2inv / s.mw;
+  const float curl = sqrtf(fmaf(s.cx, s.cx, fmaf(s.cy, s.cy, s.cz * s.cz))) * H2inv / s.mw;
+  const float P = (ph.gamma - 1.0f) * u_i * rho;
+  const float cs = sqrtf(ph.gamma * P / rho);
+  const float hf = (float)h;
+  a.h[p] = hf;
+  a.rho[p] = rho;
+  a.f[p] = fval;
+  a.div_v[p] = div;
+  a.curl_v[p] = curl;
+  a.P[p] = P;
+  a.c[p] = cs;
+  a.B[p] = fabsf(div) / (fabsf(div) + curl + ph.eps_balsara * cs / hf);
+  if (a.n_iter) a.n_iter[p] = passes;
+  if (noconv) atomicOr(a.status, SPH_ST_H_NOCONV);
+}
+
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -296,7 +336,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
   const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
   const int32_t nl = *a.n_leaves;
   unsigned long long pair_acc = 0;
-  for (int32_t li = blockIdx.x * kTWarps + warp; li < nl; li += gridDim.x * kTWarps) {
+  for (int32_t li = next_group(a.work, lane); li < nl; li = next_group(a.work, lane)) {
     const TreeLeaf Lf = a.leaves[li];
     const int32_t t_lo = Lf.start, n_t = a.leaves[li + 1].start - Lf.start;
     const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, Lf.cell)];
@@ -387,7 +427,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           if (valid && e < cnt) {
             const uint32_t je = lje[e * 32 + lane];
             const int32_t j = unpack_j(je);
-            want = want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side);
+            want = !atcap && want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side);
             rec = reverse_rec(j, ti, unpack_s(je));
           }
           emit_warp(a, want, rec, lane);
@@ -407,7 +447,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
                 const uint32_t je = sidx[k];
                 const int32_t j = unpack_j(je);
                 tdens_pair(dx, dy, dz, vi, a.vel4[j], pj.w, H, Hinv, s);
-                want = want_reverse(a, ti, j, r2, H2, H, g.side);
+                want = !atcap && want_reverse(a, ti, j, r2, H2, H, g.side);
                 rec = reverse_rec(j, ti, unpack_s(je));
               }
             }
@@ -420,7 +460,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       // 4. publish the list (16-byte vectors) for the force loop
       if (valid) {
         const int64_t col = (int64_t)ti * kTreeTpp + sub;
-        a.list_cnt[col] = (uint16_t)(direct ? 0xffff : cnt);
+        a.list_cnt[col] = (uint16_t)(atcap ? kListFallback : (direct ? kListNone : cnt));
         if (!direct) {
           uint4* dst = reinterpret_cast<uint4*>(a.lists + col * kTreeListRegion);
           for (int e = 0; e < cnt; e += 4)
@@ -429,27 +469,14 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         }
       }
       if (valid && sub == 0) {
-        const int32_t p = a.perm[ti];
-        const float H2inv = Hinv * Hinv;
-        const float rho = s.mw * H2inv * Hinv;
-        const float fval = 1.0f / (1.0f - s.mdw / (3.0f * s.mw));
-        const float div = s.div * H2inv / s.mw;
-        const float curl = sqrtf(fmaf(s.cx, s.cx, fmaf(s.cy, s.cy, s.cz * s.cz))) * H2inv / s.mw;
-        const float P = (ph.gamma - 1.0f) * vi.w * rho;
-        const float cs = sqrtf(ph.gamma * P / rho);
-        const float hf = (float)h;
-        a.h[p] = hf;
-        a.rho[p] = rho;
-        a.f[p] = fval;
-        a.div_v[p] = div;
-        a.curl_v[p] = curl;
-        a.P[p] = P;
-        a.c[p] = cs;
-        a.B[p] = fabsf(div) / (fabsf(div) + curl + ph.eps_balsara * cs / hf);
-        if (a.n_iter) a.n_iter[p] = passes;
-        if (atcap) atomicOr(a.status, SPH_ST_REBUILD);
-        else if (!conv) atomicOr(a.status, SPH_ST_H_NOCONV);
-        pair_acc += (unsigned long long)s.npair;
+        tdens_write(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
+        if (atcap) {
+          // the support outgrew this level: re-solved at a coarser one
+          const int32_t k = atomicAdd(a.fb_count, 1);
+          if (k < a.n_total) a.fb_list[k] = ti;
+        } else {
+          pair_acc += (unsigned long long)s.npair;
+        }
       }
       __syncwarp();
     }
@@ -536,7 +563,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
   const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
   const int32_t nl = *a.n_leaves;
   unsigned long long pair_acc = 0;
-  for (int32_t li = blockIdx.x * kTWarps + warp; li < nl; li += gridDim.x * kTWarps) {
+  for (int32_t li = next_group(a.work, lane); li < nl; li = next_group(a.work, lane)) {
     const TreeLeaf Lf = a.leaves[li];
     const int32_t t_lo = Lf.start, n_t = a.leaves[li + 1].start - Lf.start;
     const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, Lf.cell)];
@@ -547,7 +574,10 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
       TFSums s;
       s.ax = s.ay = s.az = s.du = s.vsig = 0.f;
       s.npair = 0;
-      if (valid) {
+      const int64_t col = (int64_t)ti * kTreeTpp + sub;
+      const int lc = (int)a.list_cnt[col];
+      const bool fb = lc == kListFallback;  // written by k_tree_force_fb
+      if (valid && !fb) {
         const float4 reli = a.rel[ti];
         const int4 fi = a.fine[ti];
         const float3 pi = rel_to(g, reli, fi, kNoShift);
@@ -555,9 +585,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
         const float4 ci = a.fC[ti];
         const float2 di = a.fD[ti];
         const float Hi = a.fA[ti].w;
-        const int64_t col = (int64_t)ti * kTreeTpp + sub;
-        const int lc = (int)a.list_cnt[col];
-        const bool direct = lc == 0xffff;
+        const bool direct = lc == kListNone;
         // own reach: the list radius, or the leaf side on the list-free path
         const float C = direct ? g.side : a.lrad[ti];
         const float C2 = C * C;
@@ -609,7 +637,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
       s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, 2));
       s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 1);
       s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 2);
-      if (valid && sub == 0) {
+      if (valid && !fb && sub == 0) {
         const int32_t p = a.perm[ti];
         a.ax[p] = s.ax;
         a.ay[p] = s.ay;
@@ -628,6 +656,225 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
   }
 }
 
+// ---- fallback: targets whose support outgrew the cells of their level ------
+//
+// One warp per queued target, all 32 lanes over its candidates: the 27 cells
+// one level coarser (twice the side) around it, then coarser still while the
+// solve keeps hitting the cap.  A target that needs more than its top cell
+// sets SPH_ST_REBUILD: the top grid itself is too fine.
+
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int wsumi(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The 27 ranges of cell L (lanes 0..26) as a TRanges record.
+__device__ __forceinline__ TRanges cell_ranges(const GridDev& G, const TreeLeaf& L,
+                                               const uint64_t* __restrict__ skey,
+                                               const int32_t* __restrict__ cell_start, int lane) {
+  TRanges R;
+  int32_t len = 0;
+  R.lo = 0;
+  R.sc = kNoShift;
+  if (lane < 27) {
+    const TreeRange t = neighbour_range(G, L, lane, skey, cell_start);
+    R.lo = t.lo;
+    len = t.hi - t.lo;
+    R.sc = t.shift;
+  }
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  R.cum = incl - len;
+  R.nsrc = __shfl_sync(0xffffffffu, incl, 31);
+  return R;
+}
+
+__global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDensityArgs a, PhysDev ph) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = tsm + (size_t)warp * kTWarpSmem;
+  float4* spos = reinterpret_cast<float4*>(base);
+  uint32_t* sidx = reinterpret_cast<uint32_t*>(spos + kTCap);
+  const int32_t nq = min(*a.fb_count, (int32_t)a.n_total);
+  unsigned long long pair_acc = 0;
+  for (int32_t q = next_group(a.fb_work, lane); q < nq; q = next_group(a.fb_work, lane)) {
+    const int32_t ti = a.fb_list[q];
+    const uint64_t key = a.skey[ti];
+    const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30))];
+    const float4 reli = a.rel[ti];
+    const int4 fi = a.fine[ti];
+    const float4 vi = a.vel4[ti];
+    double h = (double)a.h[a.perm[ti]];  // the capped h of the first solve
+    bool conv = false, atcap = true;
+    int passes = 0, d = (int)a.level[ti] - 1;
+    if (d < 0) {
+      // already at its top cell: the caller rebuilds the top grid; the first
+      // solve's (capped) outputs stand
+      if (lane == 0) {
+        atomicOr(a.status, SPH_ST_REBUILD);
+        a.fb_level[ti] = 0;
+      }
+      __syncwarp();
+      continue;
+    }
+    TGeo g;
+    TRanges R;
+    float3 pi;
+    bool one_chunk = true;
+    for (; d >= 0; --d) {
+      const TreeLeaf Lc = cell_at_depth(key, d);
+      g = leaf_geo(Lc, G);
+      R = cell_ranges(G, Lc, a.skey, a.cell_start, lane);
+      pi = rel_to(g, reli, fi, kNoShift);
+      const double hcap = fmin(g.side_d, 0.5 * g.L) * (1.0 - 1e-5) / kGammaKd;
+      one_chunk = R.nsrc <= kTCap;
+      if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx);
+      double hlo = 0.0, hhi = INFINITY;
+      int it = 0;
+      if (h > hcap) h = hcap;
+      bool done = false;
+      while (!done) {  // warp-uniform: every lane holds the same reduced sums
+        const float H = kGammaK * (float)h;
+        const float Hinv = 1.0f / H;
+        float Sw = 0.f, Sdw = 0.f;
+        for (int v0 = 0; v0 < R.nsrc; v0 += kTCap) {
+          const int c = one_chunk ? R.nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
+          for (int k = lane; k < c; k += 32) tnewton_pair(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
+          if (!one_chunk) __syncwarp();
+        }
+        Sw = wsum(Sw);
+        Sdw = wsum(Sdw);
+        ++passes;
+        done = tnewton(Sw, Sdw, h, hlo, hhi, it, hcap, ph, atcap, conv);
+      }
+      if (!atcap) break;
+    }
+    if (d < 0) {
+      // even the top cell is too small: the caller rebuilds the top grid
+      if (lane == 0) atomicOr(a.status, SPH_ST_REBUILD);
+      d = 0;
+    }
+    // final pass at h, reverse pairs of this target
+    const float H = kGammaK * (float)h;
+    const float Hinv = 1.0f / H;
+    const float H2 = H * H;
+    TDSums s;
+    tds_zero(s);
+    for (int v0 = 0; v0 < R.nsrc; v0 += kTCap) {
+      const int c = one_chunk ? R.nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
+      for (int k0 = 0; k0 < c; k0 += 32) {
+        const int k = k0 + lane;
+        bool want = false;
+        uint64_t rec = 0;
+        if (k < c) {
+          const float4 pj = spos[k];
+          const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 < H2) {
+            const uint32_t je = sidx[k];
+            const int32_t j = unpack_j(je);
+            tdens_pair(dx, dy, dz, vi, a.vel4[j], pj.w, H, Hinv, s);
+            want = want_reverse(a, ti, j, r2, H2, H, g.side);
+            rec = reverse_rec(j, ti, unpack_s(je));
+          }
+        }
+        emit_warp(a, want, rec, lane);
+      }
+      if (!one_chunk) __syncwarp();
+    }
+    s.w = wsum(s.w);
+    s.dw = wsum(s.dw);
+    s.mw = wsum(s.mw);
+    s.mdw = wsum(s.mdw);
+    s.div = wsum(s.div);
+    s.cx = wsum(s.cx);
+    s.cy = wsum(s.cy);
+    s.cz = wsum(s.cz);
+    s.npair = wsumi(s.npair);
+    if (lane == 0) {
+      tdens_write(a, ph, ti, h, s, vi.w, passes, !conv);
+      a.fb_level[ti] = (int8_t)d;
+      pair_acc += (unsigned long long)s.npair;
+    }
+    __syncwarp();
+  }
+  if (ph.count_pairs && lane == 0 && pair_acc) atomicAdd(a.pairs, pair_acc);
+}
+
+__global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceArgs a, PhysDev ph) {
+  const int lane = threadIdx.x & 31;
+  const int32_t nq = min(*a.fb_count, (int32_t)a.n_total);
+  unsigned long long pair_acc = 0;
+  for (int32_t q = next_group(a.fb_work, lane); q < nq; q = next_group(a.fb_work, lane)) {
+    const int32_t ti = a.fb_list[q];
+    const uint64_t key = a.skey[ti];
+    const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30))];
+    const TreeLeaf Lc = cell_at_depth(key, (int)a.fb_level[ti]);
+    const TGeo g = leaf_geo(Lc, G);
+    const float4 reli = a.rel[ti];
+    const float3 pi = rel_to(g, reli, a.fine[ti], kNoShift);
+    const float4 vi = a.fB[ti];
+    const float4 ci = a.fC[ti];
+    const float2 di = a.fD[ti];
+    const float Hi = a.fA[ti].w;
+    const float C2 = g.side * g.side;  // own reach: the cell of the fallback level
+    TFSums s;
+    s.ax = s.ay = s.az = s.du = s.vsig = 0.f;
+    s.npair = 0;
+    for (int r = 0; r < 27; ++r) {
+      const TreeRange Rg = neighbour_range(G, Lc, r, a.skey, a.cell_start);
+      for (int32_t j = Rg.lo + lane; j < Rg.hi; j += 32) {
+        if (j == ti) continue;
+        const float3 pj = rel_to(g, a.rel[j], a.fine[j], Rg.shift);
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2) {
+          const float2 dj = a.fD[j];
+          tforce_pair(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
+        }
+      }
+    }
+    const int32_t r0 = a.rev_start[ti], r1 = a.rev_start[ti + 1];
+    for (int32_t k = r0 + lane; k < r1; k += 32) {
+      const uint32_t je = a.rev[k];
+      const int32_t j = unpack_j(je);
+      const float3 pj = rel_to(g, a.rel[j], a.fine[j], unpack_s(je));
+      const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2) {
+        const float2 dj = a.fD[j];
+        tforce_pair(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
+      }
+    }
+    s.ax = wsum(s.ax);
+    s.ay = wsum(s.ay);
+    s.az = wsum(s.az);
+    s.du = wsum(s.du);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, o));
+    s.npair = wsumi(s.npair);
+    if (lane == 0) {
+      const int32_t p = a.perm[ti];
+      a.ax[p] = s.ax;
+      a.ay[p] = s.ay;
+      a.az[p] = s.az;
+      a.du_dt[p] = s.du;
+      a.v_sig[p] = s.vsig;
+      pair_acc += (unsigned long long)s.npair;
+    }
+  }
+  if (ph.count_pairs && lane == 0 && pair_acc) atomicAdd(a.pairs, pair_acc);
+}
+
 }  // namespace sphk
 
 namespace sphh {
@@ -643,6 +890,8 @@ cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cud
   if (!bps) {
     cudaError_t e = cudaFuncSetAttribute(k_tree_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTDensSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tree_density_fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTDensSmem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_density, kTWarps * 32, kTDensSmem);
     if (e != cudaSuccess) return e;
@@ -650,11 +899,15 @@ cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cud
   }
   const int64_t n = a.n_total;
   cudaError_t e = cudaMemsetAsync(a.rev_count, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.fb_count, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.fb_work, 0, sizeof(int32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.rev_start, 0, sizeof(int32_t) * (n + 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.rev_fill, 0, sizeof(int32_t) * (n > 0 ? n : 1), st);
   if (e != cudaSuccess) return e;
   if (n <= 0) return cudaSuccess;
   k_tree_density<<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
+  k_tree_density_fb<<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
   e = scan_exclusive_host_n(a.rev_start, n + 1, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
   k_rev_scatter<<<a.num_sms * 4, 256, 0, st>>>(a.rev_raw, a.rev_count, a.rev_cap, a.rev_start, a.rev_fill, a.rev);
@@ -669,7 +922,11 @@ cudaError_t launch_tree_force(const TreeForceArgs& a, const PhysDev& ph, cudaStr
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
   }
+  cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.fb_work, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
   k_tree_force<<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
+  k_tree_force_fb<<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
   return cudaGetLastError();
 }
 

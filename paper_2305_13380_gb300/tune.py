@@ -1,19 +1,30 @@
-"""Autotuning of the cell size (the cell margin over the largest support).
+"""Autotuning of the cell geometry of a pool: grid mode (uniform cells or
+nested grids), cell margin over the largest support, and the leaf size n_leaf
+of the nested grids.
 
 Larger cells stage more candidates per target; smaller ones leave less room
-for smoothing lengths to grow before a rebuild is needed.  The tuner times a
-few pool steps for each candidate margin and keeps the fastest; results are
-cached in a JSON file keyed by GPU name and workload key."""
+for smoothing lengths to grow before a rebuild is needed; nested grids cost a
+second sort but keep every target's neighbour cells near its own support.
+The tuner times a few pool steps for each candidate and keeps the fastest;
+results are cached in a JSON file keyed by GPU name and workload key.
+
+Uniform cells are only tried when every simulation's starting smoothing
+lengths span less than SPREAD_UNIFORM: on strongly clustered inputs a cell
+sized by the widest particle holds thousands of the densest ones, and a single
+step takes seconds."""
 from __future__ import annotations
 
 import json
 import os
 
+import numpy as np
 import torch
 
 from . import pool, sph
 
-CANDIDATES = (0.03, 0.05, 0.1, 0.2)
+MARGINS = (0.03, 0.05, 0.1, 0.2)
+LEAVES = (8, 16, 32)
+SPREAD_UNIFORM = 8.0
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_cache.json")
 
 
@@ -24,35 +35,56 @@ def _load():
         return {}
 
 
-def best_margin(sims, key: str, steps: int = 3, candidates=CANDIDATES) -> float:
+def candidates(sims) -> list[dict]:
+    """Parameter overrides to try, nested grids first."""
+    out = [dict(flags=sph.SPH_FLAG_TREE, cell_margin=m, n_leaf=k) for m in MARGINS for k in LEAVES]
+    spread = max(float(np.max(s["h0"]) / np.min(s["h0"])) for s in sims)
+    if spread < SPREAD_UNIFORM:
+        out += [dict(flags=0, cell_margin=m) for m in MARGINS]
+    return out
+
+
+def _time(sims, over: dict, steps: int, give_up_ms: float) -> float | None:
+    P = pool.Pool(sims, sph.sph_default_params(**over))
+    try:
+        P.start()
+    except sph.SPHError:
+        return None  # these cells cannot hold the supports of some simulation
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(P.stream)
+    P.step()
+    e1.record(P.stream)
+    P.stream.synchronize()
+    first = e0.elapsed_time(e1)
+    if P.status() or first > give_up_ms:
+        return None
+    e0.record(P.stream)
+    for _ in range(steps):
+        P.step()
+    e1.record(P.stream)
+    P.stream.synchronize()
+    if P.status():
+        return None
+    return e0.elapsed_time(e1) / steps
+
+
+def best_params(sims, key: str, steps: int = 3) -> dict:
+    """The fastest parameter overrides (flags, cell_margin, n_leaf) for a pool
+    of `sims`, from the cache when this GPU has seen `key`."""
     name = torch.cuda.get_device_name()
     cache = _load()
     ck = f"{name}|{key}"
     if ck in cache:
-        return float(cache[ck])
-    best, best_ms = candidates[0], float("inf")
-    for m in candidates:
-        P = pool.Pool(sims, sph.sph_default_params(cell_margin=m))
-        try:
-            P.start()
-        except sph.SPHError:
-            continue  # this margin cannot hold the supports of some simulation
-        P.step()
-        P.stream.synchronize()
-        if P.status():
-            continue
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(P.stream)
-        for _ in range(steps):
-            P.step()
-        e1.record(P.stream)
-        P.stream.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        if P.status() == 0 and ms < best_ms:
-            best, best_ms = m, ms
-        del P
+        return dict(cache[ck])
+    best, best_ms = None, float("inf")
+    for over in candidates(sims):
+        ms = _time(sims, over, steps, give_up_ms=4.0 * best_ms)
+        if ms is not None and ms < best_ms:
+            best, best_ms = over, ms
+    if best is None:
+        raise RuntimeError("no candidate cell geometry ran without a device status")
     cache[ck] = best
     os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
     with open(_CACHE, "w") as f:
         json.dump(cache, f, indent=1)
-    return best
+    return dict(best)

@@ -147,3 +147,33 @@ def test_tree_step_matches_oracle(orc):
     for k in ("ax", "ay", "az"):
         assert np.abs(g[k] - s[k]).max() < 1e-4 * arms
     torch.cuda.synchronize()
+
+
+def test_tree_coarser_level_fallback(orc):
+    # starting guesses half the converged h for a third of the particles put
+    # them at levels whose cells are too small for their support; they are
+    # re-solved one or more levels coarser inside the same call, so no
+    # rebuild is needed and the results still match the oracle
+    # (the top cells are sized by the converged h, so only levels below them
+    # are too small)
+    p = inputs.clustered(6000, n_spheres=4, seed=9)
+    q = as_f32(p)
+    h_conv = orc.density(q, q["h0"])["h"]
+    rng = np.random.default_rng(11)
+    h_start = (np.where(rng.random(len(p["x"])) < 0.33, 0.5, 1.0) * h_conv).astype(np.float32)
+    g = run_gpu(p, tree=True, h_start=h_start)
+    assert g["rebuilds"] == 0
+    od, of = orc.density_force(q, h_start.astype(np.float64))
+    compare(g, od, of)
+
+
+def test_tree_rebuild_when_top_cells_too_small(orc):
+    # every starting guess too small: the top grid itself is too fine, which
+    # only a rebuild of the top cells fixes
+    p = inputs.lattice(12, seed=4)
+    p["h0"] = p["h0"] * 0.5
+    q = as_f32(p)
+    g = run_gpu(p, tree=True)
+    assert g["rebuilds"] >= 1
+    od, of = orc.density_force(q, q["h0"])
+    compare(g, od, of)
