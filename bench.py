@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lattice128")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--served-seconds", type=float, default=6.0,
+                    help="length of the served request trace at half the saturated rate")
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -325,6 +327,81 @@ def run_batch(args, world: int, rank: int, local: int):
         print(json.dumps(line))
 
 
+def run_served(args, world: int, rank: int, local: int):
+    """Served workload: live simulations of two colliding spheres (radii
+    0.1-0.3, 10^3-5x10^5 particles log-uniform, relative speed 0.5-2) resident
+    on the device; step requests arrive as a Poisson process and are served
+    with continuous batching (several batches in flight on their own streams).
+    The offered rate is half the saturated throughput measured first.  The same
+    trace is then served one simulation per launch for comparison."""
+    import numpy as np
+    import torch
+
+    from paper_2305_13380_gb300 import build as B
+    B.build()
+    from paper_2305_13380_gb300 import inputs, serve, sph
+
+    n_sims = int(args.workload[len("served"):] or 1000)
+    t_gen = time.perf_counter()
+    sims = {s: inputs.two_spheres(seed=s) for s in range(n_sims)}
+    gen_s = time.perf_counter() - t_gen
+    total = sum(len(p["x"]) for p in sims.values())
+    largest = max(len(p["x"]) for p in sims.values())
+    slots = 3
+    batch_cap = max(4 * largest, 4 << 20)
+    budget = total * serve.STATE_BYTES + slots * batch_cap * (serve.STATE_BYTES + serve.SCRATCH_BYTES)
+    prm = sph.sph_default_params(flags=sph.SPH_FLAG_TREE)
+    srv = serve.Server(budget, store_particles=total, slots=slots, batch_particles=batch_cap,
+                       params=prm)
+    t_adm = time.perf_counter()
+    for s, p in sims.items():
+        srv.admit(s, p)
+    adm_s = time.perf_counter() - t_adm
+    del sims
+    ids = list(srv.sims)
+    # saturation: every request present at t = 0
+    sat = srv.run(serve.poisson_trace(3 * slots * 32, rate=1e9, sims=ids, seed=1))
+    cap_rate = sat["requests"] / sat["wall_s"]
+    rate = 0.5 * cap_rate
+    n_req = max(200, int(rate * args.served_seconds))
+    trace = serve.poisson_trace(n_req, rate=rate, sims=ids, seed=2)
+    srv.finished, srv.n_batches, srv.updates = [], 0, 0
+    clocks = Clocks(None)
+    time.sleep(0.25)
+    out = srv.run(trace)
+    clk = clocks.stop()
+    # the same trace, one simulation per launch on one stream
+    srv.finished, srv.n_batches, srv.updates = [], 0, 0
+    all_slots, srv.slots = srv.slots, srv.slots[:1]
+    srv.max_batch_sims = 1
+    plain = srv.run(trace)
+    srv.slots = all_slots
+    line = {
+        "metric": f"served SPH step latency p50/p99 ({n_sims} live simulations)",
+        "value": out["p50_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": world,
+        "steps": out["requests"], "warmup": sat["requests"], "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "simulations": n_sims, "particles_resident": total,
+                   "desc": "two uniform spheres per simulation, radii 0.1-0.3, N log-uniform in "
+                           "[1e3, 5e5], relative speed 0.5-2, box 2; Poisson step requests",
+                   "rate_per_s": rate, "slots": slots, "batch_particles": batch_cap,
+                   "budget_gb": budget / 1e9, "generation_s": gen_s, "admission_s": adm_s,
+                   "grid": "nested"},
+        "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "mean_ms": out["mean_ms"],
+        "requests_per_s": out["requests"] / out["wall_s"],
+        "particle_updates_per_s": out["particle_updates_per_s"],
+        "mean_sims_per_batch": out["mean_sims_per_batch"],
+        "saturated_requests_per_s": cap_rate,
+        "plain": {"p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"],
+                  "particle_updates_per_s": plain["particle_updates_per_s"],
+                  "wall_s": plain["wall_s"]},
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"], "samples": clk["samples"]},
+        "device_status": out["device_status"] | plain["device_status"],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -340,6 +417,8 @@ def main():
     torch.cuda.set_device(local)
     if args.workload.startswith("batch"):
         return run_batch(args, world, rank, local)
+    if args.workload.startswith("served"):
+        return run_served(args, world, rank, local)
     if world > 1:
         dist.init_process_group("nccl")
     from paper_2305_13380_gb300 import build as B

@@ -204,6 +204,14 @@ int sph_status(sph_ctx* ctx, int32_t* status_out);
 int sph_build_cells(sph_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
                     const float* h, sph_cells* out);
 
+/* Allocates the context's scratch for up to n_total particles in up to
+ * n_sims simulations (and the nested-grid scratch with SPH_FLAG_TREE), so that
+ * later calls of that size allocate nothing: use it before capturing a CUDA
+ * graph or before serving requests whose latency matters.  Waits for the
+ * stream when it has to reallocate.  The paper has no counterpart (a
+ * deployment aid). */
+int sph_reserve(sph_ctx* ctx, int64_t n_total, int32_t n_sims);
+
 /* Waits for the stream and fills out->n_c from the device. */
 int sph_cells_sync(sph_ctx* ctx, sph_cells* cells);
 
@@ -217,8 +225,9 @@ int sph_cells_copy(sph_ctx* ctx, sph_cells* cells, int32_t* cell_start_dst, int3
  * Newton-Raphson on n_hat(h) - (eta/h)^3, using dn_hat/dh, until the relative
  * correction is below h_tol (the last correction is applied, and the outputs
  * are evaluated at that final h); H is capped at the cell size (a particle that would
- * need more sets SPH_ST_REBUILD: rebuild the cells from out->h and call
- * again).  Sums are accumulated in FP32 on coordinates relative to the
+ * need more sets SPH_ST_REBUILD and returns twice its capped h in out->h:
+ * rebuild the cells from out->h and call again, which at least doubles the
+ * cells that particle needs).  Sums are accumulated in FP32 on coordinates relative to the
  * particle's cell; the convergence test runs in FP64.  With SPH_FLAG_TREE the
  * cell is the particle's leaf, and coordinates are relative to the leaf with
  * an exact integer part (1/1024 of a top cell), so precision follows the

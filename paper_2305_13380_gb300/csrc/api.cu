@@ -751,6 +751,13 @@ int sph_build_cells(sph_ctx* c, int64_t n, const double* x, const double* y, con
   return rc;
 }
 
+int sph_reserve(sph_ctx* c, int64_t n_total, int32_t n_sims) {
+  if (!c || n_total < 0 || n_total > INT32_MAX / 16 || n_sims < 1) return SPH_E_INVAL;
+  int rc = ensure(c, n_total, n_sims);
+  if (rc == SPH_OK && (c->p.flags & SPH_FLAG_TREE)) rc = ensure_tree(c, n_total, 0);
+  return rc;
+}
+
 int sph_cells_sync(sph_ctx* c, sph_cells* cells) {
   if (!c || !cells || !cells->n_c_dev) return SPH_E_INVAL;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;

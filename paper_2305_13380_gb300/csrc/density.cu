@@ -148,7 +148,9 @@ __device__ __forceinline__ void dens_write(const sphh::DensityArgs& a, const Phy
   const float cs = sqrtf(ph.gamma * P / rho);
   const float hf = (float)h;
   const float B_i = fabsf(div) / (fabsf(div) + curl + ph.eps_balsara * cs / hf);
-  a.h[p] = hf;
+  // a support that outgrew its cell: twice the cap is the next starting guess,
+  // so that each rebuild at least doubles the cells it needs
+  a.h[p] = atcap ? 2.0f * hf : hf;
   a.rho[p] = rho;
   a.f[p] = fi;
   a.div_v[p] = div;

@@ -719,11 +719,12 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     bool conv = false, atcap = true;
     int passes = 0, d = (int)a.level[ti] - 1;
     if (d < 0) {
-      // already at its top cell: the caller rebuilds the top grid; the first
-      // solve's (capped) outputs stand
+      // already at its top cell: the caller rebuilds the top grid from twice
+      // the capped h; the first solve's other outputs stand
       if (lane == 0) {
         atomicOr(a.status, SPH_ST_REBUILD);
         a.fb_level[ti] = 0;
+        a.h[a.perm[ti]] = 2.0f * (float)h;
       }
       __syncwarp();
       continue;
@@ -803,7 +804,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     s.cz = wsum(s.cz);
     s.npair = wsumi(s.npair);
     if (lane == 0) {
-      tdens_write(a, ph, ti, h, s, vi.w, passes, !conv);
+      tdens_write(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
+      if (atcap) a.h[a.perm[ti]] = 2.0f * (float)h;  // next starting guess
       a.fb_level[ti] = (int8_t)d;
       pair_acc += (unsigned long long)s.npair;
     }

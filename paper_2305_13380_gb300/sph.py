@@ -118,10 +118,11 @@ def lib():
         L.sph_kernel_times.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.sph_build_cells_static.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_double, C.c_double,
                                              _P, C.c_int64, _P, _P, _P, _P]
+        L.sph_reserve.argtypes = [_P, C.c_int64, C.c_int32]
         for f in ("sph_create", "sph_status", "sph_build_cells", "sph_cells_sync", "sph_cells_copy",
                   "sph_density",
                   "sph_force", "sph_step", "sph_conservation", "sph_pair_counts",
-                  "sph_kernel_times", "sph_build_cells_static"):
+                  "sph_kernel_times", "sph_build_cells_static", "sph_reserve"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -266,6 +267,12 @@ def pool(sim_offset, box_size, arrays: dict) -> sph_pool:
                  _ptr(box_size, torch.float64), *vals, _ptr(arrays.get("n_iter"), torch.int32))
     s._keep = (sim_offset, box_size, arrays)
     return s
+
+
+def sph_reserve(ctx: Context, n_total: int, n_sims: int = 1):
+    """Allocates the context's scratch for n_total particles in n_sims
+    simulations up front."""
+    _check(lib().sph_reserve(ctx.handle, C.c_int64(n_total), C.c_int32(n_sims)), "sph_reserve")
 
 
 def sph_step(ctx: Context, pl: sph_pool):

@@ -129,7 +129,9 @@ def compare(g, od, of, idx=None, cell=None, vmax=None):
         ref = od[k_o]
         scale = np.sqrt(np.mean(ref ** 2)) + 1e-300
         err = np.abs(sel(g[k_g]) - ref)
-        lim = TOL["divcurl"] * scale + floor * 5.6 * 2 * vm / H
+        # the h-error term: the gradient sums scale as H^-5 through the
+        # kernel gradient, so a relative h error d moves them by ~5 d
+        lim = TOL["divcurl"] * scale + 5 * TOL["h"] * np.abs(ref) + floor * 5.6 * 2 * vm / H
         dvc[k_g] = lim
         e = (err / lim).max()
         report[k_g] = err.max() / scale
