@@ -502,6 +502,7 @@ def main():
     arrays["n_iter"] = torch.zeros(n, dtype=torch.int32, device=dev)
     sph.sph_step(cnt, sph.pool(sim_offset, box, arrays))
     pairs_d, pairs_f = sph.sph_pair_counts(cnt)
+    tree_counts = sph.sph_tree_counts(cnt) if tree else None
     mean_pass = float(arrays.pop("n_iter").double().mean().item())
     cnt.close()
 
@@ -570,6 +571,7 @@ def main():
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "pairs_per_step": {"density_final_pass": pairs_d, "force": pairs_f,
                            "mean_newton_passes": mean_pass},
+        "nested_grids": tree_counts,
         "device_status": st,
         "wall_s": wall,
     }

@@ -266,6 +266,13 @@ int sph_kernel_times(sph_ctx* ctx, double* ms_out, int64_t* calls_out);
  * out[1] = force pairs r < max(H_i, H_j), j != i. */
 int sph_pair_counts(sph_ctx* ctx, int64_t* out);
 
+/* Diagnostics of the last nested-grid build and density (SPH_FLAG_TREE; waits
+ * for the stream): out[0] = target groups, out[1] = targets summed without a
+ * neighbour list (needs SPH_FLAG_COUNT_PAIRS, else 0), out[2] = reverse pairs
+ * emitted, out[3] = targets re-solved at a coarser level.  All zero without
+ * nested grids. */
+int sph_tree_counts(sph_ctx* ctx, int64_t* out);
+
 /* Cell build for callers that cannot allocate device memory (code running in
  * another framework's memory arena, loops whose allocator must not
  * synchronise the device, plugins that are only handed buffers).  The paper

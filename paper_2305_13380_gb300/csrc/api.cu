@@ -207,7 +207,8 @@ int ensure(sph_ctx* c, int64_t n, int n_sims) {
             dalloc(c->overflow, cc / 3 + 2) && dalloc(c->pos4, cn) &&
             dalloc(c->vel4, cn) && dalloc(c->th4, cn) && dalloc(c->hs, cn) && dalloc(c->fD, cn) &&
             dalloc(c->dt_bits, cs) && dalloc(c->hmax_bits, cs) &&
-            dalloc(c->lists, (int64_t)sphk::kListRegion * 4 * cn) && dalloc(c->list_cnt, 4 * cn) &&
+            dalloc(c->lists, (int64_t)sphk::kListRegion * 4 * cn) &&
+            dalloc(c->list_cnt, (int64_t)(sphk::kTreeTpp > 4 ? sphk::kTreeTpp : 4) * cn) &&
             dalloc(c->vpx, cn) && dalloc(c->vpy, cn) && dalloc(c->vpz, cn) && dalloc(c->up, cn);
   if (!ok) {
     free_grown(c);
@@ -413,9 +414,11 @@ int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* 
   t_begin(c, SPH_T_GATHER);
   if (sphh::launch_tree_gather(g, c->st) != cudaSuccess) return SPH_E_CUDA;
   t_end(c, SPH_T_GATHER);
-  if (c->p.flags & SPH_FLAG_COUNT_PAIRS)
-    if (cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
+  if (c->p.flags & SPH_FLAG_COUNT_PAIRS) {
+    if (cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->st) != cudaSuccess ||
+        cudaMemsetAsync(c->pairs + 2, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
       return SPH_E_CUDA;
+  }
   sphh::TreeDensityArgs d;
   d.n_sims = c->built_sims;
   d.num_sms = c->num_sms;
@@ -460,6 +463,7 @@ int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* 
   d.fb_count = c->misc + sphk::kTreeFbCount;
   d.fb_level = c->fb_level;
   d.fb_work = c->misc + sphk::kTreeFbWork;
+  d.list_free = c->pairs + 2;
   t_begin(c, SPH_T_DENSITY);
   const cudaError_t e = sphh::launch_tree_density(d, phys_of(c->p), c->st);
   t_end(c, SPH_T_DENSITY);
@@ -666,12 +670,12 @@ int sph_create(sph_ctx** out, const sph_params* p, void* stream) {
     delete c;
     return SPH_E_CUDA;
   }
-  bool ok = dalloc(c->misc, sphk::kMiscWords) && dalloc(c->pairs, 2) && dalloc(c->off1, 2) &&
+  bool ok = dalloc(c->misc, sphk::kMiscWords) && dalloc(c->pairs, 4) && dalloc(c->off1, 2) &&
             dalloc(c->box1, 1);
   if (ok) ok = cudaMallocHost((void**)&c->h_off1, 2 * sizeof(int64_t)) == cudaSuccess &&
                cudaMallocHost((void**)&c->h_box1, sizeof(double)) == cudaSuccess;
   if (ok) ok = cudaMemsetAsync(c->misc, 0, sphk::kMiscWords * sizeof(int32_t), c->st) == cudaSuccess &&
-               cudaMemsetAsync(c->pairs, 0, 2 * sizeof(unsigned long long), c->st) == cudaSuccess;
+               cudaMemsetAsync(c->pairs, 0, 4 * sizeof(unsigned long long), c->st) == cudaSuccess;
   if (!ok) {
     sph_destroy(c);
     return SPH_E_NOMEM;
@@ -913,6 +917,25 @@ int sph_kernel_times(sph_ctx* c, double* ms_out, int64_t* calls_out) {
     c->t_ms[k] = 0.0;
     c->t_calls[k] = 0;
   }
+  return SPH_OK;
+}
+
+int sph_tree_counts(sph_ctx* c, int64_t* out) {
+  if (!c || !out) return SPH_E_INVAL;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  for (int k = 0; k < 4; ++k) out[k] = 0;
+  if (!c->built_tree) return SPH_OK;
+  int32_t groups = 0, fb = 0;
+  unsigned long long rev = 0, free_t = 0;
+  if (cudaMemcpy(&groups, c->n_leaves, sizeof(groups), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&fb, c->misc + sphk::kTreeFbCount, sizeof(fb), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&rev, c->rev_count, sizeof(rev), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&free_t, c->pairs + 2, sizeof(free_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SPH_E_CUDA;
+  out[0] = groups;
+  out[1] = (int64_t)free_t;
+  out[2] = (int64_t)rev;
+  out[3] = fb;
   return SPH_OK;
 }
 

@@ -194,6 +194,7 @@ struct TreeDensityArgs {
   int32_t *fb_list, *fb_count;  // n, 1
   int8_t* fb_level;            // n: level of the fallback solve
   int32_t* fb_work;            // 1
+  unsigned long long* list_free;  // 1: targets summed without a list (counted with pairs)
 };
 cudaError_t launch_tree_density(const TreeDensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 

@@ -34,7 +34,7 @@ struct TreeRange {
 // Tree loops: lanes per target, list entries kept per (target, lane), and the
 // list radius as a multiple of the starting support (a Newton step that
 // outgrows it sends the warp to the list-free path).
-constexpr int kTreeTpp = 4;
+constexpr int kTreeTpp = 8;
 constexpr int kTreeList = 32;
 constexpr int kTreeListRegion = 32;
 constexpr float kTreeListReach = 1.1f;

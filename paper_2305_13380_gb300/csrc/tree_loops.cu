@@ -193,22 +193,42 @@ __device__ __forceinline__ bool tnewton(float Sw, float Sdw, double& h, double& 
   return false;
 }
 
-__device__ __forceinline__ float sum4(float v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  return v + __shfl_xor_sync(0xffffffffu, v, 2);
+// Sum over the kTreeTpp lanes of a target (called by all 32 lanes).
+__device__ __forceinline__ float gsum(float v) {
+#pragma unroll
+  for (int o = 1; o < kTreeTpp; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int gsumi(int v) {
+#pragma unroll
+  for (int o = 1; o < kTreeTpp; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float gmax(float v) {
+#pragma unroll
+  for (int o = 1; o < kTreeTpp; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// True for every lane of a target if any of its lanes has b (called by all
+// 32 lanes).
+__device__ __forceinline__ bool group_any(bool b, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, b);
+  return ((m >> (lane & ~(kTreeTpp - 1))) & ((1u << kTreeTpp) - 1u)) != 0u;
 }
 
 __device__ __forceinline__ void tcombine(TDSums& s) {
-  s.w = sum4(s.w);
-  s.dw = sum4(s.dw);
-  s.mw = sum4(s.mw);
-  s.mdw = sum4(s.mdw);
-  s.div = sum4(s.div);
-  s.cx = sum4(s.cx);
-  s.cy = sum4(s.cy);
-  s.cz = sum4(s.cz);
-  s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 1);
-  s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 2);
+  s.w = gsum(s.w);
+  s.dw = gsum(s.dw);
+  s.mw = gsum(s.mw);
+  s.mdw = gsum(s.mdw);
+  s.div = gsum(s.div);
+  s.cx = gsum(s.cx);
+  s.cy = gsum(s.cy);
+  s.cz = gsum(s.cz);
+  s.npair = gsumi(s.npair);
 }
 
 // The leaf's 27 ranges, lane r < 27 holding range r; lanes 27..31 hold empty
@@ -335,7 +355,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
   uint32_t* lje = reinterpret_cast<uint32_t*>(lr2 + kTRows * 32);
   const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
   const int32_t nl = *a.n_leaves;
-  unsigned long long pair_acc = 0;
+  unsigned long long pair_acc = 0, free_acc = 0;
   for (int32_t li = next_group(a.work, lane); li < nl; li = next_group(a.work, lane)) {
     const TreeLeaf Lf = a.leaves[li];
     const int32_t t_lo = Lf.start, n_t = a.leaves[li + 1].start - Lf.start;
@@ -370,12 +390,19 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         }
         if (!one_chunk) __syncwarp();
       }
-      bool direct = __any_sync(0xffffffffu, cnt > kTreeList);
+      // a target whose list overflowed, or whose support outgrows R_i, sums
+      // over every staged source instead ("list-free"); the others keep
+      // their lists.  The flag is shared by the target's lanes.
+      bool mydirect = group_any(cnt > kTreeList, lane);
       // 2. Newton-Raphson passes
       double h = valid ? (double)a.hs[ti] : hcap;
       if (!(h > 0.0)) h = 0.5 * hcap;
       if (h > hcap) h = hcap;
-      if (!direct) direct = __any_sync(0xffffffffu, valid && kGammaK * (float)h > Ri);
+      {
+        // evaluated by every lane (a ballot), then merged
+        const bool outgrown = group_any(valid && kGammaK * (float)h > Ri, lane);
+        mydirect = mydirect || outgrown;
+      }
       double hlo = 0.0, hhi = INFINITY;
       bool done = !valid, atcap = false, conv = false;
       int it = 0, passes = 0;
@@ -383,25 +410,25 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         const float H = kGammaK * (float)h;
         const float Hinv = 1.0f / H;
         float Sw = 0.f, Sdw = 0.f;
-        if (!direct) {
-          const int m = done ? 0 : cnt;
-          for (int e = 0; e < m; ++e) tnewton_pair(lr2[e * 32 + lane], H, Hinv, Sw, Sdw);
-        } else {
+        if (!mydirect && !done)
+          for (int e = 0; e < cnt; ++e) tnewton_pair(lr2[e * 32 + lane], H, Hinv, Sw, Sdw);
+        if (__any_sync(0xffffffffu, mydirect && !done)) {
           for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
             const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
-            if (!done)
+            if (mydirect && !done)
               for (int k = sub; k < c; k += kTreeTpp) tnewton_pair(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
             if (!one_chunk) __syncwarp();
           }
         }
-        Sw = sum4(Sw);
-        Sdw = sum4(Sdw);
+        Sw = gsum(Sw);
+        Sdw = gsum(Sdw);
         if (!done) {
           passes = it + 1;
           if (tnewton(Sw, Sdw, h, hlo, hhi, it, hcap, ph, atcap, conv)) done = true;
         }
         // the list holds r < R_i: a support beyond it needs every staged source
-        if (!direct) direct = __any_sync(0xffffffffu, valid && kGammaK * (float)h > Ri);
+        const bool outgrown = group_any(valid && kGammaK * (float)h > Ri, lane);
+        mydirect = mydirect || outgrown;
       }
       // 3. final pass at h
       const float H = kGammaK * (float)h;
@@ -409,37 +436,25 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       const float H2 = H * H;
       TDSums s;
       tds_zero(s);
-      if (!direct) {
-        if (valid) {
-          for (int e = 0; e < cnt; ++e) {
-            const uint32_t je = lje[e * 32 + lane];
-            const int32_t j = unpack_j(je);
-            const float4 rj = a.rel[j];
-            const float3 d = pair_vec(g, reli, fi, rj, a.fine[j], unpack_s(je));
-            tdens_pair(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
-          }
+      if (valid && !mydirect) {
+        for (int e = 0; e < cnt; ++e) {
+          const uint32_t je = lje[e * 32 + lane];
+          const int32_t j = unpack_j(je);
+          const float4 rj = a.rel[j];
+          const float3 d = pair_vec(g, reli, fi, rj, a.fine[j], unpack_s(je));
+          tdens_pair(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
         }
-        // reverse pairs from the list (warp-uniform trip count)
-        const int emax = __reduce_max_sync(0xffffffffu, valid ? cnt : 0);
-        for (int e = 0; e < emax; ++e) {
-          bool want = false;
-          uint64_t rec = 0;
-          if (valid && e < cnt) {
-            const uint32_t je = lje[e * 32 + lane];
-            const int32_t j = unpack_j(je);
-            want = !atcap && want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side);
-            rec = reverse_rec(j, ti, unpack_s(je));
-          }
-          emit_warp(a, want, rec, lane);
-        }
-      } else {
+      }
+      // list-free targets: every staged source, reverse pairs on the way
+      // (warp-uniform trip counts around emit_warp)
+      if (__any_sync(0xffffffffu, valid && mydirect)) {
         for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
           const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
           for (int k0 = 0; k0 < c; k0 += kTreeTpp) {
             const int k = k0 + sub;
             bool want = false;
             uint64_t rec = 0;
-            if (valid && k < c) {
+            if (valid && mydirect && k < c) {
               const float4 pj = spos[k];
               const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
               const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -456,12 +471,25 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           if (!one_chunk) __syncwarp();
         }
       }
+      // reverse pairs from the lists (warp-uniform trip count)
+      const int emax = __reduce_max_sync(0xffffffffu, (valid && !mydirect) ? cnt : 0);
+      for (int e = 0; e < emax; ++e) {
+        bool want = false;
+        uint64_t rec = 0;
+        if (valid && !mydirect && e < cnt) {
+          const uint32_t je = lje[e * 32 + lane];
+          const int32_t j = unpack_j(je);
+          want = !atcap && want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side);
+          rec = reverse_rec(j, ti, unpack_s(je));
+        }
+        emit_warp(a, want, rec, lane);
+      }
       tcombine(s);
       // 4. publish the list (16-byte vectors) for the force loop
       if (valid) {
         const int64_t col = (int64_t)ti * kTreeTpp + sub;
-        a.list_cnt[col] = (uint16_t)(atcap ? kListFallback : (direct ? kListNone : cnt));
-        if (!direct) {
+        a.list_cnt[col] = (uint16_t)(atcap ? kListFallback : (mydirect ? kListNone : cnt));
+        if (!mydirect) {
           uint4* dst = reinterpret_cast<uint4*>(a.lists + col * kTreeListRegion);
           for (int e = 0; e < cnt; e += 4)
             dst[e >> 2] = make_uint4(lje[e * 32 + lane], lje[(e + 1) * 32 + lane], lje[(e + 2) * 32 + lane],
@@ -477,16 +505,21 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         } else {
           pair_acc += (unsigned long long)s.npair;
         }
+        free_acc += mydirect ? 1ull : 0ull;
       }
       __syncwarp();
     }
     __syncwarp();
   }
   if (ph.count_pairs) {
-    unsigned long long v = pair_acc;
+    unsigned long long v = pair_acc, w = free_acc;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      v += __shfl_xor_sync(0xffffffffu, v, o);
+      w += __shfl_xor_sync(0xffffffffu, w, o);
+    }
     if (lane == 0 && v) atomicAdd(a.pairs, v);
+    if (lane == 0 && w) atomicAdd(a.list_free, w);
   }
 }
 
@@ -629,14 +662,12 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
           }
         }
       }
-      s.ax = sum4(s.ax);
-      s.ay = sum4(s.ay);
-      s.az = sum4(s.az);
-      s.du = sum4(s.du);
-      s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, 1));
-      s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, 2));
-      s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 1);
-      s.npair += __shfl_xor_sync(0xffffffffu, s.npair, 2);
+      s.ax = gsum(s.ax);
+      s.ay = gsum(s.ay);
+      s.az = gsum(s.az);
+      s.du = gsum(s.du);
+      s.vsig = gmax(s.vsig);
+      s.npair = gsumi(s.npair);
       if (valid && !fb && sub == 0) {
         const int32_t p = a.perm[ti];
         a.ax[p] = s.ax;

@@ -43,10 +43,10 @@ STEPPED = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du_dt",
            "f", "div_v", "curl_v", "P", "c", "balsara")
 STATE_BYTES = 8 * len(F64) + 4 * len(F32)
 # context scratch per particle of an arena: cell keys and counts, sorted
-# copies and lists (~560 B) plus the nested grids' keys, orders, groups and
-# their ranges, copies, lists and reverse pairs (~1840 B), for 1.25 n + 64
-# particles of capacity; rounded up
-SCRATCH_BYTES = 3100
+# copies and lists (~570 B) plus the nested grids' keys, orders, groups and
+# their ranges, copies, lists (8 lanes x 32 entries) and reverse pairs
+# (~2350 B), for 1.25 n + 64 particles of capacity; rounded up
+SCRATCH_BYTES = 3700
 
 
 class Store:

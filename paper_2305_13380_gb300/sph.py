@@ -119,10 +119,11 @@ def lib():
         L.sph_build_cells_static.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_double, C.c_double,
                                              _P, C.c_int64, _P, _P, _P, _P]
         L.sph_reserve.argtypes = [_P, C.c_int64, C.c_int32]
+        L.sph_tree_counts.argtypes = [_P, C.POINTER(C.c_int64)]
         for f in ("sph_create", "sph_status", "sph_build_cells", "sph_cells_sync", "sph_cells_copy",
                   "sph_density",
                   "sph_force", "sph_step", "sph_conservation", "sph_pair_counts",
-                  "sph_kernel_times", "sph_build_cells_static", "sph_reserve"):
+                  "sph_kernel_times", "sph_build_cells_static", "sph_reserve", "sph_tree_counts"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -267,6 +268,14 @@ def pool(sim_offset, box_size, arrays: dict) -> sph_pool:
                  _ptr(box_size, torch.float64), *vals, _ptr(arrays.get("n_iter"), torch.int32))
     s._keep = (sim_offset, box_size, arrays)
     return s
+
+
+def sph_tree_counts(ctx: Context) -> dict:
+    """Nested-grid diagnostics of the last build and density."""
+    v = (C.c_int64 * 4)()
+    _check(lib().sph_tree_counts(ctx.handle, v), "sph_tree_counts")
+    return {"groups": int(v[0]), "list_free_targets": int(v[1]), "reverse_pairs": int(v[2]),
+            "fallback_targets": int(v[3])}
 
 
 def sph_reserve(ctx: Context, n_total: int, n_sims: int = 1):
