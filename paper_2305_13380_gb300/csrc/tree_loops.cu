@@ -38,8 +38,18 @@ constexpr int kTWarps = 4;       // warps per CTA
 constexpr int kTCap = 384;       // staged sources per warp and chunk
 constexpr int kTRows = kTreeList + 1;  // + one scratch row for the branch-free append
 constexpr int kTPer = 32 / kTreeTpp;   // targets per round
+constexpr int kTChildren = 27 * 8;      // children of the 27 neighbour cells
+
+// Pruning tables of a warp's group (groups that do not fit one staging chunk).
+struct TPrune {
+  int32_t cv[kTChildren + 4];    // virtual start of each child (Morton order), + end
+  int32_t hoff[kTChildren + 4];  // offsets of the round's hit children, + total
+  uint8_t hch[kTChildren];       // the round's hit children, in order
+  int32_t rlo[28], rcum[28], rsc[28];  // per neighbour range: first source, virtual start, shift
+};
+constexpr size_t kTPruneBytes = (sizeof(TPrune) + 15) / 16 * 16;
 constexpr size_t kTWarpSmem = (size_t)kTCap * (sizeof(float4) + sizeof(uint32_t)) +
-                              (size_t)kTRows * 32 * (sizeof(float) + sizeof(uint32_t));
+                              (size_t)kTRows * 32 * (sizeof(float) + sizeof(uint32_t)) + kTPruneBytes;
 constexpr size_t kTDensSmem = kTWarps * kTWarpSmem;
 constexpr int kNoShift = 1 | (1 << 2) | (1 << 4);
 // list_cnt markers: sums taken without a list; target re-solved by the fallback
@@ -260,6 +270,124 @@ __device__ __forceinline__ TRanges load_ranges(const TreeRange* __restrict__ ran
   return R;
 }
 
+// Pruning tables of a group: per neighbour range its first source, virtual
+// start and shift, and the virtual start of each of its 8 children (which
+// are contiguous in Morton order; a cell of the deepest level has one).
+// Lanes 0..26 search their range's keys.  Called by the whole warp.
+__device__ __forceinline__ void prune_tables(const uint64_t* __restrict__ skey, const TRanges& R, int depth,
+                                             int lane, TPrune* pr) {
+  const int32_t cum_next = __shfl_down_sync(0xffffffffu, R.cum, 1);
+  if (lane < 27) {
+    const int32_t len = cum_next - R.cum;
+    pr->rlo[lane] = R.lo;
+    pr->rcum[lane] = R.cum;
+    pr->rsc[lane] = R.sc;
+    int32_t* cvr = pr->cv + lane * 8;
+    cvr[0] = R.cum;
+    if (depth < kTreeDepth && len > 0) {
+      const int sh = 3 * (kTreeDepth - depth - 1);
+      const uint64_t base = (skey[R.lo] >> (sh + 3)) << (sh + 3);
+      int64_t pos = R.lo;
+      for (int c = 1; c < 8; ++c) {
+        pos = lower_bound64(skey, pos, (int64_t)R.lo + len, base + ((uint64_t)c << sh));
+        cvr[c] = R.cum + (int32_t)(pos - R.lo);
+      }
+    } else {
+      for (int c = 1; c < 8; ++c) cvr[c] = R.cum + len;
+    }
+  }
+  if (lane == 0) pr->cv[kTChildren] = R.nsrc;
+  __syncwarp();
+}
+
+// Squared distance from p (relative to the group corner) to child ch's box:
+// neighbour r = ch / 8 at offset (r % 3, r / 3 % 3, r / 9) - 1 cells, child
+// bits (x, y, z) = bits 0, 1, 2 of ch % 8, child side cside.
+__device__ __forceinline__ float child_dist2(int ch, float side, float cside, const float3& p) {
+  const int r = ch >> 3, c = ch & 7;
+  const float bx = (float)(r % 3 - 1) * side + (float)(c & 1) * cside;
+  const float by = (float)((r / 3) % 3 - 1) * side + (float)((c >> 1) & 1) * cside;
+  const float bz = (float)(r / 9 - 1) * side + (float)((c >> 2) & 1) * cside;
+  const float ex = fmaxf(fmaxf(bx - p.x, p.x - (bx + cside)), 0.0f);
+  const float ey = fmaxf(fmaxf(by - p.y, p.y - (by + cside)), 0.0f);
+  const float ez = fmaxf(fmaxf(bz - p.z, p.z - (bz + cside)), 0.0f);
+  return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+}
+
+// The children any target of the round can reach: each target's lanes test
+// 27 children each (ch = sub + 8 m) against its list radius, the union over
+// the round's targets is compacted in child order with the offsets of their
+// sources.  Returns the union's source count.  Called by the whole warp.
+__device__ __forceinline__ int prune_round(bool valid, int sub, int lane, const float3& pi, float Rb2,
+                                           float side, float cside, TPrune* pr, int& nh) {
+  uint32_t mine = 0;
+  if (valid) {
+    for (int m = 0; m < 27; ++m) {
+      const int ch = sub + 8 * m;
+      if (pr->cv[ch] < pr->cv[ch + 1] && child_dist2(ch, side, cside, pi) < Rb2) mine |= 1u << m;
+    }
+  }
+#pragma unroll
+  for (int o = kTreeTpp; o < 32; o <<= 1) mine |= __shfl_xor_sync(0xffffffffu, mine, o);
+  // lanes 0..7 hold the union of children sub = lane (+ 8 m)
+  nh = 0;
+  for (int m = 0; m < 27; ++m) {
+    const bool hb = lane < kTreeTpp && ((mine >> m) & 1u);
+    const unsigned b = __ballot_sync(0xffffffffu, hb);
+    if (hb) {
+      const int ch = kTreeTpp * m + lane;
+      const int k = nh + __popc(b & ((1u << lane) - 1u));
+      pr->hch[k] = (uint8_t)ch;
+      pr->hoff[k] = pr->cv[ch + 1] - pr->cv[ch];
+    }
+    nh += __popc(b);
+  }
+  __syncwarp();
+  int run = 0;
+  for (int k0 = 0; k0 < nh; k0 += 32) {
+    const int k = k0 + lane;
+    const int v = k < nh ? pr->hoff[k] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int w = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += w;
+    }
+    if (k < nh) pr->hoff[k] = run + incl - v;
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) pr->hoff[nh] = run;
+  __syncwarp();
+  return run;
+}
+
+// Stages sources [u0, u0 + kTCap) of the round's hit children (flattened)
+// relative to the group corner.  Called by the whole warp.
+__device__ __forceinline__ int tstage_union(int u0, int total, int nh, const TPrune* pr, int lane,
+                                            const TGeo& g, const float4* __restrict__ rel,
+                                            const int4* __restrict__ fine, float4* spos, uint32_t* sidx) {
+  const int cnt = min(kTCap, total - u0);
+  for (int u = lane; u < cnt; u += 32) {
+    const int uu = u0 + u;
+    int lo = 0, hi = nh - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pr->hoff[mid] <= uu) lo = mid; else hi = mid - 1;
+    }
+    const int ch = pr->hch[lo];
+    const int vv = pr->cv[ch] + (uu - pr->hoff[lo]);
+    const int r = ch >> 3;
+    const int32_t j = pr->rlo[r] + (vv - pr->rcum[r]);
+    const int sc = pr->rsc[r];
+    const float4 rj = rel[j];
+    const float3 p = rel_to(g, rj, fine[j], sc);
+    spos[u] = make_float4(p.x, p.y, p.z, rj.w);
+    sidx[u] = pack_js(j, sc);
+  }
+  __syncwarp();
+  return cnt;
+}
+
 // Stages sources [v0, v0 + kTCap) of the concatenated ranges relative to the
 // leaf corner (position and mass, packed index).  Called by the whole warp.
 __device__ __forceinline__ int tstage(int v0, const TRanges& R, int lane, const TGeo& g,
@@ -353,6 +481,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
   uint32_t* sidx = reinterpret_cast<uint32_t*>(spos + kTCap);
   float* lr2 = reinterpret_cast<float*>(sidx + kTCap);
   uint32_t* lje = reinterpret_cast<uint32_t*>(lr2 + kTRows * 32);
+  TPrune* pr = reinterpret_cast<TPrune*>(lje + kTRows * 32);
   const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
   const int32_t nl = *a.n_leaves;
   unsigned long long pair_acc = 0, free_acc = 0;
@@ -365,7 +494,10 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
     const int nsrc = R.nsrc;
     const double hcap = fmin(g.side_d, 0.5 * g.L) * (1.0 - 1e-5) / kGammaKd;
     const bool one_chunk = nsrc <= kTCap;
+    // children are half the cell (a cell at the deepest level has one child)
+    const float cside = Lf.depth < kTreeDepth ? 0.5f * g.side : g.side;
     if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx);
+    else prune_tables(a.skey, R, Lf.depth, lane, pr);
     for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
       const bool valid = t0 + t < n_t;
       const int32_t ti = a.tgt[t_lo + (valid ? t0 + t : 0)];
@@ -375,12 +507,15 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       const float4 vi = a.vel4[ti];
       const float Ri = a.lrad[ti];
       const float R2 = Ri * Ri;
-      // 1. filter: sources with r < R_i into this lane's list
+      // 1. filter: sources with r < R_i into this lane's list.  A group that
+      // does not fit one staging chunk stages, per round, only the children
+      // of its 27 cells that some target of the round reaches: a child whose
+      // box lies beyond R_i (with a margin far above the rounding of r) holds
+      // no list entry of that target.
       int cnt = 0;
-      for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
-        const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
+      if (one_chunk) {
         if (valid) {
-          for (int k = sub; k < c; k += kTreeTpp) {
+          for (int k = sub; k < nsrc; k += kTreeTpp) {
             const float r2 = r2_of(pi, spos[k]);
             const int at = min(cnt, kTreeList) * 32 + lane;
             lr2[at] = r2;
@@ -388,7 +523,22 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
             cnt += r2 < R2;
           }
         }
-        if (!one_chunk) __syncwarp();
+      } else {
+        int nh = 0;
+        const int total = prune_round(valid, sub, lane, pi, R2 * (1.0f + 0x1p-10f), g.side, cside, pr, nh);
+        for (int u0 = 0; u0 < total; u0 += kTCap) {
+          const int c = tstage_union(u0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx);
+          if (valid) {
+            for (int k = sub; k < c; k += kTreeTpp) {
+              const float r2 = r2_of(pi, spos[k]);
+              const int at = min(cnt, kTreeList) * 32 + lane;
+              lr2[at] = r2;
+              lje[at] = sidx[k];
+              cnt += r2 < R2;
+            }
+          }
+          __syncwarp();
+        }
       }
       // a target whose list overflowed, or whose support outgrows R_i, sums
       // over every staged source instead ("list-free"); the others keep
