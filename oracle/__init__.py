@@ -83,6 +83,8 @@ def lib():
         L.oracle_wrap.argtypes = [C.c_double, C.c_double]
         L.oracle_cell_coord.restype = C.c_int32
         L.oracle_cell_coord.argtypes = [C.c_double, C.c_double, C.c_int32]
+        L.oracle_tree_order.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                        C.c_int32, C.c_void_p, C.c_void_p]
         L.oracle_build_cells.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_double, C.c_int32, C.c_void_p, C.c_void_p]
         L.oracle_density.argtypes = [C.POINTER(_Particles), C.POINTER(_Config), C.c_void_p,
@@ -172,6 +174,19 @@ def build_cells(x, y, z, L: float, n_c: int):
     perm = np.zeros(max(n, 1), dtype=np.int32)
     _check(lib().oracle_build_cells(n, keep(x), keep(y), keep(z), float(L), int(n_c),
                                     _ptr(cell_start), _ptr(perm)), "build_cells")
+    return cell_start, perm[:n]
+
+
+def tree_order(x, y, z, L: float, n_c: int):
+    """Depth-first order of the nested grids below the n_c^3 top cells
+    (Sec. 2.1, Sec. 9.1): top cells ascending, then the child indices of
+    depths 1..10, ties by input index.  Returns (cell_start, perm)."""
+    keep = _Keep()
+    n = int(np.asarray(x).shape[0])
+    cell_start = np.zeros(n_c ** 3 + 1, dtype=np.int32)
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().oracle_tree_order(n, keep(x), keep(y), keep(z), float(L), int(n_c),
+                                   _ptr(cell_start), _ptr(perm)), "tree_order")
     return cell_start, perm[:n]
 
 

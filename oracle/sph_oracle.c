@@ -141,6 +141,70 @@ int oracle_build_cells(int64_t n, const double* x, const double* y, const double
 }
 
 /* --------------------------------------------------------------------------
+ * Depth-first order of the nested grids (Sec. 2.1 and Sec. 9.1: particles of
+ * every cell of every level of the octree below a top cell are contiguous).
+ * Each top cell is split 10 times (1024 sub-cells per side); a particle's
+ * sub-cell on one axis is g = floor(1024 fl(fl(x n_c) / L)), clamped to its
+ * top cell k: g in [1024 k, 1024 k + 1023].  Inside a top cell, particles are
+ * ordered by the child index (x bit + 2 y bit + 4 z bit) at depth 1, then at
+ * depth 2, ... depth 10, i.e. by the number whose base-8 digits are those
+ * child indices; ties keep ascending input index.  Top cells come in
+ * ascending cell id (kx + n_c (ky + n_c kz)).
+ * -------------------------------------------------------------------------- */
+static int32_t or_fine(double x, double L, int32_t n_c, int32_t k) {
+  double s = (x * (double)n_c) / L;
+  double g = floor(s * 1024.0);
+  double lo = 1024.0 * (double)k, hi = lo + 1023.0;
+  if (g < lo) g = lo;
+  if (g > hi) g = hi;
+  return (int32_t)(g - lo);
+}
+
+typedef struct {
+  uint64_t key;
+  int32_t idx;
+} or_tkey;
+
+static int or_tkey_cmp(const void* a, const void* b) {
+  const or_tkey* p = (const or_tkey*)a;
+  const or_tkey* q = (const or_tkey*)b;
+  if (p->key != q->key) return p->key < q->key ? -1 : 1;
+  return p->idx < q->idx ? -1 : (p->idx > q->idx ? 1 : 0);
+}
+
+int oracle_tree_order(int64_t n, const double* x, const double* y, const double* z, double L, int32_t n_c,
+                      int32_t* cell_start, int32_t* perm) {
+  if (n < 0 || n_c < 1) return -1;
+  int64_t n_cells = (int64_t)n_c * n_c * n_c;
+  or_tkey* t = (or_tkey*)malloc(sizeof(or_tkey) * (size_t)(n > 0 ? n : 1));
+  int64_t* count = (int64_t*)calloc((size_t)n_cells + 1, sizeof(int64_t));
+  if (!t || !count) { free(t); free(count); return -2; }
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t kx = oracle_cell_coord(x[i], L, n_c);
+    int32_t ky = oracle_cell_coord(y[i], L, n_c);
+    int32_t kz = oracle_cell_coord(z[i], L, n_c);
+    int32_t gx = or_fine(x[i], L, n_c, kx), gy = or_fine(y[i], L, n_c, ky), gz = or_fine(z[i], L, n_c, kz);
+    uint64_t digits = 0;
+    for (int d = 1; d <= 10; ++d) {
+      int b = 10 - d; /* bit of the sub-cell coordinate chosen at depth d */
+      uint64_t child = (uint64_t)(((gx >> b) & 1) + 2 * ((gy >> b) & 1) + 4 * ((gz >> b) & 1));
+      digits = digits * 8 + child;
+    }
+    int64_t cell = kx + (int64_t)n_c * (ky + (int64_t)n_c * kz);
+    t[i].key = ((uint64_t)cell << 30) + digits;
+    t[i].idx = (int32_t)i;
+    count[cell + 1] += 1;
+  }
+  qsort(t, (size_t)n, sizeof(or_tkey), or_tkey_cmp);
+  for (int64_t c = 0; c < n_cells; ++c) count[c + 1] += count[c];
+  for (int64_t c = 0; c <= n_cells; ++c) cell_start[c] = (int32_t)count[c];
+  for (int64_t i = 0; i < n; ++i) perm[i] = t[i].idx;
+  free(t);
+  free(count);
+  return 0;
+}
+
+/* --------------------------------------------------------------------------
  * Range search: a bucket grid over the periodic box.  or_collect returns
  * every particle j whose minimum-image distance to point p is < R (and, if
  * skip >= 0, j != skip), with its displacement p - x_j.

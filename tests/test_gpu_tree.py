@@ -177,3 +177,26 @@ def test_tree_rebuild_when_top_cells_too_small(orc):
     assert g["rebuilds"] >= 1
     od, of = orc.density_force(q, q["h0"])
     compare(g, od, of)
+
+
+@pytest.mark.parametrize("case", ["lattice16", "clustered6000", "clustered20000"])
+def test_tree_order_bit_exact(orc, case):
+    # the nested grids' source order (top cells, then depth-first below them,
+    # ties by index) and the top cells' ranges equal the oracle's exactly
+    import torch
+    from paper_2305_13380_gb300 import sph
+    if case == "lattice16":
+        p = inputs.lattice(16)
+    elif case == "clustered6000":
+        p = inputs.clustered(6000, n_spheres=4, seed=9)
+    else:
+        p = inputs.clustered(20000, n_spheres=64, seed=1)
+    ctx = sph.Context(sph.sph_default_params(box_size=float(p["L"]), flags=sph.SPH_FLAG_TREE))
+    t = sph.to_device(p)
+    cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], t["h0"])
+    cs, perm = sph.sph_cells_copy(ctx, cells)
+    assert sph.sph_status(ctx) == 0
+    torch.cuda.synchronize()
+    ocs, operm = orc.tree_order(p["x"], p["y"], p["z"], p["L"], cells.n_c)
+    assert np.array_equal(cs, ocs)
+    assert np.array_equal(perm, operm)
