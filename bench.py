@@ -350,7 +350,11 @@ def run_served(args, world: int, rank: int, local: int):
     slots = 3
     batch_cap = max(4 * largest, 4 << 20)
     budget = total * serve.STATE_BYTES + slots * batch_cap * (serve.STATE_BYTES + serve.SCRATCH_BYTES)
-    prm = sph.sph_default_params(flags=sph.SPH_FLAG_TREE)
+    # grid mode, margin and leaf size tuned on every 64th simulation
+    from paper_2305_13380_gb300 import tune
+    sample = [sims[s] for s in range(0, n_sims, 64)]
+    over = tune.best_params(sample, key=f"served-sample-{n_sims}")
+    prm = sph.sph_default_params(**over)
     srv = serve.Server(budget, store_particles=total, slots=slots, batch_particles=batch_cap,
                        params=prm)
     t_adm = time.perf_counter()
@@ -359,19 +363,22 @@ def run_served(args, world: int, rank: int, local: int):
     adm_s = time.perf_counter() - t_adm
     del sims
     ids = list(srv.sims)
+    # warm-up: every slot serves a few batches first
+    srv.run(serve.poisson_trace(6 * slots, rate=1e9, sims=ids, seed=0))
+    srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
     # saturation: every request present at t = 0
     sat = srv.run(serve.poisson_trace(3 * slots * 32, rate=1e9, sims=ids, seed=1))
     cap_rate = sat["requests"] / sat["wall_s"]
     rate = 0.5 * cap_rate
     n_req = max(200, int(rate * args.served_seconds))
     trace = serve.poisson_trace(n_req, rate=rate, sims=ids, seed=2)
-    srv.finished, srv.n_batches, srv.updates = [], 0, 0
+    srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
     clocks = Clocks(None)
     time.sleep(0.25)
     out = srv.run(trace)
     clk = clocks.stop()
     # the same trace, one simulation per launch on one stream
-    srv.finished, srv.n_batches, srv.updates = [], 0, 0
+    srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
     all_slots, srv.slots = srv.slots, srv.slots[:1]
     srv.max_batch_sims = 1
     plain = srv.run(trace)
@@ -385,12 +392,16 @@ def run_served(args, world: int, rank: int, local: int):
                            "[1e3, 5e5], relative speed 0.5-2, box 2; Poisson step requests",
                    "rate_per_s": rate, "slots": slots, "batch_particles": batch_cap,
                    "budget_gb": budget / 1e9, "generation_s": gen_s, "admission_s": adm_s,
-                   "grid": "nested"},
+                   "tuned": over},
         "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "mean_ms": out["mean_ms"],
         "requests_per_s": out["requests"] / out["wall_s"],
         "particle_updates_per_s": out["particle_updates_per_s"],
         "mean_sims_per_batch": out["mean_sims_per_batch"],
         "saturated_requests_per_s": cap_rate,
+        "saturated_batches": {k: sat[k] for k in ("batches", "batch_sims_mean", "batch_particles_mean",
+                                                    "batch_ms_mean", "batch_ms_max")},
+        "batches": {k: out[k] for k in ("batches", "batch_sims_mean", "batch_particles_mean",
+                                         "batch_ms_mean", "batch_ms_max")},
         "plain": {"p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"],
                   "particle_updates_per_s": plain["particle_updates_per_s"],
                   "wall_s": plain["wall_s"]},

@@ -266,6 +266,17 @@ int sph_kernel_times(sph_ctx* ctx, double* ms_out, int64_t* calls_out);
  * out[1] = force pairs r < max(H_i, H_j), j != i. */
 int sph_pair_counts(sph_ctx* ctx, int64_t* out);
 
+/* Moves the particle fields (x .. balsara; not dt or n_iter) of n_ranges
+ * whole simulations between two pools (device arrays, enqueued on `stream`,
+ * a cudaStream_t): simulation r occupies offsets[r] .. offsets[r+1] of
+ * `packed` (offsets[0] = 0, offsets[n_ranges] <= packed->n_total) and the
+ * same number of particles from starts[r] on in `spread`.  to_packed = 1
+ * copies spread -> packed (gathering a batch out of a store), 0 copies back.
+ * Only sim_offset-free fields are touched; the ranges must not overlap.  The
+ * paper has no counterpart: it serves many resident simulations. */
+int sph_pool_move(const sph_pool* spread, const sph_pool* packed, int32_t n_ranges, const int64_t* starts,
+                  const int64_t* offsets, int32_t to_packed, void* stream);
+
 /* Diagnostics of the last nested-grid build and density (SPH_FLAG_TREE; waits
  * for the stream): out[0] = target groups, out[1] = targets summed without a
  * neighbour list (needs SPH_FLAG_COUNT_PAIRS, else 0), out[2] = reverse pairs

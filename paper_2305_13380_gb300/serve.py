@@ -38,9 +38,6 @@ from . import sph
 F64 = ("x", "y", "z")
 F32 = ("vx", "vy", "vz", "u", "m", "h", "ax", "ay", "az", "du_dt", "v_sig", "rho", "f", "div_v",
        "curl_v", "P", "c", "balsara")
-# fields a step reads and writes back (m is constant)
-STEPPED = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du_dt", "v_sig", "rho",
-           "f", "div_v", "curl_v", "P", "c", "balsara")
 STATE_BYTES = 8 * len(F64) + 4 * len(F32)
 # context scratch per particle of an arena: cell keys and counts, sorted
 # copies and lists (~570 B) plus the nested grids' keys, orders, groups and
@@ -116,8 +113,10 @@ class _Slot:
         self.off = torch.zeros(max_sims + 1, dtype=torch.int64, device=device)
         self.box = torch.zeros(max_sims, dtype=torch.float64, device=device)
         self.meta = torch.zeros(3 * max_sims, dtype=torch.int64, device=device)
+        self.begin = torch.cuda.Event(enable_timing=True)
         self.done = torch.cuda.Event(enable_timing=True)
         self.requests: list[Request] = []
+        self.particles = 0
         self.sims: list[Sim] = []
 
 
@@ -143,6 +142,9 @@ class Server:
             raise ValueError(f"budget {budget_bytes / 1e9:.1f} GB holds the store and "
                              f"{fit} particles per slot; asked {batch_particles}")
         self.store = Store(store_particles)
+        self.store_pool = sph.pool(torch.tensor([0, store_particles], dtype=torch.int64, device="cuda"),
+                                   torch.ones(1, dtype=torch.float64, device="cuda"),
+                                   dict(self.store.a, dt=torch.zeros(1, dtype=torch.float64, device="cuda")))
         self.slots = [_Slot(self.params, int(batch_particles), max_batch_sims) for _ in range(slots)]
         for sl in self.slots:
             # no step of a slot allocates: its latency carries no cudaMalloc
@@ -159,6 +161,7 @@ class Server:
         self.t0 = None
         self.status = 0
         self.admit_ctx = None
+        self.batch_log: list[tuple[int, int, float]] = []  # (simulations, particles, device ms)
 
     # -------------------------------------------------------------- clock --
     def start_clock(self):
@@ -252,28 +255,24 @@ class Server:
         slot.meta_h[:ns] = torch.from_numpy(np.array([s.start for s in sims], dtype=np.int64))
         st = slot.stream
         with torch.cuda.stream(st):
+            slot.begin.record(st)
             slot.off[:ns + 1].copy_(slot.off_h[:ns + 1], non_blocking=True)
             slot.box[:ns].copy_(slot.box_h[:ns], non_blocking=True)
             slot.meta[:ns].copy_(slot.meta_h[:ns], non_blocking=True)
-            # store index of every arena particle
-            starts = slot.meta[:ns]
-            boff = slot.off[:ns]
-            cnt = slot.off[1:ns + 1] - boff
-            idx = torch.repeat_interleave(starts - boff, cnt, output_size=total)
-            idx += torch.arange(total, device="cuda")
             view = {k: v[:total] for k, v in slot.a.items() if k != "dt"}
-            for k in STEPPED + ("m",):
-                torch.index_select(self.store.a[k], 0, idx, out=view[k])
             view["dt"] = slot.a["dt"][:ns]
-            sph.sph_step(slot.ctx, sph.pool(slot.off[:ns + 1], slot.box[:ns], view))
-            for k in STEPPED:
-                self.store.a[k].index_copy_(0, idx, view[k])
+            packed = sph.pool(slot.off[:ns + 1], slot.box[:ns], view)
+            # gather the simulations out of the store, step them, put them back
+            sph.sph_pool_move(self.store_pool, packed, ns, slot.meta[:ns], slot.off[:ns + 1], True, st)
+            sph.sph_step(slot.ctx, packed)
+            sph.sph_pool_move(self.store_pool, packed, ns, slot.meta[:ns], slot.off[:ns + 1], False, st)
             slot.done.record(st)
         for s in sims:
             s.busy = True
         for r in reqs:
             r.batch = self.n_batches
         slot.requests, slot.sims = reqs, sims
+        slot.particles = total
         self.n_batches += 1
         self.updates += total
         return True
@@ -284,6 +283,7 @@ class Server:
         for slot in self.slots:
             if slot.requests and slot.done.query():
                 t = self.ref.elapsed_time(slot.done) / 1e3
+                self.batch_log.append((len(slot.sims), slot.particles, slot.begin.elapsed_time(slot.done)))
                 self.status |= sph.sph_status(slot.ctx)
                 for r in slot.requests:
                     r.t_done = t
@@ -323,7 +323,10 @@ class Server:
         torch.cuda.synchronize()
         wall = self.now()
         lat = np.array([r.t_done - r.t_arrival for r in self.finished])
+        log = np.array(self.batch_log[-self.n_batches:] or [(0, 0, 0.0)], dtype=np.float64)
         return {"requests": n, "batches": self.n_batches, "wall_s": wall,
+                "batch_sims_mean": float(log[:, 0].mean()), "batch_particles_mean": float(log[:, 1].mean()),
+                "batch_ms_mean": float(log[:, 2].mean()), "batch_ms_max": float(log[:, 2].max()),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "mean_ms": float(lat.mean() * 1e3),

@@ -120,10 +120,13 @@ def lib():
                                              _P, C.c_int64, _P, _P, _P, _P]
         L.sph_reserve.argtypes = [_P, C.c_int64, C.c_int32]
         L.sph_tree_counts.argtypes = [_P, C.POINTER(C.c_int64)]
+        L.sph_pool_move.argtypes = [C.POINTER(sph_pool), C.POINTER(sph_pool), C.c_int32, _P, _P, C.c_int32,
+                                    _P]
         for f in ("sph_create", "sph_status", "sph_build_cells", "sph_cells_sync", "sph_cells_copy",
                   "sph_density",
                   "sph_force", "sph_step", "sph_conservation", "sph_pair_counts",
-                  "sph_kernel_times", "sph_build_cells_static", "sph_reserve", "sph_tree_counts"):
+                  "sph_kernel_times", "sph_build_cells_static", "sph_reserve", "sph_tree_counts",
+                  "sph_pool_move"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -268,6 +271,16 @@ def pool(sim_offset, box_size, arrays: dict) -> sph_pool:
                  _ptr(box_size, torch.float64), *vals, _ptr(arrays.get("n_iter"), torch.int32))
     s._keep = (sim_offset, box_size, arrays)
     return s
+
+
+def sph_pool_move(spread: sph_pool, packed: sph_pool, n_ranges: int, starts, offsets, to_packed: bool,
+                  stream=None):
+    """Moves whole simulations between a spread pool and a packed one
+    (starts / offsets: int64 device tensors of n_ranges and n_ranges + 1)."""
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().sph_pool_move(C.byref(spread), C.byref(packed), int(n_ranges), _ptr(starts, torch.int64),
+                               _ptr(offsets, torch.int64), 1 if to_packed else 0, C.c_void_p(st.cuda_stream)),
+           "sph_pool_move")
 
 
 def sph_tree_counts(ctx: Context) -> dict:

@@ -71,3 +71,43 @@ def test_admission_waits_for_room():
     srv.retire(1)
     assert set(srv.sims) == {2, 3}
     torch.cuda.synchronize()
+
+
+def test_pool_move_round_trip():
+    # whole simulations gathered out of a spread store into a packed arena and
+    # moved back: every field lands where it belongs, nothing else changes
+    import torch
+    from paper_2305_13380_gb300 import sph
+    g = torch.Generator(device="cuda").manual_seed(0)
+    n_store, ranges = 1000, [(700, 50), (10, 120), (400, 1), (900, 99)]
+    keys = sph.POOL_FIELDS[:-1]
+
+    def arrays(n):
+        a = {k: torch.rand(n, generator=g, device="cuda",
+                           dtype=torch.float64 if k in ("x", "y", "z") else torch.float32) for k in keys}
+        a["dt"] = torch.zeros(1, dtype=torch.float64, device="cuda")
+        return a
+    store = arrays(n_store)
+    before = {k: v.clone() for k, v in store.items()}
+    total = sum(n for _, n in ranges)
+    arena = arrays(total + 7)
+    off = torch.tensor([0] + list(np.cumsum([n for _, n in ranges])), dtype=torch.int64, device="cuda")
+    starts = torch.tensor([s for s, _ in ranges], dtype=torch.int64, device="cuda")
+    box = torch.ones(1, dtype=torch.float64, device="cuda")
+    sp = sph.pool(torch.tensor([0, n_store], dtype=torch.int64, device="cuda"), box, store)
+    pk = sph.pool(torch.tensor([0, total + 7], dtype=torch.int64, device="cuda"), box, arena)
+    sph.sph_pool_move(sp, pk, len(ranges), starts, off, True)
+    torch.cuda.synchronize()
+    for k in keys:
+        for r, (s, n) in enumerate(ranges):
+            o = int(off[r])
+            assert torch.equal(arena[k][o:o + n], store[k][s:s + n]), k
+    for k in keys:
+        arena[k][:total] *= 2
+    sph.sph_pool_move(sp, pk, len(ranges), starts, off, False)
+    torch.cuda.synchronize()
+    for k in keys:
+        exp = before[k].clone()
+        for s, n in ranges:
+            exp[s:s + n] *= 2
+        assert torch.equal(store[k], exp), k
