@@ -552,8 +552,10 @@ def main():
         kname, kms, flops = "force", force_ms, pairs_f * F_FORCE
     achieved = flops / (kms / 1e3) / 1e12
     kfull = f"k_tree_{kname}" if tree else f"k_{kname}"
+    fma_peak = sph.fp32_peak_tflops()  # measured FP32 FMA rate of this device
     roofline = {"bound": "alu", "kernel": kfull, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_measured_fma": fma_peak, "frac_of_measured": achieved / fma_peak,
                 "traffic": _traffic(kfull[2:], "tree_loops" if tree else kname),
                 "peak_basis": (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                f"lanes x 2 flop x {peak_mhz:.0f} MHz (derived; no measured FP32 "
@@ -580,6 +582,8 @@ def main():
         "roofline": roofline,
         "cpu_baseline": cpu,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        # the loops alone: density (all Newton passes) + force per step
+        "density_force_updates_per_s": n / ((kt["density"][0] + kt["force"][0]) / args.steps / 1e3),
         "pairs_per_step": {"density_final_pass": pairs_d, "force": pairs_f,
                            "mean_newton_passes": mean_pass},
         "nested_grids": tree_counts,

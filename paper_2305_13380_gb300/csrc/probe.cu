@@ -1,0 +1,34 @@
+// probe.cu -- sph_fp32_probe: a kernel of independent FP32 fused multiply-add
+// chains, timed by the caller to measure the FP32 pipe's peak rate on the
+// device at hand (the denominator of the loops' roofline, which are bound by
+// FP32 arithmetic).  Not part of the method.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph_internal.cuh"
+
+namespace {
+
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) k_fp32_probe(int64_t iters, float a, float b, float* __restrict__ sink) {
+  float acc[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc[c] = (float)(threadIdx.x + c);
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) acc[c] = fmaf(acc[c], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += acc[c];
+  if (s == 12345.678f) sink[blockIdx.x] = s;  // keeps the chains live
+}
+
+}  // namespace
+
+extern "C" int sph_fp32_probe(int32_t blocks, int64_t iters, float* sink, void* stream) {
+  if (blocks < 1 || iters < 1 || !sink) return SPH_E_INVAL;
+  k_fp32_probe<<<blocks, 256, 0, (cudaStream_t)stream>>>(iters, 0.999999f, 1e-7f, sink);
+  return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_E_CUDA;
+}
