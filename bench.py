@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lattice128")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--served-resident", type=float, default=0.25,
+                    help="fraction of the live simulations' particles the device store holds")
     ap.add_argument("--served-seconds", type=float, default=6.0,
                     help="length of the served request trace at half the saturated rate")
     ap.add_argument("--cpu-budget", type=float, default=12.0,
@@ -329,9 +331,11 @@ def run_batch(args, world: int, rank: int, local: int):
 
 def run_served(args, world: int, rank: int, local: int):
     """Served workload: live simulations of two colliding spheres (radii
-    0.1-0.3, 10^3-5x10^5 particles log-uniform, relative speed 0.5-2) resident
-    on the device; step requests arrive as a Poisson process and are served
-    with continuous batching (several batches in flight on their own streams).
+    0.1-0.3, 10^3-5x10^5 particles log-uniform, relative speed 0.5-2); the
+    device store holds a quarter of them (an HBM budget below the all-resident
+    footprint), the rest wait in pinned host memory and are admitted on
+    request; step requests arrive as a Poisson process and are served with
+    continuous batching (several batches in flight on their own streams).
     The offered rate is half the saturated throughput measured first.  The same
     trace is then served one simulation per launch for comparison."""
     import numpy as np
@@ -349,17 +353,20 @@ def run_served(args, world: int, rank: int, local: int):
     largest = max(len(p["x"]) for p in sims.values())
     slots = 3
     batch_cap = max(4 * largest, 4 << 20)
-    budget = total * serve.STATE_BYTES + slots * batch_cap * (serve.STATE_BYTES + serve.SCRATCH_BYTES)
+    # the store holds a fraction of the live simulations' particles: the rest
+    # wait in pinned host memory and are admitted (evicting idle ones) on request
+    store_n = max(int(args.served_resident * total), 2 * largest)
+    budget = store_n * serve.STATE_BYTES + slots * batch_cap * (serve.STATE_BYTES + serve.SCRATCH_BYTES)
     # grid mode, margin and leaf size tuned on every 64th simulation
     from paper_2305_13380_gb300 import tune
     sample = [sims[s] for s in range(0, n_sims, 64)]
     over = tune.best_params(sample, key=f"served-sample-{n_sims}")
     prm = sph.sph_default_params(**over)
-    srv = serve.Server(budget, store_particles=total, slots=slots, batch_particles=batch_cap,
+    srv = serve.Server(budget, store_particles=store_n, slots=slots, batch_particles=batch_cap,
                        params=prm)
     t_adm = time.perf_counter()
     for s, p in sims.items():
-        srv.admit(s, p)
+        srv.register(s, p)
     adm_s = time.perf_counter() - t_adm
     del sims
     ids = list(srv.sims)
@@ -373,10 +380,12 @@ def run_served(args, world: int, rank: int, local: int):
     n_req = max(200, int(rate * args.served_seconds))
     trace = serve.poisson_trace(n_req, rate=rate, sims=ids, seed=2)
     srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
+    up0, ev0 = srv.uploads, srv.evictions
     clocks = Clocks(None)
     time.sleep(0.25)
     out = srv.run(trace)
     clk = clocks.stop()
+    paging = {"uploads": srv.uploads - up0, "evictions": srv.evictions - ev0}
     # the same trace, one simulation per launch on one stream
     srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
     all_slots, srv.slots = srv.slots, srv.slots[:1]
@@ -391,12 +400,14 @@ def run_served(args, world: int, rank: int, local: int):
                    "desc": "two uniform spheres per simulation, radii 0.1-0.3, N log-uniform in "
                            "[1e3, 5e5], relative speed 0.5-2, box 2; Poisson step requests",
                    "rate_per_s": rate, "slots": slots, "batch_particles": batch_cap,
+                   "resident_particles": store_n, "resident_fraction": store_n / total,
                    "budget_gb": budget / 1e9, "generation_s": gen_s, "admission_s": adm_s,
                    "tuned": over},
         "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "mean_ms": out["mean_ms"],
         "requests_per_s": out["requests"] / out["wall_s"],
         "particle_updates_per_s": out["particle_updates_per_s"],
         "mean_sims_per_batch": out["mean_sims_per_batch"],
+        "paging": paging,
         "saturated_requests_per_s": cap_rate,
         "saturated_batches": {k: sat[k] for k in ("batches", "batch_sims_mean", "batch_particles_mean",
                                                     "batch_ms_mean", "batch_ms_max")},

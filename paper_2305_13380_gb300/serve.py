@@ -5,6 +5,10 @@ State.  Every admitted simulation keeps its particles resident in one device
 store (structure of arrays, one contiguous range per simulation, handed out
 by a first-fit allocator).  A simulation is admitted only while its range fits
 in the store, so the resident set never exceeds the budget it was sized for.
+Registered simulations may outnumber what the store holds: each keeps a
+pinned host copy, and a request for one that is not resident admits it,
+evicting the least recently used idle simulations (their state copied back to
+the host after their last batch) until its range fits.
 
 Requests.  A request asks for one KDK step of one simulation.  Requests of the
 same simulation run in arrival order, one at a time.
@@ -88,6 +92,11 @@ class Sim:
     start: int
     busy: bool = False
     steps: int = 0
+    resident: bool = True
+    host: dict | None = None       # pinned copy of the state (registered simulations)
+    last_event: object = None      # completion of the last batch that touched the state
+    ready: object = None           # completion of its upload, for the next batch to wait on
+    last_use: int = 0
 
 
 @dataclasses.dataclass
@@ -162,6 +171,12 @@ class Server:
         self.status = 0
         self.admit_ctx = None
         self.batch_log: list[tuple[int, int, float]] = []  # (simulations, particles, device ms)
+        # registered simulations live in pinned host memory when not resident;
+        # evictions and uploads run on their own stream
+        self.transfer = torch.cuda.Stream()
+        self.uploads = 0
+        self.evictions = 0
+        self.use_clock = 0
 
     # -------------------------------------------------------------- clock --
     def start_clock(self):
@@ -206,6 +221,79 @@ class Server:
         self.sims[sid] = Sim(sid, n, float(sim["L"]), start)
         return True
 
+    # ------------------------------------------ registered simulations --
+    def register(self, sid: int, sim: dict):
+        """A live simulation whose state may leave the device: its state is
+        kept in pinned host memory, it is made resident (evicting idle
+        simulations if the store is full) and gets its first density + force.
+        Later requests admit it again whenever it was evicted."""
+        n = len(sim["x"])
+        if n > self.batch_particles or n > self.store.capacity:
+            raise ValueError(f"simulation {sid} ({n} particles) exceeds the batch or store capacity")
+        host = {k: torch.empty(n, dtype=torch.float64, pin_memory=True) for k in F64}
+        host.update({k: torch.zeros(n, dtype=torch.float32, pin_memory=True) for k in F32})
+        for k in F64:
+            host[k].copy_(torch.as_tensor(np.asarray(sim[k], dtype=np.float64)))
+        for k, src in (("vx", "vx"), ("vy", "vy"), ("vz", "vz"), ("u", "u"), ("m", "m"), ("h", "h0")):
+            host[k].copy_(torch.as_tensor(np.asarray(sim[src], dtype=np.float32)))
+        sm = Sim(sid, n, float(sim["L"]), -1, resident=False, host=host)
+        self.sims[sid] = sm
+        if not self._make_resident(sm, set()):
+            raise RuntimeError("no room in the store even after evicting every idle simulation")
+        # first density + force on the transfer stream (synchronous context)
+        if self.admit_ctx is None:
+            q = sph.sph_params.from_buffer_copy(self.params)
+            q.flags |= sph.SPH_FLAG_SYNC
+            self.admit_ctx = sph.Context(q, self.transfer)
+        with torch.cuda.stream(self.transfer):
+            off = torch.tensor([0, n], dtype=torch.int64, device="cuda")
+            box = torch.tensor([sm.L], dtype=torch.float64, device="cuda")
+            arr = self.store.view(sm.start, n)
+            arr["dt"] = torch.zeros(1, dtype=torch.float64, device="cuda")
+            sph.sph_step(self.admit_ctx, sph.pool(off, box, arr))
+        self.transfer.synchronize()
+        sm.ready = None
+
+    def _make_resident(self, sm: Sim, exclude: set) -> bool:
+        """Gives a registered simulation a range of the store and uploads its
+        state (on the transfer stream), evicting the least recently used idle
+        simulations (not busy, not in `exclude`) while no range fits."""
+        if sm.resident:
+            return True
+        while True:
+            start = self.store.alloc(sm.n)
+            if start is not None:
+                break
+            idle = [o for o in self.sims.values()
+                    if o.resident and not o.busy and o.host is not None and o.sid not in exclude]
+            if not idle:
+                return False
+            self._evict(min(idle, key=lambda o: o.last_use))
+        sm.start, sm.resident = start, True
+        v = self.store.view(start, sm.n)
+        with torch.cuda.stream(self.transfer):
+            for k in F64 + F32:
+                v[k].copy_(sm.host[k], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.transfer)
+        sm.ready = ev
+        self.uploads += 1
+        return True
+
+    def _evict(self, sm: Sim):
+        """Copies a resident simulation's state to its pinned host copy after
+        its last batch, and frees its range (the next upload into that range
+        runs after the copy, on the same stream)."""
+        v = self.store.view(sm.start, sm.n)
+        with torch.cuda.stream(self.transfer):
+            if sm.last_event is not None:
+                self.transfer.wait_event(sm.last_event)
+            for k in F64 + F32:
+                sm.host[k].copy_(v[k], non_blocking=True)
+        self.store.release(sm.start, sm.n)
+        sm.resident, sm.start, sm.ready = False, -1, None
+        self.evictions += 1
+
     def retire(self, sid: int):
         """Frees a simulation's range and admits waiting ones that now fit."""
         s = self.sims.pop(sid)
@@ -221,6 +309,8 @@ class Server:
                                          "ay", "az", "du_dt", "v_sig")) -> dict:
         torch.cuda.synchronize()
         s = self.sims[sid]
+        if not s.resident:
+            return {k: s.host[k].numpy().copy() for k in keys}
         v = self.store.view(s.start, s.n)
         return {k: v[k].cpu().numpy() for k in keys}
 
@@ -238,6 +328,9 @@ class Server:
             if s.busy or r.sid in taken or total + s.n > slot.capacity:
                 kept.append(r)
                 continue
+            if not s.resident and not self._make_resident(s, taken):
+                kept.append(r)  # no room until running batches finish
+                continue
             reqs.append(r)
             sims.append(s)
             taken.add(r.sid)
@@ -254,7 +347,12 @@ class Server:
         slot.box_h[:ns] = torch.tensor([s.L for s in sims], dtype=torch.float64)
         slot.meta_h[:ns] = torch.from_numpy(np.array([s.start for s in sims], dtype=np.int64))
         st = slot.stream
+        slot.done = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(st):
+            for sm in sims:
+                if sm.ready is not None:  # freshly uploaded
+                    st.wait_event(sm.ready)
+                    sm.ready = None
             slot.begin.record(st)
             slot.off[:ns + 1].copy_(slot.off_h[:ns + 1], non_blocking=True)
             slot.box[:ns].copy_(slot.box_h[:ns], non_blocking=True)
@@ -267,8 +365,11 @@ class Server:
             sph.sph_step(slot.ctx, packed)
             sph.sph_pool_move(self.store_pool, packed, ns, slot.meta[:ns], slot.off[:ns + 1], False, st)
             slot.done.record(st)
+        self.use_clock += 1
         for s in sims:
             s.busy = True
+            s.last_event = slot.done
+            s.last_use = self.use_clock
         for r in reqs:
             r.batch = self.n_batches
         slot.requests, slot.sims = reqs, sims

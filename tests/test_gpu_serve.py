@@ -111,3 +111,33 @@ def test_pool_move_round_trip():
         for s, n in ranges:
             exp[s:s + n] *= 2
         assert torch.equal(store[k], exp), k
+
+
+def test_budgeted_store_pages_simulations_and_keeps_results():
+    # the store holds about a third of the registered simulations: requests
+    # admit simulations by evicting idle ones to host memory, and every
+    # simulation's state still equals its run alone
+    import torch
+    from paper_2305_13380_gb300 import pool, serve, sph
+    sims = _sims(9, 1500, 1500)
+    n = len(sims[0]["x"])
+    prm = sph.sph_default_params(flags=sph.SPH_FLAG_TREE)
+    srv = serve.Server(budget_bytes=2 << 30, store_particles=3 * n + 100, slots=2, batch_particles=2 * n,
+                       params=prm)
+    for sid, p in sims.items():
+        srv.register(sid, p)
+    trace = serve.poisson_trace(30, rate=500.0, sims=list(sims), seed=4)
+    out = srv.run(trace)
+    assert out["device_status"] == 0
+    assert srv.evictions > 0 and srv.uploads > len(sims)
+    steps = {sid: sum(1 for _, s in trace if s == sid) for sid in sims}
+    for sid, p in sims.items():
+        got = srv.host_state(sid)
+        alone = pool.Pool([p], prm)
+        alone.start()
+        for _ in range(steps[sid]):
+            alone.step()
+        ref = alone.host()
+        for k in ("x", "vx", "u", "h", "rho", "ax", "du_dt", "v_sig"):
+            assert np.array_equal(got[k], ref[k]), (sid, k)
+    torch.cuda.synchronize()
