@@ -267,7 +267,7 @@ def run_batch(args, world: int, rank: int, local: int):
 
     from paper_2305_13380_gb300 import build as B
     B.build()
-    from paper_2305_13380_gb300 import inputs, pool, sph, tune
+    from paper_2305_13380_gb300 import inputs, pool, replicas, sph, tune
 
     n_boxes = int(args.workload[len("batch"):] or 256)
     boxes = inputs.batch(n_boxes, seed0=0)
@@ -285,13 +285,19 @@ def run_batch(args, world: int, rank: int, local: int):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = Clocks(None)
     time.sleep(0.25)
+    replicas.barrier()
     ev[0].record(P.stream)
     for k in range(args.steps):
         P.replay()
         ev[k + 1].record(P.stream)
     P.stream.synchronize()
+    replicas.barrier()
     clk = clocks.stop()
     per = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])
+    # replicas: the slowest rank's latencies, the units of all ranks
+    p50 = replicas.max_over_ranks(float(np.percentile(per, 50)))
+    p99 = replicas.max_over_ranks(float(np.percentile(per, 99)))
+    rate, mean_ms = replicas.job_throughput(n, float(np.mean(per)))
     st = P.status()
     # one simulation per launch: every box has its own pool and context
     singles = [pool.Pool([b], prm(), stream=P.stream) for b in boxes]
@@ -310,17 +316,17 @@ def run_batch(args, world: int, rank: int, local: int):
     P.stream.synchronize()
     plain_ms = e0.elapsed_time(e1) / args.steps
     line = {
-        "metric": "batched SPH step p50/p99 latency (256 boxes)", "value": float(np.percentile(per, 50)),
+        "metric": "batched SPH step p50/p99 latency (256 boxes)", "value": p50,
         "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "boxes": n_boxes, "particles": n,
                    "desc": "periodic unit boxes, N log-uniform in [1e3, 1e5], even: jittered "
                            "lattice, odd: 4 Plummer spheres + background",
                    "tuned": over},
-        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
-        "particle_updates_per_s": n / (float(np.mean(per)) / 1e3),
+        "p50_ms": p50, "p99_ms": p99,
+        "particle_updates_per_s": rate,
         "plain_ms_per_step": plain_ms, "plain_particle_updates_per_s": n / (plain_ms / 1e3),
-        "speedup_vs_plain": plain_ms / float(np.mean(per)),
+        "speedup_vs_plain": plain_ms / mean_ms,
         "gpu_launches": launches_per_step(n, n_boxes, bool(over["flags"] & sph.SPH_FLAG_TREE)) * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
@@ -343,7 +349,7 @@ def run_served(args, world: int, rank: int, local: int):
 
     from paper_2305_13380_gb300 import build as B
     B.build()
-    from paper_2305_13380_gb300 import inputs, serve, sph
+    from paper_2305_13380_gb300 import inputs, replicas, serve, sph
 
     n_sims = int(args.workload[len("served"):] or 1000)
     t_gen = time.perf_counter()
@@ -383,8 +389,15 @@ def run_served(args, world: int, rank: int, local: int):
     up0, ev0 = srv.uploads, srv.evictions
     clocks = Clocks(None)
     time.sleep(0.25)
+    replicas.barrier()
     out = srv.run(trace)
+    replicas.barrier()
     clk = clocks.stop()
+    # replicas: the slowest rank's latencies, the requests of all ranks
+    out["p50_ms"] = replicas.max_over_ranks(out["p50_ms"])
+    out["p99_ms"] = replicas.max_over_ranks(out["p99_ms"])
+    req_rate, _ = replicas.job_throughput(out["requests"], 1e3 * out["wall_s"])
+    upd_rate = replicas.sum_over_ranks(out["particle_updates_per_s"])
     paging = {"uploads": srv.uploads - up0, "evictions": srv.evictions - ev0}
     # the same trace, one simulation per launch on one stream
     srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
@@ -404,8 +417,8 @@ def run_served(args, world: int, rank: int, local: int):
                    "budget_gb": budget / 1e9, "generation_s": gen_s, "admission_s": adm_s,
                    "tuned": over},
         "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "mean_ms": out["mean_ms"],
-        "requests_per_s": out["requests"] / out["wall_s"],
-        "particle_updates_per_s": out["particle_updates_per_s"],
+        "requests_per_s": req_rate,
+        "particle_updates_per_s": upd_rate,
         "mean_sims_per_batch": out["mean_sims_per_batch"],
         "paging": paging,
         "saturated_requests_per_s": cap_rate,
@@ -432,20 +445,29 @@ def main():
     if args.impl == "reference":
         return run_reference(args, world, rank)
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
     torch.cuda.set_device(local)
-    if args.workload.startswith("batch"):
-        return run_batch(args, world, rank, local)
-    if args.workload.startswith("served"):
-        return run_served(args, world, rank, local)
     if world > 1:
         dist.init_process_group("nccl")
+    if args.workload.startswith("batch"):
+        run_batch(args, world, rank, local)
+    elif args.workload.startswith("served"):
+        run_served(args, world, rank, local)
+    else:
+        run_step(args, world, rank, local)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_step(args, world: int, rank: int, local: int):
+    """The single-simulation workloads (latticeN, clusteredN): one sph_step
+    of the whole box per step."""
+    import torch
     from paper_2305_13380_gb300 import build as B
     B.build()
-    from paper_2305_13380_gb300 import sph
+    from paper_2305_13380_gb300 import replicas, sph
 
     p = make_workload(args.workload)
     n = len(p["x"])
@@ -497,8 +519,7 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(gpu_id)
     time.sleep(0.25)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     e0.record(stream)
@@ -507,17 +528,12 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
     kt = sph.sph_kernel_times(ctx)
     st = sph.sph_status(ctx)
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * n * args.steps / (ms / 1e3)
+    # every rank advances its own copy: units of all ranks over the slowest time
+    value, ms = replicas.job_throughput(n * args.steps, e0.elapsed_time(e1))
 
     # one more step (untimed) that counts pairs and Newton passes
     cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | tree))
@@ -546,8 +562,7 @@ def main():
             host[k].copy_(arrays[k], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_value = world * n * args.e2e_steps / (e2e_ms / 1e3)
+    e2e_value, e2e_ms = replicas.job_throughput(n * args.e2e_steps, e0.elapsed_time(e1))
     if sph.sph_status(e2e_ctx):
         raise SystemExit("device status set in the end-to-end run")
 
@@ -603,8 +618,6 @@ def main():
     }
     if rank == 0:
         print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
 
 
 if __name__ == "__main__":
