@@ -14,9 +14,10 @@
 //     so that n_hat = S_w / H^3 and dn_hat/dh = -S_dw / (h H^3).  The
 //     iteration of the paper, h <- h - f/f' with f = n_hat - (eta/h)^3 and
 //     f' = dn_hat/dh + 3 eta^3 / h^4, is h <- h (1 - A/B) with
-//     A = S_w/gamma_K^3 - eta^3, B = 3 eta^3 - S_dw/gamma_K^3, taken in FP64;
-//     a target stops when |A/B| <= h_tol, with that last correction applied
-//     (or at the cell cap / max_h_iter);
+//     A = S_w/gamma_K^3 - eta^3, B = 3 eta^3 - S_dw/gamma_K^3 (newton_update:
+//     the convergence test in FP64, the update in FP32); a target stops when
+//     |A/B| <= h_tol, with that last correction applied (or at the cell cap
+//     / max_h_iter);
 //  3. a final pass at the converged h accumulates, in FP32,
 //        S_mw = sum m_j w,  S_mdw = sum m_j (3 w + q w'),
 //        S_div = sum m_j g (v_j - v_i) . x_ij,  S_curl = sum m_j g (v_i - v_j) x x_ij,
@@ -91,52 +92,16 @@ __device__ __forceinline__ void dens_pair(const float4& pi, const float4& vi, co
   s.npair += q < 1.0f;
 }
 
-// One Newton-Raphson decision for a target whose pass at h gave (S_w, S_dw).
-// The relative correction is delta = A/B.  When |delta| <= h_tol the target
-// is finished and the correction is applied: Newton converges quadratically,
-// so the result is within ~2 delta^2 of the root (1e-4 -> 2e-8).  Returns
-// true when the target is finished (converged, capped or out of
-// iterations); otherwise advances h.
-__device__ __forceinline__ bool newton_step(float Sw, float Sdw, double& h, double& lo, double& hi,
-                                            int& it, double hcap, const PhysDev& ph, bool& atcap,
-                                            bool& conv) {
-  const double g3 = kGammaKd * kGammaKd * kGammaKd;
-  const double eta3 = (double)ph.eta3;
-  const double A = (double)Sw / g3 - eta3;
-  const double B = 3.0 * eta3 - (double)Sdw / g3;
-  if (A < 0.0) lo = h; else hi = h;
-  conv = (B > 0.0) && (fabs(A) <= ph.h_tol * B);
-  atcap = (h >= hcap) && (A < 0.0);
-  const bool last = it + 1 >= ph.max_h_iter;
-  if (conv) {
-    h = h * (1.0 - A / B);
-    if (h > hcap) {
-      h = hcap;
-      atcap = true;
-    }
-    return true;
-  }
-  if (atcap || last) return true;
-  double hn = (B > 0.0) ? h * (1.0 - A / B) : 2.0 * h;
-  hn = fmin(fmax(hn, 0.5 * h), 2.0 * h);
-  if (!(B > 0.0) || !(hn > lo) || !(hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
-  if (hn > hcap) hn = hcap;
-  h = hn;
-  ++it;
-  return false;
-}
-
-__device__ __forceinline__ double start_h(float h0, double hcap) {
-  double h = (double)h0;
-  if (!(h > 0.0)) h = 0.5 * hcap;
+__device__ __forceinline__ float start_h(float h0, float hcap) {
+  const float h = h0 > 0.0f ? h0 : 0.5f * hcap;
   return h > hcap ? hcap : h;
 }
 
 // Writes the outputs of one target (sorted index ti) from its sums at h.
 __device__ __forceinline__ void dens_write(const sphh::DensityArgs& a, const PhysDev& ph, int32_t ti,
-                                           double h, const DensSums& s, float u_i, int passes,
+                                           float h, const DensSums& s, float u_i, int passes,
                                            bool conv, bool atcap) {
-  const float H = kGammaK * (float)h;
+  const float H = kGammaK * h;
   const float Hinv = 1.0f / H;
   const float H2inv = Hinv * Hinv;
   const int32_t p = a.perm[ti];
@@ -146,7 +111,7 @@ __device__ __forceinline__ void dens_write(const sphh::DensityArgs& a, const Phy
   const float curl = sqrtf(fmaf(s.cx, s.cx, fmaf(s.cy, s.cy, s.cz * s.cz))) * H2inv / s.mw;
   const float P = (ph.gamma - 1.0f) * u_i * rho;
   const float cs = sqrtf(ph.gamma * P / rho);
-  const float hf = (float)h;
+  const float hf = h;
   const float B_i = fabsf(div) / (fabsf(div) + curl + ph.eps_balsara * cs / hf);
   // a support that outgrew its cell: twice the cap is the next starting guess,
   // so that each rebuild at least doubles the cells it needs
@@ -195,6 +160,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
   float* lr2 = lr2_all + warp * (kListRows * 32);
   uint16_t* lj = lj_all + warp * (kListRows * 32);
   const int32_t total = a.misc_ro[kTotalBlocks];
+  const NewtonConst nwt = newton_const(ph);
   unsigned long long pair_acc = 0;
 
   for (int32_t b = blockIdx.x; b < total; b += gridDim.x) {
@@ -219,7 +185,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
     }
     build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
 
-    const double hcap = fmin((double)g.G.cell_f, 0.5 * g.G.L) * (1.0 - 1e-5) / kGammaKd;
+    const float hcap = h_cap((double)g.G.cell_f, g.G.L);
     const float R2 = g.G.cell_f * g.G.cell_f;
     const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
     const int sub = lane & (tpp - 1);
@@ -280,12 +246,12 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
         }
       }
       // 2. Newton-Raphson passes over the list (or over all runs if it overflowed)
-      double h = valid ? start_h(a.hs[ti], hcap) : hcap;
-      double lo = 0.0, hi = INFINITY;
+      float h = valid ? start_h(a.hs[ti], hcap) : hcap;
+      float lo = 0.0f, hi = INFINITY;
       bool done = !valid, atcap = false, conv = false;
       int it = 0, passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
-        const float H = kGammaK * (float)h;
+        const float H = kGammaK * h;
         const float Hinv = 1.0f / H;
         float Sw0 = 0.f, Sdw0 = 0.f, Sw1 = 0.f, Sdw1 = 0.f;
         if (!done && !direct) {
@@ -338,11 +304,11 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
         }
         if (!done) {
           passes = it + 1;
-          if (newton_step(Sw, Sdw, h, lo, hi, it, hcap, ph, atcap, conv)) done = true;
+          if (newton_update(Sw, Sdw, nwt, hcap, h, lo, hi, it, atcap, conv)) done = true;
         }
       }
       // 3. final pass at the converged h
-      const float H = kGammaK * (float)h;
+      const float H = kGammaK * h;
       const float Hinv = 1.0f / H;
       DensSums s0, s1;
       sums_zero(s0);
@@ -396,6 +362,7 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
   float4* spos = osm + warp * (2 * kOvfCap);
   float4* svel = spos + kOvfCap;
   const int32_t n_items = a.misc_ro[kNumOverflow] * kBlkWarps;
+  const NewtonConst nwt = newton_const(ph);
   unsigned long long pair_acc = 0;
   for (int32_t item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
        item += gridDim.x * kWarpsPerBlock) {
@@ -416,19 +383,19 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
       spos[slot] = p;
       svel[slot] = a.vel4[j];
     };
-    const double hcap = fmin((double)g.G.cell_f, 0.5 * g.G.L) * (1.0 - 1e-5) / kGammaKd;
+    const float hcap = h_cap((double)g.G.cell_f, g.G.L);
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
       const bool valid = ti < te;
       const float4 pi = valid ? a.pos4[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 vi = valid ? a.vel4[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
-      double h = valid ? start_h(a.hs[ti], hcap) : hcap;
-      double lo = 0.0, hi = INFINITY;
+      float h = valid ? start_h(a.hs[ti], hcap) : hcap;
+      float lo = 0.0f, hi = INFINITY;
       bool done = !valid, atcap = false, conv = false;
       int it = 0;
       int passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
-        const float H = kGammaK * (float)h;
+        const float H = kGammaK * h;
         const float Hinv = 1.0f / H;
         DensSums s;
         sums_zero(s);
@@ -439,12 +406,12 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
         }
         if (!done) {
           passes = it + 1;
-          if (newton_step(s.w, s.dw, h, lo, hi, it, hcap, ph, atcap, conv)) done = true;
+          if (newton_update(s.w, s.dw, nwt, hcap, h, lo, hi, it, atcap, conv)) done = true;
         }
       }
       // final pass at the converged h
       {
-        const float H = kGammaK * (float)h;
+        const float H = kGammaK * h;
         const float Hinv = 1.0f / H;
         DensSums s;
         sums_zero(s);

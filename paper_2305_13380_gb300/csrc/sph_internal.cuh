@@ -53,6 +53,71 @@ struct PhysDev {
   int32_t count_pairs;
 };
 
+// One Newton-Raphson update of the smoothing length (Sec. 3.1): the root of
+// f(h) = n_hat(h) - (eta / h)^3, from the sums of a pass at h,
+//   S_w = sum_j w(q),   S_dw = sum_j (3 w + q w'(q)),   q = r / H,
+// so that with A = S_w / gamma_K^3 - eta^3 and B = 3 eta^3 - S_dw / gamma_K^3
+// the Newton step is h <- h (1 - A/B).
+//
+// The convergence test |A| <= h_tol B runs in FP64 on gamma_K^3 A and
+// gamma_K^3 B (a positive scale changes neither the test nor the ratio A/B):
+// those are one FP64 subtraction each from the FP32 sums.  The update itself
+// runs in FP32, whose rounding (~1e-7 relative) is far below h_tol; this
+// keeps FP64 division, slow on this GPU, out of the loop.  A finished target
+// gets its last correction applied (Newton converges quadratically, so the
+// result is within ~2 (A/B)^2 of the root).  Safeguards: the step is clamped
+// to [h/2, 2h] and falls back to bisection of the bracket [lo, hi] when it
+// leaves it or B <= 0; h never exceeds hcap.  Returns true when the target
+// is done (converged, capped, or out of iterations); otherwise advances h.
+struct NewtonConst {
+  double a0;  // gamma_K^3 eta^3
+  double b0;  // 3 gamma_K^3 eta^3
+  double tol;
+  int32_t max_it;
+};
+
+__device__ __forceinline__ NewtonConst newton_const(const PhysDev& ph) {
+  const double g3 = kGammaKd * kGammaKd * kGammaKd;
+  NewtonConst c;
+  c.a0 = g3 * (double)ph.eta3;
+  c.b0 = 3.0 * c.a0;
+  c.tol = ph.h_tol;
+  c.max_it = ph.max_h_iter;
+  return c;
+}
+
+__device__ __forceinline__ bool newton_update(float Sw, float Sdw, const NewtonConst& nc, float hcap,
+                                              float& h, float& lo, float& hi, int& it, bool& atcap,
+                                              bool& conv) {
+  const double A = (double)Sw - nc.a0;
+  const double B = nc.b0 - (double)Sdw;
+  if (A < 0.0) lo = h; else hi = h;
+  conv = (B > 0.0) && (fabs(A) <= nc.tol * B);
+  atcap = (h >= hcap) && (A < 0.0);
+  const float d = (float)A / (float)B;
+  if (conv) {
+    h = h * (1.0f - d);
+    if (h > hcap) {
+      h = hcap;
+      atcap = true;
+    }
+    return true;
+  }
+  if (atcap || it + 1 >= nc.max_it) return true;
+  float hn = (B > 0.0) ? h * (1.0f - d) : 2.0f * h;
+  hn = fminf(fmaxf(hn, 0.5f * h), 2.0f * h);
+  if (!(B > 0.0) || !(hn > lo) || !(hn < hi)) hn = isinf(hi) ? 2.0f * h : 0.5f * (lo + hi);
+  if (hn > hcap) hn = hcap;
+  h = hn;
+  ++it;
+  return false;
+}
+
+// The largest h whose support gamma_K h stays below `side` (and half the box).
+__device__ __forceinline__ float h_cap(double side, double L) {
+  return (float)(fmin(side, 0.5 * L) * (1.0 - 1e-5) / kGammaKd);
+}
+
 // Simulation owning a pool index (upper bound search over sim_offset).
 __device__ __forceinline__ int sim_of_particle(const int64_t* __restrict__ sim_offset, int n_sims,
                                                int64_t p) {

@@ -172,37 +172,6 @@ __device__ __forceinline__ void tnewton_pair(float r2, float H, float Hinv, floa
   Sdw += fmaf(q * q, g, 3.0f * w);
 }
 
-// One Newton-Raphson update of f(h) = n-hat(h) - (eta / h)^3 (Sec. 3.1),
-// with the bracket and cap safeguards of density.cu.  Returns true when the
-// target is done.
-__device__ __forceinline__ bool tnewton(float Sw, float Sdw, double& h, double& lo, double& hi, int& it,
-                                        double hcap, const PhysDev& ph, bool& atcap, bool& conv) {
-  const double g3 = kGammaKd * kGammaKd * kGammaKd;
-  const double eta3 = (double)ph.eta3;
-  const double A = (double)Sw / g3 - eta3;
-  const double B = 3.0 * eta3 - (double)Sdw / g3;
-  if (A < 0.0) lo = h; else hi = h;
-  conv = (B > 0.0) && (fabs(A) <= ph.h_tol * B);
-  atcap = (h >= hcap) && (A < 0.0);
-  const bool last = it + 1 >= ph.max_h_iter;
-  if (conv) {
-    h = h * (1.0 - A / B);
-    if (h > hcap) {
-      h = hcap;
-      atcap = true;
-    }
-    return true;
-  }
-  if (atcap || last) return true;
-  double hn = (B > 0.0) ? h * (1.0 - A / B) : 2.0 * h;
-  hn = fmin(fmax(hn, 0.5 * h), 2.0 * h);
-  if (!(B > 0.0) || !(hn > lo) || !(hn < hi)) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
-  if (hn > hcap) hn = hcap;
-  h = hn;
-  ++it;
-  return false;
-}
-
 // Sum over the kTreeTpp lanes of a target (called by all 32 lanes).
 __device__ __forceinline__ float gsum(float v) {
 #pragma unroll
@@ -449,9 +418,9 @@ __device__ __forceinline__ uint64_t reverse_rec(int32_t j, int32_t ti, int sc) {
 // Outputs of target ti (source index) from its sums at h (Sec. 3.1 and the
 // equation of state of Sec. 3.2).
 __device__ __forceinline__ void tdens_write(const sphh::TreeDensityArgs& a, const PhysDev& ph, int32_t ti,
-                                            double h, const TDSums& s, float u_i, int passes, bool noconv) {
+                                            float h, const TDSums& s, float u_i, int passes, bool noconv) {
   const int32_t p = a.perm[ti];
-  const float H = kGammaK * (float)h;
+  const float H = kGammaK * h;
   const float Hinv = 1.0f / H;
   const float H2inv = Hinv * Hinv;
   const float rho = s.mw * H2inv * Hinv;
@@ -460,7 +429,7 @@ __device__ __forceinline__ void tdens_write(const sphh::TreeDensityArgs& a, cons
   const float curl = sqrtf(fmaf(s.cx, s.cx, fmaf(s.cy, s.cy, s.cz * s.cz))) * H2inv / s.mw;
   const float P = (ph.gamma - 1.0f) * u_i * rho;
   const float cs = sqrtf(ph.gamma * P / rho);
-  const float hf = (float)h;
+  const float hf = h;
   a.h[p] = hf;
   a.rho[p] = rho;
   a.f[p] = fval;
@@ -476,6 +445,7 @@ __device__ __forceinline__ void tdens_write(const sphh::TreeDensityArgs& a, cons
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const NewtonConst nwt = newton_const(ph);
   unsigned char* base = tsm + (size_t)warp * kTWarpSmem;
   float4* spos = reinterpret_cast<float4*>(base);
   uint32_t* sidx = reinterpret_cast<uint32_t*>(spos + kTCap);
@@ -492,7 +462,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
     const TGeo g = leaf_geo(Lf, G);
     const TRanges R = load_ranges(a.ranges, li, lane);
     const int nsrc = R.nsrc;
-    const double hcap = fmin(g.side_d, 0.5 * g.L) * (1.0 - 1e-5) / kGammaKd;
+    const float hcap = h_cap(g.side_d, g.L);
     const bool one_chunk = nsrc <= kTCap;
     // children are half the cell (a cell at the deepest level has one child)
     const float cside = Lf.depth < kTreeDepth ? 0.5f * g.side : g.side;
@@ -545,19 +515,19 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       // their lists.  The flag is shared by the target's lanes.
       bool mydirect = group_any(cnt > kTreeList, lane);
       // 2. Newton-Raphson passes
-      double h = valid ? (double)a.hs[ti] : hcap;
-      if (!(h > 0.0)) h = 0.5 * hcap;
+      float h = valid ? a.hs[ti] : hcap;
+      if (!(h > 0.0f)) h = 0.5f * hcap;
       if (h > hcap) h = hcap;
       {
         // evaluated by every lane (a ballot), then merged
-        const bool outgrown = group_any(valid && kGammaK * (float)h > Ri, lane);
+        const bool outgrown = group_any(valid && kGammaK * h > Ri, lane);
         mydirect = mydirect || outgrown;
       }
-      double hlo = 0.0, hhi = INFINITY;
+      float hlo = 0.0f, hhi = INFINITY;
       bool done = !valid, atcap = false, conv = false;
       int it = 0, passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
-        const float H = kGammaK * (float)h;
+        const float H = kGammaK * h;
         const float Hinv = 1.0f / H;
         float Sw = 0.f, Sdw = 0.f;
         if (!mydirect && !done)
@@ -574,14 +544,14 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         Sdw = gsum(Sdw);
         if (!done) {
           passes = it + 1;
-          if (tnewton(Sw, Sdw, h, hlo, hhi, it, hcap, ph, atcap, conv)) done = true;
+          if (newton_update(Sw, Sdw, nwt, hcap, h, hlo, hhi, it, atcap, conv)) done = true;
         }
         // the list holds r < R_i: a support beyond it needs every staged source
-        const bool outgrown = group_any(valid && kGammaK * (float)h > Ri, lane);
+        const bool outgrown = group_any(valid && kGammaK * h > Ri, lane);
         mydirect = mydirect || outgrown;
       }
       // 3. final pass at h
-      const float H = kGammaK * (float)h;
+      const float H = kGammaK * h;
       const float Hinv = 1.0f / H;
       const float H2 = H * H;
       TDSums s;
@@ -884,6 +854,7 @@ __device__ __forceinline__ TRanges cell_ranges(const GridDev& G, const TreeLeaf&
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const NewtonConst nwt = newton_const(ph);
   unsigned char* base = tsm + (size_t)warp * kTWarpSmem;
   float4* spos = reinterpret_cast<float4*>(base);
   uint32_t* sidx = reinterpret_cast<uint32_t*>(spos + kTCap);
@@ -896,7 +867,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     const float4 reli = a.rel[ti];
     const int4 fi = a.fine[ti];
     const float4 vi = a.vel4[ti];
-    double h = (double)a.h[a.perm[ti]];  // the capped h of the first solve
+    float h = a.h[a.perm[ti]];  // the capped h of the first solve
     bool conv = false, atcap = true;
     int passes = 0, d = (int)a.level[ti] - 1;
     if (d < 0) {
@@ -905,7 +876,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
       if (lane == 0) {
         atomicOr(a.status, SPH_ST_REBUILD);
         a.fb_level[ti] = 0;
-        a.h[a.perm[ti]] = 2.0f * (float)h;
+        a.h[a.perm[ti]] = 2.0f * h;
       }
       __syncwarp();
       continue;
@@ -919,15 +890,15 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
       g = leaf_geo(Lc, G);
       R = cell_ranges(G, Lc, a.skey, a.cell_start, lane);
       pi = rel_to(g, reli, fi, kNoShift);
-      const double hcap = fmin(g.side_d, 0.5 * g.L) * (1.0 - 1e-5) / kGammaKd;
+      const float hcap = h_cap(g.side_d, g.L);
       one_chunk = R.nsrc <= kTCap;
       if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx);
-      double hlo = 0.0, hhi = INFINITY;
+      float hlo = 0.0f, hhi = INFINITY;
       int it = 0;
       if (h > hcap) h = hcap;
       bool done = false;
       while (!done) {  // warp-uniform: every lane holds the same reduced sums
-        const float H = kGammaK * (float)h;
+        const float H = kGammaK * h;
         const float Hinv = 1.0f / H;
         float Sw = 0.f, Sdw = 0.f;
         for (int v0 = 0; v0 < R.nsrc; v0 += kTCap) {
@@ -938,7 +909,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
         Sw = wsum(Sw);
         Sdw = wsum(Sdw);
         ++passes;
-        done = tnewton(Sw, Sdw, h, hlo, hhi, it, hcap, ph, atcap, conv);
+        done = newton_update(Sw, Sdw, nwt, hcap, h, hlo, hhi, it, atcap, conv);
       }
       if (!atcap) break;
     }
@@ -948,7 +919,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
       d = 0;
     }
     // final pass at h, reverse pairs of this target
-    const float H = kGammaK * (float)h;
+    const float H = kGammaK * h;
     const float Hinv = 1.0f / H;
     const float H2 = H * H;
     TDSums s;
@@ -986,7 +957,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     s.npair = wsumi(s.npair);
     if (lane == 0) {
       tdens_write(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
-      if (atcap) a.h[a.perm[ti]] = 2.0f * (float)h;  // next starting guess
+      if (atcap) a.h[a.perm[ti]] = 2.0f * h;  // next starting guess
       a.fb_level[ti] = (int8_t)d;
       pair_acc += (unsigned long long)s.npair;
     }
