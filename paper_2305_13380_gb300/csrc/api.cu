@@ -40,7 +40,7 @@ struct sph_ctx {
   float4 *pos4 = nullptr, *vel4 = nullptr, *th4 = nullptr;
   float* hs = nullptr;
   float2* fD = nullptr;
-  unsigned long long* dt_bits = nullptr;
+  unsigned* dt_bits = nullptr;
   int32_t* hmax_bits = nullptr;
   uint16_t *lists = nullptr, *list_cnt = nullptr;
   bool lists_valid = false;  // lists belong to the current build

@@ -86,6 +86,7 @@ __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const doubl
     g.n_c = nc;
     g.cell = L / (double)nc;
     g.cell_f = (float)g.cell;
+    g.scale_f = (float)((double)nc / L);
     g.cell_base = 0;
     g.blk_base = 0;
     g.part_base = a;
@@ -123,13 +124,16 @@ __global__ void k_key_count(int64_t n_total, const double* __restrict__ x, const
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = sim_of_particle(sim_offset, n_sims, p);
     const GridDev G = grid[s];
-    const int32_t kx = cell_coord(x[p], G.L, G.n_c);
-    const int32_t ky = cell_coord(y[p], G.L, G.n_c);
-    const int32_t kz = cell_coord(z[p], G.L, G.n_c);
+    const int32_t kx = cell_coord_fast(x[p], G.L, G.n_c, G.scale_f);
+    const int32_t ky = cell_coord_fast(y[p], G.L, G.n_c, G.scale_f);
+    const int32_t kz = cell_coord_fast(z[p], G.L, G.n_c, G.scale_f);
     const int32_t k = G.cell_base + kx + G.n_c * (ky + G.n_c * kz);
     key[p] = k;
     sort_key[p] = k;
-    atomicAdd(&count[k], 1);
+    // neighbours in index order often share a cell: one atomic per distinct
+    // cell of the converged lanes
+    const unsigned peers = __match_any_sync(__activemask(), k);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[k], __popc(peers));
   }
 }
 
@@ -166,11 +170,9 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* tota
 }
 
 // count[0 .. total) -> out (tile-local exclusive), tile sums -> sums
-__global__ void k_scan_tiles(const int32_t* __restrict__ count, int32_t* __restrict__ out,
-                             int32_t* __restrict__ sums, const int32_t* __restrict__ misc) {
-  const int32_t total = misc[kTotalCells];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  if (base >= total) return;
+__device__ __forceinline__ void scan_tile(const int32_t* __restrict__ count, int32_t* __restrict__ out,
+                                          int32_t* __restrict__ sums, int32_t total, int64_t tile) {
+  const int64_t base = tile * kScanTile;
   int32_t v[kScanItems];
   int32_t s = 0;
 #pragma unroll
@@ -187,7 +189,16 @@ __global__ void k_scan_tiles(const int32_t* __restrict__ count, int32_t* __restr
     if (c < total) out[c] = run;
     run += v[i];
   }
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+  if (threadIdx.x == 0) sums[tile] = tot;
+}
+
+// (tiles in a block-uniform grid-stride loop: the grid is sized for the
+// capacity, the cell count is only known on the device)
+__global__ void k_scan_tiles(const int32_t* __restrict__ count, int32_t* __restrict__ out,
+                             int32_t* __restrict__ sums, const int32_t* __restrict__ misc) {
+  const int32_t total = misc[kTotalCells];
+  for (int64_t tile = blockIdx.x; tile * kScanTile < total; tile += gridDim.x)
+    scan_tile(count, out, sums, total, tile);
 }
 
 // single block: exclusive scan of the tile sums; writes out[total] = grand total
@@ -210,12 +221,13 @@ __global__ void k_scan_sums(int32_t* __restrict__ sums, int32_t* __restrict__ ou
 __global__ void k_scan_add(int32_t* __restrict__ out, const int32_t* __restrict__ sums,
                            const int32_t* __restrict__ misc) {
   const int32_t total = misc[kTotalCells];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  if (base >= total) return;
-  const int32_t add = sums[blockIdx.x];
-  for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
-    const int64_t c = base + i;
-    if (c < total) out[c] += add;
+  for (int64_t tile = blockIdx.x; tile * kScanTile < total; tile += gridDim.x) {
+    const int64_t base = tile * kScanTile;
+    const int32_t add = sums[tile];
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+      const int64_t c = base + i;
+      if (c < total) out[c] += add;
+    }
   }
 }
 
@@ -300,16 +312,18 @@ cudaError_t launch_build(const BuildArgs& a, cudaStream_t st) {
   k_grid_setup<<<(a.n_sims + 127) / 128, 128, 0, st>>>(a.sim_offset, a.box, a.hmax_bits, a.n_sims,
                                                        a.margin, a.grid, a.misc);
   k_grid_base<<<1, 32, 0, st>>>(a.grid, a.n_sims, a.misc);
-  const int zb = grid_for(a.cap_cells + 1, 256, 65535);
+  // grids sized for the capacity but capped: the kernels loop up to the
+  // device-side cell count, and idle blocks would only cost launch time
+  const int zb = grid_for(a.cap_cells + 1, 256, a.num_sms * 8);
   k_zero_counts<<<zb, 256, 0, st>>>(a.count, a.misc);
   const int pb = grid_for(a.n_total, 256, 65535);
   if (a.n_total > 0)
     k_key_count<<<pb, 256, 0, st>>>(a.n_total, a.x, a.y, a.z, a.sim_offset, a.n_sims, a.grid, a.key,
                                     a.slot, a.count);  // slot receives a copy of the keys to sort
-  const int64_t tiles = (a.cap_cells + kScanTile - 1) / kScanTile;
-  k_scan_tiles<<<(unsigned)(tiles > 0 ? tiles : 1), kScanThreads, 0, st>>>(a.count, a.cell_start, a.scan_sums, a.misc);
+  const int tb = grid_for(a.cap_cells, kScanTile, a.num_sms * 4);
+  k_scan_tiles<<<tb, kScanThreads, 0, st>>>(a.count, a.cell_start, a.scan_sums, a.misc);
   k_scan_sums<<<1, kScanThreads, 0, st>>>(a.scan_sums, a.cell_start, a.misc);
-  k_scan_add<<<(unsigned)(tiles > 0 ? tiles : 1), kScanThreads, 0, st>>>(a.cell_start, a.scan_sums, a.misc);
+  k_scan_add<<<tb, kScanThreads, 0, st>>>(a.cell_start, a.scan_sums, a.misc);
   if (a.n_total > 0 && a.sort_cells) {
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) <= a.cap_cells) ++bits;

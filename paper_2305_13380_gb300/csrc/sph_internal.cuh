@@ -37,6 +37,7 @@ struct GridDev {
   int32_t n_c;        // cells per side
   int32_t cell_base;  // first global cell id of this simulation
   int32_t blk_base;   // first global 2x2x2-block id of this simulation
+  float scale_f;      // n_c / L in FP32 (estimates of cell coordinates)
   int64_t part_base;  // first pool index of this simulation
   int64_t n;          // particles in this simulation
 };
@@ -146,6 +147,32 @@ __device__ __forceinline__ int32_t cell_coord(double x, double L, int32_t n_c) {
   int32_t k = (int32_t)floor(s);
   k = k < 0 ? 0 : k;
   return k > n_c - 1 ? n_c - 1 : k;
+}
+
+// The same k with FP64 work only near cell faces.  FP64 division is slow on
+// this GPU, so an FP32 estimate comes first: x truncated to an FP32 value by
+// integer operations on its bits (sign, exponent and the leading 20 mantissa
+// bits: relative error below 2^-20) times scale_f = fl32(n_c / L).  Its
+// relative error is below 2^-20 + 2^-23, i.e. under 1.1e-6 n_c in absolute
+// terms over [0, L).  When the estimate lies farther than 4e-6 n_c from an
+// integer, the exact quotient has the same floor; otherwise, and for x that
+// is negative, zero, tiny, huge or not a number, the exact FP64 path decides.
+// The result is bit-identical to cell_coord.
+__device__ __forceinline__ int32_t cell_coord_fast(double x, double L, int32_t n_c, float scale_f) {
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (hi > 0 && e > 0 && e < 255) {
+    const float s = __int_as_float((e << 23) | ((hi & 0xfffff) << 3)) * scale_f;
+    const float k = floorf(s);
+    const float fr = s - k;
+    const float tol = 4e-6f * (float)n_c;
+    if (fr >= tol && fr <= 1.0f - tol) {
+      int32_t ki = (int32_t)k;
+      ki = ki < 0 ? 0 : ki;
+      return ki > n_c - 1 ? n_c - 1 : ki;
+    }
+  }
+  return cell_coord(x, L, n_c);
 }
 
 // Cubic spline pieces with q = r/H (Sec. 3.1): w(q) and g(q) = w'(q)/q,

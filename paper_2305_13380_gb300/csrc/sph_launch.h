@@ -246,7 +246,7 @@ struct StepArgs {
   float *ax, *ay, *az, *du_dt, *v_sig;
   float *vpx, *vpy, *vpz, *up;  // predicted velocity / energy (scratch)
   double* dt;                   // per simulation
-  unsigned long long* dt_bits;  // per simulation scratch (min of H / v_sig as FP64 bits)
+  unsigned* dt_bits;  // per simulation scratch (min of h / v_sig as FP32 bits)
   int32_t* status;
 };
 cudaError_t launch_dt(const StepArgs& a, cudaStream_t st);  // uses a.dt_bits scratch

@@ -18,69 +18,85 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// dt_s = C_CFL min_i H_i / v_sig,i over simulation s.  Non-negative doubles
-// order like their bit patterns, so the minimum is taken with an integer
-// atomicMin on the bits: each thread keeps a running minimum for the
-// simulation it is in, lanes of one simulation combine with shuffles, and one
-// lane per group publishes.  Particles with v_sig = 0 do not limit dt; a
-// simulation without any signal velocity gets dt = 0.
-constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+// dt_s = C_CFL min_i H_i / v_sig,i over simulation s, as C_CFL gamma_K
+// min_i (h_i / v_sig,i): each quotient is one correctly rounded FP32
+// division (FP64 division is slow on this GPU), the minimum is exact, and the
+// scaling by C_CFL gamma_K is FP64.  Non-negative floats order like their bit
+// patterns, so the minimum is taken with an integer atomicMin on the bits:
+// each thread keeps a running minimum for the simulation it is in, lanes of
+// one simulation combine with shuffles, and one lane per group publishes.
+// Particles with v_sig = 0 do not limit dt; a simulation without any signal
+// velocity gets dt = 0.
+constexpr unsigned kInfBits32 = 0x7f800000u;
 
-__global__ void k_dt_init(unsigned long long* __restrict__ bits, int n_sims) {
+__global__ void k_dt_init(unsigned* __restrict__ bits, int n_sims) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x)
-    bits[s] = kInfBits;
+    bits[s] = kInfBits32;
 }
 
 __global__ void k_dt_min(const int64_t* __restrict__ sim_offset, int n_sims, int64_t n_total,
                          const float* __restrict__ h, const float* __restrict__ v_sig,
-                         unsigned long long* __restrict__ bits) {
+                         unsigned* __restrict__ bits) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int cur = -1;
-  double m = INFINITY;
+  float m = INFINITY;
   for (; p < n_total; p += stride) {
     const int s = sim_of_particle(sim_offset, n_sims, p);
     if (s != cur) {
-      if (cur >= 0 && m < INFINITY) atomicMin(&bits[cur], (unsigned long long)__double_as_longlong(m));
+      if (cur >= 0 && m < INFINITY) atomicMin(&bits[cur], __float_as_uint(m));
       cur = s;
       m = INFINITY;
     }
-    const double vs = (double)v_sig[p];
-    if (vs > 0.0) m = fmin(m, kGammaKd * (double)h[p] / vs);
+    const float vs = v_sig[p];
+    if (vs > 0.0f) m = fminf(m, __fdiv_rn(h[p], vs));
   }
   // lanes holding the same simulation combine, then one of them publishes
   const unsigned grp = __match_any_sync(0xffffffffu, cur);
   const int lane = threadIdx.x & 31;
   for (int o = 0; o < 32; ++o) {
-    const double other = __shfl_sync(0xffffffffu, m, o);
-    if ((grp >> o) & 1u) m = fmin(m, other);
+    const float other = __shfl_sync(0xffffffffu, m, o);
+    if ((grp >> o) & 1u) m = fminf(m, other);
   }
-  if (cur >= 0 && m < INFINITY && lane == __ffs(grp) - 1)
-    atomicMin(&bits[cur], (unsigned long long)__double_as_longlong(m));
+  if (cur >= 0 && m < INFINITY && lane == __ffs(grp) - 1) atomicMin(&bits[cur], __float_as_uint(m));
 }
 
-__global__ void k_dt_final(const unsigned long long* __restrict__ bits, int n_sims, double cfl,
+__global__ void k_dt_final(const unsigned* __restrict__ bits, int n_sims, double cfl,
                            double* __restrict__ dt) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x) {
-    const double m = __longlong_as_double((long long)bits[s]);
-    dt[s] = isinf(m) ? 0.0 : cfl * m;
+    const float m = __uint_as_float(bits[s]);
+    dt[s] = isinf(m) ? 0.0 : cfl * kGammaKd * (double)m;
   }
 }
 
+// One periodic wrap: x < 0 -> x + L, then x >= L -> x - L.  The tests use
+// the bit patterns (integer compares instead of FP64 ones: non-negative
+// doubles order like their bits, and -0.0 counts as not negative), with the
+// same results for every input including NaN.
 __device__ __forceinline__ double wrap1(double x, double L) {
-  if (x < 0.0) x += L;
-  if (x >= L) x -= L;
+  long long b = __double_as_longlong(x);
+  if (b < 0 && (b << 1) != 0) {
+    x += L;
+    b = __double_as_longlong(x);
+  }
+  if (b >= __double_as_longlong(L)) x -= L;
   return x;
 }
 
 // First half kick, drift (FP64, one periodic wrap), prediction for the loops.
 __global__ void k_kick_drift(sphh::StepArgs a) {
+  int cur = -1;
+  double dt = 0.0, L = 0.0;
+  float hdt = 0.0f;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = sim_of_particle(a.sim_offset, a.n_sims, p);
-    const double dt = a.dt[s];
-    const double L = a.box[s];
-    const float hdt = (float)(0.5 * dt);
+    if (s != cur) {  // the simulation's dt and box, converted once
+      cur = s;
+      dt = a.dt[s];
+      L = a.box[s];
+      hdt = (float)(0.5 * dt);
+    }
     const float vx = fmaf(hdt, a.ax[p], a.vx[p]);
     const float vy = fmaf(hdt, a.ay[p], a.vy[p]);
     const float vz = fmaf(hdt, a.az[p], a.vz[p]);
@@ -103,10 +119,15 @@ __global__ void k_kick_drift(sphh::StepArgs a) {
 
 // Second half kick with the new accelerations.
 __global__ void k_kick(sphh::StepArgs a) {
+  int cur = -1;
+  float hdt = 0.0f;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = sim_of_particle(a.sim_offset, a.n_sims, p);
-    const float hdt = (float)(0.5 * a.dt[s]);
+    if (s != cur) {
+      cur = s;
+      hdt = (float)(0.5 * a.dt[s]);
+    }
     a.vx[p] = fmaf(hdt, a.ax[p], a.vx[p]);
     a.vy[p] = fmaf(hdt, a.ay[p], a.vy[p]);
     a.vz[p] = fmaf(hdt, a.az[p], a.vz[p]);

@@ -49,6 +49,40 @@ def test_cells_bit_exact(orc, case):
         assert np.diff(cs).max() > 32
 
 
+@pytest.mark.parametrize("L", [1.0, 0.7])
+def test_cells_bit_exact_at_cell_faces(orc, L):
+    # positions on cell faces and a few ulps either side: the FP32 estimate
+    # of the cell coordinate is then too close to an integer to decide, and
+    # the FP64 path must give the oracle's key (FP64 product and quotient)
+    p = inputs.lattice(12, seed=5)
+    p = dict(p)
+    for k in ("x", "y", "z"):
+        p[k] = np.asarray(p[k], dtype=np.float64) * L
+    p["h0"] = np.asarray(p["h0"]) * L
+    p["L"] = L
+    q = as_f32(p)
+    nc = expected_nc(q["h0"], L, n=len(p["x"]))
+    rng = np.random.default_rng(7)
+    n = len(p["x"])
+    for ax in ("x", "y", "z"):
+        pick = rng.random(n) < 0.4
+        k = rng.integers(0, nc, n)
+        face = k.astype(np.float64) * L / nc
+        steps = rng.integers(-3, 4, n)
+        v = face.copy()
+        for _ in range(3):
+            v = np.where(steps > 0, np.nextafter(v, np.inf), v)
+            v = np.where(steps < 0, np.nextafter(v, -np.inf), v)
+            steps = steps - np.sign(steps)
+        v = np.where(v < 0.0, face, v)
+        p[ax] = np.where(pick, v, p[ax])
+    got_nc, cs, perm = _cells(p)
+    assert got_nc == nc
+    ocs, operm = orc.build_cells(p["x"], p["y"], p["z"], L, nc)
+    assert np.array_equal(cs, ocs)
+    assert np.array_equal(perm, operm)
+
+
 def test_density_force_lattice_4096(orc):
     p = inputs.lattice(16)
     q = as_f32(p)
