@@ -536,8 +536,10 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
 int do_force(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
              const float* vy, const float* vz, const float* m, const float* h, const float* rho,
              const float* f, const float* P, const float* cs, const float* B, float* ax, float* ay,
-             float* az, float* du_dt, float* v_sig) {
+             float* az, float* du_dt, float* v_sig, bool pos_ready = false) {
   sphh::GatherForceArgs g;
+  // the nested-grid force reads positions from its own copies (fA.w only)
+  g.positions = (pos_ready || c->built_tree) ? 0 : 1;
   g.n_total = c->built_n;
   g.n_sims = c->built_sims;
   g.perm = c->perm;
@@ -887,8 +889,10 @@ int sph_step(sph_ctx* c, const sph_pool* pl) {
     // h now holds the capped values; the next build sizes the cells from
     // them with the margin, which makes every cell larger.
   }
+  // same build and positions as the density just run: its gather already
+  // wrote the cell-relative positions into the buffer the force reads
   rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P,
-                pl->c, pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig);
+                pl->c, pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig, true);
   if (rc != SPH_OK) return rc;
   t_begin(c, SPH_T_INTEGRATE);
   if (sphh::launch_kick(s, c->st) != cudaSuccess) return SPH_E_CUDA;

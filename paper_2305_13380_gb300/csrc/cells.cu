@@ -259,6 +259,11 @@ __global__ void k_gather_density(int64_t n_total, const int32_t* __restrict__ pe
 
 // Sorted copies for the force loop: position relative to the own cell with
 // the support H, velocity with the mass, (f P / rho^2, f, c, B), (rho, 1/H).
+// kPos = false: fA.xyz already holds this build's positions (the density
+// gather of the same step wrote them, or the nested-grid loops, which read
+// positions elsewhere, do not use them); only H is written, and no FP64
+// arithmetic is needed.
+template <bool kPos>
 __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm,
                                const int32_t* __restrict__ key, const GridDev* __restrict__ grid,
                                int n_sims, const double* __restrict__ x, const double* __restrict__ y,
@@ -273,15 +278,19 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_total;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p = perm[s];
-    const int32_t cc = key[p];
-    const GridDev G = grid[sim_of_cell(grid, n_sims, cc)];
-    const int32_t local = cc - G.cell_base;
-    const int32_t kx = local % G.n_c, ky = (local / G.n_c) % G.n_c, kz = local / (G.n_c * G.n_c);
-    const float rx = (float)(x[p] - (double)kx * G.cell);
-    const float ry = (float)(y[p] - (double)ky * G.cell);
-    const float rz = (float)(z[p] - (double)kz * G.cell);
     const float H = kGammaK * h[p];
-    fA[s] = make_float4(rx, ry, rz, H);
+    if (kPos) {
+      const int32_t cc = key[p];
+      const GridDev G = grid[sim_of_cell(grid, n_sims, cc)];
+      const int32_t local = cc - G.cell_base;
+      const int32_t kx = local % G.n_c, ky = (local / G.n_c) % G.n_c, kz = local / (G.n_c * G.n_c);
+      const float rx = (float)(x[p] - (double)kx * G.cell);
+      const float ry = (float)(y[p] - (double)ky * G.cell);
+      const float rz = (float)(z[p] - (double)kz * G.cell);
+      fA[s] = make_float4(rx, ry, rz, H);
+    } else {
+      reinterpret_cast<float*>(fA)[4 * s + 3] = H;
+    }
     fB[s] = make_float4(vx[p], vy[p], vz[p], m[p]);
     const float r = rho[p];
     fC[s] = make_float4(f[p] * P[p] / (r * r), f[p], c[p], B[p]);
@@ -343,7 +352,8 @@ cudaError_t launch_gather_density(const GatherDensityArgs& a, cudaStream_t st) {
 
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st) {
   if (a.n_total <= 0) return cudaSuccess;
-  k_gather_force<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
+  auto kern = a.positions ? k_gather_force<true> : k_gather_force<false>;
+  kern<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
       a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.h, a.rho,
       a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD);
   return cudaGetLastError();

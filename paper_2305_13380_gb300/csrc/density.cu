@@ -7,8 +7,8 @@
 // cells of <= 8 particles, else 2) that split the sources between them.
 //
 //  1. filter: each lane keeps, in its own column of a shared-memory list, the
-//     sources closer than the cell size (any support H <= cell can only
-//     reach those) together with their squared distance;
+//     staged slots of the sources closer than the cell size (any support
+//     H <= cell can only reach those);
 //  2. Newton-Raphson passes run over the list only, accumulating
 //        S_w = sum_j w(q),   S_dw = sum_j (3 w + q w'(q)),   q = r / H,
 //     so that n_hat = S_w / H^3 and dn_hat/dh = -S_dw / (h H^3).  The
@@ -38,10 +38,19 @@ namespace sphk {
 constexpr int kDensBlkCap = kBlkStageCap;  // staged sources per block
 constexpr int kListCap = kLaneListCap;     // list entries per lane
 constexpr int kListRows = kListCap + 1;    // + one scratch row for the branch-free append
+// The list keeps each entry's r^2 for the Newton passes (kCacheR2), or only
+// the slot, the passes then recomputing r^2 from the staged position.  The
+// slots alone leave room for three resident blocks per SM instead of two
+// (79 registers, 66 KB of shared memory per block), which was measured
+// 10 % faster on the 2M lattice: the loop is latency-bound, and the
+// recomputation costs less than the extra warps gain.
+constexpr bool kCacheR2 = false;
+constexpr int kDensMinBlocks = 3;  // resident blocks per SM the registers are sized for
 // shared memory: staged sources (32 B each), per-warp lists (r^2, slot),
 // the staging table, the block's target rounds and its target slots/cells
 constexpr size_t kDensBlkSmem = (size_t)kDensBlkCap * 2 * sizeof(float4) +
-                                (size_t)kBlkWarps * kListRows * 32 * (sizeof(float) + sizeof(uint16_t)) +
+                                (size_t)kBlkWarps * kListRows * 32 *
+                                    ((kCacheR2 ? sizeof(float) : 0) + sizeof(uint16_t)) +
                                 sizeof(StageTable) + sizeof(BlockTargets) +
                                 (size_t)kDensBlkCap * (sizeof(uint16_t) + sizeof(uint8_t));
 constexpr int kOvfCap = 256;  // per-warp staging of the overflow kernel
@@ -128,6 +137,16 @@ __device__ __forceinline__ void dens_write(const sphh::DensityArgs& a, const Phy
   else if (!conv) atomicOr(a.status, SPH_ST_H_NOCONV);
 }
 
+// r^2 of list entry `at` of a lane: cached, or recomputed (same operands,
+// same result) from the staged position.
+__device__ __forceinline__ float list_r2(const float* lr2, const uint16_t* lj, const float4* spos,
+                                         const float4& pi, int at) {
+  if (kCacheR2) return lr2[at];
+  const float4 pj = spos[lj[at]];
+  const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
 __device__ __forceinline__ void combine(DensSums& s, int tpp) {
 #pragma unroll
   for (int o = 1; o < 4; o <<= 1) {
@@ -145,13 +164,13 @@ __device__ __forceinline__ void combine(DensSums& s, int tpp) {
   }
 }
 
-__global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a, PhysDev ph) {
+__global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::DensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   float4* spos = reinterpret_cast<float4*>(dsm_raw);
   float4* svel = spos + kDensBlkCap;
   // per-lane list entries (r^2, staged slot), column layout [entry][lane]
   float* lr2_all = reinterpret_cast<float*>(svel + kDensBlkCap);
-  uint16_t* lj_all = reinterpret_cast<uint16_t*>(lr2_all + kBlkWarps * kListRows * 32);
+  uint16_t* lj_all = reinterpret_cast<uint16_t*>(lr2_all + (kCacheR2 ? kBlkWarps * kListRows * 32 : 0));
   StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * kListRows * 32);
   BlockTargets& BT = *reinterpret_cast<BlockTargets*>(&T + 1);
   uint16_t* tgt_slot = reinterpret_cast<uint16_t*>(&BT + 1);
@@ -189,7 +208,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
     const float R2 = g.G.cell_f * g.G.cell_f;
     const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
     const int sub = lane & (tpp - 1);
-    for (int rd = warp; rd < BT.rounds; rd += kBlkWarps) {
+    for (int rd = warp; rd < BT.rounds; rd = next_round(BT, lane)) {
       const int t = lane >> lg;
       const int32_t e_t = rd * per + t;
       const bool valid = (t < per) && (e_t < BT.n);
@@ -202,6 +221,8 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
       const int32_t ti = T.gstart[kc] + (slot_i - T.start[kc]);  // sorted index
       const float4 pi = spos[slot_i];
       const float4 vi = svel[slot_i];
+      // the starting h, loaded now so that its latency hides behind the filter
+      const float h_start = valid ? a.hs[ti] : 0.0f;
       // 1. filter into the lane's own list column
       int cnt = 0;
       if (valid) {
@@ -218,7 +239,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
             // kept only if in range; once the list is full, writes go to the
             // scratch row kListCap (such a lane takes the direct path)
             const int at = min(cnt, kListCap) * 32 + lane;
-            lr2[at] = r2;
+            if (kCacheR2) lr2[at] = r2;
             lj[at] = (uint16_t)k;
             cnt += r2 < R2;
           }
@@ -246,7 +267,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
         }
       }
       // 2. Newton-Raphson passes over the list (or over all runs if it overflowed)
-      float h = valid ? start_h(a.hs[ti], hcap) : hcap;
+      float h = valid ? start_h(h_start, hcap) : hcap;
       float lo = 0.0f, hi = INFINITY;
       bool done = !valid, atcap = false, conv = false;
       int it = 0, passes = 0;
@@ -257,8 +278,8 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
         if (!done && !direct) {
           int e = 0;
           for (; e + 1 < cnt; e += 2) {
-            const float r2a = lr2[e * 32 + lane];
-            const float r2b = lr2[(e + 1) * 32 + lane];
+            const float r2a = list_r2(lr2, lj, spos, pi, e * 32 + lane);
+            const float r2b = list_r2(lr2, lj, spos, pi, (e + 1) * 32 + lane);
             const float ria = rsqrtf(fmaxf(r2a, 1e-30f)), rib = rsqrtf(fmaxf(r2b, 1e-30f));
             const float qa = r2a * ria * Hinv, qb = r2b * rib * Hinv;
             float wa, ga, wb, gb;
@@ -270,7 +291,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_density(sphh::DensityArgs a,
             Sdw1 += fmaf(qb * qb, gb, 3.0f * wb);
           }
           if (e < cnt) {
-            const float r2a = lr2[e * 32 + lane];
+            const float r2a = list_r2(lr2, lj, spos, pi, e * 32 + lane);
             const float ria = rsqrtf(fmaxf(r2a, 1e-30f));
             const float qa = r2a * ria * Hinv;
             float wa, ga;

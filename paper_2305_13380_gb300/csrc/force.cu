@@ -101,6 +101,28 @@ __device__ __forceinline__ void fcombine(ForceSums& s, int tpp) {
   }
 }
 
+// The density loop's list of this lane for round rd (same build, same
+// rounds): its count (0xffff if it overflowed or the lane has no target) and
+// all kFListCap entries as 16-byte words, loaded without waiting on the count
+// so that the loads overlap other memory traffic; words beyond the count are
+// never read.
+__device__ __forceinline__ void fetch_list(const sphh::ForceArgs& a, const BlockTargets& BT,
+                                           const StageTable& T, const uint16_t* tgt_slot,
+                                           const uint8_t* tgt_cell, int rd, int lane, int& lc,
+                                           uint4 (&w)[kFListCap / 8]) {
+  const int t = lane >> BT.lg, sub = lane & (BT.tpp - 1);
+  const int32_t e_t = rd * BT.per + t;
+  lc = 0xffff;
+  if (t >= BT.per || e_t >= BT.n) return;
+  const int kc = BT.cell_k[tgt_cell[e_t]];
+  const int32_t ti = T.gstart[kc] + (tgt_slot[e_t] - T.start[kc]);
+  const int64_t col = (int64_t)ti * 4 + sub;
+  lc = (int)a.list_cnt[col];
+  const uint4* src = reinterpret_cast<const uint4*>(a.lists + col * kListRegion);
+#pragma unroll
+  for (int q = 0; q < kFListCap / 8; ++q) w[q] = src[q];
+}
+
 __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char fsm_raw[];
   float4* sA = reinterpret_cast<float4*>(fsm_raw);
@@ -125,6 +147,14 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
       __syncthreads();
       continue;
     }
+    // the targets' rounds first (they need only the table), so that each
+    // warp's first list is in flight together with the staging loads
+    build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+    const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
+    const int sub = lane & (tpp - 1);
+    int pre_lc = 0xffff;
+    uint4 pre[kFListCap / 8];
+    if (a.lists != nullptr && warp < BT.rounds) fetch_list(a, BT, T, tgt_slot, tgt_cell, warp, lane, pre_lc, pre);
     for (int32_t v = threadIdx.x; v < nsrc; v += kBlkThreads) {
       const int k = staged_cell_of(T, v);
       float ox, oy, oz;
@@ -139,11 +169,9 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
       sC[v] = a.fC[j];
       sD[v] = a.fD[j];
     }
-    build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+    __syncthreads();
 
-    const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
-    const int sub = lane & (tpp - 1);
-    for (int rd = warp; rd < BT.rounds; rd += kBlkWarps) {
+    for (int rd = warp; rd < BT.rounds; rd = next_round(BT, lane)) {
       const int t = lane >> lg;
       const int32_t e_t = rd * per + t;
       const bool valid = (t < per) && (e_t < BT.n);
@@ -154,6 +182,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
       }
       const int tx = kc % g.ex - 1, ty = (kc / g.ex) % g.ey - 1, tz = kc / (g.ex * g.ey) - 1;
       const int32_t ti = T.gstart[kc] + (self_slot - T.start[kc]);
+      if (a.lists != nullptr && rd != warp) fetch_list(a, BT, T, tgt_slot, tgt_cell, rd, lane, pre_lc, pre);
       ForceTarget Tg;
       Tg.A = sA[self_slot];
       Tg.B = sB[self_slot];
@@ -165,20 +194,21 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
       fsums_zero(s1);
       // the density loop's list of this lane (same build, same rounds): all
       // sources within the cell size, a superset of r < max(H_i, H_j)
-      const int64_t col = (int64_t)ti * 4 + sub;
       int cnt = -1;
       if (a.lists != nullptr && valid) {
-        const int lc = (int)a.list_cnt[col];
+        const int lc = pre_lc;
         if (lc <= kFListCap) {
-          const uint4* src = reinterpret_cast<const uint4*>(a.lists + col * kListRegion);
-          for (int e8 = 0; e8 < lc; e8 += 8) {
-            const uint4 v = src[e8 >> 3];
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int e0 = e8 + 2 * q;
-              if (e0 < lc) lj[e0 * 32 + lane] = (uint16_t)(w[q] & 0xffffu);
-              if (e0 + 1 < lc) lj[(e0 + 1) * 32 + lane] = (uint16_t)(w[q] >> 16);
+          for (int e8 = 0; e8 < kFListCap; e8 += 8) {
+            if (e8 < lc) {
+              const uint4 v = pre[e8 >> 3];
+              const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int e0 = e8 + 2 * q;
+                if (e0 < lc) lj[e0 * 32 + lane] = (uint16_t)(w[q] & 0xffffu);
+                if (e0 + 1 < lc) lj[(e0 + 1) * 32 + lane] = (uint16_t)(w[q] >> 16);
+              }
             }
           }
           cnt = lc;

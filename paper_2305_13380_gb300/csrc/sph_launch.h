@@ -66,6 +66,9 @@ struct GatherForceArgs {
   const float *vx, *vy, *vz, *m, *h, *rho, *f, *P, *c, *B;
   float4 *fA, *fB, *fC;
   float2* fD;
+  // 1: compute fA.xyz from x, y, z; 0: fA.xyz already holds them (or is not
+  // read), write H only
+  int positions = 1;
 };
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
 
