@@ -282,22 +282,22 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
             const float r2b = list_r2(lr2, lj, spos, pi, (e + 1) * 32 + lane);
             const float ria = rsqrtf(fmaxf(r2a, 1e-30f)), rib = rsqrtf(fmaxf(r2b, 1e-30f));
             const float qa = r2a * ria * Hinv, qb = r2b * rib * Hinv;
-            float wa, ga, wb, gb;
-            kernel_w_g(qa, H * ria, wa, ga);
-            kernel_w_g(qb, H * rib, wb, gb);
+            float wa, dwa, wb, dwb;
+            kernel_w_dw(qa, wa, dwa);
+            kernel_w_dw(qb, wb, dwb);
             Sw0 += wa;
             Sw1 += wb;
-            Sdw0 += fmaf(qa * qa, ga, 3.0f * wa);
-            Sdw1 += fmaf(qb * qb, gb, 3.0f * wb);
+            Sdw0 += dwa;
+            Sdw1 += dwb;
           }
           if (e < cnt) {
             const float r2a = list_r2(lr2, lj, spos, pi, e * 32 + lane);
             const float ria = rsqrtf(fmaxf(r2a, 1e-30f));
             const float qa = r2a * ria * Hinv;
-            float wa, ga;
-            kernel_w_g(qa, H * ria, wa, ga);
+            float wa, dwa;
+            kernel_w_dw(qa, wa, dwa);
             Sw0 += wa;
-            Sdw0 += fmaf(qa * qa, ga, 3.0f * wa);
+            Sdw0 += dwa;
           }
         } else if (!done) {
           for (int r = 0; r < 9; ++r) {
@@ -309,10 +309,10 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
               const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
               const float ri = rsqrtf(fmaxf(r2, 1e-30f));
               const float q = r2 * ri * Hinv;
-              float w, gg;
-              kernel_w_g(q, H * ri, w, gg);
+              float w, dw;
+              kernel_w_dw(q, w, dw);
               Sw0 += w;
-              Sdw0 += fmaf(q * q, gg, 3.0f * w);
+              Sdw0 += dw;
             }
           }
         }

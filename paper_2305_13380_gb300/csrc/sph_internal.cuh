@@ -189,6 +189,24 @@ __device__ __forceinline__ void kernel_w_g(float q, float H_rinv, float& w, floa
   g = inner ? g_in : g_out;
 }
 
+// w(q) and 3 w(q) + q w'(q), the two sums of the Newton passes, without
+// the gradient: on the inner piece 8/pi (1 - 6q^2 + 6q^3) and
+// 8/pi (3 - 30 q^2 + 36 q^3), on the outer piece 16/pi (1-q)^3 and
+// 48/pi (1-q)^2 (1 - 2q); both vanish for q >= 1.
+__device__ __forceinline__ void kernel_w_dw(float q, float& w, float& dw) {
+  const float c = kWNorm;
+  const float q2 = q * q;
+  const float w_in = fmaf(q2, fmaf(6.0f * c, q, -6.0f * c), c);
+  const float dw_in = fmaf(q2, fmaf(36.0f * c, q, -30.0f * c), 3.0f * c);
+  const float a = fmaxf(1.0f - q, 0.0f);
+  const float a2 = a * a;
+  const float w_out = (2.0f * c) * a2 * a;
+  const float dw_out = a2 * fmaf(-12.0f * c, q, 6.0f * c);
+  const bool inner = q < 0.5f;
+  w = inner ? w_in : w_out;
+  dw = inner ? dw_in : dw_out;
+}
+
 // g(q) = w'(q)/q only.
 __device__ __forceinline__ float kernel_g(float q, float H_rinv) {
   const float a = fmaxf(1.0f - q, 0.0f);

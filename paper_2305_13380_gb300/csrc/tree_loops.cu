@@ -166,10 +166,10 @@ __device__ __forceinline__ void tdens_pair(float dx, float dy, float dz, const f
 __device__ __forceinline__ void tnewton_pair(float r2, float H, float Hinv, float& Sw, float& Sdw) {
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float q = r2 * rinv * Hinv;
-  float w, g;
-  kernel_w_g(q, H * rinv, w, g);
+  float w, dw;
+  kernel_w_dw(q, w, dw);
   Sw += w;
-  Sdw += fmaf(q * q, g, 3.0f * w);
+  Sdw += dw;
 }
 
 // Sum over the kTreeTpp lanes of a target (called by all 32 lanes).
@@ -712,7 +712,7 @@ __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const 
 }
 
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs a, PhysDev ph) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
   const int32_t nl = *a.n_leaves;
   unsigned long long pair_acc = 0;
