@@ -24,6 +24,7 @@ namespace sphk {
 
 constexpr int kForceBlkCap = kBlkStageCap;
 constexpr int kFListCap = 48;
+constexpr int kFListEager = 4;  // 16-byte list words loaded before the count is known
 // per source: A (x, y, z, H), B (vx, vy, vz, m), C (fP, f, c, B), D (rho, 1/H)
 constexpr size_t kForceBlkSmem = (size_t)kForceBlkCap * (3 * sizeof(float4) + sizeof(float2)) +
                                  (size_t)kBlkWarps * kFListCap * 32 * sizeof(uint16_t) + sizeof(StageTable) +
@@ -103,9 +104,10 @@ __device__ __forceinline__ void fcombine(ForceSums& s, int tpp) {
 
 // The density loop's list of this lane for round rd (same build, same
 // rounds): its count (0xffff if it overflowed or the lane has no target) and
-// all kFListCap entries as 16-byte words, loaded without waiting on the count
-// so that the loads overlap other memory traffic; words beyond the count are
-// never read.
+// its entries as 16-byte words.  The first kFListEager words (which hold the
+// typical list) are loaded without waiting on the count, so that they
+// overlap other memory traffic; the rest only when the count needs them.
+// Words beyond the count are never used.
 __device__ __forceinline__ void fetch_list(const sphh::ForceArgs& a, const BlockTargets& BT,
                                            const StageTable& T, const uint16_t* tgt_slot,
                                            const uint8_t* tgt_cell, int rd, int lane, int& lc,
@@ -120,7 +122,10 @@ __device__ __forceinline__ void fetch_list(const sphh::ForceArgs& a, const Block
   lc = (int)a.list_cnt[col];
   const uint4* src = reinterpret_cast<const uint4*>(a.lists + col * kListRegion);
 #pragma unroll
-  for (int q = 0; q < kFListCap / 8; ++q) w[q] = src[q];
+  for (int q = 0; q < kFListEager; ++q) w[q] = src[q];
+#pragma unroll
+  for (int q = kFListEager; q < kFListCap / 8; ++q)
+    if (8 * q < lc && lc <= kFListCap) w[q] = src[q];
 }
 
 __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, PhysDev ph) {
