@@ -474,11 +474,26 @@ def run_step(args, world: int, rank: int, local: int):
     L = float(p["L"])
     t = sph.to_device(p)
     dev = "cuda"
-    f32 = lambda: torch.empty(n, dtype=torch.float32, device=dev)  # noqa: E731
-    arrays = dict(x=t["x"], y=t["y"], z=t["z"], vx=t["vx"], vy=t["vy"], vz=t["vz"], u=t["u"],
-                  m=t["m"], h=f32(), ax=f32(), ay=f32(), az=f32(), du_dt=f32(), v_sig=f32(),
-                  rho=f32(), f=f32(), div_v=f32(), curl_v=f32(), P=f32(), c=f32(), balsara=f32(),
-                  dt=torch.zeros(1, dtype=torch.float64, device=dev))
+    # The state lives in one device buffer, in the order of the end-to-end
+    # copies: the fields a step updates, then m, then the density outputs.
+    # A caller that keeps its host copy in the same layout moves a step's
+    # inputs and results with one copy each way.
+    f64_keys = ("x", "y", "z")
+    f32_keys = ("vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du_dt", "v_sig", "m",
+                "rho", "f", "div_v", "curl_v", "P", "c", "balsara")
+    offs, size = {}, 0
+    for k in f64_keys + f32_keys:
+        offs[k] = size
+        size += -(-n * (8 if k in f64_keys else 4) // 256) * 256
+    dbuf = torch.empty(max(size, 256), dtype=torch.uint8, device=dev)
+    arrays = {}
+    for k in f64_keys + f32_keys:
+        wide = k in f64_keys
+        arrays[k] = dbuf[offs[k]:offs[k] + n * (8 if wide else 4)].view(
+            torch.float64 if wide else torch.float32)
+    for k in ("x", "y", "z", "vx", "vy", "vz", "u", "m"):
+        arrays[k].copy_(t[k])
+    arrays["dt"] = torch.zeros(1, dtype=torch.float64, device=dev)
     sim_offset = torch.tensor([0, n], dtype=torch.int64, device=dev)
     box = torch.tensor([L], dtype=torch.float64, device=dev)
 
@@ -544,22 +559,20 @@ def run_step(args, world: int, rank: int, local: int):
     mean_pass = float(arrays.pop("n_iter").double().mean().item())
     cnt.close()
 
-    # end to end: state in pinned host memory, copied in and out every step
-    in_keys = ("x", "y", "z", "vx", "vy", "vz", "u", "m", "h", "ax", "ay", "az", "du_dt", "v_sig")
-    out_keys = ("x", "y", "z", "vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du_dt", "v_sig")
-    host = {k: arrays[k].cpu().pin_memory() for k in in_keys}
-    bi = sum(host[k].numel() * host[k].element_size() for k in in_keys)
-    bo = sum(host[k].numel() * host[k].element_size() for k in out_keys)
+    # end to end: the state in pinned host memory, in the device layout; every
+    # step copies x .. v_sig and m in (one copy) and x .. v_sig out (one copy)
+    bi = offs["m"] + 4 * n          # x, y, z, v, u, h, a, du/dt, v_sig, m
+    bo = offs["m"]                  # the same without m, which a step does not change
+    host = torch.empty(bi, dtype=torch.uint8, pin_memory=True)
+    host.copy_(dbuf[:bi])
     e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=tree))
     for it in range(2 + args.e2e_steps):
         if it == 2:
             torch.cuda.synchronize()
             e0.record(stream)
-        for k in in_keys:
-            arrays[k].copy_(host[k], non_blocking=True)
+        dbuf[:bi].copy_(host, non_blocking=True)
         sph.sph_step(e2e_ctx, pool)
-        for k in out_keys:
-            host[k].copy_(arrays[k], non_blocking=True)
+        host[:bo].copy_(dbuf[:bo], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_value, e2e_ms = replicas.job_throughput(n * args.e2e_steps, e0.elapsed_time(e1))
