@@ -38,7 +38,7 @@ F_DENSITY = 66
 F_FORCE = 72
 
 
-def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False) -> int:
+def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False, axis: bool = False) -> int:
     """Kernel launches of one sph_step over n_total particles.
 
     Uniform grid: time-step reduction (3), kick/drift (1), cell build (8 + the
@@ -48,7 +48,8 @@ def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False) -> int:
     64-bit radix sorts of 30 + c and 34 + c bits, c the cell-id bits, plus
     key, source keys, levels, target keys, flags, a 3-kernel scan, groups,
     count, neighbour ranges: 12), the tree gather (1), density with the
-    reverse-pair grouping (6), force gather (1), force (1)."""
+    reverse-pair grouping (6), force gather (1), force (1).  Sorted
+    interactions on the uniform grid add the per-cell axis orders (1)."""
     cap = 8 * n_total + 216 * n_sims
     cbits = 1
     while cbits < 30 and (1 << cbits) <= cap:
@@ -56,7 +57,7 @@ def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False) -> int:
     radix = lambda bits: 1 + 5 * ((bits + 7) // 8)  # noqa: E731
     integrate = 3 + 1 + 1
     if not tree:
-        return integrate + 8 + radix(cbits) + 2 + 2 + 2
+        return integrate + 8 + radix(cbits) + 2 + 2 + 2 + (1 if axis else 0)
     return integrate + 8 + radix(30 + cbits) + radix(34 + cbits) + 12 + 1 + 6 + 1 + 1
 FP32_LANES_PER_SM = 128
 
@@ -76,6 +77,8 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--axis-sort", action="store_true",
+                    help="uniform grid: sorted interactions in the density filter")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle work for the whole --impl reference run")
     return ap.parse_args()
@@ -498,8 +501,10 @@ def run_step(args, world: int, rank: int, local: int):
     box = torch.tensor([L], dtype=torch.float64, device=dev)
 
     tree = sph.SPH_FLAG_TREE if p["tree"] else 0
+    # grid-mode flags of every context of the run
+    mode = tree | (sph.SPH_FLAG_AXIS_SORT if args.axis_sort and not tree else 0)
     # initial density + force (untimed) through the single-simulation calls
-    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | tree))
+    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | mode))
     part = sph.particles(t)
     dout = sph.density_out({k: arrays[k] for k in sph.DENSITY_FIELDS})
     h_in = t["h0"]
@@ -515,7 +520,7 @@ def run_step(args, world: int, rank: int, local: int):
     sph.sph_force(init, cells, part, dout, sph.force_out({k: arrays[k] for k in sph.FORCE_FIELDS}))
     init.close()
 
-    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | tree))
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | mode))
     pool = sph.pool(sim_offset, box, arrays)
     for _ in range(args.warmup):
         sph.sph_step(ctx, pool)
@@ -551,7 +556,7 @@ def run_step(args, world: int, rank: int, local: int):
     value, ms = replicas.job_throughput(n * args.steps, e0.elapsed_time(e1))
 
     # one more step (untimed) that counts pairs and Newton passes
-    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | tree))
+    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | mode))
     arrays["n_iter"] = torch.zeros(n, dtype=torch.int32, device=dev)
     sph.sph_step(cnt, sph.pool(sim_offset, box, arrays))
     pairs_d, pairs_f = sph.sph_pair_counts(cnt)
@@ -565,7 +570,7 @@ def run_step(args, world: int, rank: int, local: int):
     bo = offs["m"]                  # the same without m, which a step does not change
     host = torch.empty(bi, dtype=torch.uint8, pin_memory=True)
     host.copy_(dbuf[:bi])
-    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=tree))
+    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=mode))
     for it in range(2 + args.e2e_steps):
         if it == 2:
             torch.cuda.synchronize()
@@ -612,10 +617,12 @@ def run_step(args, world: int, rank: int, local: int):
         "config": {"workload": args.workload, "desc": p["desc"], "particles_per_gpu": n,
                    "step": "sph_step: dt, kick+drift, cell build, density (h solve), force, kick",
                    "l2": "inputs larger than L2: each step touches ~0.5 GB of state and scratch",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "grid": ("nested grids" if tree else
+                            "uniform, sorted interactions" if mode & sph.SPH_FLAG_AXIS_SORT else "uniform")},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "steps": args.e2e_steps},
-        "gpu_launches": launches_per_step(n, 1, bool(tree)) * args.steps,
+        "gpu_launches": launches_per_step(n, 1, bool(tree), bool(mode & sph.SPH_FLAG_AXIS_SORT)) * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "roofline": roofline,

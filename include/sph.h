@@ -65,8 +65,18 @@ enum {
   SPH_FLAG_SYNC = 1,        /* wait after each call, return device status    */
   SPH_FLAG_COUNT_PAIRS = 2, /* count in-support pairs (diagnostics, slower)  */
   SPH_FLAG_TIMING = 4,      /* record CUDA events around each kernel group   */
-  SPH_FLAG_TREE = 8         /* nested grids below the top cells (Sec. 2.1 and
+  SPH_FLAG_TREE = 8,        /* nested grids below the top cells (Sec. 2.1 and
                                9.1) for smoothing lengths that span decades   */
+  SPH_FLAG_AXIS_SORT = 16   /* uniform grid: sorted interactions (Sec. 2.2).
+                               After each density gather, every cell's
+                               particles are ranked along the 13 axes that
+                               link it to its neighbours (kAxes x n u16 of
+                               context scratch); the density filter walks
+                               each neighbour cell along its axis, nearest
+                               first, and stops where the distance along the
+                               axis reaches the search radius.  Same
+                               neighbour sets as without the flag, summed in
+                               another order.  Ignored with SPH_FLAG_TREE.  */
 };
 
 /* Kernel groups timed with SPH_FLAG_TIMING (index into sph_kernel_times). */

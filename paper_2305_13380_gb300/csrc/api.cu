@@ -44,6 +44,8 @@ struct sph_ctx {
   int32_t* hmax_bits = nullptr;
   uint16_t *lists = nullptr, *list_cnt = nullptr;
   bool lists_valid = false;  // lists belong to the current build
+  uint16_t* axis = nullptr;  // per-cell axis orders (SPH_FLAG_AXIS_SORT), kAxes * cap_axis
+  int64_t cap_axis = 0;
   float *vpx = nullptr, *vpy = nullptr, *vpz = nullptr, *up = nullptr;
   // nested-grid scratch (SPH_FLAG_TREE), grown separately
   int64_t cap_tree = 0;
@@ -115,6 +117,8 @@ void free_grown(sph_ctx* c) {
   dfree(c->hmax_bits);
   dfree(c->lists);
   dfree(c->list_cnt);
+  dfree(c->axis);
+  c->cap_axis = 0;
   dfree(c->vpx);
   dfree(c->vpy);
   dfree(c->vpz);
@@ -209,11 +213,13 @@ int ensure(sph_ctx* c, int64_t n, int n_sims) {
             dalloc(c->dt_bits, cs) && dalloc(c->hmax_bits, cs) &&
             dalloc(c->lists, (int64_t)sphk::kListRegion * 4 * cn) &&
             dalloc(c->list_cnt, (int64_t)(sphk::kTreeTpp > 4 ? sphk::kTreeTpp : 4) * cn) &&
-            dalloc(c->vpx, cn) && dalloc(c->vpy, cn) && dalloc(c->vpz, cn) && dalloc(c->up, cn);
+            dalloc(c->vpx, cn) && dalloc(c->vpy, cn) && dalloc(c->vpz, cn) && dalloc(c->up, cn) &&
+            (!(c->p.flags & SPH_FLAG_AXIS_SORT) || dalloc(c->axis, (int64_t)sphk::kAxes * cn));
   if (!ok) {
     free_grown(c);
     return SPH_E_NOMEM;
   }
+  if (c->p.flags & SPH_FLAG_AXIS_SORT) c->cap_axis = cn;
   c->cap_n = cn;
   c->cap_sims = cs;
   c->cap_cells = cc;
@@ -497,6 +503,21 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   g.hs = c->hs;
   t_begin(c, SPH_T_GATHER);
   if (sphh::launch_gather_density(g, c->st) != cudaSuccess) return SPH_E_CUDA;
+  const bool axis = (c->p.flags & SPH_FLAG_AXIS_SORT) != 0;
+  if (axis) {
+    // per-cell orders along the neighbour axes, from this gather's positions
+    // (the buffer is sized with the other scratch, so nothing is allocated
+    // here, e.g. during graph capture)
+    if (c->cap_axis < c->built_n) return SPH_E_INVAL;
+    sphh::AxisSortArgs x;
+    x.n_total = c->built_n;
+    x.perm = c->perm;
+    x.key = c->key;
+    x.cell_start = c->cell_start;
+    x.pos4 = c->pos4;
+    x.order = c->axis;
+    if (sphh::launch_axis_sort(x, c->st) != cudaSuccess) return SPH_E_CUDA;
+  }
   t_end(c, SPH_T_GATHER);
   if (c->p.flags & SPH_FLAG_COUNT_PAIRS)
     if (cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
@@ -526,6 +547,8 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   d.n_iter = n_iter;
   d.lists = c->lists;
   d.list_cnt = c->list_cnt;
+  d.axis_order = axis ? c->axis : nullptr;
+  d.axis_stride = c->built_n;
   t_begin(c, SPH_T_DENSITY);
   const cudaError_t e = sphh::launch_density(d, phys_of(c->p), c->st);
   t_end(c, SPH_T_DENSITY);

@@ -225,7 +225,50 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       const float h_start = valid ? a.hs[ti] : 0.0f;
       // 1. filter into the lane's own list column
       int cnt = 0;
-      if (valid) {
+      if (valid && a.axis_order != nullptr) {
+        // sorted interactions (Sec. 2.2): each neighbour cell is walked along
+        // the axis linking it to the target's cell, nearest particles first,
+        // up to the first one whose distance along that axis reaches the
+        // search radius; the rest of the cell lies farther along the axis
+        const float Rn[4] = {0.0f, g.G.cell_f, g.G.cell_f * 1.41421356f, g.G.cell_f * 1.73205081f};
+#pragma unroll 1
+        for (int nb = 0; nb < 27; ++nb) {
+          const int ox = nb % 3 - 1, oy = (nb / 3) % 3 - 1, oz = nb / 9 - 1;
+          const int k = (tx + 1 + ox) + g.ex * ((ty + 1 + oy) + g.ey * (tz + 1 + oz));
+          const int32_t s0 = T.start[k], len = T.len[k];
+          if (nb == 13) {  // the own cell: every particle
+            for (int32_t r = sub; r < len; r += tpp) {
+              const float4 pj = spos[s0 + r];
+              const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const int at = min(cnt, kListCap) * 32 + lane;
+              if (kCacheR2) lr2[at] = r2;
+              lj[at] = (uint16_t)(s0 + r);
+              cnt += r2 < R2;
+            }
+            continue;
+          }
+          int sense;
+          const int q = axis_of(ox, oy, oz, sense);
+          const uint16_t* ord = a.axis_order + (int64_t)q * a.axis_stride + T.gstart[k];
+          // |x_ij . delta| <= r |delta|: beyond R |delta| (with a margin far
+          // above FP32 rounding) no pair is within R
+          const float bound = Rn[ox * ox + oy * oy + oz * oz] * 1.00001f;
+          const float sf = (float)sense;
+          const float p_i = sf * axis_proj(pi.x, pi.y, pi.z, q);
+          for (int32_t r = sub; r < len; r += tpp) {
+            const int32_t kk = s0 + (int32_t)ord[sense > 0 ? r : len - 1 - r];
+            const float4 pj = spos[kk];
+            if (sf * axis_proj(pj.x, pj.y, pj.z, q) - p_i >= bound) break;
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const int at = min(cnt, kListCap) * 32 + lane;
+            if (kCacheR2) lr2[at] = r2;
+            lj[at] = (uint16_t)kk;
+            cnt += r2 < R2;
+          }
+        }
+      } else if (valid) {
 #pragma unroll 1
         for (int r = 0; r < 9; ++r) {
           int32_t A0, B0;
@@ -245,7 +288,17 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
           }
         }
       }
-      const bool direct = cnt > kListCap;
+      bool direct = cnt > kListCap;
+      if (a.axis_order != nullptr) {
+        // the sorted walk splits a target's sources between its lanes by rank
+        // along each axis, the direct walk by position in the runs: a target
+        // whose list overflowed in any lane sends all its lanes direct, so
+        // that its lanes never mix the two splits (here, or in the force loop
+        // through the published lists)
+        const unsigned m = __ballot_sync(0xffffffffu, direct);
+        const unsigned grp = ((1u << tpp) - 1u) << (lane & ~(tpp - 1));
+        direct = (m & grp) != 0u;
+      }
       // publish the list for the force loop of this build: 16-byte vectors
       // into this lane's region (the force loop rebuilds the same rounds)
       if (a.lists != nullptr && valid) {

@@ -175,6 +175,45 @@ __device__ __forceinline__ int32_t cell_coord_fast(double x, double L, int32_t n
   return cell_coord(x, L, n_c);
 }
 
+// The 13 axes linking a cell to its neighbours (Sec. 2.2, sorted
+// interactions): delta_q with components in {-1, 0, 1}, first non-zero
+// component (z, then y, then x) positive; the other 13 neighbours lie along
+// -delta_q.  q = 0: (1,0,0); q = 1..3: (q-2, 1, 0); q = 4..12:
+// ((q-4)%3 - 1, (q-4)/3 - 1, 1).
+constexpr int kAxes = 13;
+
+__device__ __forceinline__ void axis_delta(int q, int& dx, int& dy, int& dz) {
+  if (q == 0) {
+    dx = 1;
+    dy = 0;
+    dz = 0;
+  } else if (q < 4) {
+    dx = q - 2;
+    dy = 1;
+    dz = 0;
+  } else {
+    dx = (q - 4) % 3 - 1;
+    dy = (q - 4) / 3 - 1;
+    dz = 1;
+  }
+}
+
+// Projection onto the (unnormalised) axis q.
+__device__ __forceinline__ float axis_proj(float x, float y, float z, int q) {
+  int dx, dy, dz;
+  axis_delta(q, dx, dy, dz);
+  return fmaf((float)dx, x, fmaf((float)dy, y, (float)dz * z));
+}
+
+// Axis of the neighbour offset (dx, dy, dz) != 0 and its sense: +1 when the
+// offset is delta_q, -1 when it is -delta_q.
+__device__ __forceinline__ int axis_of(int dx, int dy, int dz, int& sense) {
+  const bool pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+  sense = pos ? 1 : -1;
+  const int x = pos ? dx : -dx, y = pos ? dy : -dy, z = pos ? dz : -dz;
+  return z == 1 ? 4 + (y + 1) * 3 + (x + 1) : (y == 1 ? 1 + (x + 1) : 0);
+}
+
 // Cubic spline pieces with q = r/H (Sec. 3.1): w(q) and g(q) = w'(q)/q,
 // branch-free; both vanish for q >= 1.  h_rinv = H / r is only used on the
 // outer piece (q >= 1/2), where it is finite.

@@ -72,6 +72,16 @@ struct GatherForceArgs {
 };
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
 
+// Per-cell orders along the 13 neighbour axes (axis.cu): order[q n + s]
+// for sorted slot s (the density copies pos4 must be current).
+struct AxisSortArgs {
+  int64_t n_total;
+  const int32_t *perm, *key, *cell_start;
+  const float4* pos4;
+  uint16_t* order;  // kAxes * n_total
+};
+cudaError_t launch_axis_sort(const AxisSortArgs& a, cudaStream_t st);
+
 // Outputs of the loops are written in pool order through perm.
 struct DensityArgs {
   int n_sims;
@@ -91,6 +101,10 @@ struct DensityArgs {
   // entries of (sorted target ti, lane s) in lists[(4 ti + s) * kListRegion ...]
   uint16_t* lists;
   uint16_t* list_cnt;  // per (4 ti + s); 0xffff = overflow (not stored)
+  // optional per-cell axis orders (axis.cu): the filter walks each neighbour
+  // cell along the axis towards it and stops at the search radius
+  const uint16_t* axis_order;
+  int64_t axis_stride;  // n_total of the orders (one axis after the other)
 };
 cudaError_t launch_density(const DensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 

@@ -35,6 +35,7 @@ SPH_FLAG_SYNC = 1
 SPH_FLAG_COUNT_PAIRS = 2
 SPH_FLAG_TIMING = 4
 SPH_FLAG_TREE = 8
+SPH_FLAG_AXIS_SORT = 16
 
 TIMING_GROUPS = ("build", "gather", "density", "force", "integrate")
 
