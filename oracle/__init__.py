@@ -87,6 +87,8 @@ def lib():
                                         C.c_int32, C.c_void_p, C.c_void_p]
         L.oracle_build_cells.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_double, C.c_int32, C.c_void_p, C.c_void_p]
+        L.oracle_fof.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                 C.c_double, C.c_void_p]
         L.oracle_density.argtypes = [C.POINTER(_Particles), C.POINTER(_Config), C.c_void_p,
                                      C.c_int64, C.c_void_p, C.POINTER(_DensOut)]
         L.oracle_density_at.argtypes = [C.POINTER(_Particles), C.POINTER(_Config), C.c_void_p,
@@ -175,6 +177,16 @@ def build_cells(x, y, z, L: float, n_c: int):
     _check(lib().oracle_build_cells(n, keep(x), keep(y), keep(z), float(L), int(n_c),
                                     _ptr(cell_start), _ptr(perm)), "build_cells")
     return cell_start, perm[:n]
+
+
+def fof(x, y, z, L: float, b: float):
+    """Friends-of-friends groups with linking length b in the periodic box of
+    side L (Sec. 7.1): group[i] = the smallest index of i's group."""
+    keep = _Keep()
+    n = int(np.asarray(x).shape[0])
+    group = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().oracle_fof(n, keep(x), keep(y), keep(z), float(L), float(b), _ptr(group)), "fof")
+    return group[:n]
 
 
 def tree_order(x, y, z, L: float, n_c: int):

@@ -738,3 +738,83 @@ int oracle_step(int64_t n, double L, const oracle_config* C, double cfl,
   if (dt_out) *dt_out = dt;
   return err;
 }
+
+/* --------------------------------------------------------------------------
+ * Friends-of-friends groups (Sec. 7.1).  Particles i and j are friends when
+ * their minimum-image distance in the periodic box of side L is below the
+ * linking length b:
+ *   d = x_i - x_j per axis, wrapped once into [-L/2, L/2] (or_min_image),
+ *   r2 = dx*dx + dy*dy + dz*dz (left to right, no contraction),  r2 < b*b.
+ * Groups are the connected components of the friendship graph, found with
+ * union-find: every friend pair merges the sets of its two particles.  The
+ * root of a set is kept at its smallest index (the larger root is hooked
+ * below the smaller), so group[i] = the smallest index of i's group.
+ * Candidates: a grid of n_c = floor(L / b) cells per side (at most
+ * cbrt(8 n + 216), at least 3, so cells are at least b wide and the 27
+ * neighbour cells of a cell are distinct), each pair tested once from the
+ * particle of smaller index.  Returns -1 when b > L/3 (fewer than 3 cells).
+ * -------------------------------------------------------------------------- */
+static int64_t or_find(int64_t* parent, int64_t i) {
+  while (parent[i] != i) {
+    parent[i] = parent[parent[i]]; /* path halving */
+    i = parent[i];
+  }
+  return i;
+}
+
+int oracle_fof(int64_t n, const double* x, const double* y, const double* z, double L, double b,
+               int32_t* group) {
+  if (n < 0 || !(L > 0.0) || !(b > 0.0)) return -1;
+  if (n == 0) return 0;
+  int64_t n_c = (int64_t)floor(L / b);
+  if (n_c < 3) return -1;
+  const double lim = 8.0 * (double)n + 216.0;
+  while (n_c > 3 && (double)n_c * (double)n_c * (double)n_c > lim) --n_c;
+  const int64_t n_cells = n_c * n_c * n_c;
+  int64_t* key = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t* start = (int64_t*)calloc((size_t)n_cells + 1, sizeof(int64_t));
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_cells);
+  int64_t* parent = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  if (!key || !start || !order || !fill || !parent) {
+    free(key); free(start); free(order); free(fill); free(parent);
+    return -2;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t kx = oracle_cell_coord(x[i], L, (int32_t)n_c);
+    int64_t ky = oracle_cell_coord(y[i], L, (int32_t)n_c);
+    int64_t kz = oracle_cell_coord(z[i], L, (int32_t)n_c);
+    key[i] = kx + n_c * (ky + n_c * kz);
+    start[key[i] + 1] += 1;
+    parent[i] = i;
+  }
+  for (int64_t c = 0; c < n_cells; ++c) start[c + 1] += start[c];
+  for (int64_t c = 0; c < n_cells; ++c) fill[c] = start[c];
+  for (int64_t i = 0; i < n; ++i) order[fill[key[i]]++] = i;
+  const double b2 = b * b;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t k = key[i];
+    int64_t kx = k % n_c, ky = (k / n_c) % n_c, kz = k / (n_c * n_c);
+    for (int64_t oz = -1; oz <= 1; ++oz)
+      for (int64_t oy = -1; oy <= 1; ++oy)
+        for (int64_t ox = -1; ox <= 1; ++ox) {
+          int64_t cx = (kx + ox + n_c) % n_c, cy = (ky + oy + n_c) % n_c, cz = (kz + oz + n_c) % n_c;
+          int64_t c = cx + n_c * (cy + n_c * cz);
+          for (int64_t t = start[c]; t < start[c + 1]; ++t) {
+            int64_t j = order[t];
+            if (j <= i) continue;
+            double dx = or_min_image(x[i] - x[j], L);
+            double dy = or_min_image(y[i] - y[j], L);
+            double dz = or_min_image(z[i] - z[j], L);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < b2)) continue;
+            int64_t ri = or_find(parent, i), rj = or_find(parent, j);
+            if (ri == rj) continue;
+            if (ri < rj) parent[rj] = ri; else parent[ri] = rj;
+          }
+        }
+  }
+  for (int64_t i = 0; i < n; ++i) group[i] = (int32_t)or_find(parent, i);
+  free(key); free(start); free(order); free(fill); free(parent);
+  return 0;
+}
