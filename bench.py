@@ -214,33 +214,168 @@ def cpu_baseline(p, budget_s: float) -> dict:
                        f"{sec:.1f} s on 1 host core")}
 
 
+def measured_hbm_gbs():
+    """The measured copy bandwidth of this machine's GPUs (GB/s), if recorded."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # the earlier single GB300 measurement
+
+
+def fof_workload(name: str):
+    """fofN / fofNM: the clustered recipe with N (or N million, binary)
+    particles and the linking length 0.2 of the mean spacing (Sec. 7.1)."""
+    tail = name[len("fof"):] or "2M"
+    n = int(tail[:-1]) << 20 if tail.endswith("M") else int(tail)
+    p = make_workload(f"clustered{n}")
+    p["link"] = 0.2 * float(p["L"]) * n ** (-1.0 / 3.0)
+    p["desc"] = p["desc"].replace("; nested grids", "") + "; linking length 0.2 of the mean spacing"
+    return p
+
+
+def oracle_fof_sample(p, n_target: int, seed: int):
+    """Oracle friends-of-friends on the particles of a sub-cube holding about
+    n_target particles (same positions, box and linking length).  Returns
+    (particles labelled, seconds)."""
+    import numpy as np
+
+    import oracle
+    L, n = float(p["L"]), len(p["x"])
+    side = L * min(1.0, (n_target / n) ** (1.0 / 3.0))
+    c0 = np.random.default_rng(seed).uniform(0, L, 3)
+    d = [np.abs((np.asarray(p[k]) - c0[i] + 0.5 * L) % L - 0.5 * L) for i, k in enumerate("xyz")]
+    sel = np.where((d[0] < side / 2) & (d[1] < side / 2) & (d[2] < side / 2))[0]
+    xs = [np.ascontiguousarray(np.asarray(p[k], dtype=np.float64)[sel]) for k in "xyz"]
+    t0 = time.perf_counter()
+    oracle.fof(*xs, L, p["link"])
+    return len(sel), time.perf_counter() - t0
+
+
+def run_fof(args, world: int, rank: int, local: int):
+    """Friends-of-friends groups of the clustered box (sph_fof): every step
+    rebuilds the cells at the linking length and labels every particle."""
+    import torch
+    from paper_2305_13380_gb300 import build as B
+    B.build()
+    from paper_2305_13380_gb300 import replicas, sph
+
+    p = fof_workload(args.workload)
+    n, L, b = len(p["x"]), float(p["L"]), p["link"]
+    xyz = [torch.as_tensor(p[k], dtype=torch.float64, device="cuda") for k in "xyz"]
+    group = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING))
+    for _ in range(args.warmup):
+        sph.sph_fof(ctx, *xyz, b, group)
+    torch.cuda.synchronize()
+    if sph.sph_status(ctx):
+        raise SystemExit("device status set by the warm-up")
+    kt0 = sph.sph_kernel_times(ctx)  # reset
+    del kt0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(None)
+    time.sleep(0.25)
+    replicas.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sph.sph_fof(ctx, *xyz, b, group)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    replicas.barrier()
+    clk = clocks.stop()
+    kt = sph.sph_kernel_times(ctx)
+    value, ms = replicas.job_throughput(n * args.steps, e0.elapsed_time(e1))
+    g = group.cpu().numpy()
+    import numpy as np
+    _, counts = np.unique(g, return_counts=True)
+    # end to end: positions in from pinned host memory, labels out, every step
+    host_x = [t.cpu().pin_memory() for t in xyz]
+    host_g = torch.empty(n, dtype=torch.int32).pin_memory()
+    for it in range(2 + args.e2e_steps):
+        if it == 2:
+            torch.cuda.synchronize()
+            e0.record(stream)
+        for d, h in zip(xyz, host_x):
+            d.copy_(h, non_blocking=True)
+        sph.sph_fof(ctx, *xyz, b, group)
+        host_g.copy_(group, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value, _ = replicas.job_throughput(n * args.e2e_steps, e0.elapsed_time(e1))
+    # memory-bound kernels: algorithmic bytes of one call per particle: x, y,
+    # z read (24), the sorted copy written and read back (16 + 16), the cell
+    # key and slot (8), the labels initialised, read and written (12)
+    fof_ms = kt["density"][0] / max(kt["density"][1], 1)
+    bytes_call = n * (24 + 32 + 8 + 12)
+    hbm = measured_hbm_gbs()
+    roofline = {"bound": "hbm", "kernel": "k_fof_prep + k_fof_link + k_fof_label",
+                "achieved": bytes_call / (fof_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": bytes_call / (fof_ms / 1e3) / 1e9 / hbm if hbm else None, "traffic": None,
+                "bytes_per_launch": bytes_call}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        n0, t0 = oracle_fof_sample(p, 20000, seed=1)
+        n_target = int(max(20000, min(n, n0 * args.cpu_budget / max(t0, 1e-3))))
+        nu, sec = oracle_fof_sample(p, n_target, seed=2)
+        cpu = {"value": nu / sec, "unit": "particles/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nu} particles of a sub-cube, {sec:.1f} s on 1 host core"}
+    line = {
+        "metric": "friends-of-friends particles/s (clustered, 2M)", "value": value,
+        "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": p["desc"], "particles": n, "link": b,
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": 24 * n,
+                "d2h_bytes_per_step": 4 * n, "steps": args.e2e_steps},
+        "gpu_launches": (launches_per_step(n, 1, False) - 12 + 3) * args.steps,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"], "samples": clk["samples"]},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items() if v[1]},
+        "groups": int(len(counts)), "largest_group": int(counts.max()),
+        "particles_in_groups_of_32_or_more": int(counts[counts >= 32].sum()),
+        "device_status": sph.sph_status(ctx),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_reference(args, world: int, rank: int):
     if rank != 0:
         return
     import oracle
     oracle.build()
-    p = make_workload(args.workload)
+    fof = args.workload.startswith("fof")
+    p = fof_workload(args.workload) if fof else make_workload(args.workload)
+    metric, unit = (("friends-of-friends particles/s (clustered, 2M)", "particles/s") if fof
+                    else (METRIC, UNIT))
+    sample = (lambda q, k, seed: oracle_fof_sample(q, k, seed)) if fof else oracle_sample
     # size every sample so that the whole run stays near args.ref_budget seconds
-    n0, t0 = oracle_sample(p, 1000, seed=99)
+    n0, t0 = sample(p, 1000, seed=99)
     per_step = args.ref_budget / max(1, args.steps + args.warmup)
     n_target = int(max(200, min(len(p["x"]), n0 * per_step / max(t0, 1e-3))))
     for w in range(args.warmup):
-        oracle_sample(p, n_target, seed=100 + w)
+        sample(p, n_target, seed=100 + w)
     done, sec = 0, 0.0
     for k in range(args.steps):
-        nu, s = oracle_sample(p, n_target, seed=1000 + k)
+        nu, s = sample(p, n_target, seed=1000 + k)
         done += nu
         sec += s
     value = done / sec
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "desc": p["desc"],
                        "sample": f"{n_target}-particle sub-cubes per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} sub-cubes of ~{n_target} particles"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -456,6 +591,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload.startswith("batch"):
         run_batch(args, world, rank, local)
+    elif args.workload.startswith("fof"):
+        run_fof(args, world, rank, local)
     elif args.workload.startswith("served"):
         run_served(args, world, rank, local)
     else:

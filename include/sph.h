@@ -264,6 +264,23 @@ int sph_step(sph_ctx* ctx, const sph_pool* pool);
  * velocities given (device array out of 4 n_sims doubles). */
 int sph_conservation(sph_ctx* ctx, const sph_pool* pool, double* out);
 
+/* Friends-of-friends groups (Sec. 7.1) of n particles in the periodic box of
+ * side params.box_size.  Particles i and j are friends when their
+ * minimum-image distance is below the linking length b:
+ *   d = x_i - x_j per axis, wrapped once into [-L/2, L/2],
+ *   dx*dx + dy*dy + dz*dz < b*b   (FP64, evaluated left to right);
+ * a group is a connected component of that relation.
+ *   x, y, z   device FP64, n each, in [0, L)
+ *   link_len  b, 0 < b <= L/3 (else SPH_E_INVAL / SPH_E_BOX)
+ *   group     device int32, n, written: group[i] = the smallest index of i's
+ *             group (so group[i] == i marks one particle per group)
+ * The search reuses the cell build with cells at least b wide (it replaces
+ * the context's current cells).  Asynchronous on the context's stream;
+ * with SPH_FLAG_SYNC it waits and returns the device status
+ * (SPH_E_CAPACITY if a bounded union-find loop gave up). */
+int sph_fof(sph_ctx* ctx, int64_t n, const double* x, const double* y, const double* z,
+            double link_len, int32_t* group);
+
 /* With SPH_FLAG_TIMING: waits for the stream, then returns the summed device
  * time in milliseconds (ms_out[SPH_T_COUNT]) and the number of timed launches
  * of each group (calls_out[SPH_T_COUNT], may be NULL) since the last query,

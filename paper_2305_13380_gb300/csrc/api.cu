@@ -316,8 +316,9 @@ bool params_ok(const sph_params& p) {
 }
 
 int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const double* box,
-             const double* x, const double* y, const double* z, const float* h) {
+             const double* x, const double* y, const double* z, const float* h, double radius = 0.0) {
   sphh::BuildArgs b;
+  b.radius = radius;
   b.n_sims = n_sims;
   b.n_total = n_total;
   b.cap_cells = 8 * n_total + 216 * (int64_t)n_sims;
@@ -341,7 +342,8 @@ int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const 
   b.rk = c->rk;
   b.rv = c->rv;
   b.hist = c->rhist;
-  const bool tree = (c->p.flags & SPH_FLAG_TREE) != 0;
+  // a given radius (friends-of-friends) always builds the uniform grid
+  const bool tree = (c->p.flags & SPH_FLAG_TREE) != 0 && !(radius > 0.0);
   b.sort_cells = tree ? 0 : 1;
   if (tree) {
     const int rc = ensure_tree(c, n_total, 0);
@@ -931,6 +933,48 @@ int sph_conservation(sph_ctx* c, const sph_pool* pl, double* out) {
   if (sphh::launch_conservation(pl->n_sims, pl->sim_offset, pl->m, pl->vx, pl->vy, pl->vz, pl->ax,
                                 pl->ay, pl->az, pl->du_dt, out, c->st) != cudaSuccess)
     return SPH_E_CUDA;
+  return finish(c);
+}
+
+int sph_fof(sph_ctx* c, int64_t n, const double* x, const double* y, const double* z, double link_len,
+            int32_t* group) {
+  if (!c || n < 0 || n > INT32_MAX / 16 || !(link_len > 0.0)) return SPH_E_INVAL;
+  if (n > 0 && (!x || !y || !z || !group)) return SPH_E_INVAL;
+  if (link_len > c->p.box_size / 3.0) return SPH_E_BOX;
+  if (n == 0) return SPH_OK;
+  int rc = ensure(c, n, 1);
+  if (rc != SPH_OK) return rc;
+  if (c->h_off1[1] != n || c->h_box1[0] != c->p.box_size) {
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+    c->h_off1[0] = 0;
+    c->h_off1[1] = n;
+    c->h_box1[0] = c->p.box_size;
+    if (cudaMemcpyAsync(c->off1, c->h_off1, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->box1, c->h_box1, sizeof(double), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+  }
+  // cells at least b wide: friends lie in the same or adjacent cells
+  rc = do_build(c, 1, n, c->off1, c->box1, x, y, z, nullptr, link_len);
+  if (rc != SPH_OK) return rc;
+  sphh::FofArgs f;
+  f.n_total = n;
+  f.grid = c->grid;
+  f.perm = c->perm;
+  f.key = c->key;
+  f.cell_start = c->cell_start;
+  f.x = x;
+  f.y = y;
+  f.z = z;
+  f.link = link_len;
+  f.rel = c->pos4;  // the sorted density copies' buffer, free between loops
+  f.group = group;
+  f.status = c->misc + sphk::kStatus;
+  c->lists_valid = false;
+  t_begin(c, SPH_T_DENSITY);
+  const cudaError_t e = sphh::launch_fof(f, c->st);
+  t_end(c, SPH_T_DENSITY);
+  if (e != cudaSuccess) return SPH_E_CUDA;
   return finish(c);
 }
 

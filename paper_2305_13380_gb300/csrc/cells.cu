@@ -60,14 +60,16 @@ __global__ void k_grid_hmax(const int64_t* __restrict__ sim_offset, int n_sims, 
 }
 
 // One thread per simulation: cells per side from max h.
+// radius > 0: the search radius is given (friends-of-friends), not derived
+// from the smoothing lengths.
 __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const double* __restrict__ box,
                              const int32_t* __restrict__ hmax_bits, int n_sims, double margin,
-                             GridDev* __restrict__ grid, int32_t* __restrict__ misc) {
+                             double radius, GridDev* __restrict__ grid, int32_t* __restrict__ misc) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x) {
     const int64_t a = sim_offset[s], b = sim_offset[s + 1];
     const float m = __int_as_float(hmax_bits[s]);
     const double L = box[s];
-    const double Hmax = kGammaKd * (double)m * (1.0 + margin);
+    const double Hmax = radius > 0.0 ? radius : kGammaKd * (double)m * (1.0 + margin);
     const int32_t cap = cap_cells_per_side(b - a);
     int32_t nc = cap;
     if (Hmax > 0.0) {
@@ -313,13 +315,13 @@ static int grid_for(int64_t n, int threads, int max_blocks) {
 
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t st) {
   if (cudaMemsetAsync(a.hmax_bits, 0, sizeof(int32_t) * a.n_sims, st) != cudaSuccess) return cudaGetLastError();
-  if (a.n_total > 0) {
+  if (a.n_total > 0 && !(a.radius > 0.0)) {
     int64_t hb = (a.n_total + 255) / 256;
     if (hb > (int64_t)a.num_sms * 8) hb = (int64_t)a.num_sms * 8;
     k_grid_hmax<<<(int)hb, 256, 0, st>>>(a.sim_offset, a.n_sims, a.n_total, a.h, a.hmax_bits);
   }
   k_grid_setup<<<(a.n_sims + 127) / 128, 128, 0, st>>>(a.sim_offset, a.box, a.hmax_bits, a.n_sims,
-                                                       a.margin, a.grid, a.misc);
+                                                       a.margin, a.radius, a.grid, a.misc);
   k_grid_base<<<1, 32, 0, st>>>(a.grid, a.n_sims, a.misc);
   // grids sized for the capacity but capped: the kernels loop up to the
   // device-side cell count, and idle blocks would only cost launch time

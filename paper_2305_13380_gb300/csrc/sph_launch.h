@@ -32,8 +32,23 @@ struct BuildArgs {
   int32_t *key, *slot, *count, *cell_start, *scan_sums, *perm;
   int32_t *rk, *rv, *hist;  // radix-sort scratch: n, n, radix_hist_words(n)
   int sort_cells = 1;       // 0: counts and cell_start only (the tree build orders)
+  double radius = 0.0;      // > 0: cells at least this wide, h unused (friends-of-friends)
 };
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t st);
+
+// Friends-of-friends groups (fof.cu) on a uniform build whose cells are at
+// least the linking length wide: group[p] = smallest index of p's group.
+struct FofArgs {
+  int64_t n_total;
+  const sphk::GridDev* grid;     // one simulation
+  const int32_t *perm, *key, *cell_start;
+  const double *x, *y, *z;
+  double link;                   // linking length b
+  float4* rel;                   // n scratch: sorted cell-relative positions
+  int32_t* group;                // n: union-find parents, then the labels
+  int32_t* status;
+};
+cudaError_t launch_fof(const FofArgs& a, cudaStream_t st);
 
 // Stable radix sort of keys (bits significant bits) with values 0..n-1
 // (radix.cu); keys is clobbered, the sorted values land in vals_out.

@@ -122,13 +122,14 @@ def lib():
         L.sph_reserve.argtypes = [_P, C.c_int64, C.c_int32]
         L.sph_tree_counts.argtypes = [_P, C.POINTER(C.c_int64)]
         L.sph_fp32_probe.argtypes = [C.c_int32, C.c_int64, _P, _P]
+        L.sph_fof.argtypes = [_P, C.c_int64, _P, _P, _P, C.c_double, _P]
         L.sph_pool_move.argtypes = [C.POINTER(sph_pool), C.POINTER(sph_pool), C.c_int32, _P, _P, C.c_int32,
                                     _P]
         for f in ("sph_create", "sph_status", "sph_build_cells", "sph_cells_sync", "sph_cells_copy",
                   "sph_density",
                   "sph_force", "sph_step", "sph_conservation", "sph_pair_counts",
                   "sph_kernel_times", "sph_build_cells_static", "sph_reserve", "sph_tree_counts",
-                  "sph_pool_move", "sph_fp32_probe"):
+                  "sph_pool_move", "sph_fp32_probe", "sph_fof"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -208,6 +209,18 @@ def sph_build_cells(ctx: Context, x, y, z, h) -> sph_cells:
            "sph_build_cells")
     cells._keep = (x, y, z, h)
     return cells
+
+
+def sph_fof(ctx: Context, x, y, z, link_len: float, group=None):
+    """Friends-of-friends groups (int32 CUDA tensor): group[i] = the smallest
+    index of i's group, friends closer than link_len (minimum image in the
+    context's periodic box)."""
+    n = int(x.shape[0])
+    if group is None:
+        group = torch.empty(n, dtype=torch.int32, device=x.device)
+    _check(lib().sph_fof(ctx.handle, n, _ptr(x, torch.float64), _ptr(y, torch.float64),
+                         _ptr(z, torch.float64), float(link_len), _ptr(group, torch.int32)), "sph_fof")
+    return group
 
 
 def sph_cells_sync(ctx: Context, cells: sph_cells) -> int:
