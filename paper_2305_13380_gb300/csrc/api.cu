@@ -192,9 +192,10 @@ int ensure_tree(sph_ctx* c, int64_t n, int64_t rev_need) {
 }
 
 // Scratch for n particles in n_sims simulations; every simulation may use
-// up to 8 n_s + 216 cells, so the total is bounded by 8 n + 216 n_sims.
-int ensure(sph_ctx* c, int64_t n, int n_sims) {
-  const int64_t need_cells = 8 * n + 216 * (int64_t)n_sims;
+// up to k n_s + 216 cells (k = cells_per_particle: 8 for the SPH loops), so
+// the total is bounded by k n + 216 n_sims.
+int ensure(sph_ctx* c, int64_t n, int n_sims, int cells_per_particle = 8) {
+  const int64_t need_cells = cells_per_particle * n + 216 * (int64_t)n_sims;
   if (n <= c->cap_n && n_sims <= c->cap_sims && need_cells <= c->cap_cells) return SPH_OK;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
   free_grown(c);
@@ -203,12 +204,12 @@ int ensure(sph_ctx* c, int64_t n, int n_sims) {
   c->rev_cap = rev_keep;
   const int64_t cn = n + n / 4 + 64;
   const int cs = n_sims + n_sims / 4 + 1;
-  const int64_t cc = 8 * cn + 216 * (int64_t)cs;
+  const int64_t cc = (cells_per_particle > 8 ? cells_per_particle : 8) * cn + 216 * (int64_t)cs;
   bool ok = dalloc(c->grid, cs) && dalloc(c->key, cn) && dalloc(c->slot, cn) &&
             dalloc(c->count, cc + 1) && dalloc(c->cell_start, cc + 1) &&
             dalloc(c->scan_sums, cc / 1024 + 2) && dalloc(c->perm, cn) &&
             dalloc(c->rk, cn) && dalloc(c->rv, cn) && dalloc(c->rhist, sphh::radix_hist_words(cn)) &&
-            dalloc(c->overflow, cc / 3 + 2) && dalloc(c->pos4, cn) &&
+            dalloc(c->overflow, (8 * cn + 216 * (int64_t)cs) / 3 + 2) && dalloc(c->pos4, cn) &&
             dalloc(c->vel4, cn) && dalloc(c->th4, cn) && dalloc(c->hs, cn) && dalloc(c->fD, cn) &&
             dalloc(c->dt_bits, cs) && dalloc(c->hmax_bits, cs) &&
             dalloc(c->lists, (int64_t)sphk::kListRegion * 4 * cn) &&
@@ -316,12 +317,14 @@ bool params_ok(const sph_params& p) {
 }
 
 int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const double* box,
-             const double* x, const double* y, const double* z, const float* h, double radius = 0.0) {
+             const double* x, const double* y, const double* z, const float* h, double radius = 0.0,
+             int cells_per_particle = 8) {
   sphh::BuildArgs b;
   b.radius = radius;
+  b.cells_per_particle = cells_per_particle;
   b.n_sims = n_sims;
   b.n_total = n_total;
-  b.cap_cells = 8 * n_total + 216 * (int64_t)n_sims;
+  b.cap_cells = cells_per_particle * n_total + 216 * (int64_t)n_sims;
   b.num_sms = c->num_sms;
   b.margin = c->p.cell_margin;
   b.sim_offset = off;
@@ -936,13 +939,20 @@ int sph_conservation(sph_ctx* c, const sph_pool* pl, double* out) {
   return finish(c);
 }
 
+// Friends-of-friends grids allow 160 cells per particle (8 for the SPH
+// loops): at the usual linking length of 0.2 mean spacings, cells of b itself
+// need 125 per particle, and cells capped wider multiply the pairs to test by
+// the cube of the widening (2.5^3 = 16 at the SPH cap).  Their counts and
+// offsets take 1.3 KB per particle.
+constexpr int kFofCellsPerParticle = 160;
+
 int sph_fof(sph_ctx* c, int64_t n, const double* x, const double* y, const double* z, double link_len,
             int32_t* group) {
   if (!c || n < 0 || n > INT32_MAX / 16 || !(link_len > 0.0)) return SPH_E_INVAL;
   if (n > 0 && (!x || !y || !z || !group)) return SPH_E_INVAL;
   if (link_len > c->p.box_size / 3.0) return SPH_E_BOX;
   if (n == 0) return SPH_OK;
-  int rc = ensure(c, n, 1);
+  int rc = ensure(c, n, 1, kFofCellsPerParticle);
   if (rc != SPH_OK) return rc;
   if (c->h_off1[1] != n || c->h_box1[0] != c->p.box_size) {
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
@@ -955,7 +965,7 @@ int sph_fof(sph_ctx* c, int64_t n, const double* x, const double* y, const doubl
       return SPH_E_CUDA;
   }
   // cells at least b wide: friends lie in the same or adjacent cells
-  rc = do_build(c, 1, n, c->off1, c->box1, x, y, z, nullptr, link_len);
+  rc = do_build(c, 1, n, c->off1, c->box1, x, y, z, nullptr, link_len, kFofCellsPerParticle);
   if (rc != SPH_OK) return rc;
   sphh::FofArgs f;
   f.n_total = n;

@@ -22,9 +22,10 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Cells-per-side bound of a simulation of n particles: n_c^3 <= 8 n + 216.
-__device__ __forceinline__ int32_t cap_cells_per_side(int64_t n) {
-  double lim = 8.0 * (double)n + 216.0;
+// Cells-per-side bound of a simulation of n particles: n_c^3 <= k n + 216
+// (k = 8 for the SPH loops; friends-of-friends asks for more).
+__device__ __forceinline__ int32_t cap_cells_per_side(int64_t n, int k) {
+  double lim = (double)k * (double)n + 216.0;
   int32_t c = (int32_t)cbrt(lim);
   while ((double)(c + 1) * (c + 1) * (c + 1) <= lim) ++c;
   while (c > 3 && (double)c * c * c > lim) --c;
@@ -64,13 +65,14 @@ __global__ void k_grid_hmax(const int64_t* __restrict__ sim_offset, int n_sims, 
 // from the smoothing lengths.
 __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const double* __restrict__ box,
                              const int32_t* __restrict__ hmax_bits, int n_sims, double margin,
-                             double radius, GridDev* __restrict__ grid, int32_t* __restrict__ misc) {
+                             double radius, int cells_per_particle, GridDev* __restrict__ grid,
+                             int32_t* __restrict__ misc) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x) {
     const int64_t a = sim_offset[s], b = sim_offset[s + 1];
     const float m = __int_as_float(hmax_bits[s]);
     const double L = box[s];
     const double Hmax = radius > 0.0 ? radius : kGammaKd * (double)m * (1.0 + margin);
-    const int32_t cap = cap_cells_per_side(b - a);
+    const int32_t cap = cap_cells_per_side(b - a, cells_per_particle);
     int32_t nc = cap;
     if (Hmax > 0.0) {
       const double t = floor(L / Hmax);
@@ -321,7 +323,8 @@ cudaError_t launch_build(const BuildArgs& a, cudaStream_t st) {
     k_grid_hmax<<<(int)hb, 256, 0, st>>>(a.sim_offset, a.n_sims, a.n_total, a.h, a.hmax_bits);
   }
   k_grid_setup<<<(a.n_sims + 127) / 128, 128, 0, st>>>(a.sim_offset, a.box, a.hmax_bits, a.n_sims,
-                                                       a.margin, a.radius, a.grid, a.misc);
+                                                       a.margin, a.radius, a.cells_per_particle, a.grid,
+                                                       a.misc);
   k_grid_base<<<1, 32, 0, st>>>(a.grid, a.n_sims, a.misc);
   // grids sized for the capacity but capped: the kernels loop up to the
   // device-side cell count, and idle blocks would only cost launch time

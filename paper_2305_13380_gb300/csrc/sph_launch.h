@@ -33,6 +33,7 @@ struct BuildArgs {
   int32_t *rk, *rv, *hist;  // radix-sort scratch: n, n, radix_hist_words(n)
   int sort_cells = 1;       // 0: counts and cell_start only (the tree build orders)
   double radius = 0.0;      // > 0: cells at least this wide, h unused (friends-of-friends)
+  int cells_per_particle = 8;  // n_c^3 <= cells_per_particle n + 216 per simulation
 };
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t st);
 
