@@ -59,6 +59,7 @@ struct sph_ctx {
   float *leaf_side = nullptr, *lrad = nullptr;
   int4* fine = nullptr;
   float4* rel = nullptr;
+  float4* trec = nullptr;  // force records of the nested grids, 4 per particle
   uint32_t* tlists = nullptr;
   uint64_t* rev_raw = nullptr;
   uint32_t* rev = nullptr;
@@ -145,6 +146,7 @@ void free_tree(sph_ctx* c) {
   dfree(c->lrad);
   dfree(c->fine);
   dfree(c->rel);
+  dfree(c->trec);
   dfree(c->tlists);
   dfree(c->rev_raw);
   dfree(c->rev);
@@ -176,7 +178,7 @@ int ensure_tree(sph_ctx* c, int64_t n, int64_t rev_need) {
             dalloc(c->skey, cn) && dalloc(c->tgt, cn) && dalloc(c->flag, cn) && dalloc(c->level, cn) &&
             dalloc(c->fb_level, cn) && dalloc(c->fb_list, cn) && dalloc(c->leaf_of, cn) && dalloc(c->n_leaves, 1) &&
             dalloc(c->leaves, cn + 1) && dalloc(c->ranges, 27 * cn) && dalloc(c->leaf_side, cn) &&
-            dalloc(c->lrad, cn) && dalloc(c->fine, cn) && dalloc(c->rel, cn) &&
+            dalloc(c->lrad, cn) && dalloc(c->fine, cn) && dalloc(c->rel, cn) && dalloc(c->trec, 4 * cn) &&
             dalloc(c->tlists, (int64_t)sphk::kTreeListRegion * sphk::kTreeTpp * cn) &&
             dalloc(c->rev_raw, rc) && dalloc(c->rev, rc) && dalloc(c->rev_count, 1) &&
             dalloc(c->rev_start, cn + 1) && dalloc(c->rev_fill, cn);
@@ -590,6 +592,11 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   g.fB = c->vel4;
   g.fC = c->th4;
   g.fD = c->fD;
+  if (c->built_tree) {
+    g.rel = c->rel;
+    g.fine = c->fine;
+    g.rec = c->trec;
+  }
   t_begin(c, SPH_T_GATHER);
   if (sphh::launch_gather_force(g, c->st) != cudaSuccess) return SPH_E_CUDA;
   t_end(c, SPH_T_GATHER);
@@ -612,10 +619,7 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
     a.lrad = c->lrad;
     a.leaf_side = c->leaf_side;
     a.perm = c->perm;
-    a.fA = c->pos4;
-    a.fB = c->vel4;
-    a.fC = c->th4;
-    a.fD = c->fD;
+    a.rec = c->trec;
     a.lists = c->tlists;
     a.list_cnt = c->list_cnt;
     a.rev_start = c->rev_start;

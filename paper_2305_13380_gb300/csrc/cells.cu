@@ -278,11 +278,24 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
                                const float* __restrict__ P, const float* __restrict__ c,
                                const float* __restrict__ B, float4* __restrict__ fA,
                                float4* __restrict__ fB, float4* __restrict__ fC,
-                               float2* __restrict__ fD) {
+                               float2* __restrict__ fD, const float4* __restrict__ trel,
+                               const int4* __restrict__ tfine, float4* __restrict__ rec) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_total;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p = perm[s];
     const float H = kGammaK * h[p];
+    if (rec != nullptr) {
+      // nested grids: one record per source (the arrays below are not read)
+      const float4 rl = trel[s];
+      const int4 fn = tfine[s];
+      const float r = rho[p];
+      float4* o = rec + 4 * s;
+      o[0] = make_float4(rl.x, rl.y, rl.z, H);
+      o[1] = make_float4(__int_as_float(fn.x), __int_as_float(fn.y), __int_as_float(fn.z), r);
+      o[2] = make_float4(vx[p], vy[p], vz[p], m[p]);
+      o[3] = make_float4(f[p] * P[p] / (r * r), f[p], c[p], B[p]);
+      continue;
+    }
     if (kPos) {
       const int32_t cc = key[p];
       const GridDev G = grid[sim_of_cell(grid, n_sims, cc)];
@@ -360,7 +373,7 @@ cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st) {
   auto kern = a.positions ? k_gather_force<true> : k_gather_force<false>;
   kern<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
       a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.h, a.rho,
-      a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD);
+      a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD, a.rel, a.fine, a.rec);
   return cudaGetLastError();
 }
 

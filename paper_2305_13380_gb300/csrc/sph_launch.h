@@ -85,6 +85,11 @@ struct GatherForceArgs {
   // 1: compute fA.xyz from x, y, z; 0: fA.xyz already holds them (or is not
   // read), write H only
   int positions = 1;
+  // nested grids: 64-byte records (rel, H), (fine, rho), (v, m), (fP, f, c, B)
+  // per source instead of fA..fD; rel and fine are the tree gather's copies
+  const float4* rel = nullptr;
+  const int4* fine = nullptr;
+  float4* rec = nullptr;
 };
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
 
@@ -243,8 +248,7 @@ struct TreeForceArgs {
   const float4* rel;
   const float *lrad, *leaf_side;
   const int32_t* perm;
-  const float4 *fA, *fB, *fC;  // as GatherForceArgs (only H of fA is read)
-  const float2* fD;
+  const float4* rec;  // 4 float4 per source, as GatherForceArgs::rec
   const uint32_t* lists;
   const uint16_t* list_cnt;
   const int32_t* rev_start;

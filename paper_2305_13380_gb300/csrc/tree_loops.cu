@@ -681,6 +681,24 @@ struct TFSums {
   int npair;
 };
 
+// A source's force record, 64 bytes in source order (written by the force
+// gather): q0 = (rel x, y, z, H), q1 = (fine x, y, z, rho as bits),
+// q2 = (v, m), q3 = (f P / rho^2, f, c, B).  One record replaces six
+// gathers from six arrays; 1/H is recomputed (correctly rounded, the value
+// the arrays held).
+struct TRec {
+  float4 q0;
+  int4 q1;
+};
+
+__device__ __forceinline__ TRec trec_head(const float4* __restrict__ rec, int32_t j) {
+  const float4* r = rec + 4 * (int64_t)j;
+  TRec t;
+  t.q0 = r[0];
+  t.q1 = *reinterpret_cast<const int4*>(r + 1);
+  return t;
+}
+
 // One force pair with x_ij = (dx, dy, dz) (same terms as force.cu).
 __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const float4& vi, const float4& ci,
                                             float Hi, float Hinv_i, float rho_i, const float4& vj,
@@ -711,6 +729,19 @@ __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const 
   s.npair += in;
 }
 
+// tforce_pair with source j's data from its record (head already loaded).
+__device__ __forceinline__ void tforce_rec(float dx, float dy, float dz, const float4& vi, const float4& ci,
+                                           float Hi, float Hinv_i, float rho_i, const float4* __restrict__ rec,
+                                           int32_t j, const TRec& h, const PhysDev& ph, TFSums& s) {
+  const float4* r = rec + 4 * (int64_t)j;
+  tforce_pair(dx, dy, dz, vi, ci, Hi, Hinv_i, rho_i, r[2], r[3], h.q0.w, __frcp_rn(h.q0.w),
+              __int_as_float(h.q1.w), ph, s);
+}
+
+__device__ __forceinline__ float3 rec_rel_to(const TGeo& g, const TRec& h, int sc) {
+  return rel_to(g, h.q0, h.q1, sc);
+}
+
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs a, PhysDev ph) {
   const int lane = threadIdx.x & 31;
   const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
@@ -731,13 +762,14 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
       const int lc = (int)a.list_cnt[col];
       const bool fb = lc == kListFallback;  // written by k_tree_force_fb
       if (valid && !fb) {
-        const float4 reli = a.rel[ti];
-        const int4 fi = a.fine[ti];
+        const TRec hi = trec_head(a.rec, ti);
+        const float4 reli = hi.q0;
+        const int4 fi = hi.q1;
         const float3 pi = rel_to(g, reli, fi, kNoShift);
-        const float4 vi = a.fB[ti];
-        const float4 ci = a.fC[ti];
-        const float2 di = a.fD[ti];
-        const float Hi = a.fA[ti].w;
+        const float4 vi = a.rec[4 * (int64_t)ti + 2];
+        const float4 ci = a.rec[4 * (int64_t)ti + 3];
+        const float2 di = make_float2(__int_as_float(hi.q1.w), __frcp_rn(hi.q0.w));
+        const float Hi = hi.q0.w;
         const bool direct = lc == kListNone;
         // own reach: the list radius, or the leaf side on the list-free path
         const float C = direct ? g.side : a.lrad[ti];
@@ -748,23 +780,20 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
             const uint32_t je = lst[e];
             const int32_t j = unpack_j(je);
             if (j == ti) continue;
-            const float4 rj = a.rel[j];
-            const float3 d = pair_vec(g, reli, fi, rj, a.fine[j], unpack_s(je));
-            const float2 dj = a.fD[j];
-            tforce_pair(d.x, d.y, d.z, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
+            const TRec hj = trec_head(a.rec, j);
+            const float3 d = pair_vec(g, reli, fi, hj.q0, hj.q1, unpack_s(je));
+            tforce_rec(d.x, d.y, d.z, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
           }
         } else {
           for (int r = 0; r < 27; ++r) {
             const TreeRange Rg = a.ranges[(int64_t)li * 27 + r];
             for (int32_t j = Rg.lo + sub; j < Rg.hi; j += kTreeTpp) {
               if (j == ti) continue;
-              const float4 rj = a.rel[j];
-              const float3 pj = rel_to(g, rj, a.fine[j], Rg.shift);
+              const TRec hj = trec_head(a.rec, j);
+              const float3 pj = rec_rel_to(g, hj, Rg.shift);
               const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-              if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2) {
-                const float2 dj = a.fD[j];
-                tforce_pair(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
-              }
+              if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
+                tforce_rec(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
             }
           }
         }
@@ -773,13 +802,11 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
         for (int32_t k = r0 + sub; k < r1; k += kTreeTpp) {
           const uint32_t je = a.rev[k];
           const int32_t j = unpack_j(je);
-          const float4 rj = a.rel[j];
-          const float3 pj = rel_to(g, rj, a.fine[j], unpack_s(je));
+          const TRec hj = trec_head(a.rec, j);
+          const float3 pj = rec_rel_to(g, hj, unpack_s(je));
           const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-          if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2) {
-            const float2 dj = a.fD[j];
-            tforce_pair(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
-          }
+          if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
+            tforce_rec(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
         }
       }
       s.ax = gsum(s.ax);
@@ -976,12 +1003,12 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
     const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30))];
     const TreeLeaf Lc = cell_at_depth(key, (int)a.fb_level[ti]);
     const TGeo g = leaf_geo(Lc, G);
-    const float4 reli = a.rel[ti];
-    const float3 pi = rel_to(g, reli, a.fine[ti], kNoShift);
-    const float4 vi = a.fB[ti];
-    const float4 ci = a.fC[ti];
-    const float2 di = a.fD[ti];
-    const float Hi = a.fA[ti].w;
+    const TRec hi = trec_head(a.rec, ti);
+    const float3 pi = rec_rel_to(g, hi, kNoShift);
+    const float4 vi = a.rec[4 * (int64_t)ti + 2];
+    const float4 ci = a.rec[4 * (int64_t)ti + 3];
+    const float2 di = make_float2(__int_as_float(hi.q1.w), __frcp_rn(hi.q0.w));
+    const float Hi = hi.q0.w;
     const float C2 = g.side * g.side;  // own reach: the cell of the fallback level
     TFSums s;
     s.ax = s.ay = s.az = s.du = s.vsig = 0.f;
@@ -990,24 +1017,22 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
       const TreeRange Rg = neighbour_range(G, Lc, r, a.skey, a.cell_start);
       for (int32_t j = Rg.lo + lane; j < Rg.hi; j += 32) {
         if (j == ti) continue;
-        const float3 pj = rel_to(g, a.rel[j], a.fine[j], Rg.shift);
+        const TRec hj = trec_head(a.rec, j);
+        const float3 pj = rec_rel_to(g, hj, Rg.shift);
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2) {
-          const float2 dj = a.fD[j];
-          tforce_pair(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
-        }
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
+          tforce_rec(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
       }
     }
     const int32_t r0 = a.rev_start[ti], r1 = a.rev_start[ti + 1];
     for (int32_t k = r0 + lane; k < r1; k += 32) {
       const uint32_t je = a.rev[k];
       const int32_t j = unpack_j(je);
-      const float3 pj = rel_to(g, a.rel[j], a.fine[j], unpack_s(je));
+      const TRec hj = trec_head(a.rec, j);
+      const float3 pj = rec_rel_to(g, hj, unpack_s(je));
       const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2) {
-        const float2 dj = a.fD[j];
-        tforce_pair(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.fB[j], a.fC[j], a.fA[j].w, dj.y, dj.x, ph, s);
-      }
+      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
+        tforce_rec(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
     }
     s.ax = wsum(s.ax);
     s.ay = wsum(s.ay);
