@@ -415,6 +415,39 @@ __device__ __forceinline__ uint64_t reverse_rec(int32_t j, int32_t ti, int sc) {
   return ((uint64_t)(uint32_t)j << 32) | pack_js(ti, mirror_s(sc));
 }
 
+// Appends the list entries marked in each lane's mask wm (bit e: entry e of
+// the lane's column in lje): one counter atomic for the warp, then every
+// lane writes its records at its offset.  Called by all 32 lanes.
+__device__ __forceinline__ void emit_marked(const sphh::TreeDensityArgs& a, uint32_t wm, const uint32_t* lje,
+                                            int32_t ti, int lane) {
+  static_assert(kTreeList <= 32, "one mask bit per list entry");
+  const int my = __popc(wm);
+  int incl = my;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(a.rev_count, (unsigned long long)total);
+  unsigned long long k = __shfl_sync(0xffffffffu, base, 0) + (unsigned long long)(incl - my);
+  while (wm) {
+    const int e = __ffs(wm) - 1;
+    wm &= wm - 1u;
+    const uint32_t je = lje[e * 32 + lane];
+    const int32_t j = unpack_j(je);
+    if (k < (unsigned long long)a.rev_cap) {
+      a.rev_raw[k] = reverse_rec(j, ti, unpack_s(je));
+      atomicAdd(&a.rev_start[j], 1);
+    } else {
+      atomicOr(a.status, SPH_ST_CAPACITY);
+    }
+    ++k;
+  }
+}
+
 // Outputs of target ti (source index) from its sums at h (Sec. 3.1 and the
 // equation of state of Sec. 3.2).
 __device__ __forceinline__ void tdens_write(const sphh::TreeDensityArgs& a, const PhysDev& ph, int32_t ti,
@@ -591,19 +624,17 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           if (!one_chunk) __syncwarp();
         }
       }
-      // reverse pairs from the lists (warp-uniform trip count)
-      const int emax = __reduce_max_sync(0xffffffffu, (valid && !mydirect) ? cnt : 0);
-      for (int e = 0; e < emax; ++e) {
-        bool want = false;
-        uint64_t rec = 0;
-        if (valid && !mydirect && e < cnt) {
+      // reverse pairs from the lists: each lane marks its wanted entries (a
+      // list holds at most kTreeList = 32), then the warp takes one slot
+      // range for the whole round
+      uint32_t wm = 0;
+      if (valid && !mydirect && !atcap) {
+        for (int e = 0; e < cnt; ++e) {
           const uint32_t je = lje[e * 32 + lane];
-          const int32_t j = unpack_j(je);
-          want = !atcap && want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side);
-          rec = reverse_rec(j, ti, unpack_s(je));
+          if (want_reverse(a, ti, unpack_j(je), lr2[e * 32 + lane], H2, H, g.side)) wm |= 1u << e;
         }
-        emit_warp(a, want, rec, lane);
       }
+      emit_marked(a, wm, lje, ti, lane);
       tcombine(s);
       // 4. publish the list (16-byte vectors) for the force loop
       if (valid) {
