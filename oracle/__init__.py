@@ -70,6 +70,18 @@ class _ForceOut(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in _FORCE_F + ("n_pairs",)]
 
 
+class _SphenixCfg(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("alpha_v_max", "ell", "beta_c", "alpha_c_min",
+                                          "alpha_c_max")]
+
+
+_GRAD_F = ("lap_u", "v_c", "alpha_v_ngb", "alpha_c")
+
+
+class _GradOut(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in _GRAD_F]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -98,6 +110,17 @@ def lib():
                                    C.POINTER(_ForceOut)]
         L.oracle_neighbours.argtypes = [C.POINTER(_Particles), C.c_int64, C.c_void_p, C.c_void_p,
                                         C.c_int32, C.c_int64, C.c_void_p, C.c_void_p]
+        L.oracle_sphenix_alpha_v.restype = None
+        L.oracle_sphenix_alpha_v.argtypes = [C.c_int64, C.POINTER(_SphenixCfg), C.c_double] + \
+            [C.c_void_p] * 7
+        L.oracle_sphenix_gradient.argtypes = [C.POINTER(_Particles), C.POINTER(_Config),
+                                              C.POINTER(_SphenixCfg), C.POINTER(_DensState),
+                                              C.c_void_p, C.c_void_p, C.c_double, C.c_int64,
+                                              C.c_void_p, C.POINTER(_GradOut)]
+        L.oracle_sphenix_force.argtypes = [C.POINTER(_Particles), C.POINTER(_Config),
+                                           C.POINTER(_DensState), C.c_void_p, C.c_void_p,
+                                           C.c_int64, C.c_void_p, C.POINTER(_ForceOut),
+                                           C.c_void_p]
         L.oracle_step.argtypes = [C.c_int64, C.c_double, C.POINTER(_Config), C.c_double] + \
             [C.c_void_p] * 14 + [C.c_void_p, C.POINTER(C.c_double)]
         _lib = L
@@ -114,6 +137,20 @@ class Physics:
     eps_balsara: float = 1e-4
     h_tol: float = 1e-13
     max_iter: int = 200
+
+
+@dataclass
+class Sphenix:
+    """Constants of the SPHENIX flavour (Sec. 3.3)."""
+    alpha_v_max: float = 2.0
+    ell: float = 0.05
+    beta_c: float = 1.0
+    alpha_c_min: float = 0.0
+    alpha_c_max: float = 1.0
+
+
+def _sphenix_cfg(X: Sphenix):
+    return _SphenixCfg(X.alpha_v_max, X.ell, X.beta_c, X.alpha_c_min, X.alpha_c_max)
 
 
 def _d(a):
@@ -295,3 +332,101 @@ def step(s: dict, cfl: float, phys: Physics = Physics(), brute: bool = False) ->
                              C.byref(dt)), "step")
     s["rho"] = rho
     return dt.value
+
+
+def sphenix_alpha_v(dt: float, h, c, div_v, div_v_prev, v_sig, alpha, X: Sphenix = Sphenix()):
+    """SPHENIX viscosity parameters after a step dt (eqs. "sphenix_visc1"-"sphenix_visc4")."""
+    keep = _Keep()
+    n = int(np.asarray(h).shape[0])
+    out = np.zeros(n)
+    cfg = _sphenix_cfg(X)
+    lib().oracle_sphenix_alpha_v(n, C.byref(cfg), float(dt), keep(h), keep(c), keep(div_v),
+                                 keep(div_v_prev), keep(v_sig), keep(alpha), _ptr(out))
+    return out
+
+
+def sphenix_gradient(p: dict, state: dict, alpha_v, alpha_c, dt: float, targets=None,
+                     X: Sphenix = Sphenix(), phys: Physics = Physics(),
+                     brute: bool = False) -> dict:
+    """SPHENIX gradient pass (lap u, v_c, largest neighbour alpha_V) and the updated
+    conduction parameter alpha_c of the targets; ``alpha_v`` are the updated
+    viscosity parameters of all n particles, ``alpha_c`` the old conduction ones."""
+    keep = _Keep()
+    P = _particles(keep, p)
+    n = P.n
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else int(tg.shape[0])
+    S = _DensState(*[keep(state[k]) for k in ("h", "rho", "f", "P", "c", "B")])
+    out = {k: np.zeros(nt) for k in _GRAD_F}
+    O = _GradOut(*[_ptr(out[k]) for k in _GRAD_F])
+    cfg = _config(phys, brute)
+    xc = _sphenix_cfg(X)
+    _check(lib().oracle_sphenix_gradient(C.byref(P), C.byref(cfg), C.byref(xc), C.byref(S),
+                                         keep(alpha_v), keep(alpha_c), float(dt), nt, _ptr(tg),
+                                         C.byref(O)), "sphenix_gradient")
+    return out
+
+
+def sphenix_force(p: dict, state: dict, alpha_v, alpha_c, targets=None,
+                  phys: Physics = Physics(), brute: bool = False) -> dict:
+    """SPHENIX force loop for the given targets (``du_cond``: the conduction part of du/dt)."""
+    keep = _Keep()
+    P = _particles(keep, p)
+    n = P.n
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else int(tg.shape[0])
+    S = _DensState(*[keep(state[k]) for k in ("h", "rho", "f", "P", "c", "B")])
+    out = {k: np.zeros(nt) for k in _FORCE_F + ("du_cond",)}
+    out["n_pairs"] = np.zeros(nt, dtype=np.int32)
+    F = _ForceOut(*[_ptr(out[k]) for k in _FORCE_F + ("n_pairs",)])
+    cfg = _config(phys, brute)
+    _check(lib().oracle_sphenix_force(C.byref(P), C.byref(cfg), C.byref(S), keep(alpha_v),
+                                      keep(alpha_c), nt, _ptr(tg), C.byref(F),
+                                      _ptr(out["du_cond"])), "sphenix_force")
+    return out
+
+
+def sphenix_evaluate(p: dict, h0, alpha_v, alpha_c, div_v_prev, v_sig_prev, dt: float,
+                     X: Sphenix = Sphenix(), phys: Physics = Physics(), brute: bool = False):
+    """One SPHENIX force evaluation in the library's order: density, viscosity
+    update, gradient pass with the conduction update, force.  Returns
+    (density dict, alpha_v, gradient dict, force dict)."""
+    d = density(p, h0, None, phys, brute)
+    av = sphenix_alpha_v(dt, d["h"], d["c"], d["div_v"], div_v_prev, v_sig_prev, alpha_v, X)
+    g = sphenix_gradient(p, d, av, alpha_c, dt, None, X, phys, brute)
+    f = sphenix_force(p, d, av, g["alpha_c"], None, phys, brute)
+    return d, av, g, f
+
+
+def sphenix_step(s: dict, cfl: float, X: Sphenix = Sphenix(), phys: Physics = Physics(),
+                 brute: bool = False) -> float:
+    """One KDK step of SPHENIX in place on the state dict s (the keys of
+    ``step`` plus alpha_v, alpha_c and div_v, the divergence of the previous
+    evaluation), in the order of ``step`` with sphenix_evaluate as the force
+    evaluation on the predicted v and u; returns dt."""
+    for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "ax", "ay", "az", "du_dt", "v_sig",
+              "alpha_v", "alpha_c", "div_v"):
+        s[k] = _d(s[k]).copy()
+    L = float(s["L"])
+    dt = float(np.min(cfl * GAMMA_K * s["h"] / s["v_sig"]))
+    if not (dt > 0.0) or not np.isfinite(dt):
+        raise RuntimeError("oracle sphenix_step: no finite positive time-step")
+    wrap = lib().oracle_wrap
+    for k in ("x", "y", "z"):
+        v = "v" + k
+        s[v] = s[v] + 0.5 * dt * s["a" + k]
+        s[k] = np.array([wrap(float(q), L) for q in s[k] + s[v] * dt])
+    s["u"] = s["u"] + 0.5 * dt * s["du_dt"]
+    pred = dict(L=L, x=s["x"], y=s["y"], z=s["z"], m=s["m"],
+                vx=s["vx"] + 0.5 * dt * s["ax"], vy=s["vy"] + 0.5 * dt * s["ay"],
+                vz=s["vz"] + 0.5 * dt * s["az"], u=s["u"] + 0.5 * dt * s["du_dt"])
+    d, av, g, f = sphenix_evaluate(pred, s["h"], s["alpha_v"], s["alpha_c"], s["div_v"],
+                                   s["v_sig"], dt, X, phys, brute)
+    s["h"], s["rho"], s["div_v"] = d["h"], d["rho"], d["div_v"]
+    s["alpha_v"], s["alpha_c"] = av, g["alpha_c"]
+    for k in ("ax", "ay", "az", "du_dt", "v_sig"):
+        s[k] = f[k]
+    for k in ("x", "y", "z"):
+        s["v" + k] = s["v" + k] + 0.5 * dt * s["a" + k]
+    s["u"] = s["u"] + 0.5 * dt * s["du_dt"]
+    return dt

@@ -818,3 +818,179 @@ int oracle_fof(int64_t n, const double* x, const double* y, const double* z, dou
   free(key); free(start); free(order); free(fill); free(parent);
   return 0;
 }
+
+/* --------------------------------------------------------------------------
+ * SPHENIX flavour (Sec. 3.3): a time-dependent viscosity parameter per
+ * particle (eqs. "sphenix_visc1" to "sphenix_visc4"), the pair viscosity
+ * parameter of eq. "av_ij", and artificial conduction (eqs. "art_cond",
+ * "artconddt", "condshocklimiter", "conductionlimiter").  The dissipationless
+ * part and the form of the viscosity terms are those of oracle_force.
+ *
+ * Readings (the paper prints these equations with typos or leaves a
+ * quantity undefined):
+ *  - viscosity update: alpha_V relaxes from alpha_V(t) towards alpha_loc
+ *    with the factor exp(-ell c_i dt / H_i), and jumps to alpha_loc when
+ *    alpha_loc is larger (the printed minus sign would drive alpha negative);
+ *    the rate of the divergence is (div_v - div_v_prev) / dt, zero when
+ *    dt = 0; alpha_loc = 0 when S_i = 0; v_sig,i is the signal velocity of
+ *    the previous force evaluation;
+ *  - gradient pass (after the viscosity update), over j != i with r < H_i:
+ *      lap_u_i = 2 sum_j (m_j / rho_j) (u_i - u_j) (dW/dr)(r_ij, h_i) / r_ij
+ *    (the second-derivative estimate of Brookshaw 1985, which the paper
+ *    uses but does not print), v_c,i = max_j v_c,ij, and
+ *    alpha_V,max,i = max(alpha_V,i, max_j alpha_V,j) (updated values);
+ *  - conduction update: one explicit Euler step of eq. "artconddt" over dt,
+ *    the source term taken as zero when u_i <= 0, then the result limited to
+ *    [alpha_c,min, alpha_c,max (1 - alpha_V,max,i / alpha_V,max)];
+ *    alpha_c,max = 1 (eq. "condshocklimiter"; the second bound of 2 in the
+ *    text is read as a typo), alpha_c,min = 0;
+ *  - conduction term, over the force pairs (r < max(H_i, H_j), j != i):
+ *      du_i/dt += alpha_c,ij v_c,ij m_j (u_i - u_j)
+ *                 [f_i dW/dr(r, h_i) + f_j dW/dr(r, h_j)] / (rho_i + rho_j)
+ *    i.e. the kernel gradients of eq. "art_cond" projected on x_ij / r_ij
+ *    (the printed f_ij and grad_j W_ji, which would cancel, are read as
+ *    f_i grad_i W(h_i) + f_j grad_i W(h_j)); v_c,ij uses rho_i + rho_j (the
+ *    printed rho_j + rho_j is a typo); alpha_c,ij = 0 when P_i + P_j = 0.
+ * -------------------------------------------------------------------------- */
+typedef struct {
+  double alpha_v_max;  /* alpha_V,max, eq. "sphenix_visc2" (2)        */
+  double ell;          /* viscosity decay length, eq. "sphenix_visc1" (0.05) */
+  double beta_c;       /* beta_c of eq. "artconddt" (1)                */
+  double alpha_c_min;  /* alpha_c,min (0)                              */
+  double alpha_c_max;  /* alpha_c,max of eq. "condshocklimiter" (1)    */
+} oracle_sphenix_config;
+
+typedef struct {      /* per target */
+  double *lap_u, *v_c, *alpha_v_ngb, *alpha_c;
+} oracle_sphenix_gradient_out;
+
+/* Viscosity parameter of each of the n particles after a step dt. */
+void oracle_sphenix_alpha_v(int64_t n, const oracle_sphenix_config* X, double dt, const double* h,
+                            const double* c, const double* div_v, const double* div_v_prev,
+                            const double* v_sig, const double* alpha_in, double* alpha_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double H = OR_GAMMA_K * h[i];
+    double rate = dt > 0.0 ? (div_v[i] - div_v_prev[i]) / dt : 0.0;
+    double S = H * H * (-rate > 0.0 ? -rate : 0.0);
+    double loc = S > 0.0 ? X->alpha_v_max * S / (v_sig[i] * v_sig[i] + S) : 0.0;
+    double a = alpha_in[i];
+    if (loc > a)
+      alpha_out[i] = loc;
+    else
+      alpha_out[i] = loc + (a - loc) * exp(-X->ell * c[i] * dt / H);
+  }
+}
+
+/* Conduction signal speed of a pair (x_ij, v_ij . x_ij, r). */
+static double or_v_cond(double vdotx, double r, double Pi, double Pj, double rhoi, double rhoj) {
+  return fabs(vdotx) / r + sqrt(2.0 * fabs(Pi - Pj) / (rhoi + rhoj));
+}
+
+/* Gradient pass and conduction-parameter update for the given targets.
+ * alpha_v holds the updated viscosity parameters of all n particles,
+ * alpha_c_in the conduction parameters before the step. */
+int oracle_sphenix_gradient(const oracle_particles* P, const oracle_config* C, const oracle_sphenix_config* X,
+                            const oracle_density_state* S, const double* alpha_v, const double* alpha_c_in,
+                            double dt, int64_t n_t, const int64_t* targets, oracle_sphenix_gradient_out* out) {
+  int64_t n = P->n;
+  double L = P->L;
+  or_grid G;
+  int err = or_grid_build(&G, n, L, P->x, P->y, P->z, OR_GAMMA_K * or_median(S->h, n), C->brute);
+  if (err) { or_grid_free(&G); return err; }
+  or_list l = {0};
+  for (int64_t t = 0; t < n_t && !err; ++t) {
+    int64_t i = targets ? targets[t] : t;
+    double hi = S->h[i], Hi = OR_GAMMA_K * hi;
+    if (Hi >= 0.5 * L) { err = -5; break; }
+    err = or_collect(&G, P->x[i], P->y[i], P->z[i], Hi, i, &l);
+    if (err) break;
+    double lap = 0.0, vc = 0.0, avmax = alpha_v[i];
+    for (int64_t k = 0; k < l.len; ++k) {
+      int32_t j = l.j[k];
+      double r = l.r[k];
+      if (!(r > 0.0)) continue;
+      double vdotx = (P->vx[i] - P->vx[j]) * l.dx[k] + (P->vy[i] - P->vy[j]) * l.dy[k] +
+                     (P->vz[i] - P->vz[j]) * l.dz[k];
+      lap += P->m[j] / S->rho[j] * (P->u[i] - P->u[j]) * or_dWdr(r, hi) / r;
+      double v = or_v_cond(vdotx, r, S->P[i], S->P[j], S->rho[i], S->rho[j]);
+      if (v > vc) vc = v;
+      if (alpha_v[j] > avmax) avmax = alpha_v[j];
+    }
+    lap *= 2.0;
+    double src = P->u[i] > 0.0 ? X->beta_c * Hi * lap / sqrt(P->u[i]) : 0.0;
+    double rate = src - (alpha_c_in[i] - X->alpha_c_min) * vc / Hi;
+    double a = alpha_c_in[i] + dt * rate;
+    double cap = X->alpha_c_max * (1.0 - avmax / X->alpha_v_max);
+    if (a > cap) a = cap;
+    if (a < X->alpha_c_min) a = X->alpha_c_min;
+    out->lap_u[t] = lap;
+    out->v_c[t] = vc;
+    out->alpha_v_ngb[t] = avmax;
+    out->alpha_c[t] = a;
+  }
+  or_list_free(&l);
+  or_grid_free(&G);
+  return err;
+}
+
+/* Force loop of SPHENIX for the given targets: oracle_force with
+ * alpha_ij = (alpha_V,i + alpha_V,j)/2 (B_i + B_j)/2 and the conduction term
+ * added to du/dt (du_cond, optional, receives the conduction part alone). */
+int oracle_sphenix_force(const oracle_particles* P, const oracle_config* C, const oracle_density_state* S,
+                         const double* alpha_v, const double* alpha_c, int64_t n_t, const int64_t* targets,
+                         oracle_force_out* out, double* du_cond) {
+  int64_t n = P->n;
+  double L = P->L;
+  double hmax = 0.0;
+  for (int64_t j = 0; j < n; ++j) hmax = S->h[j] > hmax ? S->h[j] : hmax;
+  double Hmax = OR_GAMMA_K * hmax;
+  if (Hmax >= 0.5 * L) return -5;
+  or_grid G;
+  int err = or_grid_build(&G, n, L, P->x, P->y, P->z, OR_GAMMA_K * or_median(S->h, n), C->brute);
+  if (err) { or_grid_free(&G); return err; }
+  or_list l = {0};
+  for (int64_t t = 0; t < n_t && !err; ++t) {
+    int64_t i = targets ? targets[t] : t;
+    err = or_collect(&G, P->x[i], P->y[i], P->z[i], Hmax, i, &l);
+    if (err) break;
+    double hi = S->h[i], Hi = OR_GAMMA_K * hi;
+    double rhoi = S->rho[i], fi = S->f[i], Pi = S->P[i], ci = S->c[i], Bi = S->B[i];
+    double ax = 0, ay = 0, az = 0, du = 0, cond = 0, vsig = 0;
+    int32_t np = 0;
+    for (int64_t k = 0; k < l.len; ++k) {
+      int32_t j = l.j[k];
+      double r = l.r[k];
+      double hj = S->h[j], Hj = OR_GAMMA_K * hj;
+      if (!(r < (Hi > Hj ? Hi : Hj))) continue;
+      np += 1;
+      double dx = l.dx[k], dy = l.dy[k], dz = l.dz[k];
+      double vx = P->vx[i] - P->vx[j], vy = P->vy[i] - P->vy[j], vz = P->vz[i] - P->vz[j];
+      double vdotx = vx * dx + vy * dy + vz * dz;
+      double Gi = or_dWdr(r, hi) / r;
+      double Gj = or_dWdr(r, hj) / r;
+      double rhoj = S->rho[j], fj = S->f[j], Pj = S->P[j], cj = S->c[j], Bj = S->B[j];
+      double mu = vdotx < 0.0 ? vdotx / r : 0.0;
+      double vs = ci + cj - C->beta_v * mu;
+      double alpha = 0.5 * (alpha_v[i] + alpha_v[j]) * 0.5 * (Bi + Bj);
+      double nu = -alpha * mu * vs / (0.5 * (rhoi + rhoj));
+      double pi_term = fi * Pi / (rhoi * rhoi) * Gi;
+      double pj_term = fj * Pj / (rhoj * rhoj) * Gj;
+      double visc = fi * Gi + fj * Gj;
+      double s = P->m[j] * (pi_term + pj_term + 0.5 * nu * visc);
+      ax -= s * dx; ay -= s * dy; az -= s * dz;
+      du += P->m[j] * (pi_term + 0.25 * nu * visc) * vdotx;
+      double ac = Pi + Pj > 0.0 ? (Pi * alpha_c[i] + Pj * alpha_c[j]) / (Pi + Pj) : 0.0;
+      double vc = or_v_cond(vdotx, r, Pi, Pj, rhoi, rhoj);
+      double gsum = fi * or_dWdr(r, hi) + fj * or_dWdr(r, hj);
+      cond += ac * vc * P->m[j] * (P->u[i] - P->u[j]) * gsum / (rhoi + rhoj);
+      if (vs > vsig) vsig = vs;
+    }
+    out->ax[t] = ax; out->ay[t] = ay; out->az[t] = az;
+    out->du_dt[t] = du + cond; out->v_sig[t] = vsig;
+    out->n_pairs[t] = np;
+    if (du_cond) du_cond[t] = cond;
+  }
+  or_list_free(&l);
+  or_grid_free(&G);
+  return err;
+}
