@@ -259,6 +259,75 @@ int sph_force(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
  * SPH_ST_REBUILD is rebuilt with larger cells and repeated internally. */
 int sph_step(sph_ctx* ctx, const sph_pool* pool);
 
+/* ---- SPHENIX flavour (Sec. 3.3) ------------------------------------------
+ * The default flavour of the paper: a viscosity parameter alpha_V,i carried
+ * by each particle and evolved with a shock indicator (eqs. "sphenix_visc1"
+ * to "sphenix_visc4"), the pair parameter alpha_V,ij = (alpha_V,i +
+ * alpha_V,j)/2 (B_i + B_j)/2 (eq. "av_ij"), and artificial conduction with a
+ * parameter alpha_c,i evolved from the Laplacian of u and limited near shocks
+ * (eqs. "art_cond", "artconddt", "condshocklimiter", "conductionlimiter").
+ * An evaluation is: sph_density, then sph_sphenix_gradient (viscosity
+ * update, then a third neighbour loop over r < H_i that computes lap u and
+ * updates alpha_c), then sph_force_sphenix.  Where the paper's equations are
+ * garbled or silent, the library reads them as follows:
+ *   viscosity:  rate = (div_v - div_v_prev)/dt (0 if dt = 0),
+ *               S = H^2 max(0, -rate),
+ *               alpha_loc = alpha_V,max S/(v_sig^2 + S) (0 if S = 0), with
+ *               v_sig from the previous force evaluation;
+ *               alpha_V <- alpha_loc if that is larger, else
+ *               alpha_loc + (alpha_V - alpha_loc) exp(-ell c dt / H);
+ *   gradient:   lap u_i = 2 sum_{j != i, r < H_i} (m_j/rho_j)(u_i - u_j) W'(r, h_i)/r,
+ *               v_c,i = max_j v_c,ij,
+ *               v_c,ij = |v_ij . x_ij|/r + sqrt(2 |P_i - P_j|/(rho_i + rho_j)),
+ *               alpha_V,max,i = max(alpha_V,i, max_j alpha_V,j);
+ *   conduction: alpha_c += dt [beta_c H lap u / sqrt(u) - (alpha_c - alpha_c,min) v_c,i / H]
+ *               (no source where u <= 0), then limited to
+ *               [alpha_c,min, alpha_c,max (1 - alpha_V,max,i / alpha_V,max)];
+ *   force:      du_i/dt += alpha_c,ij v_c,ij m_j (u_i - u_j)
+ *                          [f_i W'(r, h_i) + f_j W'(r, h_j)] / (rho_i + rho_j)
+ *               over the force pairs, alpha_c,ij = (P_i alpha_c,i + P_j alpha_c,j)/(P_i + P_j)
+ *               (0 if P_i + P_j = 0).
+ * Uniform grid only: with SPH_FLAG_TREE these calls return SPH_E_INVAL. */
+typedef struct sph_sphenix_params {
+  double alpha_v_max;  /* alpha_V,max (2)                               */
+  double ell;          /* viscosity decay length ell (0.05)             */
+  double beta_c;       /* beta_c of eq. "artconddt" (1)                 */
+  double alpha_c_min;  /* alpha_c,min (0)                               */
+  double alpha_c_max;  /* alpha_c,max of eq. "condshocklimiter" (1)     */
+} sph_sphenix_params;
+
+/* Per-particle SPHENIX arrays of one simulation (device, length n, input order). */
+typedef struct sph_sphenix_state {
+  float *alpha_v;       /* in/out: viscosity parameter alpha_V,i               */
+  float *alpha_c;       /* in/out: conduction parameter alpha_c,i              */
+  float *div_v_prev;    /* in: the divergence of the previous evaluation;
+                           out: this evaluation's (d->div_v)                   */
+  const float *v_sig;   /* in: the signal velocity of the previous force       */
+  float *lap_u;         /* out, optional (NULL): lap u                         */
+} sph_sphenix_state;
+
+void sph_sphenix_default_params(sph_sphenix_params* x);
+
+/* Between sph_density and sph_force_sphenix on the same cells: updates
+ * st->alpha_v over the step dt (>= 0), then runs the gradient pass and
+ * updates st->alpha_c over dt.  d holds this evaluation's density results. */
+int sph_sphenix_gradient(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
+                         const sph_density_out* d, const sph_sphenix_params* x, double dt,
+                         sph_sphenix_state* st);
+/* SPHENIX force loop: sph_force with the viscosity parameters alpha_v and the
+ * conduction term with the parameters alpha_c (device, input order), both as
+ * left by sph_sphenix_gradient. */
+int sph_force_sphenix(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
+                      const sph_density_out* d, const float* alpha_v, const float* alpha_c,
+                      sph_force_out* out);
+/* sph_step with the SPHENIX force evaluation (density, viscosity update over
+ * the step's dt, gradient pass, SPHENIX force), for a pool.  pool->div_v and
+ * pool->v_sig hold the previous evaluation's values on entry (as after
+ * sph_density + sph_sphenix_gradient + sph_force_sphenix); alpha_v and
+ * alpha_c are device arrays of n_total (pool order), updated in place. */
+int sph_step_sphenix(sph_ctx* ctx, const sph_pool* pool, const sph_sphenix_params* x, float* alpha_v,
+                     float* alpha_c);
+
 /* FP64 conservation sums of a pool after a force evaluation, per simulation:
  * out[4 s + 0..2] = sum m a, out[4 s + 3] = sum m (v . a + du/dt) with the
  * velocities given (device array out of 4 n_sims doubles). */

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -60,6 +61,9 @@ struct sph_ctx {
   int4* fine = nullptr;
   float4* rel = nullptr;
   float4* trec = nullptr;  // force records of the nested grids, 4 per particle
+  float4* sx4 = nullptr;   // SPHENIX: sorted (u, alpha_V, P, alpha_c)
+  float* dvp = nullptr;    // SPHENIX step: the divergence of the previous evaluation
+  int64_t cap_sx = 0;
   uint32_t* tlists = nullptr;
   uint64_t* rev_raw = nullptr;
   uint32_t* rev = nullptr;
@@ -228,6 +232,23 @@ int ensure(sph_ctx* c, int64_t n, int n_sims, int cells_per_particle = 8) {
   c->cap_cells = cc;
   c->lists_valid = false;
   c->built_n = -1;
+  return SPH_OK;
+}
+
+// SPHENIX scratch for n particles (kept apart from the loops' scratch).
+int ensure_sphenix(sph_ctx* c, int64_t n) {
+  if (n <= c->cap_sx) return SPH_OK;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  dfree(c->sx4);
+  dfree(c->dvp);
+  c->cap_sx = 0;
+  const int64_t cn = n + n / 4 + 64;
+  if (!(dalloc(c->sx4, cn) && dalloc(c->dvp, cn))) {
+    dfree(c->sx4);
+    dfree(c->dvp);
+    return SPH_E_NOMEM;
+  }
+  c->cap_sx = cn;
   return SPH_OK;
 }
 
@@ -563,10 +584,40 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   return cuda_code(e);
 }
 
+bool sphenix_params_ok(const sph_sphenix_params& x) {
+  return std::isfinite(x.alpha_v_max) && x.alpha_v_max > 0.0 && std::isfinite(x.ell) && x.ell >= 0.0 &&
+         std::isfinite(x.beta_c) && x.beta_c >= 0.0 && std::isfinite(x.alpha_c_min) && x.alpha_c_min >= 0.0 &&
+         std::isfinite(x.alpha_c_max) && x.alpha_c_max >= x.alpha_c_min;
+}
+
+sphk::SphenixDev sphenix_dev(const sph_sphenix_params& x, double dt, const double* dt_dev) {
+  sphk::SphenixDev d;
+  d.av_max = (float)x.alpha_v_max;
+  d.ell = (float)x.ell;
+  d.beta_c = (float)x.beta_c;
+  d.ac_min = (float)x.alpha_c_min;
+  d.ac_max = (float)x.alpha_c_max;
+  d.dt = dt;
+  d.dt_dev = dt_dev;
+  return d;
+}
+
+// A SPHENIX pass of do_force: the gradient pass (gradient = true: writes
+// alpha_c_out and, if given, lap_u) or the SPHENIX force.  The E records are
+// gathered from u, alpha_v, P and alpha_c; skip_gather reuses the A..D
+// records of the previous pass on the same build and inputs.
+struct SphenixCall {
+  bool gradient = false;
+  bool skip_gather = false;
+  const float *u = nullptr, *alpha_v = nullptr, *alpha_c = nullptr;
+  float *alpha_c_out = nullptr, *lap_u = nullptr;
+  sphk::SphenixDev x;
+};
+
 int do_force(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
              const float* vy, const float* vz, const float* m, const float* h, const float* rho,
              const float* f, const float* P, const float* cs, const float* B, float* ax, float* ay,
-             float* az, float* du_dt, float* v_sig, bool pos_ready = false) {
+             float* az, float* du_dt, float* v_sig, bool pos_ready = false, const SphenixCall* sx = nullptr) {
   sphh::GatherForceArgs g;
   // the nested-grid force reads positions from its own copies (fA.w only)
   g.positions = (pos_ready || c->built_tree) ? 0 : 1;
@@ -598,9 +649,13 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
     g.rec = c->trec;
   }
   t_begin(c, SPH_T_GATHER);
-  if (sphh::launch_gather_force(g, c->st) != cudaSuccess) return SPH_E_CUDA;
+  if (!(sx && sx->skip_gather) && sphh::launch_gather_force(g, c->st) != cudaSuccess) return SPH_E_CUDA;
+  if (sx && sphh::launch_gather_sphenix(c->built_n, c->perm, sx->u, sx->alpha_v, P, sx->alpha_c, c->sx4,
+                                        c->st) != cudaSuccess)
+    return SPH_E_CUDA;
   t_end(c, SPH_T_GATHER);
-  if (c->p.flags & SPH_FLAG_COUNT_PAIRS)
+  if (sx && c->built_tree) return SPH_E_INVAL;  // SPHENIX runs on the uniform grid only
+  if (c->p.flags & SPH_FLAG_COUNT_PAIRS && !(sx && sx->gradient))
     if (cudaMemsetAsync(c->pairs + 1, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
       return SPH_E_CUDA;
   if (c->built_tree) {
@@ -665,7 +720,20 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   a.lists = c->lists_valid ? c->lists : nullptr;
   a.list_cnt = c->list_cnt;
   t_begin(c, SPH_T_FORCE);
-  const cudaError_t e = sphh::launch_force(a, phys_of(c->p), c->st);
+  cudaError_t e;
+  if (sx) {
+    a.fE = c->sx4;
+    if (sx->gradient) {
+      a.pairs = nullptr;
+      a.alpha_c_out = sx->alpha_c_out;
+      a.lap_u = sx->lap_u;
+      e = sphh::launch_sphenix_gradient(a, phys_of(c->p), sx->x, c->st);
+    } else {
+      e = sphh::launch_sphenix_force(a, phys_of(c->p), sx->x, c->st);
+    }
+  } else {
+    e = sphh::launch_force(a, phys_of(c->p), c->st);
+  }
   t_end(c, SPH_T_FORCE);
   return cuda_code(e);
 }
@@ -730,6 +798,8 @@ void sph_destroy(sph_ctx* c) {
   }
   free_grown(c);
   free_tree(c);
+  dfree(c->sx4);
+  dfree(c->dvp);
   dfree(c->misc);
   dfree(c->pairs);
   dfree(c->off1);
@@ -851,7 +921,9 @@ int sph_force(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const
   return rc != SPH_OK ? rc : finish(c);
 }
 
-int sph_step(sph_ctx* c, const sph_pool* pl) {
+// One KDK step; with X, the SPHENIX flavour with its parameters alpha_v and
+// alpha_c (in/out, pool order).
+int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float* alpha_v, float* alpha_c) {
   if (!c || !pl || pl->n_sims < 1 || pl->n_total < 0 || pl->n_total > INT32_MAX / 16) return SPH_E_INVAL;
   if (!pl->sim_offset || !pl->box_size || !pl->dt) return SPH_E_INVAL;
   if (pl->n_total > 0 &&
@@ -859,8 +931,14 @@ int sph_step(sph_ctx* c, const sph_pool* pl) {
        !pl->ax || !pl->ay || !pl->az || !pl->du_dt || !pl->v_sig || !pl->rho || !pl->f ||
        !pl->div_v || !pl->curl_v || !pl->P || !pl->c || !pl->balsara))
     return SPH_E_INVAL;
+  if (X && pl->n_total > 0 && (!alpha_v || !alpha_c)) return SPH_E_INVAL;
+  if (X && (c->p.flags & SPH_FLAG_TREE)) return SPH_E_INVAL;
   int rc = ensure(c, pl->n_total, pl->n_sims);
   if (rc != SPH_OK) return rc;
+  if (X) {
+    rc = ensure_sphenix(c, pl->n_total);
+    if (rc != SPH_OK) return rc;
+  }
   sphh::StepArgs s;
   s.n_sims = pl->n_sims;
   s.n_total = pl->n_total;
@@ -893,6 +971,12 @@ int sph_step(sph_ctx* c, const sph_pool* pl) {
   if (sphh::launch_dt(s, c->st) != cudaSuccess) return SPH_E_CUDA;
   if (sphh::launch_kick_drift(s, c->st) != cudaSuccess) return SPH_E_CUDA;
   t_end(c, SPH_T_INTEGRATE);
+  // SPHENIX: the divergence of the previous evaluation, before the density
+  // loop replaces it
+  if (X && pl->n_total > 0 &&
+      cudaMemcpyAsync(c->dvp, pl->div_v, sizeof(float) * (size_t)pl->n_total, cudaMemcpyDeviceToDevice, c->st) !=
+          cudaSuccess)
+    return SPH_E_CUDA;
   const bool sync = (c->p.flags & SPH_FLAG_SYNC) != 0;
   for (int attempt = 0;; ++attempt) {
     rc = do_build(c, pl->n_sims, pl->n_total, pl->sim_offset, pl->box_size, pl->x, pl->y, pl->z, pl->h);
@@ -923,13 +1007,102 @@ int sph_step(sph_ctx* c, const sph_pool* pl) {
   }
   // same build and positions as the density just run: its gather already
   // wrote the cell-relative positions into the buffer the force reads
-  rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P,
-                pl->c, pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig, true);
+  if (X) {
+    const sphk::SphenixDev xd = sphenix_dev(*X, 0.0, pl->dt);
+    sphh::SphenixAlphaArgs aa{pl->n_total, pl->n_sims, pl->sim_offset, pl->h, pl->c, pl->div_v, pl->v_sig,
+                              c->dvp, alpha_v};
+    t_begin(c, SPH_T_INTEGRATE);
+    if (sphh::launch_sphenix_alpha_v(aa, xd, c->st) != cudaSuccess) return SPH_E_CUDA;
+    t_end(c, SPH_T_INTEGRATE);
+    SphenixCall g;
+    g.gradient = true;
+    g.u = c->up;
+    g.alpha_v = alpha_v;
+    g.alpha_c = alpha_c;
+    g.alpha_c_out = alpha_c;
+    g.x = xd;
+    rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P, pl->c,
+                  pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig, true, &g);
+    if (rc != SPH_OK) return rc;
+    SphenixCall f = g;
+    f.gradient = false;
+    f.skip_gather = true;
+    rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P, pl->c,
+                  pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig, true, &f);
+  } else {
+    rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P,
+                  pl->c, pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig, true);
+  }
   if (rc != SPH_OK) return rc;
   t_begin(c, SPH_T_INTEGRATE);
   if (sphh::launch_kick(s, c->st) != cudaSuccess) return SPH_E_CUDA;
   t_end(c, SPH_T_INTEGRATE);
   return finish(c);
+}
+
+int sph_step(sph_ctx* c, const sph_pool* pl) { return step_impl(c, pl, nullptr, nullptr, nullptr); }
+
+void sph_sphenix_default_params(sph_sphenix_params* x) {
+  if (!x) return;
+  x->alpha_v_max = 2.0;
+  x->ell = 0.05;
+  x->beta_c = 1.0;
+  x->alpha_c_min = 0.0;
+  x->alpha_c_max = 1.0;
+}
+
+int sph_sphenix_gradient(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
+                         const sph_sphenix_params* X, double dt, sph_sphenix_state* st) {
+  if (!c || !cells || !in || !d || !X || !st || !sphenix_params_ok(*X) || !(dt >= 0.0) || !std::isfinite(dt))
+    return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n == 0) return SPH_OK;
+  if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !in->u || !d->h || !d->rho ||
+      !d->f || !d->div_v || !d->P || !d->c || !d->balsara || !st->alpha_v || !st->alpha_c || !st->div_v_prev ||
+      !st->v_sig)
+    return SPH_E_INVAL;
+  int rc = ensure_sphenix(c, in->n);
+  if (rc != SPH_OK) return rc;
+  const sphk::SphenixDev xd = sphenix_dev(*X, dt, nullptr);
+  sphh::SphenixAlphaArgs aa{in->n, 1, nullptr, d->h, d->c, d->div_v, st->v_sig, st->div_v_prev, st->alpha_v};
+  if (sphh::launch_sphenix_alpha_v(aa, xd, c->st) != cudaSuccess) return SPH_E_CUDA;
+  SphenixCall g;
+  g.gradient = true;
+  g.u = in->u;
+  g.alpha_v = st->alpha_v;
+  g.alpha_c = st->alpha_c;
+  g.alpha_c_out = st->alpha_c;
+  g.lap_u = st->lap_u;
+  g.x = xd;
+  rc = do_force(c, in->x, in->y, in->z, in->vx, in->vy, in->vz, in->m, d->h, d->rho, d->f, d->P, d->c,
+                d->balsara, nullptr, nullptr, nullptr, nullptr, nullptr, false, &g);
+  return rc != SPH_OK ? rc : finish(c);
+}
+
+int sph_force_sphenix(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
+                      const float* alpha_v, const float* alpha_c, sph_force_out* out) {
+  if (!c || !cells || !in || !d || !out) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n == 0) return SPH_OK;
+  if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !in->u || !d->h || !d->rho ||
+      !d->f || !d->P || !d->c || !d->balsara || !alpha_v || !alpha_c || !out->ax || !out->ay || !out->az ||
+      !out->du_dt || !out->v_sig)
+    return SPH_E_INVAL;
+  int rc = ensure_sphenix(c, in->n);
+  if (rc != SPH_OK) return rc;
+  SphenixCall f;
+  f.u = in->u;
+  f.alpha_v = alpha_v;
+  f.alpha_c = alpha_c;
+  rc = do_force(c, in->x, in->y, in->z, in->vx, in->vy, in->vz, in->m, d->h, d->rho, d->f, d->P, d->c,
+                d->balsara, out->ax, out->ay, out->az, out->du_dt, out->v_sig, false, &f);
+  return rc != SPH_OK ? rc : finish(c);
+}
+
+int sph_step_sphenix(sph_ctx* c, const sph_pool* pool, const sph_sphenix_params* X, float* alpha_v,
+                     float* alpha_c) {
+  if (!X || !sphenix_params_ok(*X)) return SPH_E_INVAL;
+  return step_impl(c, pool, X, alpha_v, alpha_c);
 }
 
 int sph_conservation(sph_ctx* c, const sph_pool* pl, double* out) {

@@ -15,6 +15,23 @@
 //   du_i  += m_j [ fP_i G_i + nu/4 (f_i G_i + f_j G_j) ] v_ij . x_ij
 // with fP = f P / rho^2; v_sig,i is the maximum of vsig over the list.
 // Blocks whose neighbourhood does not fit are done by k_force_overflow.
+//
+// The SPHENIX flavour (Sec. 3.3) runs the same kernels with a fifth record
+// per source, E = (u, alpha_V, P, alpha_c):
+//  - kFlSphenix, the force: alpha_V (B_i + B_j)/2 becomes
+//    (alpha_V,i + alpha_V,j)/2 (B_i + B_j)/2 (eq. "av_ij"), and du_i gains the
+//    conduction term (eq. "art_cond") over the same pairs,
+//      alpha_c,ij v_c,ij m_j (u_i - u_j) r (f_i G_i + f_j G_j) / (rho_i + rho_j),
+//    alpha_c,ij = (P_i alpha_c,i + P_j alpha_c,j) / (P_i + P_j),
+//    v_c,ij = |v_ij . x_ij| / r + sqrt(2 |P_i - P_j| / (rho_i + rho_j));
+//  - kFlGradient, the gradient pass over r < H_i: lap u_i =
+//    2 sum_j (m_j / rho_j)(u_i - u_j) G_i, v_c,i = max_j v_c,ij and the largest
+//    alpha_V of the target and its neighbours, then the conduction parameter's
+//    Euler step (eq. "artconddt") and its limiters (eqs. "condshocklimiter",
+//    "conductionlimiter").
+// The fifth record costs 16 bytes of shared memory per staged source, so the
+// SPHENIX kernels stage at most 1024 sources per block (two blocks per SM);
+// larger neighbourhoods go to the overflow kernel.
 #include "blocks.cuh"
 #include "sph_internal.cuh"
 #include "sph_launch.h"
@@ -22,15 +39,31 @@
 
 namespace sphk {
 
-constexpr int kForceBlkCap = kBlkStageCap;
+enum : int { kFlMinimal = 0, kFlSphenix = 1, kFlGradient = 2 };
+
+template <int kFl>
+__host__ __device__ constexpr int force_cap() {
+  return kFl == kFlMinimal ? kBlkStageCap : 1024;
+}
+template <int kFl>
+__host__ __device__ constexpr size_t rec_bytes() {  // staged bytes per source
+  return 3 * sizeof(float4) + sizeof(float2) + (kFl != kFlMinimal ? sizeof(float4) : 0);
+}
 constexpr int kFListCap = 48;
 constexpr int kFListEager = 4;  // 16-byte list words loaded before the count is known
-// per source: A (x, y, z, H), B (vx, vy, vz, m), C (fP, f, c, B), D (rho, 1/H)
-constexpr size_t kForceBlkSmem = (size_t)kForceBlkCap * (3 * sizeof(float4) + sizeof(float2)) +
-                                 (size_t)kBlkWarps * kFListCap * 32 * sizeof(uint16_t) + sizeof(StageTable) +
-                                 sizeof(BlockTargets) + (size_t)kForceBlkCap * (sizeof(uint16_t) + sizeof(uint8_t));
+// per source: A (x, y, z, H), B (vx, vy, vz, m), C (fP, f, c, B), D (rho, 1/H),
+// and for SPHENIX E (u, alpha_V, P, alpha_c)
+template <int kFl>
+__host__ __device__ constexpr size_t force_blk_smem() {
+  return (size_t)force_cap<kFl>() * rec_bytes<kFl>() + (size_t)kBlkWarps * kFListCap * 32 * sizeof(uint16_t) +
+         sizeof(StageTable) + sizeof(BlockTargets) + (size_t)force_cap<kFl>() * (sizeof(uint16_t) + sizeof(uint8_t));
+}
+static_assert(2 * (force_blk_smem<kFlSphenix>() + 1024) <= 228 * 1024, "two SPHENIX blocks per SM");
 constexpr int kFOvfCap = 160;
-constexpr size_t kFOvfSmem = (size_t)kWarpsPerBlock * kFOvfCap * (3 * sizeof(float4) + sizeof(float2));
+template <int kFl>
+__host__ __device__ constexpr size_t fovf_smem() {
+  return (size_t)kWarpsPerBlock * kFOvfCap * rec_bytes<kFl>();
+}
 
 struct ForceSums {
   float ax, ay, az, du, vsig;
@@ -38,7 +71,7 @@ struct ForceSums {
 };
 
 struct ForceTarget {
-  float4 A, B, C;
+  float4 A, B, C, E;
   float2 D;
   float Hinv5;
 };
@@ -48,21 +81,32 @@ __device__ __forceinline__ void fsums_zero(ForceSums& s) {
   s.npair = 0;
 }
 
+template <int kFl>
 __device__ __forceinline__ void force_pair(const ForceTarget& T, const float4& Aj, const float4& Bj,
-                                           const float4& Cj, const float2& Dj, const PhysDev& ph,
-                                           bool counted, ForceSums& s) {
+                                           const float4& Cj, const float2& Dj, const float4& Ej,
+                                           const PhysDev& ph, bool counted, ForceSums& s) {
   const float dx = T.A.x - Aj.x, dy = T.A.y - Aj.y, dz = T.A.z - Aj.z;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float r = r2 * rinv;
   const float Gi = kernel_g(r * T.D.y, T.A.w * rinv) * T.Hinv5;
-  const float Hj2 = Dj.y * Dj.y;
-  const float Gj = kernel_g(r * Dj.y, Aj.w * rinv) * (Hj2 * Hj2 * Dj.y);
   const float vx = T.B.x - Bj.x, vy = T.B.y - Bj.y, vz = T.B.z - Bj.z;
   const float vdotx = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+  if constexpr (kFl == kFlGradient) {
+    // zero beyond H_i (G_i = 0) and for the self pair (u_i - u_j = 0)
+    s.ax = fmaf(__fdividef(Bj.w, Dj.x) * (T.E.x - Ej.x), Gi, s.ax);
+    const float vc = fmaf(fabsf(vdotx), rinv, sqrtf(__fdividef(2.0f * fabsf(T.E.z - Ej.z), T.D.x + Dj.x)));
+    s.vsig = counted ? fmaxf(s.vsig, vc) : s.vsig;
+    s.ay = counted ? fmaxf(s.ay, Ej.y) : s.ay;
+    s.npair += counted;
+    return;
+  }
+  const float Hj2 = Dj.y * Dj.y;
+  const float Gj = kernel_g(r * Dj.y, Aj.w * rinv) * (Hj2 * Hj2 * Dj.y);
   const float mu = fminf(vdotx, 0.0f) * rinv;
   const float vs = fmaf(-ph.beta_v, mu, T.C.z + Cj.z);
-  const float nu = __fdividef(-ph.alpha_v * (T.C.w + Cj.w) * mu * vs, T.D.x + Dj.x);
+  const float av = kFl == kFlSphenix ? 0.5f * (T.E.y + Ej.y) : ph.alpha_v;
+  const float nu = __fdividef(-av * (T.C.w + Cj.w) * mu * vs, T.D.x + Dj.x);
   const float piG = T.C.x * Gi;
   const float visc = fmaf(T.C.y, Gi, Cj.y * Gj);
   const float sc = Bj.w * fmaf(0.5f * nu, visc, fmaf(Cj.x, Gj, piG));
@@ -70,6 +114,13 @@ __device__ __forceinline__ void force_pair(const ForceTarget& T, const float4& A
   s.ay = fmaf(-sc, dy, s.ay);
   s.az = fmaf(-sc, dz, s.az);
   s.du = fmaf(Bj.w * fmaf(0.25f * nu, visc, piG), vdotx, s.du);
+  if constexpr (kFl == kFlSphenix) {
+    // conduction: zero beyond both supports (visc = 0) and for r = 0
+    const float Ps = T.E.z + Ej.z, rs = T.D.x + Dj.x;
+    const float ac = Ps > 0.0f ? __fdividef(fmaf(T.E.z, T.E.w, Ej.z * Ej.w), Ps) : 0.0f;
+    const float vc = fmaf(fabsf(vdotx), rinv, sqrtf(__fdividef(2.0f * fabsf(T.E.z - Ej.z), rs)));
+    s.du = fmaf(Bj.w * ac * vc * (T.E.x - Ej.x) * r, __fdividef(visc, rs), s.du);
+  }
   s.vsig = counted ? fmaxf(s.vsig, vs) : s.vsig;
   s.npair += counted;
 }
@@ -77,6 +128,28 @@ __device__ __forceinline__ void force_pair(const ForceTarget& T, const float4& A
 __device__ __forceinline__ void finish_target(ForceTarget& T) {
   const float h2 = T.D.y * T.D.y;
   T.Hinv5 = h2 * h2 * T.D.y;
+}
+
+// The gradient pass's result: the Euler step of eq. "artconddt" over dt,
+//   alpha_c += dt [beta_c H lap_u / sqrt(u) - (alpha_c - alpha_c,min) v_c / H]
+// (no source where u <= 0), limited to
+// [alpha_c,min, alpha_c,max (1 - alpha_V,max,i / alpha_V,max)].
+__device__ __forceinline__ void gradient_write(const sphh::ForceArgs& a, const SphenixDev& x, float dt, int32_t ti,
+                                               const ForceTarget& T, const ForceSums& s) {
+  const int32_t p = a.perm[ti];
+  const float lap = 2.0f * s.ax;
+  const float H = T.A.w, u = T.E.x, ac = T.E.w;
+  const float src = u > 0.0f ? x.beta_c * H * lap / sqrtf(u) : 0.0f;
+  const float rate = src - (ac - x.ac_min) * s.vsig / H;
+  float an = fmaf(dt, rate, ac);
+  an = fminf(an, x.ac_max * (1.0f - s.ay / x.av_max));
+  an = fmaxf(an, x.ac_min);
+  a.alpha_c_out[p] = an;
+  if (a.lap_u != nullptr) a.lap_u[p] = lap;
+}
+
+__device__ __forceinline__ float block_dt(const sphh::ForceArgs& a, const SphenixDev& x, int32_t b) {
+  return (float)(x.dt_dev != nullptr ? x.dt_dev[sim_of_block(a.grid, a.n_sims, b)] : x.dt);
 }
 
 __device__ __forceinline__ void force_write(const sphh::ForceArgs& a, int32_t ti, const ForceSums& s) {
@@ -88,12 +161,27 @@ __device__ __forceinline__ void force_write(const sphh::ForceArgs& a, int32_t ti
   a.v_sig[p] = s.vsig;
 }
 
+// The gradient pass's SPHENIX sums in the force sums' fields: ax = the
+// Laplacian sum, ay = the largest alpha_V (a maximum), vsig = the largest
+// v_c,ij.
+template <int kFl>
+__device__ __forceinline__ void fsums_add(ForceSums& s, const ForceSums& t) {
+  s.ax += t.ax;
+  s.ay = kFl == kFlGradient ? fmaxf(s.ay, t.ay) : s.ay + t.ay;
+  s.az += t.az;
+  s.du += t.du;
+  s.vsig = fmaxf(s.vsig, t.vsig);
+  s.npair += t.npair;
+}
+
+template <int kFl>
 __device__ __forceinline__ void fcombine(ForceSums& s, int tpp) {
 #pragma unroll
   for (int o = 1; o < 4; o <<= 1) {
     if (o < tpp) {
       s.ax += __shfl_xor_sync(0xffffffffu, s.ax, o);
-      s.ay += __shfl_xor_sync(0xffffffffu, s.ay, o);
+      const float ay = __shfl_xor_sync(0xffffffffu, s.ay, o);
+      s.ay = kFl == kFlGradient ? fmaxf(s.ay, ay) : s.ay + ay;
       s.az += __shfl_xor_sync(0xffffffffu, s.az, o);
       s.du += __shfl_xor_sync(0xffffffffu, s.du, o);
       s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, o));
@@ -128,17 +216,28 @@ __device__ __forceinline__ void fetch_list(const sphh::ForceArgs& a, const Block
     if (8 * q < lc && lc <= kFListCap) w[q] = src[q];
 }
 
-__global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, PhysDev ph) {
+// The reach of a pair: r < max(H_i, H_j) for the force, r < H_i for the
+// gradient pass.
+template <int kFl>
+__device__ __forceinline__ float reach(float Hi, float Hj) {
+  return kFl == kFlGradient ? Hi : fmaxf(Hi, Hj);
+}
+
+template <int kFl>
+__global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, PhysDev ph, SphenixDev x) {
+  constexpr int kCap = force_cap<kFl>();
+  constexpr bool kE = kFl != kFlMinimal;
   extern __shared__ __align__(16) unsigned char fsm_raw[];
   float4* sA = reinterpret_cast<float4*>(fsm_raw);
-  float4* sB = sA + kForceBlkCap;
-  float4* sC = sB + kForceBlkCap;
-  float2* sD = reinterpret_cast<float2*>(sC + kForceBlkCap);
-  uint16_t* lj_all = reinterpret_cast<uint16_t*>(sD + kForceBlkCap);
+  float4* sB = sA + kCap;
+  float4* sC = sB + kCap;
+  float4* sE = sC + kCap;  // SPHENIX only
+  float2* sD = reinterpret_cast<float2*>(sC + (kE ? 2 : 1) * kCap);
+  uint16_t* lj_all = reinterpret_cast<uint16_t*>(sD + kCap);
   StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * kFListCap * 32);
   BlockTargets& BT = *reinterpret_cast<BlockTargets*>(&T + 1);
   uint16_t* tgt_slot = reinterpret_cast<uint16_t*>(&BT + 1);
-  uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + kForceBlkCap);
+  uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + kCap);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint16_t* lj = lj_all + warp * (kFListCap * 32);
   const int32_t total = a.misc_ro[kTotalBlocks];
@@ -147,11 +246,12 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
   for (int32_t b = blockIdx.x; b < total; b += gridDim.x) {
     const BlockGeom g = block_geom(a.grid, a.n_sims, b);
     const int32_t nsrc = build_stage_table(g, a.cell_start, T);
-    if (nsrc > kForceBlkCap) {
+    if (nsrc > kCap) {
       if (threadIdx.x == 0) a.overflow[atomicAdd(&a.misc[kNumOverflow], 1)] = b;
       __syncthreads();
       continue;
     }
+    const float dt = kFl == kFlGradient ? block_dt(a, x, b) : 0.0f;
     // the targets' rounds first (they need only the table), so that each
     // warp's first list is in flight together with the staging loads
     build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
@@ -173,6 +273,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
       sB[v] = a.fB[j];
       sC[v] = a.fC[j];
       sD[v] = a.fD[j];
+      if (kE) sE[v] = a.fE[j];
     }
     __syncthreads();
 
@@ -193,12 +294,14 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
       Tg.B = sB[self_slot];
       Tg.C = sC[self_slot];
       Tg.D = sD[self_slot];
+      Tg.E = kE ? sE[self_slot] : make_float4(0.f, 0.f, 0.f, 0.f);
       finish_target(Tg);
       ForceSums s0, s1;
       fsums_zero(s0);
       fsums_zero(s1);
+      if (kFl == kFlGradient) s0.ay = s1.ay = Tg.E.y;  // alpha_V,max starts at the target's
       // the density loop's list of this lane (same build, same rounds): all
-      // sources within the cell size, a superset of r < max(H_i, H_j)
+      // sources within the cell size, a superset of the pairs in reach
       int cnt = -1;
       if (a.lists != nullptr && valid) {
         const int lc = pre_lc;
@@ -230,7 +333,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
             const float4 Aj = sA[k];
             const float dx = Tg.A.x - Aj.x, dy = Tg.A.y - Aj.y, dz = Tg.A.z - Aj.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float Hm = fmaxf(Tg.A.w, Aj.w);
+            const float Hm = reach<kFl>(Tg.A.w, Aj.w);
             if (r2 < Hm * Hm && k != self_slot) {
               if (cnt < kFListCap) lj[cnt * 32 + lane] = (uint16_t)k;
               ++cnt;
@@ -239,8 +342,8 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
         }
       }
       if (valid && cnt <= kFListCap) {
-        // pairs beyond both supports add exactly zero; the self pair and
-        // pairs beyond max(H_i, H_j) do not enter v_sig or the pair count
+        // pairs beyond reach add exactly zero; the self pair and pairs beyond
+        // reach do not enter the maxima or the pair count
         int e = 0;
         for (; e + 1 < cnt; e += 2) {
           const int ka = lj[e * 32 + lane], kb = lj[(e + 1) * 32 + lane];
@@ -249,17 +352,19 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
           const float dxb = Tg.A.x - Ab.x, dyb = Tg.A.y - Ab.y, dzb = Tg.A.z - Ab.z;
           const float r2a = fmaf(dxa, dxa, fmaf(dya, dya, dza * dza));
           const float r2b = fmaf(dxb, dxb, fmaf(dyb, dyb, dzb * dzb));
-          const float Hma = fmaxf(Tg.A.w, Aa.w), Hmb = fmaxf(Tg.A.w, Ab.w);
-          force_pair(Tg, Aa, sB[ka], sC[ka], sD[ka], ph, r2a < Hma * Hma && ka != self_slot, s0);
-          force_pair(Tg, Ab, sB[kb], sC[kb], sD[kb], ph, r2b < Hmb * Hmb && kb != self_slot, s1);
+          const float Hma = reach<kFl>(Tg.A.w, Aa.w), Hmb = reach<kFl>(Tg.A.w, Ab.w);
+          const float4 Ea = kE ? sE[ka] : Tg.E, Eb = kE ? sE[kb] : Tg.E;
+          force_pair<kFl>(Tg, Aa, sB[ka], sC[ka], sD[ka], Ea, ph, r2a < Hma * Hma && ka != self_slot, s0);
+          force_pair<kFl>(Tg, Ab, sB[kb], sC[kb], sD[kb], Eb, ph, r2b < Hmb * Hmb && kb != self_slot, s1);
         }
         if (e < cnt) {
           const int ka = lj[e * 32 + lane];
           const float4 Aa = sA[ka];
           const float dxa = Tg.A.x - Aa.x, dya = Tg.A.y - Aa.y, dza = Tg.A.z - Aa.z;
           const float r2a = fmaf(dxa, dxa, fmaf(dya, dya, dza * dza));
-          const float Hma = fmaxf(Tg.A.w, Aa.w);
-          force_pair(Tg, Aa, sB[ka], sC[ka], sD[ka], ph, r2a < Hma * Hma && ka != self_slot, s0);
+          const float Hma = reach<kFl>(Tg.A.w, Aa.w);
+          const float4 Ea = kE ? sE[ka] : Tg.E;
+          force_pair<kFl>(Tg, Aa, sB[ka], sC[ka], sD[ka], Ea, ph, r2a < Hma * Hma && ka != self_slot, s0);
         }
       } else if (valid) {
         // list overflow: walk the runs directly
@@ -270,27 +375,26 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
             const float4 Aj = sA[k];
             const float dx = Tg.A.x - Aj.x, dy = Tg.A.y - Aj.y, dz = Tg.A.z - Aj.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float Hm = fmaxf(Tg.A.w, Aj.w);
-            if (r2 < Hm * Hm && k != self_slot) force_pair(Tg, Aj, sB[k], sC[k], sD[k], ph, true, s0);
+            const float Hm = reach<kFl>(Tg.A.w, Aj.w);
+            if (r2 < Hm * Hm && k != self_slot)
+              force_pair<kFl>(Tg, Aj, sB[k], sC[k], sD[k], kE ? sE[k] : Tg.E, ph, true, s0);
           }
         }
       }
-      s0.ax += s1.ax;
-      s0.ay += s1.ay;
-      s0.az += s1.az;
-      s0.du += s1.du;
-      s0.vsig = fmaxf(s0.vsig, s1.vsig);
-      s0.npair += s1.npair;
-      fcombine(s0, tpp);
+      fsums_add<kFl>(s0, s1);
+      fcombine<kFl>(s0, tpp);
       if (valid && sub == 0) {
-        force_write(a, ti, s0);
+        if (kFl == kFlGradient)
+          gradient_write(a, x, dt, ti, Tg, s0);
+        else
+          force_write(a, ti, s0);
         pair_acc += (unsigned long long)s0.npair;
       }
       __syncwarp();
     }
     __syncthreads();
   }
-  if (ph.count_pairs) {
+  if (ph.count_pairs && a.pairs != nullptr) {
     unsigned long long v = pair_acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -301,21 +405,26 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
 // Blocks whose neighbourhood exceeded the staging buffer: one warp per target
 // cell, lane = target, the 27 cells streamed through a per-warp buffer with
 // positions relative to the target cell.
-__global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, PhysDev ph) {
+template <int kFl>
+__global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, PhysDev ph, SphenixDev x) {
+  constexpr bool kE = kFl != kFlMinimal;
   extern __shared__ __align__(16) unsigned char fo_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* base = fo_raw + warp * (kFOvfSmem / kWarpsPerBlock);
+  unsigned char* base = fo_raw + warp * (fovf_smem<kFl>() / kWarpsPerBlock);
   float4* sA = reinterpret_cast<float4*>(base);
   float4* sB = sA + kFOvfCap;
   float4* sC = sB + kFOvfCap;
-  float2* sD = reinterpret_cast<float2*>(sC + kFOvfCap);
+  float4* sE = sC + kFOvfCap;  // SPHENIX only
+  float2* sD = reinterpret_cast<float2*>(sC + (kE ? 2 : 1) * kFOvfCap);
   const int32_t n_items = a.misc_ro[kNumOverflow] * kBlkWarps;
   unsigned long long pair_acc = 0;
   for (int32_t item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
        item += gridDim.x * kWarpsPerBlock) {
-    const BlockGeom g = block_geom(a.grid, a.n_sims, a.overflow[item / kBlkWarps]);
+    const int32_t b = a.overflow[item / kBlkWarps];
+    const BlockGeom g = block_geom(a.grid, a.n_sims, b);
     int tx, ty, tz;
     if (!warp_cell(g, item % kBlkWarps, tx, ty, tz)) continue;
+    const float dt = kFl == kFlGradient ? block_dt(a, x, b) : 0.0f;
     const int32_t nc = g.G.n_c;
     const int32_t cx = g.c0x + tx, cy = g.c0y + ty, cz = g.c0z + tz;
     const int32_t c = g.G.cell_base + cx + nc * (cy + nc * cz);
@@ -338,6 +447,7 @@ __global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, 
       sB[slot] = a.fB[j];
       sC[slot] = a.fC[j];
       sD[slot] = a.fD[j];
+      if (kE) sE[slot] = a.fE[j];
     };
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
@@ -348,28 +458,33 @@ __global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, 
       Tg.B = a.fB[tl];
       Tg.C = a.fC[tl];
       Tg.D = a.fD[tl];
+      Tg.E = kE ? a.fE[tl] : make_float4(0.f, 0.f, 0.f, 0.f);
       finish_target(Tg);
       ForceSums s;
       fsums_zero(s);
+      if (kFl == kFlGradient) s.ay = Tg.E.y;
       for (int v0 = 0; v0 < nsrc; v0 += kFOvfCap) {
         const int cnt = stage_sources(v0, kFOvfCap, nb, lane, put);
         for (int k = 0; k < cnt; ++k) {
           const float4 Aj = sA[k];
           const float dx = Tg.A.x - Aj.x, dy = Tg.A.y - Aj.y, dz = Tg.A.z - Aj.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float Hm = fmaxf(Tg.A.w, Aj.w);
+          const float Hm = reach<kFl>(Tg.A.w, Aj.w);
           const bool self = (v0 + k == self_base + (ti - ts));
-          if (r2 < Hm * Hm && !self) force_pair(Tg, Aj, sB[k], sC[k], sD[k], ph, true, s);
+          if (r2 < Hm * Hm && !self) force_pair<kFl>(Tg, Aj, sB[k], sC[k], sD[k], kE ? sE[k] : Tg.E, ph, true, s);
         }
         __syncwarp();
       }
       if (valid) {
-        force_write(a, ti, s);
+        if (kFl == kFlGradient)
+          gradient_write(a, x, dt, ti, Tg, s);
+        else
+          force_write(a, ti, s);
         pair_acc += (unsigned long long)s.npair;
       }
     }
   }
-  if (ph.count_pairs) {
+  if (ph.count_pairs && a.pairs != nullptr) {
     unsigned long long v = pair_acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -382,27 +497,41 @@ __global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, 
 namespace sphh {
 using namespace sphk;
 
-cudaError_t launch_force(const ForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+template <int kFl>
+static cudaError_t launch_force_fl(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
   static int bps = 0, bps_o = 0;
+  constexpr size_t kSmem = force_blk_smem<kFl>(), kSmemO = fovf_smem<kFl>();
   if (!bps) {
-    cudaError_t e = cudaFuncSetAttribute(k_force, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kForceBlkSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_force<kFl>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_force, kBlkThreads, kForceBlkSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_force<kFl>, kBlkThreads, kSmem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_force_overflow, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kFOvfSmem);
+    e = cudaFuncSetAttribute(k_force_overflow<kFl>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemO);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_o, k_force_overflow, kThreads, kFOvfSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_o, k_force_overflow<kFl>, kThreads, kSmemO);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     if (bps_o < 1) bps_o = 1;
   }
   cudaError_t e = cudaMemsetAsync(a.misc + kNumOverflow, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_force<<<a.num_sms * bps, kBlkThreads, kForceBlkSmem, st>>>(a, ph);
-  k_force_overflow<<<a.num_sms * bps_o, kThreads, kFOvfSmem, st>>>(a, ph);
+  k_force<kFl><<<a.num_sms * bps, kBlkThreads, kSmem, st>>>(a, ph, x);
+  k_force_overflow<kFl><<<a.num_sms * bps_o, kThreads, kSmemO, st>>>(a, ph, x);
   return cudaGetLastError();
+}
+
+cudaError_t launch_force(const ForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+  return launch_force_fl<kFlMinimal>(a, ph, SphenixDev{}, st);
+}
+
+cudaError_t launch_sphenix_force(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
+  if (a.fE == nullptr) return cudaErrorInvalidValue;
+  return launch_force_fl<kFlSphenix>(a, ph, x, st);
+}
+
+cudaError_t launch_sphenix_gradient(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
+  if (a.fE == nullptr || a.alpha_c_out == nullptr) return cudaErrorInvalidValue;
+  return launch_force_fl<kFlGradient>(a, ph, x, st);
 }
 
 }  // namespace sphh

@@ -54,6 +54,18 @@ struct PhysDev {
   int32_t count_pairs;
 };
 
+// Constants of the SPHENIX flavour (Sec. 3.3) and the step dt over which its
+// parameters evolve: dt_dev[s] per simulation when given, else dt.
+struct SphenixDev {
+  float av_max = 2.0f;  // alpha_V,max
+  float ell = 0.05f;    // viscosity decay length
+  float beta_c = 1.0f;
+  float ac_min = 0.0f;  // alpha_c,min
+  float ac_max = 1.0f;  // alpha_c,max
+  double dt = 0.0;
+  const double* dt_dev = nullptr;
+};
+
 // One Newton-Raphson update of the smoothing length (Sec. 3.1): the root of
 // f(h) = n_hat(h) - (eta / h)^3, from the sums of a pass at h,
 //   S_w = sum_j w(q),   S_dw = sum_j (3 w + q w'(q)),   q = r / H,

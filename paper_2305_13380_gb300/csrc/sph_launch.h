@@ -143,8 +143,33 @@ struct ForceArgs {
   float *ax, *ay, *az, *du_dt, *v_sig;
   const uint16_t* lists;  // the density loop's lists, or nullptr
   const uint16_t* list_cnt;
+  // SPHENIX: sorted (u, alpha_V, P, alpha_c) per source; the gradient pass
+  // writes alpha_c (input order) and, if given, lap u
+  const float4* fE = nullptr;
+  float* alpha_c_out = nullptr;
+  float* lap_u = nullptr;
 };
 cudaError_t launch_force(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+cudaError_t launch_sphenix_force(const ForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,
+                                 cudaStream_t st);
+cudaError_t launch_sphenix_gradient(const ForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,
+                                    cudaStream_t st);
+
+// SPHENIX per-particle steps (sphenix.cu).  The viscosity update of every
+// particle (input order): alpha_v in/out, div_v_prev in (the divergence of the
+// previous evaluation) and out (set to div_v); sim_offset / n_sims map a
+// particle to its simulation's dt when x.dt_dev is given.
+struct SphenixAlphaArgs {
+  int64_t n_total;
+  int n_sims;
+  const int64_t* sim_offset;
+  const float *h, *c, *div_v, *v_sig;
+  float *div_v_prev, *alpha_v;
+};
+cudaError_t launch_sphenix_alpha_v(const SphenixAlphaArgs& a, const sphk::SphenixDev& x, cudaStream_t st);
+// Sorted copies E[s] = (u, alpha_V, P, alpha_c) of particle perm[s].
+cudaError_t launch_gather_sphenix(int64_t n_total, const int32_t* perm, const float* u, const float* alpha_v,
+                                  const float* P, const float* alpha_c, float4* fE, cudaStream_t st);
 
 // Nested-grid build (tree.cu), after launch_build produced the top cells
 // (counts and cell_start; no cell sort).

@@ -82,6 +82,14 @@ class sph_pool(C.Structure):
                 ("box_size", _P)] + [(k, _P) for k in POOL_FIELDS] + [("n_iter", _P)]
 
 
+class sph_sphenix_params(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("alpha_v_max", "ell", "beta_c", "alpha_c_min", "alpha_c_max")]
+
+
+class sph_sphenix_state(C.Structure):
+    _fields_ = [(k, _P) for k in ("alpha_v", "alpha_c", "div_v_prev", "v_sig", "lap_u")]
+
+
 class SPHError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {error_string(code)} ({code})")
@@ -114,6 +122,14 @@ def lib():
         L.sph_force.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
                                 C.POINTER(sph_density_out), C.POINTER(sph_force_out)]
         L.sph_step.argtypes = [_P, C.POINTER(sph_pool)]
+        L.sph_sphenix_default_params.restype = None
+        L.sph_sphenix_default_params.argtypes = [C.POINTER(sph_sphenix_params)]
+        L.sph_sphenix_gradient.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
+                                           C.POINTER(sph_density_out), C.POINTER(sph_sphenix_params),
+                                           C.c_double, C.POINTER(sph_sphenix_state)]
+        L.sph_force_sphenix.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
+                                        C.POINTER(sph_density_out), _P, _P, C.POINTER(sph_force_out)]
+        L.sph_step_sphenix.argtypes = [_P, C.POINTER(sph_pool), C.POINTER(sph_sphenix_params), _P, _P]
         L.sph_conservation.argtypes = [_P, C.POINTER(sph_pool), _P]
         L.sph_pair_counts.argtypes = [_P, C.POINTER(C.c_int64)]
         L.sph_kernel_times.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
@@ -335,6 +351,42 @@ def sph_reserve(ctx: Context, n_total: int, n_sims: int = 1):
 
 def sph_step(ctx: Context, pl: sph_pool):
     _check(lib().sph_step(ctx.handle, C.byref(pl)), "sph_step")
+
+
+def sph_sphenix_default_params(**overrides) -> sph_sphenix_params:
+    x = sph_sphenix_params()
+    lib().sph_sphenix_default_params(C.byref(x))
+    for k, v in overrides.items():
+        setattr(x, k, v)
+    return x
+
+
+def sphenix_state(alpha_v, alpha_c, div_v_prev, v_sig, lap_u=None) -> sph_sphenix_state:
+    """Marshals the SPHENIX per-particle arrays (float32 CUDA tensors)."""
+    f = torch.float32
+    s = sph_sphenix_state(_ptr(alpha_v, f), _ptr(alpha_c, f), _ptr(div_v_prev, f), _ptr(v_sig, f),
+                          _ptr(lap_u, f))
+    s._keep = (alpha_v, alpha_c, div_v_prev, v_sig, lap_u)
+    return s
+
+
+def sph_sphenix_gradient(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_density_out,
+                         x: sph_sphenix_params, dt: float, st: sph_sphenix_state):
+    _check(lib().sph_sphenix_gradient(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
+                                      C.byref(x), C.c_double(dt), C.byref(st)), "sph_sphenix_gradient")
+
+
+def sph_force_sphenix(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_density_out,
+                      alpha_v, alpha_c, out: sph_force_out):
+    f = torch.float32
+    _check(lib().sph_force_sphenix(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
+                                   _ptr(alpha_v, f), _ptr(alpha_c, f), C.byref(out)), "sph_force_sphenix")
+
+
+def sph_step_sphenix(ctx: Context, pl: sph_pool, x: sph_sphenix_params, alpha_v, alpha_c):
+    f = torch.float32
+    _check(lib().sph_step_sphenix(ctx.handle, C.byref(pl), C.byref(x), _ptr(alpha_v, f), _ptr(alpha_c, f)),
+           "sph_step_sphenix")
 
 
 def sph_conservation(ctx: Context, pl: sph_pool, out):

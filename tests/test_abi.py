@@ -51,3 +51,15 @@ def test_create_rejects_bad_params_without_gpu(libsph):
     assert sph.lib().sph_create(ctypes.byref(h), ctypes.byref(p), None) == sph.SPH_E_INVAL
     assert sph.lib().sph_create(None, ctypes.byref(p), None) == sph.SPH_E_INVAL
 
+
+
+def test_sphenix_defaults_and_argument_checks_without_gpu(libsph):
+    from paper_2305_13380_gb300 import sph
+    x = sph.sph_sphenix_default_params()
+    assert (x.alpha_v_max, x.ell, x.beta_c, x.alpha_c_min, x.alpha_c_max) == (2.0, 0.05, 1.0, 0.0, 1.0)
+    # NULL context and parameters are rejected before any device work
+    L = sph.lib()
+    assert L.sph_sphenix_gradient(None, None, None, None, ctypes.byref(x), 0.0, None) == sph.SPH_E_INVAL
+    assert L.sph_force_sphenix(None, None, None, None, None, None, None) == sph.SPH_E_INVAL
+    bad = sph.sph_sphenix_default_params(alpha_c_max=-1.0)
+    assert L.sph_step_sphenix(None, None, ctypes.byref(bad), None, None) == sph.SPH_E_INVAL
