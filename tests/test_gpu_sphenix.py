@@ -75,20 +75,26 @@ def _run_gpu(p, st, dt, tree=False):
     torch.cuda.synchronize()
     out = {k: v.cpu().numpy() for k, v in d.items()}
     out.update({k: v.cpu().numpy() for k, v in f.items()})
-    out.update({k: v.cpu().numpy() for k, v in dev.items()})
+    # the updated parameters (v_sig stays the force's output)
+    out.update({k: v.cpu().numpy() for k, v in dev.items() if k != "v_sig"})
     out["lap_u"] = lap.cpu().numpy()
+    out["_cell"] = float(p["L"]) / sph.sph_cells_sync(ctx, cells)
     return out
 
 
-def _check(orc, p, seed, cell=None):
+def _check(orc, p, seed, floor=False):
+    """floor: bounds include the rounding of the FP32 cell-relative
+    coordinates (needed where cells are many supports wide)."""
     q, od0, st, dt = _setup(orc, p, seed)
     g = _run_gpu(p, st, dt)
+    cell = g["_cell"] if floor else None
+    vmax = float(np.sqrt(q["vx"] ** 2 + q["vy"] ** 2 + q["vz"] ** 2).max()) if floor else None
     X = orc.Sphenix()
     f64 = {k: v.astype(np.float64) for k, v in st.items()}
     od, av, og, of = orc.sphenix_evaluate(q, q["h0"], f64["alpha_v"], f64["alpha_c"],
                                           f64["div_v_prev"], f64["v_sig"], dt, X)
     # density and force against the SPHENIX oracle, with the plain bounds
-    rep = compare(g, od, of, cell=cell)
+    rep = compare(g, od, of, cell=cell, vmax=vmax)
     # the divergence of this evaluation is handed on
     assert np.array_equal(g["div_v_prev"], g["div_v"])
     # viscosity parameter: FP32 rounding plus the effect of the divergence's
@@ -103,10 +109,18 @@ def _check(orc, p, seed, cell=None):
     err = np.abs(g["alpha_v"] - av)
     assert (err / lim).max() <= 1.0, f"alpha_v: max error {err.max():.3e}"
     # Laplacian: a sum with cancellation, 1e-4 of its rms plus the h error
-    # (the gradient terms scale as H^-5)
+    # (the gradient terms scale as H^-5), plus, with the coordinate floor d_i,
+    # d_i times the sum of the absolute terms, which is at most
+    # max|u_i - u_j| / H_i^2 int_0^1 4 pi q |w'(q)| dq = 12 max|u_i - u_j| / H_i^2
+    # for the cubic spline
     rms = np.sqrt(np.mean(og["lap_u"] ** 2))
     err = np.abs(g["lap_u"] - og["lap_u"])
     lim = 1e-4 * rms + 5e-5 * np.abs(og["lap_u"])
+    if floor:
+        from gpu_common import coord_floor
+        Hh = GAMMA_K * od["h"]
+        du = np.maximum(np.abs(q["u"] - q["u"].min()), np.abs(q["u"] - q["u"].max()))
+        lim = lim + 2.0 * coord_floor(cell, od["h"]) * 12.0 * du / Hh ** 2
     assert (err / lim).max() <= 1.0, f"lap_u: max error / rms {err.max() / rms:.3e}"
     # conduction parameter: dt times the Laplacian and v_c errors, plus the
     # limiter's dependence on the neighbours' alpha_V
@@ -129,12 +143,12 @@ def _check(orc, p, seed, cell=None):
 
 def test_sphenix_evaluation_lattice(orc):
     p = inputs.lattice(16, seed=7, sigma_v=0.05)
-    _check(orc, p, seed=1, cell=None)
+    _check(orc, p, seed=1)
 
 
 def test_sphenix_evaluation_clustered(orc):
     p = inputs.clustered(6000, n_spheres=8, seed=5)
-    _check(orc, p, seed=2, cell=None)
+    _check(orc, p, seed=2, floor=True)
 
 
 def test_sphenix_reduces_to_minimal_force():
