@@ -36,9 +36,12 @@ UNIT = "particle-updates/s"
 # divide and square root counts 1; see the design notes for the tally).
 F_DENSITY = 66
 F_FORCE = 72
+# Starting viscosity parameter of the SPHENIX workloads (alpha_c starts at 0).
+SPHENIX_ALPHA_V0 = 0.8
 
 
-def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False, axis: bool = False) -> int:
+def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False, axis: bool = False,
+                      sphenix: bool = False) -> int:
     """Kernel launches of one sph_step over n_total particles.
 
     Uniform grid: time-step reduction (3), kick/drift (1), cell build (8 + the
@@ -49,7 +52,9 @@ def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False, axis: b
     key, source keys, levels, target keys, flags, a 3-kernel scan, groups,
     count, neighbour ranges: 12), the tree gather (1), density with the
     reverse-pair grouping (6), force gather (1), force (1).  Sorted
-    interactions on the uniform grid add the per-cell axis orders (1)."""
+    interactions on the uniform grid add the per-cell axis orders (1).  The
+    SPHENIX flavour adds the viscosity update (1), two gathers of its records
+    (2) and the gradient pass (2)."""
     cap = 8 * n_total + 216 * n_sims
     cbits = 1
     while cbits < 30 and (1 << cbits) <= cap:
@@ -57,7 +62,7 @@ def launches_per_step(n_total: int, n_sims: int = 1, tree: bool = False, axis: b
     radix = lambda bits: 1 + 5 * ((bits + 7) // 8)  # noqa: E731
     integrate = 3 + 1 + 1
     if not tree:
-        return integrate + 8 + radix(cbits) + 2 + 2 + 2 + (1 if axis else 0)
+        return integrate + 8 + radix(cbits) + 2 + 2 + 2 + (1 if axis else 0) + (5 if sphenix else 0)
     return integrate + 8 + radix(30 + cbits) + radix(34 + cbits) + 12 + 1 + 6 + 1 + 1
 FP32_LANES_PER_SM = 128
 
@@ -77,6 +82,8 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sphenix", action="store_true",
+                    help="latticeN: the SPHENIX flavour (time-dependent viscosity, conduction)")
     ap.add_argument("--axis-sort", action="store_true",
                     help="uniform grid: sorted interactions in the density filter")
     ap.add_argument("--ref-budget", type=float, default=120.0,
@@ -164,10 +171,12 @@ def _f32(p):
     return q
 
 
-def oracle_sample(p, n_target: int, seed: int):
+def oracle_sample(p, n_target: int, seed: int, sphenix: bool = False):
     """Oracle density + force for the particles of a sub-cube holding about
     n_target particles (the density also runs on a margin of one support
-    around it, which the force needs).  Returns (particles updated, seconds)."""
+    around it, which the force needs).  With sphenix, the SPHENIX evaluation:
+    the viscosity update and the gradient pass on the margin too, then the
+    SPHENIX force.  Returns (particles updated, seconds)."""
     import numpy as np
 
     import oracle
@@ -197,19 +206,32 @@ def oracle_sample(p, n_target: int, seed: int):
              "c": np.sqrt(5.0 / 3.0 * P0 / rho0), "B": np.full(n, 0.5)}
     for k in state:
         state[k][halo] = d[k]
-    oracle.force(q, state, targets=core)
+    if not sphenix:
+        oracle.force(q, state, targets=core)
+        return len(core), time.perf_counter() - t0
+    X = oracle.Sphenix()
+    av = np.full(n, SPHENIX_ALPHA_V0)
+    div = np.zeros(n)
+    div[halo] = d["div_v"]
+    dt = 1e-4 * float(np.min(q["h0"]))
+    av = oracle.sphenix_alpha_v(dt, state["h"], state["c"], div, np.zeros(n), 2.0 * state["c"], av, X)
+    g = oracle.sphenix_gradient(q, state, av, np.zeros(n), dt, halo, X)
+    ac = np.zeros(n)
+    ac[halo] = g["alpha_c"]
+    oracle.sphenix_force(q, state, av, ac, targets=core)
     return len(core), time.perf_counter() - t0
 
 
-def cpu_baseline(p, budget_s: float) -> dict:
+def cpu_baseline(p, budget_s: float, sphenix: bool = False) -> dict:
     import oracle
     oracle.build()
     # calibrate on a small sample, then size the timed sample to the budget
-    n0, t0 = oracle_sample(p, 2000, seed=1)
+    n0, t0 = oracle_sample(p, 2000, seed=1, sphenix=sphenix)
     n_target = int(max(2000, min(len(p["x"]), n0 * budget_s / max(t0, 1e-3))))
-    nu, sec = oracle_sample(p, n_target, seed=2)
+    nu, sec = oracle_sample(p, n_target, seed=2, sphenix=sphenix)
+    what = "SPHENIX density, viscosity update, gradient pass and force" if sphenix else "density + force"
     return {"value": nu / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{nu} particles of a sub-cube (density also on a one-support halo, "
+            "sample": (f"{what}: {nu} particles of a sub-cube (density also on a one-support halo, "
                        f"grid build over all {len(p['x'])} particles included), "
                        f"{sec:.1f} s on 1 host core")}
 
@@ -354,7 +376,8 @@ def run_reference(args, world: int, rank: int):
     p = fof_workload(args.workload) if fof else make_workload(args.workload)
     metric, unit = (("friends-of-friends particles/s (clustered, 2M)", "particles/s") if fof
                     else (METRIC, UNIT))
-    sample = (lambda q, k, seed: oracle_fof_sample(q, k, seed)) if fof else oracle_sample
+    sample = ((lambda q, k, seed: oracle_fof_sample(q, k, seed)) if fof else
+              (lambda q, k, seed: oracle_sample(q, k, seed, sphenix=args.sphenix)))
     # size every sample so that the whole run stays near args.ref_budget seconds
     n0, t0 = sample(p, 1000, seed=99)
     per_step = args.ref_budget / max(1, args.steps + args.warmup)
@@ -618,9 +641,15 @@ def run_step(args, world: int, rank: int, local: int):
     # copies: the fields a step updates, then m, then the density outputs.
     # A caller that keeps its host copy in the same layout moves a step's
     # inputs and results with one copy each way.
+    sphenix = bool(args.sphenix)
+    if sphenix and p["tree"]:
+        raise SystemExit("the SPHENIX flavour runs on the uniform grid (latticeN workloads)")
     f64_keys = ("x", "y", "z")
-    f32_keys = ("vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du_dt", "v_sig", "m",
-                "rho", "f", "div_v", "curl_v", "P", "c", "balsara")
+    # SPHENIX carries alpha_V, alpha_c and the previous divergence from step
+    # to step: they join the fields a step reads and updates
+    carried = ("alpha_v", "alpha_c", "div_v") if sphenix else ()
+    f32_keys = ("vx", "vy", "vz", "u", "h", "ax", "ay", "az", "du_dt", "v_sig") + carried + ("m",) + \
+        tuple(k for k in ("rho", "f", "div_v", "curl_v", "P", "c", "balsara") if k not in carried)
     offs, size = {}, 0
     for k in f64_keys + f32_keys:
         offs[k] = size
@@ -654,13 +683,29 @@ def run_step(args, world: int, rank: int, local: int):
             if e.code != sph.SPH_E_REBUILD:
                 raise
             h_in = arrays["h"].clone()
-    sph.sph_force(init, cells, part, dout, sph.force_out({k: arrays[k] for k in sph.FORCE_FIELDS}))
+    fout = sph.force_out({k: arrays[k] for k in sph.FORCE_FIELDS})
+    X = sph.sph_sphenix_default_params()
+    if sphenix:
+        arrays["alpha_v"].fill_(SPHENIX_ALPHA_V0)
+        arrays["alpha_c"].zero_()
+        dvp = arrays["div_v"].clone()
+        sph.sph_sphenix_gradient(init, cells, part, dout, X, 0.0,
+                                 sph.sphenix_state(arrays["alpha_v"], arrays["alpha_c"], dvp, arrays["v_sig"]))
+        sph.sph_force_sphenix(init, cells, part, dout, arrays["alpha_v"], arrays["alpha_c"], fout)
+    else:
+        sph.sph_force(init, cells, part, dout, fout)
     init.close()
+
+    def step(c, pl):
+        if sphenix:
+            sph.sph_step_sphenix(c, pl, X, arrays["alpha_v"], arrays["alpha_c"])
+        else:
+            sph.sph_step(c, pl)
 
     ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | mode))
     pool = sph.pool(sim_offset, box, arrays)
     for _ in range(args.warmup):
-        sph.sph_step(ctx, pool)
+        step(ctx, pool)
     torch.cuda.synchronize()
     st = sph.sph_status(ctx)
     if st:
@@ -681,7 +726,7 @@ def run_step(args, world: int, rank: int, local: int):
     wall0 = time.perf_counter()
     e0.record(stream)
     for _ in range(args.steps):
-        sph.sph_step(ctx, pool)
+        step(ctx, pool)
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -695,15 +740,16 @@ def run_step(args, world: int, rank: int, local: int):
     # one more step (untimed) that counts pairs and Newton passes
     cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | mode))
     arrays["n_iter"] = torch.zeros(n, dtype=torch.int32, device=dev)
-    sph.sph_step(cnt, sph.pool(sim_offset, box, arrays))
+    step(cnt, sph.pool(sim_offset, box, arrays))
     pairs_d, pairs_f = sph.sph_pair_counts(cnt)
     tree_counts = sph.sph_tree_counts(cnt) if tree else None
     mean_pass = float(arrays.pop("n_iter").double().mean().item())
     cnt.close()
 
     # end to end: the state in pinned host memory, in the device layout; every
-    # step copies x .. v_sig and m in (one copy) and x .. v_sig out (one copy)
-    bi = offs["m"] + 4 * n          # x, y, z, v, u, h, a, du/dt, v_sig, m
+    # step copies x .. v_sig (and the SPHENIX fields) and m in (one copy) and
+    # the same without m out (one copy)
+    bi = offs["m"] + 4 * n          # x, y, z, v, u, h, a, du/dt, v_sig, [alpha_v, alpha_c, div_v,] m
     bo = offs["m"]                  # the same without m, which a step does not change
     host = torch.empty(bi, dtype=torch.uint8, pin_memory=True)
     host.copy_(dbuf[:bi])
@@ -713,7 +759,7 @@ def run_step(args, world: int, rank: int, local: int):
             torch.cuda.synchronize()
             e0.record(stream)
         dbuf[:bi].copy_(host, non_blocking=True)
-        sph.sph_step(e2e_ctx, pool)
+        step(e2e_ctx, pool)
         host[:bo].copy_(dbuf[:bo], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -745,21 +791,25 @@ def run_step(args, world: int, rank: int, local: int):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, args.cpu_budget)
+        cpu = cpu_baseline(p, args.cpu_budget, sphenix)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "desc": p["desc"], "particles_per_gpu": n,
-                   "step": "sph_step: dt, kick+drift, cell build, density (h solve), force, kick",
+                   "step": ("sph_step_sphenix: dt, kick+drift, cell build, density (h solve), viscosity "
+                            "update, gradient pass (lap u, alpha_c), SPHENIX force, kick" if sphenix else
+                            "sph_step: dt, kick+drift, cell build, density (h solve), force, kick"),
+                   "flavour": "SPHENIX" if sphenix else "Minimal",
                    "l2": "inputs larger than L2: each step touches ~0.5 GB of state and scratch",
                    "parallelism": f"replicas x{world}",
                    "grid": ("nested grids" if tree else
                             "uniform, sorted interactions" if mode & sph.SPH_FLAG_AXIS_SORT else "uniform")},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "steps": args.e2e_steps},
-        "gpu_launches": launches_per_step(n, 1, bool(tree), bool(mode & sph.SPH_FLAG_AXIS_SORT)) * args.steps,
+        "gpu_launches": launches_per_step(n, 1, bool(tree), bool(mode & sph.SPH_FLAG_AXIS_SORT),
+                                          sphenix) * args.steps,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "roofline": roofline,
