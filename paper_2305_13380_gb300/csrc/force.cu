@@ -30,7 +30,8 @@
 //    Euler step (eq. "artconddt") and its limiters (eqs. "condshocklimiter",
 //    "conductionlimiter").
 // The fifth record costs 16 bytes of shared memory per staged source, so the
-// SPHENIX kernels stage at most 1024 sources per block (two blocks per SM);
+// SPHENIX kernels stage at most 1200 sources per block, the most that keeps
+// two blocks per SM (a 2.29-lattice-points-per-cell grid stages up to ~1050);
 // larger neighbourhoods go to the overflow kernel.
 #include "blocks.cuh"
 #include "sph_internal.cuh"
@@ -43,7 +44,7 @@ enum : int { kFlMinimal = 0, kFlSphenix = 1, kFlGradient = 2 };
 
 template <int kFl>
 __host__ __device__ constexpr int force_cap() {
-  return kFl == kFlMinimal ? kBlkStageCap : 1024;
+  return kFl == kFlMinimal ? kBlkStageCap : 1200;
 }
 template <int kFl>
 __host__ __device__ constexpr size_t rec_bytes() {  // staged bytes per source
