@@ -91,6 +91,7 @@ def lib():
         L.oracle_dw_dq.restype = C.c_double
         L.oracle_dw_dq.argtypes = [C.c_double]
         L.oracle_gamma_k.restype = C.c_double
+        L.oracle_set_kernel.argtypes = [C.c_int]
         L.oracle_wrap.restype = C.c_double
         L.oracle_wrap.argtypes = [C.c_double, C.c_double]
         L.oracle_cell_coord.restype = C.c_int32
@@ -137,6 +138,7 @@ class Physics:
     eps_balsara: float = 1e-4
     h_tol: float = 1e-13
     max_iter: int = 200
+    kernel: int = 0  # 0 cubic spline, 1 quartic spline, 2 Wendland C2 (Sec. 3.1)
 
 
 @dataclass
@@ -179,7 +181,16 @@ def _particles(keep, p):
                                           ("x", "y", "z", "vx", "vy", "vz", "m", "u")])
 
 
+KERNELS = {"cubic": 0, "quartic": 1, "wendland_c2": 2}
+
+
+def set_kernel(kernel: int):
+    """Selects the kernel of the following oracle calls."""
+    _check(lib().oracle_set_kernel(int(kernel)), "set_kernel")
+
+
 def _config(phys: Physics, brute: bool):
+    set_kernel(phys.kernel)
     return _Config(phys.gamma, phys.eta, phys.alpha_v, phys.beta_v, phys.eps_balsara,
                    phys.h_tol, phys.max_iter, 1 if brute else 0)
 
@@ -189,12 +200,20 @@ def _check(rc, what):
         raise RuntimeError(f"oracle {what} failed with code {rc}")
 
 
-def w(q: float) -> float:
+def w(q: float, kernel: int = 0) -> float:
+    set_kernel(kernel)
     return lib().oracle_w(float(q))
 
 
-def dw_dq(q: float) -> float:
+def dw_dq(q: float, kernel: int = 0) -> float:
+    set_kernel(kernel)
     return lib().oracle_dw_dq(float(q))
+
+
+def gamma_k(kernel: int = 0) -> float:
+    """H/h of the kernel."""
+    set_kernel(kernel)
+    return lib().oracle_gamma_k()
 
 
 def cell_coord(x: float, L: float, n_c: int) -> int:
@@ -334,8 +353,10 @@ def step(s: dict, cfl: float, phys: Physics = Physics(), brute: bool = False) ->
     return dt.value
 
 
-def sphenix_alpha_v(dt: float, h, c, div_v, div_v_prev, v_sig, alpha, X: Sphenix = Sphenix()):
+def sphenix_alpha_v(dt: float, h, c, div_v, div_v_prev, v_sig, alpha, X: Sphenix = Sphenix(),
+                    phys: Physics = Physics()):
     """SPHENIX viscosity parameters after a step dt (eqs. "sphenix_visc1"-"sphenix_visc4")."""
+    set_kernel(phys.kernel)
     keep = _Keep()
     n = int(np.asarray(h).shape[0])
     out = np.zeros(n)
@@ -392,7 +413,7 @@ def sphenix_evaluate(p: dict, h0, alpha_v, alpha_c, div_v_prev, v_sig_prev, dt: 
     update, gradient pass with the conduction update, force.  Returns
     (density dict, alpha_v, gradient dict, force dict)."""
     d = density(p, h0, None, phys, brute)
-    av = sphenix_alpha_v(dt, d["h"], d["c"], d["div_v"], div_v_prev, v_sig_prev, alpha_v, X)
+    av = sphenix_alpha_v(dt, d["h"], d["c"], d["div_v"], div_v_prev, v_sig_prev, alpha_v, X, phys)
     g = sphenix_gradient(p, d, av, alpha_c, dt, None, X, phys, brute)
     f = sphenix_force(p, d, av, g["alpha_c"], None, phys, brute)
     return d, av, g, f
@@ -408,7 +429,7 @@ def sphenix_step(s: dict, cfl: float, X: Sphenix = Sphenix(), phys: Physics = Ph
               "alpha_v", "alpha_c", "div_v"):
         s[k] = _d(s[k]).copy()
     L = float(s["L"])
-    dt = float(np.min(cfl * GAMMA_K * s["h"] / s["v_sig"]))
+    dt = float(np.min(cfl * gamma_k(phys.kernel) * s["h"] / s["v_sig"]))
     if not (dt > 0.0) or not np.isfinite(dt):
         raise RuntimeError("oracle sphenix_step: no finite positive time-step")
     wrap = lib().oracle_wrap

@@ -40,17 +40,41 @@
 
 #define OR_PI 3.14159265358979323846
 
-/* gamma_K = H/h of the 3-D cubic spline in the Dehnen & Aly (2012) convention. */
-static const double OR_GAMMA_K = 1.825742;
-
 /* --------------------------------------------------------------------------
- * Kernel (Sec. 3.1, eq. "kernel").  q = r/H, H = gamma_K h.
+ * Kernels (Sec. 3.1, eq. "kernel"): W(r, h) = w(q)/H^3, q = r/H, H = gamma_K h,
+ * in the Dehnen & Aly (2012) convention, where h is twice the kernel's
+ * standard deviation per dimension, so gamma_K = sqrt(3 / (4 <q^2>)) with
+ * <q^2> = int 4 pi q^4 w(q) dq.  The paper names the cubic spline (the
+ * default), the quartic spline and the Wendland C2 kernel (Sec. 3.1):
+ *   0 cubic:       w = 16/pi [(1-q)^3 - 4 (1/2-q)_+^3],             gamma_K = 1.825742
+ *   1 quartic:     w = 15625/(512 pi) [(1-q)^4 - 5 (3/5-q)_+^4
+ *                                      + 10 (1/5-q)_+^4],            gamma_K = 2.018932
+ *   2 Wendland C2: w = 21/(2 pi) (1-q)^4 (1+4q),                      gamma_K = 1.936492
+ * (w = 0 for q >= 1).  The kernel of every call is set by oracle_set_kernel.
  * -------------------------------------------------------------------------- */
+static int or_kernel = 0;
+static double OR_GAMMA_K = 1.825742;
+
+int oracle_set_kernel(int k) {
+  static const double gam[3] = {1.825742, 2.018932, 1.936492};
+  if (k < 0 || k > 2) return -1;
+  or_kernel = k;
+  OR_GAMMA_K = gam[k];
+  return 0;
+}
+
 double oracle_gamma_k(void) { return OR_GAMMA_K; }
+
+static double or_pos(double x) { return x > 0.0 ? x : 0.0; }
 
 double oracle_w(double q) {
   if (q >= 1.0) return 0.0;
   double a = 1.0 - q;
+  if (or_kernel == 1) {
+    double b = or_pos(0.6 - q), c = or_pos(0.2 - q);
+    return (15625.0 / (512.0 * OR_PI)) * (a * a * a * a - 5.0 * b * b * b * b + 10.0 * c * c * c * c);
+  }
+  if (or_kernel == 2) return (21.0 / (2.0 * OR_PI)) * a * a * a * a * (1.0 + 4.0 * q);
   double w = a * a * a;
   if (q < 0.5) {
     double b = 0.5 - q;
@@ -62,6 +86,11 @@ double oracle_w(double q) {
 double oracle_dw_dq(double q) {
   if (q >= 1.0) return 0.0;
   double a = 1.0 - q;
+  if (or_kernel == 1) {
+    double b = or_pos(0.6 - q), c = or_pos(0.2 - q);
+    return (15625.0 / (512.0 * OR_PI)) * (-4.0) * (a * a * a - 5.0 * b * b * b + 10.0 * c * c * c);
+  }
+  if (or_kernel == 2) return (21.0 / (2.0 * OR_PI)) * (-20.0) * q * a * a * a;
   double d = -3.0 * a * a;
   if (q < 0.5) {
     double b = 0.5 - q;
