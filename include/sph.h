@@ -25,8 +25,10 @@
  *    aborts or traps.  Device-side conditions (smoothing length not converged,
  *    a support larger than the cell, ...) are OR-ed into a status word that
  *    sph_status() returns and clears.
- *  - Kernel: cubic spline in the Dehnen & Aly (2012) form W(r,h) = w(r/H)/H^3,
- *    H = gamma_K h, gamma_K = 1.825742 (Sec. 3.1, eq. "kernel").
+ *  - Kernel: the cubic spline by default, in the Dehnen & Aly (2012) form
+ *    W(r,h) = w(r/H)/H^3, H = gamma_K h, gamma_K = 1.825742 (Sec. 3.1, eq.
+ *    "kernel"); sph_params.kernel selects the quartic spline or the Wendland
+ *    C2 kernel instead (SPH_KERNEL_*).
  *  - One context per stream; a context is not thread-safe.
  */
 #ifndef SPH_H
@@ -79,6 +81,17 @@ enum {
                                another order.  Ignored with SPH_FLAG_TREE.  */
 };
 
+/* Smoothing kernels (Sec. 3.1), W(r, h) = w(r/H)/H^3, H = gamma_K h, in the
+ * Dehnen & Aly (2012) convention (h is twice the kernel's standard deviation
+ * per dimension):
+ *   SPH_KERNEL_CUBIC        16/pi [(1-q)^3 - 4 (1/2-q)_+^3],         gamma_K = 1.825742
+ *   SPH_KERNEL_QUARTIC      15625/(512 pi) [(1-q)^4 - 5 (3/5-q)_+^4 + 10 (1/5-q)_+^4],
+ *                                                                     gamma_K = 2.018932
+ *   SPH_KERNEL_WENDLAND_C2  21/(2 pi) (1-q)^4 (1 + 4q),               gamma_K = 1.936492
+ * The kernel sets gamma_K everywhere it enters: cell sizes, the smoothing-
+ * length equation, the loops and the time-step. */
+enum { SPH_KERNEL_CUBIC = 0, SPH_KERNEL_QUARTIC = 1, SPH_KERNEL_WENDLAND_C2 = 2 };
+
 /* Kernel groups timed with SPH_FLAG_TIMING (index into sph_kernel_times). */
 enum {
   SPH_T_BUILD = 0,      /* cell grid, keys, counting sort, in-cell order   */
@@ -109,7 +122,7 @@ typedef struct sph_params {
   int32_t flags;       /* SPH_FLAG_*                                              */
   int32_t n_leaf;      /* SPH_FLAG_TREE: a cell with at most n_leaf particles is
                           not split (>= 1)                                        */
-  int32_t reserved;    /* 0                                                       */
+  int32_t kernel;      /* SPH_KERNEL_* (the nested grids take the cubic spline)   */
 } sph_params;
 
 /* Opaque context: holds the stream, the parameters and the device scratch

@@ -299,6 +299,7 @@ PhysDev phys_of(const sph_params& p) {
   ph.h_tol = p.h_tol;
   ph.max_h_iter = p.max_h_iter;
   ph.count_pairs = (p.flags & SPH_FLAG_COUNT_PAIRS) ? 1 : 0;
+  ph.kernel = p.kernel;
   return ph;
 }
 
@@ -336,13 +337,15 @@ int finish(sph_ctx* c) {
 bool params_ok(const sph_params& p) {
   return p.box_size > 0 && p.gamma > 1 && p.eta > 0 && p.alpha_v >= 0 && p.beta_v >= 0 &&
          p.eps_balsara > 0 && p.h_tol > 0 && p.cfl > 0 && p.cell_margin >= 0 && p.max_h_iter > 0 &&
-         (!(p.flags & SPH_FLAG_TREE) || p.n_leaf >= 1);
+         (!(p.flags & SPH_FLAG_TREE) || p.n_leaf >= 1) && p.kernel >= SPH_KERNEL_CUBIC &&
+         p.kernel <= SPH_KERNEL_WENDLAND_C2 && (!(p.flags & SPH_FLAG_TREE) || p.kernel == SPH_KERNEL_CUBIC);
 }
 
 int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const double* box,
              const double* x, const double* y, const double* z, const float* h, double radius = 0.0,
              int cells_per_particle = 8) {
   sphh::BuildArgs b;
+  b.gamma_k = sphk::kernel_gamma(c->p.kernel);
   b.radius = radius;
   b.cells_per_particle = cells_per_particle;
   b.n_sims = n_sims;
@@ -619,6 +622,7 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
              const float* f, const float* P, const float* cs, const float* B, float* ax, float* ay,
              float* az, float* du_dt, float* v_sig, bool pos_ready = false, const SphenixCall* sx = nullptr) {
   sphh::GatherForceArgs g;
+  g.gamma_k = (float)sphk::kernel_gamma(c->p.kernel);
   // the nested-grid force reads positions from its own copies (fA.w only)
   g.positions = (pos_ready || c->built_tree) ? 0 : 1;
   g.n_total = c->built_n;
@@ -756,7 +760,7 @@ void sph_default_params(sph_params* p) {
   p->max_h_iter = 30;
   p->flags = 0;
   p->n_leaf = 16;
-  p->reserved = 0;
+  p->kernel = SPH_KERNEL_CUBIC;
 }
 
 int sph_create(sph_ctx** out, const sph_params* p, void* stream) {
@@ -940,6 +944,7 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
     if (rc != SPH_OK) return rc;
   }
   sphh::StepArgs s;
+  s.gamma_k = sphk::kernel_gamma(c->p.kernel);
   s.n_sims = pl->n_sims;
   s.n_total = pl->n_total;
   s.num_sms = c->num_sms;
@@ -1010,7 +1015,7 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
   if (X) {
     const sphk::SphenixDev xd = sphenix_dev(*X, 0.0, pl->dt);
     sphh::SphenixAlphaArgs aa{pl->n_total, pl->n_sims, pl->sim_offset, pl->h, pl->c, pl->div_v, pl->v_sig,
-                              c->dvp, alpha_v};
+                              c->dvp, alpha_v, (float)sphk::kernel_gamma(c->p.kernel)};
     t_begin(c, SPH_T_INTEGRATE);
     if (sphh::launch_sphenix_alpha_v(aa, xd, c->st) != cudaSuccess) return SPH_E_CUDA;
     t_end(c, SPH_T_INTEGRATE);
@@ -1064,7 +1069,9 @@ int sph_sphenix_gradient(sph_ctx* c, const sph_cells* cells, const sph_particles
   int rc = ensure_sphenix(c, in->n);
   if (rc != SPH_OK) return rc;
   const sphk::SphenixDev xd = sphenix_dev(*X, dt, nullptr);
-  sphh::SphenixAlphaArgs aa{in->n, 1, nullptr, d->h, d->c, d->div_v, st->v_sig, st->div_v_prev, st->alpha_v};
+  sphh::SphenixAlphaArgs aa{in->n,      1,          nullptr,         d->h,
+                            d->c,       d->div_v,   st->v_sig,       st->div_v_prev,
+                            st->alpha_v, (float)sphk::kernel_gamma(c->p.kernel)};
   if (sphh::launch_sphenix_alpha_v(aa, xd, c->st) != cudaSuccess) return SPH_E_CUDA;
   SphenixCall g;
   g.gradient = true;

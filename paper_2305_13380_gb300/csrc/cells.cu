@@ -65,13 +65,13 @@ __global__ void k_grid_hmax(const int64_t* __restrict__ sim_offset, int n_sims, 
 // from the smoothing lengths.
 __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const double* __restrict__ box,
                              const int32_t* __restrict__ hmax_bits, int n_sims, double margin,
-                             double radius, int cells_per_particle, GridDev* __restrict__ grid,
-                             int32_t* __restrict__ misc) {
+                             double radius, int cells_per_particle, double gamma_k,
+                             GridDev* __restrict__ grid, int32_t* __restrict__ misc) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x) {
     const int64_t a = sim_offset[s], b = sim_offset[s + 1];
     const float m = __int_as_float(hmax_bits[s]);
     const double L = box[s];
-    const double Hmax = radius > 0.0 ? radius : kGammaKd * (double)m * (1.0 + margin);
+    const double Hmax = radius > 0.0 ? radius : gamma_k * (double)m * (1.0 + margin);
     const int32_t cap = cap_cells_per_side(b - a, cells_per_particle);
     int32_t nc = cap;
     if (Hmax > 0.0) {
@@ -279,11 +279,11 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
                                const float* __restrict__ B, float4* __restrict__ fA,
                                float4* __restrict__ fB, float4* __restrict__ fC,
                                float2* __restrict__ fD, const float4* __restrict__ trel,
-                               const int4* __restrict__ tfine, float4* __restrict__ rec) {
+                               const int4* __restrict__ tfine, float4* __restrict__ rec, float gamma_k) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_total;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p = perm[s];
-    const float H = kGammaK * h[p];
+    const float H = gamma_k * h[p];
     if (rec != nullptr) {
       // nested grids: one record per source (the arrays below are not read)
       const float4 rl = trel[s];
@@ -336,8 +336,8 @@ cudaError_t launch_build(const BuildArgs& a, cudaStream_t st) {
     k_grid_hmax<<<(int)hb, 256, 0, st>>>(a.sim_offset, a.n_sims, a.n_total, a.h, a.hmax_bits);
   }
   k_grid_setup<<<(a.n_sims + 127) / 128, 128, 0, st>>>(a.sim_offset, a.box, a.hmax_bits, a.n_sims,
-                                                       a.margin, a.radius, a.cells_per_particle, a.grid,
-                                                       a.misc);
+                                                       a.margin, a.radius, a.cells_per_particle, a.gamma_k,
+                                                       a.grid, a.misc);
   k_grid_base<<<1, 32, 0, st>>>(a.grid, a.n_sims, a.misc);
   // grids sized for the capacity but capped: the kernels loop up to the
   // device-side cell count, and idle blocks would only cost launch time
@@ -373,7 +373,7 @@ cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st) {
   auto kern = a.positions ? k_gather_force<true> : k_gather_force<false>;
   kern<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
       a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.h, a.rho,
-      a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD, a.rel, a.fine, a.rec);
+      a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD, a.rel, a.fine, a.rec, a.gamma_k);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ __device__ __forceinline__ void sums_add(DensSums& s, const DensSums& t) {
 }
 
 // Full density sums of one pair (target at pi/vi, source pj/vj) at H.
+template <int K>
 __device__ __forceinline__ void dens_pair(const float4& pi, const float4& vi, const float4& pj,
                                           const float4& vj, float H, float Hinv, DensSums& s) {
   const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
@@ -86,7 +87,7 @@ __device__ __forceinline__ void dens_pair(const float4& pi, const float4& vi, co
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float q = r2 * rinv * Hinv;
   float w, g;
-  kernel_w_g(q, H * rinv, w, g);
+  kernel_w_g<K>(q, H * rinv, w, g);
   const float dw = fmaf(q * q, g, 3.0f * w);
   s.w += w;
   s.dw += dw;
@@ -107,10 +108,11 @@ __device__ __forceinline__ float start_h(float h0, float hcap) {
 }
 
 // Writes the outputs of one target (sorted index ti) from its sums at h.
+template <int K>
 __device__ __forceinline__ void dens_write(const sphh::DensityArgs& a, const PhysDev& ph, int32_t ti,
                                            float h, const DensSums& s, float u_i, int passes,
                                            bool conv, bool atcap) {
-  const float H = kGammaK * h;
+  const float H = KernT<K>::gamma * h;
   const float Hinv = 1.0f / H;
   const float H2inv = Hinv * Hinv;
   const int32_t p = a.perm[ti];
@@ -164,6 +166,7 @@ __device__ __forceinline__ void combine(DensSums& s, int tpp) {
   }
 }
 
+template <int K>
 __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::DensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   float4* spos = reinterpret_cast<float4*>(dsm_raw);
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
   float* lr2 = lr2_all + warp * (kListRows * 32);
   uint16_t* lj = lj_all + warp * (kListRows * 32);
   const int32_t total = a.misc_ro[kTotalBlocks];
-  const NewtonConst nwt = newton_const(ph);
+  const NewtonConst nwt = newton_const<K>(ph);
   unsigned long long pair_acc = 0;
 
   for (int32_t b = blockIdx.x; b < total; b += gridDim.x) {
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
     }
     build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
 
-    const float hcap = h_cap((double)g.G.cell_f, g.G.L);
+    const float hcap = h_cap<K>((double)g.G.cell_f, g.G.L);
     const float R2 = g.G.cell_f * g.G.cell_f;
     const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
     const int sub = lane & (tpp - 1);
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       bool done = !valid, atcap = false, conv = false;
       int it = 0, passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
-        const float H = kGammaK * h;
+        const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
         float Sw0 = 0.f, Sdw0 = 0.f, Sw1 = 0.f, Sdw1 = 0.f;
         if (!done && !direct) {
@@ -336,8 +339,8 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
             const float ria = rsqrtf(fmaxf(r2a, 1e-30f)), rib = rsqrtf(fmaxf(r2b, 1e-30f));
             const float qa = r2a * ria * Hinv, qb = r2b * rib * Hinv;
             float wa, dwa, wb, dwb;
-            kernel_w_dw(qa, wa, dwa);
-            kernel_w_dw(qb, wb, dwb);
+            kernel_w_dw<K>(qa, wa, dwa);
+            kernel_w_dw<K>(qb, wb, dwb);
             Sw0 += wa;
             Sw1 += wb;
             Sdw0 += dwa;
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
             const float ria = rsqrtf(fmaxf(r2a, 1e-30f));
             const float qa = r2a * ria * Hinv;
             float wa, dwa;
-            kernel_w_dw(qa, wa, dwa);
+            kernel_w_dw<K>(qa, wa, dwa);
             Sw0 += wa;
             Sdw0 += dwa;
           }
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
               const float ri = rsqrtf(fmaxf(r2, 1e-30f));
               const float q = r2 * ri * Hinv;
               float w, dw;
-              kernel_w_dw(q, w, dw);
+              kernel_w_dw<K>(q, w, dw);
               Sw0 += w;
               Sdw0 += dw;
             }
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
         }
       }
       // 3. final pass at the converged h
-      const float H = kGammaK * h;
+      const float H = KernT<K>::gamma * h;
       const float Hinv = 1.0f / H;
       DensSums s0, s1;
       sums_zero(s0);
@@ -391,12 +394,12 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
         int e = 0;
         for (; e + 1 < cnt; e += 2) {
           const int ka = (int)lj[e * 32 + lane], kb = (int)lj[(e + 1) * 32 + lane];
-          dens_pair(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
-          dens_pair(pi, vi, spos[kb], svel[kb], H, Hinv, s1);
+          dens_pair<K>(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
+          dens_pair<K>(pi, vi, spos[kb], svel[kb], H, Hinv, s1);
         }
         if (e < cnt) {
           const int ka = (int)lj[e * 32 + lane];
-          dens_pair(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
+          dens_pair<K>(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
         }
       } else if (valid) {
         for (int r = 0; r < 9; ++r) {
@@ -405,14 +408,14 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
           for (int32_t k = A0 + sub; k < B0; k += tpp) {
             const float4 pj = spos[k];
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2) dens_pair(pi, vi, pj, svel[k], H, Hinv, s0);
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2) dens_pair<K>(pi, vi, pj, svel[k], H, Hinv, s0);
           }
         }
       }
       sums_add(s0, s1);
       combine(s0, tpp);
       if (valid && sub == 0) {
-        dens_write(a, ph, ti, h, s0, vi.w, passes, conv, atcap);
+        dens_write<K>(a, ph, ti, h, s0, vi.w, passes, conv, atcap);
         pair_acc += (unsigned long long)s0.npair;
       }
       __syncwarp();
@@ -430,13 +433,14 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
 // Blocks whose neighbourhood exceeded the staging buffer: one warp per target
 // cell; each lane owns a target and walks the 27 cells, streamed through a
 // per-warp shared buffer, with positions relative to the target cell.
+template <int K>
 __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs a, PhysDev ph) {
   extern __shared__ float4 osm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float4* spos = osm + warp * (2 * kOvfCap);
   float4* svel = spos + kOvfCap;
   const int32_t n_items = a.misc_ro[kNumOverflow] * kBlkWarps;
-  const NewtonConst nwt = newton_const(ph);
+  const NewtonConst nwt = newton_const<K>(ph);
   unsigned long long pair_acc = 0;
   for (int32_t item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
        item += gridDim.x * kWarpsPerBlock) {
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
       spos[slot] = p;
       svel[slot] = a.vel4[j];
     };
-    const float hcap = h_cap((double)g.G.cell_f, g.G.L);
+    const float hcap = h_cap<K>((double)g.G.cell_f, g.G.L);
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
       const bool valid = ti < te;
@@ -469,13 +473,13 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
       int it = 0;
       int passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
-        const float H = kGammaK * h;
+        const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
         DensSums s;
         sums_zero(s);
         for (int v0 = 0; v0 < nsrc; v0 += kOvfCap) {
           const int cnt = stage_sources(v0, kOvfCap, nb, lane, put);
-          for (int k = 0; k < cnt; ++k) dens_pair(pi, vi, spos[k], svel[k], H, Hinv, s);
+          for (int k = 0; k < cnt; ++k) dens_pair<K>(pi, vi, spos[k], svel[k], H, Hinv, s);
           __syncwarp();
         }
         if (!done) {
@@ -485,17 +489,17 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
       }
       // final pass at the converged h
       {
-        const float H = kGammaK * h;
+        const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
         DensSums s;
         sums_zero(s);
         for (int v0 = 0; v0 < nsrc; v0 += kOvfCap) {
           const int cnt = stage_sources(v0, kOvfCap, nb, lane, put);
-          for (int k = 0; k < cnt; ++k) dens_pair(pi, vi, spos[k], svel[k], H, Hinv, s);
+          for (int k = 0; k < cnt; ++k) dens_pair<K>(pi, vi, spos[k], svel[k], H, Hinv, s);
           __syncwarp();
         }
         if (valid) {
-          dens_write(a, ph, ti, h, s, vi.w, passes, conv, atcap);
+          dens_write<K>(a, ph, ti, h, s, vi.w, passes, conv, atcap);
           pair_acc += (unsigned long long)s.npair;
         }
       }
@@ -514,27 +518,39 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
 namespace sphh {
 using namespace sphk;
 
-cudaError_t launch_density(const DensityArgs& a, const PhysDev& ph, cudaStream_t st) {
+template <int K>
+static cudaError_t launch_density_k(const DensityArgs& a, const PhysDev& ph, cudaStream_t st) {
   static int bps = 0, bps_o = 0;
   if (!bps) {
-    cudaError_t e = cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_density<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kDensBlkSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_density, kBlkThreads, kDensBlkSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_density<K>, kBlkThreads, kDensBlkSmem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_density_overflow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_density_overflow<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kOvfSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_o, k_density_overflow, kThreads, kOvfSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_o, k_density_overflow<K>, kThreads, kOvfSmem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     if (bps_o < 1) bps_o = 1;
   }
   cudaError_t e = cudaMemsetAsync(a.misc + kNumOverflow, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_density<<<a.num_sms * bps, kBlkThreads, kDensBlkSmem, st>>>(a, ph);
-  k_density_overflow<<<a.num_sms * bps_o, kThreads, kOvfSmem, st>>>(a, ph);
+  k_density<K><<<a.num_sms * bps, kBlkThreads, kDensBlkSmem, st>>>(a, ph);
+  k_density_overflow<K><<<a.num_sms * bps_o, kThreads, kOvfSmem, st>>>(a, ph);
   return cudaGetLastError();
+}
+
+cudaError_t launch_density(const DensityArgs& a, const PhysDev& ph, cudaStream_t st) {
+  switch (ph.kernel) {
+    case kKernQuartic:
+      return launch_density_k<kKernQuartic>(a, ph, st);
+    case kKernWendlandC2:
+      return launch_density_k<kKernWendlandC2>(a, ph, st);
+    default:
+      return launch_density_k<kKernCubic>(a, ph, st);
+  }
 }
 
 }  // namespace sphh

@@ -82,7 +82,7 @@ __device__ __forceinline__ void fsums_zero(ForceSums& s) {
   s.npair = 0;
 }
 
-template <int kFl>
+template <int kFl, int K>
 __device__ __forceinline__ void force_pair(const ForceTarget& T, const float4& Aj, const float4& Bj,
                                            const float4& Cj, const float2& Dj, const float4& Ej,
                                            const PhysDev& ph, bool counted, ForceSums& s) {
@@ -90,7 +90,7 @@ __device__ __forceinline__ void force_pair(const ForceTarget& T, const float4& A
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float r = r2 * rinv;
-  const float Gi = kernel_g(r * T.D.y, T.A.w * rinv) * T.Hinv5;
+  const float Gi = kernel_g<K>(r * T.D.y, T.A.w * rinv) * T.Hinv5;
   const float vx = T.B.x - Bj.x, vy = T.B.y - Bj.y, vz = T.B.z - Bj.z;
   const float vdotx = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
   if constexpr (kFl == kFlGradient) {
@@ -103,7 +103,7 @@ __device__ __forceinline__ void force_pair(const ForceTarget& T, const float4& A
     return;
   }
   const float Hj2 = Dj.y * Dj.y;
-  const float Gj = kernel_g(r * Dj.y, Aj.w * rinv) * (Hj2 * Hj2 * Dj.y);
+  const float Gj = kernel_g<K>(r * Dj.y, Aj.w * rinv) * (Hj2 * Hj2 * Dj.y);
   const float mu = fminf(vdotx, 0.0f) * rinv;
   const float vs = fmaf(-ph.beta_v, mu, T.C.z + Cj.z);
   const float av = kFl == kFlSphenix ? 0.5f * (T.E.y + Ej.y) : ph.alpha_v;
@@ -224,7 +224,7 @@ __device__ __forceinline__ float reach(float Hi, float Hj) {
   return kFl == kFlGradient ? Hi : fmaxf(Hi, Hj);
 }
 
-template <int kFl>
+template <int kFl, int K>
 __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, PhysDev ph, SphenixDev x) {
   constexpr int kCap = force_cap<kFl>();
   constexpr bool kE = kFl != kFlMinimal;
@@ -355,8 +355,8 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
           const float r2b = fmaf(dxb, dxb, fmaf(dyb, dyb, dzb * dzb));
           const float Hma = reach<kFl>(Tg.A.w, Aa.w), Hmb = reach<kFl>(Tg.A.w, Ab.w);
           const float4 Ea = kE ? sE[ka] : Tg.E, Eb = kE ? sE[kb] : Tg.E;
-          force_pair<kFl>(Tg, Aa, sB[ka], sC[ka], sD[ka], Ea, ph, r2a < Hma * Hma && ka != self_slot, s0);
-          force_pair<kFl>(Tg, Ab, sB[kb], sC[kb], sD[kb], Eb, ph, r2b < Hmb * Hmb && kb != self_slot, s1);
+          force_pair<kFl, K>(Tg, Aa, sB[ka], sC[ka], sD[ka], Ea, ph, r2a < Hma * Hma && ka != self_slot, s0);
+          force_pair<kFl, K>(Tg, Ab, sB[kb], sC[kb], sD[kb], Eb, ph, r2b < Hmb * Hmb && kb != self_slot, s1);
         }
         if (e < cnt) {
           const int ka = lj[e * 32 + lane];
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
           const float r2a = fmaf(dxa, dxa, fmaf(dya, dya, dza * dza));
           const float Hma = reach<kFl>(Tg.A.w, Aa.w);
           const float4 Ea = kE ? sE[ka] : Tg.E;
-          force_pair<kFl>(Tg, Aa, sB[ka], sC[ka], sD[ka], Ea, ph, r2a < Hma * Hma && ka != self_slot, s0);
+          force_pair<kFl, K>(Tg, Aa, sB[ka], sC[ka], sD[ka], Ea, ph, r2a < Hma * Hma && ka != self_slot, s0);
         }
       } else if (valid) {
         // list overflow: walk the runs directly
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float Hm = reach<kFl>(Tg.A.w, Aj.w);
             if (r2 < Hm * Hm && k != self_slot)
-              force_pair<kFl>(Tg, Aj, sB[k], sC[k], sD[k], kE ? sE[k] : Tg.E, ph, true, s0);
+              force_pair<kFl, K>(Tg, Aj, sB[k], sC[k], sD[k], kE ? sE[k] : Tg.E, ph, true, s0);
           }
         }
       }
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
 // Blocks whose neighbourhood exceeded the staging buffer: one warp per target
 // cell, lane = target, the 27 cells streamed through a per-warp buffer with
 // positions relative to the target cell.
-template <int kFl>
+template <int kFl, int K>
 __global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, PhysDev ph, SphenixDev x) {
   constexpr bool kE = kFl != kFlMinimal;
   extern __shared__ __align__(16) unsigned char fo_raw[];
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, 
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           const float Hm = reach<kFl>(Tg.A.w, Aj.w);
           const bool self = (v0 + k == self_base + (ti - ts));
-          if (r2 < Hm * Hm && !self) force_pair<kFl>(Tg, Aj, sB[k], sC[k], sD[k], kE ? sE[k] : Tg.E, ph, true, s);
+          if (r2 < Hm * Hm && !self) force_pair<kFl, K>(Tg, Aj, sB[k], sC[k], sD[k], kE ? sE[k] : Tg.E, ph, true, s);
         }
         __syncwarp();
       }
@@ -498,27 +498,39 @@ __global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, 
 namespace sphh {
 using namespace sphk;
 
-template <int kFl>
-static cudaError_t launch_force_fl(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
+template <int kFl, int K>
+static cudaError_t launch_force_fk(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
   static int bps = 0, bps_o = 0;
   constexpr size_t kSmem = force_blk_smem<kFl>(), kSmemO = fovf_smem<kFl>();
   if (!bps) {
-    cudaError_t e = cudaFuncSetAttribute(k_force<kFl>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_force<kFl, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_force<kFl>, kBlkThreads, kSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_force<kFl, K>, kBlkThreads, kSmem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_force_overflow<kFl>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemO);
+    e = cudaFuncSetAttribute(k_force_overflow<kFl, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemO);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_o, k_force_overflow<kFl>, kThreads, kSmemO);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_o, k_force_overflow<kFl, K>, kThreads, kSmemO);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
     if (bps_o < 1) bps_o = 1;
   }
   cudaError_t e = cudaMemsetAsync(a.misc + kNumOverflow, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_force<kFl><<<a.num_sms * bps, kBlkThreads, kSmem, st>>>(a, ph, x);
-  k_force_overflow<kFl><<<a.num_sms * bps_o, kThreads, kSmemO, st>>>(a, ph, x);
+  k_force<kFl, K><<<a.num_sms * bps, kBlkThreads, kSmem, st>>>(a, ph, x);
+  k_force_overflow<kFl, K><<<a.num_sms * bps_o, kThreads, kSmemO, st>>>(a, ph, x);
   return cudaGetLastError();
+}
+
+template <int kFl>
+static cudaError_t launch_force_fl(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
+  switch (ph.kernel) {
+    case kKernQuartic:
+      return launch_force_fk<kFl, kKernQuartic>(a, ph, x, st);
+    case kKernWendlandC2:
+      return launch_force_fk<kFl, kKernWendlandC2>(a, ph, x, st);
+    default:
+      return launch_force_fk<kFl, kKernCubic>(a, ph, x, st);
+  }
 }
 
 cudaError_t launch_force(const ForceArgs& a, const PhysDev& ph, cudaStream_t st) {

@@ -42,6 +42,34 @@ struct GridDev {
   int64_t n;          // particles in this simulation
 };
 
+enum : int { kKernCubic = 0, kKernQuartic = 1, kKernWendlandC2 = 2, kNumKernels = 3 };
+
+template <int K>
+struct KernT;
+template <>
+struct KernT<kKernCubic> {
+  static constexpr float gamma = 1.825742f;
+  static constexpr double gammad = 1.825742;
+};
+template <>
+struct KernT<kKernQuartic> {
+  static constexpr float gamma = 2.018932f;
+  static constexpr double gammad = 2.018932;
+  static constexpr float c = 9.71404681957369f;  // 15625 / (512 pi)
+};
+template <>
+struct KernT<kKernWendlandC2> {
+  static constexpr float gamma = 1.936492f;
+  static constexpr double gammad = 1.936492;
+  static constexpr float c = 3.3422538049298023f;  // 21 / (2 pi)
+};
+
+// gamma_K of a kernel id (host and device; cubic for an unknown id).
+__host__ __device__ inline double kernel_gamma(int k) {
+  return k == kKernQuartic ? KernT<kKernQuartic>::gammad
+                           : (k == kKernWendlandC2 ? KernT<kKernWendlandC2>::gammad : KernT<kKernCubic>::gammad);
+}
+
 // Physics constants passed by value to the loop kernels.
 struct PhysDev {
   float gamma;
@@ -52,6 +80,7 @@ struct PhysDev {
   double h_tol;
   int32_t max_h_iter;
   int32_t count_pairs;
+  int32_t kernel;  // kKern*
 };
 
 // Constants of the SPHENIX flavour (Sec. 3.3) and the step dt over which its
@@ -89,8 +118,10 @@ struct NewtonConst {
   int32_t max_it;
 };
 
+template <int K = 0>
 __device__ __forceinline__ NewtonConst newton_const(const PhysDev& ph) {
-  const double g3 = kGammaKd * kGammaKd * kGammaKd;
+  constexpr double gk = KernT<K>::gammad;
+  const double g3 = gk * gk * gk;
   NewtonConst c;
   c.a0 = g3 * (double)ph.eta3;
   c.b0 = 3.0 * c.a0;
@@ -127,8 +158,9 @@ __device__ __forceinline__ bool newton_update(float Sw, float Sdw, const NewtonC
 }
 
 // The largest h whose support gamma_K h stays below `side` (and half the box).
+template <int K = 0>
 __device__ __forceinline__ float h_cap(double side, double L) {
-  return (float)(fmin(side, 0.5 * L) * (1.0 - 1e-5) / kGammaKd);
+  return (float)(fmin(side, 0.5 * L) * (1.0 - 1e-5) / KernT<K>::gammad);
 }
 
 // Simulation owning a pool index (upper bound search over sim_offset).
@@ -226,44 +258,101 @@ __device__ __forceinline__ int axis_of(int dx, int dy, int dz, int& sense) {
   return z == 1 ? 4 + (y + 1) * 3 + (x + 1) : (y == 1 ? 1 + (x + 1) : 0);
 }
 
-// Cubic spline pieces with q = r/H (Sec. 3.1): w(q) and g(q) = w'(q)/q,
-// branch-free; both vanish for q >= 1.  h_rinv = H / r is only used on the
-// outer piece (q >= 1/2), where it is finite.
+// Kernels (Sec. 3.1) in the Dehnen & Aly (2012) form W = w(q)/H^3, q = r/H,
+// H = gamma_K h, with h twice the kernel's standard deviation per dimension:
+//   0 cubic spline   w = 16/pi [(1-q)^3 - 4 (1/2-q)_+^3],                 gamma_K = 1.825742
+//   1 quartic spline w = 15625/(512 pi) [(1-q)^4 - 5 (3/5-q)_+^4 + 10 (1/5-q)_+^4],
+//                                                                          gamma_K = 2.018932
+//   2 Wendland C2    w = 21/(2 pi) (1-q)^4 (1 + 4q),                       gamma_K = 1.936492
+// The loops are compiled once per kernel (template parameter K).
+// The quartic spline's pieces (x)_+ and w'(q) = -4 c [a^3 - 5 b^3 + 10 d^3]
+// with a = (1-q)_+, b = (3/5-q)_+, d = (1/5-q)_+.  Near q = 0 the bracket
+// cancels, so w'(q)/q there comes from its expansion c (24 q^2 - 24/5).
+__device__ __forceinline__ void quartic_parts(float q, float& a, float& b, float& d) {
+  a = fmaxf(1.0f - q, 0.0f);
+  b = fmaxf(0.6f - q, 0.0f);
+  d = fmaxf(0.2f - q, 0.0f);
+}
+
+// w(q) and g(q) = w'(q)/q, branch-free; both vanish for q >= 1.  H_rinv =
+// H / r is only used where q is bounded away from 0.
+template <int K = kKernCubic>
 __device__ __forceinline__ void kernel_w_g(float q, float H_rinv, float& w, float& g) {
-  const float a = fmaxf(1.0f - q, 0.0f);
-  const bool inner = q < 0.5f;
-  const float w_in = kWNorm * fmaf(q * q, fmaf(6.0f, q, -6.0f), 1.0f);  // 8/pi (1 - 6q^2 + 6q^3)
-  const float w_out = 2.0f * kWNorm * a * a * a;                        // 16/pi (1 - q)^3
-  const float g_in = kWNorm * fmaf(18.0f, q, -12.0f);                   // 8/pi (18 q - 12)
-  const float g_out = -6.0f * kWNorm * a * a * H_rinv;                  // -48/pi (1-q)^2 / q
-  w = inner ? w_in : w_out;
-  g = inner ? g_in : g_out;
+  if constexpr (K == kKernCubic) {
+    const float a = fmaxf(1.0f - q, 0.0f);
+    const bool inner = q < 0.5f;
+    const float w_in = kWNorm * fmaf(q * q, fmaf(6.0f, q, -6.0f), 1.0f);  // 8/pi (1 - 6q^2 + 6q^3)
+    const float w_out = 2.0f * kWNorm * a * a * a;                        // 16/pi (1 - q)^3
+    const float g_in = kWNorm * fmaf(18.0f, q, -12.0f);                   // 8/pi (18 q - 12)
+    const float g_out = -6.0f * kWNorm * a * a * H_rinv;                  // -48/pi (1-q)^2 / q
+    w = inner ? w_in : w_out;
+    g = inner ? g_in : g_out;
+  } else if constexpr (K == kKernQuartic) {
+    constexpr float c = KernT<K>::c;
+    float a, b, d;
+    quartic_parts(q, a, b, d);
+    const float a2 = a * a, b2 = b * b, d2 = d * d;
+    w = c * fmaf(a2, a2, fmaf(-5.0f * b2, b2, 10.0f * d2 * d2));
+    const float dwq = -4.0f * c * fmaf(a2, a, fmaf(-5.0f * b2, b, 10.0f * d2 * d));
+    g = q < 0.2f ? c * fmaf(24.0f, q * q, -4.8f) : dwq * H_rinv;
+  } else {
+    constexpr float c = KernT<K>::c;
+    const float a = fmaxf(1.0f - q, 0.0f);
+    const float a3 = a * a * a;
+    w = c * a3 * a * fmaf(4.0f, q, 1.0f);
+    g = -20.0f * c * a3;
+  }
 }
 
 // w(q) and 3 w(q) + q w'(q), the two sums of the Newton passes, without
-// the gradient: on the inner piece 8/pi (1 - 6q^2 + 6q^3) and
+// the gradient.  Cubic: on the inner piece 8/pi (1 - 6q^2 + 6q^3) and
 // 8/pi (3 - 30 q^2 + 36 q^3), on the outer piece 16/pi (1-q)^3 and
-// 48/pi (1-q)^2 (1 - 2q); both vanish for q >= 1.
+// 48/pi (1-q)^2 (1 - 2q).  Wendland C2: 3w + q w' = c (1-q)^3 (3 + 9q - 32 q^2).
+// All vanish for q >= 1.
+template <int K = kKernCubic>
 __device__ __forceinline__ void kernel_w_dw(float q, float& w, float& dw) {
-  const float c = kWNorm;
-  const float q2 = q * q;
-  const float w_in = fmaf(q2, fmaf(6.0f * c, q, -6.0f * c), c);
-  const float dw_in = fmaf(q2, fmaf(36.0f * c, q, -30.0f * c), 3.0f * c);
-  const float a = fmaxf(1.0f - q, 0.0f);
-  const float a2 = a * a;
-  const float w_out = (2.0f * c) * a2 * a;
-  const float dw_out = a2 * fmaf(-12.0f * c, q, 6.0f * c);
-  const bool inner = q < 0.5f;
-  w = inner ? w_in : w_out;
-  dw = inner ? dw_in : dw_out;
+  if constexpr (K == kKernCubic) {
+    const float c = kWNorm;
+    const float q2 = q * q;
+    const float w_in = fmaf(q2, fmaf(6.0f * c, q, -6.0f * c), c);
+    const float dw_in = fmaf(q2, fmaf(36.0f * c, q, -30.0f * c), 3.0f * c);
+    const float a = fmaxf(1.0f - q, 0.0f);
+    const float a2 = a * a;
+    const float w_out = (2.0f * c) * a2 * a;
+    const float dw_out = a2 * fmaf(-12.0f * c, q, 6.0f * c);
+    const bool inner = q < 0.5f;
+    w = inner ? w_in : w_out;
+    dw = inner ? dw_in : dw_out;
+  } else if constexpr (K == kKernQuartic) {
+    constexpr float c = KernT<K>::c;
+    float a, b, d;
+    quartic_parts(q, a, b, d);
+    const float a2 = a * a, b2 = b * b, d2 = d * d;
+    w = c * fmaf(a2, a2, fmaf(-5.0f * b2, b2, 10.0f * d2 * d2));
+    const float dwq = -4.0f * c * fmaf(a2, a, fmaf(-5.0f * b2, b, 10.0f * d2 * d));
+    dw = fmaf(q, dwq, 3.0f * w);
+  } else {
+    constexpr float c = KernT<K>::c;
+    const float a = fmaxf(1.0f - q, 0.0f);
+    const float a3 = a * a * a;
+    w = c * a3 * a * fmaf(4.0f, q, 1.0f);
+    dw = c * a3 * fmaf(q, fmaf(-32.0f, q, 9.0f), 3.0f);
+  }
 }
 
 // g(q) = w'(q)/q only.
+template <int K = kKernCubic>
 __device__ __forceinline__ float kernel_g(float q, float H_rinv) {
-  const float a = fmaxf(1.0f - q, 0.0f);
-  const float g_in = kWNorm * fmaf(18.0f, q, -12.0f);
-  const float g_out = -6.0f * kWNorm * a * a * H_rinv;
-  return q < 0.5f ? g_in : g_out;
+  if constexpr (K == kKernCubic) {
+    const float a = fmaxf(1.0f - q, 0.0f);
+    const float g_in = kWNorm * fmaf(18.0f, q, -12.0f);
+    const float g_out = -6.0f * kWNorm * a * a * H_rinv;
+    return q < 0.5f ? g_in : g_out;
+  } else {
+    float w, g;
+    kernel_w_g<K>(q, H_rinv, w, g);
+    return g;
+  }
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -34,6 +34,7 @@ struct BuildArgs {
   int sort_cells = 1;       // 0: counts and cell_start only (the tree build orders)
   double radius = 0.0;      // > 0: cells at least this wide, h unused (friends-of-friends)
   int cells_per_particle = 8;  // n_c^3 <= cells_per_particle n + 216 per simulation
+  double gamma_k = sphk::kGammaKd;  // H / h of the kernel
 };
 cudaError_t launch_build(const BuildArgs& a, cudaStream_t st);
 
@@ -90,6 +91,7 @@ struct GatherForceArgs {
   const float4* rel = nullptr;
   const int4* fine = nullptr;
   float4* rec = nullptr;
+  float gamma_k = sphk::kGammaK;  // H / h of the kernel
 };
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
 
@@ -165,6 +167,7 @@ struct SphenixAlphaArgs {
   const int64_t* sim_offset;
   const float *h, *c, *div_v, *v_sig;
   float *div_v_prev, *alpha_v;
+  float gamma_k;  // H / h of the kernel
 };
 cudaError_t launch_sphenix_alpha_v(const SphenixAlphaArgs& a, const sphk::SphenixDev& x, cudaStream_t st);
 // Sorted copies E[s] = (u, alpha_V, P, alpha_c) of particle perm[s].
@@ -301,6 +304,7 @@ struct StepArgs {
   const int64_t* sim_offset;
   const double* box;
   double cfl;
+  double gamma_k = sphk::kGammaKd;  // H / h of the kernel
   double *x, *y, *z;
   float *vx, *vy, *vz, *u;
   const float* m;

@@ -61,11 +61,11 @@ __global__ void k_dt_min(const int64_t* __restrict__ sim_offset, int n_sims, int
   if (cur >= 0 && m < INFINITY && lane == __ffs(grp) - 1) atomicMin(&bits[cur], __float_as_uint(m));
 }
 
-__global__ void k_dt_final(const unsigned* __restrict__ bits, int n_sims, double cfl,
+__global__ void k_dt_final(const unsigned* __restrict__ bits, int n_sims, double cfl, double gamma_k,
                            double* __restrict__ dt) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x) {
     const float m = __uint_as_float(bits[s]);
-    dt[s] = isinf(m) ? 0.0 : cfl * kGammaKd * (double)m;
+    dt[s] = isinf(m) ? 0.0 : cfl * gamma_k * (double)m;
   }
 }
 
@@ -194,7 +194,7 @@ cudaError_t launch_dt(const StepArgs& a, cudaStream_t st) {
     if (b > cap) b = cap;
     k_dt_min<<<(int)b, 256, 0, st>>>(a.sim_offset, a.n_sims, a.n_total, a.h, a.v_sig, a.dt_bits);
   }
-  k_dt_final<<<sb, 256, 0, st>>>(a.dt_bits, a.n_sims, a.cfl, a.dt);
+  k_dt_final<<<sb, 256, 0, st>>>(a.dt_bits, a.n_sims, a.cfl, a.gamma_k, a.dt);
   return cudaGetLastError();
 }
 cudaError_t launch_kick_drift(const StepArgs& a, cudaStream_t st) {

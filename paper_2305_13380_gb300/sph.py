@@ -36,6 +36,7 @@ SPH_FLAG_COUNT_PAIRS = 2
 SPH_FLAG_TIMING = 4
 SPH_FLAG_TREE = 8
 SPH_FLAG_AXIS_SORT = 16
+SPH_KERNEL_CUBIC, SPH_KERNEL_QUARTIC, SPH_KERNEL_WENDLAND_C2 = 0, 1, 2
 
 TIMING_GROUPS = ("build", "gather", "density", "force", "integrate")
 
@@ -47,7 +48,7 @@ class sph_params(C.Structure):
                 ("alpha_v", C.c_double), ("beta_v", C.c_double), ("eps_balsara", C.c_double),
                 ("h_tol", C.c_double), ("cfl", C.c_double), ("cell_margin", C.c_double),
                 ("max_h_iter", C.c_int32), ("flags", C.c_int32), ("n_leaf", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("kernel", C.c_int32)]
 
 
 class sph_cells(C.Structure):

@@ -63,3 +63,12 @@ def test_sphenix_defaults_and_argument_checks_without_gpu(libsph):
     assert L.sph_force_sphenix(None, None, None, None, None, None, None) == sph.SPH_E_INVAL
     bad = sph.sph_sphenix_default_params(alpha_c_max=-1.0)
     assert L.sph_step_sphenix(None, None, ctypes.byref(bad), None, None) == sph.SPH_E_INVAL
+
+
+def test_kernel_parameter_checked_without_gpu(libsph):
+    from paper_2305_13380_gb300 import sph
+    h = ctypes.c_void_p()
+    for kw in (dict(kernel=3), dict(kernel=-1), dict(kernel=2, flags=sph.SPH_FLAG_TREE)):
+        p = sph.sph_default_params(**kw)
+        assert sph.lib().sph_create(ctypes.byref(h), ctypes.byref(p), None) == sph.SPH_E_INVAL, kw
+    assert sph.sph_default_params().kernel == sph.SPH_KERNEL_CUBIC
