@@ -36,6 +36,7 @@ UNIT = "particle-updates/s"
 # divide and square root counts 1; see the design notes for the tally).
 F_DENSITY = 66
 F_FORCE = 72
+KERNELS = {"cubic": 0, "quartic": 1, "wendland_c2": 2}
 # Starting viscosity parameter of the SPHENIX workloads (alpha_c starts at 0).
 SPHENIX_ALPHA_V0 = 0.8
 
@@ -82,6 +83,8 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=sorted(KERNELS), default="cubic",
+                    help="latticeN: smoothing kernel (the nested grids take the cubic spline)")
     ap.add_argument("--sphenix", action="store_true",
                     help="latticeN: the SPHENIX flavour (time-dependent viscosity, conduction)")
     ap.add_argument("--axis-sort", action="store_true",
@@ -171,12 +174,13 @@ def _f32(p):
     return q
 
 
-def oracle_sample(p, n_target: int, seed: int, sphenix: bool = False):
+def oracle_sample(p, n_target: int, seed: int, sphenix: bool = False, kernel: int = 0):
     """Oracle density + force for the particles of a sub-cube holding about
     n_target particles (the density also runs on a margin of one support
     around it, which the force needs).  With sphenix, the SPHENIX evaluation:
     the viscosity update and the gradient pass on the margin too, then the
-    SPHENIX force.  Returns (particles updated, seconds)."""
+    SPHENIX force.  kernel: SPH_KERNEL_* of the run.  Returns (particles
+    updated, seconds)."""
     import numpy as np
 
     import oracle
@@ -186,7 +190,9 @@ def oracle_sample(p, n_target: int, seed: int, sphenix: bool = False):
     side = L * min(1.0, (n_target / n) ** (1.0 / 3.0))
     rng = np.random.default_rng(seed)
     c0 = rng.uniform(0, L, 3)
-    H = 1.825742 * float(np.max(q["h0"])) * 1.1
+    phys = oracle.Physics(kernel=kernel)
+    gk = oracle.gamma_k(kernel)
+    H = gk * float(np.max(q["h0"])) * 1.1
 
     def inside(s):
         d = [np.abs((q[k] - c0[i] + 0.5 * L) % L - 0.5 * L) for i, k in enumerate("xyz")]
@@ -195,10 +201,10 @@ def oracle_sample(p, n_target: int, seed: int, sphenix: bool = False):
     if len(core):
         # the halo reaches one (generous) support of the core's particles;
         # wider particles outside it keep stand-in values from their h0
-        H = 1.825742 * float(np.max(q["h0"][core])) * 1.5
+        H = gk * float(np.max(q["h0"][core])) * 1.5
     halo = inside(side + 2 * H)
     t0 = time.perf_counter()
-    d = oracle.density(q, q["h0"], targets=halo)
+    d = oracle.density(q, q["h0"], targets=halo, phys=phys)
     h0 = q["h0"]
     rho0 = q["m"] * (1.2348 / h0) ** 3
     P0 = (5.0 / 3.0 - 1.0) * q["u"] * rho0
@@ -207,28 +213,28 @@ def oracle_sample(p, n_target: int, seed: int, sphenix: bool = False):
     for k in state:
         state[k][halo] = d[k]
     if not sphenix:
-        oracle.force(q, state, targets=core)
+        oracle.force(q, state, targets=core, phys=phys)
         return len(core), time.perf_counter() - t0
     X = oracle.Sphenix()
     av = np.full(n, SPHENIX_ALPHA_V0)
     div = np.zeros(n)
     div[halo] = d["div_v"]
     dt = 1e-4 * float(np.min(q["h0"]))
-    av = oracle.sphenix_alpha_v(dt, state["h"], state["c"], div, np.zeros(n), 2.0 * state["c"], av, X)
-    g = oracle.sphenix_gradient(q, state, av, np.zeros(n), dt, halo, X)
+    av = oracle.sphenix_alpha_v(dt, state["h"], state["c"], div, np.zeros(n), 2.0 * state["c"], av, X, phys)
+    g = oracle.sphenix_gradient(q, state, av, np.zeros(n), dt, halo, X, phys)
     ac = np.zeros(n)
     ac[halo] = g["alpha_c"]
-    oracle.sphenix_force(q, state, av, ac, targets=core)
+    oracle.sphenix_force(q, state, av, ac, targets=core, phys=phys)
     return len(core), time.perf_counter() - t0
 
 
-def cpu_baseline(p, budget_s: float, sphenix: bool = False) -> dict:
+def cpu_baseline(p, budget_s: float, sphenix: bool = False, kernel: int = 0) -> dict:
     import oracle
     oracle.build()
     # calibrate on a small sample, then size the timed sample to the budget
-    n0, t0 = oracle_sample(p, 2000, seed=1, sphenix=sphenix)
+    n0, t0 = oracle_sample(p, 2000, seed=1, sphenix=sphenix, kernel=kernel)
     n_target = int(max(2000, min(len(p["x"]), n0 * budget_s / max(t0, 1e-3))))
-    nu, sec = oracle_sample(p, n_target, seed=2, sphenix=sphenix)
+    nu, sec = oracle_sample(p, n_target, seed=2, sphenix=sphenix, kernel=kernel)
     what = "SPHENIX density, viscosity update, gradient pass and force" if sphenix else "density + force"
     return {"value": nu / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"{what}: {nu} particles of a sub-cube (density also on a one-support halo, "
@@ -377,7 +383,8 @@ def run_reference(args, world: int, rank: int):
     metric, unit = (("friends-of-friends particles/s (clustered, 2M)", "particles/s") if fof
                     else (METRIC, UNIT))
     sample = ((lambda q, k, seed: oracle_fof_sample(q, k, seed)) if fof else
-              (lambda q, k, seed: oracle_sample(q, k, seed, sphenix=args.sphenix)))
+              (lambda q, k, seed: oracle_sample(q, k, seed, sphenix=args.sphenix,
+                                                kernel=KERNELS[args.kernel])))
     # size every sample so that the whole run stays near args.ref_budget seconds
     n0, t0 = sample(p, 1000, seed=99)
     per_step = args.ref_budget / max(1, args.steps + args.warmup)
@@ -642,8 +649,9 @@ def run_step(args, world: int, rank: int, local: int):
     # A caller that keeps its host copy in the same layout moves a step's
     # inputs and results with one copy each way.
     sphenix = bool(args.sphenix)
-    if sphenix and p["tree"]:
-        raise SystemExit("the SPHENIX flavour runs on the uniform grid (latticeN workloads)")
+    kern = KERNELS[args.kernel]
+    if (sphenix or kern) and p["tree"]:
+        raise SystemExit("the SPHENIX flavour and the other kernels run on the uniform grid (latticeN)")
     f64_keys = ("x", "y", "z")
     # SPHENIX carries alpha_V, alpha_c and the previous divergence from step
     # to step: they join the fields a step reads and updates
@@ -670,7 +678,7 @@ def run_step(args, world: int, rank: int, local: int):
     # grid-mode flags of every context of the run
     mode = tree | (sph.SPH_FLAG_AXIS_SORT if args.axis_sort and not tree else 0)
     # initial density + force (untimed) through the single-simulation calls
-    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | mode))
+    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | mode, kernel=kern))
     part = sph.particles(t)
     dout = sph.density_out({k: arrays[k] for k in sph.DENSITY_FIELDS})
     h_in = t["h0"]
@@ -702,7 +710,7 @@ def run_step(args, world: int, rank: int, local: int):
         else:
             sph.sph_step(c, pl)
 
-    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | mode))
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | mode, kernel=kern))
     pool = sph.pool(sim_offset, box, arrays)
     for _ in range(args.warmup):
         step(ctx, pool)
@@ -738,7 +746,7 @@ def run_step(args, world: int, rank: int, local: int):
     value, ms = replicas.job_throughput(n * args.steps, e0.elapsed_time(e1))
 
     # one more step (untimed) that counts pairs and Newton passes
-    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | mode))
+    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | mode, kernel=kern))
     arrays["n_iter"] = torch.zeros(n, dtype=torch.int32, device=dev)
     step(cnt, sph.pool(sim_offset, box, arrays))
     pairs_d, pairs_f = sph.sph_pair_counts(cnt)
@@ -753,7 +761,7 @@ def run_step(args, world: int, rank: int, local: int):
     bo = offs["m"]                  # the same without m, which a step does not change
     host = torch.empty(bi, dtype=torch.uint8, pin_memory=True)
     host.copy_(dbuf[:bi])
-    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=mode))
+    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=mode, kernel=kern))
     for it in range(2 + args.e2e_steps):
         if it == 2:
             torch.cuda.synchronize()
@@ -791,7 +799,7 @@ def run_step(args, world: int, rank: int, local: int):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, args.cpu_budget, sphenix)
+        cpu = cpu_baseline(p, args.cpu_budget, sphenix, kern)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -802,6 +810,7 @@ def run_step(args, world: int, rank: int, local: int):
                             "update, gradient pass (lap u, alpha_c), SPHENIX force, kick" if sphenix else
                             "sph_step: dt, kick+drift, cell build, density (h solve), force, kick"),
                    "flavour": "SPHENIX" if sphenix else "Minimal",
+                   "kernel": args.kernel,
                    "l2": "inputs larger than L2: each step touches ~0.5 GB of state and scratch",
                    "parallelism": f"replicas x{world}",
                    "grid": ("nested grids" if tree else
