@@ -18,6 +18,14 @@ constexpr int kBlkWarps = 8;
 // of ~2.4 spacings holds up to ~1100 particles.  The density and force loops
 // use the same capacity, so they stage (and overflow) identically.
 constexpr int kBlkStageCap = 1216;
+// Kernels with a wider support (in units of h) have larger cells and more
+// particles per cell, in proportion to gamma_K^3: the Wendland C2 kernel
+// (x1.14) stages up to 1400 sources, the quartic spline (x1.35) up to 1520,
+// the most that keeps two force blocks per SM.
+template <int K>
+__host__ __device__ constexpr int stage_cap() {
+  return K == kKernQuartic ? 1520 : (K == kKernWendlandC2 ? 1400 : kBlkStageCap);
+}
 // Neighbour-list entries per lane (sources within one cell size; with two
 // lanes per target a lattice lane holds ~28 +- 4).
 constexpr int kLaneListCap = 44;

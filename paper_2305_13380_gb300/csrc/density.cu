@@ -35,7 +35,11 @@
 
 namespace sphk {
 
-constexpr int kDensBlkCap = kBlkStageCap;  // staged sources per block
+// staged sources per block
+template <int K>
+__host__ __device__ constexpr int dens_cap() {
+  return stage_cap<K>();
+}
 constexpr int kListCap = kLaneListCap;     // list entries per lane
 constexpr int kListRows = kListCap + 1;    // + one scratch row for the branch-free append
 // The list keeps each entry's r^2 for the Newton passes (kCacheR2), or only
@@ -48,11 +52,14 @@ constexpr bool kCacheR2 = false;
 constexpr int kDensMinBlocks = 3;  // resident blocks per SM the registers are sized for
 // shared memory: staged sources (32 B each), per-warp lists (r^2, slot),
 // the staging table, the block's target rounds and its target slots/cells
-constexpr size_t kDensBlkSmem = (size_t)kDensBlkCap * 2 * sizeof(float4) +
+template <int K>
+__host__ __device__ constexpr size_t dens_blk_smem() {
+  return (size_t)dens_cap<K>() * 2 * sizeof(float4) +
                                 (size_t)kBlkWarps * kListRows * 32 *
                                     ((kCacheR2 ? sizeof(float) : 0) + sizeof(uint16_t)) +
                                 sizeof(StageTable) + sizeof(BlockTargets) +
-                                (size_t)kDensBlkCap * (sizeof(uint16_t) + sizeof(uint8_t));
+                                (size_t)dens_cap<K>() * (sizeof(uint16_t) + sizeof(uint8_t));
+}
 constexpr int kOvfCap = 256;  // per-warp staging of the overflow kernel
 constexpr size_t kOvfSmem = (size_t)kWarpsPerBlock * kOvfCap * 2 * sizeof(float4);
 
@@ -170,14 +177,14 @@ template <int K>
 __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::DensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   float4* spos = reinterpret_cast<float4*>(dsm_raw);
-  float4* svel = spos + kDensBlkCap;
+  float4* svel = spos + dens_cap<K>();
   // per-lane list entries (r^2, staged slot), column layout [entry][lane]
-  float* lr2_all = reinterpret_cast<float*>(svel + kDensBlkCap);
+  float* lr2_all = reinterpret_cast<float*>(svel + dens_cap<K>());
   uint16_t* lj_all = reinterpret_cast<uint16_t*>(lr2_all + (kCacheR2 ? kBlkWarps * kListRows * 32 : 0));
   StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * kListRows * 32);
   BlockTargets& BT = *reinterpret_cast<BlockTargets*>(&T + 1);
   uint16_t* tgt_slot = reinterpret_cast<uint16_t*>(&BT + 1);
-  uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + kDensBlkCap);
+  uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + dens_cap<K>());
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* lr2 = lr2_all + warp * (kListRows * 32);
   uint16_t* lj = lj_all + warp * (kListRows * 32);
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
   for (int32_t b = blockIdx.x; b < total; b += gridDim.x) {
     const BlockGeom g = block_geom(a.grid, a.n_sims, b);
     const int32_t nsrc = build_stage_table(g, a.cell_start, T);
-    if (nsrc > kDensBlkCap) {
+    if (nsrc > dens_cap<K>()) {
       if (threadIdx.x == 0) a.overflow[atomicAdd(&a.misc[kNumOverflow], 1)] = b;
       __syncthreads();
       continue;
@@ -523,9 +530,9 @@ static cudaError_t launch_density_k(const DensityArgs& a, const PhysDev& ph, cud
   static int bps = 0, bps_o = 0;
   if (!bps) {
     cudaError_t e = cudaFuncSetAttribute(k_density<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kDensBlkSmem);
+                                         (int)dens_blk_smem<K>());
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_density<K>, kBlkThreads, kDensBlkSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_density<K>, kBlkThreads, dens_blk_smem<K>());
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_density_overflow<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kOvfSmem);
@@ -537,7 +544,7 @@ static cudaError_t launch_density_k(const DensityArgs& a, const PhysDev& ph, cud
   }
   cudaError_t e = cudaMemsetAsync(a.misc + kNumOverflow, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_density<K><<<a.num_sms * bps, kBlkThreads, kDensBlkSmem, st>>>(a, ph);
+  k_density<K><<<a.num_sms * bps, kBlkThreads, dens_blk_smem<K>(), st>>>(a, ph);
   k_density_overflow<K><<<a.num_sms * bps_o, kThreads, kOvfSmem, st>>>(a, ph);
   return cudaGetLastError();
 }

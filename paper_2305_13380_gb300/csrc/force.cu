@@ -42,9 +42,9 @@ namespace sphk {
 
 enum : int { kFlMinimal = 0, kFlSphenix = 1, kFlGradient = 2 };
 
-template <int kFl>
+template <int kFl, int K>
 __host__ __device__ constexpr int force_cap() {
-  return kFl == kFlMinimal ? kBlkStageCap : 1200;
+  return kFl == kFlMinimal ? stage_cap<K>() : (stage_cap<K>() < 1200 ? stage_cap<K>() : 1200);
 }
 template <int kFl>
 __host__ __device__ constexpr size_t rec_bytes() {  // staged bytes per source
@@ -54,12 +54,13 @@ constexpr int kFListCap = 48;
 constexpr int kFListEager = 4;  // 16-byte list words loaded before the count is known
 // per source: A (x, y, z, H), B (vx, vy, vz, m), C (fP, f, c, B), D (rho, 1/H),
 // and for SPHENIX E (u, alpha_V, P, alpha_c)
-template <int kFl>
+template <int kFl, int K>
 __host__ __device__ constexpr size_t force_blk_smem() {
-  return (size_t)force_cap<kFl>() * rec_bytes<kFl>() + (size_t)kBlkWarps * kFListCap * 32 * sizeof(uint16_t) +
-         sizeof(StageTable) + sizeof(BlockTargets) + (size_t)force_cap<kFl>() * (sizeof(uint16_t) + sizeof(uint8_t));
+  return (size_t)force_cap<kFl, K>() * rec_bytes<kFl>() + (size_t)kBlkWarps * kFListCap * 32 * sizeof(uint16_t) +
+         sizeof(StageTable) + sizeof(BlockTargets) + (size_t)force_cap<kFl, K>() * (sizeof(uint16_t) + sizeof(uint8_t));
 }
-static_assert(2 * (force_blk_smem<kFlSphenix>() + 1024) <= 228 * 1024, "two SPHENIX blocks per SM");
+static_assert(2 * (force_blk_smem<kFlSphenix, kKernCubic>() + 1024) <= 228 * 1024, "two SPHENIX blocks per SM");
+static_assert(2 * (force_blk_smem<kFlMinimal, kKernQuartic>() + 1024) <= 228 * 1024, "two quartic blocks per SM");
 constexpr int kFOvfCap = 160;
 template <int kFl>
 __host__ __device__ constexpr size_t fovf_smem() {
@@ -226,7 +227,7 @@ __device__ __forceinline__ float reach(float Hi, float Hj) {
 
 template <int kFl, int K>
 __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, PhysDev ph, SphenixDev x) {
-  constexpr int kCap = force_cap<kFl>();
+  constexpr int kCap = force_cap<kFl, K>();
   constexpr bool kE = kFl != kFlMinimal;
   extern __shared__ __align__(16) unsigned char fsm_raw[];
   float4* sA = reinterpret_cast<float4*>(fsm_raw);
@@ -501,7 +502,7 @@ using namespace sphk;
 template <int kFl, int K>
 static cudaError_t launch_force_fk(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
   static int bps = 0, bps_o = 0;
-  constexpr size_t kSmem = force_blk_smem<kFl>(), kSmemO = fovf_smem<kFl>();
+  constexpr size_t kSmem = force_blk_smem<kFl, K>(), kSmemO = fovf_smem<kFl>();
   if (!bps) {
     cudaError_t e = cudaFuncSetAttribute(k_force<kFl, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
