@@ -164,7 +164,14 @@ __device__ __forceinline__ int next_round(BlockTargets& B, int lane) {
   return __shfl_sync(0xffffffffu, r, 0);
 }
 
-// Block-collective; ends with __syncthreads().
+// Block-collective; ends with __syncthreads().  Targets are dealt to warps
+// in rounds of `per` targets with tpp lanes each: 4 lanes up to 8 targets a
+// round, else 2 lanes for up to 16.  Kernels wider than the cubic spline (K)
+// always take 4 lanes: their lists are 1.2-1.4 times longer, and at 2 lanes
+// a few percent of lanes would overflow their list, which sends every warp
+// holding one down the direct path.  The density and the force call this
+// with the same K, so their rounds (and list columns) agree.
+template <int K = kKernCubic>
 __device__ __forceinline__ void build_targets(const BlockGeom& g, const StageTable& T, BlockTargets& B,
                                               uint16_t* tgt_slot, uint8_t* tgt_cell) {
   if (threadIdx.x == 0) {
@@ -186,6 +193,7 @@ __device__ __forceinline__ void build_targets(const BlockGeom& g, const StageTab
     B.n = run;
     int per = (run + kBlkWarps - 1) / kBlkWarps;
     per = per < 1 ? 1 : per;
+    if (K != kKernCubic && per > 8) per = 8;
     const int tpp = per <= 8 ? 4 : 2;
     if (per > 16) per = 16;
     B.per = per;

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       spos[v] = p;
       svel[v] = a.vel4[j];
     }
-    build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+    build_targets<K>(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
 
     const float hcap = h_cap<K>((double)g.G.cell_f, g.G.L);
     const float R2 = g.G.cell_f * g.G.cell_f;

@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
     const float dt = kFl == kFlGradient ? block_dt(a, x, b) : 0.0f;
     // the targets' rounds first (they need only the table), so that each
     // warp's first list is in flight together with the staging loads
-    build_targets(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+    build_targets<K>(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
     const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
     const int sub = lane & (tpp - 1);
     int pre_lc = 0xffff;
