@@ -972,6 +972,8 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
   s.dt = pl->dt;
   s.dt_bits = c->dt_bits;
   s.status = c->misc + sphk::kStatus;
+  s.h_guess = pl->h;
+  s.div_v = pl->div_v;
   t_begin(c, SPH_T_INTEGRATE);
   if (sphh::launch_dt(s, c->st) != cudaSuccess) return SPH_E_CUDA;
   if (sphh::launch_kick_drift(s, c->st) != cudaSuccess) return SPH_E_CUDA;

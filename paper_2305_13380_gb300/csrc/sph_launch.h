@@ -314,6 +314,10 @@ struct StepArgs {
   double* dt;                   // per simulation
   unsigned* dt_bits;  // per simulation scratch (min of h / v_sig as FP32 bits)
   int32_t* status;
+  // starting guess of the next density loop: h_guess = h (1 + div_v dt / 3)
+  // (nullptr: keep h)
+  float* h_guess = nullptr;
+  const float* div_v = nullptr;
 };
 cudaError_t launch_dt(const StepArgs& a, cudaStream_t st);  // uses a.dt_bits scratch
 cudaError_t launch_kick_drift(const StepArgs& a, cudaStream_t st);

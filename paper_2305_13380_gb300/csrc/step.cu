@@ -87,7 +87,7 @@ __device__ __forceinline__ double wrap1(double x, double L) {
 __global__ void k_kick_drift(sphh::StepArgs a) {
   int cur = -1;
   double dt = 0.0, L = 0.0;
-  float hdt = 0.0f;
+  float hdt = 0.0f, dt3 = 0.0f;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_total;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int s = sim_of_particle(a.sim_offset, a.n_sims, p);
@@ -96,6 +96,7 @@ __global__ void k_kick_drift(sphh::StepArgs a) {
       dt = a.dt[s];
       L = a.box[s];
       hdt = (float)(0.5 * dt);
+      dt3 = (float)(dt / 3.0);
     }
     const float vx = fmaf(hdt, a.ax[p], a.vx[p]);
     const float vy = fmaf(hdt, a.ay[p], a.vy[p]);
@@ -114,6 +115,13 @@ __global__ void k_kick_drift(sphh::StepArgs a) {
     const float up = fmaf(hdt, a.du_dt[p], u);
     a.up[p] = up;
     if (u < 0.0f || up < 0.0f) atomicOr(a.status, SPH_ST_NEG_U);
+    if (a.h_guess != nullptr) {
+      // the smoothing length follows the density, rho ~ h^-3, whose rate is
+      // -rho div v: h (1 + div_v dt / 3) starts the next solve closer to its
+      // root (clamped to [0.8, 1.25]; a NaN rate leaves the factor at 0.8)
+      const float f = fmaf(dt3, a.div_v[p], 1.0f);
+      a.h_guess[p] *= fminf(fmaxf(f, 0.8f), 1.25f);
+    }
   }
 }
 
