@@ -232,3 +232,89 @@ def test_sphenix_step_matches_oracle(orc):
     # alpha_c: the limiter follows the neighbours' alpha_V
     err = np.abs(ac.cpu().numpy() - s["alpha_c"])
     assert err.max() <= 1e-5 + X.alpha_c_max * np.max(lim) / X.alpha_v_max, f"alpha_c: {err.max():.3e}"
+
+
+def test_sphenix_pool_equals_alone(orc):
+    """Three simulations with their own time-steps: each one's SPHENIX steps
+    are bitwise the same alone and inside a pool (the viscosity and
+    conduction updates take each simulation's own dt)."""
+    import torch
+    from paper_2305_13380_gb300 import sph
+    from test_gpu_step import _oracle_state, _pool
+    sims = [inputs.lattice(10, seed=11), inputs.lattice(13, seed=12, sigma_v=0.1),
+            inputs.two_spheres(5, n_max=4e3)]
+    states = [_oracle_state(orc, p) for p in sims]
+    rng = np.random.default_rng(3)
+    for st in states:
+        n = len(st["x"])
+        st["alpha_v"] = _f32(rng.uniform(0.0, 0.5, n))
+        st["alpha_c"] = _f32(rng.uniform(0.0, 0.3, n))
+        st["div_v"] = _f32(rng.normal(0.0, 1.0, n))
+    X = sph.sph_sphenix_default_params()
+
+    def run(sts):
+        off, box, arr = _pool(sts)
+        arr["div_v"] = torch.tensor(np.concatenate([s["div_v"] for s in sts]), device="cuda")
+        av = torch.tensor(np.concatenate([s["alpha_v"] for s in sts]), device="cuda")
+        ac = torch.tensor(np.concatenate([s["alpha_c"] for s in sts]), device="cuda")
+        ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+        for _ in range(3):
+            sph.sph_step_sphenix(ctx, sph.pool(off, box, arr), X, av, ac)
+        out = {k: v.cpu().numpy() for k, v in arr.items()}
+        out["alpha_v"], out["alpha_c"] = av.cpu().numpy(), ac.cpu().numpy()
+        return off.cpu().numpy(), out
+
+    offs, mixed = run(states)
+    dts = set()
+    for i, st in enumerate(states):
+        _, alone = run([st])
+        sl = slice(offs[i], offs[i + 1])
+        for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "rho", "div_v", "ax", "ay", "az", "du_dt",
+                  "v_sig", "alpha_v", "alpha_c"):
+            assert np.array_equal(mixed[k][sl], alone[k]), (i, k)
+        assert mixed["dt"][i] == alone["dt"][0]
+        dts.add(float(alone["dt"][0]))
+    assert len(dts) == 3
+
+
+def test_sphenix_without_time_keeps_the_viscosity_parameters(orc):
+    # dt = 0: alpha_V is unchanged bit for bit; alpha_c only meets its limits
+    p = inputs.lattice(12, seed=5, sigma_v=0.05)
+    q, od, st, _ = _setup(orc, p, seed=4)
+    g = _run_gpu(p, st, 0.0)
+    assert np.array_equal(g["alpha_v"], st["alpha_v"])
+    inside = g["alpha_c"] > 0.0
+    assert np.array_equal(g["alpha_c"][inside], st["alpha_c"][inside])
+
+
+def test_sphenix_with_sorted_interactions_and_wendland(orc):
+    """The SPHENIX loops read the density's lists, so they run unchanged on
+    the axis-sorted filter's lists, and with another kernel."""
+    import torch
+    from paper_2305_13380_gb300 import sph
+    p = inputs.lattice(14, seed=8, sigma_v=0.05)
+    q, _, st, dt = _setup(orc, p, seed=6)
+    for axis, kern in ((True, 0), (False, 2)):
+        flags = sph.SPH_FLAG_SYNC | (sph.SPH_FLAG_AXIS_SORT if axis else 0)
+        ctx = sph.Context(sph.sph_default_params(box_size=float(p["L"]), flags=flags, kernel=kern))
+        t = sph.to_device(p)
+        n = int(t["x"].shape[0])
+        part = sph.particles(t)
+        d, f = sph.alloc_density(n), sph.alloc_force(n)
+        cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], t["h0"])
+        sph.sph_density(ctx, cells, part, t["h0"], sph.density_out(d))
+        dev = {k: torch.tensor(v, device="cuda") for k, v in st.items()}
+        s = sph.sphenix_state(dev["alpha_v"], dev["alpha_c"], dev["div_v_prev"], dev["v_sig"])
+        sph.sph_sphenix_gradient(ctx, cells, part, sph.density_out(d), sph.sph_sphenix_default_params(), dt, s)
+        sph.sph_force_sphenix(ctx, cells, part, sph.density_out(d), dev["alpha_v"], dev["alpha_c"],
+                              sph.force_out(f))
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in d.items()}
+        g.update({k: v.cpu().numpy() for k, v in f.items()})
+        X = orc.Sphenix()
+        phys = orc.Physics(kernel=kern)
+        f64 = {k: v.astype(np.float64) for k, v in st.items()}
+        od, av, og, of = orc.sphenix_evaluate(q, q["h0"], f64["alpha_v"], f64["alpha_c"], f64["div_v_prev"],
+                                              f64["v_sig"], dt, X, phys)
+        compare(g, od, of)
+        assert np.abs(dev["alpha_c"].cpu().numpy() - og["alpha_c"]).max() < 1e-4
