@@ -122,7 +122,7 @@ typedef struct sph_params {
   int32_t flags;       /* SPH_FLAG_*                                              */
   int32_t n_leaf;      /* SPH_FLAG_TREE: a cell with at most n_leaf particles is
                           not split (>= 1)                                        */
-  int32_t kernel;      /* SPH_KERNEL_* (the nested grids take the cubic spline)   */
+  int32_t kernel;      /* SPH_KERNEL_*                                            */
 } sph_params;
 
 /* Opaque context: holds the stream, the parameters and the device scratch

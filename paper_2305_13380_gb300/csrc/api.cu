@@ -338,7 +338,7 @@ bool params_ok(const sph_params& p) {
   return p.box_size > 0 && p.gamma > 1 && p.eta > 0 && p.alpha_v >= 0 && p.beta_v >= 0 &&
          p.eps_balsara > 0 && p.h_tol > 0 && p.cfl > 0 && p.cell_margin >= 0 && p.max_h_iter > 0 &&
          (!(p.flags & SPH_FLAG_TREE) || p.n_leaf >= 1) && p.kernel >= SPH_KERNEL_CUBIC &&
-         p.kernel <= SPH_KERNEL_WENDLAND_C2 && (!(p.flags & SPH_FLAG_TREE) || p.kernel == SPH_KERNEL_CUBIC);
+         p.kernel <= SPH_KERNEL_WENDLAND_C2;
 }
 
 int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const double* box,
@@ -382,6 +382,7 @@ int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const 
   if (sphh::launch_build(b, c->st) != cudaSuccess) return SPH_E_CUDA;
   if (tree) {
     sphh::TreeBuildArgs t;
+    t.gamma_k = (float)sphk::kernel_gamma(c->p.kernel);
     t.n_sims = n_sims;
     t.n_total = n_total;
     t.cap_cells = b.cap_cells;
@@ -427,6 +428,7 @@ int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* 
                     float* h, float* rho, float* f, float* div_v, float* curl_v, float* P, float* cs,
                     float* B, int32_t* n_iter) {
   sphh::TreeGatherArgs g;
+  g.gamma_k = (float)sphk::kernel_gamma(c->p.kernel);
   g.n_total = c->built_n;
   g.n_sims = c->built_sims;
   g.perm = c->perm;

@@ -200,6 +200,7 @@ struct TreeBuildArgs {
   sphk::TreeRange* ranges;    // 27 n: source-order ranges of each group
   int8_t* level;              // n (source order): level of each particle
   float* leaf_side;           // n (source order): cell side of each particle's level
+  float gamma_k = sphk::kGammaK;  // H / h of the kernel
 };
 cudaError_t launch_tree_build(const TreeBuildArgs& a, cudaStream_t st);
 
@@ -218,6 +219,7 @@ struct TreeGatherArgs {
   int4* fine;
   float4 *rel, *vel4;
   float *hs, *lrad;
+  float gamma_k = sphk::kGammaK;  // H / h of the kernel
 };
 cudaError_t launch_tree_gather(const TreeGatherArgs& a, cudaStream_t st);
 

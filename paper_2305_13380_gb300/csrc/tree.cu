@@ -70,14 +70,14 @@ __global__ void k_tree_sorted(int64_t n, const int32_t* __restrict__ perm, const
 // level, level) with a copy for the sort.
 __global__ void k_tree_level(int64_t n, const uint64_t* __restrict__ skey, const int32_t* __restrict__ perm,
                              const float* __restrict__ h, const int32_t* __restrict__ cell_start, int n_sims,
-                             const GridDev* __restrict__ grid, int n_leaf, double margin,
+                             const GridDev* __restrict__ grid, int n_leaf, double margin, float gamma_k,
                              int8_t* __restrict__ level, float* __restrict__ leaf_side,
                              uint64_t* __restrict__ tkey, uint64_t* __restrict__ tkey_copy) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = skey[s];
     const int32_t c = (int32_t)(key >> 30);
     const GridDev G = grid[sim_of_cell(grid, n_sims, c)];
-    const double reach = (1.0 + margin) * (double)(kGammaK * h[perm[s]]);
+    const double reach = (1.0 + margin) * (double)(gamma_k * h[perm[s]]);
     int64_t lo = cell_start[c], hi = cell_start[c + 1];
     int d = 0;
     for (;; ++d) {
@@ -168,7 +168,8 @@ __global__ void k_tree_gather(int64_t n, const int32_t* __restrict__ perm, const
                               const float* __restrict__ m, const float* __restrict__ vx,
                               const float* __restrict__ vy, const float* __restrict__ vz,
                               const float* __restrict__ u, const float* __restrict__ h,
-                              const float* __restrict__ leaf_side, float list_reach, int4* __restrict__ fine,
+                              const float* __restrict__ leaf_side, float list_reach, float gamma_k,
+                              int4* __restrict__ fine,
                               float4* __restrict__ rel, float4* __restrict__ vel4, float* __restrict__ hs,
                               float* __restrict__ lrad) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
@@ -189,7 +190,7 @@ __global__ void k_tree_gather(int64_t n, const int32_t* __restrict__ perm, const
     vel4[s] = make_float4(vx[p], vy[p], vz[p], u[p]);
     const float hp = h[p];
     hs[s] = hp;
-    lrad[s] = fminf(leaf_side[s], list_reach * kGammaK * hp);
+    lrad[s] = fminf(leaf_side[s], list_reach * gamma_k * hp);
   }
 }
 
@@ -219,7 +220,7 @@ cudaError_t launch_tree_build(const TreeBuildArgs& a, cudaStream_t st) {
   k_tree_sorted<<<blocks_n(n), 256, 0, st>>>(n, a.perm, a.key64, a.skey);
   // levels and target order: (top cell, cell at the level, level), ties by source index
   k_tree_level<<<blocks_n(n), 256, 0, st>>>(n, a.skey, a.perm, a.h, a.cell_start, a.n_sims, a.grid, a.n_leaf,
-                                            a.margin, a.level, a.leaf_side, a.key64, a.key64_b);
+                                            a.margin, a.gamma_k, a.level, a.leaf_side, a.key64, a.key64_b);
   e = radix_sort_index64(n, 34 + cbits, a.key64_b, a.key64_c, a.tgt, a.rv, a.hist, st);
   if (e != cudaSuccess) return e;
   k_tree_tsorted<<<blocks_n(n), 256, 0, st>>>(n, a.tgt, a.key64, a.key64_c);
@@ -238,7 +239,7 @@ cudaError_t launch_tree_gather(const TreeGatherArgs& a, cudaStream_t st) {
   if (a.n_total <= 0) return cudaSuccess;
   k_tree_gather<<<blocks_n(a.n_total), 256, 0, st>>>(a.n_total, a.perm, a.skey, a.n_sims, a.grid, a.x, a.y, a.z,
                                                      a.m, a.vx, a.vy, a.vz, a.u, a.h, a.leaf_side, a.list_reach,
-                                                     a.fine, a.rel, a.vel4, a.hs, a.lrad);
+                                                     a.gamma_k, a.fine, a.rel, a.vel4, a.hs, a.lrad);
   return cudaGetLastError();
 }
 

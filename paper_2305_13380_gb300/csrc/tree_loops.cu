@@ -141,13 +141,14 @@ __device__ __forceinline__ void tds_zero(TDSums& s) {
 }
 
 // One density pair with x_ij = (dx, dy, dz) (same terms as density.cu).
+template <int K>
 __device__ __forceinline__ void tdens_pair(float dx, float dy, float dz, const float4& vi, const float4& vj,
                                            float mj, float H, float Hinv, TDSums& s) {
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float q = r2 * rinv * Hinv;
   float w, g;
-  kernel_w_g(q, H * rinv, w, g);
+  kernel_w_g<K>(q, H * rinv, w, g);
   const float dw = fmaf(q * q, g, 3.0f * w);
   s.w += w;
   s.dw += dw;
@@ -163,11 +164,12 @@ __device__ __forceinline__ void tdens_pair(float dx, float dy, float dz, const f
 }
 
 // n-hat and its h-derivative terms of one pair (Newton passes).
+template <int K>
 __device__ __forceinline__ void tnewton_pair(float r2, float H, float Hinv, float& Sw, float& Sdw) {
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float q = r2 * rinv * Hinv;
   float w, dw;
-  kernel_w_dw(q, w, dw);
+  kernel_w_dw<K>(q, w, dw);
   Sw += w;
   Sdw += dw;
 }
@@ -450,10 +452,11 @@ __device__ __forceinline__ void emit_marked(const sphh::TreeDensityArgs& a, uint
 
 // Outputs of target ti (source index) from its sums at h (Sec. 3.1 and the
 // equation of state of Sec. 3.2).
+template <int K>
 __device__ __forceinline__ void tdens_write(const sphh::TreeDensityArgs& a, const PhysDev& ph, int32_t ti,
                                             float h, const TDSums& s, float u_i, int passes, bool noconv) {
   const int32_t p = a.perm[ti];
-  const float H = kGammaK * h;
+  const float H = KernT<K>::gamma * h;
   const float Hinv = 1.0f / H;
   const float H2inv = Hinv * Hinv;
   const float rho = s.mw * H2inv * Hinv;
@@ -475,10 +478,11 @@ __device__ __forceinline__ void tdens_write(const sphh::TreeDensityArgs& a, cons
   if (noconv) atomicOr(a.status, SPH_ST_H_NOCONV);
 }
 
+template <int K>
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const NewtonConst nwt = newton_const(ph);
+  const NewtonConst nwt = newton_const<K>(ph);
   unsigned char* base = tsm + (size_t)warp * kTWarpSmem;
   float4* spos = reinterpret_cast<float4*>(base);
   uint32_t* sidx = reinterpret_cast<uint32_t*>(spos + kTCap);
@@ -495,7 +499,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
     const TGeo g = leaf_geo(Lf, G);
     const TRanges R = load_ranges(a.ranges, li, lane);
     const int nsrc = R.nsrc;
-    const float hcap = h_cap(g.side_d, g.L);
+    const float hcap = h_cap<K>(g.side_d, g.L);
     const bool one_chunk = nsrc <= kTCap;
     // children are half the cell (a cell at the deepest level has one child)
     const float cside = Lf.depth < kTreeDepth ? 0.5f * g.side : g.side;
@@ -553,23 +557,23 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       if (h > hcap) h = hcap;
       {
         // evaluated by every lane (a ballot), then merged
-        const bool outgrown = group_any(valid && kGammaK * h > Ri, lane);
+        const bool outgrown = group_any(valid && KernT<K>::gamma * h > Ri, lane);
         mydirect = mydirect || outgrown;
       }
       float hlo = 0.0f, hhi = INFINITY;
       bool done = !valid, atcap = false, conv = false;
       int it = 0, passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
-        const float H = kGammaK * h;
+        const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
         float Sw = 0.f, Sdw = 0.f;
         if (!mydirect && !done)
-          for (int e = 0; e < cnt; ++e) tnewton_pair(lr2[e * 32 + lane], H, Hinv, Sw, Sdw);
+          for (int e = 0; e < cnt; ++e) tnewton_pair<K>(lr2[e * 32 + lane], H, Hinv, Sw, Sdw);
         if (__any_sync(0xffffffffu, mydirect && !done)) {
           for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
             const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
             if (mydirect && !done)
-              for (int k = sub; k < c; k += kTreeTpp) tnewton_pair(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
+              for (int k = sub; k < c; k += kTreeTpp) tnewton_pair<K>(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
             if (!one_chunk) __syncwarp();
           }
         }
@@ -580,11 +584,11 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           if (newton_update(Sw, Sdw, nwt, hcap, h, hlo, hhi, it, atcap, conv)) done = true;
         }
         // the list holds r < R_i: a support beyond it needs every staged source
-        const bool outgrown = group_any(valid && kGammaK * h > Ri, lane);
+        const bool outgrown = group_any(valid && KernT<K>::gamma * h > Ri, lane);
         mydirect = mydirect || outgrown;
       }
       // 3. final pass at h
-      const float H = kGammaK * h;
+      const float H = KernT<K>::gamma * h;
       const float Hinv = 1.0f / H;
       const float H2 = H * H;
       TDSums s;
@@ -595,7 +599,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           const int32_t j = unpack_j(je);
           const float4 rj = a.rel[j];
           const float3 d = pair_vec(g, reli, fi, rj, a.fine[j], unpack_s(je));
-          tdens_pair(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
+          tdens_pair<K>(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
         }
       }
       // list-free targets: every staged source, reverse pairs on the way
@@ -614,7 +618,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
               if (r2 < H2) {
                 const uint32_t je = sidx[k];
                 const int32_t j = unpack_j(je);
-                tdens_pair(dx, dy, dz, vi, a.vel4[j], pj.w, H, Hinv, s);
+                tdens_pair<K>(dx, dy, dz, vi, a.vel4[j], pj.w, H, Hinv, s);
                 want = !atcap && want_reverse(a, ti, j, r2, H2, H, g.side);
                 rec = reverse_rec(j, ti, unpack_s(je));
               }
@@ -648,7 +652,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         }
       }
       if (valid && sub == 0) {
-        tdens_write(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
+        tdens_write<K>(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
         if (atcap) {
           // the support outgrew this level: re-solved at a coarser one
           const int32_t k = atomicAdd(a.fb_count, 1);
@@ -731,6 +735,7 @@ __device__ __forceinline__ TRec trec_head(const float4* __restrict__ rec, int32_
 }
 
 // One force pair with x_ij = (dx, dy, dz) (same terms as force.cu).
+template <int K>
 __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const float4& vi, const float4& ci,
                                             float Hi, float Hinv_i, float rho_i, const float4& vj,
                                             const float4& cj, float Hj, float Hinv_j, float rho_j,
@@ -739,8 +744,8 @@ __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const 
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float r = r2 * rinv;
   const float hi2 = Hinv_i * Hinv_i, hj2 = Hinv_j * Hinv_j;
-  const float Gi = kernel_g(r * Hinv_i, Hi * rinv) * (hi2 * hi2 * Hinv_i);
-  const float Gj = kernel_g(r * Hinv_j, Hj * rinv) * (hj2 * hj2 * Hinv_j);
+  const float Gi = kernel_g<K>(r * Hinv_i, Hi * rinv) * (hi2 * hi2 * Hinv_i);
+  const float Gj = kernel_g<K>(r * Hinv_j, Hj * rinv) * (hj2 * hj2 * Hinv_j);
   const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
   const float vdotx = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
   const float mu = fminf(vdotx, 0.0f) * rinv;
@@ -761,11 +766,12 @@ __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const 
 }
 
 // tforce_pair with source j's data from its record (head already loaded).
+template <int K>
 __device__ __forceinline__ void tforce_rec(float dx, float dy, float dz, const float4& vi, const float4& ci,
                                            float Hi, float Hinv_i, float rho_i, const float4* __restrict__ rec,
                                            int32_t j, const TRec& h, const PhysDev& ph, TFSums& s) {
   const float4* r = rec + 4 * (int64_t)j;
-  tforce_pair(dx, dy, dz, vi, ci, Hi, Hinv_i, rho_i, r[2], r[3], h.q0.w, __frcp_rn(h.q0.w),
+  tforce_pair<K>(dx, dy, dz, vi, ci, Hi, Hinv_i, rho_i, r[2], r[3], h.q0.w, __frcp_rn(h.q0.w),
               __int_as_float(h.q1.w), ph, s);
 }
 
@@ -773,6 +779,7 @@ __device__ __forceinline__ float3 rec_rel_to(const TGeo& g, const TRec& h, int s
   return rel_to(g, h.q0, h.q1, sc);
 }
 
+template <int K>
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs a, PhysDev ph) {
   const int lane = threadIdx.x & 31;
   const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
@@ -813,7 +820,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
             if (j == ti) continue;
             const TRec hj = trec_head(a.rec, j);
             const float3 d = pair_vec(g, reli, fi, hj.q0, hj.q1, unpack_s(je));
-            tforce_rec(d.x, d.y, d.z, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+            tforce_rec<K>(d.x, d.y, d.z, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
           }
         } else {
           for (int r = 0; r < 27; ++r) {
@@ -824,7 +831,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
               const float3 pj = rec_rel_to(g, hj, Rg.shift);
               const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
               if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
-                tforce_rec(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+                tforce_rec<K>(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
             }
           }
         }
@@ -837,7 +844,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
           const float3 pj = rec_rel_to(g, hj, unpack_s(je));
           const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
           if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
-            tforce_rec(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+            tforce_rec<K>(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
         }
       }
       s.ax = gsum(s.ax);
@@ -909,10 +916,11 @@ __device__ __forceinline__ TRanges cell_ranges(const GridDev& G, const TreeLeaf&
   return R;
 }
 
+template <int K>
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const NewtonConst nwt = newton_const(ph);
+  const NewtonConst nwt = newton_const<K>(ph);
   unsigned char* base = tsm + (size_t)warp * kTWarpSmem;
   float4* spos = reinterpret_cast<float4*>(base);
   uint32_t* sidx = reinterpret_cast<uint32_t*>(spos + kTCap);
@@ -948,7 +956,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
       g = leaf_geo(Lc, G);
       R = cell_ranges(G, Lc, a.skey, a.cell_start, lane);
       pi = rel_to(g, reli, fi, kNoShift);
-      const float hcap = h_cap(g.side_d, g.L);
+      const float hcap = h_cap<K>(g.side_d, g.L);
       one_chunk = R.nsrc <= kTCap;
       if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx);
       float hlo = 0.0f, hhi = INFINITY;
@@ -956,12 +964,12 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
       if (h > hcap) h = hcap;
       bool done = false;
       while (!done) {  // warp-uniform: every lane holds the same reduced sums
-        const float H = kGammaK * h;
+        const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
         float Sw = 0.f, Sdw = 0.f;
         for (int v0 = 0; v0 < R.nsrc; v0 += kTCap) {
           const int c = one_chunk ? R.nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
-          for (int k = lane; k < c; k += 32) tnewton_pair(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
+          for (int k = lane; k < c; k += 32) tnewton_pair<K>(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
           if (!one_chunk) __syncwarp();
         }
         Sw = wsum(Sw);
@@ -977,7 +985,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
       d = 0;
     }
     // final pass at h, reverse pairs of this target
-    const float H = kGammaK * h;
+    const float H = KernT<K>::gamma * h;
     const float Hinv = 1.0f / H;
     const float H2 = H * H;
     TDSums s;
@@ -995,7 +1003,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
           if (r2 < H2) {
             const uint32_t je = sidx[k];
             const int32_t j = unpack_j(je);
-            tdens_pair(dx, dy, dz, vi, a.vel4[j], pj.w, H, Hinv, s);
+            tdens_pair<K>(dx, dy, dz, vi, a.vel4[j], pj.w, H, Hinv, s);
             want = want_reverse(a, ti, j, r2, H2, H, g.side);
             rec = reverse_rec(j, ti, unpack_s(je));
           }
@@ -1014,7 +1022,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     s.cz = wsum(s.cz);
     s.npair = wsumi(s.npair);
     if (lane == 0) {
-      tdens_write(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
+      tdens_write<K>(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
       if (atcap) a.h[a.perm[ti]] = 2.0f * h;  // next starting guess
       a.fb_level[ti] = (int8_t)d;
       pair_acc += (unsigned long long)s.npair;
@@ -1024,6 +1032,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
   if (ph.count_pairs && lane == 0 && pair_acc) atomicAdd(a.pairs, pair_acc);
 }
 
+template <int K>
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceArgs a, PhysDev ph) {
   const int lane = threadIdx.x & 31;
   const int32_t nq = min(*a.fb_count, (int32_t)a.n_total);
@@ -1052,7 +1061,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
         const float3 pj = rec_rel_to(g, hj, Rg.shift);
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
-          tforce_rec(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+          tforce_rec<K>(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
       }
     }
     const int32_t r0 = a.rev_start[ti], r1 = a.rev_start[ti + 1];
@@ -1063,7 +1072,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
       const float3 pj = rec_rel_to(g, hj, unpack_s(je));
       const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
       if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
-        tforce_rec(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+        tforce_rec<K>(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
     }
     s.ax = wsum(s.ax);
     s.ay = wsum(s.ay);
@@ -1095,15 +1104,16 @@ static int tree_blocks(int64_t n) {
   return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
 }
 
-cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cudaStream_t st) {
+template <int K>
+static cudaError_t launch_tree_density_k(const TreeDensityArgs& a, const PhysDev& ph, cudaStream_t st) {
   static int bps = 0;
   if (!bps) {
-    cudaError_t e = cudaFuncSetAttribute(k_tree_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tree_density<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTDensSmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tree_density_fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTDensSmem);
+      e = cudaFuncSetAttribute(k_tree_density_fb<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTDensSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_density, kTWarps * 32, kTDensSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_density<K>, kTWarps * 32, kTDensSmem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
   }
@@ -1116,8 +1126,8 @@ cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cud
   if (e == cudaSuccess) e = cudaMemsetAsync(a.rev_fill, 0, sizeof(int32_t) * (n > 0 ? n : 1), st);
   if (e != cudaSuccess) return e;
   if (n <= 0) return cudaSuccess;
-  k_tree_density<<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
-  k_tree_density_fb<<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
+  k_tree_density<K><<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
+  k_tree_density_fb<K><<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
   e = scan_exclusive_host_n(a.rev_start, n + 1, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
   k_rev_scatter<<<a.num_sms * 4, 256, 0, st>>>(a.rev_raw, a.rev_count, a.rev_cap, a.rev_start, a.rev_fill, a.rev);
@@ -1125,19 +1135,42 @@ cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_tree_force(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+template <int K>
+static cudaError_t launch_tree_force_k(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
   static int bps = 0;
   if (!bps) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_force, kTWarps * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_force<K>, kTWarps * 32, 0);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
   }
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.fb_work, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_tree_force<<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
-  k_tree_force_fb<<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
+  k_tree_force<K><<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
+  k_tree_force_fb<K><<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
   return cudaGetLastError();
+}
+
+cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cudaStream_t st) {
+  switch (ph.kernel) {
+    case kKernQuartic:
+      return launch_tree_density_k<kKernQuartic>(a, ph, st);
+    case kKernWendlandC2:
+      return launch_tree_density_k<kKernWendlandC2>(a, ph, st);
+    default:
+      return launch_tree_density_k<kKernCubic>(a, ph, st);
+  }
+}
+
+cudaError_t launch_tree_force(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+  switch (ph.kernel) {
+    case kKernQuartic:
+      return launch_tree_force_k<kKernQuartic>(a, ph, st);
+    case kKernWendlandC2:
+      return launch_tree_force_k<kKernWendlandC2>(a, ph, st);
+    default:
+      return launch_tree_force_k<kKernCubic>(a, ph, st);
+  }
 }
 
 }  // namespace sphh

@@ -68,7 +68,7 @@ def test_sphenix_defaults_and_argument_checks_without_gpu(libsph):
 def test_kernel_parameter_checked_without_gpu(libsph):
     from paper_2305_13380_gb300 import sph
     h = ctypes.c_void_p()
-    for kw in (dict(kernel=3), dict(kernel=-1), dict(kernel=2, flags=sph.SPH_FLAG_TREE)):
+    for kw in (dict(kernel=3), dict(kernel=-1)):
         p = sph.sph_default_params(**kw)
         assert sph.lib().sph_create(ctypes.byref(h), ctypes.byref(p), None) == sph.SPH_E_INVAL, kw
     assert sph.sph_default_params().kernel == sph.SPH_KERNEL_CUBIC

@@ -1,7 +1,7 @@
 """The quartic spline and the Wendland C2 kernel (Sec. 3.1) on the GPU against
 the oracle: density and force on lattice and clustered inputs, and a step,
-with the kernel selected per context.  The nested grids take the cubic
-spline only."""
+with the kernel selected per context, on the uniform and the nested
+grids."""
 import numpy as np
 import pytest
 
@@ -70,10 +70,29 @@ def test_step(orc, k, name):
         assert np.abs(g[kk] - s[kk]).max() < 1e-4 * arms
 
 
-def test_nested_grids_take_the_cubic_spline_only():
+@pytest.mark.parametrize("k,name", KERNELS)
+def test_nested_grids(orc, k, name):
+    # clustered gas on the nested grids: the plain bounds, no precision floor
+    p = inputs.clustered(6000, n_spheres=8, seed=5)
+    q = as_f32(p)
+    g = run_gpu(p, tree=True, kernel=k)
+    od, of = orc.density_force(q, q["h0"], orc.Physics(kernel=k))
+    compare(g, od, of)
+
+
+@pytest.mark.parametrize("k,name", KERNELS)
+def test_nested_grids_strongly_clustered(orc, k, name):
+    # the densest configuration of the clustered workload (64 spheres)
+    p = inputs.clustered(20000, n_spheres=64, seed=1)
+    q = as_f32(p)
+    g = run_gpu(p, tree=True, kernel=k)
+    od, of = orc.density_force(q, q["h0"], orc.Physics(kernel=k))
+    assert od["h"].max() / od["h"].min() > 50
+    compare(g, od, of)
+
+
+def test_unknown_kernel_rejected():
     from paper_2305_13380_gb300 import sph
     with pytest.raises(sph.SPHError) as e:
-        sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_TREE, kernel=2))
-    assert e.value.code == sph.SPH_E_INVAL
-    with pytest.raises(sph.SPHError):
         sph.Context(sph.sph_default_params(kernel=3))
+    assert e.value.code == sph.SPH_E_INVAL
