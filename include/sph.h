@@ -263,6 +263,23 @@ int sph_density(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in, c
 int sph_force(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
               const sph_density_out* d, sph_force_out* out);
 
+/* The loops on an active subset (Sec. 2.4, the per-particle time-step
+ * hierarchy: only the particles whose step ends are updated, and every other
+ * particle is a neighbour at its drifted position).  active: device uint8,
+ * length n, input order; nonzero marks a particle to update.  Outputs are
+ * written for the active particles only; the others keep their contents.
+ * sph_force_active reads the density results of every particle (the inactive
+ * ones from their last update).  The force reuses the neighbour lists of the
+ * preceding sph_density_active on the same cells when it is given the same
+ * mask pointer (whose contents must not change in between); else it filters
+ * its own.  Uniform grid only (SPH_E_INVAL with SPH_FLAG_TREE).  The outputs
+ * of an active particle equal those of the unmasked loops up to the order of
+ * the FP32 sums (a block deals its active targets to lanes anew). */
+int sph_density_active(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in, const float* h_in,
+                       const uint8_t* active, sph_density_out* out);
+int sph_force_active(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
+                     const sph_density_out* d, const uint8_t* active, sph_force_out* out);
+
 /* One kick-drift-kick step of every simulation of the pool (Sec. 2.4):
  *   dt = C_CFL min_i H_i / v_sig,i per simulation (FP64 reduction),
  *   half kick of v and u, drift of x in FP64 with periodic wrap, prediction

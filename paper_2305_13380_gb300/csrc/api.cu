@@ -61,6 +61,9 @@ struct sph_ctx {
   int4* fine = nullptr;
   float4* rel = nullptr;
   float4* trec = nullptr;  // force records of the nested grids, 4 per particle
+  uint8_t* act_s = nullptr;         // sorted active mask (masked loops)
+  int64_t cap_act = 0;
+  const uint8_t* lists_mask = nullptr;  // the mask the current lists were built with
   float4* sx4 = nullptr;   // SPHENIX: sorted (u, alpha_V, P, alpha_c)
   float* dvp = nullptr;    // SPHENIX step: the divergence of the previous evaluation
   int64_t cap_sx = 0;
@@ -232,6 +235,18 @@ int ensure(sph_ctx* c, int64_t n, int n_sims, int cells_per_particle = 8) {
   c->cap_cells = cc;
   c->lists_valid = false;
   c->built_n = -1;
+  return SPH_OK;
+}
+
+// Sorted active mask of the masked loops, for n particles.
+int ensure_act(sph_ctx* c, int64_t n) {
+  if (n <= c->cap_act) return SPH_OK;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  dfree(c->act_s);
+  c->cap_act = 0;
+  const int64_t cn = n + n / 4 + 64;
+  if (!dalloc(c->act_s, cn)) return SPH_E_NOMEM;
+  c->cap_act = cn;
   return SPH_OK;
 }
 
@@ -513,7 +528,8 @@ int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* 
 int do_density(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
                const float* vy, const float* vz, const float* m, const float* u, const float* h_in,
                float* h, float* rho, float* f, float* div_v, float* curl_v, float* P, float* cs,
-               float* B, int32_t* n_iter) {
+               float* B, int32_t* n_iter, const uint8_t* active = nullptr) {
+  if (c->built_tree && active) return SPH_E_INVAL;  // masked loops run on the uniform grid
   if (c->built_tree)
     return do_tree_density(c, x, y, z, vx, vy, vz, m, u, h_in, h, rho, f, div_v, curl_v, P, cs, B, n_iter);
   sphh::GatherDensityArgs g;
@@ -556,6 +572,12 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
     if (cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
       return SPH_E_CUDA;
   sphh::DensityArgs d;
+  if (active) {
+    const int rc = ensure_act(c, c->built_n);
+    if (rc != SPH_OK) return rc;
+    if (sphh::launch_gather_mask(c->built_n, c->perm, active, c->act_s, c->st) != cudaSuccess) return SPH_E_CUDA;
+    d.act = c->act_s;
+  }
   d.n_sims = c->built_sims;
   d.num_sms = c->num_sms;
   d.grid = c->grid;
@@ -586,6 +608,7 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   const cudaError_t e = sphh::launch_density(d, phys_of(c->p), c->st);
   t_end(c, SPH_T_DENSITY);
   c->lists_valid = (e == cudaSuccess);
+  c->lists_mask = active;
   return cuda_code(e);
 }
 
@@ -622,7 +645,9 @@ struct SphenixCall {
 int do_force(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
              const float* vy, const float* vz, const float* m, const float* h, const float* rho,
              const float* f, const float* P, const float* cs, const float* B, float* ax, float* ay,
-             float* az, float* du_dt, float* v_sig, bool pos_ready = false, const SphenixCall* sx = nullptr) {
+             float* az, float* du_dt, float* v_sig, bool pos_ready = false, const SphenixCall* sx = nullptr,
+             const uint8_t* active = nullptr) {
+  if (active && c->built_tree) return SPH_E_INVAL;  // masked loops run on the uniform grid
   sphh::GatherForceArgs g;
   g.gamma_k = (float)sphk::kernel_gamma(c->p.kernel);
   // the nested-grid force reads positions from its own copies (fA.w only)
@@ -723,8 +748,15 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   a.az = az;
   a.du_dt = du_dt;
   a.v_sig = v_sig;
-  a.lists = c->lists_valid ? c->lists : nullptr;
+  // the density's lists are dealt by the same rounds only under the same mask
+  a.lists = (c->lists_valid && c->lists_mask == active) ? c->lists : nullptr;
   a.list_cnt = c->list_cnt;
+  if (active) {
+    const int rc = ensure_act(c, c->built_n);
+    if (rc != SPH_OK) return rc;
+    if (sphh::launch_gather_mask(c->built_n, c->perm, active, c->act_s, c->st) != cudaSuccess) return SPH_E_CUDA;
+    a.act = c->act_s;
+  }
   t_begin(c, SPH_T_FORCE);
   cudaError_t e;
   if (sx) {
@@ -806,6 +838,7 @@ void sph_destroy(sph_ctx* c) {
   free_tree(c);
   dfree(c->sx4);
   dfree(c->dvp);
+  dfree(c->act_s);
   dfree(c->misc);
   dfree(c->pairs);
   dfree(c->off1);
@@ -1050,6 +1083,34 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
 }
 
 int sph_step(sph_ctx* c, const sph_pool* pl) { return step_impl(c, pl, nullptr, nullptr, nullptr); }
+
+int sph_density_active(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const float* h_in,
+                       const uint8_t* active, sph_density_out* out) {
+  if (!c || !cells || !in || !out || !active) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n == 0) return SPH_OK;
+  if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !in->u || !h_in ||
+      !out->h || !out->rho || !out->f || !out->div_v || !out->curl_v || !out->P || !out->c ||
+      !out->balsara)
+    return SPH_E_INVAL;
+  int rc = do_density(c, in->x, in->y, in->z, in->vx, in->vy, in->vz, in->m, in->u, h_in, out->h, out->rho,
+                      out->f, out->div_v, out->curl_v, out->P, out->c, out->balsara, out->n_iter, active);
+  return rc != SPH_OK ? rc : finish(c);
+}
+
+int sph_force_active(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
+                     const uint8_t* active, sph_force_out* out) {
+  if (!c || !cells || !in || !d || !out || !active) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n == 0) return SPH_OK;
+  if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !d->h || !d->rho ||
+      !d->f || !d->P || !d->c || !d->balsara || !out->ax || !out->ay || !out->az || !out->du_dt ||
+      !out->v_sig)
+    return SPH_E_INVAL;
+  int rc = do_force(c, in->x, in->y, in->z, in->vx, in->vy, in->vz, in->m, d->h, d->rho, d->f, d->P, d->c,
+                    d->balsara, out->ax, out->ay, out->az, out->du_dt, out->v_sig, false, nullptr, active);
+  return rc != SPH_OK ? rc : finish(c);
+}
 
 void sph_sphenix_default_params(sph_sphenix_params* x) {
   if (!x) return;

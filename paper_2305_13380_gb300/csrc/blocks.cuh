@@ -155,6 +155,7 @@ struct BlockTargets {
   int32_t n;              // targets in the block
   int32_t per, tpp, lg, rounds;
   int32_t next;           // next unclaimed round
+  int32_t wcount[kBlkWarps];  // active targets per warp slice (masked builds)
 };
 
 // The round after `rd` for this warp (warp-collective).
@@ -170,10 +171,15 @@ __device__ __forceinline__ int next_round(BlockTargets& B, int lane) {
 // always take 4 lanes: their lists are 1.2-1.4 times longer, and at 2 lanes
 // a few percent of lanes would overflow their list, which sends every warp
 // holding one down the direct path.  The density and the force call this
-// with the same K, so their rounds (and list columns) agree.
+// with the same K (and mask), so their rounds (and list columns) agree.
+//
+// act (sorted order, may be null): only targets with act != 0 are dealt, in
+// the same order; the block's particles are compacted with one ballot per
+// warp and 256 targets at a time.
 template <int K = kKernCubic>
 __device__ __forceinline__ void build_targets(const BlockGeom& g, const StageTable& T, BlockTargets& B,
-                                              uint16_t* tgt_slot, uint8_t* tgt_cell) {
+                                              uint16_t* tgt_slot, uint8_t* tgt_cell,
+                                              const uint8_t* __restrict__ act = nullptr) {
   if (threadIdx.x == 0) {
     int i = 0, run = 0;
     for (int z = 1; z <= g.wz; ++z)
@@ -191,7 +197,48 @@ __device__ __forceinline__ void build_targets(const BlockGeom& g, const StageTab
     }
     B.cell_first[8] = run;
     B.n = run;
-    int per = (run + kBlkWarps - 1) / kBlkWarps;
+  }
+  __syncthreads();
+  const int run = B.cell_first[8];
+  int n = run;
+  if (act == nullptr) {
+    for (int e = threadIdx.x; e < run; e += blockDim.x) {
+      int i = 0;
+      while (i < 7 && B.cell_first[i + 1] <= e) ++i;
+      tgt_slot[e] = (uint16_t)(T.start[B.cell_k[i]] + (e - B.cell_first[i]));
+      tgt_cell[e] = (uint8_t)i;
+    }
+  } else {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    n = 0;
+    for (int e0 = 0; e0 < run; e0 += blockDim.x) {
+      const int e = e0 + threadIdx.x;
+      bool on = false;
+      int i = 0;
+      if (e < run) {
+        while (i < 7 && B.cell_first[i + 1] <= e) ++i;
+        on = act[T.gstart[B.cell_k[i]] + (e - B.cell_first[i])] != 0;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      if (lane == 0) B.wcount[warp] = __popc(m);
+      __syncthreads();
+      int off = n, tot = 0;
+      for (int w = 0; w < kBlkWarps; ++w) {
+        off += w < warp ? B.wcount[w] : 0;
+        tot += B.wcount[w];
+      }
+      if (on) {
+        const int pos = off + __popc(m & ((1u << lane) - 1u));
+        tgt_slot[pos] = (uint16_t)(T.start[B.cell_k[i]] + (e - B.cell_first[i]));
+        tgt_cell[pos] = (uint8_t)i;
+      }
+      n += tot;
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    B.n = n;
+    int per = (n + kBlkWarps - 1) / kBlkWarps;
     per = per < 1 ? 1 : per;
     if (K != kKernCubic && per > 8) per = 8;
     const int tpp = per <= 8 ? 4 : 2;
@@ -199,15 +246,8 @@ __device__ __forceinline__ void build_targets(const BlockGeom& g, const StageTab
     B.per = per;
     B.tpp = tpp;
     B.lg = tpp == 4 ? 2 : 1;
-    B.rounds = (run + per - 1) / per;
+    B.rounds = (n + per - 1) / per;
     B.next = kBlkWarps;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < B.n; e += blockDim.x) {
-    int i = 0;
-    while (i < 7 && B.cell_first[i + 1] <= e) ++i;
-    tgt_slot[e] = (uint16_t)(T.start[B.cell_k[i]] + (e - B.cell_first[i]));
-    tgt_cell[e] = (uint8_t)i;
   }
   __syncthreads();
 }

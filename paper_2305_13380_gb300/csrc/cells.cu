@@ -315,6 +315,13 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
   }
 }
 
+// Sorted copy of an active mask: act_s[s] = active[perm[s]].
+__global__ void k_gather_mask(int64_t n, const int32_t* __restrict__ perm, const uint8_t* __restrict__ active,
+                              uint8_t* __restrict__ act_s) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+    act_s[s] = active[perm[s]];
+}
+
 }  // namespace sphk
 
 // ---- host launchers --------------------------------------------------------
@@ -374,6 +381,13 @@ cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st) {
   kern<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
       a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.h, a.rho,
       a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD, a.rel, a.fine, a.rec, a.gamma_k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* act_s,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_mask<<<grid_for(n, 256, 65535), 256, 0, st>>>(n, perm, active, act_s);
   return cudaGetLastError();
 }
 

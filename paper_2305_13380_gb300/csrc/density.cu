@@ -200,6 +200,12 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       __syncthreads();
       continue;
     }
+    if (a.act != nullptr) {
+      // masked: the block's active targets first, and nothing to stage
+      // when it has none
+      build_targets<K>(g, T, BT, tgt_slot, tgt_cell, a.act);
+      if (BT.n == 0) continue;
+    }
     for (int32_t v = threadIdx.x; v < nsrc; v += kBlkThreads) {
       const int k = staged_cell_of(T, v);
       float ox, oy, oz;
@@ -212,7 +218,10 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       spos[v] = p;
       svel[v] = a.vel4[j];
     }
-    build_targets<K>(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+    if (a.act == nullptr)
+      build_targets<K>(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+    else
+      __syncthreads();  // the staging
 
     const float hcap = h_cap<K>((double)g.G.cell_f, g.G.L);
     const float R2 = g.G.cell_f * g.G.cell_f;
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
     const float hcap = h_cap<K>((double)g.G.cell_f, g.G.L);
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
-      const bool valid = ti < te;
+      const bool valid = ti < te && (a.act == nullptr || a.act[ti] != 0);
       const float4 pi = valid ? a.pos4[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 vi = valid ? a.vel4[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
       float h = valid ? start_h(a.hs[ti], hcap) : hcap;

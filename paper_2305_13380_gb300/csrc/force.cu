@@ -256,7 +256,8 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
     const float dt = kFl == kFlGradient ? block_dt(a, x, b) : 0.0f;
     // the targets' rounds first (they need only the table), so that each
     // warp's first list is in flight together with the staging loads
-    build_targets<K>(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+    build_targets<K>(g, T, BT, tgt_slot, tgt_cell, a.act);  // ends with a barrier
+    if (BT.n == 0) continue;  // a masked block without active targets
     const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
     const int sub = lane & (tpp - 1);
     int pre_lc = 0xffff;
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, 
     };
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
-      const bool valid = ti < te;
+      const bool valid = ti < te && (a.act == nullptr || a.act[ti] != 0);
       const int32_t tl = valid ? ti : ts;
       ForceTarget Tg;
       Tg.A = a.fA[tl];

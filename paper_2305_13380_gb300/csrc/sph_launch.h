@@ -94,6 +94,9 @@ struct GatherForceArgs {
   float gamma_k = sphk::kGammaK;  // H / h of the kernel
 };
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
+// Sorted copy of an active mask (act_s[s] = active[perm[s]]).
+cudaError_t launch_gather_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* act_s,
+                               cudaStream_t st);
 
 // Per-cell orders along the 13 neighbour axes (axis.cu): order[q n + s]
 // for sorted slot s (the density copies pos4 must be current).
@@ -128,6 +131,9 @@ struct DensityArgs {
   // cell along the axis towards it and stops at the search radius
   const uint16_t* axis_order;
   int64_t axis_stride;  // n_total of the orders (one axis after the other)
+  // optional active mask (sorted order): only targets with act != 0 are
+  // computed and written; every particle is a source
+  const uint8_t* act = nullptr;
 };
 cudaError_t launch_density(const DensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 
@@ -150,6 +156,8 @@ struct ForceArgs {
   const float4* fE = nullptr;
   float* alpha_c_out = nullptr;
   float* lap_u = nullptr;
+  // optional active mask (sorted order), as for the density loop
+  const uint8_t* act = nullptr;
 };
 cudaError_t launch_force(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 cudaError_t launch_sphenix_force(const ForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,

@@ -123,6 +123,10 @@ def lib():
         L.sph_force.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
                                 C.POINTER(sph_density_out), C.POINTER(sph_force_out)]
         L.sph_step.argtypes = [_P, C.POINTER(sph_pool)]
+        L.sph_density_active.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles), _P, _P,
+                                         C.POINTER(sph_density_out)]
+        L.sph_force_active.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
+                                       C.POINTER(sph_density_out), _P, C.POINTER(sph_force_out)]
         L.sph_sphenix_default_params.restype = None
         L.sph_sphenix_default_params.argtypes = [C.POINTER(sph_sphenix_params)]
         L.sph_sphenix_gradient.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
@@ -288,6 +292,20 @@ def sph_force(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_den
               out: sph_force_out):
     _check(lib().sph_force(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
                            C.byref(out)), "sph_force")
+
+
+def sph_density_active(ctx: Context, cells: sph_cells, part: sph_particles, h_in, active,
+                       out: sph_density_out):
+    """sph_density on the particles whose uint8 ``active`` entry is nonzero."""
+    _check(lib().sph_density_active(ctx.handle, C.byref(cells), C.byref(part), _ptr(h_in, torch.float32),
+                                    _ptr(active, torch.uint8), C.byref(out)), "sph_density_active")
+
+
+def sph_force_active(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_density_out, active,
+                     out: sph_force_out):
+    """sph_force on the particles whose uint8 ``active`` entry is nonzero."""
+    _check(lib().sph_force_active(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
+                                  _ptr(active, torch.uint8), C.byref(out)), "sph_force_active")
 
 
 def pool(sim_offset, box_size, arrays: dict) -> sph_pool:
