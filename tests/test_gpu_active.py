@@ -31,9 +31,17 @@ def _run(p, masks, same_pointer=True):
     t = sph.to_device(p)
     n = int(t["x"].shape[0])
     part = sph.particles(t)
-    cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], t["h0"])
     d0, f0 = sph.alloc_density(n), sph.alloc_force(n)
-    sph.sph_density(ctx, cells, part, t["h0"], sph.density_out(d0))
+    h_in = t["h0"]
+    for _ in range(8):  # rebuild until every support fits its cell
+        cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], h_in)
+        try:
+            sph.sph_density(ctx, cells, part, h_in, sph.density_out(d0))
+            break
+        except sph.SPHError as e:
+            if e.code != sph.SPH_E_REBUILD:
+                raise
+            h_in = d0["h"].clone()
     sph.sph_force(ctx, cells, part, sph.density_out(d0), sph.force_out(f0))
     base = {k: v.cpu().numpy() for k, v in d0.items()}
     base.update({k: v.cpu().numpy() for k, v in f0.items()})
@@ -44,7 +52,7 @@ def _run(p, masks, same_pointer=True):
         f = {k: torch.full_like(v, SENTINEL) for k, v in f0.items()}
         for k in ("rho", "f", "div_v", "curl_v", "P", "c", "balsara"):
             d[k][torch.tensor(m, device="cuda")] = SENTINEL
-        sph.sph_density_active(ctx, cells, part, t["h0"], act, sph.density_out(d))
+        sph.sph_density_active(ctx, cells, part, h_in, act, sph.density_out(d))
         act_f = act if same_pointer else act.clone()
         sph.sph_force_active(ctx, cells, part, sph.density_out(d), act_f, sph.force_out(f))
         torch.cuda.synchronize()
