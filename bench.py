@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=sorted(KERNELS), default="cubic",
                     help="latticeN / clusteredN: smoothing kernel")
+    ap.add_argument("--active", type=float, default=0.0,
+                    help="latticeN: time the loops on an active subset of this fraction (a "
+                         "spherical region) against the full loops, instead of the step")
     ap.add_argument("--sphenix", action="store_true",
                     help="latticeN: the SPHENIX flavour (time-dependent viscosity, conduction)")
     ap.add_argument("--axis-sort", action="store_true",
@@ -625,10 +628,90 @@ def main():
         run_fof(args, world, rank, local)
     elif args.workload.startswith("served"):
         run_served(args, world, rank, local)
+    elif args.active > 0.0:
+        run_active(args, world, rank, local)
     else:
         run_step(args, world, rank, local)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_active(args, world: int, rank: int, local: int):
+    """The density and force loops on an active subset (the particles of a
+    spherical region holding the fraction args.active of the box), against the
+    full loops on the same cells: what a step of the time-step hierarchy
+    costs when only those particles' steps end."""
+    import numpy as np
+    import torch
+    from paper_2305_13380_gb300 import build as B
+    B.build()
+    from paper_2305_13380_gb300 import replicas, sph
+
+    p = make_workload(args.workload)
+    if p["tree"]:
+        raise SystemExit("the masked loops run on the uniform grid (latticeN workloads)")
+    n, L = len(p["x"]), float(p["L"])
+    c0 = np.full(3, 0.5 * L)
+    d = [(np.asarray(p[k]) - c0[i] + 0.5 * L) % L - 0.5 * L for i, k in enumerate("xyz")]
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    mask = r < np.quantile(r, args.active)
+    n_act = int(mask.sum())
+    t = sph.to_device(p)
+    act = torch.tensor(mask.astype(np.uint8), device="cuda")
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC))
+    part = sph.particles(t)
+    dd, ff = sph.alloc_density(n), sph.alloc_force(n)
+    cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], t["h0"])
+    sph.sph_density(ctx, cells, part, t["h0"], sph.density_out(dd))
+    sph.sph_force(ctx, cells, part, sph.density_out(dd), sph.force_out(ff))
+    ctx.close()
+    ctx = sph.Context(sph.sph_default_params(box_size=L))
+    cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], dd["h"])
+    dout, fout = sph.density_out(dd), sph.force_out(ff)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        replicas.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def full():
+        sph.sph_density(ctx, cells, part, dd["h"], dout)
+        sph.sph_force(ctx, cells, part, dout, fout)
+
+    def masked():
+        sph.sph_density_active(ctx, cells, part, dd["h"], act, dout)
+        sph.sph_force_active(ctx, cells, part, dout, act, fout)
+
+    clocks = Clocks(None)
+    ms_full = timed(full)
+    ms_act = timed(masked)
+    clk = clocks.stop()
+    if sph.sph_status(ctx):
+        raise SystemExit("device status set in the masked loops")
+    value, ms = replicas.job_throughput(n_act, ms_act)
+    line = {
+        "metric": "SPH density+force active-particle updates/s (time-step hierarchy subset)",
+        "value": value, "unit": "particle-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": p["desc"], "particles": n, "active": n_act,
+                   "active_fraction": n_act / n, "subset": "a central sphere",
+                   "step": "sph_density_active + sph_force_active on fixed cells"},
+        "full_loops_ms": ms_full, "masked_over_full_time": ms_act / ms_full,
+        "gpu_launches": 8 * args.steps,  # per iteration: two gathers + mask + loop + overflow loop, twice
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+    }
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def run_step(args, world: int, rank: int, local: int):
