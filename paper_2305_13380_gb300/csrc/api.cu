@@ -62,7 +62,8 @@ struct sph_ctx {
   float4* rel = nullptr;
   float4* trec = nullptr;  // force records of the nested grids, 4 per particle
   uint8_t* act_s = nullptr;         // sorted active mask (masked loops)
-  int64_t cap_act = 0;
+  uint8_t* blk_any = nullptr;       // blocks holding an active particle
+  int64_t cap_act = 0, cap_blk = 0;
   const uint8_t* lists_mask = nullptr;  // the mask the current lists were built with
   float4* sx4 = nullptr;   // SPHENIX: sorted (u, alpha_V, P, alpha_c)
   float* dvp = nullptr;    // SPHENIX step: the divergence of the previous evaluation
@@ -239,14 +240,21 @@ int ensure(sph_ctx* c, int64_t n, int n_sims, int cells_per_particle = 8) {
 }
 
 // Sorted active mask of the masked loops, for n particles.
+// The block flags are sized by the cell capacity (at least one cell per block).
 int ensure_act(sph_ctx* c, int64_t n) {
-  if (n <= c->cap_act) return SPH_OK;
+  if (n <= c->cap_act && c->cap_cells <= c->cap_blk) return SPH_OK;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
   dfree(c->act_s);
-  c->cap_act = 0;
+  dfree(c->blk_any);
+  c->cap_act = c->cap_blk = 0;
   const int64_t cn = n + n / 4 + 64;
-  if (!dalloc(c->act_s, cn)) return SPH_E_NOMEM;
+  if (!dalloc(c->act_s, cn) || !dalloc(c->blk_any, c->cap_cells + 1)) {
+    dfree(c->act_s);
+    dfree(c->blk_any);
+    return SPH_E_NOMEM;
+  }
   c->cap_act = cn;
+  c->cap_blk = c->cap_cells;
   return SPH_OK;
 }
 
@@ -575,8 +583,11 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   if (active) {
     const int rc = ensure_act(c, c->built_n);
     if (rc != SPH_OK) return rc;
-    if (sphh::launch_gather_mask(c->built_n, c->perm, active, c->act_s, c->st) != cudaSuccess) return SPH_E_CUDA;
+    if (sphh::launch_gather_mask(c->built_n, c->perm, c->key, c->grid, active, c->act_s, c->blk_any, c->cap_blk,
+                                 c->st) != cudaSuccess)
+      return SPH_E_CUDA;
     d.act = c->act_s;
+    d.blk_any = c->blk_any;
   }
   d.n_sims = c->built_sims;
   d.num_sms = c->num_sms;
@@ -754,8 +765,11 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   if (active) {
     const int rc = ensure_act(c, c->built_n);
     if (rc != SPH_OK) return rc;
-    if (sphh::launch_gather_mask(c->built_n, c->perm, active, c->act_s, c->st) != cudaSuccess) return SPH_E_CUDA;
+    if (sphh::launch_gather_mask(c->built_n, c->perm, c->key, c->grid, active, c->act_s, c->blk_any, c->cap_blk,
+                                 c->st) != cudaSuccess)
+      return SPH_E_CUDA;
     a.act = c->act_s;
+    a.blk_any = c->blk_any;
   }
   t_begin(c, SPH_T_FORCE);
   cudaError_t e;
@@ -839,6 +853,7 @@ void sph_destroy(sph_ctx* c) {
   dfree(c->sx4);
   dfree(c->dvp);
   dfree(c->act_s);
+  dfree(c->blk_any);
   dfree(c->misc);
   dfree(c->pairs);
   dfree(c->off1);

@@ -315,11 +315,23 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
   }
 }
 
-// Sorted copy of an active mask: act_s[s] = active[perm[s]].
-__global__ void k_gather_mask(int64_t n, const int32_t* __restrict__ perm, const uint8_t* __restrict__ active,
-                              uint8_t* __restrict__ act_s) {
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
-    act_s[s] = active[perm[s]];
+// Sorted copy of an active mask, act_s[s] = active[perm[s]], and the
+// 2x2x2-cell blocks (of simulation 0) that hold an active particle.
+__global__ void k_gather_mask(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ key,
+                              const GridDev* __restrict__ grid, const uint8_t* __restrict__ active,
+                              uint8_t* __restrict__ act_s, uint8_t* __restrict__ blk_any) {
+  const GridDev G = grid[0];
+  const int32_t nc = G.n_c, nb = (nc + 1) >> 1;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = perm[s];
+    const uint8_t on = active[p];
+    act_s[s] = on;
+    if (on) {
+      const int32_t c = key[p] - G.cell_base;
+      const int32_t kx = c % nc, ky = (c / nc) % nc, kz = c / (nc * nc);
+      blk_any[G.blk_base + (kx >> 1) + nb * ((ky >> 1) + nb * (kz >> 1))] = 1;
+    }
+  }
 }
 
 }  // namespace sphk
@@ -384,10 +396,13 @@ cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* act_s,
+cudaError_t launch_gather_mask(int64_t n, const int32_t* perm, const int32_t* key, const GridDev* grid,
+                               const uint8_t* active, uint8_t* act_s, uint8_t* blk_any, int64_t blk_cap,
                                cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_gather_mask<<<grid_for(n, 256, 65535), 256, 0, st>>>(n, perm, active, act_s);
+  cudaError_t e = cudaMemsetAsync(blk_any, 0, (size_t)blk_cap, st);
+  if (e != cudaSuccess) return e;
+  k_gather_mask<<<grid_for(n, 256, 65535), 256, 0, st>>>(n, perm, key, grid, active, act_s, blk_any);
   return cudaGetLastError();
 }
 

@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
   unsigned long long pair_acc = 0;
 
   for (int32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    if (a.blk_any != nullptr && a.blk_any[b] == 0) continue;  // no active target
     const BlockGeom g = block_geom(a.grid, a.n_sims, b);
     const int32_t nsrc = build_stage_table(g, a.cell_start, T);
     if (nsrc > dens_cap<K>()) {

@@ -94,8 +94,11 @@ struct GatherForceArgs {
   float gamma_k = sphk::kGammaK;  // H / h of the kernel
 };
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
-// Sorted copy of an active mask (act_s[s] = active[perm[s]]).
-cudaError_t launch_gather_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* act_s,
+// Sorted copy of an active mask (act_s[s] = active[perm[s]]) and the flags
+// of the blocks holding an active particle (blk_any, blk_cap bytes cleared
+// first; one simulation).
+cudaError_t launch_gather_mask(int64_t n, const int32_t* perm, const int32_t* key, const sphk::GridDev* grid,
+                               const uint8_t* active, uint8_t* act_s, uint8_t* blk_any, int64_t blk_cap,
                                cudaStream_t st);
 
 // Per-cell orders along the 13 neighbour axes (axis.cu): order[q n + s]
@@ -132,8 +135,10 @@ struct DensityArgs {
   const uint16_t* axis_order;
   int64_t axis_stride;  // n_total of the orders (one axis after the other)
   // optional active mask (sorted order): only targets with act != 0 are
-  // computed and written; every particle is a source
+  // computed and written; every particle is a source.  blk_any flags the
+  // blocks with an active target (the others are skipped at once)
   const uint8_t* act = nullptr;
+  const uint8_t* blk_any = nullptr;
 };
 cudaError_t launch_density(const DensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 
@@ -156,8 +161,9 @@ struct ForceArgs {
   const float4* fE = nullptr;
   float* alpha_c_out = nullptr;
   float* lap_u = nullptr;
-  // optional active mask (sorted order), as for the density loop
+  // optional active mask (sorted order) and block flags, as for the density loop
   const uint8_t* act = nullptr;
+  const uint8_t* blk_any = nullptr;
 };
 cudaError_t launch_force(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 cudaError_t launch_sphenix_force(const ForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,
