@@ -665,7 +665,7 @@ def run_active(args, world: int, rank: int, local: int):
     sph.sph_density(ctx, cells, part, t["h0"], sph.density_out(dd))
     sph.sph_force(ctx, cells, part, sph.density_out(dd), sph.force_out(ff))
     ctx.close()
-    ctx = sph.Context(sph.sph_default_params(box_size=L))
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING))
     cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], dd["h"])
     dout, fout = sph.density_out(dd), sph.force_out(ff)
     stream = torch.cuda.current_stream()
@@ -692,9 +692,13 @@ def run_active(args, world: int, rank: int, local: int):
         sph.sph_force_active(ctx, cells, part, dout, act, fout)
 
     clocks = Clocks(None)
+    sph.sph_kernel_times(ctx)  # reset
     ms_full = timed(full)
+    kt_full = sph.sph_kernel_times(ctx)
     ms_act = timed(masked)
+    kt_act = sph.sph_kernel_times(ctx)
     clk = clocks.stop()
+    per = args.steps + args.warmup
     if sph.sph_status(ctx):
         raise SystemExit("device status set in the masked loops")
     value, ms = replicas.job_throughput(n_act, ms_act)
@@ -707,6 +711,8 @@ def run_active(args, world: int, rank: int, local: int):
                    "active_fraction": n_act / n, "subset": "a central sphere",
                    "step": "sph_density_active + sph_force_active on fixed cells"},
         "full_loops_ms": ms_full, "masked_over_full_time": ms_act / ms_full,
+        "breakdown_ms": {"full": {k: v[0] / per for k, v in kt_full.items()},
+                         "masked": {k: v[0] / per for k, v in kt_act.items()}},
         "gpu_launches": 8 * args.steps,  # per iteration: two gathers + mask + loop + overflow loop, twice
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }
