@@ -40,8 +40,22 @@ template <int K>
 __host__ __device__ constexpr int dens_cap() {
   return stage_cap<K>();
 }
-constexpr int kListCap = kLaneListCap;     // list entries per lane
-constexpr int kListRows = kListCap + 1;    // + one scratch row for the branch-free append
+// List entries per lane.  The cubic spline's rounds give a target two lanes
+// (above 8 targets a round), each holding ~28 candidates at 13 particles per
+// cell, but ~33 when the largest h makes cells 5 % wider (15 per cell): 56
+// entries keep such lanes from overflowing into the direct path (which every
+// warp holding one would then take), and still fit three blocks per SM.  The
+// wider kernels always take four lanes per target.  Lists longer than the
+// force's region (kListRegion) are not published: the force filters those
+// lanes itself.
+template <int K>
+__host__ __device__ constexpr int list_cap() {
+  return K == kKernCubic ? 56 : kLaneListCap;
+}
+template <int K>
+__host__ __device__ constexpr int list_rows() {  // + one scratch row for the branch-free append
+  return list_cap<K>() + 1;
+}
 // The list keeps each entry's r^2 for the Newton passes (kCacheR2), or only
 // the slot, the passes then recomputing r^2 from the staged position.  The
 // slots alone leave room for three resident blocks per SM instead of two
@@ -55,7 +69,7 @@ constexpr int kDensMinBlocks = 3;  // resident blocks per SM the registers are s
 template <int K>
 __host__ __device__ constexpr size_t dens_blk_smem() {
   return (size_t)dens_cap<K>() * 2 * sizeof(float4) +
-                                (size_t)kBlkWarps * kListRows * 32 *
+                                (size_t)kBlkWarps * list_rows<K>() * 32 *
                                     ((kCacheR2 ? sizeof(float) : 0) + sizeof(uint16_t)) +
                                 sizeof(StageTable) + sizeof(BlockTargets) +
                                 (size_t)dens_cap<K>() * (sizeof(uint16_t) + sizeof(uint8_t));
@@ -180,14 +194,14 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
   float4* svel = spos + dens_cap<K>();
   // per-lane list entries (r^2, staged slot), column layout [entry][lane]
   float* lr2_all = reinterpret_cast<float*>(svel + dens_cap<K>());
-  uint16_t* lj_all = reinterpret_cast<uint16_t*>(lr2_all + (kCacheR2 ? kBlkWarps * kListRows * 32 : 0));
-  StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * kListRows * 32);
+  uint16_t* lj_all = reinterpret_cast<uint16_t*>(lr2_all + (kCacheR2 ? kBlkWarps * list_rows<K>() * 32 : 0));
+  StageTable& T = *reinterpret_cast<StageTable*>(lj_all + kBlkWarps * list_rows<K>() * 32);
   BlockTargets& BT = *reinterpret_cast<BlockTargets*>(&T + 1);
   uint16_t* tgt_slot = reinterpret_cast<uint16_t*>(&BT + 1);
   uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + dens_cap<K>());
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* lr2 = lr2_all + warp * (kListRows * 32);
-  uint16_t* lj = lj_all + warp * (kListRows * 32);
+  float* lr2 = lr2_all + warp * (list_rows<K>() * 32);
+  uint16_t* lj = lj_all + warp * (list_rows<K>() * 32);
   const int32_t total = a.misc_ro[kTotalBlocks];
   const NewtonConst nwt = newton_const<K>(ph);
   unsigned long long pair_acc = 0;
@@ -261,7 +275,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
               const float4 pj = spos[s0 + r];
               const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
               const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const int at = min(cnt, kListCap) * 32 + lane;
+              const int at = min(cnt, list_cap<K>()) * 32 + lane;
               if (kCacheR2) lr2[at] = r2;
               lj[at] = (uint16_t)(s0 + r);
               cnt += r2 < R2;
@@ -282,7 +296,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
             if (sf * axis_proj(pj.x, pj.y, pj.z, q) - p_i >= bound) break;
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const int at = min(cnt, kListCap) * 32 + lane;
+            const int at = min(cnt, list_cap<K>()) * 32 + lane;
             if (kCacheR2) lr2[at] = r2;
             lj[at] = (uint16_t)kk;
             cnt += r2 < R2;
@@ -300,15 +314,15 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             // branch-free append: the entry is written at the current end and
             // kept only if in range; once the list is full, writes go to the
-            // scratch row kListCap (such a lane takes the direct path)
-            const int at = min(cnt, kListCap) * 32 + lane;
+            // scratch row list_cap<K>() (such a lane takes the direct path)
+            const int at = min(cnt, list_cap<K>()) * 32 + lane;
             if (kCacheR2) lr2[at] = r2;
             lj[at] = (uint16_t)k;
             cnt += r2 < R2;
           }
         }
       }
-      bool direct = cnt > kListCap;
+      bool direct = cnt > list_cap<K>();
       if (a.axis_order != nullptr) {
         // the sorted walk splits a target's sources between its lanes by rank
         // along each axis, the direct walk by position in the runs: a target
@@ -321,18 +335,26 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       }
       // publish the list for the force loop of this build: 16-byte vectors
       // into this lane's region (the force loop rebuilds the same rounds)
+      bool pub = valid && !direct && cnt <= kListRegion;
+      if (a.axis_order != nullptr) {
+        // the force's own filter splits by run position: under the sorted
+        // walk a target's lanes are published all together or not at all
+        const unsigned m = __ballot_sync(0xffffffffu, valid && !pub);
+        const unsigned grp = ((1u << tpp) - 1u) << (lane & ~(tpp - 1));
+        pub = pub && (m & grp) == 0u;
+      }
       if (a.lists != nullptr && valid) {
         const int64_t col = (int64_t)ti * 4 + sub;
-        a.list_cnt[col] = (uint16_t)(direct ? 0xffff : cnt);
-        if (!direct) {
+        a.list_cnt[col] = (uint16_t)(pub ? cnt : 0xffff);
+        if (pub) {
           uint4* dst = reinterpret_cast<uint4*>(a.lists + col * kListRegion);
           for (int e8 = 0; e8 < cnt; e8 += 8) {
             uint32_t w[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int e0 = e8 + 2 * q, e1 = e0 + 1;
-              const uint32_t lo = e0 < kListCap ? lj[e0 * 32 + lane] : 0u;
-              const uint32_t hi = e1 < kListCap ? lj[e1 * 32 + lane] : 0u;
+              const uint32_t lo = e0 < list_cap<K>() ? lj[e0 * 32 + lane] : 0u;
+              const uint32_t hi = e1 < list_cap<K>() ? lj[e1 * 32 + lane] : 0u;
               w[q] = lo | (hi << 16);
             }
             dst[e8 >> 3] = make_uint4(w[0], w[1], w[2], w[3]);
