@@ -880,7 +880,8 @@ def run_step(args, world: int, rank: int, local: int):
     roofline = {"bound": "alu", "kernel": kfull, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_measured_fma": fma_peak, "frac_of_measured": achieved / fma_peak,
-                "traffic": _traffic(kfull[2:], "tree_loops" if tree else kname),
+                # the records hold the cubic-spline instances' counters
+                "traffic": _traffic(kfull[2:], "tree_loops" if tree else kname) if kern == 0 else None,
                 "peak_basis": (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                f"lanes x 2 flop x {peak_mhz:.0f} MHz (derived; no measured FP32 "
                                "peak in MEASURED_PEAKS.json)"),
