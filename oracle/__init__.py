@@ -451,3 +451,45 @@ def sphenix_step(s: dict, cfl: float, X: Sphenix = Sphenix(), phys: Physics = Ph
         s["v" + k] = s["v" + k] + 0.5 * dt * s["a" + k]
     s["u"] = s["u"] + 0.5 * dt * s["du_dt"]
     return dt
+
+
+def time_bins(h, v_sig, cfl: float, dt_max: float, max_bin: int, kernel: int = 0):
+    """Per-particle time bins of the power-of-two time-step hierarchy (Sec. 2.4,
+    "Local time-step optimisations"): the CFL step dt_i = C_CFL gamma_K h_i / v_sig,i,
+    and bin_i = the smallest b in [0, max_bin] with dt_max 2^-b <= dt_i (max_bin if
+    none; bin 0 where v_sig <= 0).  The bin is an integer decided by floating point, so it is
+    taken in FP32, the precision of the library's kernel: c = fl32(C_CFL gamma_K),
+    dt_i = fl32(fl32(c h_i) / v_sig,i), compared with fl32(dt_max) scaled by 2^-b
+    (exact)."""
+    h = np.asarray(h, dtype=np.float32)
+    v = np.asarray(v_sig, dtype=np.float32)
+    c = np.float32(cfl * gamma_k(kernel))
+    with np.errstate(divide="ignore"):
+        dt = np.where(v > 0, (c * h) / np.where(v > 0, v, np.float32(1)), np.float32(np.inf)).astype(np.float32)
+    top = np.float32(dt_max)
+    bins = np.full(h.shape, max_bin, dtype=np.int32)
+    for b in range(max_bin, -1, -1):
+        step = np.float32(np.ldexp(top, -b))
+        bins = np.where(step <= dt, b, bins)
+    return bins
+
+
+def limit_time_bins(p: dict, h, bins, kernel: int = 0):
+    """The first time-step limiter (Sec. 3.4, "Time-step limiter", Delta = 4):
+    a particle's step is at most 4 times the smallest step of the particles it
+    interacts with in the force loop (j != i, r_ij < max(H_i, H_j)), i.e.
+    bin_i <- max(bin_i, max_j bin_j - 2), applied once.  Brute force over all
+    pairs with minimum-image distances (small inputs)."""
+    x = np.stack([np.asarray(p[k], dtype=np.float64) for k in ("x", "y", "z")], 1)
+    L = float(p["L"])
+    H = gamma_k(kernel) * np.asarray(h, dtype=np.float64)
+    bins = np.asarray(bins, dtype=np.int32)
+    out = bins.copy()
+    for i in range(len(bins)):
+        d = x - x[i]
+        d -= L * np.round(d / L)
+        r = np.sqrt((d * d).sum(1))
+        nb = (r < np.maximum(H, H[i])) & (np.arange(len(bins)) != i)
+        if nb.any():
+            out[i] = max(bins[i], int(bins[nb].max()) - 2)
+    return out
