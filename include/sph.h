@@ -280,6 +280,25 @@ int sph_density_active(sph_ctx* ctx, const sph_cells* cells, const sph_particles
 int sph_force_active(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
                      const sph_density_out* d, const uint8_t* active, sph_force_out* out);
 
+/* Time bins of the power-of-two time-step hierarchy (Sec. 2.4) with the first
+ * time-step limiter (the SPH section's "Time-step limiter", Delta = 4), on the
+ * cells of the last build (uniform grid; SPH_E_INVAL with SPH_FLAG_TREE):
+ *   dt_i  = C_CFL gamma_K h_i / v_sig,i        (FP32: fl(fl(c h_i) / v_sig,i),
+ *                                               c = fl(C_CFL gamma_K))
+ *   bin_i = smallest b in [0, max_bin] with dt_max 2^-b <= dt_i (max_bin if
+ *           none; 0 where v_sig <= 0), i.e. a step dt_max 2^-bin_i <= dt_i;
+ *   bin_i = max(bin_i, max_j bin_j - 2) over the force pairs j != i with
+ *           r_ij < max(H_i, H_j), applied once (a step at most 4 times the
+ *           smallest neighbour step).
+ *   d       density results of every particle (h, and the force records)
+ *   v_sig   device float, n: signal velocities (from sph_force)
+ *   cfl > 0, dt_max > 0, 0 <= max_bin <= 62
+ *   bins    device int32, n, input order: written
+ * The limiter is a neighbour pass over the lists of the preceding density
+ * (the force loop's template with a one-line pair function). */
+int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
+                  const float* v_sig, double cfl, double dt_max, int32_t max_bin, int32_t* bins);
+
 /* One kick-drift-kick step of every simulation of the pool (Sec. 2.4):
  *   dt = C_CFL min_i H_i / v_sig,i per simulation (FP64 reduction),
  *   half kick of v and u, drift of x in FP64 with periodic wrap, prediction

@@ -474,12 +474,13 @@ def time_bins(h, v_sig, cfl: float, dt_max: float, max_bin: int, kernel: int = 0
     return bins
 
 
-def limit_time_bins(p: dict, h, bins, kernel: int = 0):
+def limit_time_bins(p: dict, h, bins, kernel: int = 0, scale: float = 1.0):
     """The first time-step limiter (Sec. 3.4, "Time-step limiter", Delta = 4):
     a particle's step is at most 4 times the smallest step of the particles it
     interacts with in the force loop (j != i, r_ij < max(H_i, H_j)), i.e.
     bin_i <- max(bin_i, max_j bin_j - 2), applied once.  Brute force over all
-    pairs with minimum-image distances (small inputs)."""
+    pairs with minimum-image distances (small inputs).  scale multiplies the
+    interaction radius (tests use 1 +- 1e-5 to bound pairs at the edge)."""
     x = np.stack([np.asarray(p[k], dtype=np.float64) for k in ("x", "y", "z")], 1)
     L = float(p["L"])
     H = gamma_k(kernel) * np.asarray(h, dtype=np.float64)
@@ -489,7 +490,7 @@ def limit_time_bins(p: dict, h, bins, kernel: int = 0):
         d = x - x[i]
         d -= L * np.round(d / L)
         r = np.sqrt((d * d).sum(1))
-        nb = (r < np.maximum(H, H[i])) & (np.arange(len(bins)) != i)
+        nb = (r < scale * np.maximum(H, H[i])) & (np.arange(len(bins)) != i)
         if nb.any():
             out[i] = max(bins[i], int(bins[nb].max()) - 2)
     return out

@@ -648,6 +648,10 @@ sphk::SphenixDev sphenix_dev(const sph_sphenix_params& x, double dt, const doubl
 struct SphenixCall {
   bool gradient = false;
   bool skip_gather = false;
+  // the time-step limiter pass instead (bins_in gathered as the E records)
+  bool limit = false;
+  const int32_t* bins_in = nullptr;
+  int32_t* bins_out = nullptr;
   const float *u = nullptr, *alpha_v = nullptr, *alpha_c = nullptr;
   float *alpha_c_out = nullptr, *lap_u = nullptr;
   sphk::SphenixDev x;
@@ -692,8 +696,11 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   }
   t_begin(c, SPH_T_GATHER);
   if (!(sx && sx->skip_gather) && sphh::launch_gather_force(g, c->st) != cudaSuccess) return SPH_E_CUDA;
-  if (sx && sphh::launch_gather_sphenix(c->built_n, c->perm, sx->u, sx->alpha_v, P, sx->alpha_c, c->sx4,
-                                        c->st) != cudaSuccess)
+  if (sx && !sx->limit &&
+      sphh::launch_gather_sphenix(c->built_n, c->perm, sx->u, sx->alpha_v, P, sx->alpha_c, c->sx4, c->st) !=
+          cudaSuccess)
+    return SPH_E_CUDA;
+  if (sx && sx->limit && sphh::launch_gather_bins(c->built_n, c->perm, sx->bins_in, c->sx4, c->st) != cudaSuccess)
     return SPH_E_CUDA;
   t_end(c, SPH_T_GATHER);
   if (sx && c->built_tree) return SPH_E_INVAL;  // SPHENIX runs on the uniform grid only
@@ -773,7 +780,12 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   }
   t_begin(c, SPH_T_FORCE);
   cudaError_t e;
-  if (sx) {
+  if (sx && sx->limit) {
+    a.fE = c->sx4;
+    a.pairs = nullptr;
+    a.bins_out = sx->bins_out;
+    e = sphh::launch_limit_bins(a, phys_of(c->p), c->st);
+  } else if (sx) {
     a.fE = c->sx4;
     if (sx->gradient) {
       a.pairs = nullptr;
@@ -1098,6 +1110,31 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
 }
 
 int sph_step(sph_ctx* c, const sph_pool* pl) { return step_impl(c, pl, nullptr, nullptr, nullptr); }
+
+int sph_time_bins(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
+                  const float* v_sig, double cfl, double dt_max, int32_t max_bin, int32_t* bins) {
+  if (!c || !cells || !in || !d || !v_sig || !bins) return SPH_E_INVAL;
+  if (!(cfl > 0.0) || !std::isfinite(cfl) || !(dt_max > 0.0) || !std::isfinite(dt_max) || max_bin < 0 ||
+      max_bin > 62)
+    return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n == 0) return SPH_OK;
+  if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !d->h || !d->rho || !d->f ||
+      !d->P || !d->c || !d->balsara)
+    return SPH_E_INVAL;
+  int rc = ensure_sphenix(c, in->n);
+  if (rc != SPH_OK) return rc;
+  const float cf = (float)(cfl * sphk::kernel_gamma(c->p.kernel));
+  if (sphh::launch_time_bins(in->n, d->h, v_sig, cf, (float)dt_max, max_bin, bins, c->st) != cudaSuccess)
+    return SPH_E_CUDA;
+  SphenixCall L;
+  L.limit = true;
+  L.bins_in = bins;
+  L.bins_out = bins;
+  rc = do_force(c, in->x, in->y, in->z, in->vx, in->vy, in->vz, in->m, d->h, d->rho, d->f, d->P, d->c,
+                d->balsara, nullptr, nullptr, nullptr, nullptr, nullptr, false, &L);
+  return rc != SPH_OK ? rc : finish(c);
+}
 
 int sph_density_active(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const float* h_in,
                        const uint8_t* active, sph_density_out* out) {

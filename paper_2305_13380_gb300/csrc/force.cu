@@ -40,7 +40,7 @@
 
 namespace sphk {
 
-enum : int { kFlMinimal = 0, kFlSphenix = 1, kFlGradient = 2 };
+enum : int { kFlMinimal = 0, kFlSphenix = 1, kFlGradient = 2, kFlLimit = 3 };
 
 template <int kFl, int K>
 __host__ __device__ constexpr int force_cap() {
@@ -87,6 +87,12 @@ template <int kFl, int K>
 __device__ __forceinline__ void force_pair(const ForceTarget& T, const float4& Aj, const float4& Bj,
                                            const float4& Cj, const float2& Dj, const float4& Ej,
                                            const PhysDev& ph, bool counted, ForceSums& s) {
+  if constexpr (kFl == kFlLimit) {
+    // the first time-step limiter: the largest bin among the force pairs
+    s.vsig = counted ? fmaxf(s.vsig, Ej.x) : s.vsig;
+    s.npair += counted;
+    return;
+  }
   const float dx = T.A.x - Aj.x, dy = T.A.y - Aj.y, dz = T.A.z - Aj.z;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
@@ -148,6 +154,15 @@ __device__ __forceinline__ void gradient_write(const sphh::ForceArgs& a, const S
   an = fmaxf(an, x.ac_min);
   a.alpha_c_out[p] = an;
   if (a.lap_u != nullptr) a.lap_u[p] = lap;
+}
+
+// The limiter's result: a step at most 4 times the smallest neighbour step,
+// i.e. at most two bins below the largest neighbour bin (the sums' v_sig
+// field holds that largest bin).
+__device__ __forceinline__ void limit_write(const sphh::ForceArgs& a, int32_t ti, const ForceTarget& T,
+                                            const ForceSums& s) {
+  const int own = (int)T.E.x, nb = (int)s.vsig - 2;
+  a.bins_out[a.perm[ti]] = own > nb ? own : nb;
 }
 
 __device__ __forceinline__ float block_dt(const sphh::ForceArgs& a, const SphenixDev& x, int32_t b) {
@@ -390,6 +405,8 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
       if (valid && sub == 0) {
         if (kFl == kFlGradient)
           gradient_write(a, x, dt, ti, Tg, s0);
+        else if (kFl == kFlLimit)
+          limit_write(a, ti, Tg, s0);
         else
           force_write(a, ti, s0);
         pair_acc += (unsigned long long)s0.npair;
@@ -482,6 +499,8 @@ __global__ void __launch_bounds__(kThreads) k_force_overflow(sphh::ForceArgs a, 
       if (valid) {
         if (kFl == kFlGradient)
           gradient_write(a, x, dt, ti, Tg, s);
+        else if (kFl == kFlLimit)
+          limit_write(a, ti, Tg, s);
         else
           force_write(a, ti, s);
         pair_acc += (unsigned long long)s.npair;
@@ -543,6 +562,11 @@ cudaError_t launch_force(const ForceArgs& a, const PhysDev& ph, cudaStream_t st)
 cudaError_t launch_sphenix_force(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
   if (a.fE == nullptr) return cudaErrorInvalidValue;
   return launch_force_fl<kFlSphenix>(a, ph, x, st);
+}
+
+cudaError_t launch_limit_bins(const ForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+  if (a.fE == nullptr || a.bins_out == nullptr) return cudaErrorInvalidValue;
+  return launch_force_fl<kFlLimit>(a, ph, SphenixDev{}, st);
 }
 
 cudaError_t launch_sphenix_gradient(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {

@@ -164,12 +164,22 @@ struct ForceArgs {
   // optional active mask (sorted order) and block flags, as for the density loop
   const uint8_t* act = nullptr;
   const uint8_t* blk_any = nullptr;
+  // time-step limiter pass: bins_out[p] = max(own bin, largest neighbour bin - 2)
+  // (the bins come sorted in fE.x)
+  int32_t* bins_out = nullptr;
 };
 cudaError_t launch_force(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 cudaError_t launch_sphenix_force(const ForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,
                                  cudaStream_t st);
 cudaError_t launch_sphenix_gradient(const ForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,
                                     cudaStream_t st);
+cudaError_t launch_limit_bins(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+
+// Time bins (timebins.cu): the CFL bins of n particles (input order), and the
+// sorted limiter records E[s].x = bin of perm[s].
+cudaError_t launch_time_bins(int64_t n, const float* h, const float* v_sig, float c, float dt_max, int max_bin,
+                             int32_t* bins, cudaStream_t st);
+cudaError_t launch_gather_bins(int64_t n, const int32_t* perm, const int32_t* bins, float4* fE, cudaStream_t st);
 
 // SPHENIX per-particle steps (sphenix.cu).  The viscosity update of every
 // particle (input order): alpha_v in/out, div_v_prev in (the divergence of the

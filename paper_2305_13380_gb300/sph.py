@@ -123,6 +123,8 @@ def lib():
         L.sph_force.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
                                 C.POINTER(sph_density_out), C.POINTER(sph_force_out)]
         L.sph_step.argtypes = [_P, C.POINTER(sph_pool)]
+        L.sph_time_bins.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
+                                    C.POINTER(sph_density_out), _P, C.c_double, C.c_double, C.c_int32, _P]
         L.sph_density_active.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles), _P, _P,
                                          C.POINTER(sph_density_out)]
         L.sph_force_active.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
@@ -292,6 +294,14 @@ def sph_force(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_den
               out: sph_force_out):
     _check(lib().sph_force(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
                            C.byref(out)), "sph_force")
+
+
+def sph_time_bins(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_density_out, v_sig,
+                  cfl: float, dt_max: float, max_bin: int, bins):
+    """Time bins with the first limiter into ``bins`` (int32 CUDA tensor)."""
+    _check(lib().sph_time_bins(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
+                               _ptr(v_sig, torch.float32), C.c_double(cfl), C.c_double(dt_max),
+                               C.c_int32(max_bin), _ptr(bins, torch.int32)), "sph_time_bins")
 
 
 def sph_density_active(ctx: Context, cells: sph_cells, part: sph_particles, h_in, active,
