@@ -691,12 +691,18 @@ def run_active(args, world: int, rank: int, local: int):
         sph.sph_density_active(ctx, cells, part, dd["h"], act, dout)
         sph.sph_force_active(ctx, cells, part, dout, act, fout)
 
+    bins = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def binning():  # CFL bins of every particle + the limiter's neighbour pass
+        sph.sph_time_bins(ctx, cells, part, dout, ff["v_sig"], 0.1, 1.0, 30, bins)
+
     clocks = Clocks(None)
     sph.sph_kernel_times(ctx)  # reset
     ms_full = timed(full)
     kt_full = sph.sph_kernel_times(ctx)
     ms_act = timed(masked)
     kt_act = sph.sph_kernel_times(ctx)
+    ms_bins = timed(binning)
     clk = clocks.stop()
     per = args.steps + args.warmup
     if sph.sph_status(ctx):
@@ -711,6 +717,7 @@ def run_active(args, world: int, rank: int, local: int):
                    "active_fraction": n_act / n, "subset": "a central sphere",
                    "step": "sph_density_active + sph_force_active on fixed cells"},
         "full_loops_ms": ms_full, "masked_over_full_time": ms_act / ms_full,
+        "time_bins_ms": ms_bins,
         "breakdown_ms": {"full": {k: v[0] / per for k, v in kt_full.items()},
                          "masked": {k: v[0] / per for k, v in kt_act.items()}},
         "gpu_launches": 8 * args.steps,  # per iteration: two gathers + mask + loop + overflow loop, twice
