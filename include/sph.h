@@ -299,6 +299,29 @@ int sph_force_active(sph_ctx* ctx, const sph_cells* cells, const sph_particles* 
 int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
                   const float* v_sig, double cfl, double dt_max, int32_t max_bin, int32_t* bins);
 
+/* One sub-step of the power-of-two time-step hierarchy (Sec. 2.4, "Local
+ * time-step optimisations") for a single simulation (pool with n_sims = 1,
+ * uniform grid).  Time runs on integer ticks, tau = dt_max / 2^max_bin each; a
+ * particle in bin b takes steps of 2^(max_bin - b) ticks starting at
+ * t_begin[i] (a multiple of that length).  In this mode the pool's vx, vy, vz
+ * and u are the particle's half-kicked values for its current step, and its
+ * a, du/dt, v_sig and density results are those of its last evaluation.  The
+ * call:
+ *   t_next = min_i (t_begin_i + step_i)                  (returned, host)
+ *   every particle drifts from t_now to t_next; the loops see the predicted
+ *   v_half + a (t_next - t_begin - step/2) tau (u alike);
+ *   the particles whose step ends at t_next are active: the cells are rebuilt,
+ *   the density and force run for them (sph_density_active / sph_force_active),
+ *   then each gets the second half kick over its old step, a new bin (with
+ *   adapt: that of sph_time_bins with params.cfl, else its old bin; in both
+ *   cases shortened until the new step divides t_next), the first half kick
+ *   over its new step, and t_begin = t_next.
+ * bins (int32) and t_begin (int64) are device arrays of n, updated in place;
+ * 0 <= max_bin <= 40.  With SPH_FLAG_SYNC a density that needs larger cells is
+ * rebuilt and repeated.  Waits for the stream (it returns t_next). */
+int sph_hier_substep(sph_ctx* ctx, const sph_pool* pool, int32_t* bins, int64_t* t_begin, double dt_max,
+                     int32_t max_bin, int64_t t_now, int32_t adapt, int64_t* t_next_out);
+
 /* One kick-drift-kick step of every simulation of the pool (Sec. 2.4):
  *   dt = C_CFL min_i H_i / v_sig,i per simulation (FP64 reduction),
  *   half kick of v and u, drift of x in FP64 with periodic wrap, prediction

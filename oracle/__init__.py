@@ -494,3 +494,54 @@ def limit_time_bins(p: dict, h, bins, kernel: int = 0, scale: float = 1.0):
         if nb.any():
             out[i] = max(bins[i], int(bins[nb].max()) - 2)
     return out
+
+
+def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int, adapt: bool,
+                 cfl: float = 0.1, phys: Physics = Physics()) -> int:
+    """One sub-step of the power-of-two time-step hierarchy (Sec. 2.4), in place
+    on the state dict s (float64 arrays: x, y, z, vx, vy, vz and u half-kicked
+    for each particle's current step, m, h, ax, ay, az, du_dt, v_sig, the
+    density results rho, f, P, c, B, div_v; and L) and on bins / t_begin
+    (integer arrays).  Time runs on ticks of dt_max 2^-max_bin; a particle in
+    bin b steps 2^(max_bin - b) ticks.  Every particle drifts to the next end
+    of a step; the particles whose step ends there (the active ones) get the
+    density and the force at the predicted v and u of every particle, their
+    second half kick, a new bin (adapt: the limited CFL bin; else the old one;
+    shortened until the new step divides the tick) and the first half kick of
+    the new step.  Returns the new tick."""
+    n = len(bins)
+    step = np.left_shift(np.int64(1), (max_bin - bins).astype(np.int64))
+    tau = float(np.ldexp(dt_max, -max_bin))
+    t_next = int(np.min(t_begin + step))
+    dt = (t_next - t_now) * tau
+    wrap = lib().oracle_wrap
+    L = float(s["L"])
+    for k in ("x", "y", "z"):
+        s[k] = np.array([wrap(float(q), L) for q in s[k] + s["v" + k] * dt])
+    w = ((t_next - t_begin) - 0.5 * step) * tau
+    pred = dict(L=L, x=s["x"], y=s["y"], z=s["z"], m=s["m"], vx=s["vx"] + s["ax"] * w,
+                vy=s["vy"] + s["ay"] * w, vz=s["vz"] + s["az"] * w, u=s["u"] + s["du_dt"] * w)
+    act = np.where(t_begin + step == t_next)[0]
+    d = density(pred, s["h"], act, phys)
+    for k in ("h", "rho", "f", "P", "c", "B", "div_v"):
+        s[k][act] = d[k]
+    f = force(pred, s, act, phys)
+    for k in ("ax", "ay", "az", "du_dt", "v_sig"):
+        s[k][act] = f[k]
+    if adapt:
+        b0 = time_bins(s["h"], s["v_sig"], cfl, dt_max, max_bin, phys.kernel)
+        new = limit_time_bins(pred, s["h"], b0, phys.kernel)[act]
+    else:
+        new = bins[act].copy()
+    new = np.clip(new, 0, max_bin)
+    for q, i in enumerate(act):
+        b = int(new[q])
+        while b < max_bin and t_next % (1 << (max_bin - b)) != 0:
+            b += 1
+        h_old, h_new = 0.5 * step[i] * tau, 0.5 * (1 << (max_bin - b)) * tau
+        for k in ("x", "y", "z"):
+            s["v" + k][i] += s["a" + k][i] * (h_old + h_new)
+        s["u"][i] += s["du_dt"][i] * (h_old + h_new)
+        bins[i] = b
+        t_begin[i] = t_next
+    return t_next

@@ -65,6 +65,10 @@ struct sph_ctx {
   uint8_t* blk_any = nullptr;       // blocks holding an active particle
   int64_t cap_act = 0, cap_blk = 0;
   const uint8_t* lists_mask = nullptr;  // the mask the current lists were built with
+  uint8_t* hact = nullptr;   // time-step hierarchy: active mask (input order)
+  int32_t* hbin = nullptr;   // proposed bins
+  unsigned long long* htick = nullptr;
+  int64_t cap_hier = 0;
   float4* sx4 = nullptr;   // SPHENIX: sorted (u, alpha_V, P, alpha_c)
   float* dvp = nullptr;    // SPHENIX step: the divergence of the previous evaluation
   int64_t cap_sx = 0;
@@ -239,6 +243,25 @@ int ensure(sph_ctx* c, int64_t n, int n_sims, int cells_per_particle = 8) {
   return SPH_OK;
 }
 
+// Scratch of the time-step hierarchy's sub-steps for n particles.
+int ensure_hier(sph_ctx* c, int64_t n) {
+  if (n <= c->cap_hier) return SPH_OK;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  dfree(c->hact);
+  dfree(c->hbin);
+  dfree(c->htick);
+  c->cap_hier = 0;
+  const int64_t cn = n + n / 4 + 64;
+  if (!(dalloc(c->hact, cn) && dalloc(c->hbin, cn) && dalloc(c->htick, 1))) {
+    dfree(c->hact);
+    dfree(c->hbin);
+    dfree(c->htick);
+    return SPH_E_NOMEM;
+  }
+  c->cap_hier = cn;
+  return SPH_OK;
+}
+
 // Sorted active mask of the masked loops, for n particles.
 // The block flags are sized by the cell capacity (at least one cell per block).
 int ensure_act(sph_ctx* c, int64_t n) {
@@ -246,6 +269,9 @@ int ensure_act(sph_ctx* c, int64_t n) {
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
   dfree(c->act_s);
   dfree(c->blk_any);
+  dfree(c->hact);
+  dfree(c->hbin);
+  dfree(c->htick);
   c->cap_act = c->cap_blk = 0;
   const int64_t cn = n + n / 4 + 64;
   if (!dalloc(c->act_s, cn) || !dalloc(c->blk_any, c->cap_cells + 1)) {
@@ -1134,6 +1160,104 @@ int sph_time_bins(sph_ctx* c, const sph_cells* cells, const sph_particles* in, c
   rc = do_force(c, in->x, in->y, in->z, in->vx, in->vy, in->vz, in->m, d->h, d->rho, d->f, d->P, d->c,
                 d->balsara, nullptr, nullptr, nullptr, nullptr, nullptr, false, &L);
   return rc != SPH_OK ? rc : finish(c);
+}
+
+int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, double dt_max,
+                     int32_t max_bin, int64_t t_now, int32_t adapt, int64_t* t_next_out) {
+  if (!c || !pl || !bins || !tbeg || !t_next_out || pl->n_sims != 1 || pl->n_total < 1 ||
+      pl->n_total > INT32_MAX / 16 || !(dt_max > 0.0) || !std::isfinite(dt_max) || max_bin < 0 || max_bin > 40 ||
+      t_now < 0)
+    return SPH_E_INVAL;
+  if (!pl->sim_offset || !pl->box_size || !pl->x || !pl->y || !pl->z || !pl->vx || !pl->vy || !pl->vz ||
+      !pl->u || !pl->m || !pl->h || !pl->ax || !pl->ay || !pl->az || !pl->du_dt || !pl->v_sig || !pl->rho ||
+      !pl->f || !pl->div_v || !pl->curl_v || !pl->P || !pl->c || !pl->balsara)
+    return SPH_E_INVAL;
+  if (c->p.flags & SPH_FLAG_TREE) return SPH_E_INVAL;  // masked loops run on the uniform grid
+  const int64_t n = pl->n_total;
+  int rc = ensure(c, n, 1);
+  if (rc == SPH_OK) rc = ensure_hier(c, n);
+  if (rc == SPH_OK && adapt) rc = ensure_sphenix(c, n);
+  if (rc != SPH_OK) return rc;
+  double box = 0.0;
+  if (cudaMemcpyAsync(&box, pl->box_size, sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return SPH_E_CUDA;
+  sphh::HierArgs h;
+  h.n = n;
+  h.max_bin = max_bin;
+  h.t_now = t_now;
+  h.tau = std::ldexp(dt_max, -max_bin);
+  h.box = box;
+  h.x = pl->x;
+  h.y = pl->y;
+  h.z = pl->z;
+  h.vx = pl->vx;
+  h.vy = pl->vy;
+  h.vz = pl->vz;
+  h.u = pl->u;
+  h.ax = pl->ax;
+  h.ay = pl->ay;
+  h.az = pl->az;
+  h.du_dt = pl->du_dt;
+  h.vpx = c->vpx;
+  h.vpy = c->vpy;
+  h.vpz = c->vpz;
+  h.up = c->up;
+  h.bin = bins;
+  h.t_begin = tbeg;
+  h.bin_new = nullptr;
+  h.act = c->hact;
+  h.t_next = c->htick;
+  h.status = c->misc + sphk::kStatus;
+  t_begin(c, SPH_T_INTEGRATE);
+  if (sphh::launch_hier_next(h, c->st) != cudaSuccess || sphh::launch_hier_drift(h, c->st) != cudaSuccess)
+    return SPH_E_CUDA;
+  t_end(c, SPH_T_INTEGRATE);
+  const bool sync = (c->p.flags & SPH_FLAG_SYNC) != 0;
+  for (int attempt = 0;; ++attempt) {
+    rc = do_build(c, 1, n, pl->sim_offset, pl->box_size, pl->x, pl->y, pl->z, pl->h);
+    if (rc != SPH_OK) return rc;
+    rc = do_density(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, c->up, pl->h, pl->h, pl->rho, pl->f,
+                    pl->div_v, pl->curl_v, pl->P, pl->c, pl->balsara, pl->n_iter, c->hact);
+    if (rc != SPH_OK) return rc;
+    if (!sync) break;
+    int32_t st = 0;
+    rc = read_status(c, &st);
+    if (rc != SPH_OK) return rc;
+    if (!(st & SPH_ST_REBUILD) || attempt >= 8) {
+      const int code = code_of_status(st);
+      if (code != SPH_OK) return code;
+      break;
+    }
+  }
+  rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P, pl->c,
+                pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig, true, nullptr, c->hact);
+  if (rc != SPH_OK) return rc;
+  if (adapt) {
+    // proposed bins of the active particles: CFL bins, then the limiter over
+    // the force pairs (the masked pass reuses the density's lists)
+    const float cf = (float)(c->p.cfl * sphk::kernel_gamma(c->p.kernel));
+    if (sphh::launch_time_bins(n, pl->h, pl->v_sig, cf, (float)dt_max, max_bin, c->hbin, c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+    SphenixCall L;
+    L.limit = true;
+    L.skip_gather = true;
+    L.bins_in = c->hbin;
+    L.bins_out = c->hbin;
+    rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P, pl->c,
+                  pl->balsara, nullptr, nullptr, nullptr, nullptr, nullptr, true, &L, c->hact);
+    if (rc != SPH_OK) return rc;
+    h.bin_new = c->hbin;
+  }
+  t_begin(c, SPH_T_INTEGRATE);
+  if (sphh::launch_hier_kick(h, c->st) != cudaSuccess) return SPH_E_CUDA;
+  t_end(c, SPH_T_INTEGRATE);
+  unsigned long long tn = 0;
+  if (cudaMemcpyAsync(&tn, c->htick, sizeof(tn), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return SPH_E_CUDA;
+  *t_next_out = (int64_t)tn;
+  return finish(c);
 }
 
 int sph_density_active(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const float* h_in,

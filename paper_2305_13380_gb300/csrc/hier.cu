@@ -1,0 +1,116 @@
+// hier.cu -- sub-steps of the power-of-two time-step hierarchy (Sec. 2.4,
+// "Local time-step optimisations"): an integer timeline of 2^max_bin ticks per
+// dt_max; a particle in bin b takes steps of 2^(max_bin - b) ticks, aligned to
+// multiples of that length.  Each particle runs its own kick-drift-kick: its
+// velocity and energy are kept half-kicked for the current step, every
+// particle drifts with it, and at the end of its step it gets the second half
+// kick with the new acceleration, a new bin, and the first half kick of the
+// next step.
+#include "sph_internal.cuh"
+#include "sph_launch.h"
+
+namespace sphk {
+
+__device__ __forceinline__ int64_t step_ticks(int32_t bin, int max_bin) { return (int64_t)1 << (max_bin - bin); }
+
+// The next tick at which some particle's step ends.
+__global__ void k_hier_next(int64_t n, const int32_t* __restrict__ bin, const int64_t* __restrict__ t_begin,
+                            int max_bin, unsigned long long* __restrict__ t_next) {
+  unsigned long long m = ~0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long e = (unsigned long long)(t_begin[i] + step_ticks(bin[i], max_bin));
+    m = e < m ? e : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v < m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m != ~0ull) atomicMin(t_next, m);
+}
+
+// Drift of every particle from t_now to t_next (FP64 positions, one periodic
+// wrap), the velocity and energy predicted at t_next for the loops,
+// v(t) = v_half + a (t - t_begin - step/2) tau, and the active mask: the
+// particles whose step ends at t_next.
+__global__ void k_hier_drift(sphh::HierArgs a) {
+  const int64_t tn = (int64_t)*a.t_next;
+  const double dt = (double)(tn - a.t_now) * a.tau;
+  const double L = a.box;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = step_ticks(a.bin[i], a.max_bin);
+    double x = fma((double)a.vx[i], dt, a.x[i]), y = fma((double)a.vy[i], dt, a.y[i]),
+           z = fma((double)a.vz[i], dt, a.z[i]);
+    x = x < 0.0 ? x + L : x;
+    x = x >= L ? x - L : x;
+    y = y < 0.0 ? y + L : y;
+    y = y >= L ? y - L : y;
+    z = z < 0.0 ? z + L : z;
+    z = z >= L ? z - L : z;
+    a.x[i] = x;
+    a.y[i] = y;
+    a.z[i] = z;
+    const float w = (float)(((double)(tn - a.t_begin[i]) - 0.5 * (double)s) * a.tau);
+    a.vpx[i] = fmaf(a.ax[i], w, a.vx[i]);
+    a.vpy[i] = fmaf(a.ay[i], w, a.vy[i]);
+    a.vpz[i] = fmaf(a.az[i], w, a.vz[i]);
+    a.up[i] = fmaf(a.du_dt[i], w, a.u[i]);
+    a.act[i] = (uint8_t)(a.t_begin[i] + s == tn);
+  }
+}
+
+// The end of an active particle's step: second half kick over the old step,
+// the new bin (the proposed one, shortened until the new step is aligned with
+// t_next), first half kick over the new step.
+__global__ void k_hier_kick(sphh::HierArgs a) {
+  const int64_t tn = (int64_t)*a.t_next;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!a.act[i]) continue;
+    const float h_old = (float)(0.5 * (double)step_ticks(a.bin[i], a.max_bin) * a.tau);
+    int32_t b = a.bin_new != nullptr ? a.bin_new[i] : a.bin[i];
+    b = b < 0 ? 0 : (b > a.max_bin ? a.max_bin : b);
+    while (b < a.max_bin && tn % step_ticks(b, a.max_bin) != 0) ++b;
+    const float h_new = (float)(0.5 * (double)step_ticks(b, a.max_bin) * a.tau);
+    const float vx = fmaf(a.ax[i], h_old, a.vx[i]), vy = fmaf(a.ay[i], h_old, a.vy[i]),
+                vz = fmaf(a.az[i], h_old, a.vz[i]), u = fmaf(a.du_dt[i], h_old, a.u[i]);
+    a.vx[i] = fmaf(a.ax[i], h_new, vx);
+    a.vy[i] = fmaf(a.ay[i], h_new, vy);
+    a.vz[i] = fmaf(a.az[i], h_new, vz);
+    const float un = fmaf(a.du_dt[i], h_new, u);
+    a.u[i] = un;
+    if (u < 0.0f || un < 0.0f) atomicOr(a.status, SPH_ST_NEG_U);
+    a.bin[i] = b;
+    a.t_begin[i] = tn;
+  }
+}
+
+}  // namespace sphk
+
+namespace sphh {
+using namespace sphk;
+
+static int grid_h(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+cudaError_t launch_hier_next(const HierArgs& a, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.t_next, 0xff, sizeof(unsigned long long), st);
+  if (e != cudaSuccess || a.n <= 0) return e;
+  k_hier_next<<<grid_h(a.n), 256, 0, st>>>(a.n, a.bin, a.t_begin, a.max_bin, a.t_next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hier_drift(const HierArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  k_hier_drift<<<grid_h(a.n), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hier_kick(const HierArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  k_hier_kick<<<grid_h(a.n), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sphh

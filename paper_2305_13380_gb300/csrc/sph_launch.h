@@ -175,6 +175,28 @@ cudaError_t launch_sphenix_gradient(const ForceArgs& a, const sphk::PhysDev& ph,
                                     cudaStream_t st);
 cudaError_t launch_limit_bins(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 
+// Sub-steps of the time-step hierarchy (hier.cu), one simulation of side box.
+struct HierArgs {
+  int64_t n;
+  int max_bin;
+  int64_t t_now;
+  double tau;  // dt_max / 2^max_bin
+  double box;
+  double *x, *y, *z;
+  float *vx, *vy, *vz, *u;            // half-kicked for the current step
+  const float *ax, *ay, *az, *du_dt;  // last force of each particle
+  float *vpx, *vpy, *vpz, *up;        // predicted at t_next (scratch)
+  int32_t* bin;
+  int64_t* t_begin;
+  const int32_t* bin_new;  // proposed bins (nullptr: keep)
+  uint8_t* act;            // active mask (scratch, input order)
+  unsigned long long* t_next;
+  int32_t* status;
+};
+cudaError_t launch_hier_next(const HierArgs& a, cudaStream_t st);
+cudaError_t launch_hier_drift(const HierArgs& a, cudaStream_t st);
+cudaError_t launch_hier_kick(const HierArgs& a, cudaStream_t st);
+
 // Time bins (timebins.cu): the CFL bins of n particles (input order), and the
 // sorted limiter records E[s].x = bin of perm[s].
 cudaError_t launch_time_bins(int64_t n, const float* h, const float* v_sig, float c, float dt_max, int max_bin,

@@ -123,6 +123,8 @@ def lib():
         L.sph_force.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
                                 C.POINTER(sph_density_out), C.POINTER(sph_force_out)]
         L.sph_step.argtypes = [_P, C.POINTER(sph_pool)]
+        L.sph_hier_substep.argtypes = [_P, C.POINTER(sph_pool), _P, _P, C.c_double, C.c_int32, C.c_int64,
+                                       C.c_int32, C.POINTER(C.c_int64)]
         L.sph_time_bins.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
                                     C.POINTER(sph_density_out), _P, C.c_double, C.c_double, C.c_int32, _P]
         L.sph_density_active.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles), _P, _P,
@@ -294,6 +296,16 @@ def sph_force(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_den
               out: sph_force_out):
     _check(lib().sph_force(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
                            C.byref(out)), "sph_force")
+
+
+def sph_hier_substep(ctx: Context, pl: sph_pool, bins, t_begin, dt_max: float, max_bin: int, t_now: int,
+                     adapt: bool = True) -> int:
+    """One sub-step of the time-step hierarchy; returns the new tick."""
+    t_next = C.c_int64(0)
+    _check(lib().sph_hier_substep(ctx.handle, C.byref(pl), _ptr(bins, torch.int32), _ptr(t_begin, torch.int64),
+                                  C.c_double(dt_max), C.c_int32(max_bin), C.c_int64(t_now), C.c_int32(1 if adapt else 0),
+                                  C.byref(t_next)), "sph_hier_substep")
+    return int(t_next.value)
 
 
 def sph_time_bins(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_density_out, v_sig,

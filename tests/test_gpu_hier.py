@@ -1,0 +1,119 @@
+"""Sub-steps of the time-step hierarchy (sph_hier_substep) on the GPU against
+the oracle's: fixed bins over several sub-steps, and adaptive bins."""
+import numpy as np
+import pytest
+
+from gpu_common import as_f32
+
+from paper_2305_13380_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    from paper_2305_13380_gb300 import build
+    build.build()
+
+
+def _state(orc, seed):
+    p = inputs.lattice(12, seed=seed, sigma_v=0.05)
+    q = as_f32(p)
+    d, f = orc.density_force(q, q["h0"])
+    s = {k: q[k].copy() for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u")}
+    s.update(L=float(p["L"]), h=d["h"].copy(), ax=f["ax"].copy(), ay=f["ay"].copy(), az=f["az"].copy(),
+             du_dt=f["du_dt"].copy(), v_sig=f["v_sig"].copy())
+    for k in ("rho", "f", "P", "c", "B", "div_v"):
+        s[k] = d[k].copy()
+    return s
+
+
+def _start(s, bins, dt_max, max_bin):
+    """Half kicks of the first steps, in FP32 as the GPU holds them."""
+    dt_i = np.ldexp(dt_max, -max_bin) * 2.0 ** (max_bin - bins)
+    for k in ("x", "y", "z"):
+        s["v" + k] = (s["v" + k] + s["a" + k] * 0.5 * dt_i).astype(np.float32).astype(np.float64)
+    s["u"] = (s["u"] + s["du_dt"] * 0.5 * dt_i).astype(np.float32).astype(np.float64)
+
+
+def _pool(s):
+    import torch
+    from paper_2305_13380_gb300 import sph
+    dev = "cuda"
+    arr = {k: torch.tensor(s[k], dtype=torch.float64, device=dev) for k in ("x", "y", "z")}
+    for k in ("vx", "vy", "vz", "u", "m", "h", "ax", "ay", "az", "du_dt", "v_sig", "rho", "f", "div_v", "P", "c"):
+        arr[k] = torch.tensor(s[k], dtype=torch.float32, device=dev)
+    arr["balsara"] = torch.tensor(s["B"], dtype=torch.float32, device=dev)
+    arr["curl_v"] = torch.zeros_like(arr["h"])
+    arr["dt"] = torch.zeros(1, dtype=torch.float64, device=dev)
+    n = len(s["x"])
+    off = torch.tensor([0, n], dtype=torch.int64, device=dev)
+    box = torch.tensor([s["L"]], dtype=torch.float64, device=dev)
+    return arr, sph.pool(off, box, arr)
+
+
+def _compare(g, s, d):
+    for k in ("x", "y", "z"):
+        diff = np.abs(g[k] - s[k])
+        assert np.minimum(diff, 1.0 - diff).max() < 1e-6 * d, k
+    vs = np.sqrt(np.mean(s["vx"] ** 2 + s["vy"] ** 2 + s["vz"] ** 2))
+    for k in ("vx", "vy", "vz"):
+        assert np.abs(g[k] - s[k]).max() < 1e-4 * vs, k
+    assert np.allclose(g["u"], s["u"], rtol=1e-5)
+    assert np.allclose(g["h"], s["h"], rtol=1e-5)
+
+
+def test_fixed_bins_over_four_substeps(orc):
+    import torch
+    from paper_2305_13380_gb300 import sph
+    s = _state(orc, 3)
+    n = len(s["x"])
+    max_bin = 2
+    dt_max = 4.0 * float(np.min(0.1 * orc.GAMMA_K * s["h"] / s["v_sig"]))
+    rng = np.random.default_rng(2)
+    bins = rng.integers(0, max_bin + 1, n).astype(np.int32)
+    _start(s, bins, dt_max, max_bin)
+    arr, pool = _pool(s)
+    gb = torch.tensor(bins, device="cuda")
+    gt = torch.zeros(n, dtype=torch.int64, device="cuda")
+    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+    tb = np.zeros(n, np.int64)
+    t = tg = 0
+    while t < 4:
+        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=False)
+        t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, False)
+        assert tg == t
+    assert np.array_equal(gt.cpu().numpy(), tb) and np.array_equal(gb.cpu().numpy(), bins)
+    g = {k: v.cpu().numpy() for k, v in arr.items()}
+    _compare(g, s, 1.0 / 12)
+
+
+def test_adaptive_bins(orc):
+    import torch
+    from paper_2305_13380_gb300 import sph
+    s = _state(orc, 5)
+    n = len(s["x"])
+    max_bin = 4
+    dt_max = 16.0 * float(np.min(0.1 * orc.GAMMA_K * s["h"] / s["v_sig"]))
+    bins = orc.limit_time_bins(s, s["h"], orc.time_bins(s["h"], s["v_sig"], 0.1, dt_max, max_bin))
+    _start(s, bins, dt_max, max_bin)
+    arr, pool = _pool(s)
+    gb = torch.tensor(bins, device="cuda")
+    gt = torch.zeros(n, dtype=torch.int64, device="cuda")
+    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+    tb = np.zeros(n, np.int64)
+    t = tg = 0
+    for _ in range(3):
+        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=True)
+        t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, True)
+        assert tg == t
+        g_bins, g_tb = gb.cpu().numpy(), gt.cpu().numpy()
+        # every step starts on a multiple of its length, and the tick is an end
+        assert np.all(g_tb % (1 << (max_bin - g_bins)) == 0)
+        assert np.mean(g_bins == bins) > 0.99
+    assert len(np.unique(bins)) > 1
+    if np.array_equal(gb.cpu().numpy(), bins):
+        g = {k: v.cpu().numpy() for k, v in arr.items()}
+        _compare(g, s, 1.0 / 12)
