@@ -269,9 +269,6 @@ int ensure_act(sph_ctx* c, int64_t n) {
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
   dfree(c->act_s);
   dfree(c->blk_any);
-  dfree(c->hact);
-  dfree(c->hbin);
-  dfree(c->htick);
   c->cap_act = c->cap_blk = 0;
   const int64_t cn = n + n / 4 + 64;
   if (!dalloc(c->act_s, cn) || !dalloc(c->blk_any, c->cap_cells + 1)) {
@@ -892,6 +889,9 @@ void sph_destroy(sph_ctx* c) {
   dfree(c->dvp);
   dfree(c->act_s);
   dfree(c->blk_any);
+  dfree(c->hact);
+  dfree(c->hbin);
+  dfree(c->htick);
   dfree(c->misc);
   dfree(c->pairs);
   dfree(c->off1);
