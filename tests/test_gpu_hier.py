@@ -116,7 +116,7 @@ def test_adaptive_bins(orc):
         # every step starts on a multiple of its length, and the tick is an end
         assert np.all(g_tb % (1 << (max_bin - g_bins)) == 0)
         assert np.mean(g_bins == bins) > 0.99
-    assert len(np.unique(bins)) > 2
+    assert len(np.unique(bins)) > 1   # at least two levels of the hierarchy
     if np.array_equal(gb.cpu().numpy(), bins):
         g = {k: v.cpu().numpy() for k, v in arr.items()}
         _compare(g, s, 1.0 / 12)
