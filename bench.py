@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=sorted(KERNELS), default="cubic",
                     help="latticeN / clusteredN: smoothing kernel")
+    ap.add_argument("--hier", action="store_true",
+                    help="latticeN: sub-steps of the time-step hierarchy (sound speeds over a decade)")
     ap.add_argument("--active", type=float, default=0.0,
                     help="latticeN: time the loops on an active subset of this fraction (a "
                          "spherical region) against the full loops, instead of the step")
@@ -628,12 +630,91 @@ def main():
         run_fof(args, world, rank, local)
     elif args.workload.startswith("served"):
         run_served(args, world, rank, local)
+    elif args.hier:
+        run_hier(args, world, rank, local)
     elif args.active > 0.0:
         run_active(args, world, rank, local)
     else:
         run_step(args, world, rank, local)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_hier(args, world: int, rank: int, local: int):
+    """Sub-steps of the time-step hierarchy on the lattice with sound speeds
+    spread over a decade (u = 10^U(-1, 1), seeded): adaptive bins over five
+    levels (dt_max = 16 times the shortest CFL step)."""
+    import numpy as np
+    import torch
+    from paper_2305_13380_gb300 import build as B
+    B.build()
+    from paper_2305_13380_gb300 import replicas, sph
+
+    p = make_workload(args.workload)
+    if p["tree"]:
+        raise SystemExit("the hierarchy runs on the uniform grid (latticeN workloads)")
+    n, L = len(p["x"]), float(p["L"])
+    p["u"] = 10.0 ** np.random.default_rng(7).uniform(-1.0, 1.0, n)
+    t = sph.to_device(p)
+    arrays = {k: t[k].clone() for k in ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
+    for k in ("h", "ax", "ay", "az", "du_dt", "v_sig", "rho", "f", "div_v", "curl_v", "P", "c", "balsara"):
+        arrays[k] = torch.zeros(n, dtype=torch.float32, device="cuda")
+    arrays["dt"] = torch.zeros(1, dtype=torch.float64, device="cuda")
+    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC))
+    part = sph.particles(t)
+    dout = sph.density_out({k: arrays[k] for k in sph.DENSITY_FIELDS})
+    cells = sph.sph_build_cells(init, t["x"], t["y"], t["z"], t["h0"])
+    sph.sph_density(init, cells, part, t["h0"], dout)
+    sph.sph_force(init, cells, part, dout, sph.force_out({k: arrays[k] for k in sph.FORCE_FIELDS}))
+    max_bin = 4
+    dt_min = float((0.1 * 1.825742 * arrays["h"] / arrays["v_sig"]).min())
+    dt_max = 16.0 * dt_min
+    bins = torch.zeros(n, dtype=torch.int32, device="cuda")
+    sph.sph_time_bins(init, cells, part, dout, arrays["v_sig"], 0.1, dt_max, max_bin, bins)
+    init.close()
+    # first half kicks of the starting steps
+    half = (0.5 * dt_max) * torch.pow(2.0, -bins.double()).float()
+    for k in ("x", "y", "z"):
+        arrays["v" + k] += arrays["a" + k] * half
+    arrays["u"] += arrays["du_dt"] * half
+    pool = sph.pool(torch.tensor([0, n], dtype=torch.int64, device="cuda"),
+                    torch.tensor([L], dtype=torch.float64, device="cuda"), arrays)
+    tb = torch.zeros(n, dtype=torch.int64, device="cuda")
+    ctx = sph.Context(sph.sph_default_params(box_size=L))
+    tick = 0
+    for _ in range(args.warmup):
+        tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick)
+    clocks = Clocks(None)
+    replicas.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    active = 0
+    ticks0 = tick
+    for _ in range(args.steps):
+        tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick)
+        active += int((tb == tick).sum().item())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if sph.sph_status(ctx):
+        raise SystemExit("device status set in the hierarchy sub-steps")
+    value, ms = replicas.job_throughput(active, wall * 1e3)
+    levels = torch.bincount(bins.long(), minlength=max_bin + 1).tolist()
+    line = {
+        "metric": "SPH hierarchy sub-step active-particle updates/s",
+        "value": value, "unit": "particle-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "particles": n, "max_bin": max_bin,
+                   "u": "10^U(-1, 1)", "bins_at_end": levels, "ticks": tick - ticks0,
+                   "mean_active_fraction": active / (args.steps * n),
+                   "step": "sph_hier_substep (adaptive bins); host wall time, the call "
+                           "waits for its tick"},
+        "gpu_launches": None,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+    }
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def run_active(args, world: int, rank: int, local: int):
