@@ -86,7 +86,7 @@ def parse():
     ap.add_argument("--kernel", choices=sorted(KERNELS), default="cubic",
                     help="latticeN / clusteredN: smoothing kernel")
     ap.add_argument("--hier", action="store_true",
-                    help="latticeN: sub-steps of the time-step hierarchy (sound speeds over a decade)")
+                    help="latticeN: sub-steps of the time-step hierarchy (a smooth temperature profile)")
     ap.add_argument("--active", type=float, default=0.0,
                     help="latticeN: time the loops on an active subset of this fraction (a "
                          "spherical region) against the full loops, instead of the step")
@@ -641,9 +641,9 @@ def main():
 
 
 def run_hier(args, world: int, rank: int, local: int):
-    """Sub-steps of the time-step hierarchy on the lattice with sound speeds
-    spread over a decade (u = 10^U(-1, 1), seeded): adaptive bins over five
-    levels (dt_max = 16 times the shortest CFL step)."""
+    """Sub-steps of the time-step hierarchy on the lattice with a smooth
+    temperature profile, u = 10^sin(2 pi x / L) (sound speeds over a decade):
+    adaptive bins over five levels (dt_max = 16 times the shortest CFL step)."""
     import numpy as np
     import torch
     from paper_2305_13380_gb300 import build as B
@@ -654,7 +654,9 @@ def run_hier(args, world: int, rank: int, local: int):
     if p["tree"]:
         raise SystemExit("the hierarchy runs on the uniform grid (latticeN workloads)")
     n, L = len(p["x"]), float(p["L"])
-    p["u"] = 10.0 ** np.random.default_rng(7).uniform(-1.0, 1.0, n)
+    # a smooth temperature profile along x over a decade in sound speed:
+    # hot and cold slabs with their own step lengths, no violent mixing
+    p["u"] = 10.0 ** (np.sin(2.0 * np.pi * np.asarray(p["x"]) / L))
     t = sph.to_device(p)
     arrays = {k: t[k].clone() for k in ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
     for k in ("h", "ax", "ay", "az", "du_dt", "v_sig", "rho", "f", "div_v", "curl_v", "P", "c", "balsara"):
@@ -706,7 +708,7 @@ def run_hier(args, world: int, rank: int, local: int):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "particles": n, "max_bin": max_bin,
-                   "u": "10^U(-1, 1)", "bins_at_end": levels, "ticks": tick - ticks0,
+                   "u": "10^sin(2 pi x / L)", "bins_at_end": levels, "ticks": tick - ticks0,
                    "mean_active_fraction": active / (args.steps * n),
                    "step": "sph_hier_substep (adaptive bins); host wall time, the call "
                            "waits for its tick"},
