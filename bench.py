@@ -682,22 +682,31 @@ def run_hier(args, world: int, rank: int, local: int):
     pool = sph.pool(torch.tensor([0, n], dtype=torch.int64, device="cuda"),
                     torch.tensor([L], dtype=torch.float64, device="cuda"), arrays)
     tb = torch.zeros(n, dtype=torch.int64, device="cuda")
-    ctx = sph.Context(sph.sph_default_params(box_size=L))
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING))
     tick = 0
+    scratch = torch.zeros((), dtype=torch.int64, device="cuda")
     for _ in range(args.warmup):
         tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick)
+        scratch += (tb == tick).sum()  # loads the counting kernels before the timed region
+    torch.cuda.synchronize()
+    sph.sph_kernel_times(ctx)  # reset
     clocks = Clocks(None)
     replicas.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    active = 0
+    active_dev = torch.zeros((), dtype=torch.int64, device="cuda")
     ticks0 = tick
+    per_call = []
     for _ in range(args.steps):
+        c0 = time.perf_counter()
         tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick)
-        active += int((tb == tick).sum().item())
+        per_call.append(time.perf_counter() - c0)
+        active_dev += (tb == tick).sum()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    active = int(active_dev.item())
     clk = clocks.stop()
+    kt = sph.sph_kernel_times(ctx)
     if sph.sph_status(ctx):
         raise SystemExit("device status set in the hierarchy sub-steps")
     value, ms = replicas.job_throughput(active, wall * 1e3)
@@ -713,6 +722,8 @@ def run_hier(args, world: int, rank: int, local: int):
                    "step": "sph_hier_substep (adaptive bins); host wall time, the call "
                            "waits for its tick"},
         "gpu_launches": None,
+        "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "call_ms": {"median": 1e3 * float(np.median(per_call)), "max": 1e3 * float(np.max(per_call))},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }
     if rank == 0:
@@ -1005,6 +1016,7 @@ def run_step(args, world: int, rank: int, local: int):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "call_ms": {"median": 1e3 * float(np.median(per_call)), "max": 1e3 * float(np.max(per_call))},
         # the loops alone: density (all Newton passes) + force per step
         "density_force_updates_per_s": n / ((kt["density"][0] + kt["force"][0]) / args.steps / 1e3),
         "pairs_per_step": {"density_final_pass": pairs_d, "force": pairs_f,
