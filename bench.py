@@ -1016,7 +1016,6 @@ def run_step(args, world: int, rank: int, local: int):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
-        "call_ms": {"median": 1e3 * float(np.median(per_call)), "max": 1e3 * float(np.max(per_call))},
         # the loops alone: density (all Newton passes) + force per step
         "density_force_updates_per_s": n / ((kt["density"][0] + kt["force"][0]) / args.steps / 1e3),
         "pairs_per_step": {"density_final_pass": pairs_d, "force": pairs_f,
