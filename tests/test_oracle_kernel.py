@@ -127,3 +127,30 @@ def test_other_kernels_density_on_a_perfect_lattice(orc, k):
     assert np.allclose(d["n_hat"] * (d["h"] / phys.eta) ** 3, 1.0, rtol=1e-12)
     rho_true = 1.0  # unit mass in the unit box
     assert np.abs(d["rho"] / rho_true - 1.0).max() < 3e-2
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_other_kernels_in_the_loops(orc, k):
+    # the loops with another kernel: grid equal to brute force, dn/dh against a
+    # finite difference of n_hat (so w and w' agree inside the solve), and
+    # momentum and energy conserved by the pair terms
+    from paper_2305_13380_gb300 import inputs
+    p = inputs.clustered(800, n_spheres=3, seed=4)
+    p = {kk: (float(v) if kk == "L" else np.asarray(v, dtype=np.float64)) for kk, v in p.items()}
+    phys = orc.Physics(kernel=k)
+    d1 = orc.density(p, p["h0"], None, phys)
+    d2 = orc.density(p, p["h0"], None, phys, brute=True)
+    assert np.allclose(d1["rho"], d2["rho"], rtol=1e-12)
+    tg = np.arange(0, 800, 37)
+    h = d1["h"][tg]
+    eps = 1e-6
+    up = orc.density_at(p, h * (1 + eps), tg, phys)["n_hat"]
+    dn = orc.density_at(p, h * (1 - eps), tg, phys)["n_hat"]
+    fd = (up - dn) / (2 * eps * h)
+    assert np.allclose(d1["dn_dh"][tg], fd, rtol=1e-5)
+    f = orc.force(p, d1, None, phys)
+    m = p["m"]
+    for kk in ("ax", "ay", "az"):
+        assert abs((m * f[kk]).sum()) <= 1e-12 * np.abs(m * f[kk]).sum()
+    power = m * (p["vx"] * f["ax"] + p["vy"] * f["ay"] + p["vz"] * f["az"] + f["du_dt"])
+    assert abs(power.sum()) <= 1e-11 * np.abs(m * f["du_dt"]).sum()
