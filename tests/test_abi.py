@@ -72,3 +72,13 @@ def test_kernel_parameter_checked_without_gpu(libsph):
         p = sph.sph_default_params(**kw)
         assert sph.lib().sph_create(ctypes.byref(h), ctypes.byref(p), None) == sph.SPH_E_INVAL, kw
     assert sph.sph_default_params().kernel == sph.SPH_KERNEL_CUBIC
+
+
+def test_new_entry_points_reject_null_arguments_without_gpu(libsph):
+    from paper_2305_13380_gb300 import sph
+    L = sph.lib()
+    t = ctypes.c_int64(0)
+    assert L.sph_density_active(None, None, None, None, None, None) == sph.SPH_E_INVAL
+    assert L.sph_force_active(None, None, None, None, None, None) == sph.SPH_E_INVAL
+    assert L.sph_time_bins(None, None, None, None, None, 0.1, 1.0, 10, None) == sph.SPH_E_INVAL
+    assert L.sph_hier_substep(None, None, None, None, 1.0, 4, 0, 1, ctypes.byref(t)) == sph.SPH_E_INVAL
