@@ -664,11 +664,13 @@ sphk::SphenixDev sphenix_dev(const sph_sphenix_params& x, double dt, const doubl
   return d;
 }
 
-// A SPHENIX pass of do_force: the gradient pass (gradient = true: writes
-// alpha_c_out and, if given, lap_u) or the SPHENIX force.  The E records are
-// gathered from u, alpha_v, P and alpha_c; skip_gather reuses the A..D
-// records of the previous pass on the same build and inputs.
-struct SphenixCall {
+// A pass of do_force with a fifth staged record E per source: the SPHENIX
+// gradient pass (gradient = true: writes alpha_c_out and, if given, lap_u),
+// the SPHENIX force (E gathered from u, alpha_v, P and alpha_c), or the
+// time-step limiter (limit = true: E.x = the bins bins_in, result in
+// bins_out).  skip_gather reuses the A..D records of the previous pass on the
+// same build and inputs.
+struct LoopPass {
   bool gradient = false;
   bool skip_gather = false;
   // the time-step limiter pass instead (bins_in gathered as the E records)
@@ -683,7 +685,7 @@ struct SphenixCall {
 int do_force(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
              const float* vy, const float* vz, const float* m, const float* h, const float* rho,
              const float* f, const float* P, const float* cs, const float* B, float* ax, float* ay,
-             float* az, float* du_dt, float* v_sig, bool pos_ready = false, const SphenixCall* sx = nullptr,
+             float* az, float* du_dt, float* v_sig, bool pos_ready = false, const LoopPass* sx = nullptr,
              const uint8_t* active = nullptr) {
   if (active && c->built_tree) return SPH_E_INVAL;  // masked loops run on the uniform grid
   sphh::GatherForceArgs g;
@@ -1109,7 +1111,7 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
     t_begin(c, SPH_T_INTEGRATE);
     if (sphh::launch_sphenix_alpha_v(aa, xd, c->st) != cudaSuccess) return SPH_E_CUDA;
     t_end(c, SPH_T_INTEGRATE);
-    SphenixCall g;
+    LoopPass g;
     g.gradient = true;
     g.u = c->up;
     g.alpha_v = alpha_v;
@@ -1119,7 +1121,7 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
     rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P, pl->c,
                   pl->balsara, pl->ax, pl->ay, pl->az, pl->du_dt, pl->v_sig, true, &g);
     if (rc != SPH_OK) return rc;
-    SphenixCall f = g;
+    LoopPass f = g;
     f.gradient = false;
     f.skip_gather = true;
     rc = do_force(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, pl->h, pl->rho, pl->f, pl->P, pl->c,
@@ -1153,7 +1155,7 @@ int sph_time_bins(sph_ctx* c, const sph_cells* cells, const sph_particles* in, c
   const float cf = (float)(cfl * sphk::kernel_gamma(c->p.kernel));
   if (sphh::launch_time_bins(in->n, d->h, v_sig, cf, (float)dt_max, max_bin, bins, c->st) != cudaSuccess)
     return SPH_E_CUDA;
-  SphenixCall L;
+  LoopPass L;
   L.limit = true;
   L.bins_in = bins;
   L.bins_out = bins;
@@ -1239,7 +1241,7 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
     const float cf = (float)(c->p.cfl * sphk::kernel_gamma(c->p.kernel));
     if (sphh::launch_time_bins(n, pl->h, pl->v_sig, cf, (float)dt_max, max_bin, c->hbin, c->st) != cudaSuccess)
       return SPH_E_CUDA;
-    SphenixCall L;
+    LoopPass L;
     L.limit = true;
     L.skip_gather = true;
     L.bins_in = c->hbin;
@@ -1314,7 +1316,7 @@ int sph_sphenix_gradient(sph_ctx* c, const sph_cells* cells, const sph_particles
                             d->c,       d->div_v,   st->v_sig,       st->div_v_prev,
                             st->alpha_v, (float)sphk::kernel_gamma(c->p.kernel)};
   if (sphh::launch_sphenix_alpha_v(aa, xd, c->st) != cudaSuccess) return SPH_E_CUDA;
-  SphenixCall g;
+  LoopPass g;
   g.gradient = true;
   g.u = in->u;
   g.alpha_v = st->alpha_v;
@@ -1338,7 +1340,7 @@ int sph_force_sphenix(sph_ctx* c, const sph_cells* cells, const sph_particles* i
     return SPH_E_INVAL;
   int rc = ensure_sphenix(c, in->n);
   if (rc != SPH_OK) return rc;
-  SphenixCall f;
+  LoopPass f;
   f.u = in->u;
   f.alpha_v = alpha_v;
   f.alpha_c = alpha_c;
