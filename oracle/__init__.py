@@ -457,21 +457,36 @@ def time_bins(h, v_sig, cfl: float, dt_max: float, max_bin: int, kernel: int = 0
     """Per-particle time bins of the power-of-two time-step hierarchy (Sec. 2.4,
     "Local time-step optimisations"): the CFL step dt_i = C_CFL gamma_K h_i / v_sig,i,
     and bin_i = the smallest b in [0, max_bin] with dt_max 2^-b <= dt_i (max_bin if
-    none; bin 0 where v_sig <= 0).  The bin is an integer decided by floating point, so it is
-    taken in FP32, the precision of the library's kernel: c = fl32(C_CFL gamma_K),
-    dt_i = fl32(fl32(c h_i) / v_sig,i), compared with fl32(dt_max) scaled by 2^-b
-    (exact)."""
-    h = np.asarray(h, dtype=np.float32)
-    v = np.asarray(v_sig, dtype=np.float32)
-    c = np.float32(cfl * gamma_k(kernel))
+    none; bin 0 where v_sig <= 0).  The definition in FP64: dt_i is one FP64
+    expression and dt_max 2^-b is exact.  A kernel that decides in a lower precision
+    agrees except where dt_i lies within its rounding of a power-of-two boundary
+    (``bin_edge_band``)."""
+    h = np.asarray(h, dtype=np.float64)
+    v = np.asarray(v_sig, dtype=np.float64)
+    c = float(cfl) * gamma_k(kernel)
     with np.errstate(divide="ignore"):
-        dt = np.where(v > 0, (c * h) / np.where(v > 0, v, np.float32(1)), np.float32(np.inf)).astype(np.float32)
-    top = np.float32(dt_max)
+        dt = np.where(v > 0, c * h / np.where(v > 0, v, 1.0), np.inf)
     bins = np.full(h.shape, max_bin, dtype=np.int32)
     for b in range(max_bin, -1, -1):
-        step = np.float32(np.ldexp(top, -b))
-        bins = np.where(step <= dt, b, bins)
+        bins = np.where(np.ldexp(float(dt_max), -b) <= dt, b, bins)
     return bins
+
+
+def bin_edge_band(h, v_sig, cfl: float, dt_max: float, max_bin: int, kernel: int = 0,
+                  rel: float = 1e-6):
+    """True where the CFL step dt_i lies within a relative distance rel of one of
+    the bin boundaries dt_max 2^-b (b = 0..max_bin): there a bin decided in FP32
+    may differ by one from the FP64 definition."""
+    h = np.asarray(h, dtype=np.float64)
+    v = np.asarray(v_sig, dtype=np.float64)
+    c = float(cfl) * gamma_k(kernel)
+    with np.errstate(divide="ignore"):
+        dt = np.where(v > 0, c * h / np.where(v > 0, v, 1.0), np.inf)
+    near = np.zeros(h.shape, dtype=bool)
+    for b in range(0, max_bin + 1):
+        e = np.ldexp(float(dt_max), -b)
+        near |= np.abs(dt - e) <= rel * e
+    return near
 
 
 def limit_time_bins(p: dict, h, bins, kernel: int = 0, scale: float = 1.0):
@@ -506,7 +521,9 @@ def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int
     bin b steps 2^(max_bin - b) ticks.  Every particle drifts to the next end
     of a step; the particles whose step ends there (the active ones) get the
     density and the force at the predicted v and u of every particle, their
-    second half kick, a new bin (adapt: the limited CFL bin; else the old one;
+    second half kick, a new bin (adapt: the CFL bin limited against the
+    neighbours' bins -- proposed ones for active neighbours, held ones for
+    inactive neighbours; else the old one;
     shortened until the new step divides the tick) and the first half kick of
     the new step.  Returns the new tick."""
     n = len(bins)
@@ -529,7 +546,13 @@ def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int
     for k in ("ax", "ay", "az", "du_dt", "v_sig"):
         s[k][act] = f[k]
     if adapt:
+        # the limiter compares an active particle's proposed bin with the bins
+        # its force-loop neighbours step in: the proposals of the active ones,
+        # the bins that the inactive ones hold for their current step
         b0 = time_bins(s["h"], s["v_sig"], cfl, dt_max, max_bin, phys.kernel)
+        held = np.ones(n, dtype=bool)
+        held[act] = False
+        b0[held] = bins[held]
         new = limit_time_bins(pred, s["h"], b0, phys.kernel)[act]
     else:
         new = bins[act].copy()

@@ -1237,9 +1237,11 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
   if (rc != SPH_OK) return rc;
   if (adapt) {
     // proposed bins of the active particles: CFL bins, then the limiter over
-    // the force pairs (the masked pass reuses the density's lists)
+    // the force pairs (the masked pass reuses the density's lists) against
+    // the active neighbours' proposals and the bins the inactive ones hold
     const float cf = (float)(c->p.cfl * sphk::kernel_gamma(c->p.kernel));
-    if (sphh::launch_time_bins(n, pl->h, pl->v_sig, cf, (float)dt_max, max_bin, c->hbin, c->st) != cudaSuccess)
+    if (sphh::launch_time_bins(n, pl->h, pl->v_sig, cf, (float)dt_max, max_bin, c->hbin, c->st) != cudaSuccess ||
+        sphh::launch_hier_held_bins(h, c->hbin, c->st) != cudaSuccess)
       return SPH_E_CUDA;
     LoopPass L;
     L.limit = true;

@@ -59,6 +59,15 @@ __global__ void k_hier_drift(sphh::HierArgs a) {
   }
 }
 
+// The limiter's input: the CFL proposal of an active particle, the bin that
+// an inactive particle holds for its current step (the step it takes in the
+// force loops until it ends).
+__global__ void k_hier_held_bins(int64_t n, const uint8_t* __restrict__ act, const int32_t* __restrict__ bin,
+                                 int32_t* __restrict__ prop) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!act[i]) prop[i] = bin[i];
+}
+
 // The end of an active particle's step: second half kick over the old step,
 // the new bin (the proposed one, shortened until the new step is aligned with
 // t_next), first half kick over the new step.
@@ -104,6 +113,12 @@ cudaError_t launch_hier_next(const HierArgs& a, cudaStream_t st) {
 cudaError_t launch_hier_drift(const HierArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   k_hier_drift<<<grid_h(a.n), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hier_held_bins(const HierArgs& a, int32_t* prop, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  k_hier_held_bins<<<grid_h(a.n), 256, 0, st>>>(a.n, a.act, a.bin, prop);
   return cudaGetLastError();
 }
 

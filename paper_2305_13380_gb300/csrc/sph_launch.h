@@ -196,6 +196,8 @@ struct HierArgs {
 cudaError_t launch_hier_next(const HierArgs& a, cudaStream_t st);
 cudaError_t launch_hier_drift(const HierArgs& a, cudaStream_t st);
 cudaError_t launch_hier_kick(const HierArgs& a, cudaStream_t st);
+// prop[i] = bin[i] where act[i] == 0 (the limiter's input for inactive particles)
+cudaError_t launch_hier_held_bins(const HierArgs& a, int32_t* prop, cudaStream_t st);
 
 // Time bins (timebins.cu): the CFL bins of n particles (input order), and the
 // sorted limiter records E[s].x = bin of perm[s].

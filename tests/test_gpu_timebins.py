@@ -1,7 +1,11 @@
 """Time bins and the first time-step limiter (sph_time_bins) on the GPU
-against the oracle: the CFL bins bit for bit (both decide in FP32), the
-limited bins within the bins that the force-pair set with its radius moved by
-1e-5 gives (pairs at the edge of max(H_i, H_j) may fall either way)."""
+against the oracle.  The oracle decides the CFL bins in FP64 (the definition),
+the kernel in FP32: they agree except where the CFL step lies within 1e-6 of a
+bin boundary (a few FP32 roundings), where the kernel's bin may be one off.
+The limited bins lie within what the oracle's limiter gives with those edge
+bins moved either way and the force-pair radius moved by 1e-5 (pairs at the
+edge of max(H_i, H_j) may fall either way), and equal the oracle's almost
+everywhere."""
 import numpy as np
 import pytest
 
@@ -45,11 +49,21 @@ def _case(seed, v):
     return p, h, np.asarray(v(rng, len(p["x"])), dtype=np.float32)
 
 
+def _bounds(orc, p, h, v):
+    b0 = orc.time_bins(h, v, CFL, DT_MAX, MAX_BIN)
+    edge = orc.bin_edge_band(h, v, CFL, DT_MAX, MAX_BIN).astype(np.int32)
+    lo = orc.limit_time_bins(p, h, np.maximum(b0 - edge, 0), scale=1 - 1e-5)
+    hi = orc.limit_time_bins(p, h, np.minimum(b0 + edge, MAX_BIN), scale=1 + 1e-5)
+    return b0, edge, lo, hi
+
+
 def test_uniform_speed_gives_one_bin(orc):
     p, h, v = _case(1, lambda r, n: np.full(n, 3.0))
     g = _gpu_bins(p, h, v)
-    b0 = orc.time_bins(h, v, CFL, DT_MAX, MAX_BIN)
-    assert np.array_equal(g, orc.limit_time_bins(p, h, b0))
+    b0, edge, lo, hi = _bounds(orc, p, h, v)
+    assert np.all(g >= lo) and np.all(g <= hi)
+    if not edge.any():
+        assert np.array_equal(g, orc.limit_time_bins(p, h, b0))
     assert len(np.unique(b0)) <= 2
 
 
@@ -57,9 +71,7 @@ def test_uniform_speed_gives_one_bin(orc):
 def test_random_speeds_and_the_limiter(orc, seed):
     p, h, v = _case(seed, lambda r, n: np.exp(r.uniform(np.log(0.5), np.log(500.0), n)))
     g = _gpu_bins(p, h, v)
-    b0 = orc.time_bins(h, v, CFL, DT_MAX, MAX_BIN)
-    lo = orc.limit_time_bins(p, h, b0, scale=1 - 1e-5)
-    hi = orc.limit_time_bins(p, h, b0, scale=1 + 1e-5)
+    b0, edge, lo, hi = _bounds(orc, p, h, v)
     assert np.all(g >= lo) and np.all(g <= hi)
     assert np.mean(g == orc.limit_time_bins(p, h, b0)) > 0.99
     assert np.all(g >= b0) and np.sum(g > b0) > 50   # the limiter acted
@@ -69,11 +81,42 @@ def test_one_fast_particle_raises_its_neighbours(orc):
     p, h, v = _case(4, lambda r, n: np.full(n, 1.0))
     v[17] = 1e4
     g = _gpu_bins(p, h, v)
-    b0 = orc.time_bins(h, v, CFL, DT_MAX, MAX_BIN)
-    assert np.array_equal(g, orc.limit_time_bins(p, h, b0))
+    b0, edge, lo, hi = _bounds(orc, p, h, v)
+    assert np.all(g >= lo) and np.all(g <= hi)
+    if not edge.any():
+        assert np.array_equal(g, orc.limit_time_bins(p, h, b0))
     assert g[17] == b0[17] and (g == b0[17] - 2).sum() > 30
 
 
 def test_resting_particles_take_the_longest_bin(orc):
     p, h, v = _case(5, lambda r, n: np.zeros(n))
     assert np.all(_gpu_bins(p, h, v) == 0)
+
+
+def test_cfl_bins_match_the_fp64_definition_off_the_edges(orc):
+    """Without neighbours in reach (particles far apart), the limiter leaves
+    the CFL bins alone: the kernel's FP32 bins equal the FP64 definition except
+    within the edge band, including speeds placed exactly on and next to the
+    bin boundaries."""
+    rng = np.random.default_rng(9)
+    n_side = 4
+    p = inputs.lattice(n_side, seed=9, jitter=0.0, sigma_v=0.0)
+    n = len(p["x"])
+    h = np.full(n, 0.05, np.float32)      # supports far below the spacing
+    c = CFL * orc.GAMMA_K
+    # speeds whose CFL step falls on, just above and just below boundaries
+    k = rng.integers(1, 20, n)
+    v = (c * 0.05 / np.ldexp(DT_MAX, -k)).astype(np.float32)
+    v[::3] = np.nextafter(v[::3], np.float32(np.inf))
+    v[1::3] = np.nextafter(v[1::3], np.float32(0))
+    g = _gpu_bins(p, h, v)
+    b0 = orc.time_bins(h, v, CFL, DT_MAX, MAX_BIN)
+    edge = orc.bin_edge_band(h, v, CFL, DT_MAX, MAX_BIN)
+    assert np.array_equal(g[~edge], b0[~edge])
+    assert np.all(np.abs(g[edge] - b0[edge]) <= 1)
+    # random speeds: almost none on an edge, all equal
+    v2 = np.exp(rng.uniform(0.0, 8.0, n)).astype(np.float32)
+    g2 = _gpu_bins(p, h, v2)
+    b2 = orc.time_bins(h, v2, CFL, DT_MAX, MAX_BIN)
+    e2 = orc.bin_edge_band(h, v2, CFL, DT_MAX, MAX_BIN)
+    assert np.array_equal(g2[~e2], b2[~e2])

@@ -64,3 +64,34 @@ def test_long_steps_only_drift_until_they_end():
     assert not np.array_equal(hs["vx"][short], v0[short])
     t = oracle.hier_substep(hs, bins, tb, dt_max, 1, t, False)
     assert t == 2 and np.all(tb == 2)
+
+
+def test_limiter_takes_the_bins_that_inactive_neighbours_hold():
+    """Adaptive bins: an active particle's new bin is limited against the bin an
+    inactive neighbour holds for its current step, not against a CFL bin
+    recomputed from that neighbour's last h and v_sig.  Particle b steps 16
+    ticks (bin 0) with a stale signal speed whose CFL bin would be the deepest;
+    the others step 8 ticks (bin 1) and end their step first."""
+    s = _state()
+    n = len(s["x"])
+    max_bin = 4
+    dt_cfl = 0.1 * oracle.GAMMA_K * s["h"] / s["v_sig"]
+    dt_max = 0.5 * float(np.min(dt_cfl))        # every fresh CFL bin is 0
+    b = 0
+    s["v_sig"][b] *= 1e6                          # stale: its CFL bin would be 4
+    assert oracle.time_bins(s["h"], s["v_sig"], 0.1, dt_max, max_bin)[b] == max_bin
+    bins = np.ones(n, np.int32)
+    bins[b] = 0
+    tb = np.zeros(n, np.int64)
+    hs = _half_kicked(s, 2.0 ** (max_bin - bins) * np.ldexp(dt_max, -max_bin))
+    t = oracle.hier_substep(hs, bins, tb, dt_max, max_bin, 0, True)
+    assert t == 8 and tb[b] == 0 and bins[b] == 0
+    d = [(np.asarray(s[k]) - s[k][b] + 0.5) % 1.0 - 0.5 for k in "xyz"]
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    H = oracle.GAMMA_K * s["h"]
+    near = (r < np.maximum(H, H[b])) & (np.arange(n) != b)
+    assert near.sum() > 20
+    # held bin 0 limits nothing: the step of 8 ticks stays (aligned at tick 8);
+    # a limiter fed with b's recomputed CFL bin (4) would force bin 2
+    assert np.all(bins[near] == 1)
+    assert np.all(bins[np.arange(n) != b] == 1)
