@@ -822,6 +822,39 @@ def run_active(args, world: int, rank: int, local: int):
         print(json.dumps(line))
 
 
+def fp32_peak_tflops(reps: int = 5) -> float:
+    """Measured FP32 fused-multiply-add rate of the current device (TFLOP/s):
+    the best of `reps` timed launches of the FP32 probe, a benchmark-only
+    shared object built beside the library (not part of it)."""
+    import ctypes
+    import torch
+    from paper_2305_13380_gb300 import build as pkg_build
+    probe = ctypes.CDLL(pkg_build.build_probe())
+    probe.fp32_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    probe.fp32_probe.restype = ctypes.c_int
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = sms * 8, 20000
+    sink = torch.zeros(blocks, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def launch():
+        rc = probe.fp32_probe(blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+        if rc != 0:
+            raise RuntimeError(f"fp32_probe failed with {rc}")
+    launch()
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        launch()
+        e1.record(st)
+        st.synchronize()
+        flops = blocks * 256 * 8 * 2 * iters
+        best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
+
+
 def run_step(args, world: int, rank: int, local: int):
     """The single-simulation workloads (latticeN, clusteredN): one sph_step
     of the whole box per step."""
@@ -978,7 +1011,7 @@ def run_step(args, world: int, rank: int, local: int):
         kname, kms, flops = "force", force_ms, pairs_f * F_FORCE
     achieved = flops / (kms / 1e3) / 1e12
     kfull = f"k_tree_{kname}" if tree else f"k_{kname}"
-    fma_peak = sph.fp32_peak_tflops()  # measured FP32 FMA rate of this device
+    fma_peak = fp32_peak_tflops()  # measured FP32 FMA rate of this device
     roofline = {"bound": "alu", "kernel": kfull, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_measured_fma": fma_peak, "frac_of_measured": achieved / fma_peak,

@@ -445,13 +445,6 @@ int sph_pair_counts(sph_ctx* ctx, int64_t* out);
 int sph_pool_move(const sph_pool* spread, const sph_pool* packed, int32_t n_ranges, const int64_t* starts,
                   const int64_t* offsets, int32_t to_packed, void* stream);
 
-/* Enqueues `blocks` blocks of 256 threads, each thread running 8 independent
- * FP32 fused multiply-add chains for `iters` iterations (2 flop each:
- * blocks x 256 x 8 x 2 x iters flop in all).  Timed by the caller, it measures
- * the FP32 pipe's peak, the roofline denominator of the loops.  sink: device
- * float[blocks], written only to keep the chains live.  Not part of the method. */
-int sph_fp32_probe(int32_t blocks, int64_t iters, float* sink, void* stream);
-
 /* Diagnostics of the last nested-grid build and density (SPH_FLAG_TREE; waits
  * for the stream): out[0] = target groups, out[1] = targets summed without a
  * neighbour list (needs SPH_FLAG_COUNT_PAIRS, else 0), out[2] = reverse pairs

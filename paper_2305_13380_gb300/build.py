@@ -1,7 +1,10 @@
 """Builds the CUDA library ``_lib/libsph.so`` from ``csrc/*.cu`` for sm_103a.
 
 Each translation unit is compiled in parallel with nvcc, then linked into one
-shared library with the C ABI of ``include/sph.h``."""
+shared library with the C ABI of ``include/sph.h``.  The benchmark's FP32 rate
+probe (``csrc/bench/fp32_probe.cu``) is built into a separate
+``_lib/libsph_fp32_probe.so``: it is a measurement tool, not part of the
+library."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -16,6 +19,8 @@ ROOT = os.path.dirname(PKG)
 SRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libsph.so")
+PROBE_SRC = os.path.join(SRC, "bench", "fp32_probe.cu")
+PROBE_LIB = os.path.join(OUT_DIR, "libsph_fp32_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-ffp-contract=off"]
@@ -42,6 +47,20 @@ def up_to_date() -> bool:
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
+
+
+def build_probe(force: bool = False) -> str:
+    """Builds the benchmark's FP32 rate probe into its own shared object."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PROBE_LIB + f".{os.getpid()}.tmp"
+    cmd = [nvcc(), *ARCH, *FLAGS, "-shared", PROBE_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:

@@ -146,7 +146,6 @@ def lib():
                                              _P, C.c_int64, _P, _P, _P, _P]
         L.sph_reserve.argtypes = [_P, C.c_int64, C.c_int32]
         L.sph_tree_counts.argtypes = [_P, C.POINTER(C.c_int64)]
-        L.sph_fp32_probe.argtypes = [C.c_int32, C.c_int64, _P, _P]
         L.sph_fof.argtypes = [_P, C.c_int64, _P, _P, _P, C.c_double, _P]
         L.sph_pool_move.argtypes = [C.POINTER(sph_pool), C.POINTER(sph_pool), C.c_int32, _P, _P, C.c_int32,
                                     _P]
@@ -154,7 +153,7 @@ def lib():
                   "sph_density",
                   "sph_force", "sph_step", "sph_conservation", "sph_pair_counts",
                   "sph_kernel_times", "sph_build_cells_static", "sph_reserve", "sph_tree_counts",
-                  "sph_pool_move", "sph_fp32_probe", "sph_fof"):
+                  "sph_pool_move", "sph_fof"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -353,27 +352,6 @@ def sph_pool_move(spread: sph_pool, packed: sph_pool, n_ranges: int, starts, off
     _check(lib().sph_pool_move(C.byref(spread), C.byref(packed), int(n_ranges), _ptr(starts, torch.int64),
                                _ptr(offsets, torch.int64), 1 if to_packed else 0, C.c_void_p(st.cuda_stream)),
            "sph_pool_move")
-
-
-def fp32_peak_tflops(reps: int = 5) -> float:
-    """Measured FP32 fused-multiply-add rate of the current device (TFLOP/s):
-    the best of `reps` timed launches of sph_fp32_probe."""
-    dev = torch.cuda.current_device()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    blocks, iters = sms * 8, 20000
-    sink = torch.zeros(blocks, dtype=torch.float32, device="cuda")
-    st = torch.cuda.current_stream()
-    _check(lib().sph_fp32_probe(blocks, iters, _ptr(sink), C.c_void_p(st.cuda_stream)), "sph_fp32_probe")
-    best = 0.0
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        _check(lib().sph_fp32_probe(blocks, iters, _ptr(sink), C.c_void_p(st.cuda_stream)), "sph_fp32_probe")
-        e1.record(st)
-        st.synchronize()
-        flops = blocks * 256 * 8 * 2 * iters
-        best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
-    return best
 
 
 def sph_tree_counts(ctx: Context) -> dict:
