@@ -458,10 +458,14 @@ int sph_tree_counts(sph_ctx* ctx, int64_t* out);
  * has no counterpart: this is a deployment variant of sph_build_cells.
  *
  * It computes the same grid and the same lists as sph_build_cells on a
- * context whose parameters have box_size and cell_margin (bit-identical
- * cell_start and perm), but keeps all of its scratch in one fixed array
- * compiled into the library (about 3.1 MB, held by every GPU that loads the
- * library until the process exits) and calls no allocating routine.
+ * context with the cubic-spline kernel (the default), the uniform grid (no
+ * SPH_FLAG_TREE) and the same box_size and cell_margin: bit-identical
+ * cell_start and perm.  The cells are sized for the cubic spline's support
+ * H = 1.825742 h; a caller of the quartic or Wendland C2 kernel passes h
+ * scaled by gamma_K(kernel) / 1.825742, or uses sph_build_cells.  All of its
+ * scratch is one fixed array compiled into the library (about 3.1 MB, held
+ * by every GPU that loads the library until the process exits); it calls no
+ * allocating routine.
  *   n              particles, 0 <= n <= 65536 (more: SPH_E_CAPACITY)
  *   x, y, z, h     device inputs (length n)
  *   cell_start     device output, cell_start_cap >= 8 n + 217 entries; the
@@ -471,8 +475,10 @@ int sph_tree_counts(sph_ctx* ctx, int64_t* out);
  *   status_out     optional device int32: SPH_ST_* bits of this build
  *   stream         cudaStream_t (NULL = legacy default stream)
  * The first call on a device resolves the address of the fixed array on that
- * device (with that device current); make that first call before any stream
- * capture.  Every call on a device shares the array: calls whose work
+ * device (with that device current) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not call
+ * it again on a device after cudaDeviceReset (the kept address would be
+ * stale).  Every call on a device shares the array: calls whose work
  * overlaps on the GPU (different streams, or different host threads) race
  * and corrupt each other's results.  Returns SPH_OK when the work is
  * enqueued. */

@@ -45,7 +45,8 @@ constexpr int64_t kWords = kOffHist + align64(kStaticHist);
 // until the process exits.
 static __device__ __align__(256) int32_t g_scratch[kWords];
 
-// Device address of g_scratch per device, resolved once per device.
+// Device address of g_scratch per device, resolved once per device and kept
+// for the life of the process (a cudaDeviceReset would make it stale).
 std::mutex g_mu;
 int32_t* g_addr[64] = {nullptr};
 

@@ -71,3 +71,28 @@ def test_static_build_rejects_oversize():
     with pytest.raises(sph.SPHError) as e:
         sph.sph_build_cells_static(x[:100], x[:100], x[:100], h[:100], 1.0, 0.05, small, perm[:100])
     assert e.value.code == sph.SPH_E_INVAL
+
+
+def test_static_build_at_capacity_and_empty():
+    """n = STATIC_MAX_N fills every part of the fixed array (keys, slots, counts
+    of 8 n + 216 cells, scan partials, histograms): an off-by-one in the layout
+    would corrupt the next part.  n = 0 writes an empty grid."""
+    import torch
+    from paper_2305_13380_gb300 import sph
+    p = inputs.clustered(sph.STATIC_MAX_N, 7, seed=12)
+    assert len(p["x"]) == sph.STATIC_MAX_N
+    for margin in (0.05, 0.0):
+        nc, cs, perm, st = _static(p, margin)
+        rnc, rcs, rperm = _reference(p, margin)
+        assert st == 0 and nc == rnc
+        assert np.array_equal(cs, rcs) and np.array_equal(perm, rperm)
+    e = torch.zeros(0, dtype=torch.float64, device="cuda")
+    he = torch.zeros(0, dtype=torch.float32, device="cuda")
+    cs = torch.full((217,), -7, dtype=torch.int32, device="cuda")
+    perm = torch.zeros(0, dtype=torch.int32, device="cuda")
+    nc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sph.sph_build_cells_static(e, e, e, he, 1.0, 0.05, cs, perm, nc)
+    torch.cuda.synchronize()
+    k = int(nc.item())
+    assert 3 <= k <= 6
+    assert np.all(cs[:k ** 3 + 1].cpu().numpy() == 0)
