@@ -33,7 +33,10 @@ sys.path.insert(0, ROOT)
 METRIC = "SPH density+force particle-updates/s at 2M"
 UNIT = "particle-updates/s"
 # Flops per in-support pair of the oracle's formulas (every add, multiply,
-# divide and square root counts 1; see the design notes for the tally).
+# divide and square root counts 1; see the design notes for the tally):
+# a Newton pass of the density loop (n_hat and dn_hat/dh only), the density
+# loop's final pass at the converged h (every sum), and the force loop.
+F_NEWTON = 33
 F_DENSITY = 66
 F_FORCE = 72
 KERNELS = {"cubic": 0, "quartic": 1, "wendland_c2": 2}
@@ -96,6 +99,12 @@ def parse():
                     help="uniform grid: sorted interactions in the density filter")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle work for the whole --impl reference run")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="lattice128 default line: skip the batched and served measurements")
+    ap.add_argument("--batched-boxes", type=int, default=256)
+    ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--served-sims", type=int, default=200,
+                    help="simulations of the served run inside the default line")
     return ap.parse_args()
 
 
@@ -368,7 +377,10 @@ def run_fof(args, world: int, rank: int, local: int):
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "roofline": roofline,
+        "roofline_loops": loops,
         "cpu_baseline": cpu,
+        "batched": batched,
+        "served": served,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items() if v[1]},
         "groups": int(len(counts)), "largest_group": int(counts.max()),
         "particles_in_groups_of_32_or_more": int(counts[counts >= 32].sum()),
@@ -431,10 +443,13 @@ def _traffic(kernel: str, source: str):
     return None
 
 
-def run_batch(args, world: int, rank: int, local: int):
-    """256 independent boxes (config of the batched workload): one sph_step per
-    step for all boxes, captured in a CUDA graph; against the same boxes each
-    stepped by its own sph_step call (one simulation per launch)."""
+def batch_measure(n_boxes: int, steps: int, warmup: int, plain_steps: int) -> dict:
+    """The batched workload: n_boxes independent periodic boxes (N log-uniform
+    in [1e3, 1e5], even boxes jittered lattices, odd ones Plummer-clustered),
+    one sph_step per step for all boxes, captured in a CUDA graph, cell
+    geometry from the autotuner; against the same boxes each stepped by its
+    own sph_step call (one simulation per launch).  Per-step latencies from
+    CUDA events on the pool's stream; the slowest rank's under replicas."""
     import numpy as np
     import torch
 
@@ -442,32 +457,32 @@ def run_batch(args, world: int, rank: int, local: int):
     B.build()
     from paper_2305_13380_gb300 import inputs, pool, replicas, sph, tune
 
-    n_boxes = int(args.workload[len("batch"):] or 256)
     boxes = inputs.batch(n_boxes, seed0=0)
     n = sum(len(b["x"]) for b in boxes)
+    t_tune = time.perf_counter()
     over = tune.best_params(boxes, key=f"batch{n_boxes}")
+    tune_s = time.perf_counter() - t_tune
     prm = lambda: sph.sph_default_params(**over)  # noqa: E731
     P = pool.Pool(boxes, prm())
     P.start()
     P.capture()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         P.replay()
     P.stream.synchronize()
     if P.status():
-        raise SystemExit(f"device status {P.status()} after warm-up")
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        raise SystemExit(f"device status {P.status()} after the batched warm-up")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     clocks = Clocks(None)
     time.sleep(0.25)
     replicas.barrier()
     ev[0].record(P.stream)
-    for k in range(args.steps):
+    for k in range(steps):
         P.replay()
         ev[k + 1].record(P.stream)
     P.stream.synchronize()
     replicas.barrier()
     clk = clocks.stop()
-    per = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])
-    # replicas: the slowest rank's latencies, the units of all ranks
+    per = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(steps)])
     p50 = replicas.max_over_ranks(float(np.percentile(per, 50)))
     p99 = replicas.max_over_ranks(float(np.percentile(per, 99)))
     rate, mean_ms = replicas.job_throughput(n, float(np.mean(per)))
@@ -476,55 +491,68 @@ def run_batch(args, world: int, rank: int, local: int):
     singles = [pool.Pool([b], prm(), stream=P.stream) for b in boxes]
     for S in singles:
         S.start()
-    for _ in range(2):
-        for S in singles:
-            S.step()
+    for S in singles:
+        S.step()
     P.stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(P.stream)
-    for _ in range(args.steps):
+    for _ in range(plain_steps):
         for S in singles:
             S.step()
     e1.record(P.stream)
     P.stream.synchronize()
-    plain_ms = e0.elapsed_time(e1) / args.steps
+    plain_ms = replicas.max_over_ranks(e0.elapsed_time(e1) / plain_steps)
+    return {"boxes": n_boxes, "particles": n, "steps": steps, "warmup": warmup,
+            "p50_ms": p50, "p99_ms": p99, "mean_ms": mean_ms, "updates_per_s": rate,
+            "plain_per_launch_ms": plain_ms, "plain_updates_per_s": replicas.sum_over_ranks(n) / (plain_ms / 1e3),
+            "plain_steps": plain_steps, "speedup_vs_plain": plain_ms / mean_ms,
+            "tuned": over, "tune_s": tune_s,
+            "gpu_launches": launches_per_step(n, n_boxes, bool(over["flags"] & sph.SPH_FLAG_TREE)) * steps,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                       "reasons": clk["reasons"], "samples": clk["samples"]},
+            "device_status": st}
+
+
+def run_batch(args, world: int, rank: int, local: int):
+    """256 independent boxes (config of the batched workload), printed as their
+    own line (p50 latency as the value)."""
+    n_boxes = int(args.workload[len("batch"):] or 256)
+    b = batch_measure(n_boxes, args.steps, args.warmup, plain_steps=args.steps)
     line = {
-        "metric": "batched SPH step p50/p99 latency (256 boxes)", "value": p50,
+        "metric": f"batched SPH step p50/p99 latency ({n_boxes} boxes)", "value": b["p50_ms"],
         "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "boxes": n_boxes, "particles": n,
+        "config": {"workload": args.workload, "boxes": n_boxes, "particles": b["particles"],
                    "desc": "periodic unit boxes, N log-uniform in [1e3, 1e5], even: jittered "
                            "lattice, odd: 4 Plummer spheres + background",
-                   "tuned": over},
-        "p50_ms": p50, "p99_ms": p99,
-        "particle_updates_per_s": rate,
-        "plain_ms_per_step": plain_ms, "plain_particle_updates_per_s": n / (plain_ms / 1e3),
-        "speedup_vs_plain": plain_ms / mean_ms,
-        "gpu_launches": launches_per_step(n, n_boxes, bool(over["flags"] & sph.SPH_FLAG_TREE)) * args.steps,
-        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
-                   "reasons": clk["reasons"], "samples": clk["samples"]},
-        "device_status": st}
+                   "tuned": b["tuned"]},
+        "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"],
+        "particle_updates_per_s": b["updates_per_s"],
+        "plain_ms_per_step": b["plain_per_launch_ms"], "plain_particle_updates_per_s": b["plain_updates_per_s"],
+        "speedup_vs_plain": b["speedup_vs_plain"],
+        "gpu_launches": b["gpu_launches"], "clocks": b["clocks"], "device_status": b["device_status"]}
     if rank == 0:
         print(json.dumps(line))
 
 
-def run_served(args, world: int, rank: int, local: int):
+def served_measure(n_sims: int, seconds: float, resident: float) -> dict:
     """Served workload: live simulations of two colliding spheres (radii
     0.1-0.3, 10^3-5x10^5 particles log-uniform, relative speed 0.5-2); the
-    device store holds a quarter of them (an HBM budget below the all-resident
-    footprint), the rest wait in pinned host memory and are admitted on
-    request; step requests arrive as a Poisson process and are served with
-    continuous batching (several batches in flight on their own streams).
-    The offered rate is half the saturated throughput measured first.  The same
-    trace is then served one simulation per launch for comparison."""
+    device store holds the fraction `resident` of their particles (an HBM
+    budget below the all-resident footprint), the rest wait in pinned host
+    memory and are admitted on request; step requests arrive as a Poisson
+    process and are served with continuous batching (several batches in flight
+    on their own streams).  Measured: the saturated rate of both paths (every
+    request present at once), a trace at half the batched path's saturated rate
+    (batched only: one simulation per launch cannot sustain it), and a trace at
+    half the plain path's saturated rate, which both sustain, served both ways."""
     import numpy as np
     import torch
 
     from paper_2305_13380_gb300 import build as B
     B.build()
-    from paper_2305_13380_gb300 import inputs, replicas, serve, sph
+    from paper_2305_13380_gb300 import inputs, replicas, serve, sph, tune
 
-    n_sims = int(args.workload[len("served"):] or 1000)
     t_gen = time.perf_counter()
     sims = {s: inputs.two_spheres(seed=s) for s in range(n_sims)}
     gen_s = time.perf_counter() - t_gen
@@ -532,33 +560,42 @@ def run_served(args, world: int, rank: int, local: int):
     largest = max(len(p["x"]) for p in sims.values())
     slots = 3
     batch_cap = max(4 * largest, 4 << 20)
-    # the store holds a fraction of the live simulations' particles: the rest
-    # wait in pinned host memory and are admitted (evicting idle ones) on request
-    store_n = max(int(args.served_resident * total), 2 * largest)
+    store_n = max(int(resident * total), 2 * largest)
     budget = store_n * serve.STATE_BYTES + slots * batch_cap * (serve.STATE_BYTES + serve.SCRATCH_BYTES)
     # grid mode, margin and leaf size tuned on every 64th simulation
-    from paper_2305_13380_gb300 import tune
     sample = [sims[s] for s in range(0, n_sims, 64)]
     over = tune.best_params(sample, key=f"served-sample-{n_sims}")
     prm = sph.sph_default_params(**over)
     srv = serve.Server(budget, store_particles=store_n, slots=slots, batch_particles=batch_cap,
                        params=prm)
-    t_adm = time.perf_counter()
     for s, p in sims.items():
         srv.register(s, p)
-    adm_s = time.perf_counter() - t_adm
     del sims
     ids = list(srv.sims)
-    # warm-up: every slot serves a few batches first
-    srv.run(serve.poisson_trace(6 * slots, rate=1e9, sims=ids, seed=0))
-    srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
-    # saturation: every request present at t = 0
+
+    def reset():
+        srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
+
+    def plain_mode(on: bool, keep=[]):
+        # one simulation per launch on one stream, or continuous batching
+        if on:
+            keep[:] = [srv.slots, srv.max_batch_sims]
+            srv.slots, srv.max_batch_sims = srv.slots[:1], 1
+        else:
+            srv.slots, srv.max_batch_sims = keep
+
+    srv.run(serve.poisson_trace(6 * slots, rate=1e9, sims=ids, seed=0))   # warm-up
+    reset()
     sat = srv.run(serve.poisson_trace(3 * slots * 32, rate=1e9, sims=ids, seed=1))
     cap_rate = sat["requests"] / sat["wall_s"]
+    plain_mode(True)
+    reset()
+    psat = srv.run(serve.poisson_trace(96, rate=1e9, sims=ids, seed=3))
+    plain_mode(False)
+    plain_cap = psat["requests"] / psat["wall_s"]
     rate = 0.5 * cap_rate
-    n_req = max(200, int(rate * args.served_seconds))
-    trace = serve.poisson_trace(n_req, rate=rate, sims=ids, seed=2)
-    srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
+    trace = serve.poisson_trace(max(200, int(rate * seconds)), rate=rate, sims=ids, seed=2)
+    reset()
     up0, ev0 = srv.uploads, srv.evictions
     clocks = Clocks(None)
     time.sleep(0.25)
@@ -566,45 +603,56 @@ def run_served(args, world: int, rank: int, local: int):
     out = srv.run(trace)
     replicas.barrier()
     clk = clocks.stop()
-    # replicas: the slowest rank's latencies, the requests of all ranks
-    out["p50_ms"] = replicas.max_over_ranks(out["p50_ms"])
-    out["p99_ms"] = replicas.max_over_ranks(out["p99_ms"])
-    req_rate, _ = replicas.job_throughput(out["requests"], 1e3 * out["wall_s"])
-    upd_rate = replicas.sum_over_ranks(out["particle_updates_per_s"])
     paging = {"uploads": srv.uploads - up0, "evictions": srv.evictions - ev0}
-    # the same trace, one simulation per launch on one stream
-    srv.finished, srv.n_batches, srv.updates, srv.batch_log = [], 0, 0, []
-    all_slots, srv.slots = srv.slots, srv.slots[:1]
-    srv.max_batch_sims = 1
-    plain = srv.run(trace)
-    srv.slots = all_slots
+    # like for like: a trace that both paths sustain, served both ways
+    low = 0.5 * plain_cap
+    ltrace = serve.poisson_trace(max(100, int(low * seconds)), rate=low, sims=ids, seed=4)
+    reset()
+    both_b = srv.run(ltrace)
+    plain_mode(True)
+    reset()
+    both_p = srv.run(ltrace)
+    plain_mode(False)
+    req_rate, _ = replicas.job_throughput(out["requests"], 1e3 * out["wall_s"])
+    pick = lambda r: {"p50_ms": replicas.max_over_ranks(r["p50_ms"]),  # noqa: E731
+                      "p99_ms": replicas.max_over_ranks(r["p99_ms"]),
+                      "particle_updates_per_s": replicas.sum_over_ranks(r["particle_updates_per_s"]),
+                      "requests": r["requests"]}
+    return {"simulations": n_sims, "particles": total, "resident_particles": store_n,
+            "resident_fraction": store_n / total, "budget_gb": budget / 1e9, "slots": slots,
+            "batch_particles": batch_cap, "generation_s": gen_s, "tuned": over,
+            "saturated_requests_per_s": cap_rate, "plain_saturated_requests_per_s": plain_cap,
+            "rate_per_s": rate, "p50_ms": replicas.max_over_ranks(out["p50_ms"]),
+            "p99_ms": replicas.max_over_ranks(out["p99_ms"]), "mean_ms": out["mean_ms"],
+            "requests": out["requests"], "requests_per_s": req_rate,
+            "particle_updates_per_s": replicas.sum_over_ranks(out["particle_updates_per_s"]),
+            "mean_sims_per_batch": out["mean_sims_per_batch"], "paging": paging,
+            "batches": {k: out[k] for k in ("batches", "batch_sims_mean", "batch_particles_mean",
+                                             "batch_ms_mean", "batch_ms_max")},
+            "both_sustain": {"rate_per_s": low, "batched": pick(both_b), "plain": pick(both_p)},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                       "reasons": clk["reasons"], "samples": clk["samples"]},
+            "device_status": out["device_status"] | both_b["device_status"] | both_p["device_status"]}
+
+
+def run_served(args, world: int, rank: int, local: int):
+    """The served workload printed as its own line (p50 latency as the value)."""
+    n_sims = int(args.workload[len("served"):] or 1000)
+    r = served_measure(n_sims, args.served_seconds, args.served_resident)
     line = {
         "metric": f"served SPH step latency p50/p99 ({n_sims} live simulations)",
-        "value": out["p50_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": world,
-        "steps": out["requests"], "warmup": sat["requests"], "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "simulations": n_sims, "particles_resident": total,
+        "value": r["p50_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": world,
+        "steps": r["requests"], "warmup": 18, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "simulations": n_sims, "particles_resident": r["particles"],
                    "desc": "two uniform spheres per simulation, radii 0.1-0.3, N log-uniform in "
                            "[1e3, 5e5], relative speed 0.5-2, box 2; Poisson step requests",
-                   "rate_per_s": rate, "slots": slots, "batch_particles": batch_cap,
-                   "resident_particles": store_n, "resident_fraction": store_n / total,
-                   "budget_gb": budget / 1e9, "generation_s": gen_s, "admission_s": adm_s,
-                   "tuned": over},
-        "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "mean_ms": out["mean_ms"],
-        "requests_per_s": req_rate,
-        "particle_updates_per_s": upd_rate,
-        "mean_sims_per_batch": out["mean_sims_per_batch"],
-        "paging": paging,
-        "saturated_requests_per_s": cap_rate,
-        "saturated_batches": {k: sat[k] for k in ("batches", "batch_sims_mean", "batch_particles_mean",
-                                                    "batch_ms_mean", "batch_ms_max")},
-        "batches": {k: out[k] for k in ("batches", "batch_sims_mean", "batch_particles_mean",
-                                         "batch_ms_mean", "batch_ms_max")},
-        "plain": {"p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"],
-                  "particle_updates_per_s": plain["particle_updates_per_s"],
-                  "wall_s": plain["wall_s"]},
-        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
-                   "reasons": clk["reasons"], "samples": clk["samples"]},
-        "device_status": out["device_status"] | plain["device_status"],
+                   "rate_per_s": r["rate_per_s"], "slots": r["slots"], "batch_particles": r["batch_particles"],
+                   "resident_particles": r["resident_particles"], "resident_fraction": r["resident_fraction"],
+                   "budget_gb": r["budget_gb"], "generation_s": r["generation_s"], "tuned": r["tuned"]},
+        **{k: r[k] for k in ("p50_ms", "p99_ms", "mean_ms", "requests_per_s", "particle_updates_per_s",
+                             "mean_sims_per_batch", "paging", "saturated_requests_per_s",
+                             "plain_saturated_requests_per_s", "batches", "both_sustain", "clocks",
+                             "device_status")},
     }
     if rank == 0:
         print(json.dumps(line))
@@ -999,32 +1047,47 @@ def run_step(args, world: int, rank: int, local: int):
     if sph.sph_status(e2e_ctx):
         raise SystemExit("device status set in the end-to-end run")
 
-    # roofline of the dominant loop kernel (ALU bound: FP32 pipe, no tensor cores)
+    # roofline of each loop kernel (ALU bound: FP32 pipe, no tensor cores); the
+    # line's "roofline" is the dominant one
     props = torch.cuda.get_device_properties(local)
     peak_mhz = clk["sm_max_mhz"] or 2070.0
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
-    dens_ms = kt["density"][0] / max(kt["density"][1], 1)
-    force_ms = kt["force"][0] / max(kt["force"][1], 1)
-    if dens_ms >= force_ms:
-        kname, kms, flops = "density", dens_ms, pairs_d * mean_pass * F_DENSITY
-    else:
-        kname, kms, flops = "force", force_ms, pairs_f * F_FORCE
-    achieved = flops / (kms / 1e3) / 1e12
-    kfull = f"k_tree_{kname}" if tree else f"k_{kname}"
     fma_peak = fp32_peak_tflops()  # measured FP32 FMA rate of this device
-    roofline = {"bound": "alu", "kernel": kfull, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_measured_fma": fma_peak, "frac_of_measured": achieved / fma_peak,
-                # the records hold the cubic-spline instances' counters
-                "traffic": _traffic(kfull[2:], "tree_loops" if tree else kname) if kern == 0 else None,
-                "peak_basis": (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
-                               f"lanes x 2 flop x {peak_mhz:.0f} MHz (derived; no measured FP32 "
-                               "peak in MEASURED_PEAKS.json)"),
-                "flops_per_launch": flops}
+    loops = {}
+    for kname, flops in (("density", pairs_d * (mean_pass * F_NEWTON + F_DENSITY)),
+                         ("force", pairs_f * F_FORCE)):
+        kms = kt[kname][0] / max(kt[kname][1], 1)
+        achieved = flops / (kms / 1e3) / 1e12
+        kfull = f"k_tree_{kname}" if tree else f"k_{kname}"
+        loops[kfull] = {
+            "bound": "alu", "kernel": kfull, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_measured_fma": fma_peak, "frac_of_measured": achieved / fma_peak,
+            # the records hold the cubic-spline instances' counters
+            "traffic": _traffic(kfull[2:], "tree_loops" if tree else kname) if kern == 0 else None,
+            "peak_basis": (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
+                           f"lanes x 2 flop x {peak_mhz:.0f} MHz (derived; no measured FP32 "
+                           "peak in MEASURED_PEAKS.json)"),
+            "launch_ms": kms, "flops_per_launch": flops,
+            "flops_basis": (f"{pairs_d} pairs x ({mean_pass:.4f} Newton passes x {F_NEWTON} + {F_DENSITY})"
+                            if kname == "density" else f"{pairs_f} pairs x {F_FORCE}")}
+    roofline = max(loops.values(), key=lambda r: r["launch_ms"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p, args.cpu_budget, sphenix, kern)
+
+    # the metric's second half: batched step latency (and a short served run)
+    batched = served = None
+    if (args.workload == "lattice128" and not args.no_batched and not sphenix and kern == 0
+            and not args.axis_sort):
+        ctx.close()
+        e2e_ctx.close()
+        del dbuf, arrays, pool, host
+        torch.cuda.empty_cache()
+        batched = batch_measure(args.batched_boxes, args.batched_steps, 3, plain_steps=2)
+        torch.cuda.empty_cache()
+        served = served_measure(args.served_sims, 3.0, args.served_resident)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1047,7 +1110,10 @@ def run_step(args, world: int, rank: int, local: int):
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "roofline": roofline,
+        "roofline_loops": loops,
         "cpu_baseline": cpu,
+        "batched": batched,
+        "served": served,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         # the loops alone: density (all Newton passes) + force per step
         "density_force_updates_per_s": n / ((kt["density"][0] + kt["force"][0]) / args.steps / 1e3),

@@ -86,6 +86,22 @@ def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-4, tree=False, n_leaf=16
     return out
 
 
+def support_bound(q, k=20):
+    """Upper bound on each particle's support H_j = gamma_K h_j of the cubic
+    spline from the positions alone.  With d_k the distance to the k-th nearest
+    particle (itself the first), H = 2 d_k puts k particles at q <= 1/2, where
+    w(q) >= w(1/2) = 2/pi, so sum_j w(r_ij / H) >= 2k/pi, which reaches
+    (gamma_K eta)^3 = 11.458 (eta = 1.2348) once k >= 18.  The partition
+    condition's left side grows with h, so H_j <= 2 d_k for k = 20.
+    Returns (bound, cKDTree of the positions, positions)."""
+    from scipy.spatial import cKDTree
+    L = float(q["L"])
+    X = np.stack([np.mod(np.asarray(q[c], dtype=np.float64), L) for c in ("x", "y", "z")], 1)
+    tree = cKDTree(X, boxsize=L)
+    d, _ = tree.query(X, k=k)
+    return 2.0 * d[:, -1], tree, X
+
+
 def rel_err(a, b):
     return np.abs(a - b) / np.abs(b)
 

@@ -152,3 +152,16 @@ def test_eos_and_factors(orc):
     # f-factor is the inverse of the grad-h term
     assert np.allclose(1.0 / d["f"], 1 + d["h"] / (3 * d["rho"]) * d["drho_dh"], rtol=1e-13)
     assert np.all((d["B"] >= 0) & (d["B"] <= 1))
+
+
+@pytest.mark.parametrize("kind", ["lattice", "clustered"])
+def test_support_bound_from_positions(orc, kind):
+    """The position-only bound H_j <= 2 d_20 that the full-size GPU tests use
+    to pick the particles a sampled force reads holds for the oracle's h."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from gpu_common import support_bound
+    p = inputs.lattice(12, seed=3) if kind == "lattice" else inputs.clustered(4000, n_spheres=4, seed=2)
+    Hb = support_bound(p)[0]
+    d = orc.density(p, p["h0"])
+    assert np.all(orc.GAMMA_K * d["h"] <= Hb)
