@@ -87,18 +87,6 @@ __device__ __forceinline__ void sums_zero(DensSums& s) {
   s.npair = 0;
 }
 
-__device__ __forceinline__ void sums_add(DensSums& s, const DensSums& t) {
-  s.w += t.w;
-  s.dw += t.dw;
-  s.mw += t.mw;
-  s.mdw += t.mdw;
-  s.div += t.div;
-  s.cx += t.cx;
-  s.cy += t.cy;
-  s.cz += t.cz;
-  s.npair += t.npair;
-}
-
 // Full density sums of one pair (target at pi/vi, source pj/vj) at H.
 template <int K>
 __device__ __forceinline__ void dens_pair(const float4& pi, const float4& vi, const float4& pj,
@@ -123,6 +111,106 @@ __device__ __forceinline__ void dens_pair(const float4& pi, const float4& vi, co
   s.npair += q < 1.0f;
 }
 
+
+// Terms of the Newton passes: w(q) and 3 w + q w'(q), up to the constant
+// factors w_scale<K>() and dw_scale<K>() applied to the sums.  For the cubic
+// spline, with a = (1-q)_+ and b = (1-2q)_+ (saturations, as q >= 0),
+//   w = (8/pi)(2a^3 - b^3),  w'(q) = -(48/pi)(a^2 - b^2),
+//   3w + q w' = (24/pi)(2a^3 - b^3 - 2q (a^2 - b^2)).
+template <int K>
+__device__ __forceinline__ void newton_terms(float q, float& w, float& dw) {
+  if constexpr (K == kKernCubic) {
+    const float a = __saturatef(1.0f - q), b = __saturatef(fmaf(-2.0f, q, 1.0f));
+    const float a2 = a * a, b2 = b * b;
+    w = fmaf(2.0f * a2, a, -b2 * b);
+    dw = fmaf(-2.0f * q, a2 - b2, w);
+  } else {
+    kernel_w_dw<K>(q, w, dw);
+  }
+}
+template <int K>
+__host__ __device__ constexpr float w_scale() {
+  return K == kKernCubic ? kWNorm : 1.0f;
+}
+template <int K>
+__host__ __device__ constexpr float dw_scale() {
+  return K == kKernCubic ? 3.0f * kWNorm : 1.0f;
+}
+
+// Sums of the final pass at the converged h.
+struct FinSums {
+  float mw, mdw, div, cx, cy, cz;
+  int npair;
+};
+
+__device__ __forceinline__ void fin_zero(FinSums& s) {
+  s.mw = s.mdw = s.div = s.cx = s.cy = s.cz = 0.f;
+  s.npair = 0;
+}
+
+// One pair of the final pass.  Cubic spline: the bracketed terms of
+// newton_terms and g~ = (a^2 - b^2)/r, where w'(q)/q = -(48/pi) H g~; the
+// constants are applied once per target by fin_scale.  Other kernels: w,
+// 3w + q w' and g = w'(q)/q.
+template <int K>
+__device__ __forceinline__ void fin_pair(const float4& pi, const float4& vi, const float4& pj, const float4& vj,
+                                         float H, float Hinv, FinSums& s) {
+  const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+  const float q = r2 * rinv * Hinv;
+  float w, dw, g;
+  if constexpr (K == kKernCubic) {
+    const float a = __saturatef(1.0f - q), b = __saturatef(fmaf(-2.0f, q, 1.0f));
+    const float a2 = a * a, b2 = b * b, t = a2 - b2;
+    w = fmaf(2.0f * a2, a, -b2 * b);
+    dw = fmaf(-2.0f * q, t, w);
+    g = t * rinv;
+  } else {
+    kernel_w_g<K>(q, H * rinv, w, g);
+    dw = fmaf(q * q, g, 3.0f * w);
+  }
+  s.mw = fmaf(pj.w, w, s.mw);
+  s.mdw = fmaf(pj.w, dw, s.mdw);
+  const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
+  const float mg = pj.w * g;
+  s.div = fmaf(mg, fmaf(ux, dx, fmaf(uy, dy, uz * dz)), s.div);
+  s.cx = fmaf(mg, fmaf(uz, dy, -uy * dz), s.cx);
+  s.cy = fmaf(mg, fmaf(ux, dz, -uz * dx), s.cy);
+  s.cz = fmaf(mg, fmaf(uy, dx, -ux * dy), s.cz);
+  s.npair += q < 1.0f;
+}
+
+// The final-pass sums in the units of dens_write: sum m w, sum m (3w + q w')
+// and the gradient sums with g = w'(q)/q.
+template <int K>
+__device__ __forceinline__ void fin_scale(FinSums& s, float H) {
+  if constexpr (K == kKernCubic) {
+    s.mw *= kWNorm;
+    s.mdw *= 3.0f * kWNorm;
+    const float gs = -6.0f * kWNorm * H;
+    s.div *= gs;
+    s.cx *= gs;
+    s.cy *= gs;
+    s.cz *= gs;
+  }
+}
+
+__device__ __forceinline__ void fin_combine(FinSums& s, int tpp) {
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    if (o < tpp) {
+      s.mw += __shfl_xor_sync(0xffffffffu, s.mw, o);
+      s.mdw += __shfl_xor_sync(0xffffffffu, s.mdw, o);
+      s.div += __shfl_xor_sync(0xffffffffu, s.div, o);
+      s.cx += __shfl_xor_sync(0xffffffffu, s.cx, o);
+      s.cy += __shfl_xor_sync(0xffffffffu, s.cy, o);
+      s.cz += __shfl_xor_sync(0xffffffffu, s.cz, o);
+      s.npair += __shfl_xor_sync(0xffffffffu, s.npair, o);
+    }
+  }
+}
+
 __device__ __forceinline__ float start_h(float h0, float hcap) {
   const float h = h0 > 0.0f ? h0 : 0.5f * hcap;
   return h > hcap ? hcap : h;
@@ -131,7 +219,7 @@ __device__ __forceinline__ float start_h(float h0, float hcap) {
 // Writes the outputs of one target (sorted index ti) from its sums at h.
 template <int K>
 __device__ __forceinline__ void dens_write(const sphh::DensityArgs& a, const PhysDev& ph, int32_t ti,
-                                           float h, const DensSums& s, float u_i, int passes,
+                                           float h, const FinSums& s, float u_i, int passes,
                                            bool conv, bool atcap) {
   const float H = KernT<K>::gamma * h;
   const float Hinv = 1.0f / H;
@@ -168,23 +256,6 @@ __device__ __forceinline__ float list_r2(const float* lr2, const uint16_t* lj, c
   const float4 pj = spos[lj[at]];
   const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
   return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-}
-
-__device__ __forceinline__ void combine(DensSums& s, int tpp) {
-#pragma unroll
-  for (int o = 1; o < 4; o <<= 1) {
-    if (o < tpp) {
-      s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
-      s.dw += __shfl_xor_sync(0xffffffffu, s.dw, o);
-      s.mw += __shfl_xor_sync(0xffffffffu, s.mw, o);
-      s.mdw += __shfl_xor_sync(0xffffffffu, s.mdw, o);
-      s.div += __shfl_xor_sync(0xffffffffu, s.div, o);
-      s.cx += __shfl_xor_sync(0xffffffffu, s.cx, o);
-      s.cy += __shfl_xor_sync(0xffffffffu, s.cy, o);
-      s.cz += __shfl_xor_sync(0xffffffffu, s.cz, o);
-      s.npair += __shfl_xor_sync(0xffffffffu, s.npair, o);
-    }
-  }
 }
 
 template <int K>
@@ -303,22 +374,21 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
           }
         }
       } else if (valid) {
+        {
 #pragma unroll 1
-        for (int r = 0; r < 9; ++r) {
-          int32_t A0, B0;
-          warp_run(g, T, tx, ty, tz, r, A0, B0);
+          for (int r = 0; r < 9; ++r) {
+            int32_t A0, B0;
+            warp_run(g, T, tx, ty, tz, r, A0, B0);
 #pragma unroll 4
-          for (int32_t k = A0 + sub; k < B0; k += tpp) {
-            const float4 pj = spos[k];
-            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            // branch-free append: the entry is written at the current end and
-            // kept only if in range; once the list is full, writes go to the
-            // scratch row list_cap<K>() (such a lane takes the direct path)
-            const int at = min(cnt, list_cap<K>()) * 32 + lane;
-            if (kCacheR2) lr2[at] = r2;
-            lj[at] = (uint16_t)k;
-            cnt += r2 < R2;
+            for (int32_t k = A0 + sub; k < B0; k += tpp) {
+              const float4 pj = spos[k];
+              const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const int at = min(cnt, list_cap<K>()) * 32 + lane;
+              if (kCacheR2) lr2[at] = r2;
+              lj[at] = (uint16_t)k;
+              cnt += r2 < R2;
+            }
           }
         }
       }
@@ -370,31 +440,30 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
         const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
         float Sw0 = 0.f, Sdw0 = 0.f, Sw1 = 0.f, Sdw1 = 0.f;
-        if (!done && !direct) {
-          int e = 0;
-          for (; e + 1 < cnt; e += 2) {
-            const float r2a = list_r2(lr2, lj, spos, pi, e * 32 + lane);
-            const float r2b = list_r2(lr2, lj, spos, pi, (e + 1) * 32 + lane);
-            const float ria = rsqrtf(fmaxf(r2a, 1e-30f)), rib = rsqrtf(fmaxf(r2b, 1e-30f));
-            const float qa = r2a * ria * Hinv, qb = r2b * rib * Hinv;
-            float wa, dwa, wb, dwb;
-            kernel_w_dw<K>(qa, wa, dwa);
-            kernel_w_dw<K>(qb, wb, dwb);
-            Sw0 += wa;
-            Sw1 += wb;
-            Sdw0 += dwa;
-            Sdw1 += dwb;
-          }
-          if (e < cnt) {
-            const float r2a = list_r2(lr2, lj, spos, pi, e * 32 + lane);
-            const float ria = rsqrtf(fmaxf(r2a, 1e-30f));
-            const float qa = r2a * ria * Hinv;
-            float wa, dwa;
-            kernel_w_dw<K>(qa, wa, dwa);
-            Sw0 += wa;
-            Sdw0 += dwa;
-          }
-        } else if (!done) {
+        const int n_l = (!done && !direct) ? cnt : 0;
+        int e = 0;
+        for (; e + 1 < n_l; e += 2) {
+          const float r2a = list_r2(lr2, lj, spos, pi, e * 32 + lane);
+          const float r2b = list_r2(lr2, lj, spos, pi, (e + 1) * 32 + lane);
+          const float ria = rsqrtf(fmaxf(r2a, 1e-30f)), rib = rsqrtf(fmaxf(r2b, 1e-30f));
+          const float qa = r2a * ria * Hinv, qb = r2b * rib * Hinv;
+          float wa, dwa, wb, dwb;
+          newton_terms<K>(qa, wa, dwa);
+          newton_terms<K>(qb, wb, dwb);
+          Sw0 += wa;
+          Sw1 += wb;
+          Sdw0 += dwa;
+          Sdw1 += dwb;
+        }
+        if (e < n_l) {
+          const float r2a = list_r2(lr2, lj, spos, pi, e * 32 + lane);
+          const float ria = rsqrtf(fmaxf(r2a, 1e-30f));
+          float wa, dwa;
+          newton_terms<K>(r2a * ria * Hinv, wa, dwa);
+          Sw0 += wa;
+          Sdw0 += dwa;
+        }
+        if (!done && direct) {
           for (int r = 0; r < 9; ++r) {
             int32_t A0, B0;
             warp_run(g, T, tx, ty, tz, r, A0, B0);
@@ -405,13 +474,13 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
               const float ri = rsqrtf(fmaxf(r2, 1e-30f));
               const float q = r2 * ri * Hinv;
               float w, dw;
-              kernel_w_dw<K>(q, w, dw);
+              newton_terms<K>(q, w, dw);
               Sw0 += w;
               Sdw0 += dw;
             }
           }
         }
-        float Sw = Sw0 + Sw1, Sdw = Sdw0 + Sdw1;
+        float Sw = w_scale<K>() * (Sw0 + Sw1), Sdw = dw_scale<K>() * (Sdw0 + Sdw1);
         Sw += __shfl_xor_sync(0xffffffffu, Sw, 1);
         Sdw += __shfl_xor_sync(0xffffffffu, Sdw, 1);
         if (tpp == 4) {
@@ -426,33 +495,27 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       // 3. final pass at the converged h
       const float H = KernT<K>::gamma * h;
       const float Hinv = 1.0f / H;
-      DensSums s0, s1;
-      sums_zero(s0);
-      sums_zero(s1);
+      FinSums s0;
+      fin_zero(s0);
       if (valid && !direct) {
-        int e = 0;
-        for (; e + 1 < cnt; e += 2) {
-          const int ka = (int)lj[e * 32 + lane], kb = (int)lj[(e + 1) * 32 + lane];
-          dens_pair<K>(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
-          dens_pair<K>(pi, vi, spos[kb], svel[kb], H, Hinv, s1);
-        }
-        if (e < cnt) {
+        for (int e = 0; e < cnt; ++e) {
           const int ka = (int)lj[e * 32 + lane];
-          dens_pair<K>(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
+          fin_pair<K>(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
         }
-      } else if (valid) {
+      }
+      if (valid && direct) {
         for (int r = 0; r < 9; ++r) {
           int32_t A0, B0;
           warp_run(g, T, tx, ty, tz, r, A0, B0);
           for (int32_t k = A0 + sub; k < B0; k += tpp) {
             const float4 pj = spos[k];
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2) dens_pair<K>(pi, vi, pj, svel[k], H, Hinv, s0);
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2) fin_pair<K>(pi, vi, pj, svel[k], H, Hinv, s0);
           }
         }
       }
-      sums_add(s0, s1);
-      combine(s0, tpp);
+      fin_combine(s0, tpp);
+      fin_scale<K>(s0, H);
       if (valid && sub == 0) {
         dens_write<K>(a, ph, ti, h, s0, vi.w, passes, conv, atcap);
         pair_acc += (unsigned long long)s0.npair;
@@ -530,13 +593,14 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
       {
         const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
-        DensSums s;
-        sums_zero(s);
+        FinSums s;
+        fin_zero(s);
         for (int v0 = 0; v0 < nsrc; v0 += kOvfCap) {
           const int cnt = stage_sources(v0, kOvfCap, nb, lane, put);
-          for (int k = 0; k < cnt; ++k) dens_pair<K>(pi, vi, spos[k], svel[k], H, Hinv, s);
+          for (int k = 0; k < cnt; ++k) fin_pair<K>(pi, vi, spos[k], svel[k], H, Hinv, s);
           __syncwarp();
         }
+        fin_scale<K>(s, H);
         if (valid) {
           dens_write<K>(a, ph, ti, h, s, vi.w, passes, conv, atcap);
           pair_acc += (unsigned long long)s.npair;

@@ -423,6 +423,216 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_force_min: the "Minimal" force with the cubic spline, the path of the
+// plain and batched steps.  Same blocks, rounds, lanes and density lists as
+// k_force, with the pair arithmetic reduced by folding the kernel gradient's
+// constants into per-particle factors when the sources are staged.
+//
+// For the cubic spline, w'(q) = -(48/pi) [(1-q)_+^2 - (1-2q)_+^2], so
+//   grad_i W(r_ij, h) = G x_ij,  G = -kappa t(q) / r,
+//   kappa = (48/pi) / H^4,  t(q) = (1-q)_+^2 - (1-2q)_+^2 >= 0,
+// and with the staged factors P~ = kappa f P / rho^2, F~ = kappa f and
+// B~ = (alpha_V / 2) B the equations of k_force become
+//   nu/2  = -(B~_i + B~_j) mu vsig / (rho_i + rho_j)
+//   a_i  += m_j / r [P~_i t_i + P~_j t_j + nu/2 (F~_i t_i + F~_j t_j)] x_ij
+//   du_i -= m_j / r [P~_i t_i + nu/4 (F~_i t_i + F~_j t_j)] v_ij . x_ij
+// A pair beyond both supports has t_i = t_j = 0 and adds exactly zero, as
+// does the target itself (r = 0, t = 0); neither enters v_sig,i or the pair
+// count (t_i + t_j = 0).  So the lane walks its density list (all sources
+// within one cell size) without testing the reach.  The list is read from
+// global memory into registers, 16 bytes (8 entries) at a time with the next
+// word in flight, so no shared memory is spent on lists and three blocks fit
+// an SM.
+// ---------------------------------------------------------------------------
+constexpr float kKappaCubic = 15.278874536821951f;  // 48 / pi
+constexpr int kMinBlocks = 3;
+
+struct MinTarget {
+  float x, y, z, Hinv, vx, vy, vz, P, F, c, B, rho;
+};
+
+struct MinSums {
+  float ax, ay, az, du, vsig;
+  int npair;
+};
+
+template <bool kCount>
+__device__ __forceinline__ void min_pair(const MinTarget& T, const float4& A, const float4& V, const float4& C,
+                                         float rho_j, float beta, MinSums& s) {
+  const float dx = T.x - A.x, dy = T.y - A.y, dz = T.z - A.z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+  const float r = r2 * rinv;
+  const float qi = r * T.Hinv, qj = r * A.w;
+  // q >= 0, so max(1 - q, 0) and max(1 - 2q, 0) are saturations to [0, 1]
+  const float ai = __saturatef(1.0f - qi), bi = __saturatef(fmaf(-2.0f, qi, 1.0f));
+  const float aj = __saturatef(1.0f - qj), bj = __saturatef(fmaf(-2.0f, qj, 1.0f));
+  const float ti = fmaf(ai, ai, -bi * bi), tj = fmaf(aj, aj, -bj * bj);
+  const float vx = T.vx - V.x, vy = T.vy - V.y, vz = T.vz - V.z;
+  const float vdotx = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+  const float mu = fminf(vdotx, 0.0f) * rinv;
+  const float vs = fmaf(-beta, mu, T.c + C.z);
+  const float nu2 = __fdividef(-(T.B + C.w) * mu * vs, T.rho + rho_j);
+  const float piT = T.P * ti;
+  const float Pt = fmaf(C.x, tj, piT);
+  const float Ft = fmaf(T.F, ti, C.y * tj);
+  const float mr = V.w * rinv;
+  const float S = mr * fmaf(nu2, Ft, Pt);
+  s.ax = fmaf(S, dx, s.ax);
+  s.ay = fmaf(S, dy, s.ay);
+  s.az = fmaf(S, dz, s.az);
+  const float D = fmaf(0.5f * nu2, Ft, piT);
+  s.du = fmaf(-mr * D, vdotx, s.du);
+  const bool in = ti + tj > 0.0f;
+  s.vsig = in ? fmaxf(s.vsig, vs) : s.vsig;
+  if (kCount) s.npair += in ? 1 : 0;
+}
+
+// Staged slot of entry e (0..7) of a 16-byte list word.
+__device__ __forceinline__ int list_entry(const uint4& w, int e) {
+  const uint32_t v = e < 2 ? w.x : (e < 4 ? w.y : (e < 6 ? w.z : w.w));
+  return (int)((e & 1) ? (v >> 16) : (v & 0xffffu));
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kBlkThreads, kMinBlocks) k_force_min(sphh::ForceArgs a, PhysDev ph) {
+  constexpr int kCap = kBlkStageCap;
+  constexpr int kSlots = kCap;
+  extern __shared__ __align__(16) unsigned char msm_raw[];
+  float4* sA = reinterpret_cast<float4*>(msm_raw);  // (x, y, z, 1/H)
+  float4* sB = sA + kSlots;                         // (vx, vy, vz, m)
+  float4* sC = sB + kSlots;                         // (P~, F~, c, B~)
+  float* sR = reinterpret_cast<float*>(sC + kSlots);  // rho
+  StageTable& T = *reinterpret_cast<StageTable*>(sR + kSlots);
+  BlockTargets& BT = *reinterpret_cast<BlockTargets*>(&T + 1);
+  uint16_t* tgt_slot = reinterpret_cast<uint16_t*>(&BT + 1);
+  uint8_t* tgt_cell = reinterpret_cast<uint8_t*>(tgt_slot + kCap);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t total = a.misc_ro[kTotalBlocks];
+  const float half_alpha = 0.5f * ph.alpha_v, beta = ph.beta_v;
+  unsigned long long pair_acc = 0;
+
+  for (int32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    if (a.blk_any != nullptr && a.blk_any[b] == 0) continue;  // no active target
+    const BlockGeom g = block_geom(a.grid, a.n_sims, b);
+    const int32_t nsrc = build_stage_table(g, a.cell_start, T);
+    if (nsrc > kCap) {
+      if (threadIdx.x == 0) a.overflow[atomicAdd(&a.misc[kNumOverflow], 1)] = b;
+      __syncthreads();
+      continue;
+    }
+    build_targets<kKernCubic>(g, T, BT, tgt_slot, tgt_cell, a.act);  // ends with a barrier
+    if (BT.n == 0) continue;
+    for (int32_t v = threadIdx.x; v < nsrc; v += kBlkThreads) {
+      const int k = staged_cell_of(T, v);
+      float ox, oy, oz;
+      staged_offset(g, k, ox, oy, oz);
+      const int32_t j = T.gstart[k] + (v - T.start[k]);
+      const float4 A = a.fA[j];
+      const float4 C = a.fC[j];
+      const float2 D = a.fD[j];
+      const float h2 = D.y * D.y;
+      const float kap = kKappaCubic * h2 * h2;
+      sA[v] = make_float4(A.x + ox, A.y + oy, A.z + oz, D.y);
+      sB[v] = a.fB[j];
+      sC[v] = make_float4(kap * C.x, kap * C.y, C.z, half_alpha * C.w);
+      sR[v] = D.x;
+    }
+    __syncthreads();
+
+    const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
+    const int sub = lane & (tpp - 1);
+    for (int rd = warp; rd < BT.rounds; rd = next_round(BT, lane)) {
+      const int t = lane >> lg;
+      const int32_t e_t = rd * per + t;
+      const bool valid = (t < per) && (e_t < BT.n);
+      int slot = 0, kc = BT.cell_k[0];
+      if (valid) {
+        slot = tgt_slot[e_t];
+        kc = BT.cell_k[tgt_cell[e_t]];
+      }
+      const int32_t ti = T.gstart[kc] + (slot - T.start[kc]);
+      int cnt = valid ? 0xffff : 0;
+      const uint4* src = nullptr;
+      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+      if (valid && a.lists != nullptr) {
+        const int64_t col = (int64_t)ti * 4 + sub;
+        cnt = (int)a.list_cnt[col];
+        src = reinterpret_cast<const uint4*>(a.lists + col * kListRegion);
+        w = src[0];
+      }
+      const bool direct = cnt > kFListCap;
+      const int nw = direct ? 0 : (cnt + 7) >> 3;
+      MinTarget Tg;
+      {
+        const float4 A = sA[slot], V = sB[slot], C = sC[slot];
+        Tg.x = A.x; Tg.y = A.y; Tg.z = A.z; Tg.Hinv = A.w;
+        Tg.vx = V.x; Tg.vy = V.y; Tg.vz = V.z;
+        Tg.P = C.x; Tg.F = C.y; Tg.c = C.z; Tg.B = C.w;
+        Tg.rho = sR[slot];
+      }
+      MinSums s;
+      s.ax = s.ay = s.az = s.du = s.vsig = 0.0f;
+      s.npair = 0;
+      for (int q = 0; q < nw; ++q) {
+        const uint4 wn = q + 1 < nw ? src[q + 1] : w;  // the next word in flight
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          if (8 * q + e < cnt) {
+            const int k = list_entry(w, e);
+            min_pair<kCount>(Tg, sA[k], sB[k], sC[k], sR[k], beta, s);
+          }
+        }
+        w = wn;
+      }
+      if (direct && valid) {
+        // no list, or the density list overflowed: every source of the runs
+        // (the pairs beyond reach add exactly zero)
+        const int tx = kc % g.ex - 1, ty = (kc / g.ex) % g.ey - 1, tz = kc / (g.ex * g.ey) - 1;
+        for (int r = 0; r < 9; ++r) {
+          int32_t A0, B0;
+          warp_run(g, T, tx, ty, tz, r, A0, B0);
+          for (int32_t k = A0 + sub; k < B0; k += tpp) min_pair<kCount>(Tg, sA[k], sB[k], sC[k], sR[k], beta, s);
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1) {
+        if (o < tpp) {
+          s.ax += __shfl_xor_sync(0xffffffffu, s.ax, o);
+          s.ay += __shfl_xor_sync(0xffffffffu, s.ay, o);
+          s.az += __shfl_xor_sync(0xffffffffu, s.az, o);
+          s.du += __shfl_xor_sync(0xffffffffu, s.du, o);
+          s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, o));
+          if (kCount) s.npair += __shfl_xor_sync(0xffffffffu, s.npair, o);
+        }
+      }
+      if (valid && sub == 0) {
+        const int32_t p = a.perm[ti];
+        a.ax[p] = s.ax;
+        a.ay[p] = s.ay;
+        a.az[p] = s.az;
+        a.du_dt[p] = s.du;
+        a.v_sig[p] = s.vsig;
+        if (kCount) pair_acc += (unsigned long long)s.npair;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  if (kCount && a.pairs != nullptr) {
+    unsigned long long v = pair_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v) atomicAdd(a.pairs, v);
+  }
+}
+
+constexpr size_t kMinSmem = (size_t)kBlkStageCap * (3 * sizeof(float4) + sizeof(float)) + sizeof(StageTable) +
+                            sizeof(BlockTargets) +
+                            (size_t)kBlkStageCap * (sizeof(uint16_t) + sizeof(uint8_t));
+static_assert(kMinBlocks * (kMinSmem + 1024) <= 228 * 1024, "three k_force_min blocks per SM");
+
 // Blocks whose neighbourhood exceeded the staging buffer: one warp per target
 // cell, lane = target, the 27 cells streamed through a per-warp buffer with
 // positions relative to the target cell.
@@ -523,11 +733,22 @@ using namespace sphk;
 template <int kFl, int K>
 static cudaError_t launch_force_fk(const ForceArgs& a, const PhysDev& ph, const SphenixDev& x, cudaStream_t st) {
   static int bps = 0, bps_o = 0;
-  constexpr size_t kSmem = force_blk_smem<kFl, K>(), kSmemO = fovf_smem<kFl>();
+  // the Minimal flavour with the cubic spline runs k_force_min
+  constexpr bool kMin = kFl == kFlMinimal && K == kKernCubic;
+  constexpr size_t kSmem = kMin ? kMinSmem : force_blk_smem<kFl, K>(), kSmemO = fovf_smem<kFl>();
   if (!bps) {
-    cudaError_t e = cudaFuncSetAttribute(k_force<kFl, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_force<kFl, K>, kBlkThreads, kSmem);
+    cudaError_t e;
+    if (kMin) {
+      e = cudaFuncSetAttribute(k_force_min<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(k_force_min<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_force_min<false>, kBlkThreads, kSmem);
+    } else {
+      e = cudaFuncSetAttribute(k_force<kFl, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_force<kFl, K>, kBlkThreads, kSmem);
+    }
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_force_overflow<kFl, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemO);
     if (e != cudaSuccess) return e;
@@ -538,7 +759,12 @@ static cudaError_t launch_force_fk(const ForceArgs& a, const PhysDev& ph, const 
   }
   cudaError_t e = cudaMemsetAsync(a.misc + kNumOverflow, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_force<kFl, K><<<a.num_sms * bps, kBlkThreads, kSmem, st>>>(a, ph, x);
+  if (kMin && ph.count_pairs)
+    k_force_min<true><<<a.num_sms * bps, kBlkThreads, kSmem, st>>>(a, ph);
+  else if (kMin)
+    k_force_min<false><<<a.num_sms * bps, kBlkThreads, kSmem, st>>>(a, ph);
+  else
+    k_force<kFl, K><<<a.num_sms * bps, kBlkThreads, kSmem, st>>>(a, ph, x);
   k_force_overflow<kFl, K><<<a.num_sms * bps_o, kThreads, kSmemO, st>>>(a, ph, x);
   return cudaGetLastError();
 }
