@@ -97,6 +97,8 @@ def parse():
                     help="latticeN: the SPHENIX flavour (time-dependent viscosity, conduction)")
     ap.add_argument("--axis-sort", action="store_true",
                     help="uniform grid: sorted interactions in the density filter")
+    ap.add_argument("--symmetric", action="store_true",
+                    help="uniform grid: each force pair evaluated once (SPH_FLAG_SYMMETRIC)")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds of oracle work for the whole --impl reference run")
     ap.add_argument("--no-batched", action="store_true",
@@ -948,7 +950,8 @@ def run_step(args, world: int, rank: int, local: int):
 
     tree = sph.SPH_FLAG_TREE if p["tree"] else 0
     # grid-mode flags of every context of the run
-    mode = tree | (sph.SPH_FLAG_AXIS_SORT if args.axis_sort and not tree else 0)
+    mode = tree | (sph.SPH_FLAG_AXIS_SORT if args.axis_sort and not tree else 0) | \
+        (sph.SPH_FLAG_SYMMETRIC if args.symmetric and not tree else 0)
     # initial density + force (untimed) through the single-simulation calls
     init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | mode, kernel=kern))
     part = sph.particles(t)
@@ -1080,7 +1083,7 @@ def run_step(args, world: int, rank: int, local: int):
     # the metric's second half: batched step latency (and a short served run)
     batched = served = None
     if (args.workload == "lattice128" and not args.no_batched and not sphenix and kern == 0
-            and not args.axis_sort):
+            and not args.axis_sort and not args.symmetric):
         ctx.close()
         e2e_ctx.close()
         del dbuf, arrays, pool, host
@@ -1102,7 +1105,8 @@ def run_step(args, world: int, rank: int, local: int):
                    "l2": "inputs larger than L2: each step touches ~0.5 GB of state and scratch",
                    "parallelism": f"replicas x{world}",
                    "grid": ("nested grids" if tree else
-                            "uniform, sorted interactions" if mode & sph.SPH_FLAG_AXIS_SORT else "uniform")},
+                            "uniform, sorted interactions" if mode & sph.SPH_FLAG_AXIS_SORT else "uniform"),
+                   "force_pairs": "each pair once (symmetric)" if mode & sph.SPH_FLAG_SYMMETRIC else "gather"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "steps": args.e2e_steps},
         "gpu_launches": launches_per_step(n, 1, bool(tree), bool(mode & sph.SPH_FLAG_AXIS_SORT),

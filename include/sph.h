@@ -69,7 +69,7 @@ enum {
   SPH_FLAG_TIMING = 4,      /* record CUDA events around each kernel group   */
   SPH_FLAG_TREE = 8,        /* nested grids below the top cells (Sec. 2.1 and
                                9.1) for smoothing lengths that span decades   */
-  SPH_FLAG_AXIS_SORT = 16   /* uniform grid: sorted interactions (Sec. 2.2).
+  SPH_FLAG_AXIS_SORT = 16,  /* uniform grid: sorted interactions (Sec. 2.2).
                                After each density gather, every cell's
                                particles are ranked along the 13 axes that
                                link it to its neighbours (kAxes x n u16 of
@@ -79,6 +79,21 @@ enum {
                                axis reaches the search radius.  Same
                                neighbour sets as without the flag, summed in
                                another order.  Ignored with SPH_FLAG_TREE.  */
+  SPH_FLAG_SYMMETRIC = 32   /* uniform grid, cubic spline, Minimal force:
+                               each pair within reach is evaluated once
+                               (Sec. 2.1, the pair terms are antisymmetric).
+                               The density publishes only the neighbours
+                               later in sorted order; the force keeps the
+                               target's side and writes the partner's side
+                               as a record, and the records are grouped by
+                               receiver and added in order of their source,
+                               so results do not depend on scheduling and a
+                               simulation's result is the same alone or in a
+                               pool.  Needs context scratch for 64 records
+                               (40 bytes each) per particle; more pairs set
+                               SPH_ST_CAPACITY.  Masked loops, SPHENIX calls
+                               and the other kernels keep the gather form
+                               (they then filter the cells themselves).  */
 };
 
 /* Smoothing kernels (Sec. 3.1), W(r, h) = w(r/H)/H^3, H = gamma_K h, in the

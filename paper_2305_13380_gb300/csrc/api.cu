@@ -78,6 +78,14 @@ struct sph_ctx {
   unsigned long long* rev_count = nullptr;
   int32_t *rev_start = nullptr, *rev_fill = nullptr;
   bool built_tree = false;
+  // symmetric force (SPH_FLAG_SYMMETRIC): the density's lists hold only the
+  // later sources; records of the partners' sides and their grouping
+  bool lists_upper = false;
+  int64_t cap_sym = 0, cap_sym_rec = 0;
+  float4* sym_a = nullptr;
+  int2* sym_b = nullptr;
+  int32_t *sym_recv = nullptr, *sym_order = nullptr, *sym_cnt = nullptr, *sym_off = nullptr;
+  int32_t *sym_cursor = nullptr, *sym_tiles = nullptr, *sym_counter = nullptr;
   // CUDA-event timing of kernel groups (SPH_FLAG_TIMING)
   std::vector<cudaEvent_t> ev_start[SPH_T_COUNT], ev_stop[SPH_T_COUNT];
   int ev_used[SPH_T_COUNT] = {0, 0, 0, 0, 0};
@@ -279,6 +287,48 @@ int ensure_act(sph_ctx* c, int64_t n) {
   c->cap_act = cn;
   c->cap_blk = c->cap_cells;
   return SPH_OK;
+}
+
+void free_sym(sph_ctx* c) {
+  dfree(c->sym_a);
+  dfree(c->sym_b);
+  dfree(c->sym_recv);
+  dfree(c->sym_order);
+  dfree(c->sym_cnt);
+  dfree(c->sym_off);
+  dfree(c->sym_cursor);
+  dfree(c->sym_tiles);
+  dfree(c->sym_counter);
+  c->cap_sym = c->cap_sym_rec = 0;
+}
+
+// Scratch of the symmetric force for n particles: room for 64 records (pairs
+// met from the earlier particle) per particle; a lattice with ~48 neighbours
+// needs ~24, a strongly clustered box on the uniform grid ~60.  More pairs
+// set SPH_ST_CAPACITY.
+constexpr int64_t kSymRecPerParticle = 64;
+int ensure_sym(sph_ctx* c, int64_t n) {
+  if (n <= c->cap_sym) return SPH_OK;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
+  free_sym(c);
+  const int64_t cn = n + n / 4 + 64;
+  const int64_t cr = kSymRecPerParticle * cn;
+  if (!(dalloc(c->sym_a, cr) && dalloc(c->sym_b, cr) && dalloc(c->sym_recv, cr) && dalloc(c->sym_order, cr) &&
+        dalloc(c->sym_cnt, cn) && dalloc(c->sym_off, cn + 1) && dalloc(c->sym_cursor, cn) &&
+        dalloc(c->sym_tiles, sphh::sym_tiles(cn) + 2) && dalloc(c->sym_counter, 1))) {
+    free_sym(c);
+    return SPH_E_NOMEM;
+  }
+  c->cap_sym = cn;
+  c->cap_sym_rec = cr;
+  return SPH_OK;
+}
+
+// The symmetric force serves the Minimal flavour with the cubic spline on the
+// uniform grid, all particles active.
+bool sym_applies(const sph_ctx* c, const uint8_t* active) {
+  return (c->p.flags & SPH_FLAG_SYMMETRIC) && !(c->p.flags & SPH_FLAG_TREE) && !c->built_tree &&
+         c->p.kernel == SPH_KERNEL_CUBIC && active == nullptr;
 }
 
 // SPHENIX scratch for n particles (kept apart from the loops' scratch).
@@ -638,11 +688,14 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   d.list_cnt = c->list_cnt;
   d.axis_order = axis ? c->axis : nullptr;
   d.axis_stride = c->built_n;
+  const bool upper = sym_applies(c, active);
+  d.upper = upper ? 1 : 0;
   t_begin(c, SPH_T_DENSITY);
   const cudaError_t e = sphh::launch_density(d, phys_of(c->p), c->st);
   t_end(c, SPH_T_DENSITY);
   c->lists_valid = (e == cudaSuccess);
   c->lists_mask = active;
+  c->lists_upper = upper;
   return cuda_code(e);
 }
 
@@ -791,9 +844,35 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   a.az = az;
   a.du_dt = du_dt;
   a.v_sig = v_sig;
-  // the density's lists are dealt by the same rounds only under the same mask
-  a.lists = (c->lists_valid && c->lists_mask == active) ? c->lists : nullptr;
+  // the density's lists are dealt by the same rounds only under the same
+  // mask; lists of later sources only (symmetric mode) serve the symmetric
+  // force alone (the other forces then filter the cells themselves)
+  const bool sym = sx == nullptr && sym_applies(c, active);
+  a.lists = (c->lists_valid && c->lists_mask == active && c->lists_upper == sym) ? c->lists : nullptr;
   a.list_cnt = c->list_cnt;
+  if (sym) {
+    // the density published full lists (or none): with the later sources only
+    // the symmetric force would need them too, so walk the cells instead
+    if (!c->lists_upper) a.lists = nullptr;
+    const int rc = ensure_sym(c, c->built_n);
+    if (rc != SPH_OK) return rc;
+    sphh::SymArgs y;
+    y.rec_a = c->sym_a;
+    y.rec_b = c->sym_b;
+    y.recv = c->sym_recv;
+    y.order = c->sym_order;
+    y.cnt = c->sym_cnt;
+    y.off = c->sym_off;
+    y.cursor = c->sym_cursor;
+    y.tile_sum = c->sym_tiles;
+    y.counter = c->sym_counter;
+    y.cap = c->cap_sym_rec;
+    y.status = c->misc + sphk::kStatus;
+    t_begin(c, SPH_T_FORCE);
+    const cudaError_t e = sphh::launch_force_sym(a, y, phys_of(c->p), c->built_n, c->st);
+    t_end(c, SPH_T_FORCE);
+    return cuda_code(e);
+  }
   if (active) {
     const int rc = ensure_act(c, c->built_n);
     if (rc != SPH_OK) return rc;
@@ -887,6 +966,7 @@ void sph_destroy(sph_ctx* c) {
   }
   free_grown(c);
   free_tree(c);
+  free_sym(c);
   dfree(c->sx4);
   dfree(c->dvp);
   dfree(c->act_s);
@@ -957,6 +1037,7 @@ int sph_reserve(sph_ctx* c, int64_t n_total, int32_t n_sims) {
   if (!c || n_total < 0 || n_total > INT32_MAX / 16 || n_sims < 1) return SPH_E_INVAL;
   int rc = ensure(c, n_total, n_sims);
   if (rc == SPH_OK && (c->p.flags & SPH_FLAG_TREE)) rc = ensure_tree(c, n_total, 0);
+  if (rc == SPH_OK && (c->p.flags & SPH_FLAG_SYMMETRIC)) rc = ensure_sym(c, n_total);
   return rc;
 }
 

@@ -413,7 +413,29 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
         const unsigned grp = ((1u << tpp) - 1u) << (lane & ~(tpp - 1));
         pub = pub && (m & grp) == 0u;
       }
-      if (a.lists != nullptr && valid) {
+      if (a.lists != nullptr && valid && a.upper) {
+        // symmetric force pairs: only the sources later in sorted order, so
+        // that each pair is met by one of its two particles
+        const int64_t col = (int64_t)ti * 4 + sub;
+        int kept = 0;
+        if (pub) {
+          uint16_t* dst = a.lists + col * kListRegion;
+          // without a periodic wrap the staged order of a block is the sorted
+          // order (cells z, y, x major to minor in both), so the slot decides
+          const bool wraps = g.c0x == 0 || g.c0y == 0 || g.c0z == 0 || g.c0x + g.wx >= g.G.n_c ||
+                             g.c0y + g.wy >= g.G.n_c || g.c0z + g.wz >= g.G.n_c;
+          for (int e = 0; e < cnt; ++e) {
+            const int slot = lj[e * 32 + lane];
+            bool later = slot > slot_i;
+            if (wraps) {
+              const int kk = staged_cell_of(T, slot);
+              later = T.gstart[kk] + (slot - T.start[kk]) > ti;
+            }
+            if (later) dst[kept++] = (uint16_t)slot;
+          }
+        }
+        a.list_cnt[col] = (uint16_t)(pub ? kept : 0xffff);
+      } else if (a.lists != nullptr && valid) {
         const int64_t col = (int64_t)ti * 4 + sub;
         a.list_cnt[col] = (uint16_t)(pub ? cnt : 0xffff);
         if (pub) {

@@ -139,6 +139,9 @@ struct DensityArgs {
   // blocks with an active target (the others are skipped at once)
   const uint8_t* act = nullptr;
   const uint8_t* blk_any = nullptr;
+  // publish only the list entries later in sorted order than the target
+  // (the symmetric force, sym.cu)
+  int32_t upper = 0;
 };
 cudaError_t launch_density(const DensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 
@@ -174,6 +177,23 @@ cudaError_t launch_sphenix_force(const ForceArgs& a, const sphk::PhysDev& ph, co
 cudaError_t launch_sphenix_gradient(const ForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,
                                     cudaStream_t st);
 cudaError_t launch_limit_bins(const ForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+
+// The symmetric force (sym.cu): records of the partners' sides, grouped by
+// receiver.  Sizes: rec_a, rec_b, recv, order: cap; cnt, cursor: n;
+// off: n + 1; tile_sum: sym_tiles(n) + 1.
+struct SymArgs {
+  float4* rec_a;   // (a_x, a_y, a_z, du/dt) of the receiver
+  int2* rec_b;     // (v_sig bits, source sorted index)
+  int32_t* recv;   // receiver sorted index
+  int32_t* order;  // records by receiver
+  int32_t *cnt, *off, *cursor, *tile_sum;
+  int32_t* counter;
+  int64_t cap;
+  int32_t* status;
+};
+int64_t sym_tiles(int64_t n);
+cudaError_t launch_force_sym(const ForceArgs& a, const SymArgs& y, const sphk::PhysDev& ph, int64_t n,
+                             cudaStream_t st);
 
 // Sub-steps of the time-step hierarchy (hier.cu), one simulation of side box.
 struct HierArgs {

@@ -36,6 +36,7 @@ SPH_FLAG_COUNT_PAIRS = 2
 SPH_FLAG_TIMING = 4
 SPH_FLAG_TREE = 8
 SPH_FLAG_AXIS_SORT = 16
+SPH_FLAG_SYMMETRIC = 32
 SPH_KERNEL_CUBIC, SPH_KERNEL_QUARTIC, SPH_KERNEL_WENDLAND_C2 = 0, 1, 2
 
 TIMING_GROUPS = ("build", "gather", "density", "force", "integrate")

@@ -1,6 +1,7 @@
 """Autotuning of the cell geometry of a pool: grid mode (uniform cells or
-nested grids), cell margin over the largest support, and the leaf size n_leaf
-of the nested grids.
+nested grids), cell margin over the largest support, the leaf size n_leaf
+of the nested grids, and on the uniform grid the force's pair evaluation
+(gather, or each pair once with SPH_FLAG_SYMMETRIC).
 
 Larger cells stage more candidates per target; smaller ones leave less room
 for smoothing lengths to grow before a rebuild is needed; nested grids cost a
@@ -41,6 +42,9 @@ def candidates(sims) -> list[dict]:
     spread = max(float(np.max(s["h0"]) / np.min(s["h0"])) for s in sims)
     if spread < SPREAD_UNIFORM:
         out += [dict(flags=0, cell_margin=m) for m in MARGINS]
+        # each force pair evaluated once (measured slower on this GPU; kept so
+        # that the choice is measured per workload)
+        out += [dict(flags=sph.SPH_FLAG_SYMMETRIC, cell_margin=0.05)]
     return out
 
 
