@@ -97,6 +97,11 @@ def parse():
                     help="latticeN: the SPHENIX flavour (time-dependent viscosity, conduction)")
     ap.add_argument("--axis-sort", action="store_true",
                     help="uniform grid: sorted interactions in the density filter")
+    ap.add_argument("--tune", action="store_true",
+                    help="run the autotuner on the workload (latticeN, clusteredN, batchN) and print its "
+                         "record: the chosen parameters, their time and the defaults' time")
+    ap.add_argument("--lanes-per-target", type=int, default=0, choices=(0, 2, 4),
+                    help="uniform grid: lanes per target of the loops (0: automatic)")
     ap.add_argument("--symmetric", action="store_true",
                     help="uniform grid: each force pair evaluated once (SPH_FLAG_SYMMETRIC)")
     ap.add_argument("--ref-budget", type=float, default=120.0,
@@ -515,6 +520,31 @@ def batch_measure(n_boxes: int, steps: int, warmup: int, plain_steps: int) -> di
             "device_status": st}
 
 
+def run_tune(args, world: int, rank: int, local: int):
+    """The autotuner on one workload: every candidate timed over a few pool
+    steps (CUDA events), the fastest kept; prints the record."""
+    from paper_2305_13380_gb300 import build as B
+    B.build()
+    from paper_2305_13380_gb300 import inputs, tune
+    if args.workload.startswith("batch"):
+        n_boxes = int(args.workload[len("batch"):] or 256)
+        sims = inputs.batch(n_boxes, seed0=0)
+        key = f"batch{n_boxes}"
+    else:
+        p = make_workload(args.workload)
+        sims = [{k: v for k, v in p.items() if k not in ("desc", "tree")}]
+        key = args.workload
+    t0 = time.perf_counter()
+    rec = tune.tune(sims, key=key, steps=max(3, min(args.steps, 10)))
+    line = {"metric": "autotuned step time", "value": rec["best_ms"], "unit": "ms", "higher_is_better": False,
+            "n_gpus": world, "config": {"workload": args.workload, "particles": sum(len(s["x"]) for s in sims)},
+            "best": rec["best"], "default_ms": rec["default_ms"],
+            "gain_vs_default": (rec["default_ms"] / rec["best_ms"]) if rec["default_ms"] else None,
+            "candidates": rec["times"], "tune_s": time.perf_counter() - t0}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_batch(args, world: int, rank: int, local: int):
     """256 independent boxes (config of the batched workload), printed as their
     own line (p50 latency as the value)."""
@@ -674,7 +704,9 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    if args.workload.startswith("batch"):
+    if args.tune:
+        run_tune(args, world, rank, local)
+    elif args.workload.startswith("batch"):
         run_batch(args, world, rank, local)
     elif args.workload.startswith("fof"):
         run_fof(args, world, rank, local)
@@ -952,8 +984,20 @@ def run_step(args, world: int, rank: int, local: int):
     # grid-mode flags of every context of the run
     mode = tree | (sph.SPH_FLAG_AXIS_SORT if args.axis_sort and not tree else 0) | \
         (sph.SPH_FLAG_SYMMETRIC if args.symmetric and not tree else 0)
+    knobs = {"lanes_per_target": args.lanes_per_target}
+    tuned = None
+    if args.workload == "lattice128" and not (args.axis_sort or args.symmetric or args.lanes_per_target or
+                                              sphenix or kern):
+        # the default run takes the autotuner's choice for this workload (cached per GPU)
+        from paper_2305_13380_gb300 import tune
+        sims = [{k: v for k, v in p.items() if k not in ("desc", "tree")}]
+        tuned = tune.best_params(sims, key=args.workload)
+        knobs = {k: v for k, v in tuned.items() if k in ("cell_margin", "lanes_per_target", "n_leaf")}
+        mode = (mode & ~(sph.SPH_FLAG_TREE | sph.SPH_FLAG_SYMMETRIC)) | (tuned.get("flags", 0) & (
+            sph.SPH_FLAG_TREE | sph.SPH_FLAG_SYMMETRIC))
+        tree = mode & sph.SPH_FLAG_TREE
     # initial density + force (untimed) through the single-simulation calls
-    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | mode, kernel=kern))
+    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | mode, kernel=kern, **knobs))
     part = sph.particles(t)
     dout = sph.density_out({k: arrays[k] for k in sph.DENSITY_FIELDS})
     h_in = t["h0"]
@@ -985,7 +1029,7 @@ def run_step(args, world: int, rank: int, local: int):
         else:
             sph.sph_step(c, pl)
 
-    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | mode, kernel=kern))
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | mode, kernel=kern, **knobs))
     pool = sph.pool(sim_offset, box, arrays)
     for _ in range(args.warmup):
         step(ctx, pool)
@@ -1021,7 +1065,7 @@ def run_step(args, world: int, rank: int, local: int):
     value, ms = replicas.job_throughput(n * args.steps, e0.elapsed_time(e1))
 
     # one more step (untimed) that counts pairs and Newton passes
-    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | mode, kernel=kern))
+    cnt = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_COUNT_PAIRS | mode, kernel=kern, **knobs))
     arrays["n_iter"] = torch.zeros(n, dtype=torch.int32, device=dev)
     step(cnt, sph.pool(sim_offset, box, arrays))
     pairs_d, pairs_f = sph.sph_pair_counts(cnt)
@@ -1036,7 +1080,7 @@ def run_step(args, world: int, rank: int, local: int):
     bo = offs["m"]                  # the same without m, which a step does not change
     host = torch.empty(bi, dtype=torch.uint8, pin_memory=True)
     host.copy_(dbuf[:bi])
-    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=mode, kernel=kern))
+    e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=mode, kernel=kern, **knobs))
     for it in range(2 + args.e2e_steps):
         if it == 2:
             torch.cuda.synchronize()
@@ -1106,7 +1150,10 @@ def run_step(args, world: int, rank: int, local: int):
                    "parallelism": f"replicas x{world}",
                    "grid": ("nested grids" if tree else
                             "uniform, sorted interactions" if mode & sph.SPH_FLAG_AXIS_SORT else "uniform"),
-                   "force_pairs": "each pair once (symmetric)" if mode & sph.SPH_FLAG_SYMMETRIC else "gather"},
+                   "force_pairs": "each pair once (symmetric)" if mode & sph.SPH_FLAG_SYMMETRIC else "gather",
+                   "params": {"cell_margin": knobs.get("cell_margin", 0.05),
+                              "lanes_per_target": knobs.get("lanes_per_target", 0),
+                              "tuned": tuned is not None}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "steps": args.e2e_steps},
         "gpu_launches": launches_per_step(n, 1, bool(tree), bool(mode & sph.SPH_FLAG_AXIS_SORT),

@@ -138,6 +138,10 @@ typedef struct sph_params {
   int32_t n_leaf;      /* SPH_FLAG_TREE: a cell with at most n_leaf particles is
                           not split (>= 1)                                        */
   int32_t kernel;      /* SPH_KERNEL_*                                            */
+  int32_t lanes_per_target; /* uniform-grid loops: 0 = automatic (four lanes per
+                          target in rounds of up to 8 targets, else two), 2 or
+                          4 = that many lanes for every target (a tuning knob;
+                          results agree to rounding, as the lanes split the sums) */
 } sph_params;
 
 /* Opaque context: holds the stream, the parameters and the device scratch

@@ -396,6 +396,7 @@ PhysDev phys_of(const sph_params& p) {
   ph.max_h_iter = p.max_h_iter;
   ph.count_pairs = (p.flags & SPH_FLAG_COUNT_PAIRS) ? 1 : 0;
   ph.kernel = p.kernel;
+  ph.lanes = p.lanes_per_target;
   return ph;
 }
 
@@ -434,7 +435,8 @@ bool params_ok(const sph_params& p) {
   return p.box_size > 0 && p.gamma > 1 && p.eta > 0 && p.alpha_v >= 0 && p.beta_v >= 0 &&
          p.eps_balsara > 0 && p.h_tol > 0 && p.cfl > 0 && p.cell_margin >= 0 && p.max_h_iter > 0 &&
          (!(p.flags & SPH_FLAG_TREE) || p.n_leaf >= 1) && p.kernel >= SPH_KERNEL_CUBIC &&
-         p.kernel <= SPH_KERNEL_WENDLAND_C2;
+         p.kernel <= SPH_KERNEL_WENDLAND_C2 &&
+         (p.lanes_per_target == 0 || p.lanes_per_target == 2 || p.lanes_per_target == 4);
 }
 
 int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const double* box,
@@ -925,6 +927,7 @@ void sph_default_params(sph_params* p) {
   p->flags = 0;
   p->n_leaf = 16;
   p->kernel = SPH_KERNEL_CUBIC;
+  p->lanes_per_target = 0;
 }
 
 int sph_create(sph_ctx** out, const sph_params* p, void* stream) {

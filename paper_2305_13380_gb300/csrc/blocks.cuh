@@ -176,10 +176,14 @@ __device__ __forceinline__ int next_round(BlockTargets& B, int lane) {
 // act (sorted order, may be null): only targets with act != 0 are dealt, in
 // the same order; the block's particles are compacted with one ballot per
 // warp and 256 targets at a time.
+//
+// lanes (a tuning knob, the same for the density and the force): 0 = the
+// rule above, 2 or 4 = that many lanes for every target (up to 16 or 8
+// targets a round).
 template <int K = kKernCubic>
 __device__ __forceinline__ void build_targets(const BlockGeom& g, const StageTable& T, BlockTargets& B,
                                               uint16_t* tgt_slot, uint8_t* tgt_cell,
-                                              const uint8_t* __restrict__ act = nullptr) {
+                                              const uint8_t* __restrict__ act = nullptr, int lanes = 0) {
   if (threadIdx.x == 0) {
     int i = 0, run = 0;
     for (int z = 1; z <= g.wz; ++z)
@@ -240,8 +244,8 @@ __device__ __forceinline__ void build_targets(const BlockGeom& g, const StageTab
     B.n = n;
     int per = (n + kBlkWarps - 1) / kBlkWarps;
     per = per < 1 ? 1 : per;
-    if (K != kKernCubic && per > 8) per = 8;
-    const int tpp = per <= 8 ? 4 : 2;
+    if ((K != kKernCubic || lanes == 4) && per > 8) per = 8;
+    const int tpp = lanes == 2 ? 2 : (per <= 8 ? 4 : 2);
     if (per > 16) per = 16;
     B.per = per;
     B.tpp = tpp;

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
     if (a.act != nullptr) {
       // masked: the block's active targets first, and nothing to stage
       // when it has none
-      build_targets<K>(g, T, BT, tgt_slot, tgt_cell, a.act);
+      build_targets<K>(g, T, BT, tgt_slot, tgt_cell, a.act, ph.lanes);
       if (BT.n == 0) continue;
     }
     for (int32_t v = threadIdx.x; v < nsrc; v += kBlkThreads) {
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       svel[v] = a.vel4[j];
     }
     if (a.act == nullptr)
-      build_targets<K>(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+      build_targets<K>(g, T, BT, tgt_slot, tgt_cell, nullptr, ph.lanes);  // ends with a barrier
     else
       __syncthreads();  // the staging
 

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force(sphh::ForceArgs a, Phy
     const float dt = kFl == kFlGradient ? block_dt(a, x, b) : 0.0f;
     // the targets' rounds first (they need only the table), so that each
     // warp's first list is in flight together with the staging loads
-    build_targets<K>(g, T, BT, tgt_slot, tgt_cell, a.act);  // ends with a barrier
+    build_targets<K>(g, T, BT, tgt_slot, tgt_cell, a.act, ph.lanes);  // ends with a barrier
     if (BT.n == 0) continue;  // a masked block without active targets
     const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
     const int sub = lane & (tpp - 1);
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kBlkThreads, kMinBlocks) k_force_min(sphh::For
       __syncthreads();
       continue;
     }
-    build_targets<kKernCubic>(g, T, BT, tgt_slot, tgt_cell, a.act);  // ends with a barrier
+    build_targets<kKernCubic>(g, T, BT, tgt_slot, tgt_cell, a.act, ph.lanes);  // ends with a barrier
     if (BT.n == 0) continue;
     for (int32_t v = threadIdx.x; v < nsrc; v += kBlkThreads) {
       const int k = staged_cell_of(T, v);

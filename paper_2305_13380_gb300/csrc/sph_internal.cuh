@@ -81,6 +81,7 @@ struct PhysDev {
   int32_t max_h_iter;
   int32_t count_pairs;
   int32_t kernel;  // kKern*
+  int32_t lanes;   // lanes per target of the uniform loops (0: automatic)
 };
 
 // Constants of the SPHENIX flavour (Sec. 3.3) and the step dt over which its

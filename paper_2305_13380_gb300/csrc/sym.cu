@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_force_sym(sphh::ForceArgs a,
       __syncthreads();
       continue;
     }
-    build_targets<kKernCubic>(g, T, BT, tgt_slot, tgt_cell);  // ends with a barrier
+    build_targets<kKernCubic>(g, T, BT, tgt_slot, tgt_cell, nullptr, ph.lanes);  // ends with a barrier
     for (int32_t v = threadIdx.x; v < nsrc; v += kBlkThreads) {
       const int k = staged_cell_of(T, v);
       float ox, oy, oz;

@@ -49,7 +49,7 @@ class sph_params(C.Structure):
                 ("alpha_v", C.c_double), ("beta_v", C.c_double), ("eps_balsara", C.c_double),
                 ("h_tol", C.c_double), ("cfl", C.c_double), ("cell_margin", C.c_double),
                 ("max_h_iter", C.c_int32), ("flags", C.c_int32), ("n_leaf", C.c_int32),
-                ("kernel", C.c_int32)]
+                ("kernel", C.c_int32), ("lanes_per_target", C.c_int32)]
 
 
 class sph_cells(C.Structure):

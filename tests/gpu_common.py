@@ -41,11 +41,12 @@ def expected_nc(h0_f32, L, margin=0.05, n=None):
 
 
 def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-4, tree=False, n_leaf=16, h_start=None,
-            axis=False, kernel=0, extra_flags=0):
+            axis=False, kernel=0, extra_flags=0, lanes=0):
     """build -> density -> (rebuild while the status asks) -> force on cuda:0.
     tree: nested grids below the top cells; axis: sorted interactions on the
     uniform grid; h_start: starting guess of h (default p["h0"]); kernel:
-    SPH_KERNEL_* of the context; extra_flags: further SPH_FLAG_* bits."""
+    SPH_KERNEL_* of the context; extra_flags: further SPH_FLAG_* bits; lanes:
+    lanes per target of the uniform loops (0: automatic)."""
     import torch
     from paper_2305_13380_gb300 import sph
     flags = sph.SPH_FLAG_COUNT_PAIRS if count_pairs else 0
@@ -55,7 +56,7 @@ def run_gpu(p, margin=0.05, count_pairs=False, h_tol=1e-4, tree=False, n_leaf=16
         flags |= sph.SPH_FLAG_AXIS_SORT
     flags |= extra_flags
     params = sph.sph_default_params(box_size=float(p["L"]), cell_margin=margin, flags=flags,
-                                    h_tol=h_tol, n_leaf=n_leaf, kernel=kernel)
+                                    h_tol=h_tol, n_leaf=n_leaf, kernel=kernel, lanes_per_target=lanes)
     ctx = sph.Context(params)
     t = sph.to_device(p)
     n = int(t["x"].shape[0])

@@ -82,3 +82,13 @@ def test_new_entry_points_reject_null_arguments_without_gpu(libsph):
     assert L.sph_force_active(None, None, None, None, None, None) == sph.SPH_E_INVAL
     assert L.sph_time_bins(None, None, None, None, None, 0.1, 1.0, 10, None) == sph.SPH_E_INVAL
     assert L.sph_hier_substep(None, None, None, None, 1.0, 4, 0, 1, ctypes.byref(t)) == sph.SPH_E_INVAL
+
+
+def test_lanes_per_target_checked_without_gpu(libsph):
+    import ctypes
+    from paper_2305_13380_gb300 import sph
+    assert sph.sph_default_params().lanes_per_target == 0
+    for bad in (1, 3, 8, -2):
+        p = sph.sph_default_params(lanes_per_target=bad)
+        h = ctypes.c_void_p()
+        assert sph.lib().sph_create(ctypes.byref(h), ctypes.byref(p), None) == sph.SPH_E_INVAL, bad

@@ -205,20 +205,30 @@ def test_bad_arguments_are_rejected():
     torch.cuda.synchronize()
 
 
-def test_full_size_lattice_2M_sampled(orc):
-    # 128^3 jittered lattice, the benchmark's workload and launch shape;
-    # sampled targets are checked one by one against the oracle
+@pytest.mark.parametrize("margin", [0.05, 0.03])
+def test_full_size_lattice_2M_sampled(orc, margin):
+    # 128^3 jittered lattice, the benchmark's workload and launch shape (the
+    # tuned cell margin 0.03 and the default 0.05); sampled targets are checked
+    # one by one against the oracle, the particles their force reads chosen
+    # from the positions alone (the support bound of gpu_common)
+    from gpu_common import support_bound
     p = inputs.lattice(128)
     q = as_f32(p)
-    g = run_gpu(p)
+    g = run_gpu(p, margin=margin)
     rng = np.random.default_rng(0)
     n = len(p["x"])
     tg = np.sort(rng.choice(n, 200, replace=False))
-    # the force of a target needs the density of every neighbour
-    hmax = float(g["h"].max()) * 1.01
-    nb = orc.neighbours(q, tg, np.full(len(tg), 1.825742 * hmax))
-    need = np.unique(np.concatenate([tg] + nb))
+    Hb, tree, X = support_bound(q)
+    need = set(int(t) for t in tg)
+    for t in tg:
+        js = np.array(tree.query_ball_point(X[t], Hb.max()), dtype=np.int64)
+        d = X[js] - X[t]
+        d -= q["L"] * np.round(d / q["L"])
+        r = np.sqrt((d ** 2).sum(1))
+        need.update(int(j) for j in js[r < np.maximum(Hb[t], Hb[js])])
+    need = np.array(sorted(need))
     od_need = orc.density(q, q["h0"], targets=need)
+    assert np.all(1.825742 * od_need["h"] <= Hb[need])
     pos = {int(j): k for k, j in enumerate(need)}
     # oracle force with the oracle density of the needed particles
     state = {k: np.zeros(n) for k in ("h", "rho", "f", "P", "c", "B")}
@@ -233,3 +243,16 @@ def test_full_size_lattice_2M_sampled(orc):
     mom = np.abs([(m * g[k]).sum() for k in ("ax", "ay", "az")])
     scale = (m * np.sqrt(g["ax"] ** 2 + g["ay"] ** 2 + g["az"] ** 2)).sum()
     assert np.all(mom < 1e-5 * scale)
+
+
+@pytest.mark.parametrize("lanes", [2, 4])
+@pytest.mark.parametrize("kernel", [0, 2])
+def test_lanes_per_target_knob(orc, lanes, kernel):
+    # the tuner's threads-per-particle knob: every target gets `lanes` lanes
+    # in the density and the force (the lists are split the same way)
+    p = inputs.lattice(16, seed=5, sigma_v=0.1)
+    q = as_f32(p)
+    g = run_gpu(p, lanes=lanes, kernel=kernel, count_pairs=True)
+    od, of = orc.density_force(q, q["h0"], phys=orc.Physics(kernel=kernel))
+    compare(g, od, of)
+    assert abs(g["pairs"][1] - of["n_pairs"].sum()) <= 1e-4 * of["n_pairs"].sum()
