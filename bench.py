@@ -956,8 +956,6 @@ def run_step(args, world: int, rank: int, local: int):
     # inputs and results with one copy each way.
     sphenix = bool(args.sphenix)
     kern = KERNELS[args.kernel]
-    if sphenix and p["tree"]:
-        raise SystemExit("the SPHENIX flavour runs on the uniform grid (latticeN workloads)")
     f64_keys = ("x", "y", "z")
     # SPHENIX carries alpha_V, alpha_c and the previous divergence from step
     # to step: they join the fields a step reads and updates

@@ -378,7 +378,9 @@ int sph_step(sph_ctx* ctx, const sph_pool* pool);
  *                          [f_i W'(r, h_i) + f_j W'(r, h_j)] / (rho_i + rho_j)
  *               over the force pairs, alpha_c,ij = (P_i alpha_c,i + P_j alpha_c,j)/(P_i + P_j)
  *               (0 if P_i + P_j = 0).
- * Uniform grid only: with SPH_FLAG_TREE these calls return SPH_E_INVAL. */
+ * Both grid modes: with SPH_FLAG_TREE the gradient pass and the force walk
+ * the nested grids' lists and reverse pairs (the gradient pass only the
+ * lists: it reaches r < H_i, inside each target's list radius). */
 typedef struct sph_sphenix_params {
   double alpha_v_max;  /* alpha_V,max (2)                               */
   double ell;          /* viscosity decay length ell (0.05)             */

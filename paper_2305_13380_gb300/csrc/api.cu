@@ -783,7 +783,7 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   if (sx && sx->limit && sphh::launch_gather_bins(c->built_n, c->perm, sx->bins_in, c->sx4, c->st) != cudaSuccess)
     return SPH_E_CUDA;
   t_end(c, SPH_T_GATHER);
-  if (sx && c->built_tree) return SPH_E_INVAL;  // SPHENIX runs on the uniform grid only
+  if (sx && sx->limit && c->built_tree) return SPH_E_INVAL;  // time bins: uniform grid only
   if (c->p.flags & SPH_FLAG_COUNT_PAIRS && !(sx && sx->gradient))
     if (cudaMemsetAsync(c->pairs + 1, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
       return SPH_E_CUDA;
@@ -823,7 +823,22 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
     a.fb_level = c->fb_level;
     a.fb_work = c->misc + sphk::kTreeFbWork;
     t_begin(c, SPH_T_FORCE);
-    const cudaError_t e = sphh::launch_tree_force(a, phys_of(c->p), c->st);
+    cudaError_t e;
+    if (sx) {
+      // SPHENIX on the nested grids: the same lists and reverse pairs, the
+      // fifth record in tree order
+      a.fE = c->sx4;
+      if (sx->gradient) {
+        a.pairs = nullptr;
+        a.alpha_c_out = sx->alpha_c_out;
+        a.lap_u = sx->lap_u;
+        e = sphh::launch_tree_sphenix_gradient(a, phys_of(c->p), sx->x, c->st);
+      } else {
+        e = sphh::launch_tree_sphenix_force(a, phys_of(c->p), sx->x, c->st);
+      }
+    } else {
+      e = sphh::launch_tree_force(a, phys_of(c->p), c->st);
+    }
     t_end(c, SPH_T_FORCE);
     return cuda_code(e);
   }
@@ -1110,7 +1125,6 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
        !pl->div_v || !pl->curl_v || !pl->P || !pl->c || !pl->balsara))
     return SPH_E_INVAL;
   if (X && pl->n_total > 0 && (!alpha_v || !alpha_c)) return SPH_E_INVAL;
-  if (X && (c->p.flags & SPH_FLAG_TREE)) return SPH_E_INVAL;
   int rc = ensure(c, pl->n_total, pl->n_sims);
   if (rc != SPH_OK) return rc;
   if (X) {
@@ -1389,7 +1403,7 @@ int sph_sphenix_gradient(sph_ctx* c, const sph_cells* cells, const sph_particles
                          const sph_sphenix_params* X, double dt, sph_sphenix_state* st) {
   if (!c || !cells || !in || !d || !X || !st || !sphenix_params_ok(*X) || !(dt >= 0.0) || !std::isfinite(dt))
     return SPH_E_INVAL;
-  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1) return SPH_E_INVAL;
   if (in->n == 0) return SPH_OK;
   if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !in->u || !d->h || !d->rho ||
       !d->f || !d->div_v || !d->P || !d->c || !d->balsara || !st->alpha_v || !st->alpha_c || !st->div_v_prev ||
@@ -1418,7 +1432,7 @@ int sph_sphenix_gradient(sph_ctx* c, const sph_cells* cells, const sph_particles
 int sph_force_sphenix(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
                       const float* alpha_v, const float* alpha_c, sph_force_out* out) {
   if (!c || !cells || !in || !d || !out) return SPH_E_INVAL;
-  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1) return SPH_E_INVAL;
   if (in->n == 0) return SPH_OK;
   if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !in->u || !d->h || !d->rho ||
       !d->f || !d->P || !d->c || !d->balsara || !alpha_v || !alpha_c || !out->ax || !out->ay || !out->az ||

@@ -360,8 +360,17 @@ struct TreeForceArgs {
   const int32_t *fb_list, *fb_count;
   const int8_t* fb_level;
   int32_t* fb_work;
+  // SPHENIX: (u, alpha_V, P, alpha_c) per source in tree order; the gradient
+  // pass writes alpha_c (input order) and, if given, lap u
+  const float4* fE = nullptr;
+  float* alpha_c_out = nullptr;
+  float* lap_u = nullptr;
 };
 cudaError_t launch_tree_force(const TreeForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+cudaError_t launch_tree_sphenix_force(const TreeForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,
+                                      cudaStream_t st);
+cudaError_t launch_tree_sphenix_gradient(const TreeForceArgs& a, const sphk::PhysDev& ph,
+                                         const sphk::SphenixDev& x, cudaStream_t st);
 // Exclusive scan of m int32 in place with a host-known length (radix.cu);
 // tmp holds m / 1024 + 2 entries.
 cudaError_t scan_exclusive_host_n(int32_t* a, int64_t m, int32_t* tmp, cudaStream_t st);

@@ -24,6 +24,8 @@
 // pairs are grouped by receiver and sorted by source (deterministic order).
 //
 // Force, one warp per leaf: each target walks its list and its reverse pairs.
+// The same kernels run the SPHENIX force and gradient pass (Sec. 3.3) with a
+// fifth record per source (kTSphenix, kTGradient).
 // Whether a pair is the list's or a reverse pair is decided in the target's
 // own leaf frame with the same arithmetic as the density filter, so no pair is
 // counted twice or dropped at the boundary; emission uses a margin so that the
@@ -734,23 +736,42 @@ __device__ __forceinline__ TRec trec_head(const float4* __restrict__ rec, int32_
   return t;
 }
 
-// One force pair with x_ij = (dx, dy, dz) (same terms as force.cu).
-template <int K>
+// Flavours of the force kernels: the "Minimal" force, the SPHENIX force and
+// the SPHENIX gradient pass (Sec. 3.3; the terms are those of force.cu's
+// flavours, with the fifth record E = (u, alpha_V, P, alpha_c) per source).
+enum : int { kTMin = 0, kTSphenix = 1, kTGradient = 2 };
+
+// One force pair with x_ij = (dx, dy, dz) (same terms as force.cu).  The
+// gradient pass keeps only r < H_i (G_i = 0 beyond): the Laplacian sum
+// (m_j / rho_j)(u_i - u_j) G_i in ax, the largest alpha_V in ay and the
+// largest conduction speed v_c,ij in vsig.
+template <int kFl, int K>
 __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const float4& vi, const float4& ci,
-                                            float Hi, float Hinv_i, float rho_i, const float4& vj,
-                                            const float4& cj, float Hj, float Hinv_j, float rho_j,
-                                            const PhysDev& ph, TFSums& s) {
+                                            const float4& ei, float Hi, float Hinv_i, float rho_i, const float4& vj,
+                                            const float4& cj, const float4& ej, float Hj, float Hinv_j,
+                                            float rho_j, const PhysDev& ph, TFSums& s) {
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float r = r2 * rinv;
-  const float hi2 = Hinv_i * Hinv_i, hj2 = Hinv_j * Hinv_j;
+  const float hi2 = Hinv_i * Hinv_i;
   const float Gi = kernel_g<K>(r * Hinv_i, Hi * rinv) * (hi2 * hi2 * Hinv_i);
-  const float Gj = kernel_g<K>(r * Hinv_j, Hj * rinv) * (hj2 * hj2 * Hinv_j);
   const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
   const float vdotx = fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+  if constexpr (kFl == kTGradient) {
+    s.ax = fmaf(__fdividef(vj.w, rho_j) * (ei.x - ej.x), Gi, s.ax);
+    const float vc = fmaf(fabsf(vdotx), rinv, sqrtf(__fdividef(2.0f * fabsf(ei.z - ej.z), rho_i + rho_j)));
+    const bool in = r2 < Hi * Hi;
+    s.vsig = in ? fmaxf(s.vsig, vc) : s.vsig;
+    s.ay = in ? fmaxf(s.ay, ej.y) : s.ay;
+    s.npair += in;
+    return;
+  }
+  const float hj2 = Hinv_j * Hinv_j;
+  const float Gj = kernel_g<K>(r * Hinv_j, Hj * rinv) * (hj2 * hj2 * Hinv_j);
   const float mu = fminf(vdotx, 0.0f) * rinv;
   const float vs = fmaf(-ph.beta_v, mu, ci.z + cj.z);
-  const float nu = __fdividef(-ph.alpha_v * (ci.w + cj.w) * mu * vs, rho_i + rho_j);
+  const float av = kFl == kTSphenix ? 0.5f * (ei.y + ej.y) : ph.alpha_v;
+  const float nu = __fdividef(-av * (ci.w + cj.w) * mu * vs, rho_i + rho_j);
   const float piG = ci.x * Gi;
   const float visc = fmaf(ci.y, Gi, cj.y * Gj);
   const float mj = vj.w;
@@ -759,28 +780,63 @@ __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const 
   s.ay = fmaf(-sc, dy, s.ay);
   s.az = fmaf(-sc, dz, s.az);
   s.du = fmaf(mj * fmaf(0.25f * nu, visc, piG), vdotx, s.du);
+  if constexpr (kFl == kTSphenix) {
+    // conduction: zero beyond both supports (visc = 0) and for r = 0
+    const float Ps = ei.z + ej.z, rs = rho_i + rho_j;
+    const float ac = Ps > 0.0f ? __fdividef(fmaf(ei.z, ei.w, ej.z * ej.w), Ps) : 0.0f;
+    const float vc = fmaf(fabsf(vdotx), rinv, sqrtf(__fdividef(2.0f * fabsf(ei.z - ej.z), rs)));
+    s.du = fmaf(mj * ac * vc * (ei.x - ej.x) * r, __fdividef(visc, rs), s.du);
+  }
   const float Hm = fmaxf(Hi, Hj);
   const bool in = r2 < Hm * Hm;
   s.vsig = in ? fmaxf(s.vsig, vs) : s.vsig;
   s.npair += in;
 }
 
-// tforce_pair with source j's data from its record (head already loaded).
-template <int K>
+// tforce_pair with source j's data from its record (head already loaded) and,
+// for SPHENIX, its fifth record.
+template <int kFl, int K>
 __device__ __forceinline__ void tforce_rec(float dx, float dy, float dz, const float4& vi, const float4& ci,
-                                           float Hi, float Hinv_i, float rho_i, const float4* __restrict__ rec,
+                                           const float4& ei, float Hi, float Hinv_i, float rho_i,
+                                           const float4* __restrict__ rec, const float4* __restrict__ fE,
                                            int32_t j, const TRec& h, const PhysDev& ph, TFSums& s) {
   const float4* r = rec + 4 * (int64_t)j;
-  tforce_pair<K>(dx, dy, dz, vi, ci, Hi, Hinv_i, rho_i, r[2], r[3], h.q0.w, __frcp_rn(h.q0.w),
-              __int_as_float(h.q1.w), ph, s);
+  const float4 ej = kFl != kTMin ? fE[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  tforce_pair<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, Hinv_i, rho_i, r[2], r[3], ej, h.q0.w, __frcp_rn(h.q0.w),
+                      __int_as_float(h.q1.w), ph, s);
+}
+
+// The result of a target: the force, or the gradient pass's conduction
+// parameter (the Euler step of eq. "artconddt" and its limiters, as in
+// force.cu) and Laplacian.
+template <int kFl>
+__device__ __forceinline__ void tforce_write(const sphh::TreeForceArgs& a, const SphenixDev& x, float dt,
+                                             int32_t ti, float Hi, const float4& ei, const TFSums& s) {
+  const int32_t p = a.perm[ti];
+  if constexpr (kFl == kTGradient) {
+    const float lap = 2.0f * s.ax;
+    const float src = ei.x > 0.0f ? x.beta_c * Hi * lap / sqrtf(ei.x) : 0.0f;
+    const float rate = src - (ei.w - x.ac_min) * s.vsig / Hi;
+    float an = fmaf(dt, rate, ei.w);
+    an = fminf(an, x.ac_max * (1.0f - s.ay / x.av_max));
+    an = fmaxf(an, x.ac_min);
+    a.alpha_c_out[p] = an;
+    if (a.lap_u != nullptr) a.lap_u[p] = lap;
+  } else {
+    a.ax[p] = s.ax;
+    a.ay[p] = s.ay;
+    a.az[p] = s.az;
+    a.du_dt[p] = s.du;
+    a.v_sig[p] = s.vsig;
+  }
 }
 
 __device__ __forceinline__ float3 rec_rel_to(const TGeo& g, const TRec& h, int sc) {
   return rel_to(g, h.q0, h.q1, sc);
 }
 
-template <int K>
-__global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs a, PhysDev ph) {
+template <int kFl, int K>
+__global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs a, PhysDev ph, SphenixDev x) {
   const int lane = threadIdx.x & 31;
   const int t = lane / kTreeTpp, sub = lane % kTreeTpp;
   const int32_t nl = *a.n_leaves;
@@ -788,8 +844,10 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
   for (int32_t li = next_group(a.work, lane); li < nl; li = next_group(a.work, lane)) {
     const TreeLeaf Lf = a.leaves[li];
     const int32_t t_lo = Lf.start, n_t = a.leaves[li + 1].start - Lf.start;
-    const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, Lf.cell)];
+    const int sim = sim_of_cell(a.grid, a.n_sims, Lf.cell);
+    const GridDev G = a.grid[sim];
     const TGeo g = leaf_geo(Lf, G);
+    const float dt = kFl == kTGradient ? (float)(x.dt_dev != nullptr ? x.dt_dev[sim] : x.dt) : 0.0f;
     for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
       const bool valid = t0 + t < n_t;
       const int32_t ti = a.tgt[t_lo + (valid ? t0 + t : 0)];
@@ -799,15 +857,17 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
       const int64_t col = (int64_t)ti * kTreeTpp + sub;
       const int lc = (int)a.list_cnt[col];
       const bool fb = lc == kListFallback;  // written by k_tree_force_fb
+      const float4 ei = kFl != kTMin ? a.fE[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (kFl == kTGradient) s.ay = ei.y;  // alpha_V,max starts at the target's
+      const TRec hi = trec_head(a.rec, ti);
+      const float Hi = hi.q0.w;
       if (valid && !fb) {
-        const TRec hi = trec_head(a.rec, ti);
         const float4 reli = hi.q0;
         const int4 fi = hi.q1;
         const float3 pi = rel_to(g, reli, fi, kNoShift);
         const float4 vi = a.rec[4 * (int64_t)ti + 2];
         const float4 ci = a.rec[4 * (int64_t)ti + 3];
         const float2 di = make_float2(__int_as_float(hi.q1.w), __frcp_rn(hi.q0.w));
-        const float Hi = hi.q0.w;
         const bool direct = lc == kListNone;
         // own reach: the list radius, or the leaf side on the list-free path
         const float C = direct ? g.side : a.lrad[ti];
@@ -820,7 +880,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
             if (j == ti) continue;
             const TRec hj = trec_head(a.rec, j);
             const float3 d = pair_vec(g, reli, fi, hj.q0, hj.q1, unpack_s(je));
-            tforce_rec<K>(d.x, d.y, d.z, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+            tforce_rec<kFl, K>(d.x, d.y, d.z, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
           }
         } else {
           for (int r = 0; r < 27; ++r) {
@@ -831,40 +891,38 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
               const float3 pj = rec_rel_to(g, hj, Rg.shift);
               const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
               if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
-                tforce_rec<K>(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+                tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
             }
           }
         }
-        // reverse pairs beyond the own reach, split between the lanes
-        const int32_t r0 = a.rev_start[ti], r1 = a.rev_start[ti + 1];
-        for (int32_t k = r0 + sub; k < r1; k += kTreeTpp) {
-          const uint32_t je = a.rev[k];
-          const int32_t j = unpack_j(je);
-          const TRec hj = trec_head(a.rec, j);
-          const float3 pj = rec_rel_to(g, hj, unpack_s(je));
-          const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-          if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
-            tforce_rec<K>(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+        // reverse pairs beyond the own reach, split between the lanes (the
+        // gradient pass reaches only H_i <= the own reach: none of them)
+        if (kFl != kTGradient) {
+          const int32_t r0 = a.rev_start[ti], r1 = a.rev_start[ti + 1];
+          for (int32_t k = r0 + sub; k < r1; k += kTreeTpp) {
+            const uint32_t je = a.rev[k];
+            const int32_t j = unpack_j(je);
+            const TRec hj = trec_head(a.rec, j);
+            const float3 pj = rec_rel_to(g, hj, unpack_s(je));
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
+              tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
+          }
         }
       }
       s.ax = gsum(s.ax);
-      s.ay = gsum(s.ay);
+      s.ay = kFl == kTGradient ? gmax(s.ay) : gsum(s.ay);
       s.az = gsum(s.az);
       s.du = gsum(s.du);
       s.vsig = gmax(s.vsig);
       s.npair = gsumi(s.npair);
       if (valid && !fb && sub == 0) {
-        const int32_t p = a.perm[ti];
-        a.ax[p] = s.ax;
-        a.ay[p] = s.ay;
-        a.az[p] = s.az;
-        a.du_dt[p] = s.du;
-        a.v_sig[p] = s.vsig;
+        tforce_write<kFl>(a, x, dt, ti, Hi, ei, s);
         pair_acc += (unsigned long long)s.npair;
       }
     }
   }
-  if (ph.count_pairs) {
+  if (ph.count_pairs && a.pairs != nullptr) {
     unsigned long long v = pair_acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1032,27 +1090,31 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
   if (ph.count_pairs && lane == 0 && pair_acc) atomicAdd(a.pairs, pair_acc);
 }
 
-template <int K>
-__global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceArgs a, PhysDev ph) {
+template <int kFl, int K>
+__global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceArgs a, PhysDev ph, SphenixDev x) {
   const int lane = threadIdx.x & 31;
   const int32_t nq = min(*a.fb_count, (int32_t)a.n_total);
   unsigned long long pair_acc = 0;
   for (int32_t q = next_group(a.fb_work, lane); q < nq; q = next_group(a.fb_work, lane)) {
     const int32_t ti = a.fb_list[q];
     const uint64_t key = a.skey[ti];
-    const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30))];
+    const int sim = sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30));
+    const GridDev G = a.grid[sim];
     const TreeLeaf Lc = cell_at_depth(key, (int)a.fb_level[ti]);
     const TGeo g = leaf_geo(Lc, G);
+    const float dt = kFl == kTGradient ? (float)(x.dt_dev != nullptr ? x.dt_dev[sim] : x.dt) : 0.0f;
     const TRec hi = trec_head(a.rec, ti);
     const float3 pi = rec_rel_to(g, hi, kNoShift);
     const float4 vi = a.rec[4 * (int64_t)ti + 2];
     const float4 ci = a.rec[4 * (int64_t)ti + 3];
+    const float4 ei = kFl != kTMin ? a.fE[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float2 di = make_float2(__int_as_float(hi.q1.w), __frcp_rn(hi.q0.w));
     const float Hi = hi.q0.w;
     const float C2 = g.side * g.side;  // own reach: the cell of the fallback level
     TFSums s;
     s.ax = s.ay = s.az = s.du = s.vsig = 0.f;
     s.npair = 0;
+    if (kFl == kTGradient) s.ay = ei.y;
     for (int r = 0; r < 27; ++r) {
       const TreeRange Rg = neighbour_range(G, Lc, r, a.skey, a.cell_start);
       for (int32_t j = Rg.lo + lane; j < Rg.hi; j += 32) {
@@ -1061,37 +1123,39 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
         const float3 pj = rec_rel_to(g, hj, Rg.shift);
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
-          tforce_rec<K>(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+          tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
       }
     }
-    const int32_t r0 = a.rev_start[ti], r1 = a.rev_start[ti + 1];
-    for (int32_t k = r0 + lane; k < r1; k += 32) {
-      const uint32_t je = a.rev[k];
-      const int32_t j = unpack_j(je);
-      const TRec hj = trec_head(a.rec, j);
-      const float3 pj = rec_rel_to(g, hj, unpack_s(je));
-      const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
-        tforce_rec<K>(dx, dy, dz, vi, ci, Hi, di.y, di.x, a.rec, j, hj, ph, s);
+    if (kFl != kTGradient) {
+      const int32_t r0 = a.rev_start[ti], r1 = a.rev_start[ti + 1];
+      for (int32_t k = r0 + lane; k < r1; k += 32) {
+        const uint32_t je = a.rev[k];
+        const int32_t j = unpack_j(je);
+        const TRec hj = trec_head(a.rec, j);
+        const float3 pj = rec_rel_to(g, hj, unpack_s(je));
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
+          tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
+      }
     }
     s.ax = wsum(s.ax);
-    s.ay = wsum(s.ay);
+    if (kFl == kTGradient) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s.ay = fmaxf(s.ay, __shfl_xor_sync(0xffffffffu, s.ay, o));
+    } else {
+      s.ay = wsum(s.ay);
+    }
     s.az = wsum(s.az);
     s.du = wsum(s.du);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s.vsig = fmaxf(s.vsig, __shfl_xor_sync(0xffffffffu, s.vsig, o));
     s.npair = wsumi(s.npair);
     if (lane == 0) {
-      const int32_t p = a.perm[ti];
-      a.ax[p] = s.ax;
-      a.ay[p] = s.ay;
-      a.az[p] = s.az;
-      a.du_dt[p] = s.du;
-      a.v_sig[p] = s.vsig;
+      tforce_write<kFl>(a, x, dt, ti, Hi, ei, s);
       pair_acc += (unsigned long long)s.npair;
     }
   }
-  if (ph.count_pairs && lane == 0 && pair_acc) atomicAdd(a.pairs, pair_acc);
+  if (ph.count_pairs && a.pairs != nullptr && lane == 0 && pair_acc) atomicAdd(a.pairs, pair_acc);
 }
 
 }  // namespace sphk
@@ -1135,20 +1199,46 @@ static cudaError_t launch_tree_density_k(const TreeDensityArgs& a, const PhysDev
   return cudaGetLastError();
 }
 
-template <int K>
-static cudaError_t launch_tree_force_k(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+template <int kFl, int K>
+static cudaError_t launch_tree_force_k(const TreeForceArgs& a, const PhysDev& ph, const SphenixDev& x,
+                                       cudaStream_t st) {
   static int bps = 0;
   if (!bps) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_force<K>, kTWarps * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_force<kFl, K>, kTWarps * 32, 0);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
   }
   cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.fb_work, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_tree_force<K><<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
-  k_tree_force_fb<K><<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph);
+  k_tree_force<kFl, K><<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph, x);
+  k_tree_force_fb<kFl, K><<<a.num_sms * bps, kTWarps * 32, 0, st>>>(a, ph, x);
   return cudaGetLastError();
+}
+
+template <int kFl>
+static cudaError_t launch_tree_force_fl(const TreeForceArgs& a, const PhysDev& ph, const SphenixDev& x,
+                                        cudaStream_t st) {
+  switch (ph.kernel) {
+    case kKernQuartic:
+      return launch_tree_force_k<kFl, kKernQuartic>(a, ph, x, st);
+    case kKernWendlandC2:
+      return launch_tree_force_k<kFl, kKernWendlandC2>(a, ph, x, st);
+    default:
+      return launch_tree_force_k<kFl, kKernCubic>(a, ph, x, st);
+  }
+}
+
+cudaError_t launch_tree_sphenix_force(const TreeForceArgs& a, const PhysDev& ph, const SphenixDev& x,
+                                      cudaStream_t st) {
+  if (a.fE == nullptr) return cudaErrorInvalidValue;
+  return launch_tree_force_fl<kTSphenix>(a, ph, x, st);
+}
+
+cudaError_t launch_tree_sphenix_gradient(const TreeForceArgs& a, const PhysDev& ph, const SphenixDev& x,
+                                         cudaStream_t st) {
+  if (a.fE == nullptr || a.alpha_c_out == nullptr) return cudaErrorInvalidValue;
+  return launch_tree_force_fl<kTGradient>(a, ph, x, st);
 }
 
 cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cudaStream_t st) {
@@ -1163,14 +1253,7 @@ cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cud
 }
 
 cudaError_t launch_tree_force(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
-  switch (ph.kernel) {
-    case kKernQuartic:
-      return launch_tree_force_k<kKernQuartic>(a, ph, st);
-    case kKernWendlandC2:
-      return launch_tree_force_k<kKernWendlandC2>(a, ph, st);
-    default:
-      return launch_tree_force_k<kKernCubic>(a, ph, st);
-  }
+  return launch_tree_force_fl<kTMin>(a, ph, SphenixDev{}, st);
 }
 
 }  // namespace sphh

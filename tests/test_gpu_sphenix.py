@@ -1,7 +1,8 @@
 """The SPHENIX flavour (Sec. 3.3) on the GPU against the oracle: the viscosity
 update, the gradient pass (Laplacian of u, conduction parameter) and the
-force with conduction, through the C ABI, on lattice and clustered inputs;
-a pool step; and the reduction to the "Minimal" force."""
+force with conduction, through the C ABI, on lattice and clustered inputs, on
+the uniform grid and the nested grids; steps and pools on both; and the
+reduction to the "Minimal" force."""
 import numpy as np
 import pytest
 
@@ -82,11 +83,13 @@ def _run_gpu(p, st, dt, tree=False):
     return out
 
 
-def _check(orc, p, seed, floor=False):
+def _check(orc, p, seed, floor=False, tree=False):
     """floor: bounds include the rounding of the FP32 cell-relative
-    coordinates (needed where cells are many supports wide)."""
+    coordinates (needed where cells are many supports wide); tree: on the
+    nested grids (positions relative to each target's own level: the plain
+    bounds)."""
     q, od0, st, dt = _setup(orc, p, seed)
-    g = _run_gpu(p, st, dt)
+    g = _run_gpu(p, st, dt, tree=tree)
     cell = g["_cell"] if floor else None
     vmax = float(np.sqrt(q["vx"] ** 2 + q["vy"] ** 2 + q["vz"] ** 2).max()) if floor else None
     X = orc.Sphenix()
@@ -175,16 +178,36 @@ def test_sphenix_reduces_to_minimal_force():
         assert np.abs(a - b).max() <= 2e-6 * scale, k
 
 
-def test_sphenix_rejects_nested_grids():
-    from paper_2305_13380_gb300 import sph
-    p = inputs.lattice(8, seed=1)
-    st = {k: np.zeros(len(p["x"]), dtype=np.float32) for k in ("alpha_v", "alpha_c", "div_v_prev", "v_sig")}
-    with pytest.raises(sph.SPHError) as e:
-        _run_gpu(p, st, 0.0, tree=True)
-    assert e.value.code == sph.SPH_E_INVAL
+def test_sphenix_evaluation_clustered_nested_grids(orc):
+    # the clustered case on the nested grids: lists, reverse pairs and the
+    # list-free path carry the fifth record
+    p = inputs.clustered(6000, n_spheres=8, seed=5)
+    _check(orc, p, seed=2, tree=True)
 
 
-def test_sphenix_step_matches_oracle(orc):
+def test_sphenix_evaluation_strongly_clustered_nested_grids(orc):
+    # h over more than 30x (four dense spheres)
+    p = inputs.clustered(6000, n_spheres=4, seed=9)
+    q = as_f32(p)
+    assert q["h0"].max() / q["h0"].min() > 10
+    _check(orc, p, seed=3, tree=True)
+
+
+def test_sphenix_nested_grids_match_uniform_grid(orc):
+    # the same evaluation on both grid modes agrees to the FP32 rounding
+    p = inputs.lattice(14, seed=6, sigma_v=0.05)
+    q, od, st, dt = _setup(orc, p, seed=5)
+    gu = _run_gpu(p, st, dt, tree=False)
+    gt = _run_gpu(p, st, dt, tree=True)
+    for k in ("ax", "ay", "az", "du_dt"):
+        scale = np.sqrt(np.mean(gu[k] ** 2)) + 1e-30
+        assert np.abs(gt[k] - gu[k]).max() <= 2e-5 * scale, k
+    for k in ("alpha_v", "alpha_c", "v_sig"):
+        assert np.allclose(gt[k], gu[k], rtol=2e-5, atol=2e-6), k
+
+
+@pytest.mark.parametrize("tree", [False, True])
+def test_sphenix_step_matches_oracle(orc, tree):
     import torch
     from paper_2305_13380_gb300 import sph
     from test_gpu_step import _oracle_state, _pool
@@ -202,7 +225,8 @@ def test_sphenix_step_matches_oracle(orc):
     arr["div_v"] = torch.tensor(s["div_v"], dtype=torch.float32, device="cuda")
     av = torch.tensor(s["alpha_v"], dtype=torch.float32, device="cuda")
     ac = torch.tensor(s["alpha_c"], dtype=torch.float32, device="cuda")
-    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+    flags = sph.SPH_FLAG_SYNC | (sph.SPH_FLAG_TREE if tree else 0)
+    ctx = sph.Context(sph.sph_default_params(flags=flags))
     pool = sph.pool(off, box, arr)
     sph.sph_step_sphenix(ctx, pool, sph.sph_sphenix_default_params(), av, ac)
     vsig_prev = s["v_sig"].copy()
@@ -234,10 +258,11 @@ def test_sphenix_step_matches_oracle(orc):
     assert err.max() <= 1e-5 + X.alpha_c_max * np.max(lim) / X.alpha_v_max, f"alpha_c: {err.max():.3e}"
 
 
-def test_sphenix_pool_equals_alone(orc):
+@pytest.mark.parametrize("tree", [False, True])
+def test_sphenix_pool_equals_alone(orc, tree):
     """Three simulations with their own time-steps: each one's SPHENIX steps
     are bitwise the same alone and inside a pool (the viscosity and
-    conduction updates take each simulation's own dt)."""
+    conduction updates take each simulation's own dt), on both grid modes."""
     import torch
     from paper_2305_13380_gb300 import sph
     from test_gpu_step import _oracle_state, _pool
@@ -257,7 +282,8 @@ def test_sphenix_pool_equals_alone(orc):
         arr["div_v"] = torch.tensor(np.concatenate([s["div_v"] for s in sts]), device="cuda")
         av = torch.tensor(np.concatenate([s["alpha_v"] for s in sts]), device="cuda")
         ac = torch.tensor(np.concatenate([s["alpha_c"] for s in sts]), device="cuda")
-        ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+        flags = sph.SPH_FLAG_SYNC | (sph.SPH_FLAG_TREE if tree else 0)
+        ctx = sph.Context(sph.sph_default_params(flags=flags))
         for _ in range(3):
             sph.sph_step_sphenix(ctx, sph.pool(off, box, arr), X, av, ac)
         out = {k: v.cpu().numpy() for k, v in arr.items()}
