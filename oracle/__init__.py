@@ -512,7 +512,7 @@ def limit_time_bins(p: dict, h, bins, kernel: int = 0, scale: float = 1.0):
 
 
 def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int, adapt: bool,
-                 cfl: float = 0.1, phys: Physics = Physics()) -> int:
+                 cfl: float = 0.1, phys: Physics = Physics(), wakeup: bool = False, sync=None) -> int:
     """One sub-step of the power-of-two time-step hierarchy (Sec. 2.4), in place
     on the state dict s (float64 arrays: x, y, z, vx, vy, vz and u half-kicked
     for each particle's current step, m, h, ax, ay, az, du_dt, v_sig, the
@@ -525,7 +525,23 @@ def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int
     neighbours' bins -- proposed ones for active neighbours, held ones for
     inactive neighbours; else the old one;
     shortened until the new step divides the tick) and the first half kick of
-    the new step.  Returns the new tick."""
+    the new step.
+
+    The second and third limiters of Sec. 3.4 ("Time-step limiter") end the
+    current step of an inactive particle j at the new tick: its velocity and
+    energy are kicked to the tick with its last a and du/dt, it takes a new bin
+    (shortened until its step divides the tick), the first half kick of that
+    step, and t_begin = tick.
+      wakeup: after the active particles have their new bins, every inactive j
+        with an active force-loop neighbour i (r_ij < max(H_i, H_j)) whose new
+        step is more than 4 times shorter (bin_i - 2 > bin_j) is woken with
+        bin max_i (bin_i - 2) (Saitoh & Makino 2009);
+      sync: a boolean array of flagged particles (say, touched by a source
+        term between sub-steps); a flagged inactive one is synchronised with
+        its CFL bin (adapt; the limiter of the active ones then sees that bin)
+        or its held bin, raised to its wake-up bin if it has one.  The flags
+        are cleared in place.
+    Returns the new tick."""
     n = len(bins)
     step = np.left_shift(np.int64(1), (max_bin - bins).astype(np.int64))
     tau = float(np.ldexp(dt_max, -max_bin))
@@ -545,26 +561,59 @@ def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int
     f = force(pred, s, act, phys)
     for k in ("ax", "ay", "az", "du_dt", "v_sig"):
         s[k][act] = f[k]
+    inactive = np.ones(n, dtype=bool)
+    inactive[act] = False
+    flagged = np.zeros(n, dtype=bool) if sync is None else np.asarray(sync, dtype=bool).copy()
+    synced = flagged & inactive
     if adapt:
         # the limiter compares an active particle's proposed bin with the bins
-        # its force-loop neighbours step in: the proposals of the active ones,
-        # the bins that the inactive ones hold for their current step
+        # its force-loop neighbours step in: the proposals of the active ones
+        # (and of the synchronised ones), the bins that the other inactive
+        # ones hold for their current step
         b0 = time_bins(s["h"], s["v_sig"], cfl, dt_max, max_bin, phys.kernel)
-        held = np.ones(n, dtype=bool)
-        held[act] = False
+        held = inactive & ~synced
         b0[held] = bins[held]
         new = limit_time_bins(pred, s["h"], b0, phys.kernel)[act]
     else:
         new = bins[act].copy()
-    new = np.clip(new, 0, max_bin)
-    for q, i in enumerate(act):
-        b = int(new[q])
+
+    def aligned(b):
+        b = min(max(int(b), 0), max_bin)
         while b < max_bin and t_next % (1 << (max_bin - b)) != 0:
             b += 1
+        return b
+
+    for q, i in enumerate(act):
+        b = aligned(new[q])
         h_old, h_new = 0.5 * step[i] * tau, 0.5 * (1 << (max_bin - b)) * tau
         for k in ("x", "y", "z"):
             s["v" + k][i] += s["a" + k][i] * (h_old + h_new)
         s["u"][i] += s["du_dt"][i] * (h_old + h_new)
         bins[i] = b
         t_begin[i] = t_next
+    # the steps that end early: requested bin of each interrupted particle
+    want = {int(j): int(b0[j]) if adapt else int(bins[j]) for j in np.where(synced)[0]}
+    if wakeup and len(act):
+        X = np.stack([s["x"], s["y"], s["z"]], 1)
+        H = gamma_k(phys.kernel) * np.asarray(s["h"], dtype=np.float64)
+        for j in np.where(inactive)[0]:
+            d = X[act] - X[j]
+            d -= L * np.round(d / L)
+            r = np.sqrt((d * d).sum(1))
+            nb = r < np.maximum(H[act], H[j])
+            if nb.any():
+                w = int(bins[act][nb].max()) - 2
+                if w > bins[j]:
+                    want[int(j)] = max(want.get(int(j), w), w)
+    for j, b in sorted(want.items()):
+        b = aligned(b)
+        # end of the current step at the tick, then the first half of the new
+        w = ((t_next - t_begin[j]) - 0.5 * step[j]) * tau + 0.5 * (1 << (max_bin - b)) * tau
+        for k in ("x", "y", "z"):
+            s["v" + k][j] += s["a" + k][j] * w
+        s["u"][j] += s["du_dt"][j] * w
+        bins[j] = b
+        t_begin[j] = t_next
+    if sync is not None:
+        sync[...] = False
     return t_next

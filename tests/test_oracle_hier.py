@@ -95,3 +95,131 @@ def test_limiter_takes_the_bins_that_inactive_neighbours_hold():
     # a limiter fed with b's recomputed CFL bin (4) would force bin 2
     assert np.all(bins[near] == 1)
     assert np.all(bins[np.arange(n) != b] == 1)
+
+
+def _neighbours(s, i):
+    """Force-loop neighbours of particle i (r < max(H_i, H_j), j != i) by
+    brute force on the unit box."""
+    d = [(np.asarray(s[k]) - s[k][i] + 0.5) % 1.0 - 0.5 for k in "xyz"]
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    H = oracle.GAMMA_K * np.asarray(s["h"])
+    nb = r < np.maximum(H, H[i])
+    nb[i] = False
+    return nb
+
+
+def test_wakeup_ends_the_long_steps_next_to_a_short_one():
+    """Saitoh & Makino wake-up (Sec. 3.4, Delta = 4): particle a steps 1 tick
+    (bin 4); its neighbours on 16- and 8-tick steps (bins 0, 1) differ by more
+    than a factor 4 and are woken at tick 1, those on 4-tick steps (bin 2,
+    exactly a factor 4) are not; the far ones keep their steps.  A woken
+    particle's velocity is then v0 + a (t + step_new / 2) tau, the kick of a
+    step [0, t] followed by the first half kick of the new one."""
+    s = _state()
+    n = len(s["x"])
+    max_bin = 4
+    dt_max = 0.25 * float(np.min(0.1 * oracle.GAMMA_K * s["h"] / s["v_sig"]))
+    tau = np.ldexp(dt_max, -max_bin)
+    a = 0
+    bins = (np.arange(n) % 3).astype(np.int32)
+    bins[a] = max_bin
+    near = _neighbours(s, a)
+    assert near.sum() > 30 and len(set(bins[near])) == 3
+    tb = np.zeros(n, np.int64)
+    v0, u0 = s["vx"].copy(), s["u"].copy()
+    hs = _half_kicked(s, 2.0 ** (max_bin - bins) * tau)
+    vh = hs["vx"].copy()
+    t = oracle.hier_substep(hs, bins, tb, dt_max, max_bin, 0, False, wakeup=True)
+    assert t == 1 and bins[a] == max_bin and tb[a] == 1
+    woken = near & (np.arange(n) % 3 < 2)
+    # the requested bin 2 (4 ticks) does not divide tick 1: shortened to bin 4
+    assert np.all(bins[woken] == max_bin) and np.all(tb[woken] == 1)
+    assert np.allclose(hs["vx"][woken], (v0 + s["ax"] * 1.5 * tau)[woken], rtol=0, atol=1e-15)
+    assert np.allclose(hs["u"][woken], (u0 + s["du_dt"] * 1.5 * tau)[woken], rtol=1e-15)
+    rest = ~woken
+    rest[a] = False
+    assert np.all(tb[rest] == 0) and np.array_equal(bins[rest], (np.arange(n) % 3)[rest])
+    assert np.array_equal(hs["vx"][rest], vh[rest])
+    # the woken particles end their new step with a at tick 2
+    t = oracle.hier_substep(hs, bins, tb, dt_max, max_bin, t, False, wakeup=True)
+    assert t == 2 and np.all(tb[woken] == 2)
+    # without the wake-up nothing but a moves on
+    s2 = _state()
+    b2 = (np.arange(n) % 3).astype(np.int32)
+    b2[a] = max_bin
+    t2 = np.zeros(n, np.int64)
+    hs2 = _half_kicked(s2, 2.0 ** (max_bin - b2) * tau)
+    oracle.hier_substep(hs2, b2, t2, dt_max, max_bin, 0, False)
+    assert np.count_nonzero(t2) == 1
+
+
+def test_sync_puts_a_flagged_particle_back_on_the_timeline():
+    """Synchronisation (Sec. 3.4): a flagged particle in the middle of a
+    16-tick step ends it at the next tick (8, the end of the others' 8-tick
+    steps) and steps on in the longest bin that divides 8; with adapt its CFL
+    bin is taken instead.  The flags are cleared."""
+    s = _state()
+    n = len(s["x"])
+    max_bin = 4
+    dt_max = 0.25 * float(np.min(0.1 * oracle.GAMMA_K * s["h"] / s["v_sig"]))
+    tau = np.ldexp(dt_max, -max_bin)
+    f = 5
+    for adapt in (False, True):
+        s1 = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
+        if adapt:
+            # its CFL step becomes 1.5 dt_max / 16: bin 4
+            s1["v_sig"][f] = 0.1 * oracle.GAMMA_K * s["h"][f] / (1.5 * dt_max / 16.0)
+        bins = np.ones(n, np.int32)
+        bins[f] = 0
+        tb = np.zeros(n, np.int64)
+        hs = _half_kicked(s1, 2.0 ** (max_bin - bins) * tau)
+        sync = np.zeros(n, bool)
+        sync[f] = True
+        t = oracle.hier_substep(hs, bins, tb, dt_max, max_bin, 0, adapt, wakeup=False, sync=sync)
+        assert t == 8 and tb[f] == 8 and not sync.any()
+        want = 4 if adapt else 1
+        assert bins[f] == want
+        v = s["vx"][f] + s["ax"][f] * (8 + 0.5 * 2 ** (max_bin - want)) * tau
+        assert abs(hs["vx"][f] - v) < 1e-15
+
+
+def test_after_a_wakeup_no_neighbour_steps_more_than_4_times_longer():
+    """The invariant the wake-up establishes, in the scenario that needs it: a
+    particle f heated in the middle of its step (u x 10^4, its signal speed
+    x 100) is synchronised, steps in the deepest bin, and at its next end
+    wakes its neighbours, which hold steps 16 times longer.  After every
+    sub-step each force-loop neighbour j of a particle i active at the tick
+    steps at most 4 times longer (bin_j >= bin_i - 2), checked pair by pair;
+    without the wake-up it fails."""
+    def run(wakeup):
+        s = _state(seed=4)
+        n = len(s["x"])
+        max_bin = 6
+        dt_max = 3.0 * float(np.min(0.1 * oracle.GAMMA_K * s["h"] / s["v_sig"]))
+        bins = np.full(n, 2, np.int32)
+        bins[::7] = 3
+        f = 1
+        tb = np.zeros(n, np.int64)
+        hs = _half_kicked(s, 2.0 ** (max_bin - bins) * np.ldexp(dt_max, -max_bin))
+        hs["u"][f] *= 1e4
+        hs["v_sig"][f] *= 100.0
+        sync = np.zeros(n, bool)
+        sync[f] = True
+        t, woke, bad = 0, 0, 0
+        for k in range(4):
+            end = tb + (1 << (max_bin - bins))
+            t = oracle.hier_substep(hs, bins, tb, dt_max, max_bin, t, True, wakeup=wakeup,
+                                    sync=sync if k == 0 else None)
+            if k == 0:
+                assert t == 8 and tb[f] == 8 and bins[f] == max_bin
+            else:
+                woke += int(np.count_nonzero((end != t) & (tb == t)))
+            for i in np.where(end == t)[0]:
+                nb = _neighbours(hs, i)
+                bad += int(np.count_nonzero(bins[nb] < bins[i] - 2))
+        return woke, bad
+
+    woke, bad = run(True)
+    assert woke > 20 and bad == 0
+    woke, bad = run(False)
+    assert woke == 0 and bad > 20
