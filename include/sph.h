@@ -332,14 +332,34 @@ int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
  *   the particles whose step ends at t_next are active: the cells are rebuilt,
  *   the density and force run for them (sph_density_active / sph_force_active),
  *   then each gets the second half kick over its old step, a new bin (with
- *   adapt: that of sph_time_bins with params.cfl, else its old bin; in both
- *   cases shortened until the new step divides t_next), the first half kick
- *   over its new step, and t_begin = t_next.
+ *   SPH_HIER_ADAPT: that of sph_time_bins with params.cfl, limited against the
+ *   bins the inactive neighbours hold; else its old bin; in both cases
+ *   shortened until the new step divides t_next), the first half kick over
+ *   its new step, and t_begin = t_next.
+ * The second and third time-step limiters of the SPH section ("Time-step
+ * limiter") end the current step of an inactive particle j at t_next: its v
+ * and u become the predicted ones at t_next, it takes a new bin (shortened
+ * until its step divides t_next), the first half kick over that step, and
+ * t_begin = t_next.
+ *   SPH_HIER_WAKEUP (Saitoh & Makino 2009): after the active particles have
+ *     their new bins, every inactive j within r_ij < max(H_i, H_j) of an
+ *     active i (FP64 minimum-image distance) whose step is more than 4 times
+ *     longer, bin_j < bin_i - 2, is woken with bin max_i (bin_i - 2);
+ *   sync (device uint8, n, or NULL): flags of particles to synchronise, say
+ *     those a source term changed between sub-steps.  A flagged inactive
+ *     particle ends its step with its CFL bin (SPH_HIER_ADAPT; the limiter of
+ *     the active particles then sees that bin) or its held bin, raised to its
+ *     wake-up bin if it has one.  Every flag is cleared (set to 0).
  * bins (int32) and t_begin (int64) are device arrays of n, updated in place;
- * 0 <= max_bin <= 40.  With SPH_FLAG_SYNC a density that needs larger cells is
- * rebuilt and repeated.  Waits for the stream (it returns t_next). */
+ * 0 <= max_bin <= 40; options: SPH_HIER_* bits (others: SPH_E_INVAL).  With
+ * SPH_FLAG_SYNC a density that needs larger cells is rebuilt and repeated.
+ * Waits for the stream (it returns t_next). */
+enum {
+  SPH_HIER_ADAPT = 1,  /* new bins from the CFL condition and the first limiter */
+  SPH_HIER_WAKEUP = 2  /* the wake-up limiter                                   */
+};
 int sph_hier_substep(sph_ctx* ctx, const sph_pool* pool, int32_t* bins, int64_t* t_begin, double dt_max,
-                     int32_t max_bin, int64_t t_now, int32_t adapt, int64_t* t_next_out);
+                     int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync, int64_t* t_next_out);
 
 /* One kick-drift-kick step of every simulation of the pool (Sec. 2.4):
  *   dt = C_CFL min_i H_i / v_sig,i per simulation (FP64 reduction),

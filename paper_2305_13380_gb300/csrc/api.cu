@@ -67,6 +67,7 @@ struct sph_ctx {
   const uint8_t* lists_mask = nullptr;  // the mask the current lists were built with
   uint8_t* hact = nullptr;   // time-step hierarchy: active mask (input order)
   int32_t* hbin = nullptr;   // proposed bins
+  int32_t* hwake = nullptr;  // wake-up bins
   unsigned long long* htick = nullptr;
   int64_t cap_hier = 0;
   float4* sx4 = nullptr;   // SPHENIX: sorted (u, alpha_V, P, alpha_c)
@@ -257,12 +258,14 @@ int ensure_hier(sph_ctx* c, int64_t n) {
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
   dfree(c->hact);
   dfree(c->hbin);
+  dfree(c->hwake);
   dfree(c->htick);
   c->cap_hier = 0;
   const int64_t cn = n + n / 4 + 64;
-  if (!(dalloc(c->hact, cn) && dalloc(c->hbin, cn) && dalloc(c->htick, 1))) {
+  if (!(dalloc(c->hact, cn) && dalloc(c->hbin, cn) && dalloc(c->hwake, cn) && dalloc(c->htick, 1))) {
     dfree(c->hact);
     dfree(c->hbin);
+    dfree(c->hwake);
     dfree(c->htick);
     return SPH_E_NOMEM;
   }
@@ -991,6 +994,7 @@ void sph_destroy(sph_ctx* c) {
   dfree(c->blk_any);
   dfree(c->hact);
   dfree(c->hbin);
+  dfree(c->hwake);
   dfree(c->htick);
   dfree(c->misc);
   dfree(c->pairs);
@@ -1263,11 +1267,12 @@ int sph_time_bins(sph_ctx* c, const sph_cells* cells, const sph_particles* in, c
 }
 
 int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, double dt_max,
-                     int32_t max_bin, int64_t t_now, int32_t adapt, int64_t* t_next_out) {
+                     int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync_flags, int64_t* t_next_out) {
   if (!c || !pl || !bins || !tbeg || !t_next_out || pl->n_sims != 1 || pl->n_total < 1 ||
       pl->n_total > INT32_MAX / 16 || !(dt_max > 0.0) || !std::isfinite(dt_max) || max_bin < 0 || max_bin > 40 ||
-      t_now < 0)
+      t_now < 0 || (options & ~(SPH_HIER_ADAPT | SPH_HIER_WAKEUP)) != 0)
     return SPH_E_INVAL;
+  const bool adapt = (options & SPH_HIER_ADAPT) != 0, wakeup = (options & SPH_HIER_WAKEUP) != 0;
   if (!pl->sim_offset || !pl->box_size || !pl->x || !pl->y || !pl->z || !pl->vx || !pl->vy || !pl->vz ||
       !pl->u || !pl->m || !pl->h || !pl->ax || !pl->ay || !pl->az || !pl->du_dt || !pl->v_sig || !pl->rho ||
       !pl->f || !pl->div_v || !pl->curl_v || !pl->P || !pl->c || !pl->balsara)
@@ -1307,6 +1312,8 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
   h.t_begin = tbeg;
   h.bin_new = nullptr;
   h.act = c->hact;
+  h.sync = sync_flags;
+  h.wake = nullptr;
   h.t_next = c->htick;
   h.status = c->misc + sphk::kStatus;
   t_begin(c, SPH_T_INTEGRATE);
@@ -1353,6 +1360,27 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
   }
   t_begin(c, SPH_T_INTEGRATE);
   if (sphh::launch_hier_kick(h, c->st) != cudaSuccess) return SPH_E_CUDA;
+  if (wakeup) {
+    // the wake-up pass over the cells of this sub-step's build (the density
+    // made them wide enough for every new H)
+    sphh::WakeArgs w;
+    w.n = n;
+    w.grid = c->grid;
+    w.cell_start = c->cell_start;
+    w.perm = c->perm;
+    w.key = c->key;
+    w.x = pl->x;
+    w.y = pl->y;
+    w.z = pl->z;
+    w.h = pl->h;
+    w.gamma = sphk::kernel_gamma(c->p.kernel);
+    w.act = c->hact;
+    w.bin = bins;
+    w.wake = c->hwake;
+    if (sphh::launch_hier_wake(w, c->st) != cudaSuccess) return SPH_E_CUDA;
+    h.wake = c->hwake;
+  }
+  if ((wakeup || sync_flags != nullptr) && sphh::launch_hier_interrupt(h, c->st) != cudaSuccess) return SPH_E_CUDA;
   t_end(c, SPH_T_INTEGRATE);
   unsigned long long tn = 0;
   if (cudaMemcpyAsync(&tn, c->htick, sizeof(tn), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||

@@ -59,13 +59,99 @@ __global__ void k_hier_drift(sphh::HierArgs a) {
   }
 }
 
-// The limiter's input: the CFL proposal of an active particle, the bin that
-// an inactive particle holds for its current step (the step it takes in the
-// force loops until it ends).
-__global__ void k_hier_held_bins(int64_t n, const uint8_t* __restrict__ act, const int32_t* __restrict__ bin,
-                                 int32_t* __restrict__ prop) {
+// The limiter's input: the CFL proposal of an active particle (and of one
+// flagged for synchronisation, which starts a step at t_next too), the bin
+// that another inactive particle holds for its current step (the step it
+// takes in the force loops until it ends).
+__global__ void k_hier_held_bins(int64_t n, const uint8_t* __restrict__ act, const uint8_t* __restrict__ sync,
+                                 const int32_t* __restrict__ bin, int32_t* __restrict__ prop) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (!act[i]) prop[i] = bin[i];
+    if (!act[i] && !(sync != nullptr && sync[i])) prop[i] = bin[i];
+}
+
+__device__ __forceinline__ int32_t wrap_cell(int32_t k, int32_t nc) {
+  k += k < 0 ? nc : 0;
+  return k >= nc ? k - nc : k;
+}
+
+// The wake-up limiter's neighbour pass (Sec. 3.4, after Saitoh & Makino
+// 2009): once the active particles hold their new bins, every inactive
+// force-loop neighbour j of an active i (r_ij < max(H_i, H_j), minimum image,
+// decided in FP64) whose step is more than 4 times longer, bin_j < bin_i - 2,
+// gets wake[j] = max(wake[j], bin_i - 2).  A warp takes 32 particles at a time
+// and walks the cells around each active one, a lane per candidate; the cells
+// of the build are at least as wide as every H, so the 27 cells around i's
+// (the distinct ones when n_c < 3) hold all its neighbours.
+__global__ void k_hier_wake(sphh::WakeArgs a) {
+  const GridDev G = a.grid[0];
+  const int32_t nc = G.n_c;
+  const int d0 = nc >= 3 ? -1 : 0, d1 = nc >= 3 ? 1 : nc - 1;
+  const double L = G.L;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (((int64_t)gridDim.x * blockDim.x) >> 5) << 5;
+  for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; base < a.n; base += stride) {
+    const int64_t me = base + lane;
+    unsigned m = __ballot_sync(0xffffffffu, me < a.n && a.act[me] != 0);
+    while (m != 0u) {
+      const int64_t i = base + (__ffs((int)m) - 1);
+      m &= m - 1u;
+      const int32_t w = a.bin[i] - 2;
+      if (w <= 0) continue;  // no bin lies below
+      const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
+      const double Hi = a.gamma * (double)a.h[i];
+      const int32_t c = a.key[i] - G.cell_base;
+      const int32_t kx = c % nc, ky = (c / nc) % nc, kz = c / (nc * nc);
+      for (int dz = d0; dz <= d1; ++dz)
+        for (int dy = d0; dy <= d1; ++dy)
+          for (int dx = d0; dx <= d1; ++dx) {
+            const int32_t cn =
+                G.cell_base + wrap_cell(kx + dx, nc) + nc * (wrap_cell(ky + dy, nc) + nc * wrap_cell(kz + dz, nc));
+            const int32_t t1 = a.cell_start[cn + 1];
+            for (int32_t t = a.cell_start[cn] + lane; t < t1; t += 32) {
+              const int32_t j = a.perm[t];
+              if (a.act[j] || a.bin[j] >= w) continue;
+              double ex = a.x[j] - xi, ey = a.y[j] - yi, ez = a.z[j] - zi;
+              ex -= L * rint(ex / L);
+              ey -= L * rint(ey / L);
+              ez -= L * rint(ez / L);
+              const double Hm = fmax(Hi, a.gamma * (double)a.h[j]);
+              if (ex * ex + ey * ey + ez * ez < Hm * Hm) atomicMax(&a.wake[j], w);
+            }
+          }
+    }
+  }
+}
+
+// The steps that end early (Sec. 3.4, second and third limiters): an
+// inactive particle that is woken (wake[i] > bin[i]) or flagged for
+// synchronisation ends its current step at t_next, where its velocity and
+// energy are the predicted ones (its last a and du/dt over the part of the
+// step it ran), and starts a new step there: the flagged one in its CFL bin
+// (adapt) or its held bin, either raised to the wake-up bin, shortened until
+// the step divides t_next, with the first half kick.  Every flag is cleared.
+__global__ void k_hier_interrupt(sphh::HierArgs a) {
+  const int64_t tn = (int64_t)*a.t_next;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool fl = a.sync != nullptr && a.sync[i] != 0;
+    if (fl) a.sync[i] = 0;
+    if (a.act[i]) continue;
+    const int32_t held = a.bin[i], wk = a.wake != nullptr ? a.wake[i] : -1;
+    const bool woken = wk > held;
+    if (!fl && !woken) continue;
+    int32_t b = fl ? (a.bin_new != nullptr ? a.bin_new[i] : held) : wk;
+    b = woken && wk > b ? wk : b;
+    b = b < 0 ? 0 : (b > a.max_bin ? a.max_bin : b);
+    while (b < a.max_bin && tn % step_ticks(b, a.max_bin) != 0) ++b;
+    const float h_new = (float)(0.5 * (double)step_ticks(b, a.max_bin) * a.tau);
+    a.vx[i] = fmaf(a.ax[i], h_new, a.vpx[i]);
+    a.vy[i] = fmaf(a.ay[i], h_new, a.vpy[i]);
+    a.vz[i] = fmaf(a.az[i], h_new, a.vpz[i]);
+    const float u = a.up[i], un = fmaf(a.du_dt[i], h_new, u);
+    a.u[i] = un;
+    if (u < 0.0f || un < 0.0f) atomicOr(a.status, SPH_ST_NEG_U);
+    a.bin[i] = b;
+    a.t_begin[i] = tn;
+  }
 }
 
 // The end of an active particle's step: second half kick over the old step,
@@ -118,7 +204,21 @@ cudaError_t launch_hier_drift(const HierArgs& a, cudaStream_t st) {
 
 cudaError_t launch_hier_held_bins(const HierArgs& a, int32_t* prop, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
-  k_hier_held_bins<<<grid_h(a.n), 256, 0, st>>>(a.n, a.act, a.bin, prop);
+  k_hier_held_bins<<<grid_h(a.n), 256, 0, st>>>(a.n, a.act, a.sync, a.bin, prop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hier_wake(const WakeArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(a.wake, 0xff, (size_t)a.n * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  k_hier_wake<<<grid_h(a.n), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hier_interrupt(const HierArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  k_hier_interrupt<<<grid_h(a.n), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

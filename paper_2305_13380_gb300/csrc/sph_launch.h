@@ -210,14 +210,33 @@ struct HierArgs {
   int64_t* t_begin;
   const int32_t* bin_new;  // proposed bins (nullptr: keep)
   uint8_t* act;            // active mask (scratch, input order)
+  uint8_t* sync;           // synchronisation flags (nullptr: none; cleared)
+  const int32_t* wake;     // wake-up bins (nullptr: no wake-up pass)
   unsigned long long* t_next;
   int32_t* status;
+};
+// The wake-up pass's view of the cells of the last uniform build.
+struct WakeArgs {
+  int64_t n;
+  const sphk::GridDev* grid;
+  const int32_t *cell_start, *perm, *key;
+  const double *x, *y, *z;
+  const float* h;
+  double gamma;  // H / h of the kernel
+  const uint8_t* act;
+  const int32_t* bin;
+  int32_t* wake;  // written: -1, or the largest bin_i - 2 above bin_j
 };
 cudaError_t launch_hier_next(const HierArgs& a, cudaStream_t st);
 cudaError_t launch_hier_drift(const HierArgs& a, cudaStream_t st);
 cudaError_t launch_hier_kick(const HierArgs& a, cudaStream_t st);
-// prop[i] = bin[i] where act[i] == 0 (the limiter's input for inactive particles)
+// prop[i] = bin[i] where act[i] == 0 and i is not flagged for synchronisation
+// (the limiter's input for the particles that keep their step)
 cudaError_t launch_hier_held_bins(const HierArgs& a, int32_t* prop, cudaStream_t st);
+// The wake-up limiter's neighbour pass, and the early end of the steps of the
+// woken and the synchronised particles.
+cudaError_t launch_hier_wake(const WakeArgs& a, cudaStream_t st);
+cudaError_t launch_hier_interrupt(const HierArgs& a, cudaStream_t st);
 
 // Time bins (timebins.cu): the CFL bins of n particles (input order), and the
 // sorted limiter records E[s].x = bin of perm[s].

@@ -37,6 +37,8 @@ SPH_FLAG_TIMING = 4
 SPH_FLAG_TREE = 8
 SPH_FLAG_AXIS_SORT = 16
 SPH_FLAG_SYMMETRIC = 32
+SPH_HIER_ADAPT = 1
+SPH_HIER_WAKEUP = 2
 SPH_KERNEL_CUBIC, SPH_KERNEL_QUARTIC, SPH_KERNEL_WENDLAND_C2 = 0, 1, 2
 
 TIMING_GROUPS = ("build", "gather", "density", "force", "integrate")
@@ -125,7 +127,7 @@ def lib():
                                 C.POINTER(sph_density_out), C.POINTER(sph_force_out)]
         L.sph_step.argtypes = [_P, C.POINTER(sph_pool)]
         L.sph_hier_substep.argtypes = [_P, C.POINTER(sph_pool), _P, _P, C.c_double, C.c_int32, C.c_int64,
-                                       C.c_int32, C.POINTER(C.c_int64)]
+                                       C.c_int32, _P, C.POINTER(C.c_int64)]
         L.sph_time_bins.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
                                     C.POINTER(sph_density_out), _P, C.c_double, C.c_double, C.c_int32, _P]
         L.sph_density_active.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles), _P, _P,
@@ -299,12 +301,15 @@ def sph_force(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_den
 
 
 def sph_hier_substep(ctx: Context, pl: sph_pool, bins, t_begin, dt_max: float, max_bin: int, t_now: int,
-                     adapt: bool = True) -> int:
-    """One sub-step of the time-step hierarchy; returns the new tick."""
+                     adapt: bool = True, wakeup: bool = False, sync=None) -> int:
+    """One sub-step of the time-step hierarchy; returns the new tick.  sync is
+    an optional uint8 device tensor of flags (cleared by the call)."""
     t_next = C.c_int64(0)
+    opts = (SPH_HIER_ADAPT if adapt else 0) | (SPH_HIER_WAKEUP if wakeup else 0)
     _check(lib().sph_hier_substep(ctx.handle, C.byref(pl), _ptr(bins, torch.int32), _ptr(t_begin, torch.int64),
-                                  C.c_double(dt_max), C.c_int32(max_bin), C.c_int64(t_now), C.c_int32(1 if adapt else 0),
-                                  C.byref(t_next)), "sph_hier_substep")
+                                  C.c_double(dt_max), C.c_int32(max_bin), C.c_int64(t_now), C.c_int32(opts),
+                                  None if sync is None else _ptr(sync, torch.uint8), C.byref(t_next)),
+           "sph_hier_substep")
     return int(t_next.value)
 
 

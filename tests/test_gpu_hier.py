@@ -120,3 +120,67 @@ def test_adaptive_bins(orc):
     if np.array_equal(gb.cpu().numpy(), bins):
         g = {k: v.cpu().numpy() for k, v in arr.items()}
         _compare(g, s, 1.0 / 12)
+
+
+def _heated(orc, seed, heat):
+    """A lattice box on bins 2 and 3 (64- and 32-tick steps of max_bin 8) in
+    which particle f is heated in the middle of its step (u x heat^2 and its
+    signal speed x heat, as a source term would leave it) and flagged."""
+    s = _state(orc, seed)
+    n = len(s["x"])
+    max_bin = 8
+    dt_max = 3.0 * float(np.min(0.1 * orc.GAMMA_K * s["h"] / s["v_sig"]))
+    bins = np.full(n, 2, np.int32)
+    bins[::7] = 3
+    _start(s, bins, dt_max, max_bin)
+    f = 1
+    s["u"][f] = float(np.float32(s["u"][f] * heat * heat))
+    s["v_sig"][f] = float(np.float32(s["v_sig"][f] * heat))
+    return s, bins, dt_max, max_bin, f
+
+
+@pytest.mark.parametrize("adapt", [False, True])
+def test_sync_and_wakeup(orc, adapt):
+    """The synchronisation step and the wake-up limiter (Sec. 3.4) against the
+    oracle over five sub-steps: the flagged particle ends its step at the
+    first tick, and (adapt) its deep bin wakes its neighbours at its next end;
+    without adapt the bins stay fixed and only the synchronisation acts (a
+    mild heating, which the fixed steps can carry)."""
+    import torch
+    from paper_2305_13380_gb300 import sph
+    s, bins, dt_max, max_bin, f = _heated(orc, 6, 10.0 if adapt else 1.2)
+    n = len(s["x"])
+    arr, pool = _pool(s)
+    gb = torch.tensor(bins, device="cuda")
+    gt = torch.zeros(n, dtype=torch.int64, device="cuda")
+    sync_g = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    sync_g[f] = 1
+    sync_o = np.zeros(n, bool)
+    sync_o[f] = True
+    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+    tb = np.zeros(n, np.int64)
+    t = tg = 0
+    exact, woken = True, 0
+    for k in range(5):
+        end = tb + (1 << (max_bin - bins))
+        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=adapt, wakeup=True,
+                                  sync=sync_g if k == 0 else None)
+        t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, adapt, wakeup=True,
+                             sync=sync_o if k == 0 else None)
+        assert tg == t
+        g_bins, g_tb = gb.cpu().numpy(), gt.cpu().numpy()
+        assert np.all(g_tb % (1 << (max_bin - g_bins)) == 0)
+        if k == 0:
+            assert int(sync_g.sum()) == 0 and t == 32 and g_tb[f] == 32
+            assert g_bins[f] == bins[f] and bins[f] >= (5 if adapt else 3)
+        else:
+            woken += int(np.count_nonzero((end != t) & (tb == t)))
+        assert np.mean((g_bins == bins) & (g_tb == tb)) > 0.995
+        if not (np.array_equal(g_bins, bins) and np.array_equal(g_tb, tb)):
+            exact = False   # a CFL bin at an edge: the two timelines part
+            break
+    if adapt:
+        assert woken > 20
+    if exact:
+        g = {k: v.cpu().numpy() for k, v in arr.items()}
+        _compare(g, s, 1.0 / 12)
