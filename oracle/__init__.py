@@ -512,7 +512,8 @@ def limit_time_bins(p: dict, h, bins, kernel: int = 0, scale: float = 1.0):
 
 
 def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int, adapt: bool,
-                 cfl: float = 0.1, phys: Physics = Physics(), wakeup: bool = False, sync=None) -> int:
+                 cfl: float = 0.1, phys: Physics = Physics(), wakeup: bool = False, sync=None,
+                 predict: bool = False) -> int:
     """One sub-step of the power-of-two time-step hierarchy (Sec. 2.4), in place
     on the state dict s (float64 arrays: x, y, z, vx, vy, vz and u half-kicked
     for each particle's current step, m, h, ax, ay, az, du_dt, v_sig, the
@@ -541,6 +542,13 @@ def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int
         its CFL bin (adapt; the limiter of the active ones then sees that bin)
         or its held bin, raised to its wake-up bin if it has one.  The flags
         are cleared in place.
+    predict: the drift also carries every particle's smoothing length and
+    density over the interval with its last velocity divergence held fixed,
+    dh/dt = h div_v / 3 and the continuity equation drho/dt = -rho div_v
+    (h e^(div_v dt / 3), rho e^(-div_v dt)), and its pressure and sound speed
+    from the equation of state (Sec. 3.2) at the predicted density and u.  The
+    active particles' values are then replaced by their density loop (h is
+    its starting guess).
     Returns the new tick."""
     n = len(bins)
     step = np.left_shift(np.int64(1), (max_bin - bins).astype(np.int64))
@@ -554,6 +562,12 @@ def hier_substep(s: dict, bins, t_begin, dt_max: float, max_bin: int, t_now: int
     w = ((t_next - t_begin) - 0.5 * step) * tau
     pred = dict(L=L, x=s["x"], y=s["y"], z=s["z"], m=s["m"], vx=s["vx"] + s["ax"] * w,
                 vy=s["vy"] + s["ay"] * w, vz=s["vz"] + s["az"] * w, u=s["u"] + s["du_dt"] * w)
+    if predict:
+        dv = np.asarray(s["div_v"], dtype=np.float64) * dt
+        s["h"] = s["h"] * np.exp(dv / 3.0)
+        s["rho"] = s["rho"] * np.exp(-dv)
+        s["P"] = (phys.gamma - 1.0) * pred["u"] * s["rho"]
+        s["c"] = np.sqrt(phys.gamma * s["P"] / s["rho"])
     act = np.where(t_begin + step == t_next)[0]
     d = density(pred, s["h"], act, phys)
     for k in ("h", "rho", "f", "P", "c", "B", "div_v"):

@@ -223,3 +223,70 @@ def test_after_a_wakeup_no_neighbour_steps_more_than_4_times_longer():
     assert woke > 20 and bad == 0
     woke, bad = run(False)
     assert woke == 0 and bad > 20
+
+
+def _expanding_blob(kappa=1.0, n=12, d=0.02):
+    """A perfect lattice blob (n^3, spacing d) in the middle of the unit box,
+    expanding homologously, v = kappa (x - centre), with a and du/dt zero.
+    Its interior (three layers in) is scale-invariant: after a time t its
+    positions are (1 + kappa t) times further apart, so its exact SPH h and
+    rho are h0 (1 + kappa t) and rho0 (1 + kappa t)^-3."""
+    i = np.arange(n)
+    g = np.stack(np.meshgrid(i, i, i, indexing="ij"), -1).reshape(-1, 3)
+    X = 0.5 + (g - 0.5 * (n - 1)) * d
+    N = len(X)
+    s = dict(L=1.0, x=X[:, 0].copy(), y=X[:, 1].copy(), z=X[:, 2].copy(),
+             vx=kappa * (X[:, 0] - 0.5), vy=kappa * (X[:, 1] - 0.5), vz=kappa * (X[:, 2] - 0.5),
+             m=np.full(N, 1.0 / N), u=np.ones(N))
+    dens = oracle.density(s, np.full(N, 1.2348 * d))
+    for k in ("h", "rho", "f", "P", "c", "B", "div_v"):
+        s[k] = dens[k].copy()
+    for k in ("ax", "ay", "az", "du_dt"):
+        s[k] = np.zeros(N)
+    s["v_sig"] = np.full(N, 1.0)
+    interior = np.all((g >= 3) & (g <= n - 4), 1)
+    return s, interior
+
+
+def test_prediction_follows_a_homologous_expansion():
+    """predict: an inactive particle's h and rho are carried by its last
+    divergence, h e^(div dt/3) and rho e^(-div dt).  In an expanding lattice
+    blob the exact values are h0 (1 + k t) and rho0 (1 + k t)^-3; with the
+    measured divergence div = 3 k (1 + eps) the prediction is off by
+    3 |eps| k t plus second order.  Held values (no prediction) are off at
+    first order; the mass within a smoothing volume, rho h^3, is conserved;
+    P and c follow the equation of state."""
+    kappa = 1.0
+    for kt in (0.02, 0.01):
+        s, inner = _expanding_blob(kappa)
+        N = len(s["x"])
+        h0, rho0 = s["h"].copy(), s["rho"].copy()
+        eps = s["div_v"][inner] / (3.0 * kappa) - 1.0
+        assert np.abs(eps).max() < 0.05
+        max_bin = 4
+        dt_max = kt / kappa * 2 ** max_bin             # one tick = t
+        bins = np.zeros(N, np.int32)
+        bins[0] = max_bin                              # a corner particle sets the tick
+        tb = np.zeros(N, np.int64)
+        s["du_dt"][:] = 0.5
+        u_half = s["u"].copy()
+        t = oracle.hier_substep(s, bins, tb, dt_max, max_bin, 0, False, predict=True)
+        assert t == 1 and tb[inner].max() == 0
+        # an inactive particle's u at the tick: its half-kicked u less the
+        # part of the half kick beyond the tick, (step / 2 - t) du/dt
+        u_t = u_half - 0.5 * ((2 ** max_bin) / 2 - 1) * (dt_max / 2 ** max_bin)
+        g = 1.0 + kappa * kt
+        bound = 3.0 * np.abs(eps) * kappa * kt + 6.0 * (kappa * kt) ** 2
+        assert np.all(np.abs(s["rho"][inner] / (rho0[inner] / g ** 3) - 1.0) <= bound)
+        assert np.all(np.abs(s["h"][inner] / (h0[inner] * g) - 1.0) <= bound / 3.0)
+        # without the prediction the held values are off by ~3 k t and k t
+        assert np.all(np.abs(rho0[inner] / (rho0[inner] / g ** 3) - 1.0) > 2.5 * kappa * kt)
+        assert np.allclose(s["rho"][inner] * s["h"][inner] ** 3, rho0[inner] * h0[inner] ** 3, rtol=1e-12)
+        P = (5.0 / 3.0 - 1.0) * u_t * s["rho"]
+        assert np.allclose(s["P"][inner], P[inner], rtol=1e-12)
+        assert np.allclose(s["c"][inner], np.sqrt(5.0 / 3.0 * P / s["rho"])[inner], rtol=1e-12)
+        # and the truth itself: the oracle's density of the drifted blob
+        if kt == 0.01:
+            tru = oracle.density(s, s["h"], targets=np.where(inner)[0])
+            assert np.allclose(tru["rho"], rho0[inner] / g ** 3, rtol=1e-9)
+            assert np.allclose(tru["h"], h0[inner] * g, rtol=1e-9)
