@@ -984,8 +984,8 @@ def run_step(args, world: int, rank: int, local: int):
         (sph.SPH_FLAG_SYMMETRIC if args.symmetric and not tree else 0)
     knobs = {"lanes_per_target": args.lanes_per_target}
     tuned = None
-    if args.workload == "lattice128" and not (args.axis_sort or args.symmetric or args.lanes_per_target or
-                                              sphenix or kern):
+    if args.workload in ("lattice128", "clustered2M") and not (args.axis_sort or args.symmetric or
+                                                               args.lanes_per_target or sphenix or kern):
         # the default run takes the autotuner's choice for this workload (cached per GPU)
         from paper_2305_13380_gb300 import tune
         sims = [{k: v for k, v in p.items() if k not in ("desc", "tree")}]

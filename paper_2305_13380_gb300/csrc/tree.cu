@@ -158,7 +158,7 @@ __global__ void k_tree_neigh(const TreeLeaf* __restrict__ leaves, const int32_t*
 }
 
 // Per particle in tree order: the fine integer position (kTreeFine sub-cells
-// per top cell, over the whole box), the FP32 offset from that sub-cell's
+// per top cell, over the whole box) with the reverse-pair threshold, the FP32 offset from that sub-cell's
 // corner (differences of positions stay exact at the leaf scale) with the
 // mass, the velocity with u, the starting h, and the list radius
 // min(leaf side, kListReach * gamma_K * h).
@@ -184,13 +184,16 @@ __global__ void k_tree_gather(int64_t n, const int32_t* __restrict__ perm, const
     const int32_t gy = ky * kTreeFine + (int32_t)compact3(mc >> 1);
     const int32_t gz = kz * kTreeFine + (int32_t)compact3(mc >> 2);
     const double sf = G.cell / (double)kTreeFine;
-    fine[s] = make_int4(gx, gy, gz, 0);
+    const float hp = h[p];
+    const float R = fminf(leaf_side[s], list_reach * gamma_k * hp);
+    // w: the list radius lowered by a margin of the leaf side (the reverse
+    // pairs' threshold, read with the fine position)
+    fine[s] = make_int4(gx, gy, gz, __float_as_int(R - 0x1p-18f * leaf_side[s]));
     rel[s] = make_float4((float)(x[p] - (double)gx * sf), (float)(y[p] - (double)gy * sf),
                          (float)(z[p] - (double)gz * sf), m[p]);
     vel4[s] = make_float4(vx[p], vy[p], vz[p], u[p]);
-    const float hp = h[p];
     hs[s] = hp;
-    lrad[s] = fminf(leaf_side[s], list_reach * gamma_k * hp);
+    lrad[s] = R;
   }
 }
 

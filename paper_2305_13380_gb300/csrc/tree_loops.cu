@@ -388,12 +388,17 @@ __device__ __forceinline__ int tstage(int v0, const TRanges& R, int lane, const 
 // Reverse pair of target ti (support H, leaf side s_i) and source j (shift
 // code sc of j seen from ti) at r^2 = r2 in ti's frame: wanted when r < H and
 // r reaches past j's list radius, lowered by a margin above the rounding of r
-// in either frame (the force decides again, exactly, in j's frame).
+// in either frame (the force decides again, exactly, in j's frame).  thr_j
+// is j's list radius less 2^-18 of its leaf side (fine[j].w).
+__device__ __forceinline__ bool want_reverse_t(float thr_j, int32_t ti, int32_t j, float r2, float H2, float H,
+                                               float s_i) {
+  if (!(r2 < H2) || j == ti) return false;
+  const float thr = thr_j - 0x1p-18f * (s_i + H);
+  return !(thr > 0.0f && r2 < thr * thr);
+}
 __device__ __forceinline__ bool want_reverse(const sphh::TreeDensityArgs& a, int32_t ti, int32_t j, float r2,
                                              float H2, float H, float s_i) {
-  if (!(r2 < H2) || j == ti) return false;
-  const float thr = a.lrad[j] - 0x1p-18f * (s_i + a.leaf_side[j] + H);
-  return !(thr > 0.0f && r2 < thr * thr);
+  return want_reverse_t(__int_as_float(a.fine[j].w), ti, j, r2, H2, H, s_i);
 }
 
 // Appends the wanted records of the warp (one counter atomic per warp).
@@ -595,13 +600,20 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       const float H2 = H * H;
       TDSums s;
       tds_zero(s);
+      // the list's reverse pairs are marked on the way (bit e: entry e; a
+      // list holds at most kTreeList = 32), with j's threshold read with its
+      // fine position
+      uint32_t wm = 0;
       if (valid && !mydirect) {
         for (int e = 0; e < cnt; ++e) {
           const uint32_t je = lje[e * 32 + lane];
           const int32_t j = unpack_j(je);
           const float4 rj = a.rel[j];
-          const float3 d = pair_vec(g, reli, fi, rj, a.fine[j], unpack_s(je));
+          const int4 fj = a.fine[j];
+          const float3 d = pair_vec(g, reli, fi, rj, fj, unpack_s(je));
           tdens_pair<K>(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
+          if (!atcap && want_reverse_t(__int_as_float(fj.w), ti, j, lr2[e * 32 + lane], H2, H, g.side))
+            wm |= 1u << e;
         }
       }
       // list-free targets: every staged source, reverse pairs on the way
@@ -630,16 +642,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           if (!one_chunk) __syncwarp();
         }
       }
-      // reverse pairs from the lists: each lane marks its wanted entries (a
-      // list holds at most kTreeList = 32), then the warp takes one slot
-      // range for the whole round
-      uint32_t wm = 0;
-      if (valid && !mydirect && !atcap) {
-        for (int e = 0; e < cnt; ++e) {
-          const uint32_t je = lje[e * 32 + lane];
-          if (want_reverse(a, ti, unpack_j(je), lr2[e * 32 + lane], H2, H, g.side)) wm |= 1u << e;
-        }
-      }
+      // reverse pairs from the lists: the warp takes one slot range for the
+      // whole round
       emit_marked(a, wm, lje, ti, lane);
       tcombine(s);
       // 4. publish the list (16-byte vectors) for the force loop
