@@ -350,13 +350,20 @@ int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
  *     particle ends its step with its CFL bin (SPH_HIER_ADAPT; the limiter of
  *     the active particles then sees that bin) or its held bin, raised to its
  *     wake-up bin if it has one.  Every flag is cleared (set to 0).
+ * SPH_HIER_PREDICT: the drift also carries every particle's h and density
+ * over [t_now, t_next] with its last velocity divergence held (dh/dt =
+ * h div_v / 3, continuity drho/dt = -rho div_v: h e^(div_v dt/3),
+ * rho e^(-div_v dt), in place in the pool), and sets P = (gamma - 1) u rho and
+ * c = sqrt(gamma P / rho) at the predicted u; the inactive particles enter the
+ * loops with these values, the active ones start their h solve from them.
  * bins (int32) and t_begin (int64) are device arrays of n, updated in place;
  * 0 <= max_bin <= 40; options: SPH_HIER_* bits (others: SPH_E_INVAL).  With
  * SPH_FLAG_SYNC a density that needs larger cells is rebuilt and repeated.
  * Waits for the stream (it returns t_next). */
 enum {
-  SPH_HIER_ADAPT = 1,  /* new bins from the CFL condition and the first limiter */
-  SPH_HIER_WAKEUP = 2  /* the wake-up limiter                                   */
+  SPH_HIER_ADAPT = 1,   /* new bins from the CFL condition and the first limiter */
+  SPH_HIER_WAKEUP = 2,  /* the wake-up limiter                                   */
+  SPH_HIER_PREDICT = 4  /* prediction of h, rho, P, c in the drift (below)       */
 };
 int sph_hier_substep(sph_ctx* ctx, const sph_pool* pool, int32_t* bins, int64_t* t_begin, double dt_max,
                      int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync, int64_t* t_next_out);

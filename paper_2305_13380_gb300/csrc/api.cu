@@ -1270,7 +1270,7 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
                      int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync_flags, int64_t* t_next_out) {
   if (!c || !pl || !bins || !tbeg || !t_next_out || pl->n_sims != 1 || pl->n_total < 1 ||
       pl->n_total > INT32_MAX / 16 || !(dt_max > 0.0) || !std::isfinite(dt_max) || max_bin < 0 || max_bin > 40 ||
-      t_now < 0 || (options & ~(SPH_HIER_ADAPT | SPH_HIER_WAKEUP)) != 0)
+      t_now < 0 || (options & ~(SPH_HIER_ADAPT | SPH_HIER_WAKEUP | SPH_HIER_PREDICT)) != 0)
     return SPH_E_INVAL;
   const bool adapt = (options & SPH_HIER_ADAPT) != 0, wakeup = (options & SPH_HIER_WAKEUP) != 0;
   if (!pl->sim_offset || !pl->box_size || !pl->x || !pl->y || !pl->z || !pl->vx || !pl->vy || !pl->vz ||
@@ -1314,6 +1314,13 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
   h.act = c->hact;
   h.sync = sync_flags;
   h.wake = nullptr;
+  h.predict = (options & SPH_HIER_PREDICT) != 0;
+  h.gamma = (float)c->p.gamma;
+  h.h = pl->h;
+  h.rho = pl->rho;
+  h.P = pl->P;
+  h.c = pl->c;
+  h.div_v = pl->div_v;
   h.t_next = c->htick;
   h.status = c->misc + sphk::kStatus;
   t_begin(c, SPH_T_INTEGRATE);

@@ -32,7 +32,10 @@ __global__ void k_hier_next(int64_t n, const int32_t* __restrict__ bin, const in
 // Drift of every particle from t_now to t_next (FP64 positions, one periodic
 // wrap), the velocity and energy predicted at t_next for the loops,
 // v(t) = v_half + a (t - t_begin - step/2) tau, and the active mask: the
-// particles whose step ends at t_next.
+// particles whose step ends at t_next.  With predict, h and rho follow the
+// last divergence over the drift, h e^(div_v dt / 3) and rho e^(-div_v dt)
+// (continuity), and P and c the equation of state at that rho and the
+// predicted u (the density loop replaces them for the active particles).
 __global__ void k_hier_drift(sphh::HierArgs a) {
   const int64_t tn = (int64_t)*a.t_next;
   const double dt = (double)(tn - a.t_now) * a.tau;
@@ -54,8 +57,18 @@ __global__ void k_hier_drift(sphh::HierArgs a) {
     a.vpx[i] = fmaf(a.ax[i], w, a.vx[i]);
     a.vpy[i] = fmaf(a.ay[i], w, a.vy[i]);
     a.vpz[i] = fmaf(a.az[i], w, a.vz[i]);
-    a.up[i] = fmaf(a.du_dt[i], w, a.u[i]);
+    const float up = fmaf(a.du_dt[i], w, a.u[i]);
+    a.up[i] = up;
     a.act[i] = (uint8_t)(a.t_begin[i] + s == tn);
+    if (a.predict) {
+      const float dv = (float)((double)a.div_v[i] * dt);
+      a.h[i] *= expf(dv * (1.0f / 3.0f));
+      const float rho = a.rho[i] * expf(-dv);
+      const float P = (a.gamma - 1.0f) * up * rho;
+      a.rho[i] = rho;
+      a.P[i] = P;
+      a.c[i] = sqrtf(a.gamma * P / rho);
+    }
   }
 }
 

@@ -212,6 +212,11 @@ struct HierArgs {
   uint8_t* act;            // active mask (scratch, input order)
   uint8_t* sync;           // synchronisation flags (nullptr: none; cleared)
   const int32_t* wake;     // wake-up bins (nullptr: no wake-up pass)
+  // prediction of h, rho, P and c in the drift (predict != 0)
+  int predict;
+  float gamma;  // adiabatic index
+  float *h, *rho, *P, *c;
+  const float* div_v;
   unsigned long long* t_next;
   int32_t* status;
 };

@@ -57,7 +57,11 @@ def _pool(s):
     return arr, sph.pool(off, box, arr)
 
 
-def _compare(g, s, d):
+def _compare(g, s, d, predict=False):
+    if predict:
+        # predicted (inactive) and re-evaluated (active) densities alike
+        for k in ("rho", "P", "c"):
+            assert np.allclose(g[k], s[k], rtol=1e-5), k
     for k in ("x", "y", "z"):
         diff = np.abs(g[k] - s[k])
         assert np.minimum(diff, 1.0 - diff).max() < 1e-6 * d, k
@@ -68,7 +72,8 @@ def _compare(g, s, d):
     assert np.allclose(g["h"], s["h"], rtol=1e-5)
 
 
-def test_fixed_bins_over_four_substeps(orc):
+@pytest.mark.parametrize("predict", [False, True])
+def test_fixed_bins_over_four_substeps(orc, predict):
     import torch
     from paper_2305_13380_gb300 import sph
     s = _state(orc, 3)
@@ -85,15 +90,16 @@ def test_fixed_bins_over_four_substeps(orc):
     tb = np.zeros(n, np.int64)
     t = tg = 0
     while t < 4:
-        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=False)
-        t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, False)
+        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=False, predict=predict)
+        t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, False, predict=predict)
         assert tg == t
     assert np.array_equal(gt.cpu().numpy(), tb) and np.array_equal(gb.cpu().numpy(), bins)
     g = {k: v.cpu().numpy() for k, v in arr.items()}
-    _compare(g, s, 1.0 / 12)
+    _compare(g, s, 1.0 / 12, predict)
 
 
-def test_adaptive_bins(orc):
+@pytest.mark.parametrize("predict", [False, True])
+def test_adaptive_bins(orc, predict):
     import torch
     from paper_2305_13380_gb300 import sph
     s = _state(orc, 5, u_spread=True)
@@ -109,8 +115,8 @@ def test_adaptive_bins(orc):
     tb = np.zeros(n, np.int64)
     t = tg = 0
     for _ in range(3):
-        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=True)
-        t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, True)
+        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=True, predict=predict)
+        t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, True, predict=predict)
         assert tg == t
         g_bins, g_tb = gb.cpu().numpy(), gt.cpu().numpy()
         # every step starts on a multiple of its length, and the tick is an end
@@ -119,7 +125,7 @@ def test_adaptive_bins(orc):
     assert len(np.unique(bins)) > 1   # at least two levels of the hierarchy
     if np.array_equal(gb.cpu().numpy(), bins):
         g = {k: v.cpu().numpy() for k, v in arr.items()}
-        _compare(g, s, 1.0 / 12)
+        _compare(g, s, 1.0 / 12, predict)
 
 
 def _heated(orc, seed, heat):
