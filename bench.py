@@ -467,10 +467,17 @@ def batch_measure(n_boxes: int, steps: int, warmup: int, plain_steps: int) -> di
     boxes = inputs.batch(n_boxes, seed0=0)
     n = sum(len(b["x"]) for b in boxes)
     t_tune = time.perf_counter()
-    over = tune.best_params(boxes, key=f"batch{n_boxes}")
+    # the boxes split by the spread of their smoothing lengths (lattices may
+    # take the uniform grid, clustered boxes need nested grids), each part
+    # with its own tuned cell geometry; one pool per part, stepped together
+    parts = tune.best_split(boxes, key=f"batch{n_boxes}")
     tune_s = time.perf_counter() - t_tune
-    prm = lambda: sph.sph_default_params(**over)  # noqa: E731
-    P = pool.Pool(boxes, prm())
+    over_of = {}
+    for idx, over in parts:
+        for i in idx:
+            over_of[i] = over
+    prm = lambda i: sph.sph_default_params(**over_of[i])  # noqa: E731
+    P = pool.Group([pool.Pool([boxes[i] for i in idx], sph.sph_default_params(**over)) for idx, over in parts])
     P.start()
     P.capture()
     for _ in range(warmup):
@@ -495,7 +502,7 @@ def batch_measure(n_boxes: int, steps: int, warmup: int, plain_steps: int) -> di
     rate, mean_ms = replicas.job_throughput(n, float(np.mean(per)))
     st = P.status()
     # one simulation per launch: every box has its own pool and context
-    singles = [pool.Pool([b], prm(), stream=P.stream) for b in boxes]
+    singles = [pool.Pool([b], prm(i), stream=P.stream) for i, b in enumerate(boxes)]
     for S in singles:
         S.start()
     for S in singles:
@@ -513,8 +520,12 @@ def batch_measure(n_boxes: int, steps: int, warmup: int, plain_steps: int) -> di
             "p50_ms": p50, "p99_ms": p99, "mean_ms": mean_ms, "updates_per_s": rate,
             "plain_per_launch_ms": plain_ms, "plain_updates_per_s": replicas.sum_over_ranks(n) / (plain_ms / 1e3),
             "plain_steps": plain_steps, "speedup_vs_plain": plain_ms / mean_ms,
-            "tuned": over, "tune_s": tune_s,
-            "gpu_launches": launches_per_step(n, n_boxes, bool(over["flags"] & sph.SPH_FLAG_TREE)) * steps,
+            "tuned": [{"boxes": len(idx), "particles": sum(len(boxes[i]["x"]) for i in idx), "params": over}
+                      for idx, over in parts],
+            "tune_s": tune_s,
+            "gpu_launches": sum(launches_per_step(sum(len(boxes[i]["x"]) for i in idx), len(idx),
+                                                  bool(over.get("flags", 0) & sph.SPH_FLAG_TREE))
+                                for idx, over in parts) * steps,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"]},
             "device_status": st}
@@ -527,9 +538,23 @@ def run_tune(args, world: int, rank: int, local: int):
     B.build()
     from paper_2305_13380_gb300 import inputs, tune
     if args.workload.startswith("batch"):
+        # each part of the split (tune.partition) tuned on its own
         n_boxes = int(args.workload[len("batch"):] or 256)
         sims = inputs.batch(n_boxes, seed0=0)
-        key = f"batch{n_boxes}"
+        t0 = time.perf_counter()
+        recs = []
+        for k, idx in enumerate(tune.partition(sims)):
+            part = [sims[i] for i in idx]
+            rec = tune.tune(part, key=f"batch{n_boxes}|part{k}-{len(idx)}", steps=max(3, min(args.steps, 10)))
+            recs.append({"boxes": len(idx), "particles": sum(len(s["x"]) for s in part), "best": rec["best"],
+                         "best_ms": rec["best_ms"], "default_ms": rec["default_ms"], "candidates": rec["times"]})
+        line = {"metric": "autotuned step time per part", "value": sum(r["best_ms"] for r in recs), "unit": "ms",
+                "higher_is_better": False, "n_gpus": world,
+                "config": {"workload": args.workload, "particles": sum(len(s["x"]) for s in sims)},
+                "parts": recs, "tune_s": time.perf_counter() - t0}
+        if rank == 0:
+            print(json.dumps(line))
+        return
     else:
         p = make_workload(args.workload)
         sims = [{k: v for k, v in p.items() if k not in ("desc", "tree")}]

@@ -98,3 +98,60 @@ class Pool:
                          "du_dt", "v_sig")) -> dict:
         self.stream.synchronize()
         return {k: self.a[k].cpu().numpy() for k in keys}
+
+
+class Group:
+    """Pools stepped together, each with its own parameters (say, lattice
+    boxes on the uniform grid and clustered boxes on nested grids): every
+    step forks the pools onto their own streams from the first pool's stream
+    and joins them back, so their kernels overlap on the device, and one CUDA
+    graph captures the whole step."""
+
+    def __init__(self, pools: list[Pool]):
+        if not pools:
+            raise ValueError("a group needs at least one pool")
+        self.pools = pools
+        self.stream = pools[0].stream
+        self.graph = None
+
+    def start(self):
+        for P in self.pools:
+            P.start()
+
+    def step(self):
+        main = self.stream
+        for P in self.pools[1:]:
+            P.stream.wait_stream(main)
+        for P in self.pools:
+            with torch.cuda.stream(P.stream):
+                sph.sph_step(P.ctx, P.pool)
+        for P in self.pools[1:]:
+            main.wait_stream(P.stream)
+
+    def capture(self):
+        """One graph for the step of every pool (after a warm-up step)."""
+        self.step()
+        self.stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            self.step()
+        self.graph = g
+        return g
+
+    def replay(self):
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
+
+    def synchronize(self):
+        """Waits for the step (a replayed graph runs on the first pool's stream)."""
+        self.stream.synchronize()
+        for P in self.pools[1:]:
+            P.stream.synchronize()
+
+    def status(self) -> int:
+        self.synchronize()
+        st = 0
+        for P in self.pools:
+            st |= P.status()
+        return st
+

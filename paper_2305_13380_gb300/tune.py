@@ -111,3 +111,24 @@ def best_params(sims, key: str, steps: int = 3) -> dict:
     lanes_per_target) for a pool of `sims`, from the cache when this GPU has
     seen `key`."""
     return dict(tune(sims, key, steps)["best"])
+
+
+def partition(sims) -> list[list[int]]:
+    """Indices of the simulations whose starting smoothing lengths span less
+    than SPREAD_UNIFORM (candidates for the uniform grid), then of the rest
+    (nested grids only); empty parts are dropped."""
+    spread = [float(np.max(s["h0"]) / np.min(s["h0"])) for s in sims]
+    parts = [[i for i, v in enumerate(spread) if v < SPREAD_UNIFORM],
+             [i for i, v in enumerate(spread) if v >= SPREAD_UNIFORM]]
+    return [p for p in parts if p]
+
+
+def best_split(sims, key: str, steps: int = 3) -> list[tuple[list[int], dict]]:
+    """The simulations split by partition(), each part with its own tuned
+    parameter overrides (cached per part)."""
+    out = []
+    for k, idx in enumerate(partition(sims)):
+        part = [sims[i] for i in idx]
+        out.append((idx, best_params(part, key=f"{key}|part{k}-{len(idx)}", steps=steps)))
+    return out
+

@@ -78,3 +78,45 @@ def test_batched_box_matches_oracle(orc, grid):
             nc = expected_nc(q["h0"], p["L"], n=len(p["x"]))
             vmax = float(np.sqrt(q["vx"] ** 2 + q["vy"] ** 2 + q["vz"] ** 2).max())
             compare(gs, od, of, cell=p["L"] / nc, vmax=vmax)
+
+
+def test_split_group_equals_its_pools_alone(orc):
+    """The batched bench's split: the lattice boxes on the uniform grid and the
+    clustered boxes on nested grids, two pools forked onto their own streams
+    and captured in one graph.  Each pool's results equal those of the same
+    pool stepped alone (bitwise), and every box holds the plain bounds against
+    the oracle."""
+    from gpu_common import compare
+    from paper_2305_13380_gb300 import pool, sph, tune
+    boxes = _boxes()
+    parts = tune.partition(boxes)
+    assert [sorted(p) for p in parts] == [[0, 2, 4], [1, 3, 5]]
+    prm = [_params("uniform"), _params("nested")]
+    alone = [pool.Pool([boxes[i] for i in idx], prm[k]) for k, idx in enumerate(parts)]
+    G = pool.Group([pool.Pool([boxes[i] for i in idx], prm[k]) for k, idx in enumerate(parts)])
+    for A in alone:
+        A.start()
+    G.start()
+    g0 = [P.host(("h", "rho", "f", "div_v", "curl_v", "P", "c", "balsara", "ax", "ay", "az", "du_dt",
+                  "v_sig")) for P in G.pools]
+    for k, idx in enumerate(parts):
+        for j, s in enumerate(idx):
+            q = as_f32(boxes[s])
+            od, of = orc.density_force(q, q["h0"])
+            sl = G.pools[k].sim_slice(j)
+            compare({key: v[sl] for key, v in g0[k].items()}, od, of)
+    G.capture()          # includes one warm-up step
+    for A in alone:
+        A.step()
+    for _ in range(3):
+        G.replay()
+        for A in alone:
+            A.step()
+    G.synchronize()
+    assert G.status() == 0 and all(A.status() == 0 for A in alone)
+    assert G.pools[0].ctx is not G.pools[1].ctx
+    for A, P in zip(alone, G.pools):
+        ha, hp = A.host(), P.host()
+        for key in ha:
+            assert np.array_equal(ha[key], hp[key]), key
+    assert sph.SPH_FLAG_TREE & G.pools[1].params.flags
