@@ -32,12 +32,22 @@ struct TreeRange {
 };
 
 // Tree loops: lanes per target, list entries kept per (target, lane), and the
-// list radius as a multiple of the starting support (a Newton step that
-// outgrows it sends the warp to the list-free path).
+// list radius as a multiple of the starting support (a target whose support
+// outgrows it is solved by the per-target kernel).  A reach just above the
+// starting support keeps the lists (and the force pairs read from them) short;
+// measured on the 2M clustered box with the per-target kernel: 1.01-1.03
+// within 1 % of each other, 1.05 10 % and 1.1 15 % slower per step, 1.0 (every
+// growing support queued) four times slower.
+#ifndef SPH_TREE_LIST
+#define SPH_TREE_LIST 32
+#endif
+#ifndef SPH_TREE_LIST_REACH
+#define SPH_TREE_LIST_REACH 1.02f
+#endif
 constexpr int kTreeTpp = 8;
-constexpr int kTreeList = 32;
-constexpr int kTreeListRegion = 32;
-constexpr float kTreeListReach = 1.1f;
+constexpr int kTreeList = SPH_TREE_LIST;
+constexpr int kTreeListRegion = SPH_TREE_LIST;
+constexpr float kTreeListReach = SPH_TREE_LIST_REACH;
 
 __device__ __forceinline__ uint32_t spread3(uint32_t v) {
   // 10 bits -> every third bit of 30

@@ -13,9 +13,10 @@
 //   1. the 27 ranges are staged in chunks relative to the leaf corner;
 //   2. each target keeps, in per-lane lists, the sources closer than its list
 //      radius R_i = min(leaf side, kTreeListReach * starting support);
-//   3. Newton-Raphson passes read r^2 from the lists; if a support outgrows
-//      R_i (or a list overflows) the warp takes the list-free path, which sums
-//      over every staged source;
+//   3. Newton-Raphson passes read r^2 from the lists; a target whose support
+//      outgrows R_i (or whose list overflows) leaves its group for the
+//      per-target kernel (k_tree_density_fb at its own level: a warp per
+//      target over its 27 cells), so that its round-mates do not wait;
 //   4. the final pass at the converged h gathers the sources from memory and
 //      publishes the lists for the force loop.
 // A force pair needs r < max(H_i, H_j).  The list of i holds every j with
@@ -30,6 +31,8 @@
 // own leaf frame with the same arithmetic as the density filter, so no pair is
 // counted twice or dropped at the boundary; emission uses a margin so that the
 // reverse pairs are a superset.
+#include <type_traits>
+
 #include "sph_internal.cuh"
 #include "sph_launch.h"
 #include "tree.cuh"
@@ -57,6 +60,9 @@ constexpr int kNoShift = 1 | (1 << 2) | (1 << 4);
 // list_cnt markers: sums taken without a list; target re-solved by the fallback
 constexpr uint16_t kListNone = 0xffff;
 constexpr uint16_t kListFallback = 0xfffe;
+// fallback queue entries: a target index, with this bit for a target queued
+// from its group (solved at its own level); indices stay below 2^30
+constexpr int32_t kFbOwnLevel = 1 << 30;
 static_assert(kTWarpSmem % 16 == 0, "per-warp regions keep float4 alignment");
 static_assert(kTreeList <= kTreeListRegion, "published lists fit their regions");
 static_assert(kTreeListRegion % 4 == 0, "lists are published as 16-byte vectors");
@@ -427,10 +433,17 @@ __device__ __forceinline__ uint64_t reverse_rec(int32_t j, int32_t ti, int sc) {
 // Appends the list entries marked in each lane's mask wm (bit e: entry e of
 // the lane's column in lje): one counter atomic for the warp, then every
 // lane writes its records at its offset.  Called by all 32 lanes.
-__device__ __forceinline__ void emit_marked(const sphh::TreeDensityArgs& a, uint32_t wm, const uint32_t* lje,
+// one mask bit per list entry
+using TMark = std::conditional_t<(kTreeList > 32), unsigned long long, uint32_t>;
+__device__ __forceinline__ int tmark_popc(uint32_t m) { return __popc(m); }
+__device__ __forceinline__ int tmark_popc(unsigned long long m) { return __popcll(m); }
+__device__ __forceinline__ int tmark_ffs(uint32_t m) { return __ffs((int)m); }
+__device__ __forceinline__ int tmark_ffs(unsigned long long m) { return __ffsll((long long)m); }
+
+__device__ __forceinline__ void emit_marked(const sphh::TreeDensityArgs& a, TMark wm, const uint32_t* lje,
                                             int32_t ti, int lane) {
-  static_assert(kTreeList <= 32, "one mask bit per list entry");
-  const int my = __popc(wm);
+  static_assert(kTreeList <= 64, "one mask bit per list entry");
+  const int my = tmark_popc(wm);
   int incl = my;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -443,7 +456,7 @@ __device__ __forceinline__ void emit_marked(const sphh::TreeDensityArgs& a, uint
   if (lane == 0) base = atomicAdd(a.rev_count, (unsigned long long)total);
   unsigned long long k = __shfl_sync(0xffffffffu, base, 0) + (unsigned long long)(incl - my);
   while (wm) {
-    const int e = __ffs(wm) - 1;
+    const int e = tmark_ffs(wm) - 1;
     wm &= wm - 1u;
     const uint32_t je = lje[e * 32 + lane];
     const int32_t j = unpack_j(je);
@@ -554,10 +567,12 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           __syncwarp();
         }
       }
-      // a target whose list overflowed, or whose support outgrows R_i, sums
-      // over every staged source instead ("list-free"); the others keep
-      // their lists.  The flag is shared by the target's lanes.
-      bool mydirect = group_any(cnt > kTreeList, lane);
+      // a target whose list overflowed, or whose support outgrows R_i, leaves
+      // the group: it is queued for the per-target kernel, which solves it at
+      // its own level with all 32 lanes of a warp over its 27 cells (so the
+      // other targets of its round do not wait for it).  The flag is shared by
+      // the target's lanes.
+      bool queued = group_any(cnt > kTreeList, lane);
       // 2. Newton-Raphson passes
       float h = valid ? a.hs[ti] : hcap;
       if (!(h > 0.0f)) h = 0.5f * hcap;
@@ -565,34 +580,29 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       {
         // evaluated by every lane (a ballot), then merged
         const bool outgrown = group_any(valid && KernT<K>::gamma * h > Ri, lane);
-        mydirect = mydirect || outgrown;
+        queued = queued || outgrown;
       }
       float hlo = 0.0f, hhi = INFINITY;
-      bool done = !valid, atcap = false, conv = false;
+      bool done = !valid || queued, atcap = false, conv = false;
       int it = 0, passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
         const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
         float Sw = 0.f, Sdw = 0.f;
-        if (!mydirect && !done)
+        if (!done)
           for (int e = 0; e < cnt; ++e) tnewton_pair<K>(lr2[e * 32 + lane], H, Hinv, Sw, Sdw);
-        if (__any_sync(0xffffffffu, mydirect && !done)) {
-          for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
-            const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
-            if (mydirect && !done)
-              for (int k = sub; k < c; k += kTreeTpp) tnewton_pair<K>(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
-            if (!one_chunk) __syncwarp();
-          }
-        }
         Sw = gsum(Sw);
         Sdw = gsum(Sdw);
         if (!done) {
           passes = it + 1;
           if (newton_update(Sw, Sdw, nwt, hcap, h, hlo, hhi, it, atcap, conv)) done = true;
         }
-        // the list holds r < R_i: a support beyond it needs every staged source
-        const bool outgrown = group_any(valid && KernT<K>::gamma * h > Ri, lane);
-        mydirect = mydirect || outgrown;
+        // the list holds r < R_i: a support beyond it is queued
+        const bool outgrown = group_any(valid && !queued && !atcap && KernT<K>::gamma * h > Ri, lane);
+        if (outgrown) {
+          queued = true;
+          done = true;
+        }
       }
       // 3. final pass at h
       const float H = KernT<K>::gamma * h;
@@ -603,8 +613,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       // the list's reverse pairs are marked on the way (bit e: entry e; a
       // list holds at most kTreeList = 32), with j's threshold read with its
       // fine position
-      uint32_t wm = 0;
-      if (valid && !mydirect) {
+      TMark wm = 0;
+      if (valid && !queued) {
         for (int e = 0; e < cnt; ++e) {
           const uint32_t je = lje[e * 32 + lane];
           const int32_t j = unpack_j(je);
@@ -613,33 +623,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           const float3 d = pair_vec(g, reli, fi, rj, fj, unpack_s(je));
           tdens_pair<K>(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
           if (!atcap && want_reverse_t(__int_as_float(fj.w), ti, j, lr2[e * 32 + lane], H2, H, g.side))
-            wm |= 1u << e;
-        }
-      }
-      // list-free targets: every staged source, reverse pairs on the way
-      // (warp-uniform trip counts around emit_warp)
-      if (__any_sync(0xffffffffu, valid && mydirect)) {
-        for (int v0 = 0; v0 < nsrc; v0 += kTCap) {
-          const int c = one_chunk ? nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
-          for (int k0 = 0; k0 < c; k0 += kTreeTpp) {
-            const int k = k0 + sub;
-            bool want = false;
-            uint64_t rec = 0;
-            if (valid && mydirect && k < c) {
-              const float4 pj = spos[k];
-              const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              if (r2 < H2) {
-                const uint32_t je = sidx[k];
-                const int32_t j = unpack_j(je);
-                tdens_pair<K>(dx, dy, dz, vi, a.vel4[j], pj.w, H, Hinv, s);
-                want = !atcap && want_reverse(a, ti, j, r2, H2, H, g.side);
-                rec = reverse_rec(j, ti, unpack_s(je));
-              }
-            }
-            emit_warp(a, want, rec, lane);
-          }
-          if (!one_chunk) __syncwarp();
+            wm |= (TMark)1 << e;
         }
       }
       // reverse pairs from the lists: the warp takes one slot range for the
@@ -649,8 +633,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       // 4. publish the list (16-byte vectors) for the force loop
       if (valid) {
         const int64_t col = (int64_t)ti * kTreeTpp + sub;
-        a.list_cnt[col] = (uint16_t)(atcap ? kListFallback : (mydirect ? kListNone : cnt));
-        if (!mydirect) {
+        a.list_cnt[col] = (uint16_t)(atcap || queued ? kListFallback : cnt);
+        if (!queued) {
           uint4* dst = reinterpret_cast<uint4*>(a.lists + col * kTreeListRegion);
           for (int e = 0; e < cnt; e += 4)
             dst[e >> 2] = make_uint4(lje[e * 32 + lane], lje[(e + 1) * 32 + lane], lje[(e + 2) * 32 + lane],
@@ -658,15 +642,21 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         }
       }
       if (valid && sub == 0) {
-        tdens_write<K>(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
-        if (atcap) {
-          // the support outgrew this level: re-solved at a coarser one
+        if (queued) {
+          // solved at its own level by the per-target kernel
           const int32_t k = atomicAdd(a.fb_count, 1);
-          if (k < a.n_total) a.fb_list[k] = ti;
+          if (k < a.n_total) a.fb_list[k] = ti | kFbOwnLevel;
+          free_acc += 1ull;
         } else {
-          pair_acc += (unsigned long long)s.npair;
+          tdens_write<K>(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
+          if (atcap) {
+            // the support outgrew this level: re-solved at a coarser one
+            const int32_t k = atomicAdd(a.fb_count, 1);
+            if (k < a.n_total) a.fb_list[k] = ti;
+          } else {
+            pair_acc += (unsigned long long)s.npair;
+          }
         }
-        free_acc += mydirect ? 1ull : 0ull;
       }
       __syncwarp();
     }
@@ -989,15 +979,20 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
   const int32_t nq = min(*a.fb_count, (int32_t)a.n_total);
   unsigned long long pair_acc = 0;
   for (int32_t q = next_group(a.fb_work, lane); q < nq; q = next_group(a.fb_work, lane)) {
-    const int32_t ti = a.fb_list[q];
+    const int32_t qe = a.fb_list[q];
+    const bool own = (qe & kFbOwnLevel) != 0;
+    const int32_t ti = qe & ~kFbOwnLevel;
     const uint64_t key = a.skey[ti];
     const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30))];
     const float4 reli = a.rel[ti];
     const int4 fi = a.fine[ti];
     const float4 vi = a.vel4[ti];
-    float h = a.h[a.perm[ti]];  // the capped h of the first solve
+    // a target queued from its group starts at its own level from its
+    // starting h; one that hit its level's cap one level coarser from the
+    // capped h of the first solve
+    float h = own ? a.hs[ti] : a.h[a.perm[ti]];
     bool conv = false, atcap = true;
-    int passes = 0, d = (int)a.level[ti] - 1;
+    int passes = 0, d = (int)a.level[ti] - (own ? 0 : 1);
     if (d < 0) {
       // already at its top cell: the caller rebuilds the top grid from twice
       // the capped h; the first solve's other outputs stand
@@ -1100,7 +1095,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
   const int32_t nq = min(*a.fb_count, (int32_t)a.n_total);
   unsigned long long pair_acc = 0;
   for (int32_t q = next_group(a.fb_work, lane); q < nq; q = next_group(a.fb_work, lane)) {
-    const int32_t ti = a.fb_list[q];
+    const int32_t ti = a.fb_list[q] & ~kFbOwnLevel;
     const uint64_t key = a.skey[ti];
     const int sim = sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30));
     const GridDev G = a.grid[sim];
