@@ -40,7 +40,10 @@
 namespace sphk {
 
 constexpr int kTWarps = 4;       // warps per CTA
-constexpr int kTCap = 384;       // staged sources per warp and chunk
+#ifndef SPH_TREE_TCAP
+#define SPH_TREE_TCAP 384
+#endif
+constexpr int kTCap = SPH_TREE_TCAP;  // staged sources per warp and chunk
 constexpr int kTRows = kTreeList + 1;  // + one scratch row for the branch-free append
 constexpr int kTPer = 32 / kTreeTpp;   // targets per round
 constexpr int kTChildren = 27 * 8;      // children of the 27 neighbour cells
@@ -976,6 +979,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
   unsigned char* base = tsm + (size_t)warp * kTWarpSmem;
   float4* spos = reinterpret_cast<float4*>(base);
   uint32_t* sidx = reinterpret_cast<uint32_t*>(spos + kTCap);
+  TPrune* pr = reinterpret_cast<TPrune*>(sidx + kTCap + kTRows * 32 * 2);
   const int32_t nq = min(*a.fb_count, (int32_t)a.n_total);
   unsigned long long pair_acc = 0;
   for (int32_t q = next_group(a.fb_work, lane); q < nq; q = next_group(a.fb_work, lane)) {
@@ -1008,14 +1012,22 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     TRanges R;
     float3 pi;
     bool one_chunk = true;
+    int nh = 0, total = 0;
     for (; d >= 0; --d) {
       const TreeLeaf Lc = cell_at_depth(key, d);
       g = leaf_geo(Lc, G);
       R = cell_ranges(G, Lc, a.skey, a.cell_start, lane);
       pi = rel_to(g, reli, fi, kNoShift);
       const float hcap = h_cap<K>(g.side_d, g.L);
-      one_chunk = R.nsrc <= kTCap;
-      if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx);
+      // the sources: the children of the 27 cells whose box lies within the
+      // cell side (the largest support this level holds, with a margin far
+      // above the rounding of r), staged in chunks
+      prune_tables(a.skey, R, Lc.depth, lane, pr);
+      const float cside = Lc.depth < kTreeDepth ? 0.5f * g.side : g.side;
+      total = prune_round(true, lane % kTreeTpp, lane, pi, g.side * g.side * (1.0f + 0x1p-10f), g.side, cside, pr,
+                          nh);
+      one_chunk = total <= kTCap;
+      if (one_chunk) tstage_union(0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx);
       float hlo = 0.0f, hhi = INFINITY;
       int it = 0;
       if (h > hcap) h = hcap;
@@ -1024,8 +1036,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
         const float H = KernT<K>::gamma * h;
         const float Hinv = 1.0f / H;
         float Sw = 0.f, Sdw = 0.f;
-        for (int v0 = 0; v0 < R.nsrc; v0 += kTCap) {
-          const int c = one_chunk ? R.nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
+        for (int v0 = 0; v0 < total; v0 += kTCap) {
+          const int c = one_chunk ? total : tstage_union(v0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx);
           for (int k = lane; k < c; k += 32) tnewton_pair<K>(r2_of(pi, spos[k]), H, Hinv, Sw, Sdw);
           if (!one_chunk) __syncwarp();
         }
@@ -1047,8 +1059,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     const float H2 = H * H;
     TDSums s;
     tds_zero(s);
-    for (int v0 = 0; v0 < R.nsrc; v0 += kTCap) {
-      const int c = one_chunk ? R.nsrc : tstage(v0, R, lane, g, a.rel, a.fine, spos, sidx);
+    for (int v0 = 0; v0 < total; v0 += kTCap) {
+      const int c = one_chunk ? total : tstage_union(v0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx);
       for (int k0 = 0; k0 < c; k0 += 32) {
         const int k = k0 + lane;
         bool want = false;
@@ -1109,20 +1121,48 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
     const float4 ei = kFl != kTMin ? a.fE[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float2 di = make_float2(__int_as_float(hi.q1.w), __frcp_rn(hi.q0.w));
     const float Hi = hi.q0.w;
-    const float C2 = g.side * g.side;  // own reach: the cell of the fallback level
+    // own reach: the list radius, or the support where it outgrew the list
+    // (both within the cell of the fallback level, whose 27 cells hold every
+    // source closer than that); the sources beyond it with a larger support
+    // sent their pairs as reverse pairs (each emitted from r >= the list radius)
+    const float C = fmaxf(a.lrad[ti], Hi);
+    const float C2 = C * C;
     TFSums s;
     s.ax = s.ay = s.az = s.du = s.vsig = 0.f;
     s.npair = 0;
     if (kFl == kTGradient) s.ay = ei.y;
+    const float cside = Lc.depth < kTreeDepth ? 0.5f * g.side : g.side;
+    const float Cb2 = C2 * (1.0f + 0x1p-10f);
     for (int r = 0; r < 27; ++r) {
       const TreeRange Rg = neighbour_range(G, Lc, r, a.skey, a.cell_start);
-      for (int32_t j = Rg.lo + lane; j < Rg.hi; j += 32) {
-        if (j == ti) continue;
-        const TRec hj = trec_head(a.rec, j);
-        const float3 pj = rec_rel_to(g, hj, Rg.shift);
-        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
-          tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
+      if (Rg.hi <= Rg.lo) continue;
+      // the range's 8 children (contiguous in Morton order; a cell of the
+      // deepest level is its own single child): lane c < 8 finds child c's
+      // start and tests its box against the reach (with a margin far above
+      // the rounding of r)
+      int32_t c0 = Rg.lo;
+      if (Lc.depth < kTreeDepth && lane > 0 && lane < 8) {
+        const int sh = 3 * (kTreeDepth - Lc.depth - 1);
+        const uint64_t base = (a.skey[Rg.lo] >> (sh + 3)) << (sh + 3);
+        c0 = (int32_t)lower_bound64(a.skey, Rg.lo, Rg.hi, base + ((uint64_t)lane << sh));
+      }
+      if (Lc.depth >= kTreeDepth && lane > 0) c0 = Rg.hi;
+      const int32_t nx = __shfl_down_sync(0xffffffffu, c0, 1);  // every lane takes part
+      const int32_t c1 = lane < 7 ? nx : Rg.hi;
+      const bool hit = lane < 8 && c1 > c0 && child_dist2(r * 8 + lane, g.side, cside, pi) < Cb2;
+      unsigned hm = __ballot_sync(0xffffffffu, hit);
+      while (hm) {
+        const int ch = __ffs((int)hm) - 1;
+        hm &= hm - 1u;
+        const int32_t lo = __shfl_sync(0xffffffffu, c0, ch), hi = __shfl_sync(0xffffffffu, c1, ch);
+        for (int32_t j = lo + lane; j < hi; j += 32) {
+          if (j == ti) continue;
+          const TRec hj = trec_head(a.rec, j);
+          const float3 pj = rec_rel_to(g, hj, Rg.shift);
+          const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+          if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
+            tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
+        }
       }
     }
     if (kFl != kTGradient) {
