@@ -38,11 +38,12 @@ __device__ __forceinline__ int32_t cap_cells_per_side(int64_t n, int k) {
 // atomicMax.  Non-positive and NaN values are ignored.
 __global__ void k_grid_hmax(const int64_t* __restrict__ sim_offset, int n_sims, int64_t n_total,
                             const float* __restrict__ h, int32_t* __restrict__ hmax_bits) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const WarpRange wr = warp_range(n_total);
+  SimCursor sc;
   int cur = -1;
   float m = 0.0f;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_total; p += stride) {
-    const int s = sim_of_particle(sim_offset, n_sims, p);
+  for (int64_t p = wr.lo + (threadIdx.x & 31); p < wr.hi; p += 32) {
+    const int s = sc.at(sim_offset, n_sims, p);
     if (s != cur) {
       if (cur >= 0 && m > 0.0f) atomicMax(&hmax_bits[cur], __float_as_int(m));
       cur = s;
@@ -124,9 +125,10 @@ __global__ void k_key_count(int64_t n_total, const double* __restrict__ x, const
                             const double* __restrict__ z, const int64_t* __restrict__ sim_offset,
                             int n_sims, const GridDev* __restrict__ grid, int32_t* __restrict__ key,
                             int32_t* __restrict__ sort_key, int32_t* __restrict__ count) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int s = sim_of_particle(sim_offset, n_sims, p);
+  const WarpRange wr = warp_range(n_total);
+  SimCursor sc;
+  for (int64_t p = wr.lo + (threadIdx.x & 31); p < wr.hi; p += 32) {
+    const int s = sc.at(sim_offset, n_sims, p);
     const GridDev G = grid[s];
     const int32_t kx = cell_coord_fast(x[p], G.L, G.n_c, G.scale_f);
     const int32_t ky = cell_coord_fast(y[p], G.L, G.n_c, G.scale_f);

@@ -175,6 +175,37 @@ __device__ __forceinline__ int sim_of_particle(const int64_t* __restrict__ sim_o
   return lo;
 }
 
+// Warp-contiguous split of [0, n) over the grid: warp w takes [lo, hi), runs
+// of ceil(n / warps) rounded up to a multiple of 32, and lane l the indices
+// lo + l + 32 k.  Loads stay coalesced, and a thread's indices stay in one
+// simulation over long runs (a grid-stride loop jumps across many small
+// simulations at every step).  blockDim.x is a multiple of 32.
+struct WarpRange {
+  int64_t lo, hi;
+};
+__device__ __forceinline__ WarpRange warp_range(int64_t n) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t run = ((n + nw - 1) / nw + 31) & ~(int64_t)31;
+  const int64_t lo = w * run;
+  return {lo, lo + run < n ? lo + run : n};
+}
+
+// Simulation of a pool index, searched again only when the index leaves the
+// range of the last one found.
+struct SimCursor {
+  int s = -1;
+  int64_t lo = 0, hi = 0;
+  __device__ __forceinline__ int at(const int64_t* __restrict__ sim_offset, int n_sims, int64_t p) {
+    if (p < lo || p >= hi) {
+      s = sim_of_particle(sim_offset, n_sims, p);
+      lo = sim_offset[s];
+      hi = sim_offset[s + 1];
+    }
+    return s;
+  }
+};
+
 // Simulation owning a global cell id.
 __device__ __forceinline__ int sim_of_cell(const GridDev* __restrict__ grid, int n_sims, int32_t c) {
   int lo = 0, hi = n_sims - 1;

@@ -16,9 +16,10 @@
 namespace sphk {
 
 __global__ void k_sphenix_alpha_v(sphh::SphenixAlphaArgs a, SphenixDev x) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float dt = (float)(x.dt_dev != nullptr ? x.dt_dev[sim_of_particle(a.sim_offset, a.n_sims, i)] : x.dt);
+  const WarpRange wr = warp_range(a.n_total);
+  SimCursor sc;
+  for (int64_t i = wr.lo + (threadIdx.x & 31); i < wr.hi; i += 32) {
+    const float dt = (float)(x.dt_dev != nullptr ? x.dt_dev[sc.at(a.sim_offset, a.n_sims, i)] : x.dt);
     const float H = a.gamma_k * a.h[i];
     const float div = a.div_v[i];
     const float rate = dt > 0.0f ? (div - a.div_v_prev[i]) / dt : 0.0f;

@@ -37,12 +37,12 @@ __global__ void k_dt_init(unsigned* __restrict__ bits, int n_sims) {
 __global__ void k_dt_min(const int64_t* __restrict__ sim_offset, int n_sims, int64_t n_total,
                          const float* __restrict__ h, const float* __restrict__ v_sig,
                          unsigned* __restrict__ bits) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const WarpRange wr = warp_range(n_total);
+  SimCursor sc;
   int cur = -1;
   float m = INFINITY;
-  for (; p < n_total; p += stride) {
-    const int s = sim_of_particle(sim_offset, n_sims, p);
+  for (int64_t p = wr.lo + (threadIdx.x & 31); p < wr.hi; p += 32) {
+    const int s = sc.at(sim_offset, n_sims, p);
     if (s != cur) {
       if (cur >= 0 && m < INFINITY) atomicMin(&bits[cur], __float_as_uint(m));
       cur = s;
@@ -88,9 +88,10 @@ __global__ void k_kick_drift(sphh::StepArgs a) {
   int cur = -1;
   double dt = 0.0, L = 0.0;
   float hdt = 0.0f, dt3 = 0.0f;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int s = sim_of_particle(a.sim_offset, a.n_sims, p);
+  const WarpRange wr = warp_range(a.n_total);
+  SimCursor sc;
+  for (int64_t p = wr.lo + (threadIdx.x & 31); p < wr.hi; p += 32) {
+    const int s = sc.at(a.sim_offset, a.n_sims, p);
     if (s != cur) {  // the simulation's dt and box, converted once
       cur = s;
       dt = a.dt[s];
@@ -129,9 +130,10 @@ __global__ void k_kick_drift(sphh::StepArgs a) {
 __global__ void k_kick(sphh::StepArgs a) {
   int cur = -1;
   float hdt = 0.0f;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n_total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int s = sim_of_particle(a.sim_offset, a.n_sims, p);
+  const WarpRange wr = warp_range(a.n_total);
+  SimCursor sc;
+  for (int64_t p = wr.lo + (threadIdx.x & 31); p < wr.hi; p += 32) {
+    const int s = sc.at(a.sim_offset, a.n_sims, p);
     if (s != cur) {
       cur = s;
       hdt = (float)(0.5 * a.dt[s]);

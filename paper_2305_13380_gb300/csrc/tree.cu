@@ -43,8 +43,10 @@ __global__ void k_tree_key(int64_t n, const double* __restrict__ x, const double
                            int n_sims, const GridDev* __restrict__ grid,
                            const int32_t* __restrict__ cell_key, uint64_t* __restrict__ key64,
                            uint64_t* __restrict__ key64_copy) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int s = sim_of_particle(sim_offset, n_sims, p);
+  const WarpRange wr = warp_range(n);
+  SimCursor sc;
+  for (int64_t p = wr.lo + (threadIdx.x & 31); p < wr.hi; p += 32) {
+    const int s = sc.at(sim_offset, n_sims, p);
     const GridDev G = grid[s];
     const int32_t c = cell_key[p];
     const int32_t local = c - G.cell_base;
