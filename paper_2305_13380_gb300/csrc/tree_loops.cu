@@ -1013,27 +1013,34 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     float3 pi;
     bool one_chunk = true;
     int nh = 0, total = 0;
+    float Rp = 0.0f, cside = 0.0f;
+    // the sources: the children of the 27 cells whose box lies within the
+    // selection radius Rp (with a margin far above the rounding of r), staged
+    // in chunks; Rp = min(cell side, 1.25 H) leaves room for the support to
+    // grow, and a support beyond it selects again (H is warp-uniform)
+#define TREE_FB_SELECT(Hsup)                                                                                   \
+  if ((Hsup) > Rp) {                                                                                           \
+    Rp = fminf(g.side, 1.25f * (Hsup));                                                                        \
+    total = prune_round(true, lane % kTreeTpp, lane, pi, Rp * Rp * (1.0f + 0x1p-10f), g.side, cside, pr, nh); \
+    one_chunk = total <= kTCap;                                                                                \
+    if (one_chunk) tstage_union(0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx);                         \
+  }
     for (; d >= 0; --d) {
       const TreeLeaf Lc = cell_at_depth(key, d);
       g = leaf_geo(Lc, G);
       R = cell_ranges(G, Lc, a.skey, a.cell_start, lane);
       pi = rel_to(g, reli, fi, kNoShift);
       const float hcap = h_cap<K>(g.side_d, g.L);
-      // the sources: the children of the 27 cells whose box lies within the
-      // cell side (the largest support this level holds, with a margin far
-      // above the rounding of r), staged in chunks
       prune_tables(a.skey, R, Lc.depth, lane, pr);
-      const float cside = Lc.depth < kTreeDepth ? 0.5f * g.side : g.side;
-      total = prune_round(true, lane % kTreeTpp, lane, pi, g.side * g.side * (1.0f + 0x1p-10f), g.side, cside, pr,
-                          nh);
-      one_chunk = total <= kTCap;
-      if (one_chunk) tstage_union(0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx);
+      cside = Lc.depth < kTreeDepth ? 0.5f * g.side : g.side;
+      Rp = 0.0f;  // nothing selected at this level yet
       float hlo = 0.0f, hhi = INFINITY;
       int it = 0;
       if (h > hcap) h = hcap;
       bool done = false;
       while (!done) {  // warp-uniform: every lane holds the same reduced sums
         const float H = KernT<K>::gamma * h;
+        TREE_FB_SELECT(H)
         const float Hinv = 1.0f / H;
         float Sw = 0.f, Sdw = 0.f;
         for (int v0 = 0; v0 < total; v0 += kTCap) {
@@ -1055,6 +1062,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
     }
     // final pass at h, reverse pairs of this target
     const float H = KernT<K>::gamma * h;
+    TREE_FB_SELECT(H)
+#undef TREE_FB_SELECT
     const float Hinv = 1.0f / H;
     const float H2 = H * H;
     TDSums s;
