@@ -44,7 +44,10 @@ struct TreeRange {
 #ifndef SPH_TREE_LIST_REACH
 #define SPH_TREE_LIST_REACH 1.02f
 #endif
-constexpr int kTreeTpp = 8;
+#ifndef SPH_TREE_TPP
+#define SPH_TREE_TPP 8
+#endif
+constexpr int kTreeTpp = SPH_TREE_TPP;  // a power of two dividing 8
 constexpr int kTreeList = SPH_TREE_LIST;
 constexpr int kTreeListRegion = SPH_TREE_LIST;
 constexpr float kTreeListReach = SPH_TREE_LIST_REACH;

@@ -302,27 +302,36 @@ __device__ __forceinline__ float child_dist2(int ch, float side, float cside, co
 // sources.  Returns the union's source count.  Called by the whole warp.
 __device__ __forceinline__ int prune_round(bool valid, int sub, int lane, const float3& pi, float Rb2,
                                            float side, float cside, TPrune* pr, int& nh) {
-  uint32_t mine = 0;
+  // lane sub owns children sub + kTreeTpp k (k < kCh) of every neighbour cell
+  constexpr int kCh = 8 / kTreeTpp;
+  using Mask = std::conditional_t<(27 * kCh > 32), unsigned long long, uint32_t>;
+  Mask mine = 0;
   if (valid) {
     for (int m = 0; m < 27; ++m) {
-      const int ch = sub + 8 * m;
-      if (pr->cv[ch] < pr->cv[ch + 1] && child_dist2(ch, side, cside, pi) < Rb2) mine |= 1u << m;
+#pragma unroll
+      for (int k = 0; k < kCh; ++k) {
+        const int ch = 8 * m + sub + kTreeTpp * k;
+        if (pr->cv[ch] < pr->cv[ch + 1] && child_dist2(ch, side, cside, pi) < Rb2) mine |= (Mask)1 << (m * kCh + k);
+      }
     }
   }
 #pragma unroll
   for (int o = kTreeTpp; o < 32; o <<= 1) mine |= __shfl_xor_sync(0xffffffffu, mine, o);
-  // lanes 0..7 hold the union of children sub = lane (+ 8 m)
+  // lanes 0..kTreeTpp-1 hold the union; compacted in child order
   nh = 0;
   for (int m = 0; m < 27; ++m) {
-    const bool hb = lane < kTreeTpp && ((mine >> m) & 1u);
-    const unsigned b = __ballot_sync(0xffffffffu, hb);
-    if (hb) {
-      const int ch = kTreeTpp * m + lane;
-      const int k = nh + __popc(b & ((1u << lane) - 1u));
-      pr->hch[k] = (uint8_t)ch;
-      pr->hoff[k] = pr->cv[ch + 1] - pr->cv[ch];
+#pragma unroll
+    for (int k = 0; k < kCh; ++k) {
+      const bool hb = lane < kTreeTpp && ((mine >> (m * kCh + k)) & 1u);
+      const unsigned b = __ballot_sync(0xffffffffu, hb);
+      if (hb) {
+        const int ch = 8 * m + kTreeTpp * k + lane;
+        const int idx = nh + __popc(b & ((1u << lane) - 1u));
+        pr->hch[idx] = (uint8_t)ch;
+        pr->hoff[idx] = pr->cv[ch + 1] - pr->cv[ch];
+      }
+      nh += __popc(b);
     }
-    nh += __popc(b);
   }
   __syncwarp();
   int run = 0;
