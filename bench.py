@@ -90,6 +90,10 @@ def parse():
                     help="latticeN / clusteredN: smoothing kernel")
     ap.add_argument("--hier", action="store_true",
                     help="latticeN: sub-steps of the time-step hierarchy (a smooth temperature profile)")
+    ap.add_argument("--hier-levels", type=int, default=4,
+                    help="--hier: bins 0..this (dt_max = 2^levels x the shortest CFL step)")
+    ap.add_argument("--hier-options", default="",
+                    help="--hier: comma-separated sub-step options: wakeup, predict, keep_cells")
     ap.add_argument("--active", type=float, default=0.0,
                     help="latticeN: time the loops on an active subset of this fraction (a "
                          "spherical region) against the full loops, instead of the step")
@@ -775,9 +779,12 @@ def run_hier(args, world: int, rank: int, local: int):
     cells = sph.sph_build_cells(init, t["x"], t["y"], t["z"], t["h0"])
     sph.sph_density(init, cells, part, t["h0"], dout)
     sph.sph_force(init, cells, part, dout, sph.force_out({k: arrays[k] for k in sph.FORCE_FIELDS}))
-    max_bin = 4
+    max_bin = args.hier_levels
     dt_min = float((0.1 * 1.825742 * arrays["h"] / arrays["v_sig"]).min())
-    dt_max = 16.0 * dt_min
+    dt_max = float(2 ** max_bin) * dt_min
+    opts = {o: True for o in args.hier_options.split(",") if o}
+    if set(opts) - {"wakeup", "predict", "keep_cells"}:
+        raise SystemExit(f"unknown --hier-options {args.hier_options}")
     bins = torch.zeros(n, dtype=torch.int32, device="cuda")
     sph.sph_time_bins(init, cells, part, dout, arrays["v_sig"], 0.1, dt_max, max_bin, bins)
     init.close()
@@ -793,7 +800,7 @@ def run_hier(args, world: int, rank: int, local: int):
     tick = 0
     scratch = torch.zeros((), dtype=torch.int64, device="cuda")
     for _ in range(args.warmup):
-        tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick)
+        tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick, **opts)
         scratch += (tb == tick).sum()  # loads the counting kernels before the timed region
     torch.cuda.synchronize()
     sph.sph_kernel_times(ctx)  # reset
@@ -806,7 +813,7 @@ def run_hier(args, world: int, rank: int, local: int):
     per_call = []
     for _ in range(args.steps):
         c0 = time.perf_counter()
-        tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick)
+        tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick, **opts)
         per_call.append(time.perf_counter() - c0)
         active_dev += (tb == tick).sum()
     torch.cuda.synchronize()
@@ -825,6 +832,7 @@ def run_hier(args, world: int, rank: int, local: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "particles": n, "max_bin": max_bin,
                    "u": "10^sin(2 pi x / L)", "bins_at_end": levels, "ticks": tick - ticks0,
+                   "options": sorted(opts), "cell_builds": kt["build"][1],
                    "mean_active_fraction": active / (args.steps * n),
                    "step": "sph_hier_substep (adaptive bins); host wall time, the call "
                            "waits for its tick"},

@@ -356,6 +356,17 @@ int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
  * rho e^(-div_v dt), in place in the pool), and sets P = (gamma - 1) u rho and
  * c = sqrt(gamma P / rho) at the predicted u; the inactive particles enter the
  * loops with these values, the active ones start their h solve from them.
+ * SPH_HIER_KEEP_CELLS: the cells are rebuilt only when they may no longer hold
+ * every pair: while the largest support (gamma_K max h after the drift) plus
+ * twice the drift bound since the last build (max |v| dt summed over the
+ * sub-steps) stays below a cell side, the sub-step keeps the cells of the last
+ * build of this call's kind (positions taken relative to the cell each particle
+ * is filed in, nearest periodic image) and caps the supports of the density
+ * at the cell less twice the drift bound; a support reaching that cap rebuilds
+ * and repeats the density.  The results then differ from a fresh build's by
+ * the FP32 rounding of the relative positions only.  Between calls the pool's
+ * positions must change only through sph_hier_substep (any other build on the
+ * context, or a different n, rebuilds).
  * bins (int32) and t_begin (int64) are device arrays of n, updated in place;
  * 0 <= max_bin <= 40; options: SPH_HIER_* bits (others: SPH_E_INVAL).  With
  * SPH_FLAG_SYNC a density that needs larger cells is rebuilt and repeated.
@@ -363,7 +374,8 @@ int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
 enum {
   SPH_HIER_ADAPT = 1,   /* new bins from the CFL condition and the first limiter */
   SPH_HIER_WAKEUP = 2,  /* the wake-up limiter                                   */
-  SPH_HIER_PREDICT = 4  /* prediction of h, rho, P, c in the drift (below)       */
+  SPH_HIER_PREDICT = 4,    /* prediction of h, rho, P, c in the drift (below)    */
+  SPH_HIER_KEEP_CELLS = 8  /* keep the cells of an earlier sub-step (below)      */
 };
 int sph_hier_substep(sph_ctx* ctx, const sph_pool* pool, int32_t* bins, int64_t* t_begin, double dt_max,
                      int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync, int64_t* t_next_out);

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <cstddef>
 #include <new>
 #include <vector>
 
@@ -68,8 +69,13 @@ struct sph_ctx {
   uint8_t* hact = nullptr;   // time-step hierarchy: active mask (input order)
   int32_t* hbin = nullptr;   // proposed bins
   int32_t* hwake = nullptr;  // wake-up bins
+  int32_t* hcellmin = nullptr;  // per cell: the smallest bin of its inactive particles
   unsigned long long* htick = nullptr;
   int64_t cap_hier = 0;
+  // cells kept across sub-steps (SPH_HIER_KEEP_CELLS): the build they come
+  // from, its cell side, and the drift bound accumulated since
+  int64_t build_epoch = 0, hier_epoch = -1, hier_n = -1;
+  double hier_cell = 0.0, hier_drift = 0.0;
   float4* sx4 = nullptr;   // SPHENIX: sorted (u, alpha_V, P, alpha_c)
   float* dvp = nullptr;    // SPHENIX step: the divergence of the previous evaluation
   int64_t cap_sx = 0;
@@ -259,13 +265,17 @@ int ensure_hier(sph_ctx* c, int64_t n) {
   dfree(c->hact);
   dfree(c->hbin);
   dfree(c->hwake);
+  dfree(c->hcellmin);
   dfree(c->htick);
   c->cap_hier = 0;
   const int64_t cn = n + n / 4 + 64;
-  if (!(dalloc(c->hact, cn) && dalloc(c->hbin, cn) && dalloc(c->hwake, cn) && dalloc(c->htick, 1))) {
+  // cells of one simulation: at most 8 n + 216 (the build's cap), + 1
+  if (!(dalloc(c->hact, cn) && dalloc(c->hbin, cn) && dalloc(c->hwake, cn) && dalloc(c->hcellmin, 8 * cn + 217) &&
+        dalloc(c->htick, 1))) {
     dfree(c->hact);
     dfree(c->hbin);
     dfree(c->hwake);
+    dfree(c->hcellmin);
     dfree(c->htick);
     return SPH_E_NOMEM;
   }
@@ -445,6 +455,7 @@ bool params_ok(const sph_params& p) {
 int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const double* box,
              const double* x, const double* y, const double* z, const float* h, double radius = 0.0,
              int cells_per_particle = 8) {
+  ++c->build_epoch;
   sphh::BuildArgs b;
   b.gamma_k = sphk::kernel_gamma(c->p.kernel);
   b.radius = radius;
@@ -995,6 +1006,7 @@ void sph_destroy(sph_ctx* c) {
   dfree(c->hact);
   dfree(c->hbin);
   dfree(c->hwake);
+  dfree(c->hcellmin);
   dfree(c->htick);
   dfree(c->misc);
   dfree(c->pairs);
@@ -1270,7 +1282,7 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
                      int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync_flags, int64_t* t_next_out) {
   if (!c || !pl || !bins || !tbeg || !t_next_out || pl->n_sims != 1 || pl->n_total < 1 ||
       pl->n_total > INT32_MAX / 16 || !(dt_max > 0.0) || !std::isfinite(dt_max) || max_bin < 0 || max_bin > 40 ||
-      t_now < 0 || (options & ~(SPH_HIER_ADAPT | SPH_HIER_WAKEUP | SPH_HIER_PREDICT)) != 0)
+      t_now < 0 || (options & ~(SPH_HIER_ADAPT | SPH_HIER_WAKEUP | SPH_HIER_PREDICT | SPH_HIER_KEEP_CELLS)) != 0)
     return SPH_E_INVAL;
   const bool adapt = (options & SPH_HIER_ADAPT) != 0, wakeup = (options & SPH_HIER_WAKEUP) != 0;
   if (!pl->sim_offset || !pl->box_size || !pl->x || !pl->y || !pl->z || !pl->vx || !pl->vy || !pl->vz ||
@@ -1321,23 +1333,74 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
   h.P = pl->P;
   h.c = pl->c;
   h.div_v = pl->div_v;
+  const bool keep = (options & SPH_HIER_KEEP_CELLS) != 0;
+  h.vmax2_bits = keep ? reinterpret_cast<unsigned*>(c->misc + sphk::kHierVmax) : nullptr;
+  h.hmax_bits = keep ? reinterpret_cast<unsigned*>(c->misc + sphk::kHierHmax) : nullptr;
   h.t_next = c->htick;
   h.status = c->misc + sphk::kStatus;
   t_begin(c, SPH_T_INTEGRATE);
+  if (keep && cudaMemsetAsync(c->misc + sphk::kHierVmax, 0, 2 * sizeof(int32_t), c->st) != cudaSuccess)
+    return SPH_E_CUDA;
   if (sphh::launch_hier_next(h, c->st) != cudaSuccess || sphh::launch_hier_drift(h, c->st) != cudaSuccess)
     return SPH_E_CUDA;
   t_end(c, SPH_T_INTEGRATE);
+  // SPH_HIER_KEEP_CELLS: the cells of the last build still hold every pair
+  // within the supports while the largest support plus twice the drift bound
+  // since that build (the largest |v| times dt, summed over the sub-steps)
+  // fits a cell; the loops then cap the supports at that reach
+  bool kept = false;
+  double drift = 0.0;
+  if (keep) {
+    unsigned long long tn = 0;
+    uint32_t bits[2] = {0u, 0u};
+    if (cudaMemcpyAsync(&tn, c->htick, sizeof(tn), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(bits, c->misc + sphk::kHierVmax, sizeof(bits), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+    float v2 = 0.0f, hm = 0.0f;
+    memcpy(&v2, &bits[0], sizeof(float));
+    memcpy(&hm, &bits[1], sizeof(float));
+    drift = c->hier_drift + std::sqrt((double)v2) * (double)(tn - (unsigned long long)t_now) * h.tau;
+    const double Hmax = sphk::kernel_gamma(c->p.kernel) * (double)hm;
+    kept = c->hier_epoch == c->build_epoch && c->hier_n == n && c->hier_cell > 0.0 && std::isfinite(drift) &&
+           Hmax * (1.0 + 1e-4) + 2.0 * drift * (1.0 + 1e-6) < c->hier_cell * (1.0 - 1e-5);
+  }
   const bool sync = (c->p.flags & SPH_FLAG_SYNC) != 0;
   for (int attempt = 0;; ++attempt) {
-    rc = do_build(c, 1, n, pl->sim_offset, pl->box_size, pl->x, pl->y, pl->z, pl->h);
-    if (rc != SPH_OK) return rc;
+    if (kept) {
+      // the supports' cap: the cell less twice the drift (rounded down)
+      const float reach = (float)((c->hier_cell - 2.0 * drift * (1.0 + 1e-6)) * (1.0 - 1e-6));
+      if (cudaMemcpyAsync(reinterpret_cast<char*>(c->grid) + offsetof(GridDev, reach_f), &reach, sizeof(float),
+                          cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+        return SPH_E_CUDA;
+      c->hier_drift = drift;
+    } else {
+      rc = do_build(c, 1, n, pl->sim_offset, pl->box_size, pl->x, pl->y, pl->z, pl->h);
+      if (rc != SPH_OK) return rc;
+      if (keep) {
+        double cell = 0.0;
+        if (cudaMemcpyAsync(&cell, reinterpret_cast<char*>(c->grid) + offsetof(GridDev, cell), sizeof(double),
+                            cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+            cudaStreamSynchronize(c->st) != cudaSuccess)
+          return SPH_E_CUDA;
+        c->hier_epoch = c->build_epoch;
+        c->hier_n = n;
+        c->hier_cell = cell;
+        c->hier_drift = 0.0;
+      }
+    }
     rc = do_density(c, pl->x, pl->y, pl->z, c->vpx, c->vpy, c->vpz, pl->m, c->up, pl->h, pl->h, pl->rho, pl->f,
                     pl->div_v, pl->curl_v, pl->P, pl->c, pl->balsara, pl->n_iter, c->hact);
     if (rc != SPH_OK) return rc;
-    if (!sync) break;
+    if (!sync && !kept) break;
     int32_t st = 0;
     rc = read_status(c, &st);
     if (rc != SPH_OK) return rc;
+    if (kept && (st & SPH_ST_REBUILD)) {
+      // a support reached the kept cells' reach: build afresh and repeat
+      kept = false;
+      continue;
+    }
     if (!(st & SPH_ST_REBUILD) || attempt >= 8) {
       const int code = code_of_status(st);
       if (code != SPH_OK) return code;
@@ -1384,6 +1447,10 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
     w.act = c->hact;
     w.bin = bins;
     w.wake = c->hwake;
+    w.act_s = c->act_s;
+    w.pos4 = c->pos4;
+    w.cellmin = c->hcellmin;
+    w.total_cells = c->misc + sphk::kTotalCells;
     if (sphh::launch_hier_wake(w, c->st) != cudaSuccess) return SPH_E_CUDA;
     h.wake = c->hwake;
   }

@@ -91,6 +91,7 @@ __global__ void k_grid_setup(const int64_t* __restrict__ sim_offset, const doubl
     g.n_c = nc;
     g.cell = L / (double)nc;
     g.cell_f = (float)g.cell;
+    g.reach_f = g.cell_f;
     g.scale_f = (float)((double)nc / L);
     g.cell_base = 0;
     g.blk_base = 0;
@@ -254,9 +255,9 @@ __global__ void k_gather_density(int64_t n_total, const int32_t* __restrict__ pe
     const GridDev G = grid[sim_of_cell(grid, n_sims, c)];
     const int32_t local = c - G.cell_base;
     const int32_t kx = local % G.n_c, ky = (local / G.n_c) % G.n_c, kz = local / (G.n_c * G.n_c);
-    const float rx = (float)(x[p] - (double)kx * G.cell);
-    const float ry = (float)(y[p] - (double)ky * G.cell);
-    const float rz = (float)(z[p] - (double)kz * G.cell);
+    const float rx = (float)cell_offset(x[p], kx, G);
+    const float ry = (float)cell_offset(y[p], ky, G);
+    const float rz = (float)cell_offset(z[p], kz, G);
     pos4[s] = make_float4(rx, ry, rz, m[p]);
     vel4[s] = make_float4(vx[p], vy[p], vz[p], u[p]);
     hs[s] = h[p];
@@ -303,9 +304,9 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
       const GridDev G = grid[sim_of_cell(grid, n_sims, cc)];
       const int32_t local = cc - G.cell_base;
       const int32_t kx = local % G.n_c, ky = (local / G.n_c) % G.n_c, kz = local / (G.n_c * G.n_c);
-      const float rx = (float)(x[p] - (double)kx * G.cell);
-      const float ry = (float)(y[p] - (double)ky * G.cell);
-      const float rz = (float)(z[p] - (double)kz * G.cell);
+      const float rx = (float)cell_offset(x[p], kx, G);
+      const float ry = (float)cell_offset(y[p], ky, G);
+      const float rz = (float)cell_offset(z[p], kz, G);
       fA[s] = make_float4(rx, ry, rz, H);
     } else {
       reinterpret_cast<float*>(fA)[4 * s + 3] = H;

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
     else
       __syncthreads();  // the staging
 
-    const float hcap = h_cap<K>((double)g.G.cell_f, g.G.L);
+    const float hcap = h_cap<K>((double)g.G.reach_f, g.G.L);
     const float R2 = g.G.cell_f * g.G.cell_f;
     const int tpp = BT.tpp, lg = BT.lg, per = BT.per;
     const int sub = lane & (tpp - 1);
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
       spos[slot] = p;
       svel[slot] = a.vel4[j];
     };
-    const float hcap = h_cap<K>((double)g.G.cell_f, g.G.L);
+    const float hcap = h_cap<K>((double)g.G.reach_f, g.G.L);
     for (int32_t t0 = ts; t0 < te; t0 += 32) {
       const int32_t ti = t0 + lane;
       const bool valid = ti < te && (a.act == nullptr || a.act[ti] != 0);

@@ -6,6 +6,8 @@
 // particle drifts with it, and at the end of its step it gets the second half
 // kick with the new acceleration, a new bin, and the first half kick of the
 // next step.
+#include <climits>
+
 #include "sph_internal.cuh"
 #include "sph_launch.h"
 
@@ -40,7 +42,9 @@ __global__ void k_hier_drift(sphh::HierArgs a) {
   const int64_t tn = (int64_t)*a.t_next;
   const double dt = (double)(tn - a.t_now) * a.tau;
   const double L = a.box;
+  float v2max = 0.0f, hmax = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    v2max = fmaxf(v2max, fmaf(a.vx[i], a.vx[i], fmaf(a.vy[i], a.vy[i], a.vz[i] * a.vz[i])));
     const int64_t s = step_ticks(a.bin[i], a.max_bin);
     double x = fma((double)a.vx[i], dt, a.x[i]), y = fma((double)a.vy[i], dt, a.y[i]),
            z = fma((double)a.vz[i], dt, a.z[i]);
@@ -69,6 +73,19 @@ __global__ void k_hier_drift(sphh::HierArgs a) {
       a.P[i] = P;
       a.c[i] = sqrtf(a.gamma * P / rho);
     }
+    hmax = fmaxf(hmax, a.h[i]);
+  }
+  if (a.vmax2_bits != nullptr) {
+    // non-negative floats order like their bits
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v2max = fmaxf(v2max, __shfl_xor_sync(0xffffffffu, v2max, o));
+      hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(a.vmax2_bits, __float_as_uint(v2max));
+      atomicMax(a.hmax_bits, __float_as_uint(hmax));
+    }
   }
 }
 
@@ -87,42 +104,86 @@ __device__ __forceinline__ int32_t wrap_cell(int32_t k, int32_t nc) {
   return k >= nc ? k - nc : k;
 }
 
+// Per cell, the smallest bin among its inactive particles (the wake-up pass
+// walks only around active particles whose new bin is more than two above the
+// smallest bin in their 27 cells).
+__global__ void k_hier_cellmin_init(int32_t* __restrict__ cellmin, const int32_t* __restrict__ total_cells) {
+  const int32_t nc = *total_cells;
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) cellmin[c] = INT_MAX;
+}
+__global__ void k_hier_cellmin(sphh::WakeArgs a) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += (int64_t)gridDim.x * blockDim.x) {
+    if (a.act_s[s]) continue;
+    const int32_t p = a.perm[s];
+    atomicMin(&a.cellmin[a.key[p]], a.bin[p]);
+  }
+}
+
 // The wake-up limiter's neighbour pass (Sec. 3.4, after Saitoh & Makino
 // 2009): once the active particles hold their new bins, every inactive
 // force-loop neighbour j of an active i (r_ij < max(H_i, H_j), minimum image,
 // decided in FP64) whose step is more than 4 times longer, bin_j < bin_i - 2,
-// gets wake[j] = max(wake[j], bin_i - 2).  A warp takes 32 particles at a time
-// and walks the cells around each active one, a lane per candidate; the cells
-// of the build are at least as wide as every H, so the 27 cells around i's
-// (the distinct ones when n_c < 3) hold all its neighbours.
+// gets wake[j] = max(wake[j], bin_i - 2).  A warp takes 32 particles of the
+// sorted order at a time and walks the cells around each active one, a lane
+// per candidate (sorted, so the loads of a cell's candidates coalesce): the
+// inactive ones within max(H_i, H_j) by the loops' FP32 cell-relative
+// positions, with a margin far above their rounding, get the bin test and
+// then the FP64 decision.  The cells are at least as wide as every H, so the
+// 27 cells around i's (the distinct ones when n_c < 3, without the FP32 test)
+// hold all its neighbours.
 __global__ void k_hier_wake(sphh::WakeArgs a) {
   const GridDev G = a.grid[0];
   const int32_t nc = G.n_c;
   const int d0 = nc >= 3 ? -1 : 0, d1 = nc >= 3 ? 1 : nc - 1;
+  const bool pre = nc >= 3;
   const double L = G.L;
+  const float cs = G.cell_f;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (((int64_t)gridDim.x * blockDim.x) >> 5) << 5;
   for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; base < a.n; base += stride) {
     const int64_t me = base + lane;
-    unsigned m = __ballot_sync(0xffffffffu, me < a.n && a.act[me] != 0);
+    unsigned m = __ballot_sync(0xffffffffu, me < a.n && a.act_s[me] != 0);
     while (m != 0u) {
-      const int64_t i = base + (__ffs((int)m) - 1);
+      const int64_t si = base + (__ffs((int)m) - 1);
       m &= m - 1u;
+      const int32_t i = a.perm[si];
       const int32_t w = a.bin[i] - 2;
       if (w <= 0) continue;  // no bin lies below
-      const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
-      const double Hi = a.gamma * (double)a.h[i];
       const int32_t c = a.key[i] - G.cell_base;
       const int32_t kx = c % nc, ky = (c / nc) % nc, kz = c / (nc * nc);
+      {
+        // skip when no inactive particle of the 27 cells steps in a bin below w
+        const int nd = d1 - d0 + 1;
+        int32_t lo = INT_MAX;
+        if (lane < nd * nd * nd) {
+          const int dx = d0 + lane % nd, dy = d0 + (lane / nd) % nd, dz = d0 + lane / (nd * nd);
+          lo = a.cellmin[G.cell_base + wrap_cell(kx + dx, nc) +
+                         nc * (wrap_cell(ky + dy, nc) + nc * wrap_cell(kz + dz, nc))];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        if (lo >= w) continue;
+      }
+      const float4 Pi = a.pos4[si];
+      const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
+      const double Hi = a.gamma * (double)a.h[i];
       for (int dz = d0; dz <= d1; ++dz)
         for (int dy = d0; dy <= d1; ++dy)
           for (int dx = d0; dx <= d1; ++dx) {
             const int32_t cn =
                 G.cell_base + wrap_cell(kx + dx, nc) + nc * (wrap_cell(ky + dy, nc) + nc * wrap_cell(kz + dz, nc));
+            const float ox = (float)dx * cs, oy = (float)dy * cs, oz = (float)dz * cs;
             const int32_t t1 = a.cell_start[cn + 1];
             for (int32_t t = a.cell_start[cn] + lane; t < t1; t += 32) {
+              if (a.act_s[t]) continue;
+              if (pre) {
+                const float4 Pj = a.pos4[t];
+                const float fx = Pi.x - (Pj.x + ox), fy = Pi.y - (Pj.y + oy), fz = Pi.z - (Pj.z + oz);
+                const float Hm = fmaxf(Pi.w, Pj.w);
+                if (fmaf(fx, fx, fmaf(fy, fy, fz * fz)) >= Hm * Hm * (1.0f + 1e-4f)) continue;
+              }
               const int32_t j = a.perm[t];
-              if (a.act[j] || a.bin[j] >= w) continue;
+              if (a.bin[j] >= w) continue;
               double ex = a.x[j] - xi, ey = a.y[j] - yi, ez = a.z[j] - zi;
               ex -= L * rint(ex / L);
               ey -= L * rint(ey / L);
@@ -225,6 +286,8 @@ cudaError_t launch_hier_wake(const WakeArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.wake, 0xff, (size_t)a.n * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
+  k_hier_cellmin_init<<<grid_h(a.n), 256, 0, st>>>(a.cellmin, a.total_cells);
+  k_hier_cellmin<<<grid_h(a.n), 256, 0, st>>>(a);
   k_hier_wake<<<grid_h(a.n), 256, 0, st>>>(a);
   return cudaGetLastError();
 }

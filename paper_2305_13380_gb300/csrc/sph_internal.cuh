@@ -26,7 +26,9 @@ enum MiscSlot {
   kNumOverflow = 4,  // blocks queued for the overflow kernel of a loop
   kTreeFbCount = 5,  // targets queued for the coarser-level solve of the tree loops
   kTreeFbWork = 6,   // queue counter of the tree fallback kernels
-  kMiscWords = 8
+  kHierVmax = 7,     // largest |v| of a sub-step's drift (float bits)
+  kHierHmax = 8,     // largest h after a sub-step's drift (float bits)
+  kMiscWords = 10
 };
 
 // One simulation's grid, computed on the device by the build.
@@ -38,6 +40,8 @@ struct GridDev {
   int32_t cell_base;  // first global cell id of this simulation
   int32_t blk_base;   // first global 2x2x2-block id of this simulation
   float scale_f;      // n_c / L in FP32 (estimates of cell coordinates)
+  float reach_f;      // largest support the cells serve: cell_f after a build,
+                      // less twice the drift since, while cells are kept
   int64_t part_base;  // first pool index of this simulation
   int64_t n;          // particles in this simulation
 };
@@ -205,6 +209,19 @@ struct SimCursor {
     return s;
   }
 };
+
+// Offset of a position from the lower corner of the cell k it is filed in
+// (FP64).  After a build it lies in [0, cell); while a sub-step keeps the
+// cells of an earlier build a particle may have drifted a little out of its
+// cell, and across the periodic boundary: the image nearest the cell is taken
+// (no change to an offset within half a box of the cell's centre).
+__device__ __forceinline__ double cell_offset(double x, int32_t k, const GridDev& G) {
+  double d = x - (double)k * G.cell;
+  const double o = d - 0.5 * G.cell;
+  if (o > 0.5 * G.L) d -= G.L;
+  else if (o < -0.5 * G.L) d += G.L;
+  return d;
+}
 
 // Simulation owning a global cell id.
 __device__ __forceinline__ int sim_of_cell(const GridDev* __restrict__ grid, int n_sims, int32_t c) {

@@ -212,6 +212,9 @@ struct HierArgs {
   uint8_t* act;            // active mask (scratch, input order)
   uint8_t* sync;           // synchronisation flags (nullptr: none; cleared)
   const int32_t* wake;     // wake-up bins (nullptr: no wake-up pass)
+  // largest |v|^2 of the drift and largest h after it (float bits, reset by
+  // the caller; nullptr: not taken)
+  unsigned *vmax2_bits, *hmax_bits;
   // prediction of h, rho, P and c in the drift (predict != 0)
   int predict;
   float gamma;  // adiabatic index
@@ -231,6 +234,12 @@ struct WakeArgs {
   const uint8_t* act;
   const int32_t* bin;
   int32_t* wake;  // written: -1, or the largest bin_i - 2 above bin_j
+  // sorted copies of this sub-step's loops: the active mask, and the
+  // cell-relative positions with H (the force gather's records)
+  const uint8_t* act_s;
+  const float4* pos4;
+  int32_t* cellmin;            // scratch, one per cell
+  const int32_t* total_cells;  // device count of the build's cells
 };
 cudaError_t launch_hier_next(const HierArgs& a, cudaStream_t st);
 cudaError_t launch_hier_drift(const HierArgs& a, cudaStream_t st);

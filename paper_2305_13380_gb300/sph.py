@@ -40,6 +40,7 @@ SPH_FLAG_SYMMETRIC = 32
 SPH_HIER_ADAPT = 1
 SPH_HIER_WAKEUP = 2
 SPH_HIER_PREDICT = 4
+SPH_HIER_KEEP_CELLS = 8
 SPH_KERNEL_CUBIC, SPH_KERNEL_QUARTIC, SPH_KERNEL_WENDLAND_C2 = 0, 1, 2
 
 TIMING_GROUPS = ("build", "gather", "density", "force", "integrate")
@@ -302,12 +303,13 @@ def sph_force(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_den
 
 
 def sph_hier_substep(ctx: Context, pl: sph_pool, bins, t_begin, dt_max: float, max_bin: int, t_now: int,
-                     adapt: bool = True, wakeup: bool = False, sync=None, predict: bool = False) -> int:
+                     adapt: bool = True, wakeup: bool = False, sync=None, predict: bool = False,
+                     keep_cells: bool = False) -> int:
     """One sub-step of the time-step hierarchy; returns the new tick.  sync is
     an optional uint8 device tensor of flags (cleared by the call)."""
     t_next = C.c_int64(0)
     opts = (SPH_HIER_ADAPT if adapt else 0) | (SPH_HIER_WAKEUP if wakeup else 0) | \
-        (SPH_HIER_PREDICT if predict else 0)
+        (SPH_HIER_PREDICT if predict else 0) | (SPH_HIER_KEEP_CELLS if keep_cells else 0)
     _check(lib().sph_hier_substep(ctx.handle, C.byref(pl), _ptr(bins, torch.int32), _ptr(t_begin, torch.int64),
                                   C.c_double(dt_max), C.c_int32(max_bin), C.c_int64(t_now), C.c_int32(opts),
                                   None if sync is None else _ptr(sync, torch.uint8), C.byref(t_next)),

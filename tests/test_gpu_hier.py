@@ -72,8 +72,8 @@ def _compare(g, s, d, predict=False):
     assert np.allclose(g["h"], s["h"], rtol=1e-5)
 
 
-@pytest.mark.parametrize("predict", [False, True])
-def test_fixed_bins_over_four_substeps(orc, predict):
+@pytest.mark.parametrize("predict,keep", [(False, False), (True, False), (True, True)])
+def test_fixed_bins_over_four_substeps(orc, predict, keep):
     import torch
     from paper_2305_13380_gb300 import sph
     s = _state(orc, 3)
@@ -86,20 +86,27 @@ def test_fixed_bins_over_four_substeps(orc, predict):
     arr, pool = _pool(s)
     gb = torch.tensor(bins, device="cuda")
     gt = torch.zeros(n, dtype=torch.int64, device="cuda")
-    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC | sph.SPH_FLAG_TIMING))
     tb = np.zeros(n, np.int64)
     t = tg = 0
+    calls = 0
     while t < 4:
-        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=False, predict=predict)
+        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=False, predict=predict,
+                                  keep_cells=keep)
         t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, False, predict=predict)
         assert tg == t
+        calls += 1
     assert np.array_equal(gt.cpu().numpy(), tb) and np.array_equal(gb.cpu().numpy(), bins)
     g = {k: v.cpu().numpy() for k, v in arr.items()}
     _compare(g, s, 1.0 / 12, predict)
+    builds = sph.sph_kernel_times(ctx)["build"][1]
+    # kept cells: the first sub-step builds, later ones keep its cells while
+    # the drift leaves room in them
+    assert (builds < calls) if keep else (builds == calls)
 
 
-@pytest.mark.parametrize("predict", [False, True])
-def test_adaptive_bins(orc, predict):
+@pytest.mark.parametrize("predict,keep", [(False, False), (True, False), (True, True)])
+def test_adaptive_bins(orc, predict, keep):
     import torch
     from paper_2305_13380_gb300 import sph
     s = _state(orc, 5, u_spread=True)
@@ -115,7 +122,8 @@ def test_adaptive_bins(orc, predict):
     tb = np.zeros(n, np.int64)
     t = tg = 0
     for _ in range(3):
-        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=True, predict=predict)
+        tg = sph.sph_hier_substep(ctx, pool, gb, gt, dt_max, max_bin, tg, adapt=True, predict=predict,
+                                  keep_cells=keep)
         t = orc.hier_substep(s, bins, tb, dt_max, max_bin, t, True, predict=predict)
         assert tg == t
         g_bins, g_tb = gb.cpu().numpy(), gt.cpu().numpy()
