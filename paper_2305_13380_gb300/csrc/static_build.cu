@@ -27,7 +27,7 @@ constexpr int64_t kStaticHist = 256 * ((kStaticMaxN + 2047) / 2048) + 16;
 
 // Layout of the scratch, in 4-byte words, each part 256-byte aligned.
 constexpr int64_t align64(int64_t w) { return (w + 63) / 64 * 64; }
-constexpr int64_t kOffGrid = 0;  // one GridDev (48 bytes)
+constexpr int64_t kOffGrid = 0;  // one GridDev
 constexpr int64_t kOffOffset = kOffGrid + align64(sizeof(sphk::GridDev) / 4);  // int64[2]
 constexpr int64_t kOffBox = kOffOffset + 64;                                     // double[1]
 constexpr int64_t kOffMisc = kOffBox + 64;                                       // int32[8]
