@@ -94,6 +94,9 @@ def parse():
                     help="--hier: bins 0..this (dt_max = 2^levels x the shortest CFL step)")
     ap.add_argument("--hier-options", default="",
                     help="--hier: comma-separated sub-step options: wakeup, predict, keep_cells")
+    ap.add_argument("--hier-hot", type=float, default=0.0,
+                    help="--hier: instead of the smooth profile, a hot sphere (u x 100) holding this "
+                         "fraction of the particles in gas at u = 1: few particles on short steps")
     ap.add_argument("--active", type=float, default=0.0,
                     help="latticeN: time the loops on an active subset of this fraction (a "
                          "spherical region) against the full loops, instead of the step")
@@ -765,9 +768,19 @@ def run_hier(args, world: int, rank: int, local: int):
     if p["tree"]:
         raise SystemExit("the hierarchy runs on the uniform grid (latticeN workloads)")
     n, L = len(p["x"]), float(p["L"])
-    # a smooth temperature profile along x over a decade in sound speed:
-    # hot and cold slabs with their own step lengths, no violent mixing
-    p["u"] = 10.0 ** (np.sin(2.0 * np.pi * np.asarray(p["x"]) / L))
+    if args.hier_hot > 0.0:
+        # a hot sphere (sound speed x 10) in uniform gas: its particles step
+        # 8-16 times shorter than the rest
+        X = np.stack([np.asarray(p[k]) for k in ("x", "y", "z")], 1) - 0.5 * L
+        r = np.sqrt((X ** 2).sum(1))
+        rad = float(np.quantile(r, args.hier_hot))
+        p["u"] = np.where(r <= rad, 100.0, 1.0)
+        profile = f"hot sphere (u = 100) of {args.hier_hot:g} of the particles in u = 1"
+    else:
+        # a smooth temperature profile along x over a decade in sound speed:
+        # hot and cold slabs with their own step lengths, no violent mixing
+        p["u"] = 10.0 ** (np.sin(2.0 * np.pi * np.asarray(p["x"]) / L))
+        profile = "10^sin(2 pi x / L)"
     t = sph.to_device(p)
     arrays = {k: t[k].clone() for k in ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
     for k in ("h", "ax", "ay", "az", "du_dt", "v_sig", "rho", "f", "div_v", "curl_v", "P", "c", "balsara"):
@@ -831,7 +844,7 @@ def run_hier(args, world: int, rank: int, local: int):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "particles": n, "max_bin": max_bin,
-                   "u": "10^sin(2 pi x / L)", "bins_at_end": levels, "ticks": tick - ticks0,
+                   "u": profile, "bins_at_end": levels, "ticks": tick - ticks0,
                    "options": sorted(opts), "cell_builds": kt["build"][1],
                    "mean_active_fraction": active / (args.steps * n),
                    "step": "sph_hier_substep (adaptive bins); host wall time, the call "

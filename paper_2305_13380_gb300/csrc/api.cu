@@ -1362,8 +1362,11 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
     memcpy(&hm, &bits[1], sizeof(float));
     drift = c->hier_drift + std::sqrt((double)v2) * (double)(tn - (unsigned long long)t_now) * h.tau;
     const double Hmax = sphk::kernel_gamma(c->p.kernel) * (double)hm;
+    // room for the active supports to grow in this sub-step's solve (2 %):
+    // a support that reaches the reach anyway costs a rebuild and a second
+    // density
     kept = c->hier_epoch == c->build_epoch && c->hier_n == n && c->hier_cell > 0.0 && std::isfinite(drift) &&
-           Hmax * (1.0 + 1e-4) + 2.0 * drift * (1.0 + 1e-6) < c->hier_cell * (1.0 - 1e-5);
+           Hmax * 1.02 + 2.0 * drift * (1.0 + 1e-6) < c->hier_cell * (1.0 - 1e-5);
   }
   const bool sync = (c->p.flags & SPH_FLAG_SYNC) != 0;
   for (int attempt = 0;; ++attempt) {
