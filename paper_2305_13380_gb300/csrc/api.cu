@@ -64,6 +64,7 @@ struct sph_ctx {
   float4* trec = nullptr;  // force records of the nested grids, 4 per particle
   uint8_t* act_s = nullptr;         // sorted active mask (masked loops)
   uint8_t* blk_any = nullptr;       // blocks holding an active particle
+  uint8_t* blk_need = nullptr;      // those blocks and their neighbours (the gathers' set)
   int64_t cap_act = 0, cap_blk = 0;
   const uint8_t* lists_mask = nullptr;  // the mask the current lists were built with
   uint8_t* hact = nullptr;   // time-step hierarchy: active mask (input order)
@@ -290,11 +291,13 @@ int ensure_act(sph_ctx* c, int64_t n) {
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
   dfree(c->act_s);
   dfree(c->blk_any);
+  dfree(c->blk_need);
   c->cap_act = c->cap_blk = 0;
   const int64_t cn = n + n / 4 + 64;
-  if (!dalloc(c->act_s, cn) || !dalloc(c->blk_any, c->cap_cells + 1)) {
+  if (!dalloc(c->act_s, cn) || !dalloc(c->blk_any, c->cap_cells + 1) || !dalloc(c->blk_need, c->cap_cells + 1)) {
     dfree(c->act_s);
     dfree(c->blk_any);
+    dfree(c->blk_need);
     return SPH_E_NOMEM;
   }
   c->cap_act = cn;
@@ -647,6 +650,18 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
   g.pos4 = c->pos4;
   g.vel4 = c->vel4;
   g.hs = c->hs;
+  if (active) {
+    // the masked loops read only the blocks around the active particles:
+    // the mask first, then the gather of those blocks' particles
+    const int rc = ensure_act(c, c->built_n);
+    if (rc != SPH_OK) return rc;
+    if (sphh::launch_gather_mask(c->built_n, c->perm, c->key, c->grid, active, c->act_s, c->blk_any, c->cap_blk,
+                                 c->st) != cudaSuccess ||
+        sphh::launch_dilate_blocks(c->grid, c->misc + sphk::kTotalBlocks, c->blk_any, c->blk_need, c->cap_blk,
+                                   c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+    g.blk_need = c->blk_need;
+  }
   t_begin(c, SPH_T_GATHER);
   if (sphh::launch_gather_density(g, c->st) != cudaSuccess) return SPH_E_CUDA;
   const bool axis = (c->p.flags & SPH_FLAG_AXIS_SORT) != 0;
@@ -670,11 +685,6 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
       return SPH_E_CUDA;
   sphh::DensityArgs d;
   if (active) {
-    const int rc = ensure_act(c, c->built_n);
-    if (rc != SPH_OK) return rc;
-    if (sphh::launch_gather_mask(c->built_n, c->perm, c->key, c->grid, active, c->act_s, c->blk_any, c->cap_blk,
-                                 c->st) != cudaSuccess)
-      return SPH_E_CUDA;
     d.act = c->act_s;
     d.blk_any = c->blk_any;
   }
@@ -787,6 +797,17 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
     g.rel = c->rel;
     g.fine = c->fine;
     g.rec = c->trec;
+  }
+  if (active) {
+    // as in the density: the mask, and the gather of the blocks around it
+    const int rc = ensure_act(c, c->built_n);
+    if (rc != SPH_OK) return rc;
+    if (sphh::launch_gather_mask(c->built_n, c->perm, c->key, c->grid, active, c->act_s, c->blk_any, c->cap_blk,
+                                 c->st) != cudaSuccess ||
+        sphh::launch_dilate_blocks(c->grid, c->misc + sphk::kTotalBlocks, c->blk_any, c->blk_need, c->cap_blk,
+                                   c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+    g.blk_need = c->blk_need;
   }
   t_begin(c, SPH_T_GATHER);
   if (!(sx && sx->skip_gather) && sphh::launch_gather_force(g, c->st) != cudaSuccess) return SPH_E_CUDA;
@@ -905,11 +926,6 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
     return cuda_code(e);
   }
   if (active) {
-    const int rc = ensure_act(c, c->built_n);
-    if (rc != SPH_OK) return rc;
-    if (sphh::launch_gather_mask(c->built_n, c->perm, c->key, c->grid, active, c->act_s, c->blk_any, c->cap_blk,
-                                 c->st) != cudaSuccess)
-      return SPH_E_CUDA;
     a.act = c->act_s;
     a.blk_any = c->blk_any;
   }
@@ -1003,6 +1019,7 @@ void sph_destroy(sph_ctx* c) {
   dfree(c->dvp);
   dfree(c->act_s);
   dfree(c->blk_any);
+  dfree(c->blk_need);
   dfree(c->hact);
   dfree(c->hbin);
   dfree(c->hwake);
@@ -1295,16 +1312,12 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
   if (rc == SPH_OK) rc = ensure_hier(c, n);
   if (rc == SPH_OK && adapt) rc = ensure_sphenix(c, n);
   if (rc != SPH_OK) return rc;
-  double box = 0.0;
-  if (cudaMemcpyAsync(&box, pl->box_size, sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
-      cudaStreamSynchronize(c->st) != cudaSuccess)
-    return SPH_E_CUDA;
   sphh::HierArgs h;
   h.n = n;
   h.max_bin = max_bin;
   h.t_now = t_now;
   h.tau = std::ldexp(dt_max, -max_bin);
-  h.box = box;
+  h.box = pl->box_size;
   h.x = pl->x;
   h.y = pl->y;
   h.z = pl->z;

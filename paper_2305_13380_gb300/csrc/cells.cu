@@ -247,12 +247,14 @@ __global__ void k_gather_density(int64_t n_total, const int32_t* __restrict__ pe
                                  const float* __restrict__ vy, const float* __restrict__ vz,
                                  const float* __restrict__ m, const float* __restrict__ u,
                                  const float* __restrict__ h, float4* __restrict__ pos4,
-                                 float4* __restrict__ vel4, float* __restrict__ hs) {
+                                 float4* __restrict__ vel4, float* __restrict__ hs,
+                                 const uint8_t* __restrict__ blk_need) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_total;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p = perm[s];
     const int32_t c = key[p];
     const GridDev G = grid[sim_of_cell(grid, n_sims, c)];
+    if (blk_need != nullptr && !blk_need[block_of_cell(c, G)]) continue;
     const int32_t local = c - G.cell_base;
     const int32_t kx = local % G.n_c, ky = (local / G.n_c) % G.n_c, kz = local / (G.n_c * G.n_c);
     const float rx = (float)cell_offset(x[p], kx, G);
@@ -282,10 +284,15 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
                                const float* __restrict__ B, float4* __restrict__ fA,
                                float4* __restrict__ fB, float4* __restrict__ fC,
                                float2* __restrict__ fD, const float4* __restrict__ trel,
-                               const int4* __restrict__ tfine, float4* __restrict__ rec, float gamma_k) {
+                               const int4* __restrict__ tfine, float4* __restrict__ rec, float gamma_k,
+                               const uint8_t* __restrict__ blk_need) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_total;
        s += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p = perm[s];
+    if (blk_need != nullptr) {
+      const int32_t cc = key[p];
+      if (!blk_need[block_of_cell(cc, grid[sim_of_cell(grid, n_sims, cc)])]) continue;
+    }
     const float H = gamma_k * h[p];
     if (rec != nullptr) {
       // nested grids: one record per source (the arrays below are not read)
@@ -315,6 +322,27 @@ __global__ void k_gather_force(int64_t n_total, const int32_t* __restrict__ perm
     const float r = rho[p];
     fC[s] = make_float4(f[p] * P[p] / (r * r), f[p], c[p], B[p]);
     fD[s] = make_float2(r, 1.0f / H);
+  }
+}
+
+// blk_need[b] = 1 where block b or one of its 26 periodic neighbours holds an
+// active particle (simulation 0): the blocks whose cells the masked loops
+// stage or walk.
+__global__ void k_dilate_blocks(const GridDev* __restrict__ grid, const int32_t* __restrict__ total_blocks,
+                                const uint8_t* __restrict__ blk_any, uint8_t* __restrict__ blk_need) {
+  const GridDev G = grid[0];
+  const int32_t nb = (G.n_c + 1) >> 1, nblk = *total_blocks;
+  for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+    const int32_t l = b - G.blk_base;
+    const int32_t bx = l % nb, by = (l / nb) % nb, bz = l / (nb * nb);
+    uint8_t any = 0;
+    for (int dz = -1; dz <= 1 && !any; ++dz)
+      for (int dy = -1; dy <= 1 && !any; ++dy)
+        for (int dx = -1; dx <= 1 && !any; ++dx) {
+          const int32_t x = (bx + dx + nb) % nb, y = (by + dy + nb) % nb, z = (bz + dz + nb) % nb;
+          any = blk_any[G.blk_base + x + nb * (y + nb * z)];
+        }
+    blk_need[b] = any;
   }
 }
 
@@ -386,7 +414,7 @@ cudaError_t launch_gather_density(const GatherDensityArgs& a, cudaStream_t st) {
   if (a.n_total <= 0) return cudaSuccess;
   k_gather_density<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
       a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.u, a.h,
-      a.pos4, a.vel4, a.hs);
+      a.pos4, a.vel4, a.hs, a.blk_need);
   return cudaGetLastError();
 }
 
@@ -395,7 +423,13 @@ cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st) {
   auto kern = a.positions ? k_gather_force<true> : k_gather_force<false>;
   kern<<<grid_for(a.n_total, 256, 65535), 256, 0, st>>>(
       a.n_total, a.perm, a.key, a.grid, a.n_sims, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.m, a.h, a.rho,
-      a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD, a.rel, a.fine, a.rec, a.gamma_k);
+      a.f, a.P, a.c, a.B, a.fA, a.fB, a.fC, a.fD, a.rel, a.fine, a.rec, a.gamma_k, a.blk_need);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dilate_blocks(const GridDev* grid, const int32_t* total_blocks, const uint8_t* blk_any,
+                                 uint8_t* blk_need, int64_t blk_cap, cudaStream_t st) {
+  k_dilate_blocks<<<grid_for(blk_cap, 256, 65535), 256, 0, st>>>(grid, total_blocks, blk_any, blk_need);
   return cudaGetLastError();
 }
 

@@ -223,6 +223,14 @@ __device__ __forceinline__ double cell_offset(double x, int32_t k, const GridDev
   return d;
 }
 
+// Global 2x2x2-block id of a global cell id of simulation G.
+__device__ __forceinline__ int32_t block_of_cell(int32_t c, const GridDev& G) {
+  const int32_t nc = G.n_c, nb = (nc + 1) >> 1;
+  const int32_t local = c - G.cell_base;
+  const int32_t kx = local % nc, ky = (local / nc) % nc, kz = local / (nc * nc);
+  return G.blk_base + (kx >> 1) + nb * ((ky >> 1) + nb * (kz >> 1));
+}
+
 // Simulation owning a global cell id.
 __device__ __forceinline__ int sim_of_cell(const GridDev* __restrict__ grid, int n_sims, int32_t c) {
   int lo = 0, hi = n_sims - 1;

@@ -69,6 +69,9 @@ struct GatherDensityArgs {
   const float *vx, *vy, *vz, *m, *u, *h;
   float4 *pos4, *vel4;
   float* hs;
+  // masked loops (one simulation): only the particles of the blocks flagged
+  // here are gathered (nullptr: every particle)
+  const uint8_t* blk_need = nullptr;
 };
 cudaError_t launch_gather_density(const GatherDensityArgs& a, cudaStream_t st);
 
@@ -92,8 +95,13 @@ struct GatherForceArgs {
   const int4* fine = nullptr;
   float4* rec = nullptr;
   float gamma_k = sphk::kGammaK;  // H / h of the kernel
+  const uint8_t* blk_need = nullptr;  // as for the density gather
 };
 cudaError_t launch_gather_force(const GatherForceArgs& a, cudaStream_t st);
+// Blocks within one block of a block holding an active particle (the blocks
+// whose staged cells the masked loops read), one simulation, periodic.
+cudaError_t launch_dilate_blocks(const sphk::GridDev* grid, const int32_t* total_blocks, const uint8_t* blk_any,
+                                 uint8_t* blk_need, int64_t blk_cap, cudaStream_t st);
 // Sorted copy of an active mask (act_s[s] = active[perm[s]]) and the flags
 // of the blocks holding an active particle (blk_any, blk_cap bytes cleared
 // first; one simulation).
@@ -201,7 +209,7 @@ struct HierArgs {
   int max_bin;
   int64_t t_now;
   double tau;  // dt_max / 2^max_bin
-  double box;
+  const double* box;  // the pool's box side (device)
   double *x, *y, *z;
   float *vx, *vy, *vz, *u;            // half-kicked for the current step
   const float *ax, *ay, *az, *du_dt;  // last force of each particle
