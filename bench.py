@@ -93,7 +93,8 @@ def parse():
     ap.add_argument("--hier-levels", type=int, default=4,
                     help="--hier: bins 0..this (dt_max = 2^levels x the shortest CFL step)")
     ap.add_argument("--hier-options", default="",
-                    help="--hier: comma-separated sub-step options: wakeup, predict, keep_cells")
+                    help="--hier: comma-separated sub-step options: wakeup, predict, keep_cells; graph: "
+                         "one sub-step captured in a CUDA graph and replayed")
     ap.add_argument("--hier-hot", type=float, default=0.0,
                     help="--hier: instead of the smooth profile, a hot sphere (u x 100) holding this "
                          "fraction of the particles in gas at u = 1: few particles on short steps")
@@ -796,6 +797,7 @@ def run_hier(args, world: int, rank: int, local: int):
     dt_min = float((0.1 * 1.825742 * arrays["h"] / arrays["v_sig"]).min())
     dt_max = float(2 ** max_bin) * dt_min
     opts = {o: True for o in args.hier_options.split(",") if o}
+    graph = opts.pop("graph", False)
     if set(opts) - {"wakeup", "predict", "keep_cells"}:
         raise SystemExit(f"unknown --hier-options {args.hier_options}")
     bins = torch.zeros(n, dtype=torch.int32, device="cuda")
@@ -812,9 +814,31 @@ def run_hier(args, world: int, rank: int, local: int):
     ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING))
     tick = 0
     scratch = torch.zeros((), dtype=torch.int64, device="cuda")
-    for _ in range(args.warmup):
-        tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick, **opts)
-        scratch += (tb == tick).sum()  # loads the counting kernels before the timed region
+    if graph:
+        # one sub-step captured in a CUDA graph (the tick on the device), each
+        # replay one more sub-step; launched from the context's stream
+        if opts.get("keep_cells"):
+            raise SystemExit("--hier-options graph: kept cells need the host (not capturable)")
+        st = torch.cuda.Stream()
+        ctx.close()
+        ctx = sph.Context(sph.sph_default_params(box_size=L), st)
+        tick_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(st):
+            sph.sph_hier_substep_dev(ctx, pool, bins, tb, dt_max, max_bin, tick_dev, **opts)
+        st.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            sph.sph_hier_substep_dev(ctx, pool, bins, tb, dt_max, max_bin, tick_dev, **opts)
+        for _ in range(args.warmup):
+            with torch.cuda.stream(st):
+                g.replay()
+                scratch += (tb == tick_dev).sum()
+        st.synchronize()
+        tick = int(tick_dev.item())
+    else:
+        for _ in range(args.warmup):
+            tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick, **opts)
+            scratch += (tb == tick).sum()  # loads the counting kernels before the timed region
     torch.cuda.synchronize()
     sph.sph_kernel_times(ctx)  # reset
     clocks = Clocks(None)
@@ -824,11 +848,21 @@ def run_hier(args, world: int, rank: int, local: int):
     active_dev = torch.zeros((), dtype=torch.int64, device="cuda")
     ticks0 = tick
     per_call = []
-    for _ in range(args.steps):
-        c0 = time.perf_counter()
-        tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick, **opts)
-        per_call.append(time.perf_counter() - c0)
-        active_dev += (tb == tick).sum()
+    if graph:
+        with torch.cuda.stream(st):
+            for _ in range(args.steps):
+                c0 = time.perf_counter()
+                g.replay()
+                active_dev += (tb == tick_dev).sum()
+                per_call.append(time.perf_counter() - c0)
+        st.synchronize()
+        tick = int(tick_dev.item())
+    else:
+        for _ in range(args.steps):
+            c0 = time.perf_counter()
+            tick = sph.sph_hier_substep(ctx, pool, bins, tb, dt_max, max_bin, tick, **opts)
+            per_call.append(time.perf_counter() - c0)
+            active_dev += (tb == tick).sum()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     active = int(active_dev.item())
@@ -845,12 +879,13 @@ def run_hier(args, world: int, rank: int, local: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "particles": n, "max_bin": max_bin,
                    "u": profile, "bins_at_end": levels, "ticks": tick - ticks0,
-                   "options": sorted(opts), "cell_builds": kt["build"][1],
+                   "options": sorted(opts) + (["graph"] if graph else []), "cell_builds": kt["build"][1],
                    "mean_active_fraction": active / (args.steps * n),
                    "step": "sph_hier_substep (adaptive bins); host wall time, the call "
                            "waits for its tick"},
         "gpu_launches": None,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        # (graph replays: the host's enqueue time only)
         "call_ms": {"median": 1e3 * float(np.median(per_call)), "max": 1e3 * float(np.max(per_call))},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }

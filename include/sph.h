@@ -380,6 +380,15 @@ enum {
 int sph_hier_substep(sph_ctx* ctx, const sph_pool* pool, int32_t* bins, int64_t* t_begin, double dt_max,
                      int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync, int64_t* t_next_out);
 
+/* The same sub-step with the tick on the device: *tick (device int64) is the
+ * current tick t_now on entry and is replaced by t_next on the stream.  Nothing
+ * waits for the stream, so a CUDA graph can capture the call and replay it,
+ * each replay one more sub-step (small sub-steps are launch-bound).  Not with
+ * SPH_HIER_KEEP_CELLS, SPH_FLAG_SYNC or SPH_FLAG_TIMING (SPH_E_INVAL).  The
+ * first call on a context allocates its scratch: make it before a capture. */
+int sph_hier_substep_dev(sph_ctx* ctx, const sph_pool* pool, int32_t* bins, int64_t* t_begin, double dt_max,
+                         int32_t max_bin, int64_t* tick, int32_t options, uint8_t* sync);
+
 /* One kick-drift-kick step of every simulation of the pool (Sec. 2.4):
  *   dt = C_CFL min_i H_i / v_sig,i per simulation (FP64 reduction),
  *   half kick of v and u, drift of x in FP64 with periodic wrap, prediction

@@ -1295,11 +1295,23 @@ int sph_time_bins(sph_ctx* c, const sph_cells* cells, const sph_particles* in, c
   return rc != SPH_OK ? rc : finish(c);
 }
 
-int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, double dt_max,
-                     int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync_flags, int64_t* t_next_out) {
-  if (!c || !pl || !bins || !tbeg || !t_next_out || pl->n_sims != 1 || pl->n_total < 1 ||
+}  // extern "C"
+
+namespace {
+
+// One sub-step (the two entry points below): with tick_dev the current tick is
+// read from and the next written to device memory, and nothing waits for the
+// stream (a CUDA graph can capture the call); else t_now comes from the host
+// and the next tick is read back into *t_next_out.
+int hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, double dt_max, int32_t max_bin,
+                 int64_t t_now, int64_t* tick_dev, int32_t options, uint8_t* sync_flags, int64_t* t_next_out) {
+  if (!c || !pl || !bins || !tbeg || (!t_next_out && !tick_dev) || pl->n_sims != 1 || pl->n_total < 1 ||
       pl->n_total > INT32_MAX / 16 || !(dt_max > 0.0) || !std::isfinite(dt_max) || max_bin < 0 || max_bin > 40 ||
       t_now < 0 || (options & ~(SPH_HIER_ADAPT | SPH_HIER_WAKEUP | SPH_HIER_PREDICT | SPH_HIER_KEEP_CELLS)) != 0)
+    return SPH_E_INVAL;
+  // the device-tick form waits for nothing: no kept cells (a host decision),
+  // no synchronous context, no kernel timing
+  if (tick_dev && ((options & SPH_HIER_KEEP_CELLS) || (c->p.flags & (SPH_FLAG_SYNC | SPH_FLAG_TIMING))))
     return SPH_E_INVAL;
   const bool adapt = (options & SPH_HIER_ADAPT) != 0, wakeup = (options & SPH_HIER_WAKEUP) != 0;
   if (!pl->sim_offset || !pl->box_size || !pl->x || !pl->y || !pl->z || !pl->vx || !pl->vy || !pl->vz ||
@@ -1316,6 +1328,7 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
   h.n = n;
   h.max_bin = max_bin;
   h.t_now = t_now;
+  h.t_now_dev = tick_dev;
   h.tau = std::ldexp(dt_max, -max_bin);
   h.box = pl->box_size;
   h.x = pl->x;
@@ -1472,12 +1485,34 @@ int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbe
   }
   if ((wakeup || sync_flags != nullptr) && sphh::launch_hier_interrupt(h, c->st) != cudaSuccess) return SPH_E_CUDA;
   t_end(c, SPH_T_INTEGRATE);
+  if (tick_dev) {
+    // the next tick replaces the current one on the device
+    if (cudaMemcpyAsync(tick_dev, c->htick, sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+    return SPH_OK;
+  }
   unsigned long long tn = 0;
   if (cudaMemcpyAsync(&tn, c->htick, sizeof(tn), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
       cudaStreamSynchronize(c->st) != cudaSuccess)
     return SPH_E_CUDA;
   *t_next_out = (int64_t)tn;
   return finish(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, double dt_max,
+                     int32_t max_bin, int64_t t_now, int32_t options, uint8_t* sync_flags, int64_t* t_next_out) {
+  if (!t_next_out) return SPH_E_INVAL;
+  return hier_substep(c, pl, bins, tbeg, dt_max, max_bin, t_now, nullptr, options, sync_flags, t_next_out);
+}
+
+int sph_hier_substep_dev(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, double dt_max,
+                         int32_t max_bin, int64_t* tick, int32_t options, uint8_t* sync_flags) {
+  if (!tick) return SPH_E_INVAL;
+  return hier_substep(c, pl, bins, tbeg, dt_max, max_bin, 0, tick, options, sync_flags, nullptr);
 }
 
 int sph_density_active(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const float* h_in,

@@ -40,7 +40,8 @@ __global__ void k_hier_next(int64_t n, const int32_t* __restrict__ bin, const in
 // predicted u (the density loop replaces them for the active particles).
 __global__ void k_hier_drift(sphh::HierArgs a) {
   const int64_t tn = (int64_t)*a.t_next;
-  const double dt = (double)(tn - a.t_now) * a.tau;
+  const int64_t t_now = a.t_now_dev != nullptr ? *a.t_now_dev : a.t_now;
+  const double dt = (double)(tn - t_now) * a.tau;
   const double L = *a.box;
   float v2max = 0.0f, hmax = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {

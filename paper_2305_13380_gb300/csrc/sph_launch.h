@@ -208,6 +208,7 @@ struct HierArgs {
   int64_t n;
   int max_bin;
   int64_t t_now;
+  const int64_t* t_now_dev;  // when set, the current tick is read from here
   double tau;  // dt_max / 2^max_bin
   const double* box;  // the pool's box side (device)
   double *x, *y, *z;

@@ -130,6 +130,8 @@ def lib():
         L.sph_step.argtypes = [_P, C.POINTER(sph_pool)]
         L.sph_hier_substep.argtypes = [_P, C.POINTER(sph_pool), _P, _P, C.c_double, C.c_int32, C.c_int64,
                                        C.c_int32, _P, C.POINTER(C.c_int64)]
+        L.sph_hier_substep_dev.argtypes = [_P, C.POINTER(sph_pool), _P, _P, C.c_double, C.c_int32, _P,
+                                           C.c_int32, _P]
         L.sph_time_bins.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles),
                                     C.POINTER(sph_density_out), _P, C.c_double, C.c_double, C.c_int32, _P]
         L.sph_density_active.argtypes = [_P, C.POINTER(sph_cells), C.POINTER(sph_particles), _P, _P,
@@ -300,6 +302,19 @@ def sph_force(ctx: Context, cells: sph_cells, part: sph_particles, dens: sph_den
               out: sph_force_out):
     _check(lib().sph_force(ctx.handle, C.byref(cells), C.byref(part), C.byref(dens),
                            C.byref(out)), "sph_force")
+
+
+def sph_hier_substep_dev(ctx: Context, pl: sph_pool, bins, t_begin, dt_max: float, max_bin: int, tick,
+                         adapt: bool = True, wakeup: bool = False, sync=None, predict: bool = False) -> None:
+    """One sub-step with the tick in a device int64 tensor (read, then
+    replaced by the next tick); waits for nothing, so it can be captured in a
+    CUDA graph."""
+    opts = (SPH_HIER_ADAPT if adapt else 0) | (SPH_HIER_WAKEUP if wakeup else 0) | \
+        (SPH_HIER_PREDICT if predict else 0)
+    _check(lib().sph_hier_substep_dev(ctx.handle, C.byref(pl), _ptr(bins, torch.int32), _ptr(t_begin, torch.int64),
+                                      C.c_double(dt_max), C.c_int32(max_bin), _ptr(tick, torch.int64),
+                                      C.c_int32(opts), None if sync is None else _ptr(sync, torch.uint8)),
+           "sph_hier_substep_dev")
 
 
 def sph_hier_substep(ctx: Context, pl: sph_pool, bins, t_begin, dt_max: float, max_bin: int, t_now: int,

@@ -82,6 +82,7 @@ def test_new_entry_points_reject_null_arguments_without_gpu(libsph):
     assert L.sph_force_active(None, None, None, None, None, None) == sph.SPH_E_INVAL
     assert L.sph_time_bins(None, None, None, None, None, 0.1, 1.0, 10, None) == sph.SPH_E_INVAL
     assert L.sph_hier_substep(None, None, None, None, 1.0, 4, 0, 1, None, ctypes.byref(t)) == sph.SPH_E_INVAL
+    assert L.sph_hier_substep_dev(None, None, None, None, 1.0, 4, None, 1, None) == sph.SPH_E_INVAL
 
 
 def test_lanes_per_target_checked_without_gpu(libsph):

@@ -233,3 +233,50 @@ def test_kept_cells_across_the_periodic_boundary(orc):
     assert np.array_equal(gt.cpu().numpy(), tb) and np.array_equal(gb.cpu().numpy(), bins)
     g = {k: v.cpu().numpy() for k, v in arr.items()}
     _compare(g, s, 1.0 / 12)
+
+
+def test_graph_replayed_substeps_equal_the_host_calls(orc):
+    """sph_hier_substep_dev captured once in a CUDA graph and replayed: each
+    replay one sub-step, the tick advanced on the device; five replays equal
+    five host calls on an identical pool bit for bit (adaptive bins, wake-up
+    and prediction on)."""
+    import torch
+    from paper_2305_13380_gb300 import sph
+    s = _state(orc, 5, u_spread=True)
+    n = len(s["x"])
+    max_bin = 4
+    dt_max = 16.0 * float(np.min(0.1 * orc.GAMMA_K * s["h"] / s["v_sig"]))
+    bins = orc.limit_time_bins(s, s["h"], orc.time_bins(s["h"], s["v_sig"], 0.1, dt_max, max_bin))
+    _start(s, bins, dt_max, max_bin)
+    arr_a, pool_a = _pool(s)
+    arr_b, pool_b = _pool(s)
+    gb_a, gb_b = torch.tensor(bins, device="cuda"), torch.tensor(bins, device="cuda")
+    gt_a, gt_b = torch.zeros(n, dtype=torch.int64, device="cuda"), torch.zeros(n, dtype=torch.int64, device="cuda")
+    st = torch.cuda.Stream()
+    ctx_a = sph.Context(sph.sph_default_params(), st)
+    ctx_b = sph.Context(sph.sph_default_params(), st)
+    tick = torch.zeros(1, dtype=torch.int64, device="cuda")
+    kw = dict(adapt=True, wakeup=True, predict=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        t_a = sph.sph_hier_substep(ctx_a, pool_a, gb_a, gt_a, dt_max, max_bin, 0, **kw)
+        sph.sph_hier_substep_dev(ctx_b, pool_b, gb_b, gt_b, dt_max, max_bin, tick, **kw)   # allocates
+    st.synchronize()
+    assert int(tick.item()) == t_a
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        sph.sph_hier_substep_dev(ctx_b, pool_b, gb_b, gt_b, dt_max, max_bin, tick, **kw)
+    st.synchronize()
+    assert int(tick.item()) == t_a          # capturing ran nothing
+    ticks = []
+    for _ in range(5):
+        with torch.cuda.stream(st):
+            t_a = sph.sph_hier_substep(ctx_a, pool_a, gb_a, gt_a, dt_max, max_bin, t_a, **kw)
+            g.replay()
+        st.synchronize()
+        ticks.append(t_a)
+        assert int(tick.item()) == t_a
+    assert len(set(ticks)) == 5
+    assert torch.equal(gb_a, gb_b) and torch.equal(gt_a, gt_b)
+    for k in arr_a:
+        assert torch.equal(arr_a[k], arr_b[k]), k
