@@ -515,10 +515,11 @@ int sph_pool_move(const sph_pool* spread, const sph_pool* packed, int32_t n_rang
                   const int64_t* offsets, int32_t to_packed, void* stream);
 
 /* Diagnostics of the last nested-grid build and density (SPH_FLAG_TREE; waits
- * for the stream): out[0] = target groups, out[1] = targets summed without a
- * neighbour list (needs SPH_FLAG_COUNT_PAIRS, else 0), out[2] = reverse pairs
- * emitted, out[3] = targets re-solved at a coarser level.  All zero without
- * nested grids. */
+ * for the stream): out[0] = target groups, out[1] = targets that left their
+ * group for the per-target kernel (a list overflow or a support past the list
+ * radius; needs SPH_FLAG_COUNT_PAIRS, else 0), out[2] = reverse pairs emitted,
+ * out[3] = targets solved by the per-target kernel (those, and the ones
+ * re-solved at a coarser level).  All zero without nested grids. */
 int sph_tree_counts(sph_ctx* ctx, int64_t* out);
 
 /* Cell build for callers that cannot allocate device memory (code running in
