@@ -319,3 +319,38 @@ def test_two_particle_step_by_hand(orc, K):
     assert (Vp[0] - Vp[1]) @ (X1[0] - X1[1]) < 0 and np.all(st1["B"] > 0.1)
     a1_inviscid = _force_by_hand(K, X1, Vp, m, st1, 0.0)[0]
     assert np.abs(a1 - a1_inviscid).max() > 0.5 * np.abs(a1_inviscid).max()
+
+
+@pytest.mark.parametrize("case", [
+    (0.5, 0.0, -0.7, 0.0),    # approaching: |v.x|/r adds to the conduction speed
+    (0.3, 0.25, -0.4, 0.3),   # oblique, r < H_j < H_i
+    (0.9, 0.0, -0.5, 0.0),    # H_j < r < H_i: only h_i's kernel reaches
+])
+def test_conduction_by_hand(orc, K, case):
+    """SPHENIX artificial conduction (Sec. 3.3, eq. "art_cond"), two particles:
+    du_i/dt|cond = alpha_c,ij v_c,ij m_j (u_i - u_j) [f_i grad_i W(h_i) +
+    f_j grad_i W(h_j)] . x_ij / r / (rho_i + rho_j), with the pressure-weighted
+    alpha_c,ij and v_c,ij = |v_ij . x_ij| / r + sqrt(2 |P_i - P_j| /
+    (rho_i + rho_j)) (the readings of the garbled terms), against the oracle's
+    conduction part of du/dt.  A dropped 1/2-weighting, a wrong density sum or
+    a swapped sign of (u_i - u_j) changes these values."""
+    p, st = _pair_input(*case)
+    X, V = _xv(p)
+    alpha_c = np.array([0.3, 0.9])
+    alpha_v = np.array([0.5, 1.0])
+    out = orc.sphenix_force(p, st, alpha_v, alpha_c)
+    for i, j in ((0, 1), (1, 0)):
+        xij = X[i] - X[j]
+        vij = V[i] - V[j]
+        r = float(np.sqrt(xij @ xij))
+        gi = K.grad(X[i], X[j], st["h"][i]) @ xij / r
+        gj = K.grad(X[i], X[j], st["h"][j]) @ xij / r
+        a_c = (st["P"][i] * alpha_c[i] + st["P"][j] * alpha_c[j]) / (st["P"][i] + st["P"][j])
+        rs = st["rho"][i] + st["rho"][j]
+        v_c = abs(vij @ xij) / r + math.sqrt(2.0 * abs(st["P"][i] - st["P"][j]) / rs)
+        du = a_c * v_c * p["m"][j] * (p["u"][i] - p["u"][j]) * (st["f"][i] * gi + st["f"][j] * gj) / rs
+        assert out["du_cond"][i] == pytest.approx(du, rel=1e-10, abs=1e-14)
+    # heat flows from the hotter particle (u = 1.5) to the colder one
+    assert out["du_cond"][1] < 0.0 < out["du_cond"][0]
+    # energy: m_i du_i + m_j du_j = 0
+    assert p["m"] @ out["du_cond"] == pytest.approx(0.0, abs=1e-12)
