@@ -354,3 +354,26 @@ def test_conduction_by_hand(orc, K, case):
     assert out["du_cond"][1] < 0.0 < out["du_cond"][0]
     # energy: m_i du_i + m_j du_j = 0
     assert p["m"] @ out["du_cond"] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_sphenix_viscosity_by_hand(orc, K):
+    """SPHENIX viscosity (Sec. 3.3, eq. "av_ij"): the pair's alpha is the mean
+    of the two particles' alpha_V times the mean Balsara switch; with the
+    conduction off (equal u) the SPHENIX a and du/dt of two approaching
+    particles are the hand-evaluated Minimal pair terms with that alpha."""
+    p, st = _pair_input(0.3, 0.25, -0.4, 0.3)
+    p["u"] = np.array([1.2, 1.2])                 # no conduction
+    X, V = _xv(p)
+    alpha_v = np.array([0.4, 1.6])
+    out = orc.sphenix_force(p, st, alpha_v, np.zeros(2))
+    for i, j in ((0, 1), (1, 0)):
+        B = st["B"]
+        # _pair_terms takes alpha_V (B_i + B_j)/2: pass the mean alpha_V
+        a, du, _ = _pair_terms(K, i, j, X, V, p["m"], st, 0.5 * (alpha_v[i] + alpha_v[j]))
+        for k, ax in enumerate(("ax", "ay", "az")):
+            assert out[ax][i] == pytest.approx(a[k], rel=1e-10, abs=1e-13)
+        assert out["du_dt"][i] == pytest.approx(du, rel=1e-10, abs=1e-13)
+        assert B[i] != B[j]
+    # a single alpha_V (either particle's) gives other values
+    a0, _, _ = _pair_terms(K, 0, 1, X, V, p["m"], st, alpha_v[0])
+    assert abs(out["ax"][0] - a0[0]) > 1e-6 * abs(a0[0])
