@@ -217,9 +217,10 @@ struct SimCursor {
 // (no change to an offset within half a box of the cell's centre).
 __device__ __forceinline__ double cell_offset(double x, int32_t k, const GridDev& G) {
   double d = x - (double)k * G.cell;
-  const double o = d - 0.5 * G.cell;
-  if (o > 0.5 * G.L) d -= G.L;
-  else if (o < -0.5 * G.L) d += G.L;
+  // the test in FP32 (a wrapped offset is off by about a box; FP64 is slow on
+  // this GPU), the shift in FP64
+  const float o = (float)d - 0.5f * G.cell_f, half = 0.5f * (float)G.L;
+  if (fabsf(o) > half) d += o > 0.0f ? -G.L : G.L;
   return d;
 }
 
