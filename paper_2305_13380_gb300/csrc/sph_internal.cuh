@@ -217,10 +217,13 @@ struct SimCursor {
 // (no change to an offset within half a box of the cell's centre).
 __device__ __forceinline__ double cell_offset(double x, int32_t k, const GridDev& G) {
   double d = x - (double)k * G.cell;
-  // the test in FP32 (a wrapped offset is off by about a box; FP64 is slow on
-  // this GPU), the shift in FP64
-  const float o = (float)d - 0.5f * G.cell_f, half = 0.5f * (float)G.L;
-  if (fabsf(o) > half) d += o > 0.0f ? -G.L : G.L;
+  if (G.reach_f < G.cell_f) {
+    // cells kept from an earlier build (a fresh build's offsets need no test):
+    // the test in FP32 (a wrapped offset is off by about a box; FP64 is slow
+    // on this GPU), the shift in FP64
+    const float o = (float)d - 0.5f * G.cell_f, half = 0.5f * (float)G.L;
+    if (fabsf(o) > half) d += o > 0.0f ? -G.L : G.L;
+  }
   return d;
 }
 
