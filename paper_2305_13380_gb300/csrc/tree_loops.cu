@@ -60,8 +60,7 @@ constexpr size_t kTWarpSmem = (size_t)kTCap * (sizeof(float4) + sizeof(uint32_t)
                               (size_t)kTRows * 32 * (sizeof(float) + sizeof(uint32_t)) + kTPruneBytes;
 constexpr size_t kTDensSmem = kTWarps * kTWarpSmem;
 constexpr int kNoShift = 1 | (1 << 2) | (1 << 4);
-// list_cnt markers: sums taken without a list; target re-solved by the fallback
-constexpr uint16_t kListNone = 0xffff;
+// list_cnt marker: the target is solved by the per-target kernels
 constexpr uint16_t kListFallback = 0xfffe;
 // fallback queue entries: a target index, with this bit for a target queued
 // from its group (solved at its own level); indices stay below 2^30
@@ -874,32 +873,18 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
         const float4 vi = a.rec[4 * (int64_t)ti + 2];
         const float4 ci = a.rec[4 * (int64_t)ti + 3];
         const float2 di = make_float2(__int_as_float(hi.q1.w), __frcp_rn(hi.q0.w));
-        const bool direct = lc == kListNone;
-        // own reach: the list radius, or the leaf side on the list-free path
-        const float C = direct ? g.side : a.lrad[ti];
+        // own reach: the list radius (a target without a complete list went
+        // to the per-target kernel, kListFallback)
+        const float C = a.lrad[ti];
         const float C2 = C * C;
-        if (!direct) {
-          const uint32_t* lst = a.lists + col * kTreeListRegion;
-          for (int e = 0; e < lc; ++e) {
-            const uint32_t je = lst[e];
-            const int32_t j = unpack_j(je);
-            if (j == ti) continue;
-            const TRec hj = trec_head(a.rec, j);
-            const float3 d = pair_vec(g, reli, fi, hj.q0, hj.q1, unpack_s(je));
-            tforce_rec<kFl, K>(d.x, d.y, d.z, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
-          }
-        } else {
-          for (int r = 0; r < 27; ++r) {
-            const TreeRange Rg = a.ranges[(int64_t)li * 27 + r];
-            for (int32_t j = Rg.lo + sub; j < Rg.hi; j += kTreeTpp) {
-              if (j == ti) continue;
-              const TRec hj = trec_head(a.rec, j);
-              const float3 pj = rec_rel_to(g, hj, Rg.shift);
-              const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-              if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
-                tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
-            }
-          }
+        const uint32_t* lst = a.lists + col * kTreeListRegion;
+        for (int e = 0; e < lc; ++e) {
+          const uint32_t je = lst[e];
+          const int32_t j = unpack_j(je);
+          if (j == ti) continue;
+          const TRec hj = trec_head(a.rec, j);
+          const float3 d = pair_vec(g, reli, fi, hj.q0, hj.q1, unpack_s(je));
+          tforce_rec<kFl, K>(d.x, d.y, d.z, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
         }
         // reverse pairs beyond the own reach, split between the lanes (the
         // gradient pass reaches only H_i <= the own reach: none of them)
