@@ -288,12 +288,17 @@ int sph_force(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
  * length n, input order; nonzero marks a particle to update.  Outputs are
  * written for the active particles only; the others keep their contents.
  * sph_force_active reads the density results of every particle (the inactive
- * ones from their last update).  The force reuses the neighbour lists of the
- * preceding sph_density_active on the same cells when it is given the same
- * mask pointer (whose contents must not change in between); else it filters
- * its own.  Uniform grid only (SPH_E_INVAL with SPH_FLAG_TREE).  The outputs
- * of an active particle equal those of the unmasked loops up to the order of
- * the FP32 sums (a block deals its active targets to lanes anew). */
+ * ones from their last update).  On the uniform grid the force reuses the
+ * neighbour lists of the preceding sph_density_active on the same cells when
+ * it is given the same mask pointer (whose contents must not change in
+ * between); else it filters its own.  On the nested grids (SPH_FLAG_TREE) the
+ * force needs them: it takes the same mask pointer as the preceding density
+ * on the same cells, or follows an unmasked density (else SPH_E_INVAL); the
+ * density also walks the inactive particles' lists at their current supports,
+ * for the pairs an active particle receives from a larger inactive support
+ * (its outputs stay untouched).  The outputs of an active particle equal those
+ * of the unmasked loops up to the order of the FP32 sums (a block deals its
+ * active targets to lanes anew). */
 int sph_density_active(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in, const float* h_in,
                        const uint8_t* active, sph_density_out* out);
 int sph_force_active(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
@@ -301,7 +306,8 @@ int sph_force_active(sph_ctx* ctx, const sph_cells* cells, const sph_particles* 
 
 /* Time bins of the power-of-two time-step hierarchy (Sec. 2.4) with the first
  * time-step limiter (the SPH section's "Time-step limiter", Delta = 4), on the
- * cells of the last build (uniform grid; SPH_E_INVAL with SPH_FLAG_TREE):
+ * cells of the last build (both grid modes; on the nested grids after an
+ * unmasked density of that build, whose lists and reverse pairs it walks):
  *   dt_i  = C_CFL gamma_K h_i / v_sig,i        (FP32: fl(fl(c h_i) / v_sig,i),
  *                                               c = fl(C_CFL gamma_K))
  *   bin_i = smallest b in [0, max_bin] with dt_max 2^-b <= dt_i (max_bin if
@@ -319,8 +325,8 @@ int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
                   const float* v_sig, double cfl, double dt_max, int32_t max_bin, int32_t* bins);
 
 /* One sub-step of the power-of-two time-step hierarchy (Sec. 2.4, "Local
- * time-step optimisations") for a single simulation (pool with n_sims = 1,
- * uniform grid).  Time runs on integer ticks, tau = dt_max / 2^max_bin each; a
+ * time-step optimisations") for a single simulation (pool with n_sims = 1;
+ * both grid modes).  Time runs on integer ticks, tau = dt_max / 2^max_bin each; a
  * particle in bin b takes steps of 2^(max_bin - b) ticks starting at
  * t_begin[i] (a multiple of that length).  In this mode the pool's vx, vy, vz
  * and u are the particle's half-kicked values for its current step, and its
@@ -343,8 +349,10 @@ int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
  * t_begin = t_next.
  *   SPH_HIER_WAKEUP (Saitoh & Makino 2009): after the active particles have
  *     their new bins, every inactive j within r_ij < max(H_i, H_j) of an
- *     active i (FP64 minimum-image distance) whose step is more than 4 times
- *     longer, bin_j < bin_i - 2, is woken with bin max_i (bin_i - 2);
+ *     active i (uniform grid: FP64 minimum-image distance; nested grids: the
+ *     force pairs of the sub-step, decided in FP32 like the force's) whose
+ *     step is more than 4 times longer, bin_j < bin_i - 2, is woken with bin
+ *     max_i (bin_i - 2);
  *   sync (device uint8, n, or NULL): flags of particles to synchronise, say
  *     those a source term changed between sub-steps.  A flagged inactive
  *     particle ends its step with its CFL bin (SPH_HIER_ADAPT; the limiter of
@@ -366,7 +374,8 @@ int sph_time_bins(sph_ctx* ctx, const sph_cells* cells, const sph_particles* in,
  * and repeats the density.  The results then differ from a fresh build's by
  * the FP32 rounding of the relative positions only.  Between calls the pool's
  * positions must change only through sph_hier_substep (any other build on the
- * context, or a different n, rebuilds).
+ * context, or a different n, rebuilds).  Uniform grid only (SPH_E_INVAL with
+ * SPH_FLAG_TREE: the nested grids are rebuilt every sub-step).
  * bins (int32) and t_begin (int64) are device arrays of n, updated in place;
  * 0 <= max_bin <= 40; options: SPH_HIER_* bits (others: SPH_E_INVAL).  With
  * SPH_FLAG_SYNC a density that needs larger cells is rebuilt and repeated.

@@ -541,7 +541,7 @@ int do_build(sph_ctx* c, int n_sims, int64_t n_total, const int64_t* off, const 
 int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
                     const float* vy, const float* vz, const float* m, const float* u, const float* h_in,
                     float* h, float* rho, float* f, float* div_v, float* curl_v, float* P, float* cs,
-                    float* B, int32_t* n_iter) {
+                    float* B, int32_t* n_iter, const uint8_t* active) {
   sphh::TreeGatherArgs g;
   g.gamma_k = (float)sphk::kernel_gamma(c->p.kernel);
   g.n_total = c->built_n;
@@ -618,10 +618,18 @@ int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* 
   d.fb_level = c->fb_level;
   d.fb_work = c->misc + sphk::kTreeFbWork;
   d.list_free = c->pairs + 2;
+  if (active) {
+    // masked loops: the mask in tree order
+    const int rc = ensure_act(c, c->built_n);
+    if (rc != SPH_OK) return rc;
+    if (sphh::launch_tree_mask(c->built_n, c->perm, active, c->act_s, c->st) != cudaSuccess) return SPH_E_CUDA;
+    d.act = c->act_s;
+  }
   t_begin(c, SPH_T_DENSITY);
   const cudaError_t e = sphh::launch_tree_density(d, phys_of(c->p), c->st);
   t_end(c, SPH_T_DENSITY);
   c->lists_valid = (e == cudaSuccess);
+  c->lists_mask = active;
   return cuda_code(e);
 }
 
@@ -629,9 +637,8 @@ int do_density(sph_ctx* c, const double* x, const double* y, const double* z, co
                const float* vy, const float* vz, const float* m, const float* u, const float* h_in,
                float* h, float* rho, float* f, float* div_v, float* curl_v, float* P, float* cs,
                float* B, int32_t* n_iter, const uint8_t* active = nullptr) {
-  if (c->built_tree && active) return SPH_E_INVAL;  // masked loops run on the uniform grid
   if (c->built_tree)
-    return do_tree_density(c, x, y, z, vx, vy, vz, m, u, h_in, h, rho, f, div_v, curl_v, P, cs, B, n_iter);
+    return do_tree_density(c, x, y, z, vx, vy, vz, m, u, h_in, h, rho, f, div_v, curl_v, P, cs, B, n_iter, active);
   sphh::GatherDensityArgs g;
   g.n_total = c->built_n;
   g.n_sims = c->built_sims;
@@ -761,12 +768,44 @@ struct LoopPass {
   sphk::SphenixDev x;
 };
 
+// The nested grids' force-pass arguments of the current build (lists,
+// reverse pairs, records, fallback queue); outputs and flavour fields unset.
+sphh::TreeForceArgs tree_force_args(sph_ctx* c) {
+  sphh::TreeForceArgs a;
+  a.n_sims = c->built_sims;
+  a.num_sms = c->num_sms;
+  a.grid = c->grid;
+  a.tgt = c->tgt;
+  a.leaves = c->leaves;
+  a.n_leaves = c->n_leaves;
+  a.ranges = c->ranges;
+  a.fine = c->fine;
+  a.rel = c->rel;
+  a.lrad = c->lrad;
+  a.leaf_side = c->leaf_side;
+  a.perm = c->perm;
+  a.rec = c->trec;
+  a.lists = c->tlists;
+  a.list_cnt = c->list_cnt;
+  a.rev_start = c->rev_start;
+  a.rev = c->rev;
+  a.pairs = c->pairs + 1;
+  a.work = c->misc + sphk::kTreeWork;
+  a.n_total = c->built_n;
+  a.skey = c->skey;
+  a.cell_start = c->cell_start;
+  a.fb_list = c->fb_list;
+  a.fb_count = c->misc + sphk::kTreeFbCount;
+  a.fb_level = c->fb_level;
+  a.fb_work = c->misc + sphk::kTreeFbWork;
+  return a;
+}
+
 int do_force(sph_ctx* c, const double* x, const double* y, const double* z, const float* vx,
              const float* vy, const float* vz, const float* m, const float* h, const float* rho,
              const float* f, const float* P, const float* cs, const float* B, float* ax, float* ay,
              float* az, float* du_dt, float* v_sig, bool pos_ready = false, const LoopPass* sx = nullptr,
              const uint8_t* active = nullptr) {
-  if (active && c->built_tree) return SPH_E_INVAL;  // masked loops run on the uniform grid
   sphh::GatherForceArgs g;
   g.gamma_k = (float)sphk::kernel_gamma(c->p.kernel);
   // the nested-grid force reads positions from its own copies (fA.w only)
@@ -798,7 +837,7 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
     g.fine = c->fine;
     g.rec = c->trec;
   }
-  if (active) {
+  if (active && !c->built_tree) {
     // as in the density: the mask, and the gather of the blocks around it
     const int rc = ensure_act(c, c->built_n);
     if (rc != SPH_OK) return rc;
@@ -818,48 +857,34 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
   if (sx && sx->limit && sphh::launch_gather_bins(c->built_n, c->perm, sx->bins_in, c->sx4, c->st) != cudaSuccess)
     return SPH_E_CUDA;
   t_end(c, SPH_T_GATHER);
-  if (sx && sx->limit && c->built_tree) return SPH_E_INVAL;  // time bins: uniform grid only
   if (c->p.flags & SPH_FLAG_COUNT_PAIRS && !(sx && sx->gradient))
     if (cudaMemsetAsync(c->pairs + 1, 0, sizeof(unsigned long long), c->st) != cudaSuccess)
       return SPH_E_CUDA;
   if (c->built_tree) {
-    // the tree force needs the lists and reverse pairs of this build's density
-    if (!c->lists_valid) return SPH_E_INVAL;
-    sphh::TreeForceArgs a;
-    a.n_sims = c->built_sims;
-    a.num_sms = c->num_sms;
-    a.grid = c->grid;
-    a.tgt = c->tgt;
-    a.leaves = c->leaves;
-    a.n_leaves = c->n_leaves;
-    a.ranges = c->ranges;
-    a.fine = c->fine;
-    a.rel = c->rel;
-    a.lrad = c->lrad;
-    a.leaf_side = c->leaf_side;
-    a.perm = c->perm;
-    a.rec = c->trec;
-    a.lists = c->tlists;
-    a.list_cnt = c->list_cnt;
-    a.rev_start = c->rev_start;
-    a.rev = c->rev;
-    a.pairs = c->pairs + 1;
+    // the tree force needs the lists and reverse pairs of this build's
+    // density, taken over every target or under the same mask
+    if (!c->lists_valid || (c->lists_mask != nullptr && c->lists_mask != active)) return SPH_E_INVAL;
+    sphh::TreeForceArgs a = tree_force_args(c);
     a.ax = ax;
     a.ay = ay;
     a.az = az;
     a.du_dt = du_dt;
     a.v_sig = v_sig;
-    a.work = c->misc + sphk::kTreeWork;
-    a.n_total = c->built_n;
-    a.skey = c->skey;
-    a.cell_start = c->cell_start;
-    a.fb_list = c->fb_list;
-    a.fb_count = c->misc + sphk::kTreeFbCount;
-    a.fb_level = c->fb_level;
-    a.fb_work = c->misc + sphk::kTreeFbWork;
+    if (active) {
+      const int rc = ensure_act(c, c->built_n);
+      if (rc != SPH_OK) return rc;
+      if (sphh::launch_tree_mask(c->built_n, c->perm, active, c->act_s, c->st) != cudaSuccess) return SPH_E_CUDA;
+      a.act = c->act_s;
+    }
     t_begin(c, SPH_T_FORCE);
     cudaError_t e;
-    if (sx) {
+    if (sx && sx->limit) {
+      // the time-step limiter over the same pairs (bins in tree order)
+      a.fE = c->sx4;
+      a.pairs = nullptr;
+      a.bins_out = sx->bins_out;
+      e = sphh::launch_tree_limit(a, phys_of(c->p), c->st);
+    } else if (sx) {
       // SPHENIX on the nested grids: the same lists and reverse pairs, the
       // fifth record in tree order
       a.fE = c->sx4;
@@ -1276,7 +1301,7 @@ int sph_time_bins(sph_ctx* c, const sph_cells* cells, const sph_particles* in, c
   if (!(cfl > 0.0) || !std::isfinite(cfl) || !(dt_max > 0.0) || !std::isfinite(dt_max) || max_bin < 0 ||
       max_bin > 62)
     return SPH_E_INVAL;
-  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1) return SPH_E_INVAL;
   if (in->n == 0) return SPH_OK;
   if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !d->h || !d->rho || !d->f ||
       !d->P || !d->c || !d->balsara)
@@ -1318,11 +1343,13 @@ int hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, d
       !pl->u || !pl->m || !pl->h || !pl->ax || !pl->ay || !pl->az || !pl->du_dt || !pl->v_sig || !pl->rho ||
       !pl->f || !pl->div_v || !pl->curl_v || !pl->P || !pl->c || !pl->balsara)
     return SPH_E_INVAL;
-  if (c->p.flags & SPH_FLAG_TREE) return SPH_E_INVAL;  // masked loops run on the uniform grid
+  // kept cells are uniform-grid cells
+  const bool tree = (c->p.flags & SPH_FLAG_TREE) != 0;
+  if (tree && (options & SPH_HIER_KEEP_CELLS)) return SPH_E_INVAL;
   const int64_t n = pl->n_total;
   int rc = ensure(c, n, 1);
   if (rc == SPH_OK) rc = ensure_hier(c, n);
-  if (rc == SPH_OK && adapt) rc = ensure_sphenix(c, n);
+  if (rc == SPH_OK && (adapt || (tree && wakeup))) rc = ensure_sphenix(c, n);
   if (rc != SPH_OK) return rc;
   sphh::HierArgs h;
   h.n = n;
@@ -1459,7 +1486,21 @@ int hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, d
   }
   t_begin(c, SPH_T_INTEGRATE);
   if (sphh::launch_hier_kick(h, c->st) != cudaSuccess) return SPH_E_CUDA;
-  if (wakeup) {
+  if (wakeup && tree) {
+    // the wake-up pass over the nested grids' force pairs of this sub-step
+    // (every pair within either support), with the bins after the kick
+    sphh::TreeForceArgs a = tree_force_args(c);
+    a.pairs = nullptr;
+    a.fE = c->sx4;
+    a.act = c->act_s;
+    a.wake = c->hwake;
+    if (cudaMemsetAsync(c->hwake, 0xff, (size_t)n * sizeof(int32_t), c->st) != cudaSuccess ||
+        sphh::launch_gather_bins(n, c->perm, bins, c->sx4, c->st) != cudaSuccess ||
+        sphh::launch_tree_mask(n, c->perm, c->hact, c->act_s, c->st) != cudaSuccess ||
+        sphh::launch_tree_wake(a, phys_of(c->p), c->st) != cudaSuccess)
+      return SPH_E_CUDA;
+    h.wake = c->hwake;
+  } else if (wakeup) {
     // the wake-up pass over the cells of this sub-step's build (the density
     // made them wide enough for every new H)
     sphh::WakeArgs w;
@@ -1518,7 +1559,7 @@ int sph_hier_substep_dev(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t*
 int sph_density_active(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const float* h_in,
                        const uint8_t* active, sph_density_out* out) {
   if (!c || !cells || !in || !out || !active) return SPH_E_INVAL;
-  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1) return SPH_E_INVAL;
   if (in->n == 0) return SPH_OK;
   if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !in->u || !h_in ||
       !out->h || !out->rho || !out->f || !out->div_v || !out->curl_v || !out->P || !out->c ||
@@ -1532,7 +1573,7 @@ int sph_density_active(sph_ctx* c, const sph_cells* cells, const sph_particles* 
 int sph_force_active(sph_ctx* c, const sph_cells* cells, const sph_particles* in, const sph_density_out* d,
                      const uint8_t* active, sph_force_out* out) {
   if (!c || !cells || !in || !d || !out || !active) return SPH_E_INVAL;
-  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1 || c->built_tree) return SPH_E_INVAL;
+  if (in->n != cells->n || cells->n != c->built_n || c->built_sims != 1) return SPH_E_INVAL;
   if (in->n == 0) return SPH_OK;
   if (!in->x || !in->y || !in->z || !in->vx || !in->vy || !in->vz || !in->m || !d->h || !d->rho ||
       !d->f || !d->P || !d->c || !d->balsara || !out->ax || !out->ay || !out->az || !out->du_dt ||

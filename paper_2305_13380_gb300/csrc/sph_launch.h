@@ -373,8 +373,12 @@ struct TreeDensityArgs {
   int8_t* fb_level;            // n: level of the fallback solve
   int32_t* fb_work;            // 1
   unsigned long long* list_free;  // 1: targets summed without a list (counted with pairs)
+  // masked loops: 1 per target in tree order (nullptr: every target)
+  const uint8_t* act = nullptr;
 };
 cudaError_t launch_tree_density(const TreeDensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+// The mask in tree order: out[k] = active[perm[k]].
+cudaError_t launch_tree_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* out, cudaStream_t st);
 
 struct TreeForceArgs {
   int n_sims;
@@ -407,12 +411,23 @@ struct TreeForceArgs {
   const float4* fE = nullptr;
   float* alpha_c_out = nullptr;
   float* lap_u = nullptr;
+  // masked loops: 1 per target in tree order (nullptr: every target)
+  const uint8_t* act = nullptr;
+  // the time-step limiter (fE.x = each source's bin): bins in input order
+  int32_t* bins_out = nullptr;
+  // the wake-up pass (fE.x = each source's bin): per input-order particle
+  // outside the mask, the largest bin - 2 of a masked neighbour above its bin
+  int32_t* wake = nullptr;
 };
 cudaError_t launch_tree_force(const TreeForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 cudaError_t launch_tree_sphenix_force(const TreeForceArgs& a, const sphk::PhysDev& ph, const sphk::SphenixDev& x,
                                       cudaStream_t st);
 cudaError_t launch_tree_sphenix_gradient(const TreeForceArgs& a, const sphk::PhysDev& ph,
                                          const sphk::SphenixDev& x, cudaStream_t st);
+// The first time-step limiter over the nested grids' force pairs (a.fE,
+// a.bins_out), and the wake-up pass (a.fE, a.act, a.wake).
+cudaError_t launch_tree_limit(const TreeForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
+cudaError_t launch_tree_wake(const TreeForceArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
 // Exclusive scan of m int32 in place with a host-known length (radix.cu);
 // tmp holds m / 1024 + 2 entries.
 cudaError_t scan_exclusive_host_n(int32_t* a, int64_t m, int32_t* tmp, cudaStream_t st);

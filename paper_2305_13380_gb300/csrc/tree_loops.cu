@@ -63,8 +63,12 @@ constexpr int kNoShift = 1 | (1 << 2) | (1 << 4);
 // list_cnt marker: the target is solved by the per-target kernels
 constexpr uint16_t kListFallback = 0xfffe;
 // fallback queue entries: a target index, with this bit for a target queued
-// from its group (solved at its own level); indices stay below 2^30
+// from its group (solved at its own level), and this one for a target outside
+// the mask of masked loops (its current support sends reverse pairs only);
+// indices stay below 2^29
 constexpr int32_t kFbOwnLevel = 1 << 30;
+constexpr int32_t kFbPassive = 1 << 29;
+constexpr int32_t kFbIndex = kFbPassive - 1;
 static_assert(kTWarpSmem % 16 == 0, "per-warp regions keep float4 alignment");
 static_assert(kTreeList <= kTreeListRegion, "published lists fit their regions");
 static_assert(kTreeListRegion % 4 == 0, "lists are published as 16-byte vectors");
@@ -539,6 +543,10 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
     for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
       const bool valid = t0 + t < n_t;
       const int32_t ti = a.tgt[t_lo + (valid ? t0 + t : 0)];
+      // masked loops: a target outside the mask keeps its h and outputs; its
+      // list at its current support only sends reverse pairs to the masked
+      // particles (whose forces need every pair within either support)
+      const bool on = valid && (a.act == nullptr || a.act[ti] != 0);
       const float4 reli = a.rel[ti];
       const int4 fi = a.fine[ti];
       const float3 pi = rel_to(g, reli, fi, kNoShift);
@@ -586,15 +594,17 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       bool queued = group_any(cnt > kTreeList, lane);
       // 2. Newton-Raphson passes
       float h = valid ? a.hs[ti] : hcap;
-      if (!(h > 0.0f)) h = 0.5f * hcap;
-      if (h > hcap) h = hcap;
+      if (on) {
+        if (!(h > 0.0f)) h = 0.5f * hcap;
+        if (h > hcap) h = hcap;
+      }
       {
         // evaluated by every lane (a ballot), then merged
         const bool outgrown = group_any(valid && KernT<K>::gamma * h > Ri, lane);
         queued = queued || outgrown;
       }
       float hlo = 0.0f, hhi = INFINITY;
-      bool done = !valid || queued, atcap = false, conv = false;
+      bool done = !on || queued, atcap = false, conv = false;
       int it = 0, passes = 0;
       while (__any_sync(0xffffffffu, !done)) {
         const float H = KernT<K>::gamma * h;
@@ -625,7 +635,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       // list holds at most kTreeList = 32), with j's threshold read with its
       // fine position
       TMark wm = 0;
-      if (valid && !queued) {
+      if (on && !queued) {
         for (int e = 0; e < cnt; ++e) {
           const uint32_t je = lje[e * 32 + lane];
           const int32_t j = unpack_j(je);
@@ -633,8 +643,15 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           const int4 fj = a.fine[j];
           const float3 d = pair_vec(g, reli, fi, rj, fj, unpack_s(je));
           tdens_pair<K>(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
-          if (!atcap && want_reverse_t(__int_as_float(fj.w), ti, j, lr2[e * 32 + lane], H2, H, g.side))
+          if (!atcap && want_reverse_t(__int_as_float(fj.w), ti, j, lr2[e * 32 + lane], H2, H, g.side) &&
+              (a.act == nullptr || a.act[j] != 0))
             wm |= (TMark)1 << e;
+        }
+      } else if (valid && !queued) {
+        // outside the mask: the reverse pairs to masked receivers only
+        for (int e = 0; e < cnt; ++e) {
+          const int32_t j = unpack_j(lje[e * 32 + lane]);
+          if (a.act[j] != 0 && want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side)) wm |= (TMark)1 << e;
         }
       }
       // reverse pairs from the lists: the warp takes one slot range for the
@@ -642,7 +659,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       emit_marked(a, wm, lje, ti, lane);
       tcombine(s);
       // 4. publish the list (16-byte vectors) for the force loop
-      if (valid) {
+      if (on) {
         const int64_t col = (int64_t)ti * kTreeTpp + sub;
         a.list_cnt[col] = (uint16_t)(atcap || queued ? kListFallback : cnt);
         if (!queued) {
@@ -656,9 +673,9 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         if (queued) {
           // solved at its own level by the per-target kernel
           const int32_t k = atomicAdd(a.fb_count, 1);
-          if (k < a.n_total) a.fb_list[k] = ti | kFbOwnLevel;
-          free_acc += 1ull;
-        } else {
+          if (k < a.n_total) a.fb_list[k] = ti | kFbOwnLevel | (on ? 0 : kFbPassive);
+          free_acc += on ? 1ull : 0ull;
+        } else if (on) {
           tdens_write<K>(a, ph, ti, h, s, vi.w, passes, !conv && !atcap);
           if (atcap) {
             // the support outgrew this level: re-solved at a coarser one
@@ -744,7 +761,9 @@ __device__ __forceinline__ TRec trec_head(const float4* __restrict__ rec, int32_
 // Flavours of the force kernels: the "Minimal" force, the SPHENIX force and
 // the SPHENIX gradient pass (Sec. 3.3; the terms are those of force.cu's
 // flavours, with the fifth record E = (u, alpha_V, P, alpha_c) per source).
-enum : int { kTMin = 0, kTSphenix = 1, kTGradient = 2 };
+// The time-step limiter (kTLimit, Sec. 3.4) and the wake-up pass (kTWake)
+// walk the same pairs with fE.x = each source's time bin.
+enum : int { kTMin = 0, kTSphenix = 1, kTGradient = 2, kTLimit = 3, kTWake = 4 };
 
 // One force pair with x_ij = (dx, dy, dz) (same terms as force.cu).  The
 // gradient pass keeps only r < H_i (G_i = 0 beyond): the Laplacian sum
@@ -756,6 +775,14 @@ __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const 
                                             const float4& cj, const float4& ej, float Hj, float Hinv_j,
                                             float rho_j, const PhysDev& ph, TFSums& s) {
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  if constexpr (kFl == kTLimit) {
+    // the largest bin among the force pairs (r < max(H_i, H_j)) in vsig
+    const float Hm = fmaxf(Hi, Hj);
+    const bool in = r2 < Hm * Hm;
+    s.vsig = in ? fmaxf(s.vsig, ej.x) : s.vsig;
+    s.npair += in;
+    return;
+  }
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float r = r2 * rinv;
   const float hi2 = Hinv_i * Hinv_i;
@@ -799,16 +826,29 @@ __device__ __forceinline__ void tforce_pair(float dx, float dy, float dz, const 
 }
 
 // tforce_pair with source j's data from its record (head already loaded) and,
-// for SPHENIX, its fifth record.
+// for the flavours with one, its fifth record.  The wake-up pass raises the
+// wake-up bin of a source outside the mask within r < max(H_i, H_j) whose bin
+// lies below the target's bin - 2 (Saitoh & Makino's limiter, Sec. 3.4).
 template <int kFl, int K>
 __device__ __forceinline__ void tforce_rec(float dx, float dy, float dz, const float4& vi, const float4& ci,
                                            const float4& ei, float Hi, float Hinv_i, float rho_i,
-                                           const float4* __restrict__ rec, const float4* __restrict__ fE,
-                                           int32_t j, const TRec& h, const PhysDev& ph, TFSums& s) {
-  const float4* r = rec + 4 * (int64_t)j;
-  const float4 ej = kFl != kTMin ? fE[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-  tforce_pair<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, Hinv_i, rho_i, r[2], r[3], ej, h.q0.w, __frcp_rn(h.q0.w),
-                      __int_as_float(h.q1.w), ph, s);
+                                           const sphh::TreeForceArgs& a, int32_t j, const TRec& h, const PhysDev& ph,
+                                           TFSums& s) {
+  if constexpr (kFl == kTWake) {
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float Hm = fmaxf(Hi, h.q0.w);
+    const int w = (int)ei.x - 2;
+    if (r2 < Hm * Hm && a.act[j] == 0 && w > (int)a.fE[j].x) atomicMax(a.wake + a.perm[j], w);
+    return;
+  }
+  const float4* r = a.rec + 4 * (int64_t)j;
+  const float4 ej = kFl != kTMin ? a.fE[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (kFl == kTLimit) {
+    tforce_pair<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, Hinv_i, rho_i, vi, ci, ej, h.q0.w, 0.0f, 0.0f, ph, s);
+  } else {
+    tforce_pair<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, Hinv_i, rho_i, r[2], r[3], ej, h.q0.w, __frcp_rn(h.q0.w),
+                        __int_as_float(h.q1.w), ph, s);
+  }
 }
 
 // The result of a target: the force, or the gradient pass's conduction
@@ -818,7 +858,14 @@ template <int kFl>
 __device__ __forceinline__ void tforce_write(const sphh::TreeForceArgs& a, const SphenixDev& x, float dt,
                                              int32_t ti, float Hi, const float4& ei, const TFSums& s) {
   const int32_t p = a.perm[ti];
-  if constexpr (kFl == kTGradient) {
+  if constexpr (kFl == kTLimit) {
+    // a step at most 4 times the smallest neighbour step: at most two bins
+    // below the largest neighbour bin
+    const int own = (int)ei.x, nb = (int)s.vsig - 2;
+    a.bins_out[p] = own > nb ? own : nb;
+  } else if constexpr (kFl == kTWake) {
+    // the wake-up pass writes per source
+  } else if constexpr (kFl == kTGradient) {
     const float lap = 2.0f * s.ax;
     const float src = ei.x > 0.0f ? x.beta_c * Hi * lap / sqrtf(ei.x) : 0.0f;
     const float rate = src - (ei.w - x.ac_min) * s.vsig / Hi;
@@ -866,7 +913,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
       if (kFl == kTGradient) s.ay = ei.y;  // alpha_V,max starts at the target's
       const TRec hi = trec_head(a.rec, ti);
       const float Hi = hi.q0.w;
-      if (valid && !fb) {
+      const bool on = valid && !fb && (a.act == nullptr || a.act[ti] != 0);
+      if (on) {
         const float4 reli = hi.q0;
         const int4 fi = hi.q1;
         const float3 pi = rel_to(g, reli, fi, kNoShift);
@@ -884,7 +932,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
           if (j == ti) continue;
           const TRec hj = trec_head(a.rec, j);
           const float3 d = pair_vec(g, reli, fi, hj.q0, hj.q1, unpack_s(je));
-          tforce_rec<kFl, K>(d.x, d.y, d.z, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
+          tforce_rec<kFl, K>(d.x, d.y, d.z, vi, ci, ei, Hi, di.y, di.x, a, j, hj, ph, s);
         }
         // reverse pairs beyond the own reach, split between the lanes (the
         // gradient pass reaches only H_i <= the own reach: none of them)
@@ -897,7 +945,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
             const float3 pj = rec_rel_to(g, hj, unpack_s(je));
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
             if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
-              tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
+              tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a, j, hj, ph, s);
           }
         }
       }
@@ -907,7 +955,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
       s.du = gsum(s.du);
       s.vsig = gmax(s.vsig);
       s.npair = gsumi(s.npair);
-      if (valid && !fb && sub == 0) {
+      if (on && sub == 0) {
         tforce_write<kFl>(a, x, dt, ti, Hi, ei, s);
         pair_acc += (unsigned long long)s.npair;
       }
@@ -979,12 +1027,52 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density_fb(sphh::TreeDens
   for (int32_t q = next_group(a.fb_work, lane); q < nq; q = next_group(a.fb_work, lane)) {
     const int32_t qe = a.fb_list[q];
     const bool own = (qe & kFbOwnLevel) != 0;
-    const int32_t ti = qe & ~kFbOwnLevel;
+    const int32_t ti = qe & kFbIndex;
     const uint64_t key = a.skey[ti];
     const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30))];
     const float4 reli = a.rel[ti];
     const int4 fi = a.fine[ti];
     const float4 vi = a.vel4[ti];
+    if (qe & kFbPassive) {
+      // outside the mask: the reverse pairs of its current support H to the
+      // masked particles, from the finest level whose 27 cells hold it (the
+      // top cells hold every support)
+      const float hp = a.hs[ti];
+      const float H = KernT<K>::gamma * hp;
+      int dp = (int)a.level[ti];
+      TreeLeaf Lp = cell_at_depth(key, dp);
+      TGeo gp = leaf_geo(Lp, G);
+      while (dp > 0 && hp > h_cap<K>(gp.side_d, gp.L)) {
+        --dp;
+        Lp = cell_at_depth(key, dp);
+        gp = leaf_geo(Lp, G);
+      }
+      const float3 pp = rel_to(gp, reli, fi, kNoShift);
+      const TRanges Rr = cell_ranges(G, Lp, a.skey, a.cell_start, lane);
+      prune_tables(a.skey, Rr, Lp.depth, lane, pr);
+      const float cs = Lp.depth < kTreeDepth ? 0.5f * gp.side : gp.side;
+      const float H2 = H * H;
+      int nhp = 0;
+      const int tot = prune_round(true, lane % kTreeTpp, lane, pp, H2 * (1.0f + 0x1p-10f), gp.side, cs, pr, nhp);
+      for (int v0 = 0; v0 < tot; v0 += kTCap) {
+        const int c = tstage_union(v0, tot, nhp, pr, lane, gp, a.rel, a.fine, spos, sidx);
+        for (int k0 = 0; k0 < c; k0 += 32) {
+          const int k = k0 + lane;
+          bool want = false;
+          uint64_t rec = 0;
+          if (k < c) {
+            const float r2 = r2_of(pp, spos[k]);
+            const uint32_t je = sidx[k];
+            const int32_t j = unpack_j(je);
+            want = a.act[j] != 0 && want_reverse(a, ti, j, r2, H2, H, gp.side);
+            rec = reverse_rec(j, ti, unpack_s(je));
+          }
+          emit_warp(a, want, rec, lane);
+        }
+        __syncwarp();
+      }
+      continue;
+    }
     // a target queued from its group starts at its own level from its
     // starting h; one that hit its level's cap one level coarser from the
     // capped h of the first solve
@@ -1110,7 +1198,9 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
   const int32_t nq = min(*a.fb_count, (int32_t)a.n_total);
   unsigned long long pair_acc = 0;
   for (int32_t q = next_group(a.fb_work, lane); q < nq; q = next_group(a.fb_work, lane)) {
-    const int32_t ti = a.fb_list[q] & ~kFbOwnLevel;
+    const int32_t qe = a.fb_list[q];
+    if (qe & kFbPassive) continue;  // outside the mask: no force
+    const int32_t ti = qe & kFbIndex;
     const uint64_t key = a.skey[ti];
     const int sim = sim_of_cell(a.grid, a.n_sims, (int32_t)(key >> 30));
     const GridDev G = a.grid[sim];
@@ -1164,7 +1254,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
           const float3 pj = rec_rel_to(g, hj, Rg.shift);
           const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
           if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < C2)
-            tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
+            tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a, j, hj, ph, s);
         }
       }
     }
@@ -1177,7 +1267,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
         const float3 pj = rec_rel_to(g, hj, unpack_s(je));
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= C2)
-          tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a.rec, a.fE, j, hj, ph, s);
+          tforce_rec<kFl, K>(dx, dy, dz, vi, ci, ei, Hi, di.y, di.x, a, j, hj, ph, s);
       }
     }
     s.ax = wsum(s.ax);
@@ -1204,6 +1294,12 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force_fb(sphh::TreeForceA
 
 namespace sphh {
 using namespace sphk;
+
+__global__ void k_tree_mask(int64_t n, const int32_t* __restrict__ perm, const uint8_t* __restrict__ active,
+                            uint8_t* __restrict__ out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = active[perm[k]] != 0 ? 1 : 0;
+}
 
 static int tree_blocks(int64_t n) {
   int64_t b = (n + 255) / 256;
@@ -1296,6 +1392,22 @@ cudaError_t launch_tree_density(const TreeDensityArgs& a, const PhysDev& ph, cud
 
 cudaError_t launch_tree_force(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
   return launch_tree_force_fl<kTMin>(a, ph, SphenixDev{}, st);
+}
+
+cudaError_t launch_tree_limit(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+  if (a.fE == nullptr || a.bins_out == nullptr) return cudaErrorInvalidValue;
+  return launch_tree_force_fl<kTLimit>(a, ph, SphenixDev{}, st);
+}
+
+cudaError_t launch_tree_wake(const TreeForceArgs& a, const PhysDev& ph, cudaStream_t st) {
+  if (a.fE == nullptr || a.act == nullptr || a.wake == nullptr) return cudaErrorInvalidValue;
+  return launch_tree_force_fl<kTWake>(a, ph, SphenixDev{}, st);
+}
+
+cudaError_t launch_tree_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_tree_mask<<<tree_blocks(n), 256, 0, st>>>(n, perm, active, out);
+  return cudaGetLastError();
 }
 
 }  // namespace sphh

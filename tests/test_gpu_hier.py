@@ -1,5 +1,6 @@
 """Sub-steps of the time-step hierarchy (sph_hier_substep) on the GPU against
-the oracle's: fixed bins over several sub-steps, and adaptive bins."""
+the oracle's: fixed bins over several sub-steps, and adaptive bins, on the
+uniform grid and on the nested grids."""
 import numpy as np
 import pytest
 
@@ -72,8 +73,15 @@ def _compare(g, s, d, predict=False):
     assert np.allclose(g["h"], s["h"], rtol=1e-5)
 
 
-@pytest.mark.parametrize("predict,keep", [(False, False), (True, False), (True, True)])
-def test_fixed_bins_over_four_substeps(orc, predict, keep):
+def _flags(grid):
+    from paper_2305_13380_gb300 import sph
+    return sph.SPH_FLAG_TREE if grid == "nested" else 0
+
+
+@pytest.mark.parametrize("predict,keep,grid", [(False, False, "uniform"), (True, False, "uniform"),
+                                               (True, True, "uniform"), (False, False, "nested"),
+                                               (True, False, "nested")])
+def test_fixed_bins_over_four_substeps(orc, predict, keep, grid):
     import torch
     from paper_2305_13380_gb300 import sph
     s = _state(orc, 3)
@@ -86,7 +94,7 @@ def test_fixed_bins_over_four_substeps(orc, predict, keep):
     arr, pool = _pool(s)
     gb = torch.tensor(bins, device="cuda")
     gt = torch.zeros(n, dtype=torch.int64, device="cuda")
-    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC | sph.SPH_FLAG_TIMING))
+    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC | sph.SPH_FLAG_TIMING | _flags(grid)))
     tb = np.zeros(n, np.int64)
     t = tg = 0
     calls = 0
@@ -105,8 +113,10 @@ def test_fixed_bins_over_four_substeps(orc, predict, keep):
     assert (builds < calls) if keep else (builds == calls)
 
 
-@pytest.mark.parametrize("predict,keep", [(False, False), (True, False), (True, True)])
-def test_adaptive_bins(orc, predict, keep):
+@pytest.mark.parametrize("predict,keep,grid", [(False, False, "uniform"), (True, False, "uniform"),
+                                               (True, True, "uniform"), (False, False, "nested"),
+                                               (True, False, "nested")])
+def test_adaptive_bins(orc, predict, keep, grid):
     import torch
     from paper_2305_13380_gb300 import sph
     s = _state(orc, 5, u_spread=True)
@@ -118,7 +128,7 @@ def test_adaptive_bins(orc, predict, keep):
     arr, pool = _pool(s)
     gb = torch.tensor(bins, device="cuda")
     gt = torch.zeros(n, dtype=torch.int64, device="cuda")
-    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC | _flags(grid)))
     tb = np.zeros(n, np.int64)
     t = tg = 0
     for _ in range(3):
@@ -153,8 +163,8 @@ def _heated(orc, seed, heat):
     return s, bins, dt_max, max_bin, f
 
 
-@pytest.mark.parametrize("adapt", [False, True])
-def test_sync_and_wakeup(orc, adapt):
+@pytest.mark.parametrize("adapt,grid", [(False, "uniform"), (True, "uniform"), (True, "nested")])
+def test_sync_and_wakeup(orc, adapt, grid):
     """The synchronisation step and the wake-up limiter (Sec. 3.4) against the
     oracle over five sub-steps: the flagged particle ends its step at the
     first tick, and (adapt) its deep bin wakes its neighbours at its next end;
@@ -171,7 +181,7 @@ def test_sync_and_wakeup(orc, adapt):
     sync_g[f] = 1
     sync_o = np.zeros(n, bool)
     sync_o[f] = True
-    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC))
+    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC | _flags(grid)))
     tb = np.zeros(n, np.int64)
     t = tg = 0
     exact, woken = True, 0
@@ -235,7 +245,8 @@ def test_kept_cells_across_the_periodic_boundary(orc):
     _compare(g, s, 1.0 / 12)
 
 
-def test_graph_replayed_substeps_equal_the_host_calls(orc):
+@pytest.mark.parametrize("grid", ["uniform", "nested"])
+def test_graph_replayed_substeps_equal_the_host_calls(orc, grid):
     """sph_hier_substep_dev captured once in a CUDA graph and replayed: each
     replay one sub-step, the tick advanced on the device; five replays equal
     five host calls on an identical pool bit for bit (adaptive bins, wake-up
@@ -253,8 +264,8 @@ def test_graph_replayed_substeps_equal_the_host_calls(orc):
     gb_a, gb_b = torch.tensor(bins, device="cuda"), torch.tensor(bins, device="cuda")
     gt_a, gt_b = torch.zeros(n, dtype=torch.int64, device="cuda"), torch.zeros(n, dtype=torch.int64, device="cuda")
     st = torch.cuda.Stream()
-    ctx_a = sph.Context(sph.sph_default_params(), st)
-    ctx_b = sph.Context(sph.sph_default_params(), st)
+    ctx_a = sph.Context(sph.sph_default_params(flags=_flags(grid)), st)
+    ctx_b = sph.Context(sph.sph_default_params(flags=_flags(grid)), st)
     tick = torch.zeros(1, dtype=torch.int64, device="cuda")
     kw = dict(adapt=True, wakeup=True, predict=True)
     torch.cuda.synchronize()
@@ -280,3 +291,20 @@ def test_graph_replayed_substeps_equal_the_host_calls(orc):
     assert torch.equal(gb_a, gb_b) and torch.equal(gt_a, gt_b)
     for k in arr_a:
         assert torch.equal(arr_a[k], arr_b[k]), k
+
+
+def test_kept_cells_refused_on_the_nested_grids(orc):
+    """Kept cells are cells of the uniform grid: the option is refused on the
+    nested grids (which rebuild every sub-step)."""
+    import torch
+    from paper_2305_13380_gb300 import sph
+    s = _state(orc, 3)
+    n = len(s["x"])
+    bins = np.zeros(n, np.int32)
+    arr, pool = _pool(s)
+    gb = torch.tensor(bins, device="cuda")
+    gt = torch.zeros(n, dtype=torch.int64, device="cuda")
+    ctx = sph.Context(sph.sph_default_params(flags=sph.SPH_FLAG_SYNC | sph.SPH_FLAG_TREE))
+    with pytest.raises(sph.SPHError) as e:
+        sph.sph_hier_substep(ctx, pool, gb, gt, 1e-3, 2, 0, adapt=False, keep_cells=True)
+    assert e.value.code == sph.SPH_E_INVAL

@@ -120,3 +120,65 @@ def test_cfl_bins_match_the_fp64_definition_off_the_edges(orc):
     b2 = orc.time_bins(h, v2, CFL, DT_MAX, MAX_BIN)
     e2 = orc.bin_edge_band(h, v2, CFL, DT_MAX, MAX_BIN)
     assert np.array_equal(g2[~e2], b2[~e2])
+
+
+def _gpu_bins_nested(p, v):
+    """sph_time_bins on the nested grids, after the density and force of the
+    same build (the limiter walks their lists and reverse pairs); returns the
+    bins and the density's h."""
+    import torch
+    from paper_2305_13380_gb300 import sph
+    ctx = sph.Context(sph.sph_default_params(box_size=float(p["L"]), flags=sph.SPH_FLAG_SYNC | sph.SPH_FLAG_TREE))
+    t = sph.to_device(p)
+    n = int(t["x"].shape[0])
+    part = sph.particles(t)
+    d, f = sph.alloc_density(n), sph.alloc_force(n)
+    h_in = t["h0"]
+    for _ in range(8):  # rebuild until the top cells hold every support
+        cells = sph.sph_build_cells(ctx, t["x"], t["y"], t["z"], h_in)
+        try:
+            sph.sph_density(ctx, cells, part, h_in, sph.density_out(d))
+            break
+        except sph.SPHError as e:
+            if e.code != sph.SPH_E_REBUILD:
+                raise
+            h_in = d["h"].clone()
+    sph.sph_force(ctx, cells, part, sph.density_out(d), sph.force_out(f))
+    bins = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    sph.sph_time_bins(ctx, cells, part, sph.density_out(d), torch.tensor(v, dtype=torch.float32, device="cuda"),
+                      CFL, DT_MAX, MAX_BIN, bins)
+    return bins.cpu().numpy()
+
+
+@pytest.mark.parametrize("case", ["clustered", "fast_particle"])
+def test_limiter_on_the_nested_grids(orc, case):
+    """The limiter over the nested grids' force pairs (lists and reverse
+    pairs) against the oracle's brute force: clustered gas whose supports span
+    decades, and one fast particle raising its neighbours.  The bins are
+    decided from the oracle's own h (the GPU's agrees within 1e-5), so the
+    edge band and the pair radius carry that difference too (1e-4)."""
+    from gpu_common import as_f32
+    if case == "clustered":
+        p = inputs.clustered(3000, n_spheres=3, seed=11, a_min=0.03, a_max=0.08)
+    else:
+        p = inputs.lattice(12, seed=4, sigma_v=0.05)
+    rng = np.random.default_rng(21)
+    n = len(p["x"])
+    v = np.exp(rng.uniform(np.log(0.5), np.log(50.0), n)).astype(np.float32)
+    if case == "fast_particle":
+        v[:] = 1.0
+        v[17] = 1e4
+    g = _gpu_bins_nested(p, v)
+    q = as_f32(p)
+    h = orc.density(q, q["h0"])["h"]
+    b0 = orc.time_bins(h, v, CFL, DT_MAX, MAX_BIN)
+    edge = orc.bin_edge_band(h, v, CFL, DT_MAX, MAX_BIN, rel=1e-4).astype(np.int32)
+    lo = orc.limit_time_bins(p, h, np.maximum(b0 - edge, 0), scale=1 - 1e-4)
+    hi = orc.limit_time_bins(p, h, np.minimum(b0 + edge, MAX_BIN), scale=1 + 1e-4)
+    assert np.all(g >= lo) and np.all(g <= hi)
+    exact = orc.limit_time_bins(p, h, b0)
+    assert np.mean(g == exact) > 0.99
+    if case == "fast_particle":
+        assert g[17] == b0[17] and (g == b0[17] - 2).sum() > 30
+    else:
+        assert np.sum(exact > b0) > 50   # the limiter acted
