@@ -756,9 +756,12 @@ def main():
 
 
 def run_hier(args, world: int, rank: int, local: int):
-    """Sub-steps of the time-step hierarchy on the lattice with a smooth
-    temperature profile, u = 10^sin(2 pi x / L) (sound speeds over a decade):
-    adaptive bins over five levels (dt_max = 16 times the shortest CFL step)."""
+    """Sub-steps of the time-step hierarchy with adaptive bins over
+    args.hier_levels + 1 levels (dt_max = 2^levels times the shortest CFL
+    step): on the lattice (uniform grid) with a smooth temperature profile,
+    u = 10^sin(2 pi x / L) (sound speeds over a decade), or a hot sphere; on
+    the clustered box (nested grids) with its own energies, where the small
+    supports of the Plummer cores give the short steps."""
     import numpy as np
     import torch
     from paper_2305_13380_gb300 import build as B
@@ -766,10 +769,13 @@ def run_hier(args, world: int, rank: int, local: int):
     from paper_2305_13380_gb300 import replicas, sph
 
     p = make_workload(args.workload)
-    if p["tree"]:
-        raise SystemExit("the hierarchy runs on the uniform grid (latticeN workloads)")
+    tree = bool(p["tree"])
     n, L = len(p["x"]), float(p["L"])
-    if args.hier_hot > 0.0:
+    if tree:
+        if args.hier_hot > 0.0:
+            raise SystemExit("--hier-hot: lattice workloads only")
+        profile = "the clustered box's log-normal u (Plummer cores: small h, short steps)"
+    elif args.hier_hot > 0.0:
         # a hot sphere (sound speed x 10) in uniform gas: its particles step
         # 8-16 times shorter than the rest
         X = np.stack([np.asarray(p[k]) for k in ("x", "y", "z")], 1) - 0.5 * L
@@ -787,11 +793,23 @@ def run_hier(args, world: int, rank: int, local: int):
     for k in ("h", "ax", "ay", "az", "du_dt", "v_sig", "rho", "f", "div_v", "curl_v", "P", "c", "balsara"):
         arrays[k] = torch.zeros(n, dtype=torch.float32, device="cuda")
     arrays["dt"] = torch.zeros(1, dtype=torch.float64, device="cuda")
-    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC))
+    # nested grids: the tuner's choice for the clustered box (margin 0.03, 32
+    # particles per leaf)
+    gflags = sph.SPH_FLAG_TREE if tree else 0
+    gprm = dict(cell_margin=0.03, n_leaf=32) if tree else {}
+    init = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_SYNC | gflags, **gprm))
     part = sph.particles(t)
     dout = sph.density_out({k: arrays[k] for k in sph.DENSITY_FIELDS})
-    cells = sph.sph_build_cells(init, t["x"], t["y"], t["z"], t["h0"])
-    sph.sph_density(init, cells, part, t["h0"], dout)
+    h_in = t["h0"]
+    for _ in range(8):  # rebuild until the top cells hold every support
+        cells = sph.sph_build_cells(init, t["x"], t["y"], t["z"], h_in)
+        try:
+            sph.sph_density(init, cells, part, h_in, dout)
+            break
+        except sph.SPHError as e:
+            if e.code != sph.SPH_E_REBUILD:
+                raise
+            h_in = arrays["h"].clone()
     sph.sph_force(init, cells, part, dout, sph.force_out({k: arrays[k] for k in sph.FORCE_FIELDS}))
     max_bin = args.hier_levels
     dt_min = float((0.1 * 1.825742 * arrays["h"] / arrays["v_sig"]).min())
@@ -811,7 +829,10 @@ def run_hier(args, world: int, rank: int, local: int):
     pool = sph.pool(torch.tensor([0, n], dtype=torch.int64, device="cuda"),
                     torch.tensor([L], dtype=torch.float64, device="cuda"), arrays)
     tb = torch.zeros(n, dtype=torch.int64, device="cuda")
-    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING))
+    # (the nested grids: a synchronous context, so that a support outgrowing
+    # the top cells rebuilds and repeats the density inside the call)
+    ctx = sph.Context(sph.sph_default_params(box_size=L, flags=sph.SPH_FLAG_TIMING | gflags |
+                                             (sph.SPH_FLAG_SYNC if tree else 0), **gprm))
     tick = 0
     scratch = torch.zeros((), dtype=torch.int64, device="cuda")
     if graph:
@@ -821,7 +842,7 @@ def run_hier(args, world: int, rank: int, local: int):
             raise SystemExit("--hier-options graph: kept cells need the host (not capturable)")
         st = torch.cuda.Stream()
         ctx.close()
-        ctx = sph.Context(sph.sph_default_params(box_size=L), st)
+        ctx = sph.Context(sph.sph_default_params(box_size=L, flags=gflags, **gprm), st)
         tick_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
         with torch.cuda.stream(st):
             sph.sph_hier_substep_dev(ctx, pool, bins, tb, dt_max, max_bin, tick_dev, **opts)
@@ -879,6 +900,7 @@ def run_hier(args, world: int, rank: int, local: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "particles": n, "max_bin": max_bin,
                    "u": profile, "bins_at_end": levels, "ticks": tick - ticks0,
+                   "grid": "nested" if tree else "uniform",
                    "options": sorted(opts) + (["graph"] if graph else []), "cell_builds": kt["build"][1],
                    "mean_active_fraction": active / (args.steps * n),
                    "step": "sph_hier_substep (adaptive bins); host wall time, the call "

@@ -63,6 +63,7 @@ struct sph_ctx {
   float4* rel = nullptr;
   float4* trec = nullptr;  // force records of the nested grids, 4 per particle
   uint8_t* act_s = nullptr;         // sorted active mask (masked loops)
+  int32_t* act_pre = nullptr;       // nested grids: its exclusive prefix sums (n + 1)
   uint8_t* blk_any = nullptr;       // blocks holding an active particle
   uint8_t* blk_need = nullptr;      // those blocks and their neighbours (the gathers' set)
   int64_t cap_act = 0, cap_blk = 0;
@@ -290,12 +291,15 @@ int ensure_act(sph_ctx* c, int64_t n) {
   if (n <= c->cap_act && c->cap_cells <= c->cap_blk) return SPH_OK;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_E_CUDA;
   dfree(c->act_s);
+  dfree(c->act_pre);
   dfree(c->blk_any);
   dfree(c->blk_need);
   c->cap_act = c->cap_blk = 0;
   const int64_t cn = n + n / 4 + 64;
-  if (!dalloc(c->act_s, cn) || !dalloc(c->blk_any, c->cap_cells + 1) || !dalloc(c->blk_need, c->cap_cells + 1)) {
+  if (!dalloc(c->act_s, cn) || !dalloc(c->act_pre, cn + 1) || !dalloc(c->blk_any, c->cap_cells + 1) ||
+      !dalloc(c->blk_need, c->cap_cells + 1)) {
     dfree(c->act_s);
+    dfree(c->act_pre);
     dfree(c->blk_any);
     dfree(c->blk_need);
     return SPH_E_NOMEM;
@@ -622,8 +626,11 @@ int do_tree_density(sph_ctx* c, const double* x, const double* y, const double* 
     // masked loops: the mask in tree order
     const int rc = ensure_act(c, c->built_n);
     if (rc != SPH_OK) return rc;
-    if (sphh::launch_tree_mask(c->built_n, c->perm, active, c->act_s, c->st) != cudaSuccess) return SPH_E_CUDA;
+    if (sphh::launch_tree_mask(c->built_n, c->perm, active, c->act_s, c->act_pre, c->scan_sums, c->st) !=
+        cudaSuccess)
+      return SPH_E_CUDA;
     d.act = c->act_s;
+    d.act_pre = c->act_pre;
   }
   t_begin(c, SPH_T_DENSITY);
   const cudaError_t e = sphh::launch_tree_density(d, phys_of(c->p), c->st);
@@ -873,7 +880,8 @@ int do_force(sph_ctx* c, const double* x, const double* y, const double* z, cons
     if (active) {
       const int rc = ensure_act(c, c->built_n);
       if (rc != SPH_OK) return rc;
-      if (sphh::launch_tree_mask(c->built_n, c->perm, active, c->act_s, c->st) != cudaSuccess) return SPH_E_CUDA;
+      if (sphh::launch_tree_mask(c->built_n, c->perm, active, c->act_s, nullptr, nullptr, c->st) != cudaSuccess)
+        return SPH_E_CUDA;
       a.act = c->act_s;
     }
     t_begin(c, SPH_T_FORCE);
@@ -1043,6 +1051,7 @@ void sph_destroy(sph_ctx* c) {
   dfree(c->sx4);
   dfree(c->dvp);
   dfree(c->act_s);
+  dfree(c->act_pre);
   dfree(c->blk_any);
   dfree(c->blk_need);
   dfree(c->hact);
@@ -1496,7 +1505,7 @@ int hier_substep(sph_ctx* c, const sph_pool* pl, int32_t* bins, int64_t* tbeg, d
     a.wake = c->hwake;
     if (cudaMemsetAsync(c->hwake, 0xff, (size_t)n * sizeof(int32_t), c->st) != cudaSuccess ||
         sphh::launch_gather_bins(n, c->perm, bins, c->sx4, c->st) != cudaSuccess ||
-        sphh::launch_tree_mask(n, c->perm, c->hact, c->act_s, c->st) != cudaSuccess ||
+        sphh::launch_tree_mask(n, c->perm, c->hact, c->act_s, nullptr, nullptr, c->st) != cudaSuccess ||
         sphh::launch_tree_wake(a, phys_of(c->p), c->st) != cudaSuccess)
       return SPH_E_CUDA;
     h.wake = c->hwake;

@@ -373,12 +373,17 @@ struct TreeDensityArgs {
   int8_t* fb_level;            // n: level of the fallback solve
   int32_t* fb_work;            // 1
   unsigned long long* list_free;  // 1: targets summed without a list (counted with pairs)
-  // masked loops: 1 per target in tree order (nullptr: every target)
+  // masked loops: 1 per target in tree order (nullptr: every target), and
+  // its exclusive prefix sums (n + 1; a group without a masked particle in
+  // its 27 cells is skipped)
   const uint8_t* act = nullptr;
+  const int32_t* act_pre = nullptr;
 };
 cudaError_t launch_tree_density(const TreeDensityArgs& a, const sphk::PhysDev& ph, cudaStream_t st);
-// The mask in tree order: out[k] = active[perm[k]].
-cudaError_t launch_tree_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* out, cudaStream_t st);
+// The mask in tree order: out[k] = active[perm[k]]; with pre (n + 1 int32,
+// scan scratch tmp of (n + 1) / 1024 + 2) also its exclusive prefix sums.
+cudaError_t launch_tree_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* out, int32_t* pre,
+                             int32_t* tmp, cudaStream_t st);
 
 struct TreeForceArgs {
   int n_sims;

@@ -54,6 +54,7 @@ struct TPrune {
   int32_t hoff[kTChildren + 4];  // offsets of the round's hit children, + total
   uint8_t hch[kTChildren];       // the round's hit children, in order
   int32_t rlo[28], rcum[28], rsc[28];  // per neighbour range: first source, virtual start, shift
+  uint32_t cact[(kTChildren + 31) / 32];  // masked loops: children holding a masked source
 };
 constexpr size_t kTPruneBytes = (sizeof(TPrune) + 15) / 16 * 16;
 constexpr size_t kTWarpSmem = (size_t)kTCap * (sizeof(float4) + sizeof(uint32_t)) +
@@ -260,8 +261,12 @@ __device__ __forceinline__ TRanges load_ranges(const TreeRange* __restrict__ ran
 // are contiguous in Morton order; a cell of the deepest level has one).
 // Lanes 0..26 search their range's keys.  Called by the whole warp.
 __device__ __forceinline__ void prune_tables(const uint64_t* __restrict__ skey, const TRanges& R, int depth,
-                                             int lane, TPrune* pr) {
+                                             int lane, TPrune* pr, const int32_t* __restrict__ act_pre = nullptr) {
   const int32_t cum_next = __shfl_down_sync(0xffffffffu, R.cum, 1);
+  if (act_pre != nullptr) {
+    if (lane < (kTChildren + 31) / 32) pr->cact[lane] = 0u;
+    __syncwarp();
+  }
   if (lane < 27) {
     const int32_t len = cum_next - R.cum;
     pr->rlo[lane] = R.lo;
@@ -279,6 +284,19 @@ __device__ __forceinline__ void prune_tables(const uint64_t* __restrict__ skey, 
       }
     } else {
       for (int c = 1; c < 8; ++c) cvr[c] = R.cum + len;
+    }
+    if (act_pre != nullptr) {
+      // which children hold a masked source (prefix sums over the range)
+      unsigned bits = 0u;
+      int32_t a0 = act_pre[R.lo];
+      for (int c = 0; c < 8; ++c) {
+        const int32_t v1 = c < 7 ? cvr[c + 1] : R.cum + len;
+        const int32_t a1 = act_pre[R.lo + (v1 - R.cum)];
+        bits |= (a1 > a0 ? 1u : 0u) << c;
+        a0 = a1;
+      }
+      // 8 children of range `lane` are bits 8 lane .. 8 lane + 7
+      if (bits) atomicOr(&pr->cact[lane >> 2], bits << (8 * (lane & 3)));
     }
   }
   if (lane == 0) pr->cv[kTChildren] = R.nsrc;
@@ -304,7 +322,7 @@ __device__ __forceinline__ float child_dist2(int ch, float side, float cside, co
 // the round's targets is compacted in child order with the offsets of their
 // sources.  Returns the union's source count.  Called by the whole warp.
 __device__ __forceinline__ int prune_round(bool valid, int sub, int lane, const float3& pi, float Rb2,
-                                           float side, float cside, TPrune* pr, int& nh) {
+                                           float side, float cside, TPrune* pr, int& nh, bool need_act = false) {
   // lane sub owns children sub + kTreeTpp k (k < kCh) of every neighbour cell
   constexpr int kCh = 8 / kTreeTpp;
   using Mask = std::conditional_t<(27 * kCh > 32), unsigned long long, uint32_t>;
@@ -314,7 +332,11 @@ __device__ __forceinline__ int prune_round(bool valid, int sub, int lane, const 
 #pragma unroll
       for (int k = 0; k < kCh; ++k) {
         const int ch = 8 * m + sub + kTreeTpp * k;
-        if (pr->cv[ch] < pr->cv[ch + 1] && child_dist2(ch, side, cside, pi) < Rb2) mine |= (Mask)1 << (m * kCh + k);
+        // a target outside the mask reaches only the children with a masked
+        // source (its list serves only reverse pairs to those)
+        if (pr->cv[ch] < pr->cv[ch + 1] && (!need_act || ((pr->cact[ch >> 5] >> (ch & 31)) & 1u)) &&
+            child_dist2(ch, side, cside, pi) < Rb2)
+          mine |= (Mask)1 << (m * kCh + k);
       }
     }
   }
@@ -359,7 +381,8 @@ __device__ __forceinline__ int prune_round(bool valid, int sub, int lane, const 
 // relative to the group corner.  Called by the whole warp.
 __device__ __forceinline__ int tstage_union(int u0, int total, int nh, const TPrune* pr, int lane,
                                             const TGeo& g, const float4* __restrict__ rel,
-                                            const int4* __restrict__ fine, float4* spos, uint32_t* sidx) {
+                                            const int4* __restrict__ fine, float4* spos, uint32_t* sidx,
+                                            const uint8_t* __restrict__ act = nullptr) {
   const int cnt = min(kTCap, total - u0);
   for (int u = lane; u < cnt; u += 32) {
     const int uu = u0 + u;
@@ -375,7 +398,7 @@ __device__ __forceinline__ int tstage_union(int u0, int total, int nh, const TPr
     const int sc = pr->rsc[r];
     const float4 rj = rel[j];
     const float3 p = rel_to(g, rj, fine[j], sc);
-    spos[u] = make_float4(p.x, p.y, p.z, rj.w);
+    spos[u] = make_float4(p.x, p.y, p.z, act != nullptr ? (float)act[j] : rj.w);
     sidx[u] = pack_js(j, sc);
   }
   __syncwarp();
@@ -386,7 +409,7 @@ __device__ __forceinline__ int tstage_union(int u0, int total, int nh, const TPr
 // leaf corner (position and mass, packed index).  Called by the whole warp.
 __device__ __forceinline__ int tstage(int v0, const TRanges& R, int lane, const TGeo& g,
                                       const float4* __restrict__ rel, const int4* __restrict__ fine, float4* spos,
-                                      uint32_t* sidx) {
+                                      uint32_t* sidx, const uint8_t* __restrict__ act = nullptr) {
   const int cnt = min(kTCap, R.nsrc - v0);
   for (int r = 0; r < 27; ++r) {
     const int32_t cm = __shfl_sync(0xffffffffu, R.cum, r);
@@ -398,7 +421,7 @@ __device__ __forceinline__ int tstage(int v0, const TRanges& R, int lane, const 
       const int32_t j = lo + (v - cm);
       const float4 rj = rel[j];
       const float3 p = rel_to(g, rj, fine[j], sc);
-      spos[v - v0] = make_float4(p.x, p.y, p.z, rj.w);
+      spos[v - v0] = make_float4(p.x, p.y, p.z, act != nullptr ? (float)act[j] : rj.w);
       sidx[v - v0] = pack_js(j, sc);
     }
   }
@@ -513,7 +536,9 @@ __device__ __forceinline__ void tdens_write(const sphh::TreeDensityArgs& a, cons
   if (noconv) atomicOr(a.status, SPH_ST_H_NOCONV);
 }
 
-template <int K>
+// kMask: the masked loops (a.act, a.act_pre set); the plain instance carries
+// none of their tests.
+template <int K, bool kMask>
 __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensityArgs a, PhysDev ph) {
   extern __shared__ __align__(16) unsigned char tsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -533,26 +558,36 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
     const GridDev G = a.grid[sim_of_cell(a.grid, a.n_sims, Lf.cell)];
     const TGeo g = leaf_geo(Lf, G);
     const TRanges R = load_ranges(a.ranges, li, lane);
+    if (kMask) {
+      // masked loops: a group without a masked particle in its 27 cells has
+      // no masked target and no masked receiver of a reverse pair
+      const int32_t cum_next = __shfl_down_sync(0xffffffffu, R.cum, 1);
+      const int32_t na = lane < 27 ? a.act_pre[R.lo + (cum_next - R.cum)] - a.act_pre[R.lo] : 0;
+      if (!__any_sync(0xffffffffu, na > 0)) continue;
+    }
     const int nsrc = R.nsrc;
     const float hcap = h_cap<K>(g.side_d, g.L);
     const bool one_chunk = nsrc <= kTCap;
     // children are half the cell (a cell at the deepest level has one child)
     const float cside = Lf.depth < kTreeDepth ? 0.5f * g.side : g.side;
-    if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx);
-    else prune_tables(a.skey, R, Lf.depth, lane, pr);
+    // (masked loops: the staged w is 1 for a masked source, else 0)
+    if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx, kMask ? a.act : nullptr);
+    else prune_tables(a.skey, R, Lf.depth, lane, pr, kMask ? a.act_pre : nullptr);
     for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
       const bool valid = t0 + t < n_t;
       const int32_t ti = a.tgt[t_lo + (valid ? t0 + t : 0)];
       // masked loops: a target outside the mask keeps its h and outputs; its
       // list at its current support only sends reverse pairs to the masked
       // particles (whose forces need every pair within either support)
-      const bool on = valid && (a.act == nullptr || a.act[ti] != 0);
+      const bool on = valid && (!kMask || a.act[ti] != 0);
       const float4 reli = a.rel[ti];
       const int4 fi = a.fine[ti];
       const float3 pi = rel_to(g, reli, fi, kNoShift);
       const float4 vi = a.vel4[ti];
       const float Ri = a.lrad[ti];
       const float R2 = Ri * Ri;
+      // (a target outside the mask lists the masked sources only)
+      const bool all_src = !kMask || on;
       // 1. filter: sources with r < R_i into this lane's list.  A group that
       // does not fit one staging chunk stages, per round, only the children
       // of its 27 cells that some target of the round reaches: a child whose
@@ -562,25 +597,28 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       if (one_chunk) {
         if (valid) {
           for (int k = sub; k < nsrc; k += kTreeTpp) {
-            const float r2 = r2_of(pi, spos[k]);
+            const float4 sk = spos[k];
+            const float r2 = r2_of(pi, sk);
             const int at = min(cnt, kTreeList) * 32 + lane;
             lr2[at] = r2;
             lje[at] = sidx[k];
-            cnt += r2 < R2;
+            cnt += r2 < R2 && (all_src || sk.w != 0.0f);
           }
         }
       } else {
         int nh = 0;
-        const int total = prune_round(valid, sub, lane, pi, R2 * (1.0f + 0x1p-10f), g.side, cside, pr, nh);
+        const int total = prune_round(valid, sub, lane, pi, R2 * (1.0f + 0x1p-10f), g.side, cside, pr, nh,
+                                      valid && !all_src);
         for (int u0 = 0; u0 < total; u0 += kTCap) {
-          const int c = tstage_union(u0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx);
+          const int c = tstage_union(u0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx, kMask ? a.act : nullptr);
           if (valid) {
             for (int k = sub; k < c; k += kTreeTpp) {
-              const float r2 = r2_of(pi, spos[k]);
+              const float4 sk = spos[k];
+              const float r2 = r2_of(pi, sk);
               const int at = min(cnt, kTreeList) * 32 + lane;
               lr2[at] = r2;
               lje[at] = sidx[k];
-              cnt += r2 < R2;
+              cnt += r2 < R2 && (all_src || sk.w != 0.0f);
             }
           }
           __syncwarp();
@@ -644,14 +682,14 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
           const float3 d = pair_vec(g, reli, fi, rj, fj, unpack_s(je));
           tdens_pair<K>(d.x, d.y, d.z, vi, a.vel4[j], rj.w, H, Hinv, s);
           if (!atcap && want_reverse_t(__int_as_float(fj.w), ti, j, lr2[e * 32 + lane], H2, H, g.side) &&
-              (a.act == nullptr || a.act[j] != 0))
+              (!kMask || a.act[j] != 0))
             wm |= (TMark)1 << e;
         }
-      } else if (valid && !queued) {
-        // outside the mask: the reverse pairs to masked receivers only
+      } else if (kMask && valid && !queued) {
+        // outside the mask: the reverse pairs to its listed (masked) sources
         for (int e = 0; e < cnt; ++e) {
           const int32_t j = unpack_j(lje[e * 32 + lane]);
-          if (a.act[j] != 0 && want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side)) wm |= (TMark)1 << e;
+          if (want_reverse(a, ti, j, lr2[e * 32 + lane], H2, H, g.side)) wm |= (TMark)1 << e;
         }
       }
       // reverse pairs from the lists: the warp takes one slot range for the
@@ -900,6 +938,12 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
     const GridDev G = a.grid[sim];
     const TGeo g = leaf_geo(Lf, G);
     const float dt = kFl == kTGradient ? (float)(x.dt_dev != nullptr ? x.dt_dev[sim] : x.dt) : 0.0f;
+    if (a.act != nullptr) {
+      // masked loops: skip a group without a masked target
+      bool any = false;
+      for (int32_t k = lane; k < n_t; k += 32) any = any || a.act[a.tgt[t_lo + k]] != 0;
+      if (!__any_sync(0xffffffffu, any)) continue;
+    }
     for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
       const bool valid = t0 + t < n_t;
       const int32_t ti = a.tgt[t_lo + (valid ? t0 + t : 0)];
@@ -1296,9 +1340,12 @@ namespace sphh {
 using namespace sphk;
 
 __global__ void k_tree_mask(int64_t n, const int32_t* __restrict__ perm, const uint8_t* __restrict__ active,
-                            uint8_t* __restrict__ out) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = active[perm[k]] != 0 ? 1 : 0;
+                            uint8_t* __restrict__ out, int32_t* __restrict__ pre) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t v = k < n && active[perm[k]] != 0 ? 1 : 0;
+    if (k < n) out[k] = v;
+    if (pre != nullptr) pre[k] = v;
+  }
 }
 
 static int tree_blocks(int64_t n) {
@@ -1310,12 +1357,14 @@ template <int K>
 static cudaError_t launch_tree_density_k(const TreeDensityArgs& a, const PhysDev& ph, cudaStream_t st) {
   static int bps = 0;
   if (!bps) {
-    cudaError_t e = cudaFuncSetAttribute(k_tree_density<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tree_density<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTDensSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tree_density<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTDensSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_tree_density_fb<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTDensSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_density<K>, kTWarps * 32, kTDensSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_tree_density<K, false>, kTWarps * 32, kTDensSmem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
   }
@@ -1328,7 +1377,10 @@ static cudaError_t launch_tree_density_k(const TreeDensityArgs& a, const PhysDev
   if (e == cudaSuccess) e = cudaMemsetAsync(a.rev_fill, 0, sizeof(int32_t) * (n > 0 ? n : 1), st);
   if (e != cudaSuccess) return e;
   if (n <= 0) return cudaSuccess;
-  k_tree_density<K><<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
+  if (a.act != nullptr)
+    k_tree_density<K, true><<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
+  else
+    k_tree_density<K, false><<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
   k_tree_density_fb<K><<<a.num_sms * bps, kTWarps * 32, kTDensSmem, st>>>(a, ph);
   e = scan_exclusive_host_n(a.rev_start, n + 1, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
@@ -1404,9 +1456,14 @@ cudaError_t launch_tree_wake(const TreeForceArgs& a, const PhysDev& ph, cudaStre
   return launch_tree_force_fl<kTWake>(a, ph, SphenixDev{}, st);
 }
 
-cudaError_t launch_tree_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* out, cudaStream_t st) {
+cudaError_t launch_tree_mask(int64_t n, const int32_t* perm, const uint8_t* active, uint8_t* out, int32_t* pre,
+                             int32_t* tmp, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_tree_mask<<<tree_blocks(n), 256, 0, st>>>(n, perm, active, out);
+  k_tree_mask<<<tree_blocks(n + 1), 256, 0, st>>>(n, perm, active, out, pre);
+  if (pre != nullptr) {
+    const cudaError_t e = scan_exclusive_host_n(pre, n + 1, tmp, st);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
