@@ -1175,20 +1175,46 @@ def run_step(args, world: int, rank: int, local: int):
     cnt.close()
 
     # end to end: the state in pinned host memory, in the device layout; every
-    # step copies x .. v_sig (and the SPHENIX fields) and m in (one copy) and
-    # the same without m out (one copy)
+    # step copies x .. v_sig (and the SPHENIX fields) and m in and the same
+    # without m out.  A step's inputs are the previous step's results as the
+    # host holds them: the read-back of step k and the upload of step k + 1
+    # run in chunks on two streams, each chunk's upload after its own
+    # read-back, so the two directions of the link overlap (every byte still
+    # goes out and comes back through host memory)
     bi = offs["m"] + 4 * n          # x, y, z, v, u, h, a, du/dt, v_sig, [alpha_v, alpha_c, div_v,] m
     bo = offs["m"]                  # the same without m, which a step does not change
     host = torch.empty(bi, dtype=torch.uint8, pin_memory=True)
     host.copy_(dbuf[:bi])
     e2e_ctx = sph.Context(sph.sph_default_params(box_size=L, flags=mode, kernel=kern, **knobs))
+    up = torch.cuda.Stream()
+    n_chunk = 8
+    cuts = [bo * c // n_chunk // 16 * 16 for c in range(n_chunk)] + [bo]
+    ev = [torch.cuda.Event() for _ in range(n_chunk)]
+    up_done = torch.cuda.Event()
+    dbuf[:bi].copy_(host, non_blocking=True)
+    # timed: from the read-back of step 1 to that of step 1 + e2e_steps (the
+    # steps 2 .. 1 + e2e_steps with their uploads, and one read-back more)
     for it in range(2 + args.e2e_steps):
-        if it == 2:
+        if it > 0:
+            stream.wait_event(up_done)   # this step's inputs are in
+        step(e2e_ctx, pool)
+        if it == 1:
             torch.cuda.synchronize()
             e0.record(stream)
-        dbuf[:bi].copy_(host, non_blocking=True)
-        step(e2e_ctx, pool)
-        host[:bo].copy_(dbuf[:bo], non_blocking=True)
+        last = it == 1 + args.e2e_steps
+        if not last:
+            up.wait_stream(stream)
+            with torch.cuda.stream(up):
+                dbuf[bo:bi].copy_(host[bo:bi], non_blocking=True)   # m
+        for c in range(n_chunk):
+            host[cuts[c]:cuts[c + 1]].copy_(dbuf[cuts[c]:cuts[c + 1]], non_blocking=True)
+            if not last:
+                ev[c].record(stream)
+                up.wait_event(ev[c])
+                with torch.cuda.stream(up):
+                    dbuf[cuts[c]:cuts[c + 1]].copy_(host[cuts[c]:cuts[c + 1]], non_blocking=True)
+        if not last:
+            up_done.record(up)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_value, e2e_ms = replicas.job_throughput(n * args.e2e_steps, e0.elapsed_time(e1))
