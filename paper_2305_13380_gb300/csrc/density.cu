@@ -154,7 +154,7 @@ __device__ __forceinline__ void fin_zero(FinSums& s) {
 // 3w + q w' and g = w'(q)/q.
 template <int K>
 __device__ __forceinline__ void fin_pair(const float4& pi, const float4& vi, const float4& pj, const float4& vj,
-                                         float H, float Hinv, FinSums& s) {
+                                         float mj, float H, float Hinv, FinSums& s) {
   const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
@@ -170,10 +170,10 @@ __device__ __forceinline__ void fin_pair(const float4& pi, const float4& vi, con
     kernel_w_g<K>(q, H * rinv, w, g);
     dw = fmaf(q * q, g, 3.0f * w);
   }
-  s.mw = fmaf(pj.w, w, s.mw);
-  s.mdw = fmaf(pj.w, dw, s.mdw);
+  s.mw = fmaf(mj, w, s.mw);
+  s.mdw = fmaf(mj, dw, s.mdw);
   const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
-  const float mg = pj.w * g;
+  const float mg = mj * g;
   s.div = fmaf(mg, fmaf(ux, dx, fmaf(uy, dy, uz * dz)), s.div);
   s.cx = fmaf(mg, fmaf(uz, dy, -uy * dz), s.cx);
   s.cy = fmaf(mg, fmaf(ux, dz, -uz * dx), s.cy);
@@ -298,11 +298,15 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       staged_offset(g, k, ox, oy, oz);
       const int32_t j = T.gstart[k] + (v - T.start[k]);
       float4 p = a.pos4[j];
+      const float4 v4 = a.vel4[j];
       p.x += ox;
       p.y += oy;
       p.z += oz;
-      spos[v] = p;
-      svel[v] = a.vel4[j];
+      // staged: the position about the block centre (|p| < 2 sqrt(3) cells)
+      // with |p|^2 for the filter's expanded distance, the velocity with the
+      // mass (the target's u is read from vel4)
+      spos[v] = make_float4(p.x, p.y, p.z, fmaf(p.x, p.x, fmaf(p.y, p.y, p.z * p.z)));
+      svel[v] = make_float4(v4.x, v4.y, v4.z, p.w);
     }
     if (a.act == nullptr)
       build_targets<K>(g, T, BT, tgt_slot, tgt_cell, nullptr, ph.lanes);  // ends with a barrier
@@ -326,8 +330,10 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       const int32_t ti = T.gstart[kc] + (slot_i - T.start[kc]);  // sorted index
       const float4 pi = spos[slot_i];
       const float4 vi = svel[slot_i];
-      // the starting h, loaded now so that its latency hides behind the filter
+      // the starting h and u, loaded now so that their latency hides behind
+      // the filter
       const float h_start = valid ? a.hs[ti] : 0.0f;
+      const float u_i = valid ? a.vel4[ti].w : 0.0f;
       // 1. filter into the lane's own list column
       int cnt = 0;
       if (valid && a.axis_order != nullptr) {
@@ -374,21 +380,26 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
           }
         }
       } else if (valid) {
-        {
+        // r^2 = |p_i|^2 + |p_j|^2 - 2 p_i . p_j: three FMAs from the staged
+        // |p_j|^2 against R^2 - |p_i|^2.  Its rounding (a few 1e-6 R^2 at
+        // |p| < 2 sqrt(3) cells) lies far inside the 2e-5 R^2 margin, so every
+        // source within R is listed (a listed source just beyond R adds
+        // nothing: the passes recompute r^2 exactly, and the force tests
+        // its own reach)
+        static_assert(!kCacheR2, "the expanded filter keeps no r^2");
+        const float mx = -2.0f * pi.x, my = -2.0f * pi.y, mz = -2.0f * pi.z;
+        const float cthr = fmaf(R2, 2e-5f, R2) - pi.w;
 #pragma unroll 1
-          for (int r = 0; r < 9; ++r) {
-            int32_t A0, B0;
-            warp_run(g, T, tx, ty, tz, r, A0, B0);
+        for (int r = 0; r < 9; ++r) {
+          int32_t A0, B0;
+          warp_run(g, T, tx, ty, tz, r, A0, B0);
 #pragma unroll 4
-            for (int32_t k = A0 + sub; k < B0; k += tpp) {
-              const float4 pj = spos[k];
-              const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const int at = min(cnt, list_cap<K>()) * 32 + lane;
-              if (kCacheR2) lr2[at] = r2;
-              lj[at] = (uint16_t)k;
-              cnt += r2 < R2;
-            }
+          for (int32_t k = A0 + sub; k < B0; k += tpp) {
+            const float4 pj = spos[k];
+            const float tq = fmaf(mz, pj.z, fmaf(my, pj.y, fmaf(mx, pj.x, pj.w)));
+            const int at = min(cnt, list_cap<K>()) * 32 + lane;
+            lj[at] = (uint16_t)k;
+            cnt += tq < cthr;
           }
         }
       }
@@ -522,7 +533,8 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
       if (valid && !direct) {
         for (int e = 0; e < cnt; ++e) {
           const int ka = (int)lj[e * 32 + lane];
-          fin_pair<K>(pi, vi, spos[ka], svel[ka], H, Hinv, s0);
+          const float4 vk = svel[ka];
+          fin_pair<K>(pi, vi, spos[ka], vk, vk.w, H, Hinv, s0);
         }
       }
       if (valid && direct) {
@@ -532,14 +544,17 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
           for (int32_t k = A0 + sub; k < B0; k += tpp) {
             const float4 pj = spos[k];
             const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2) fin_pair<K>(pi, vi, pj, svel[k], H, Hinv, s0);
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2) {
+              const float4 vk = svel[k];
+              fin_pair<K>(pi, vi, pj, vk, vk.w, H, Hinv, s0);
+            }
           }
         }
       }
       fin_combine(s0, tpp);
       fin_scale<K>(s0, H);
       if (valid && sub == 0) {
-        dens_write<K>(a, ph, ti, h, s0, vi.w, passes, conv, atcap);
+        dens_write<K>(a, ph, ti, h, s0, u_i, passes, conv, atcap);
         pair_acc += (unsigned long long)s0.npair;
       }
       __syncwarp();
@@ -619,7 +634,7 @@ __global__ void __launch_bounds__(kThreads) k_density_overflow(sphh::DensityArgs
         fin_zero(s);
         for (int v0 = 0; v0 < nsrc; v0 += kOvfCap) {
           const int cnt = stage_sources(v0, kOvfCap, nb, lane, put);
-          for (int k = 0; k < cnt; ++k) fin_pair<K>(pi, vi, spos[k], svel[k], H, Hinv, s);
+          for (int k = 0; k < cnt; ++k) fin_pair<K>(pi, vi, spos[k], svel[k], spos[k].w, H, Hinv, s);
           __syncwarp();
         }
         fin_scale<K>(s, H);
