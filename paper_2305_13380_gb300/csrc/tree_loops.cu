@@ -277,11 +277,28 @@ __device__ __forceinline__ void prune_tables(const uint64_t* __restrict__ skey, 
     if (depth < kTreeDepth && len > 0) {
       const int sh = 3 * (kTreeDepth - depth - 1);
       const uint64_t base = (skey[R.lo] >> (sh + 3)) << (sh + 3);
-      int64_t pos = R.lo;
-      for (int c = 1; c < 8; ++c) {
-        pos = lower_bound64(skey, pos, (int64_t)R.lo + len, base + ((uint64_t)c << sh));
-        cvr[c] = R.cum + (int32_t)(pos - R.lo);
+      // the seven child boundaries bisected together: each round takes one
+      // step of every search, so its loads are in flight at once (a chain of
+      // log2(len) loads instead of seven such chains)
+      int32_t lo[7], hi[7];
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        lo[c] = R.lo;
+        hi[c] = R.lo + len;
       }
+      for (bool more = true; more;) {
+        more = false;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+          if (lo[c] < hi[c]) {
+            const int32_t mid = (int32_t)(((uint32_t)lo[c] + (uint32_t)hi[c]) >> 1);
+            if (skey[mid] < base + ((uint64_t)(c + 1) << sh)) lo[c] = mid + 1; else hi[c] = mid;
+            more = more || lo[c] < hi[c];
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 7; ++c) cvr[c + 1] = R.cum + (lo[c] - R.lo);
     } else {
       for (int c = 1; c < 8; ++c) cvr[c] = R.cum + len;
     }
