@@ -72,7 +72,9 @@ constexpr int32_t kFbPassive = 1 << 29;
 constexpr int32_t kFbIndex = kFbPassive - 1;
 static_assert(kTWarpSmem % 16 == 0, "per-warp regions keep float4 alignment");
 static_assert(kTreeList <= kTreeListRegion, "published lists fit their regions");
-static_assert(kTreeListRegion % 4 == 0, "lists are published as 16-byte vectors");
+// a target's published list: its lanes' lists packed one after another in a
+// region of kTreeTpp * kTreeListRegion entries, the count in list_cnt[target]
+constexpr int kTreeListTarget = kTreeTpp * kTreeListRegion;
 
 struct TGeo {
   float s_fine;        // side of a fine sub-cell
@@ -713,15 +715,23 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
       // whole round
       emit_marked(a, wm, lje, ti, lane);
       tcombine(s);
-      // 4. publish the list (16-byte vectors) for the force loop
-      if (on) {
-        const int64_t col = (int64_t)ti * kTreeTpp + sub;
-        a.list_cnt[col] = (uint16_t)(atcap || queued ? kListFallback : cnt);
-        if (!queued) {
-          uint4* dst = reinterpret_cast<uint4*>(a.lists + col * kTreeListRegion);
-          for (int e = 0; e < cnt; e += 4)
-            dst[e >> 2] = make_uint4(lje[e * 32 + lane], lje[(e + 1) * 32 + lane], lje[(e + 2) * 32 + lane],
-                                     lje[(e + 3) * 32 + lane]);
+      // 4. publish the list for the force loop: the target's lanes' lists
+      // packed one after another (lane sub's entries after those of the
+      // lanes below it), so that the force reads them in whole sectors
+      {
+        int incl = on && !queued ? cnt : 0;
+#pragma unroll
+        for (int o = 1; o < kTreeTpp; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o, kTreeTpp);
+          if (sub >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, kTreeTpp - 1, kTreeTpp);
+        if (on) {
+          if (sub == 0) a.list_cnt[ti] = (uint16_t)(atcap || queued ? kListFallback : total);
+          if (!queued) {
+            uint32_t* dst = a.lists + (int64_t)ti * kTreeListTarget + (incl - cnt);
+            for (int e = 0; e < cnt; ++e) dst[e] = lje[e * 32 + lane];
+          }
         }
       }
       if (valid && sub == 0) {
@@ -967,8 +977,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
       TFSums s;
       s.ax = s.ay = s.az = s.du = s.vsig = 0.f;
       s.npair = 0;
-      const int64_t col = (int64_t)ti * kTreeTpp + sub;
-      const int lc = (int)a.list_cnt[col];
+      const int lc = (int)a.list_cnt[ti];   // the target's packed list
       const bool fb = lc == kListFallback;  // written by k_tree_force_fb
       const float4 ei = kFl != kTMin ? a.fE[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
       if (kFl == kTGradient) s.ay = ei.y;  // alpha_V,max starts at the target's
@@ -986,8 +995,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_force(sphh::TreeForceArgs
         // to the per-target kernel, kListFallback)
         const float C = a.lrad[ti];
         const float C2 = C * C;
-        const uint32_t* lst = a.lists + col * kTreeListRegion;
-        for (int e = 0; e < lc; ++e) {
+        const uint32_t* lst = a.lists + (int64_t)ti * kTreeListTarget;
+        for (int e = sub; e < lc; e += kTreeTpp) {
           const uint32_t je = lst[e];
           const int32_t j = unpack_j(je);
           if (j == ti) continue;
