@@ -781,19 +781,57 @@ __global__ void k_rev_scatter(const uint64_t* __restrict__ raw, const unsigned l
   }
 }
 
+// A segment of at most N entries sorted in registers: a bitonic network
+// (every index fixed at compile time), padded with the largest key.
+template <int N>
+__device__ __forceinline__ void sort_segment_regs(uint32_t* __restrict__ rev, int32_t b, int32_t len) {
+  uint32_t v[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = k < len ? rev[b + k] : 0xffffffffu;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint32_t x = v[i], y = v[l];
+          const bool up = (i & k) == 0;
+          v[i] = up ? min(x, y) : max(x, y);
+          v[l] = up ? max(x, y) : min(x, y);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (k < len) rev[b + k] = v[k];
+}
+
 // Sorts each receiver's segment by packed source (the slot order above is
-// arbitrary), so the force sums run in a fixed order.
+// arbitrary), so the force sums run in a fixed order: up to 32 entries in
+// registers, longer segments by insertion.
 __global__ void k_rev_sort(int64_t n, const int32_t* __restrict__ start, uint32_t* __restrict__ rev) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t b = start[i], e = start[i + 1];
-    for (int32_t k = b + 1; k < e; ++k) {
-      const uint32_t v = rev[k];
-      int32_t q = k - 1;
-      while (q >= b && rev[q] > v) {
-        rev[q + 1] = rev[q];
-        --q;
+    const int32_t b = start[i], e = start[i + 1], len = e - b;
+    if (len <= 1) continue;
+    if (len <= 8) {
+      sort_segment_regs<8>(rev, b, len);
+    } else if (len <= 16) {
+      sort_segment_regs<16>(rev, b, len);
+    } else if (len <= 32) {
+      sort_segment_regs<32>(rev, b, len);
+    } else {
+      for (int32_t k = b + 1; k < e; ++k) {
+        const uint32_t v = rev[k];
+        int32_t q = k - 1;
+        while (q >= b && rev[q] > v) {
+          rev[q + 1] = rev[q];
+          --q;
+        }
+        rev[q + 1] = v;
       }
-      rev[q + 1] = v;
     }
   }
 }
