@@ -30,8 +30,23 @@ __host__ __device__ constexpr int stage_cap() {
 // lanes per target a lattice lane holds ~28 +- 4).
 constexpr int kLaneListCap = 44;
 // Global neighbour-list region per (target, lane): 48 u16 entries = 96 bytes,
-// written and read as 16-byte vectors so every DRAM sector is written whole.
+// written and read as 16-byte vectors.  The plain lists of a target's lanes
+// lie one after another in the target's 4 regions (list_offset); the
+// symmetric force's lists keep one region per lane.
 constexpr int kListRegion = 48;
+
+// Offset (u16 entries) of lane sub's plain list in its target's regions: the
+// lower lanes' published counts (0xffff: not published) rounded up to
+// 16-byte words.
+__device__ __forceinline__ int list_offset(const uint16_t* __restrict__ list_cnt, int32_t ti, int sub) {
+  const uint2 c = *reinterpret_cast<const uint2*>(list_cnt + (int64_t)ti * 4);
+  const uint32_t n0 = c.x & 0xffffu, n1 = c.x >> 16, n2 = c.y & 0xffffu;
+  int off = 0;
+  if (sub > 0 && n0 != 0xffffu) off += (int)((n0 + 7u) & ~7u);
+  if (sub > 1 && n1 != 0xffffu) off += (int)((n1 + 7u) & ~7u);
+  if (sub > 2 && n2 != 0xffffu) off += (int)((n2 + 7u) & ~7u);
+  return off;
+}
 constexpr int kBlkThreads = 32 * kBlkWarps;
 constexpr int kMaxStaged = 64;  // staged cells per block (4 x 4 x 4)
 

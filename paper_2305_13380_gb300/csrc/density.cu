@@ -424,6 +424,20 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
         const unsigned grp = ((1u << tpp) - 1u) << (lane & ~(tpp - 1));
         pub = pub && (m & grp) == 0u;
       }
+      // a target's lanes' lists are published one after another, each from a
+      // 16-byte word: lane sub's after the lower lanes' counts rounded up to
+      // words (the force reads the target's counts and finds its offset), so
+      // that the lists move in whole sectors
+      int poff = 0;
+      {
+        const int mine = (a.lists != nullptr && valid && !a.upper && pub) ? ((cnt + 7) & ~7) : 0;
+        int incl = mine;
+        for (int o = 1; o < tpp; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o, tpp);
+          if (sub >= o) incl += v;
+        }
+        poff = incl - mine;
+      }
       if (a.lists != nullptr && valid && a.upper) {
         // symmetric force pairs: only the sources later in sorted order, so
         // that each pair is met by one of its two particles
@@ -450,7 +464,7 @@ __global__ void __launch_bounds__(kBlkThreads, kDensMinBlocks) k_density(sphh::D
         const int64_t col = (int64_t)ti * 4 + sub;
         a.list_cnt[col] = (uint16_t)(pub ? cnt : 0xffff);
         if (pub) {
-          uint4* dst = reinterpret_cast<uint4*>(a.lists + col * kListRegion);
+          uint4* dst = reinterpret_cast<uint4*>(a.lists + (int64_t)ti * (4 * kListRegion) + poff);
           for (int e8 = 0; e8 < cnt; e8 += 8) {
             uint32_t w[4];
 #pragma unroll

@@ -225,7 +225,8 @@ __device__ __forceinline__ void fetch_list(const sphh::ForceArgs& a, const Block
   const int32_t ti = T.gstart[kc] + (tgt_slot[e_t] - T.start[kc]);
   const int64_t col = (int64_t)ti * 4 + sub;
   lc = (int)a.list_cnt[col];
-  const uint4* src = reinterpret_cast<const uint4*>(a.lists + col * kListRegion);
+  const uint4* src = reinterpret_cast<const uint4*>(a.lists + (int64_t)ti * (4 * kListRegion) +
+                                                    list_offset(a.list_cnt, ti, sub));
 #pragma unroll
   for (int q = 0; q < kFListEager; ++q) w[q] = src[q];
 #pragma unroll
@@ -559,7 +560,8 @@ __global__ void __launch_bounds__(kBlkThreads, kMinBlocks) k_force_min(sphh::For
       if (valid && a.lists != nullptr) {
         const int64_t col = (int64_t)ti * 4 + sub;
         cnt = (int)a.list_cnt[col];
-        src = reinterpret_cast<const uint4*>(a.lists + col * kListRegion);
+        src = reinterpret_cast<const uint4*>(a.lists + (int64_t)ti * (4 * kListRegion) +
+                                             list_offset(a.list_cnt, ti, sub));
         w = src[0];
       }
       const bool direct = cnt > kFListCap;
