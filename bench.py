@@ -392,10 +392,7 @@ def run_fof(args, world: int, rank: int, local: int):
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
         "roofline": roofline,
-        "roofline_loops": loops,
         "cpu_baseline": cpu,
-        "batched": batched,
-        "served": served,
         "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in kt.items() if v[1]},
         "groups": int(len(counts)), "largest_group": int(counts.max()),
         "particles_in_groups_of_32_or_more": int(counts[counts >= 32].sum()),
