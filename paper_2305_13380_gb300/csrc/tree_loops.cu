@@ -396,6 +396,51 @@ __device__ __forceinline__ int prune_round(bool valid, int sub, int lane, const 
   return run;
 }
 
+// Stages cnt sources into spos / sidx [0, cnt) relative to the group corner
+// (w: the mass, or the mask bit of masked loops); item u is source map(u) (its
+// index and shift code).  A lane takes its items four at a time and issues
+// their loads together, so that four L2 latencies overlap instead of running
+// one after another.  Called by the whole warp.
+template <class Map>
+__device__ __forceinline__ void tstage_items(int cnt, int lane, const TGeo& g, const float4* __restrict__ rel,
+                                             const int4* __restrict__ fine, float4* spos, uint32_t* sidx,
+                                             const uint8_t* __restrict__ act, Map map) {
+  for (int u0 = lane; u0 < cnt; u0 += 4 * 32) {
+    int32_t j[4];
+    int sc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      j[i] = 0;
+      sc[i] = kNoShift;
+      if (u0 + 32 * i < cnt) map(u0 + 32 * i, j[i], sc[i]);
+    }
+    float4 rj[4];
+    int4 fj[4];
+    float aw[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      rj[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      fj[i] = make_int4(0, 0, 0, 0);
+      aw[i] = 0.0f;
+      if (u0 + 32 * i < cnt) {
+        rj[i] = rel[j[i]];
+        fj[i] = fine[j[i]];
+        if (act != nullptr) aw[i] = (float)act[j[i]];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int u = u0 + 32 * i;
+      if (u < cnt) {
+        const float3 p = rel_to(g, rj[i], fj[i], sc[i]);
+        spos[u] = make_float4(p.x, p.y, p.z, act != nullptr ? aw[i] : rj[i].w);
+        sidx[u] = pack_js(j[i], sc[i]);
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // Stages sources [u0, u0 + kTCap) of the round's hit children (flattened)
 // relative to the group corner.  Called by the whole warp.
 __device__ __forceinline__ int tstage_union(int u0, int total, int nh, const TPrune* pr, int lane,
@@ -403,7 +448,7 @@ __device__ __forceinline__ int tstage_union(int u0, int total, int nh, const TPr
                                             const int4* __restrict__ fine, float4* spos, uint32_t* sidx,
                                             const uint8_t* __restrict__ act = nullptr) {
   const int cnt = min(kTCap, total - u0);
-  for (int u = lane; u < cnt; u += 32) {
+  tstage_items(cnt, lane, g, rel, fine, spos, sidx, act, [&](int u, int32_t& j, int& sc) {
     const int uu = u0 + u;
     int lo = 0, hi = nh - 1;
     while (lo < hi) {
@@ -413,38 +458,37 @@ __device__ __forceinline__ int tstage_union(int u0, int total, int nh, const TPr
     const int ch = pr->hch[lo];
     const int vv = pr->cv[ch] + (uu - pr->hoff[lo]);
     const int r = ch >> 3;
-    const int32_t j = pr->rlo[r] + (vv - pr->rcum[r]);
-    const int sc = pr->rsc[r];
-    const float4 rj = rel[j];
-    const float3 p = rel_to(g, rj, fine[j], sc);
-    spos[u] = make_float4(p.x, p.y, p.z, act != nullptr ? (float)act[j] : rj.w);
-    sidx[u] = pack_js(j, sc);
-  }
-  __syncwarp();
+    j = pr->rlo[r] + (vv - pr->rcum[r]);
+    sc = pr->rsc[r];
+  });
   return cnt;
 }
 
 // Stages sources [v0, v0 + kTCap) of the concatenated ranges relative to the
-// leaf corner (position and mass, packed index).  Called by the whole warp.
+// leaf corner (the ranges' first sources, starts and shifts go to pr first).
+// Called by the whole warp.
 __device__ __forceinline__ int tstage(int v0, const TRanges& R, int lane, const TGeo& g,
                                       const float4* __restrict__ rel, const int4* __restrict__ fine, float4* spos,
-                                      uint32_t* sidx, const uint8_t* __restrict__ act = nullptr) {
+                                      uint32_t* sidx, TPrune* pr, const uint8_t* __restrict__ act = nullptr) {
   const int cnt = min(kTCap, R.nsrc - v0);
-  for (int r = 0; r < 27; ++r) {
-    const int32_t cm = __shfl_sync(0xffffffffu, R.cum, r);
-    const int32_t cm1 = __shfl_sync(0xffffffffu, R.cum, r + 1);
-    const int32_t lo = __shfl_sync(0xffffffffu, R.lo, r);
-    const int sc = __shfl_sync(0xffffffffu, R.sc, r);
-    const int a0 = max(cm, v0), b0 = min(cm1, v0 + cnt);
-    for (int v = a0 + lane; v < b0; v += 32) {
-      const int32_t j = lo + (v - cm);
-      const float4 rj = rel[j];
-      const float3 p = rel_to(g, rj, fine[j], sc);
-      spos[v - v0] = make_float4(p.x, p.y, p.z, act != nullptr ? (float)act[j] : rj.w);
-      sidx[v - v0] = pack_js(j, sc);
-    }
+  if (lane < 28) {
+    pr->rlo[lane] = R.lo;
+    pr->rcum[lane] = R.cum;  // lane 27 (an empty range): the total
+    pr->rsc[lane] = R.sc;
   }
   __syncwarp();
+  tstage_items(cnt, lane, g, rel, fine, spos, sidx, act, [&](int u, int32_t& j, int& sc) {
+    const int v = v0 + u;
+    // the last range starting at or before v (an empty range shares its
+    // start with the next one)
+    int lo = 0, hi = 26;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pr->rcum[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    j = pr->rlo[lo] + (v - pr->rcum[lo]);
+    sc = pr->rsc[lo];
+  });
   return cnt;
 }
 
@@ -590,7 +634,7 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
     // children are half the cell (a cell at the deepest level has one child)
     const float cside = Lf.depth < kTreeDepth ? 0.5f * g.side : g.side;
     // (masked loops: the staged w is 1 for a masked source, else 0)
-    if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx, kMask ? a.act : nullptr);
+    if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx, pr, kMask ? a.act : nullptr);
     else prune_tables(a.skey, R, Lf.depth, lane, pr, kMask ? a.act_pre : nullptr);
     for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
       const bool valid = t0 + t < n_t;
