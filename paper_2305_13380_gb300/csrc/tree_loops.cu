@@ -340,11 +340,16 @@ __device__ __forceinline__ float child_dist2(int ch, float side, float cside, co
 // 27 children each (ch = sub + 8 m) against its list radius, the union over
 // the round's targets is compacted in child order with the offsets of their
 // sources.  Returns the union's source count.  Called by the whole warp.
+// lane sub owns children sub + kTreeTpp k (k < kCh) of every neighbour cell:
+// bit m kCh + k of a lane's child mask
+constexpr int kCh = 8 / kTreeTpp;
+using ChMask = std::conditional_t<(27 * kCh > 32), unsigned long long, uint32_t>;
+
+__device__ __forceinline__ int union_round(ChMask mine, int lane, TPrune* pr, int& nh);
+
 __device__ __forceinline__ int prune_round(bool valid, int sub, int lane, const float3& pi, float Rb2,
                                            float side, float cside, TPrune* pr, int& nh, bool need_act = false) {
-  // lane sub owns children sub + kTreeTpp k (k < kCh) of every neighbour cell
-  constexpr int kCh = 8 / kTreeTpp;
-  using Mask = std::conditional_t<(27 * kCh > 32), unsigned long long, uint32_t>;
+  using Mask = ChMask;
   Mask mine = 0;
   if (valid) {
     for (int m = 0; m < 27; ++m) {
@@ -359,6 +364,63 @@ __device__ __forceinline__ int prune_round(bool valid, int sub, int lane, const 
       }
     }
   }
+  return union_round(mine, lane, pr, nh);
+}
+
+// The lane's candidate children of a group (bits as above): those holding a
+// source, and (mask_only) a masked one.  Called once per group, after
+// prune_tables.
+__device__ __forceinline__ ChMask group_candidates(int sub, const TPrune* pr, bool mask_only) {
+  ChMask c = 0;
+  for (int m = 0; m < 27; ++m) {
+#pragma unroll
+    for (int k = 0; k < kCh; ++k) {
+      const int ch = 8 * m + sub + kTreeTpp * k;
+      if (pr->cv[ch] < pr->cv[ch + 1] && (!mask_only || ((pr->cact[ch >> 5] >> (ch & 31)) & 1u)))
+        c |= (ChMask)1 << (m * kCh + k);
+    }
+  }
+  return c;
+}
+
+// prune_round with the candidates precomputed per group and the box
+// distances taken per axis: along each axis a lane's child boxes take three
+// positions (the neighbour offset, its child bit fixed), so nine squared
+// distances give all 27 (the sum's rounding lies far inside the margin of
+// Rb2).
+__device__ __forceinline__ int prune_round_fast(bool valid, int sub, int lane, const float3& pi, float Rb2,
+                                                float side, float cside, TPrune* pr, int& nh, ChMask cand) {
+  ChMask mine = 0;
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < kCh; ++k) {
+      const int c = sub + kTreeTpp * k;
+      const float cx = (float)(c & 1) * cside, cy = (float)((c >> 1) & 1) * cside, cz = (float)(c >> 2) * cside;
+      float ex[3], ey[3], ez[3];
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        const float b0 = (float)(o - 1) * side;
+        const float dx = fmaxf(fmaxf(b0 + cx - pi.x, pi.x - (b0 + cx + cside)), 0.0f);
+        const float dy = fmaxf(fmaxf(b0 + cy - pi.y, pi.y - (b0 + cy + cside)), 0.0f);
+        const float dz = fmaxf(fmaxf(b0 + cz - pi.z, pi.z - (b0 + cz + cside)), 0.0f);
+        ex[o] = dx * dx;
+        ey[o] = dy * dy;
+        ez[o] = dz * dz;
+      }
+#pragma unroll
+      for (int m = 0; m < 27; ++m) {
+        const ChMask bit = (ChMask)1 << (m * kCh + k);
+        if ((cand & bit) && ex[m % 3] + ey[(m / 3) % 3] + ez[m / 9] < Rb2) mine |= bit;
+      }
+    }
+  }
+  return union_round(mine, lane, pr, nh);
+}
+
+// The union over the round's targets of their children, compacted in child
+// order with the offsets of their sources; returns the union's source count.
+// Called by the whole warp.
+__device__ __forceinline__ int union_round(ChMask mine, int lane, TPrune* pr, int& nh) {
 #pragma unroll
   for (int o = kTreeTpp; o < 32; o <<= 1) mine |= __shfl_xor_sync(0xffffffffu, mine, o);
   // lanes 0..kTreeTpp-1 hold the union; compacted in child order
@@ -634,8 +696,14 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
     // children are half the cell (a cell at the deepest level has one child)
     const float cside = Lf.depth < kTreeDepth ? 0.5f * g.side : g.side;
     // (masked loops: the staged w is 1 for a masked source, else 0)
-    if (one_chunk) tstage(0, R, lane, g, a.rel, a.fine, spos, sidx, pr, kMask ? a.act : nullptr);
-    else prune_tables(a.skey, R, Lf.depth, lane, pr, kMask ? a.act_pre : nullptr);
+    ChMask cand_all = 0, cand_act = 0;
+    if (one_chunk) {
+      tstage(0, R, lane, g, a.rel, a.fine, spos, sidx, pr, kMask ? a.act : nullptr);
+    } else {
+      prune_tables(a.skey, R, Lf.depth, lane, pr, kMask ? a.act_pre : nullptr);
+      cand_all = group_candidates(sub, pr, false);
+      if (kMask) cand_act = group_candidates(sub, pr, true);
+    }
     for (int32_t t0 = 0; t0 < n_t; t0 += kTPer) {
       const bool valid = t0 + t < n_t;
       const int32_t ti = a.tgt[t_lo + (valid ? t0 + t : 0)];
@@ -670,8 +738,8 @@ __global__ void __launch_bounds__(kTWarps * 32) k_tree_density(sphh::TreeDensity
         }
       } else {
         int nh = 0;
-        const int total = prune_round(valid, sub, lane, pi, R2 * (1.0f + 0x1p-10f), g.side, cside, pr, nh,
-                                      valid && !all_src);
+        const int total = prune_round_fast(valid, sub, lane, pi, R2 * (1.0f + 0x1p-10f), g.side, cside, pr, nh,
+                                           all_src ? cand_all : cand_act);
         for (int u0 = 0; u0 < total; u0 += kTCap) {
           const int c = tstage_union(u0, total, nh, pr, lane, g, a.rel, a.fine, spos, sidx, kMask ? a.act : nullptr);
           if (valid) {
