@@ -43,6 +43,7 @@ struct sph_ctx {
   float* hs = nullptr;
   float2* fD = nullptr;
   unsigned* dt_bits = nullptr;
+  float* dt_f = nullptr;  // per simulation: 0.5 dt, dt / 3 (FP32)
   int32_t* hmax_bits = nullptr;
   uint16_t *lists = nullptr, *list_cnt = nullptr;
   bool lists_valid = false;  // lists belong to the current build
@@ -144,6 +145,7 @@ void free_grown(sph_ctx* c) {
   dfree(c->hs);
   dfree(c->fD);
   dfree(c->dt_bits);
+  dfree(c->dt_f);
   dfree(c->hmax_bits);
   dfree(c->lists);
   dfree(c->list_cnt);
@@ -242,7 +244,7 @@ int ensure(sph_ctx* c, int64_t n, int n_sims, int cells_per_particle = 8) {
             dalloc(c->rk, cn) && dalloc(c->rv, cn) && dalloc(c->rhist, sphh::radix_hist_words(cn)) &&
             dalloc(c->overflow, (8 * cn + 216 * (int64_t)cs) / 3 + 2) && dalloc(c->pos4, cn) &&
             dalloc(c->vel4, cn) && dalloc(c->th4, cn) && dalloc(c->hs, cn) && dalloc(c->fD, cn) &&
-            dalloc(c->dt_bits, cs) && dalloc(c->hmax_bits, cs) &&
+            dalloc(c->dt_bits, cs) && dalloc(c->dt_f, 2 * cs) && dalloc(c->hmax_bits, cs) &&
             dalloc(c->lists, (int64_t)sphk::kListRegion * 4 * cn) &&
             dalloc(c->list_cnt, (int64_t)(sphk::kTreeTpp > 4 ? sphk::kTreeTpp : 4) * cn) &&
             dalloc(c->vpx, cn) && dalloc(c->vpy, cn) && dalloc(c->vpz, cn) && dalloc(c->up, cn) &&
@@ -1226,6 +1228,7 @@ int step_impl(sph_ctx* c, const sph_pool* pl, const sph_sphenix_params* X, float
   s.up = c->up;
   s.dt = pl->dt;
   s.dt_bits = c->dt_bits;
+  s.dt_f = c->dt_f;
   s.status = c->misc + sphk::kStatus;
   s.h_guess = pl->h;
   s.div_v = pl->div_v;

@@ -454,6 +454,10 @@ struct StepArgs {
   float *vpx, *vpy, *vpz, *up;  // predicted velocity / energy (scratch)
   double* dt;                   // per simulation
   unsigned* dt_bits;  // per simulation scratch (min of h / v_sig as FP32 bits)
+  // per simulation: 0.5 dt and dt / 3 rounded to FP32, written by launch_dt
+  // with dt (the kicks read them instead of each thread deriving them in
+  // FP64, which this GPU runs at a small fraction of its FP32 rate)
+  float* dt_f;
   int32_t* status;
   // starting guess of the next density loop: h_guess = h (1 + div_v dt / 3)
   // (nullptr: keep h)

@@ -62,10 +62,13 @@ __global__ void k_dt_min(const int64_t* __restrict__ sim_offset, int n_sims, int
 }
 
 __global__ void k_dt_final(const unsigned* __restrict__ bits, int n_sims, double cfl, double gamma_k,
-                           double* __restrict__ dt) {
+                           double* __restrict__ dt, float* __restrict__ dt_f) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x) {
     const float m = __uint_as_float(bits[s]);
-    dt[s] = isinf(m) ? 0.0 : cfl * gamma_k * (double)m;
+    const double d = isinf(m) ? 0.0 : cfl * gamma_k * (double)m;
+    dt[s] = d;
+    dt_f[2 * s] = (float)(0.5 * d);
+    dt_f[2 * s + 1] = (float)(d / 3.0);
   }
 }
 
@@ -92,12 +95,12 @@ __global__ void k_kick_drift(sphh::StepArgs a) {
   SimCursor sc;
   for (int64_t p = wr.lo + (threadIdx.x & 31); p < wr.hi; p += 32) {
     const int s = sc.at(a.sim_offset, a.n_sims, p);
-    if (s != cur) {  // the simulation's dt and box, converted once
+    if (s != cur) {  // the simulation's dt and box (0.5 dt and dt / 3 in FP32)
       cur = s;
       dt = a.dt[s];
       L = a.box[s];
-      hdt = (float)(0.5 * dt);
-      dt3 = (float)(dt / 3.0);
+      hdt = a.dt_f[2 * s];
+      dt3 = a.dt_f[2 * s + 1];
     }
     const float vx = fmaf(hdt, a.ax[p], a.vx[p]);
     const float vy = fmaf(hdt, a.ay[p], a.vy[p]);
@@ -136,7 +139,7 @@ __global__ void k_kick(sphh::StepArgs a) {
     const int s = sc.at(a.sim_offset, a.n_sims, p);
     if (s != cur) {
       cur = s;
-      hdt = (float)(0.5 * a.dt[s]);
+      hdt = a.dt_f[2 * s];
     }
     a.vx[p] = fmaf(hdt, a.ax[p], a.vx[p]);
     a.vy[p] = fmaf(hdt, a.ay[p], a.vy[p]);
@@ -204,7 +207,7 @@ cudaError_t launch_dt(const StepArgs& a, cudaStream_t st) {
     if (b > cap) b = cap;
     k_dt_min<<<(int)b, 256, 0, st>>>(a.sim_offset, a.n_sims, a.n_total, a.h, a.v_sig, a.dt_bits);
   }
-  k_dt_final<<<sb, 256, 0, st>>>(a.dt_bits, a.n_sims, a.cfl, a.gamma_k, a.dt);
+  k_dt_final<<<sb, 256, 0, st>>>(a.dt_bits, a.n_sims, a.cfl, a.gamma_k, a.dt, a.dt_f);
   return cudaGetLastError();
 }
 cudaError_t launch_kick_drift(const StepArgs& a, cudaStream_t st) {
