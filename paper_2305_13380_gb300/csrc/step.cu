@@ -86,6 +86,19 @@ __device__ __forceinline__ double wrap1(double x, double L) {
   return x;
 }
 
+// Widening of a float to double (exact): a normal float's sign, exponent
+// rebiased from 127 to 1023 and its 23 fraction bits at the top of the 52,
+// built with integer operations (this GPU's FP64 pipe, which a conversion
+// instruction would use, is slow); zero, subnormals, infinities and NaN take
+// the native conversion.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const uint64_t d = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 // First half kick, drift (FP64, one periodic wrap), prediction for the loops.
 __global__ void k_kick_drift(sphh::StepArgs a) {
   int cur = -1;
@@ -110,9 +123,9 @@ __global__ void k_kick_drift(sphh::StepArgs a) {
     a.vy[p] = vy;
     a.vz[p] = vz;
     a.u[p] = u;
-    a.x[p] = wrap1(fma((double)vx, dt, a.x[p]), L);
-    a.y[p] = wrap1(fma((double)vy, dt, a.y[p]), L);
-    a.z[p] = wrap1(fma((double)vz, dt, a.z[p]), L);
+    a.x[p] = wrap1(fma(widen(vx), dt, a.x[p]), L);
+    a.y[p] = wrap1(fma(widen(vy), dt, a.y[p]), L);
+    a.z[p] = wrap1(fma(widen(vz), dt, a.z[p]), L);
     a.vpx[p] = fmaf(hdt, a.ax[p], vx);
     a.vpy[p] = fmaf(hdt, a.ay[p], vy);
     a.vpz[p] = fmaf(hdt, a.az[p], vz);
