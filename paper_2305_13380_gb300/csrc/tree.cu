@@ -82,7 +82,10 @@ __global__ void k_tree_level(int64_t n, const uint64_t* __restrict__ skey, const
     const double reach = (1.0 + margin) * (double)(gamma_k * h[perm[s]]);
     int64_t lo = cell_start[c], hi = cell_start[c + 1];
     int d = 0;
-    for (;; ++d) {
+    // the side of level d + 1, G.cell / 2^(d + 1), by exact halvings (no
+    // FP64 division: this GPU's FP64 pipe is slow)
+    double side_next = 0.5 * G.cell;
+    for (;; ++d, side_next *= 0.5) {
       if (d > 0) {
         const int sh = 3 * (kTreeDepth - d);
         const uint64_t pre = key >> sh;
@@ -90,10 +93,10 @@ __global__ void k_tree_level(int64_t n, const uint64_t* __restrict__ skey, const
         hi = lower_bound64(skey, lo, hi, (pre + 1) << sh);
       }
       if (d == kTreeDepth || hi - lo <= n_leaf) break;
-      if (G.cell / (double)(1 << (d + 1)) < reach) break;
+      if (side_next < reach) break;
     }
     level[s] = (int8_t)d;
-    leaf_side[s] = G.cell_f / (float)(1 << d);
+    leaf_side[s] = G.cell_f * __int_as_float((127 - d) << 23);  // G.cell_f / 2^d, exact
     const int sh = 3 * (kTreeDepth - d);
     const uint64_t m = ((key & 0x3fffffffull) >> sh) << sh;
     const uint64_t t = ((uint64_t)(uint32_t)c << 34) | (m << 4) | (uint64_t)d;

@@ -94,7 +94,7 @@ __device__ __forceinline__ TGeo leaf_geo(const TreeLeaf& Lf, const GridDev& G) {
   g.oy = ky * kTreeFine + (Lf.ly << sh);
   g.oz = kz * kTreeFine + (Lf.lz << sh);
   g.s_fine = (float)(G.cell / (double)kTreeFine);
-  g.side_d = G.cell / (double)(1 << Lf.depth);
+  g.side_d = G.cell * __longlong_as_double((long long)(1023 - Lf.depth) << 52);  // G.cell / 2^depth, exact
   g.side = (float)g.side_d;
   g.nfine = nc * kTreeFine;
   g.L = G.L;
