@@ -71,7 +71,7 @@ __global__ void k_tree_sorted(int64_t n, const int32_t* __restrict__ perm, const
 // level and cell side, and its target key (top cell, Morton prefix of its cell at that
 // level, level) with a copy for the sort.
 __global__ void k_tree_level(int64_t n, const uint64_t* __restrict__ skey, const int32_t* __restrict__ perm,
-                             const float* __restrict__ h, const int32_t* __restrict__ cell_start, int n_sims,
+                             const float* __restrict__ h, int n_sims,
                              const GridDev* __restrict__ grid, int n_leaf, double margin, float gamma_k,
                              int8_t* __restrict__ level, float* __restrict__ leaf_side,
                              uint64_t* __restrict__ tkey, uint64_t* __restrict__ tkey_copy) {
@@ -80,19 +80,27 @@ __global__ void k_tree_level(int64_t n, const uint64_t* __restrict__ skey, const
     const int32_t c = (int32_t)(key >> 30);
     const GridDev G = grid[sim_of_cell(grid, n_sims, c)];
     const double reach = (1.0 + margin) * (double)(gamma_k * h[perm[s]]);
-    int64_t lo = cell_start[c], hi = cell_start[c + 1];
+    // A cell holding s has at most n_leaf particles only if it lies within
+    // (s - n_leaf, s + n_leaf) in source order: if the key n_leaf places away
+    // on either side shares its prefix, the cell holds more; else its bounds
+    // are searched in that window (a few loads near s, instead of bisecting
+    // each level's cell from its parent's range)
+    const int64_t wl = s - n_leaf, wr = s + n_leaf;
+    const uint64_t kl = wl >= 0 ? skey[wl] : 0ull, kr = wr < n ? skey[wr] : 0ull;
     int d = 0;
     // the side of level d + 1, G.cell / 2^(d + 1), by exact halvings (no
     // FP64 division: this GPU's FP64 pipe is slow)
     double side_next = 0.5 * G.cell;
     for (;; ++d, side_next *= 0.5) {
-      if (d > 0) {
-        const int sh = 3 * (kTreeDepth - d);
-        const uint64_t pre = key >> sh;
-        lo = lower_bound64(skey, lo, hi, pre << sh);
-        hi = lower_bound64(skey, lo, hi, (pre + 1) << sh);
+      const int sh = 3 * (kTreeDepth - d);
+      const uint64_t pre = key >> sh;
+      bool small = false;  // the cell holds at most n_leaf particles
+      if (!((wl >= 0 && (kl >> sh) == pre) || (wr < n && (kr >> sh) == pre))) {
+        const int64_t lo = lower_bound64(skey, wl + 1 > 0 ? wl + 1 : 0, s + 1, pre << sh);
+        const int64_t hi = lower_bound64(skey, s + 1, wr < n ? wr : n, (pre + 1) << sh);
+        small = hi - lo <= n_leaf;
       }
-      if (d == kTreeDepth || hi - lo <= n_leaf) break;
+      if (d == kTreeDepth || small) break;
       if (side_next < reach) break;
     }
     level[s] = (int8_t)d;
@@ -227,7 +235,7 @@ cudaError_t launch_tree_build(const TreeBuildArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   k_tree_sorted<<<blocks_n(n), 256, 0, st>>>(n, a.perm, a.key64, a.skey);
   // levels and target order: (top cell, cell at the level, level), ties by source index
-  k_tree_level<<<blocks_n(n), 256, 0, st>>>(n, a.skey, a.perm, a.h, a.cell_start, a.n_sims, a.grid, a.n_leaf,
+  k_tree_level<<<blocks_n(n), 256, 0, st>>>(n, a.skey, a.perm, a.h, a.n_sims, a.grid, a.n_leaf,
                                             a.margin, a.gamma_k, a.level, a.leaf_side, a.key64, a.key64_b);
   e = radix_sort_index64(n, 34 + cbits, a.key64_b, a.key64_c, a.tgt, a.rv, a.hist, st);
   if (e != cudaSuccess) return e;
